@@ -1,0 +1,500 @@
+/*
+ * cc_oracle.c -- plain serial FP64 oracle of the CC split integrator
+ * (arXiv:1407.7105, Sec. 2).  TEST INFRASTRUCTURE ONLY: used by tests/,
+ * __graft_entry__.smoke() and bench.py's CPU baseline; never by the CUDA
+ * product path.  Build: gcc -O2 -ffp-contract=off -fPIC -shared.
+ *
+ * Readings of the paper taken here (each one is listed in the design doc):
+ *  R1  tau_freefall / tau_flyby are not defined in the paper (it defers to
+ *      Pelupessy et al. 2012).  From first principles, for the pair
+ *      dx = x_i - x_j, dv = v_i - v_j, r^2 = |dx|^2 + eps^2, mu = G(m_i+m_j):
+ *        T_ff  = eta * sqrt(r^3 / mu)              (free-fall time)
+ *        T_fb  = eta * r / |dv|                    (flyby time, +inf if dv = 0)
+ *        dT_ff/dt = 3/2 * T_ff * (dx.dv) / r^2
+ *        dT_fb/dt = T_fb * (dx.dv)/r^2 * (1 + mu / (r |dv|^2))
+ *      the last from differentiating r/|dv| with the pair's own relative
+ *      acceleration -mu dx / r^3.
+ *  R2  eta sits inside T and dT/dt (the approximately time-symmetric step
+ *      T/(1 - T'/2) needs the derivative of the actual step); the literal
+ *      placement, eta multiplying the min of Eq. (tauij), is selectable.
+ *  R3  dT/dt is clamped at 1 before the denominator, so tau <= 2T > 0.
+ *  R4  the edge test is strict: tau(i,j) < h (Sec. 2.2).
+ *  R5  kick order: for each i of the set in ascending id, a_i is summed
+ *      over j in ascending id, then v_i += h a_i.
+ *
+ * Exact operation order (no FMA, IEEE sqrt and division), for the pair:
+ *   r2  = ((dx0*dx0 + dx1*dx1) + dx2*dx2) + eps2,  eps2 = eps*eps
+ *   r   = sqrt(r2)
+ *   v2  = (dv0*dv0 + dv1*dv1) + dv2*dv2
+ *   rv  = (dx0*dv0 + dx1*dv1) + dx2*dv2
+ *   mu  = G * (mi + mj)
+ *   Tff = eta * sqrt((r2 * r) / mu)
+ *   dTff = ((1.5 * Tff) * rv) / r2
+ *   Tfb = eta * (r / sqrt(v2))                         (v2 > 0)
+ *   dTfb = (Tfb * (rv / r2)) * (1.0 + mu / (r * v2))
+ *   c(d) = d < 1.0 ? d : 1.0
+ *   tau_ff = Tff / (1.0 - 0.5 * c(dTff)),  tau_fb likewise (+inf if v2 == 0)
+ *   tau = tau_ff < tau_fb ? tau_ff : tau_fb
+ */
+#include "cc_oracle.h"
+#include <math.h>
+#include <stdlib.h>
+#include <string.h>
+
+/* ------------------------------------------------------------------ */
+/* tau(i,j), Eq. (tauij)                                               */
+/* ------------------------------------------------------------------ */
+static double clamp1(double d) { return d < 1.0 ? d : 1.0; }
+
+double orc_tau(const double *xi, const double *vi, double mi,
+               const double *xj, const double *vj, double mj,
+               const orc_params *p, double *parts)
+{
+    double dx0 = xi[0] - xj[0], dx1 = xi[1] - xj[1], dx2 = xi[2] - xj[2];
+    double dv0 = vi[0] - vj[0], dv1 = vi[1] - vj[1], dv2 = vi[2] - vj[2];
+    double eps2 = p->eps * p->eps;
+    double r2 = ((dx0 * dx0 + dx1 * dx1) + dx2 * dx2) + eps2;
+    double r = sqrt(r2);
+    double v2 = (dv0 * dv0 + dv1 * dv1) + dv2 * dv2;
+    double rv = (dx0 * dv0 + dx1 * dv1) + dx2 * dv2;
+    double mu = p->G * (mi + mj);
+    double e_in = p->eta_outside ? 1.0 : p->eta;
+
+    double Tff = e_in * sqrt((r2 * r) / mu);
+    double dTff = ((1.5 * Tff) * rv) / r2;
+    double tau_ff = Tff / (1.0 - 0.5 * clamp1(dTff));
+
+    double Tfb = INFINITY, dTfb = 0.0, tau_fb = INFINITY;
+    if (v2 > 0.0) {
+        Tfb = e_in * (r / sqrt(v2));
+        dTfb = (Tfb * (rv / r2)) * (1.0 + mu / (r * v2));
+        tau_fb = Tfb / (1.0 - 0.5 * clamp1(dTfb));
+    }
+    double tau = tau_ff < tau_fb ? tau_ff : tau_fb;
+    if (p->eta_outside) tau = p->eta * tau;
+    if (parts) {
+        parts[0] = Tff; parts[1] = dTff; parts[2] = Tfb;
+        parts[3] = dTfb; parts[4] = tau_ff; parts[5] = tau_fb;
+    }
+    return tau;
+}
+
+double orc_tau_ids(int64_t n, const double *x3, const double *v3, const double *m,
+                   const orc_params *p, int64_t i, int64_t j)
+{
+    /* evaluate with the smaller id first so tau(i,j) and tau(j,i) take the
+     * same path (they are equal bitwise anyway: negation is exact) */
+    if (j < i) { int64_t t = i; i = j; j = t; }
+    double xi[3] = {x3[i], x3[n + i], x3[2 * n + i]};
+    double xj[3] = {x3[j], x3[n + j], x3[2 * n + j]};
+    double vi[3] = {v3[i], v3[n + i], v3[2 * n + i]};
+    double vj[3] = {v3[j], v3[n + j], v3[2 * n + j]};
+    return orc_tau(xi, vi, m[i], xj, vj, m[j], p, NULL);
+}
+
+/* ------------------------------------------------------------------ */
+/* split_cc: breadth-first search over lazily evaluated tau (Sec. 2.3)  */
+/* ------------------------------------------------------------------ */
+int64_t orc_components(int64_t n, const double *x3, const double *v3, const double *m,
+                       const orc_params *p, const int32_t *set, int64_t nset,
+                       double h, int32_t *labels_out, orc_stats *st)
+{
+    if (nset < 0) return ORC_E_ARG;
+    int64_t *queue = (int64_t *)malloc(sizeof(int64_t) * (nset > 0 ? nset : 1));
+    char *assigned = (char *)calloc(nset > 0 ? nset : 1, 1);
+    int64_t ncomp = 0;
+    if (st) {
+        st->splits++;
+        st->tau_pairs += (uint64_t)(nset * (nset - 1) / 2);
+    }
+    /* seeds are taken in ascending id, so every member found from a seed
+     * has a larger id and the seed id is the smallest id of the component */
+    for (int64_t s = 0; s < nset; ++s) {
+        if (assigned[s]) continue;
+        assigned[s] = 1;
+        labels_out[s] = set[s];
+        int64_t qh = 0, qt = 0, size = 1;
+        queue[qt++] = s;
+        while (qh < qt) {
+            int64_t X = queue[qh++];
+            /* assign to X's component every unassigned U with tau(X,U) < h */
+            for (int64_t U = 0; U < nset; ++U) {
+                if (assigned[U]) continue;
+                double t = orc_tau_ids(n, x3, v3, m, p, set[X], set[U]);
+                if (st) st->tau_evals++;
+                if (t < h) {
+                    assigned[U] = 1;
+                    labels_out[U] = set[s];
+                    queue[qt++] = U;
+                    size++;
+                }
+            }
+        }
+        if (size >= 2) ncomp++;
+    }
+    if (st) st->components += (uint64_t)ncomp;
+    free(queue);
+    free(assigned);
+    return ncomp;
+}
+
+int64_t orc_edges(int64_t n, const double *x3, const double *v3, const double *m,
+                  const orc_params *p, const int32_t *set, int64_t nset, double h,
+                  int32_t *edges_out, int64_t cap, double near_tol, int64_t *n_near)
+{
+    int64_t ne = 0, nn = 0;
+    for (int64_t a = 0; a < nset; ++a) {
+        for (int64_t b = a + 1; b < nset; ++b) {
+            double t = orc_tau_ids(n, x3, v3, m, p, set[a], set[b]);
+            if (fabs(t - h) < near_tol * h) nn++;
+            if (t < h) {
+                if (ne < cap && edges_out) {
+                    int32_t i = set[a], j = set[b];
+                    edges_out[2 * ne] = i < j ? i : j;
+                    edges_out[2 * ne + 1] = i < j ? j : i;
+                }
+                ne++;
+            }
+        }
+    }
+    if (n_near) *n_near = nn;
+    return ne;
+}
+
+/* ------------------------------------------------------------------ */
+/* kick and drift (Eqs. drift, kickij, kickji)                          */
+/* ------------------------------------------------------------------ */
+void orc_kick(int64_t n, const double *x3, double *v3, const double *m,
+              const orc_params *p, const int32_t *set, const int32_t *labels,
+              int64_t nset, double h, orc_stats *st)
+{
+    double eps2 = p->eps * p->eps;
+    double *acc = (double *)calloc((size_t)(3 * (nset > 0 ? nset : 1)), sizeof(double));
+    uint64_t pairs = 0;
+    for (int64_t a = 0; a < nset; ++a) {
+        int64_t i = set[a];
+        double ax = 0.0, ay = 0.0, az = 0.0;
+        for (int64_t b = 0; b < nset; ++b) {
+            if (b == a || labels[b] == labels[a]) continue;
+            int64_t j = set[b];
+            if (b > a) pairs++;
+            double dx0 = x3[j] - x3[i];
+            double dx1 = x3[n + j] - x3[n + i];
+            double dx2 = x3[2 * n + j] - x3[2 * n + i];
+            double r2 = ((dx0 * dx0 + dx1 * dx1) + dx2 * dx2) + eps2;
+            double rinv3 = 1.0 / (r2 * sqrt(r2));
+            double w = (p->G * m[j]) * rinv3;
+            ax = ax + w * dx0;
+            ay = ay + w * dx1;
+            az = az + w * dx2;
+        }
+        acc[3 * a] = ax; acc[3 * a + 1] = ay; acc[3 * a + 2] = az;
+    }
+    for (int64_t a = 0; a < nset; ++a) {
+        int64_t i = set[a];
+        v3[i] = v3[i] + h * acc[3 * a];
+        v3[n + i] = v3[n + i] + h * acc[3 * a + 1];
+        v3[2 * n + i] = v3[2 * n + i] + h * acc[3 * a + 2];
+    }
+    if (st) st->kick_pairs += pairs;
+    free(acc);
+}
+
+void orc_drift(int64_t n, double *x3, const double *v3,
+               const int32_t *set, const int32_t *labels, int64_t nset,
+               double dt, orc_stats *st)
+{
+    for (int64_t a = 0; a < nset; ++a) {
+        /* a label shared with any other member marks a component member */
+        int single = 1;
+        for (int64_t b = 0; b < nset && single; ++b)
+            if (b != a && labels[b] == labels[a]) single = 0;
+        if (!single) continue;
+        int64_t i = set[a];
+        x3[i] = x3[i] + dt * v3[i];
+        x3[n + i] = x3[n + i] + dt * v3[n + i];
+        x3[2 * n + i] = x3[2 * n + i] + dt * v3[2 * n + i];
+        if (st) st->drifts++;
+    }
+}
+
+/* ------------------------------------------------------------------ */
+/* Two-body flow (Eq. kepler, eps = 0) by the classical Kepler equation */
+/* in difference form: eccentric anomaly for bound orbits, hyperbolic   */
+/* anomaly for unbound ones, Barker's cubic for the exact parabola.     */
+/* ------------------------------------------------------------------ */
+/* x - sin x and sinh x - x without cancellation for small |x| */
+static double x_minus_sin(double x)
+{
+    if (fabs(x) > 0.5) return x - sin(x);
+    double x2 = x * x, term = x * x2 / 6.0, s = 0.0;
+    for (int k = 1; k < 30 && term != 0.0; ++k) {
+        s += term;
+        term = -term * x2 / ((2.0 * k + 2.0) * (2.0 * k + 3.0));
+    }
+    return s;
+}
+static double sinh_minus_x(double x)
+{
+    if (fabs(x) > 0.5) return sinh(x) - x;
+    double x2 = x * x, term = x * x2 / 6.0, s = 0.0;
+    for (int k = 1; k < 30 && term != 0.0; ++k) {
+        s += term;
+        term = term * x2 / ((2.0 * k + 2.0) * (2.0 * k + 3.0));
+    }
+    return s;
+}
+
+/* safeguarded Newton on an increasing function on [lo, hi] */
+typedef double (*fn_t)(double x, const double *c, double *df);
+static int solve_increasing(fn_t f, const double *c, double lo, double hi,
+                            double x0, double *root)
+{
+    double x = x0;
+    if (!(x > lo && x < hi)) x = 0.5 * (lo + hi);
+    for (int it = 0; it < 400; ++it) {
+        double df, fx = f(x, c, &df);
+        if (fx == 0.0) { *root = x; return 0; }
+        if (fx < 0.0) lo = x; else hi = x;
+        double xn = x - fx / df;
+        if (!(xn > lo && xn < hi) || !isfinite(xn)) xn = 0.5 * (lo + hi);
+        double step = fabs(xn - x);
+        x = xn;
+        if (step <= 2e-16 * fabs(x) || hi - lo <= 2e-16 * fabs(x) || step == 0.0) {
+            /* one polishing Newton step from the converged point */
+            fx = f(x, c, &df);
+            xn = x - fx / df;
+            if (xn >= lo && xn <= hi && isfinite(xn)) x = xn;
+            *root = x;
+            return 0;
+        }
+    }
+    *root = x;
+    return -1;
+}
+
+/* c = {r0a, es, ndt}:  (x - sin x) + r0a sin x + es (1 - cos x) - ndt */
+static double f_ell(double x, const double *c, double *df)
+{
+    double s = sin(x), hs = sin(0.5 * x), omc = 2.0 * hs * hs;
+    *df = omc + c[0] * cos(x) + c[1] * s;
+    return x_minus_sin(x) + c[0] * s + c[1] * omc - c[2];
+}
+/* c = {r0b, es, ndt}:  (sinh x - x) + r0b sinh x + es (cosh x - 1) - ndt */
+static double f_hyp(double x, const double *c, double *df)
+{
+    double s = sinh(x), hs = sinh(0.5 * x), cm1 = 2.0 * hs * hs;
+    *df = cm1 + c[0] * cosh(x) + c[1] * s;
+    return sinh_minus_x(x) + c[0] * s + c[1] * cm1 - c[2];
+}
+/* c = {r0, sig = sigma/sqrt(mu), sqmu*dt}: Barker's equation in chi */
+static double f_par(double x, const double *c, double *df)
+{
+    *df = c[0] + c[1] * x + 0.5 * x * x;
+    return c[0] * x + 0.5 * c[1] * x * x + x * x * x / 6.0 - c[2];
+}
+
+int orc_kepler(int64_t n, double *x3, double *v3, const double *m,
+               double G, int64_t i, int64_t j, double dt)
+{
+    double mi = m[i], mj = m[j], M = mi + mj, mu = G * M;
+    double xc[3], vc[3], r0[3], v0[3];
+    for (int k = 0; k < 3; ++k) {
+        double xi = x3[k * n + i], xj = x3[k * n + j];
+        double vi = v3[k * n + i], vj = v3[k * n + j];
+        xc[k] = (mi * xi + mj * xj) / M;
+        vc[k] = (mi * vi + mj * vj) / M;
+        r0[k] = xi - xj;
+        v0[k] = vi - vj;
+    }
+    double r0n = sqrt(r0[0] * r0[0] + r0[1] * r0[1] + r0[2] * r0[2]);
+    double vv = v0[0] * v0[0] + v0[1] * v0[1] + v0[2] * v0[2];
+    double sig = r0[0] * v0[0] + r0[1] * v0[1] + r0[2] * v0[2];
+    double alpha = 2.0 / r0n - vv / mu; /* 1/a */
+    double f, g, fd, gd;
+    if (!(r0n > 0.0) || !(mu > 0.0) || !isfinite(alpha)) return ORC_E_KEPLER;
+    if (dt == 0.0) {
+        f = 1.0; g = 0.0; fd = 0.0; gd = 1.0;
+    } else if (alpha > 0.0) {
+        double a = 1.0 / alpha, nmm = sqrt(mu / (a * a * a));
+        double c[3] = {r0n / a, sig / sqrt(mu * a), nmm * dt};
+        double x;
+        if (solve_increasing(f_ell, c, c[2] - 3.0, c[2] + 3.0, c[2], &x)) return ORC_E_KEPLER;
+        double s = sin(x), hs = sin(0.5 * x), omc = 2.0 * hs * hs;
+        double r = a * omc + r0n * cos(x) + a * c[1] * s;
+        f = 1.0 - (a / r0n) * omc;
+        g = dt - x_minus_sin(x) / nmm;
+        fd = -sqrt(mu * a) * s / (r * r0n);
+        gd = 1.0 - (a / r) * omc;
+    } else if (alpha < 0.0) {
+        double b = -1.0 / alpha, nmm = sqrt(mu / (b * b * b));
+        double c[3] = {r0n / b, sig / sqrt(mu * b), nmm * dt};
+        double lo = 0.0, hi = 1.0;
+        if (dt < 0.0) { lo = -1.0; hi = 0.0; }
+        double dfd;
+        while (f_hyp(hi, c, &dfd) < 0.0) { lo = hi; hi *= 2.0; if (hi > 1e4) return ORC_E_KEPLER; }
+        while (f_hyp(lo, c, &dfd) > 0.0) { hi = lo; lo *= 2.0; if (lo < -1e4) return ORC_E_KEPLER; }
+        double x;
+        if (solve_increasing(f_hyp, c, lo, hi, 0.5 * (lo + hi), &x)) return ORC_E_KEPLER;
+        double s = sinh(x), hs = sinh(0.5 * x), cm1 = 2.0 * hs * hs;
+        double r = b * cm1 + r0n * cosh(x) + b * c[1] * s;
+        f = 1.0 - (b / r0n) * cm1;
+        g = dt - sinh_minus_x(x) / nmm;
+        fd = -sqrt(mu * b) * s / (r * r0n);
+        gd = 1.0 - (b / r) * cm1;
+    } else {
+        double sqmu = sqrt(mu);
+        double c[3] = {r0n, sig / sqmu, sqmu * dt};
+        double lo = 0.0, hi = 1.0, dfd;
+        if (dt < 0.0) { lo = -1.0; hi = 0.0; }
+        while (f_par(hi, c, &dfd) < 0.0) { lo = hi; hi *= 2.0; }
+        while (f_par(lo, c, &dfd) > 0.0) { hi = lo; lo *= 2.0; }
+        double x;
+        if (solve_increasing(f_par, c, lo, hi, 0.5 * (lo + hi), &x)) return ORC_E_KEPLER;
+        double r = r0n + c[1] * x + 0.5 * x * x;
+        f = 1.0 - x * x / (2.0 * r0n);
+        g = dt - x * x * x / (6.0 * sqmu);
+        fd = -sqmu * x / (r * r0n);
+        gd = 1.0 - x * x / (2.0 * r);
+    }
+    for (int k = 0; k < 3; ++k) {
+        double r1 = f * r0[k] + g * v0[k];
+        double v1 = fd * r0[k] + gd * v0[k];
+        double xcn = xc[k] + vc[k] * dt;
+        x3[k * n + i] = xcn + (mj / M) * r1;
+        x3[k * n + j] = xcn - (mi / M) * r1;
+        v3[k * n + i] = vc[k] + (mj / M) * v1;
+        v3[k * n + j] = vc[k] - (mi / M) * v1;
+    }
+    return ORC_OK;
+}
+
+/* ------------------------------------------------------------------ */
+/* evolve_cc (CC pseudocode figure, Sec. 2.3)                           */
+/* ------------------------------------------------------------------ */
+static int cmp_i32(const void *a, const void *b)
+{
+    int32_t x = *(const int32_t *)a, y = *(const int32_t *)b;
+    return (x > y) - (x < y);
+}
+
+int orc_evolve_cc(int64_t n, double *x3, double *v3, const double *m,
+                  const orc_params *p, const int32_t *set, int64_t nset,
+                  double h, int depth, orc_stats *st)
+{
+    if (depth > p->max_depth) return ORC_E_DEPTH;
+    if (st && depth > st->max_depth_seen) st->max_depth_seen = depth;
+    int32_t *labels = (int32_t *)malloc(sizeof(int32_t) * (nset > 0 ? nset : 1));
+    /* 1) split_cc: C_1..C_K and R */
+    int64_t K = orc_components(n, x3, v3, m, p, set, nset, h, labels, st);
+    int rc = ORC_OK;
+    /* gather each C_i as an ascending id list, components in ascending label */
+    int32_t *members = NULL, *coff = NULL;
+    int64_t nc = 0;
+    if (K > 0) {
+        members = (int32_t *)malloc(sizeof(int32_t) * nset);
+        coff = (int32_t *)malloc(sizeof(int32_t) * (K + 1));
+        int32_t *lab_sorted = (int32_t *)malloc(sizeof(int32_t) * nset);
+        memcpy(lab_sorted, labels, sizeof(int32_t) * nset);
+        qsort(lab_sorted, nset, sizeof(int32_t), cmp_i32);
+        int64_t pos = 0;
+        for (int64_t a = 0; a < nset;) {
+            int64_t b = a;
+            while (b < nset && lab_sorted[b] == lab_sorted[a]) b++;
+            if (b - a >= 2) {
+                coff[nc] = (int32_t)pos;
+                for (int64_t k = 0; k < nset; ++k)
+                    if (labels[k] == lab_sorted[a]) members[pos++] = set[k];
+                nc++;
+            }
+            a = b;
+        }
+        coff[nc] = (int32_t)pos;
+        free(lab_sorted);
+    }
+    /* 2) + 6) evolve every C_i at h/2 (Kepler for two-body C_i in CC_KEPLER);
+     * the second pass re-enters the same C_i, which re-split themselves */
+    for (int pass = 0; pass < 2 && rc == ORC_OK; ++pass) {
+        if (pass == 1) {
+            /* 3)-5) D_{h/2,T_R} K_{h,V_R+V_CC+V_CR} D_{h/2,T_R} */
+            orc_drift(n, x3, v3, set, labels, nset, 0.5 * h, st);
+            orc_kick(n, x3, v3, m, p, set, labels, nset, h, st);
+            orc_drift(n, x3, v3, set, labels, nset, 0.5 * h, st);
+        }
+        for (int64_t c = 0; c < nc && rc == ORC_OK; ++c) {
+            const int32_t *cs = members + coff[c];
+            int64_t cn = coff[c + 1] - coff[c];
+            if (p->kepler && cn == 2) {
+                rc = orc_kepler(n, x3, v3, m, p->G, cs[0], cs[1], 0.5 * h);
+                if (st) st->kepler_calls++;
+            } else {
+                rc = orc_evolve_cc(n, x3, v3, m, p, cs, cn, 0.5 * h, depth + 1, st);
+            }
+        }
+    }
+    free(labels);
+    free(members);
+    free(coff);
+    return rc;
+}
+
+static int check_state(int64_t n, const double *x3, const double *v3, const double *m)
+{
+    for (int64_t k = 0; k < 3 * n; ++k)
+        if (!isfinite(x3[k]) || !isfinite(v3[k])) return ORC_E_NONFINITE;
+    for (int64_t k = 0; k < n; ++k)
+        if (!isfinite(m[k]) || !(m[k] > 0.0)) return ORC_E_NONFINITE;
+    return ORC_OK;
+}
+
+int orc_evolve(int64_t n, double *x3, double *v3, const double *m,
+               const orc_params *p, int64_t nsteps, orc_stats *st)
+{
+    int64_t off[2] = {0, n};
+    return orc_evolve_systems(n, x3, v3, m, p, off, 1, nsteps, st);
+}
+
+int orc_evolve_systems(int64_t n, double *x3, double *v3, const double *m,
+                       const orc_params *p, const int64_t *sys_off, int64_t nsys,
+                       int64_t nsteps, orc_stats *st)
+{
+    if (n < 0 || nsteps < 0 || !(p->dt > 0.0)) return ORC_E_ARG;
+    if (p->kepler && p->eps != 0.0) return ORC_E_ARG;
+    int rc = check_state(n, x3, v3, m);
+    if (rc) return rc;
+    int32_t *set = (int32_t *)malloc(sizeof(int32_t) * (n > 0 ? n : 1));
+    for (int64_t k = 0; k < n; ++k) set[k] = (int32_t)k;
+    for (int64_t s = 0; s < nsteps && rc == ORC_OK; ++s)
+        for (int64_t q = 0; q < nsys && rc == ORC_OK; ++q)
+            rc = orc_evolve_cc(n, x3, v3, m, p, set + sys_off[q],
+                               sys_off[q + 1] - sys_off[q], p->dt, 0, st);
+    free(set);
+    if (rc == ORC_OK) rc = check_state(n, x3, v3, m);
+    return rc;
+}
+
+/* ------------------------------------------------------------------ */
+/* diagnostics: H of Eq. (Hamiltonian), P, L                           */
+/* ------------------------------------------------------------------ */
+void orc_energy(int64_t n, const double *x3, const double *v3, const double *m,
+                double G, double eps, double *E, double *P3, double *L3)
+{
+    double T = 0.0, V = 0.0, eps2 = eps * eps;
+    double P[3] = {0, 0, 0}, L[3] = {0, 0, 0};
+    for (int64_t i = 0; i < n; ++i) {
+        double x = x3[i], y = x3[n + i], z = x3[2 * n + i];
+        double vx = v3[i], vy = v3[n + i], vz = v3[2 * n + i];
+        T += 0.5 * m[i] * ((vx * vx + vy * vy) + vz * vz);
+        P[0] += m[i] * vx; P[1] += m[i] * vy; P[2] += m[i] * vz;
+        L[0] += m[i] * (y * vz - z * vy);
+        L[1] += m[i] * (z * vx - x * vz);
+        L[2] += m[i] * (x * vy - y * vx);
+        for (int64_t j = i + 1; j < n; ++j) {
+            double dx = x3[j] - x, dy = x3[n + j] - y, dz = x3[2 * n + j] - z;
+            V -= G * m[i] * m[j] / sqrt(((dx * dx + dy * dy) + dz * dz) + eps2);
+        }
+    }
+    if (E) *E = T + V;
+    if (P3) { P3[0] = P[0]; P3[1] = P[1]; P3[2] = P[2]; }
+    if (L3) { L3[0] = L[0]; L3[1] = L[1]; L3[2] = L[2]; }
+}
