@@ -1,0 +1,314 @@
+"""Benchmark of the CC split integrator hot path (arXiv:1407.7105).
+
+One step = one outer step evolve_cc(all, dt) of the 16384-body Plummer
+sphere (N-body units, eta = 0.03, dt = 1/256, eps = 0): the tau + edge +
+union-find split, segmentation, kicks, drifts and the recursion into every
+component, all in libcc.so's kernels.  The metric counts interactions =
+tau pairs (n(n-1)/2 per split set) + cross-component kick pairs, per second.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--form fp64|mixed]
+  python bench.py --impl reference ...   (the FP64 CPU oracle, bounded sample)
+
+Multi-GPU: the integrator does not shard (one system per GPU); N ranks run
+N independent replicas (different seeds) and value sums their work over the
+slowest rank's time ("scaling": "weak").
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "CC interactions/s, mixed vs FP64 at |dE/E|≤1e-6; % of FP64/FP32 roofline"
+UNIT = "interactions/s"
+N_BODY = 16384
+DT = 1.0 / 256
+ETA = 0.03
+# algorithmic FP64 operations per unordered pair (sqrt and division count 1)
+TAU_FLOPS = 47   # Eq. tauij as evaluated: 3 sqrt, 6 div, 38 add/sub/mul
+KICK_FLOPS = 28  # one pair force applied to both bodies (Eqs. kickij/kickji)
+
+
+def workload_name():
+    return (f"Plummer N={N_BODY}, equal masses, N-body units, eps=0, eta={ETA}, outer step dt=1/256 "
+            f"(one evolve_cc step per bench step)")
+
+
+# ------------------------------------------------------------------ clocks
+class ClockSampler:
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int):
+        self.gpu = gpu_index
+        self.proc = None
+        self.lines = []
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.gpu), f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
+                 "-lms", "200"], stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.t = threading.Thread(target=self._read, daemon=True)
+            self.t.start()
+        except (OSError, FileNotFoundError):
+            self.proc = None
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        self.t.join(timeout=2)
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            f = [x.strip() for x in ln.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                sm.append(float(f[1]))
+                smax.append(float(f[2]))
+            except ValueError:
+                continue
+            for nm, val in zip(names, f[5:9]):
+                if val.lower() == "active":
+                    reasons.add(nm)
+        return {"sm_mhz": float(np.median(sm)) if sm else None, "sm_max_mhz": max(smax) if smax else None,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+# ------------------------------------------------------------------ peaks
+def measured_peaks():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    try:
+        with open(path) as f:
+            return json.load(f)
+    except (OSError, ValueError):
+        return {}
+
+
+# ------------------------------------------------------------------ oracle
+def oracle_sample(m, x, v, reps: int = 1):
+    """The FP64 CPU oracle on a bounded sample of the workload: the top-level
+    split_cc of all N bodies at h = dt followed by the level's
+    drift-kick-drift (no recursion).  Returns (interactions, seconds)."""
+    from oracle import oracle as O
+    s = O.State(m, x, v)
+    p = O.params(eta=ETA, dt=DT)
+    inter = 0
+    t0 = time.perf_counter()
+    for _ in range(reps):
+        st = O.Stats()
+        lab, _ = O.components(s, p, DT, stats=st)
+        ids = np.arange(s.n, dtype=np.int32)
+        O.drift(s, ids, lab, 0.5 * DT, stats=st)
+        O.kick(s, p, ids, lab, DT, stats=st)
+        O.drift(s, ids, lab, 0.5 * DT, stats=st)
+        inter += st.tau_pairs + st.kick_pairs
+    return inter, time.perf_counter() - t0
+
+
+def run_reference(args, rank, world):
+    from oracle import oracle as O
+    O.build()
+    if rank != 0:
+        return 0
+    from paper_1407_7105_gb300 import ics
+    m, x, v = ics.plummer(N_BODY, seed=args.seed)
+    for _ in range(args.warmup):
+        oracle_sample(m, x, v)
+    inter, sec = 0, 0.0
+    for _ in range(args.steps):
+        i, s = oracle_sample(m, x, v)
+        inter += i
+        sec += s
+    val = inter / sec
+    line = {
+        "impl": "reference", "metric": METRIC, "value": val, "unit": UNIT, "n_gpus": args.gpus,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * sec / max(1, args.steps),
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": workload_name(), "form": "oracle"},
+        "cpu_baseline": {"value": val, "unit": UNIT, "cores": 1, "kind": "oracle",
+                         "sample": "per step: top-level split_cc (BFS, lazy tau) of all 16384 bodies at h=dt "
+                                   "plus that level's drift-kick-drift, single thread"},
+        "e2e": {"value": val, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+# ------------------------------------------------------------------ GPU arm
+def run_gpu(args, rank, world):
+    import torch
+    import torch.distributed as dist
+
+    from paper_1407_7105_gb300 import build, cc, ics
+
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    build.build()
+    seed = args.seed + rank
+    m, x, v = ics.plummer(N_BODY, seed=seed)
+
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        from oracle import oracle as O
+        O.build()
+        inter, sec = oracle_sample(m, x, v)
+        cpu = {"value": inter / sec, "unit": UNIT, "cores": 1, "kind": "oracle",
+               "sample": "top-level split_cc (BFS, lazy tau) of all 16384 bodies at h=dt plus that level's "
+                         "drift-kick-drift, single thread, same initial state"}
+
+    stream = torch.cuda.current_stream(dev)
+    prec = cc.PREC_MIXED if args.form == "mixed" else cc.PREC_FP64
+    dm, dx, dv = (torch.tensor(a, device=dev) for a in (m, x, v))
+    ctx = cc.Context(dm, dx, dv, dt=DT, eta=ETA, precision=prec)
+    E0, _, _ = ctx.energy()
+    f64_peak, f32_peak = cc.probe_peaks()
+    l2_flush = torch.empty(64 * 1024 * 1024, dtype=torch.int32, device=dev)  # 256 MB > L2
+
+    t = 0.0
+    for _ in range(args.warmup):
+        t += DT
+        ctx.evolve(t)
+    torch.cuda.synchronize()
+    st0 = ctx.stats()
+    ctx.set_timing(True)
+    sampler = ClockSampler(local)
+    if dist.is_initialized():
+        dist.barrier()
+    torch.cuda.synchronize()
+    sampler.start()
+    total_ms = 0.0
+    for _ in range(args.steps):
+        l2_flush.fill_(1)
+        torch.cuda.synchronize()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        t += DT
+        ctx.evolve(t)
+        e1.record(stream)
+        e1.synchronize()
+        total_ms += e0.elapsed_time(e1)
+    torch.cuda.synchronize()
+    clocks = sampler.stop()
+    st1 = ctx.stats()
+    tm = ctx.timing()
+    ctx.set_timing(False)
+    inter = (st1["tau_pairs"] - st0["tau_pairs"]) + (st1["kick_pairs"] - st0["kick_pairs"])
+    launches = st1["launches"] - st0["launches"]
+    E1, _, _ = ctx.energy()
+
+    # end to end through the C ABI with host buffers (pinned)
+    hm = torch.empty(N_BODY, dtype=torch.float64).pin_memory()
+    hx = torch.empty(3, N_BODY, dtype=torch.float64).pin_memory()
+    hv = torch.empty(3, N_BODY, dtype=torch.float64).pin_memory()
+    ctx.get_state(hm, hx, hv)
+    e2e_steps = max(1, min(args.steps, 3))
+    st2 = ctx.stats()
+    torch.cuda.synchronize()
+    w0 = time.perf_counter()
+    for _ in range(e2e_steps):
+        ctx.set_state(t, hm, hx, hv)
+        t += DT
+        ctx.evolve(t)
+        ctx.get_state(None, hx, hv, alloc=False)
+    torch.cuda.synchronize()
+    e2e_sec = time.perf_counter() - w0
+    st3 = ctx.stats()
+    e2e_inter = (st3["tau_pairs"] - st2["tau_pairs"]) + (st3["kick_pairs"] - st2["kick_pairs"])
+
+    # max over ranks, sums of work
+    sec = total_ms * 1e-3
+    if dist.is_initialized():
+        tt = torch.tensor([sec, e2e_sec], device=dev, dtype=torch.float64)
+        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+        w = torch.tensor([float(inter), float(e2e_inter)], device=dev, dtype=torch.float64)
+        dist.all_reduce(w, op=dist.ReduceOp.SUM)
+        sec, e2e_sec = float(tt[0]), float(tt[1])
+        inter, e2e_inter = float(w[0]), float(w[1])
+    value = inter / sec
+
+    # roofline of the dominant pairwise kernel (measured live above)
+    if tm["tau_ms"] >= tm["kick_ms"]:
+        kname, kms, kl, flops = "tau_hook", tm["tau_ms"], tm["tau_launches"], TAU_FLOPS * tm["tau_pairs"]
+    else:
+        kname, kms, kl, flops = "kick", tm["kick_ms"], tm["kick_launches"], KICK_FLOPS * tm["kick_pairs"]
+    achieved = flops / (kms * 1e-3) / 1e12 if kms > 0 else None
+    peak = f64_peak / 1e12
+    roof = {"bound": "alu", "kernel": kname, "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
+            "frac": (achieved / peak) if achieved else None, "traffic": None,
+            "peak_source": "FP64 FMA throughput measured by cc_probe_peaks on this GPU",
+            "kernel_ms_per_step": kms / args.steps, "launches_per_step": kl / args.steps,
+            "tau_ms_per_step": tm["tau_ms"] / args.steps, "kick_ms_per_step": tm["kick_ms"] / args.steps,
+            "fp32_peak_tflops": f32_peak / 1e12}
+
+    if rank == 0:
+        line = {
+            "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": total_ms / args.steps, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": workload_name(), "form": args.form, "l2": "flushed (256 MB write) before each step",
+                       "parallelism": "replicas" if world > 1 else "single GPU"},
+            "e2e": {"value": e2e_inter / e2e_sec, "unit": UNIT, "h2d_bytes_per_step": 7 * N_BODY * 8,
+                    "d2h_bytes_per_step": 6 * N_BODY * 8, "steps": e2e_steps},
+            "gpu_launches": launches,
+            "roofline": roof,
+            "cpu_baseline": cpu,
+            "clocks": clocks,
+            "dE_over_E": (E1 - E0) / abs(E0),
+            "interactions_per_step": inter / args.steps / world,
+        }
+        print(json.dumps(line), flush=True)
+    ctx.close()
+    return 0
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="cc", choices=["cc", "reference"])
+    ap.add_argument("--form", default="fp64", choices=["fp64", "mixed"])
+    ap.add_argument("--seed", type=int, default=1)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    if args.impl == "reference":
+        return run_reference(args, rank, world)
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl")
+    try:
+        return run_gpu(args, rank, world)
+    finally:
+        import torch.distributed as dist
+        if dist.is_initialized():
+            dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    sys.exit(main())

@@ -1,0 +1,186 @@
+/*
+ * cc.h -- C ABI of libcc.so, the GB300 (sm_103a) CUDA implementation of the
+ * connected-component (CC) Hamiltonian-splitting N-body integrator of
+ * Jaenes, Pelupessy & Portegies Zwart, "A connected component-based method
+ * for efficiently integrating multiscale N-body systems" (arXiv:1407.7105).
+ *
+ * Conventions shared by every entry point
+ *  - Every function returns 0 (CC_OK) or a negative CC_E_* code; none
+ *    throws, traps or aborts.  cc_last_error(ctx) describes the last error.
+ *  - Particle state is SoA: x3[k*n + i] is coordinate k (0,1,2) of particle
+ *    i, likewise v3; m[i] is the mass.  Particle ids are 0..n-1.
+ *  - Pointer arguments may point to host or device memory (the library asks
+ *    cudaPointerGetAttributes); caller buffers stay caller-owned, the
+ *    context owns all device memory it allocates.
+ *  - Work is ordered on the CUDA stream given to cc_init / cc_set_stream.
+ *    Functions that return host values synchronise that stream.
+ *  - A "set" is an array of distinct particle ids in ascending order;
+ *    NULL with n_set = n means all particles.
+ *  - A context is not thread safe: one host thread at a time.
+ */
+#ifndef CC_H
+#define CC_H
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define CC_OK            0
+#define CC_E_ARG        -1  /* invalid argument                                */
+#define CC_E_CUDA       -2  /* a CUDA runtime call failed                       */
+#define CC_E_DEPTH      -3  /* recursion deeper than max_depth                  */
+#define CC_E_TIMEOUT    -4  /* a bounded device wait or retry loop gave up       */
+#define CC_E_NONFINITE  -5  /* non-finite or non-positive input                 */
+#define CC_E_CAPACITY   -6  /* output buffer too small (counts still reported)  */
+#define CC_E_KEPLER     -7  /* Kepler solver did not converge                   */
+#define CC_E_NOMEM      -8  /* device allocation failed                         */
+
+#define CC_PREC_FP64   0    /* every force and tau in FP64                      */
+#define CC_PREC_MIXED  1    /* FP32 forces between components, certified FP32
+                               tau pre-filter; FP64 state, drift, predicate     */
+
+typedef struct {
+    double G;          /* gravitational constant (N-body units: 1)                     */
+    double eps;        /* softening length in V_ij (Sec. 2.1, Eq. Hamiltonian)         */
+    double eta;        /* accuracy parameter of tau(i,j) (Eq. tauij)                   */
+    double dt;         /* outer pivot time step h of evolve_cc(all, h)                 */
+    double h_fp64;     /* CC_PREC_MIXED: sets split at a threshold h < h_fp64 take
+                          FP64 forces (close subsystems where FP32 cancels)            */
+    double near_tol;   /* pairs with |tau - h| < near_tol * h are logged (1e-12)       */
+    int    precision;  /* CC_PREC_FP64 or CC_PREC_MIXED                                 */
+    int    kepler;     /* 1: CC_KEPLER (Sec. 3.2), two-body components by Kepler flow   */
+    int    max_depth;  /* recursion depth cap (levels below the outer step)            */
+    int    s_small;    /* components of at most s_small (<= 32) members run entirely in
+                          the persistent small-component kernel; 0 disables it         */
+    int    eta_outside;/* 0: eta inside T and dT/dt (default reading); 1: eta
+                          multiplies the min of Eq. (tauij) literally                  */
+    int    reserved[5];
+} cc_params;
+
+typedef struct {
+    uint64_t tau_pairs;     /* pairs whose tau the splits covered: n(n-1)/2 per set  */
+    uint64_t tau_fp64;      /* pairs whose predicate was evaluated in FP64           */
+    uint64_t kick_pairs;    /* unordered cross-component pairs kicked                 */
+    uint64_t drifts;        /* particle drifts                                        */
+    uint64_t kepler_calls;  /* two-body Kepler solves                                 */
+    uint64_t splits;        /* set splits (split_cc calls)                            */
+    uint64_t components;    /* non-trivial components found                           */
+    uint64_t edges;         /* edges (tau < h) found                                  */
+    uint64_t near_pairs;    /* pairs with |tau-h| < near_tol*h                        */
+    uint64_t small_tasks;   /* components run by the small-component kernel          */
+    uint64_t launches;      /* kernels this context launched                          */
+    int32_t  max_depth_seen;
+    int32_t  reserved;
+} cc_stats_t;
+
+/* Device time of the pairwise kernels, measured with CUDA events on the
+ * context's stream while timing is on (cc_set_timing).  pairs = unordered
+ * pairs those launches covered (tau: n(n-1)/2 per set; kick: cross-
+ * component pairs). */
+typedef struct {
+    double   tau_ms, kick_ms;
+    int64_t  tau_launches, kick_launches;
+    uint64_t tau_pairs, kick_pairs;
+} cc_timing_t;
+
+typedef struct cc_ctx cc_ctx;
+
+/* Fill *p with defaults: G=1, eps=0, eta=0.03, dt=1/64, h_fp64=0,
+ * near_tol=1e-12, FP64, kepler off, max_depth=64, s_small=32. */
+int cc_default_params(cc_params *p);
+
+/* Create a context holding n particles (Sec. 2.1: masses m_i, positions q_i,
+ * velocities v_i = p_i/m_i).  m[n], x3[3n], v3[3n] host or device.
+ * stream: a cudaStream_t (NULL = default stream).  Errors: CC_E_ARG (n < 1,
+ * bad params), CC_E_NONFINITE (non-finite state or m <= 0), CC_E_NOMEM. */
+int cc_init(cc_ctx **out, int64_t n, const double *m, const double *x3,
+            const double *v3, const cc_params *p, void *stream);
+
+/* Declare independent systems: system s is the id range
+ * [sys_off[s], sys_off[s+1]) (host array, nsys+1 entries, sys_off[0] = 0,
+ * sys_off[nsys] = n); pairs of different systems never interact, and each
+ * outer step runs evolve_cc(system, dt) for every system.  Default: one
+ * system.  Errors: CC_E_ARG. */
+int cc_set_systems(cc_ctx *ctx, const int64_t *sys_off, int64_t nsys);
+
+int cc_set_stream(cc_ctx *ctx, void *stream);
+
+/* Time-step graph of Sec. 2.2 on `set` at threshold h: all pairs of the set,
+ * tau(i,j) by Eq. (tauij) in FP64 (reading in the design doc), edge iff
+ * tau(i,j) < h.  *n_edges = edge count.  edges_out (may be NULL) receives
+ * min(cap, n_edges) pairs (i<j as particle ids, int32[cap][2]) in
+ * lexicographic order.  *n_near = pairs with |tau-h| < near_tol*h (their
+ * (i, j, tau) are readable with cc_near_pairs).  Returns CC_E_CAPACITY when
+ * n_edges > cap and edges_out != NULL (the first cap edges of the sorted
+ * order are not guaranteed then: only the count is). */
+int cc_timestep_graph(cc_ctx *ctx, const int32_t *set, int64_t n_set, double h,
+                      int64_t *n_edges, int32_t *edges_out, int64_t cap,
+                      int64_t *n_near);
+
+/* split_cc of Sec. 2.3 by union-find: labels_out[k] (int32[n_set]) = the
+ * smallest particle id of the connected component of set[k] in the
+ * time-step graph at h (singletons: their own id; they form the rest set
+ * R).  *n_comp = number of non-trivial components (>= 2 members). */
+int cc_components(cc_ctx *ctx, const int32_t *set, int64_t n_set, double h,
+                  int32_t *labels_out, int64_t *n_comp);
+
+/* K_{h,V} of Eqs. (kickij, kickji) for every pair of `set` whose labels
+ * differ (labels int32[n_set], any values): v_i += h * a_i.  Sec. 2.2 splits
+ * V_R + V_CC + V_CR this way.  Precision follows params.precision (mixed
+ * forces unless h < h_fp64). */
+int cc_kick(cc_ctx *ctx, const int32_t *set, int64_t n_set,
+            const int32_t *labels, double h);
+
+/* D_{h,T_i} of Eq. (drift), x_i += h * v_i, for the members of `set` whose
+ * label no other member shares (the rest set R). */
+int cc_drift(cc_ctx *ctx, const int32_t *set, int64_t n_set,
+             const int32_t *labels, double h);
+
+/* Outer loop: while t < t_end, evolve_cc(system, dt) for every system (CC
+ * pseudocode figure, Sec. 2.3), then t += dt.  (t_end - t) must be a whole
+ * number of steps dt (relative slack 1e-9) else CC_E_ARG.  eta > 0
+ * overrides params.eta.  Errors: CC_E_DEPTH, CC_E_TIMEOUT, CC_E_KEPLER,
+ * CC_E_NONFINITE (state became non-finite). */
+int cc_evolve(cc_ctx *ctx, double t_end, double eta);
+
+/* Copy out / replace the state (any pointer may be NULL to skip). */
+int cc_get_state(cc_ctx *ctx, double *t, double *m, double *x3, double *v3);
+int cc_set_state(cc_ctx *ctx, double t, const double *m, const double *x3,
+                 const double *v3);
+
+/* Counters accumulated since cc_init or the last cc_reset_stats. */
+int cc_stats(cc_ctx *ctx, cc_stats_t *out);
+int cc_reset_stats(cc_ctx *ctx);
+
+/* Total energy H (Eq. Hamiltonian, FP64 all pairs), momentum P[3] and
+ * angular momentum L[3] (host pointers, any may be NULL). */
+int cc_energy(cc_ctx *ctx, double *E, double *P3, double *L3);
+
+/* Near-threshold pairs logged since the last cc_timestep_graph /
+ * cc_components / cc_evolve call: ids int32[cap][2], tau double[cap]
+ * (either may be NULL); *n = total logged (may exceed cap). */
+int cc_near_pairs(cc_ctx *ctx, int32_t *pairs, double *tau, int64_t cap, int64_t *n);
+
+/* Turn per-launch event timing of the tau and kick kernels on (1) or off
+ * (0); turning it on clears the accumulated times. */
+int cc_set_timing(cc_ctx *ctx, int on);
+int cc_timing(cc_ctx *ctx, cc_timing_t *out);
+
+/* FMA throughput of the current device, measured by a microbenchmark on
+ * `stream` (flop/s, an FMA counting 2): the ALU roofline denominators of
+ * the FP64 and FP32 pair kernels.  Errors (message via cc_last_error(NULL)):
+ * CC_E_CUDA. */
+int cc_probe_peaks(void *stream, double *fp64_flops, double *fp32_flops);
+
+/* Release the context and all its device memory. */
+int cc_destroy(cc_ctx *ctx);
+
+/* Static description of the last error on ctx (or of the last failed
+ * cc_init when ctx is NULL). */
+const char *cc_last_error(cc_ctx *ctx);
+
+#ifdef __cplusplus
+}
+#endif
+#endif

@@ -1,0 +1,881 @@
+// cc_api.cu -- host driver and C ABI of libcc.so: the recursive CC split
+// integrator evolve_cc (arXiv:1407.7105 Sec. 2.3, CC pseudocode figure)
+// run level-synchronously on one GPU.
+//
+// All sets at recursion depth d that share the pivot h = dt / 2^d are
+// processed as one batch (they are independent closed Hamiltonians,
+// Sec. 2.2 Eq. for E_{h/2,H_C}).  process(d, h):
+//   split   : tau + union-find over every set of the batch, compress,
+//             segment components (stable, ascending ids);
+//   for each half (before and after the DKD of this level):
+//             two-body components -> batched Kepler (CC_KEPLER);
+//             small components    -> persistent small-component kernel;
+//             large components    -> gathered into level d+1, process(d+1, h/2),
+//                                    scattered back;
+//   DKD     : D_{h/2,T_R} K_{h,V_R+V_CC+V_CR} D_{h/2,T_R} on the batch.
+#include <algorithm>
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include "cc_internal.cuh"
+
+namespace cc {
+unsigned long long g_launches = 0;
+}
+
+using namespace cc;
+
+namespace {
+
+constexpr int TAU_TILE = 128;   // must match the tau kernel
+constexpr int KICK_TILE = 64;   // must match the kick kernel
+
+thread_local std::string g_init_err;
+
+struct LevelAlloc {
+    Level L{};
+    int cap = 0;      // element capacity (excluding PAD_TAIL)
+    int set_cap = 0;  // set-array capacity
+    void *block = nullptr;
+    void *setblock = nullptr;
+    // split products of this level
+    int32_t *root = nullptr, *members = nullptr, *comp_start = nullptr, *comp_size = nullptr, *d_ncomp = nullptr;
+    // component lists handed to the children
+    int32_t *klist = nullptr, *slist = nullptr, *lcomp_start = nullptr, *lpref = nullptr, *ldst = nullptr;
+    void *listblock = nullptr;
+    int list_cap = 0;
+    std::vector<int32_t> h_size, h_start;
+    std::vector<int32_t> h_set_n;  // set sizes of this level (host copy)
+};
+
+}  // namespace
+
+struct cc_ctx {
+    int64_t n = 0;
+    cc_params p{};
+    cudaStream_t stream = nullptr;
+    double t = 0.0;
+    double *d_x3 = nullptr, *d_v3 = nullptr, *d_m = nullptr;
+    std::vector<int64_t> sys_off;
+    int32_t *d_sys_off = nullptr;
+    std::vector<LevelAlloc> lv;  // recursion levels
+    LevelAlloc unit;             // staging level of the unit entry points
+    void *seg_scratch = nullptr;
+    size_t seg_scratch_sz = 0;
+    DevCounters *d_ctr = nullptr;
+    int32_t *d_near_ij = nullptr;
+    double *d_near_tau = nullptr;
+    long long near_cap = 4096;
+    double *d_partial = nullptr;
+    int partial_cap = 0;
+    void *tmp = nullptr;  // staging for caller buffers
+    size_t tmp_sz = 0;
+    unsigned *d_bad = nullptr;
+    cc_stats_t st{};
+    std::string err;
+    double eta_run = 0.03;
+    // optional per-launch event timing of the tau and kick kernels
+    bool timing = false;
+    std::vector<cudaEvent_t> evs;
+    std::vector<int> ev_kind;  // 0 = tau, 1 = kick, per event pair
+    size_t ev_used = 0;
+    cc_timing_t tm{};
+    unsigned long long launch_mark = 0;
+};
+
+// record the start of a timed launch; returns the pair index or -1
+static int ev_begin(cc_ctx *c, int kind)
+{
+    if (!c->timing) return -1;
+    if (c->ev_used + 2 > c->evs.size()) {
+        for (int k = 0; k < 64; ++k) {
+            cudaEvent_t e;
+            cudaEventCreate(&e);
+            c->evs.push_back(e);
+        }
+        c->ev_kind.resize(c->evs.size() / 2);
+    }
+    const int pair = (int)(c->ev_used / 2);
+    c->ev_kind[pair] = kind;
+    cudaEventRecord(c->evs[c->ev_used], c->stream);
+    c->ev_used += 2;
+    return pair;
+}
+
+static void ev_end(cc_ctx *c, int pair)
+{
+    if (pair >= 0) cudaEventRecord(c->evs[2 * pair + 1], c->stream);
+}
+
+// fold the recorded event pairs into the totals (stream must be idle)
+static void ev_resolve(cc_ctx *c)
+{
+    for (size_t q = 0; q < c->ev_used / 2; ++q) {
+        float ms = 0.f;
+        cudaEventElapsedTime(&ms, c->evs[2 * q], c->evs[2 * q + 1]);
+        if (c->ev_kind[q] == 0) {
+            c->tm.tau_ms += ms;
+            c->tm.tau_launches++;
+        } else {
+            c->tm.kick_ms += ms;
+            c->tm.kick_launches++;
+        }
+    }
+    c->ev_used = 0;
+}
+
+// ------------------------------------------------------------ utilities
+#define CC_CUDA(ctx, call)                                                                             \
+    do {                                                                                                \
+        cudaError_t e_ = (call);                                                                        \
+        if (e_ != cudaSuccess) {                                                                        \
+            (ctx)->err = std::string("CUDA error ") + cudaGetErrorString(e_) + " at " #call;            \
+            return CC_E_CUDA;                                                                           \
+        }                                                                                               \
+    } while (0)
+
+#define CC_TRY(expr)           \
+    do {                       \
+        int rc_ = (expr);      \
+        if (rc_) return rc_;   \
+    } while (0)
+
+static int fail(cc_ctx *c, int code, const char *msg)
+{
+    c->err = msg;
+    return code;
+}
+
+static int ensure_tmp(cc_ctx *c, size_t bytes)
+{
+    if (c->tmp_sz >= bytes) return CC_OK;
+    if (c->tmp) cudaFree(c->tmp);
+    c->tmp = nullptr;
+    c->tmp_sz = 0;
+    size_t sz = std::max(bytes, (size_t)1 << 20);
+    if (cudaMalloc(&c->tmp, sz) != cudaSuccess) {
+        cudaGetLastError();
+        return fail(c, CC_E_NOMEM, "device allocation failed (staging buffer)");
+    }
+    c->tmp_sz = sz;
+    return CC_OK;
+}
+
+// copy `bytes` from a host or device pointer into device memory dst
+static int copy_in(cc_ctx *c, void *dst, const void *src, size_t bytes)
+{
+    if (bytes == 0) return CC_OK;
+    CC_CUDA(c, cudaMemcpyAsync(dst, src, bytes, cudaMemcpyDefault, c->stream));
+    return CC_OK;
+}
+
+static int copy_out(cc_ctx *c, void *dst, const void *src, size_t bytes)
+{
+    if (bytes == 0 || !dst) return CC_OK;
+    CC_CUDA(c, cudaMemcpyAsync(dst, src, bytes, cudaMemcpyDefault, c->stream));
+    return CC_OK;
+}
+
+static int align_up(int v, int a) { return (v + a - 1) / a * a; }
+
+static void free_level(LevelAlloc &a)
+{
+    if (a.block) cudaFree(a.block);
+    if (a.setblock) cudaFree(a.setblock);
+    if (a.listblock) cudaFree(a.listblock);
+    a.block = a.setblock = a.listblock = nullptr;
+    a.cap = a.set_cap = a.list_cap = 0;
+}
+
+// (re)allocate a level for `need` packed elements and `nsets` sets
+static int ensure_level(cc_ctx *c, LevelAlloc &a, int need, int nsets)
+{
+    if (need > a.cap) {
+        if (a.block) cudaFree(a.block);
+        a.block = nullptr;
+        int cap = align_up(std::max(need, 64), 64);
+        size_t nd = (size_t)cap + PAD_TAIL;
+        size_t bytes = nd * 8 * 7 + nd * 4 * 10 + 4096;
+        if (cudaMalloc(&a.block, bytes) != cudaSuccess) {
+            cudaGetLastError();
+            return fail(c, CC_E_NOMEM, "device allocation failed (level buffer)");
+        }
+        cudaMemsetAsync(a.block, 0, bytes, c->stream);
+        char *q = (char *)a.block;
+        double **dp[7] = {&a.L.x, &a.L.y, &a.L.z, &a.L.vx, &a.L.vy, &a.L.vz, &a.L.m};
+        for (int k = 0; k < 7; ++k) { *dp[k] = (double *)q; q += nd * 8; }
+        int32_t **ip[10] = {&a.L.gid, &a.L.sidx, &a.L.src, &a.L.parent, &a.L.cnt,
+                            &a.root, &a.members, &a.comp_start, &a.comp_size, &a.d_ncomp};
+        for (int k = 0; k < 10; ++k) { *ip[k] = (int32_t *)q; q += nd * 4; }
+        a.cap = cap;
+        // lists: at most cap/2 components
+        if (a.listblock) cudaFree(a.listblock);
+        a.listblock = nullptr;
+        a.list_cap = cap / 2 + 8;
+        if (cudaMalloc(&a.listblock, (size_t)a.list_cap * 4 * 5 + 1024) != cudaSuccess) {
+            cudaGetLastError();
+            return fail(c, CC_E_NOMEM, "device allocation failed (component lists)");
+        }
+        int32_t *lq = (int32_t *)a.listblock;
+        a.klist = lq; lq += a.list_cap;
+        a.slist = lq; lq += a.list_cap;
+        a.lcomp_start = lq; lq += a.list_cap;
+        a.lpref = lq; lq += a.list_cap + 1;
+        a.ldst = lq;
+    }
+    if (nsets + 2 > a.set_cap) {
+        if (a.setblock) cudaFree(a.setblock);
+        a.setblock = nullptr;
+        int sc = align_up(nsets + 2, 256);
+        if (cudaMalloc(&a.setblock, (size_t)sc * 4 * 4) != cudaSuccess) {
+            cudaGetLastError();
+            return fail(c, CC_E_NOMEM, "device allocation failed (set arrays)");
+        }
+        int32_t *sq = (int32_t *)a.setblock;
+        a.L.set_start = sq; sq += sc;
+        a.L.set_n = sq; sq += sc;
+        a.L.tile_off = sq; sq += sc;
+        a.L.itile_off = sq;
+        a.set_cap = sc;
+    }
+    // the segmentation scratch is shared by all levels: size for the largest
+    size_t need_seg = seg_scratch_bytes(a.cap + PAD_TAIL);
+    if (need_seg > c->seg_scratch_sz) {
+        if (c->seg_scratch) cudaFree(c->seg_scratch);
+        c->seg_scratch = nullptr;
+        if (cudaMalloc(&c->seg_scratch, need_seg) != cudaSuccess) {
+            cudaGetLastError();
+            return fail(c, CC_E_NOMEM, "device allocation failed (segment scratch)");
+        }
+        c->seg_scratch_sz = need_seg;
+    }
+    return CC_OK;
+}
+
+// upload the set layout (sizes -> aligned starts, tile prefixes); returns
+// the packed total through L.total
+struct SetLayout {
+    std::vector<int32_t> start, n, toff, ioff;
+    int total = 0;
+    long long tiles = 0, itiles = 0;
+};
+
+static void make_layout(const std::vector<int32_t> &sizes, SetLayout &S)
+{
+    const size_t ns = sizes.size();
+    S.start.resize(ns);
+    S.n = sizes;
+    S.toff.resize(ns + 1);
+    S.ioff.resize(ns + 1);
+    int pos = 0;
+    long long tt = 0, it = 0;
+    for (size_t s = 0; s < ns; ++s) {
+        S.start[s] = pos;
+        pos += align_up(sizes[s], SET_ALIGN);
+        S.toff[s] = (int32_t)tt;
+        S.ioff[s] = (int32_t)it;
+        const long long nt = (sizes[s] + TAU_TILE - 1) / TAU_TILE;
+        tt += nt * (nt + 1) / 2;
+        it += (sizes[s] + KICK_TILE - 1) / KICK_TILE;
+    }
+    S.toff[ns] = (int32_t)tt;
+    S.ioff[ns] = (int32_t)it;
+    S.total = pos;
+    S.tiles = tt;
+    S.itiles = it;
+}
+
+static int upload_layout(cc_ctx *c, LevelAlloc &a, const SetLayout &S)
+{
+    const int ns = (int)S.n.size();
+    CC_TRY(ensure_level(c, a, std::max(S.total, 1), ns));
+    CC_CUDA(c, cudaMemcpyAsync(a.L.set_start, S.start.data(), ns * 4, cudaMemcpyHostToDevice, c->stream));
+    CC_CUDA(c, cudaMemcpyAsync(a.L.set_n, S.n.data(), ns * 4, cudaMemcpyHostToDevice, c->stream));
+    CC_CUDA(c, cudaMemcpyAsync(a.L.tile_off, S.toff.data(), (ns + 1) * 4, cudaMemcpyHostToDevice, c->stream));
+    CC_CUDA(c, cudaMemcpyAsync(a.L.itile_off, S.ioff.data(), (ns + 1) * 4, cudaMemcpyHostToDevice, c->stream));
+    a.L.total = S.total;
+    a.L.nsets = ns;
+    a.h_set_n = S.n;
+    return CC_OK;
+}
+
+static TauParams tau_params(const cc_ctx *c, double h)
+{
+    TauParams P;
+    P.G = c->p.G;
+    P.eps2 = c->p.eps * c->p.eps;
+    P.eta = c->eta_run;
+    P.eta_in = c->p.eta_outside ? 1.0 : c->eta_run;
+    P.eta_outside = c->p.eta_outside;
+    P.h = h;
+    P.near_tol = c->p.near_tol;
+    return P;
+}
+
+static int check_device_error(cc_ctx *c)
+{
+    unsigned e = 0;
+    CC_CUDA(c, cudaMemcpyAsync(&e, &c->d_ctr->err, sizeof(unsigned), cudaMemcpyDeviceToHost, c->stream));
+    CC_CUDA(c, cudaStreamSynchronize(c->stream));
+    if (e == 0) return CC_OK;
+    unsigned z = 0;
+    cudaMemcpyAsync(&c->d_ctr->err, &z, sizeof(unsigned), cudaMemcpyHostToDevice, c->stream);
+    cudaStreamSynchronize(c->stream);
+    switch (e) {
+    case DERR_TMA_TIMEOUT: return fail(c, CC_E_TIMEOUT, "a bounded TMA/mbarrier wait timed out");
+    case DERR_UF_RETRY: return fail(c, CC_E_TIMEOUT, "union-find retry limit reached");
+    case DERR_KEPLER: return fail(c, CC_E_KEPLER, "Kepler solver did not converge");
+    case DERR_DEPTH: return fail(c, CC_E_DEPTH, "recursion deeper than max_depth");
+    default: return fail(c, CC_E_TIMEOUT, "device error");
+    }
+}
+
+// ------------------------------------------------------------ recursion
+static int process(cc_ctx *c, int d, double h);
+
+// split the batch of level d at h: union-find components and segments
+static int split_level(cc_ctx *c, LevelAlloc &a, double h, int &ncomp)
+{
+    const cudaStream_t s = c->stream;
+    const TauParams P = tau_params(c, h);
+    launch_init_parent(a.L, s);
+    long long ntiles = 0;
+    {
+        // number of tau tiles of this level = last prefix entry (host copy)
+        for (int32_t n : a.h_set_n) {
+            const long long nt = (n + TAU_TILE - 1) / TAU_TILE;
+            ntiles += nt * (nt + 1) / 2;
+        }
+    }
+    if (ntiles > 0x7fffffff) return fail(c, CC_E_ARG, "set too large for the tile grid");
+    const int ev = ev_begin(c, 0);
+    launch_tau_hook(a.L, (int)ntiles, P, c->p.precision, c->d_ctr, nullptr, 0, c->d_near_ij, c->d_near_tau,
+                    c->near_cap, s);
+    ev_end(c, ev);
+    launch_compress(a.L, a.root, s);
+    launch_segment(a.L, a.root, a.members, a.comp_start, a.comp_size, a.d_ncomp, c->seg_scratch, s);
+    int32_t nc = 0;
+    CC_CUDA(c, cudaMemcpyAsync(&nc, a.d_ncomp, 4, cudaMemcpyDeviceToHost, s));
+    CC_CUDA(c, cudaStreamSynchronize(s));
+    ncomp = nc;
+    a.h_size.resize(nc);
+    a.h_start.resize(nc);
+    if (nc > 0) {
+        CC_CUDA(c, cudaMemcpyAsync(a.h_size.data(), a.comp_size, nc * 4, cudaMemcpyDeviceToHost, s));
+        CC_CUDA(c, cudaMemcpyAsync(a.h_start.data(), a.comp_start, nc * 4, cudaMemcpyDeviceToHost, s));
+        CC_CUDA(c, cudaStreamSynchronize(s));
+    }
+    // statistics: n(n-1)/2 tau pairs per set, cross-component kick pairs
+    unsigned long long tp = 0, inner = 0, memb = 0, all = 0;
+    for (int32_t n : a.h_set_n) {
+        tp += (unsigned long long)n * (n - 1) / 2;
+        all += n;
+    }
+    for (int32_t k : a.h_size) {
+        inner += (unsigned long long)k * (k - 1) / 2;
+        memb += k;
+    }
+    c->st.splits += a.h_set_n.size();
+    c->st.tau_pairs += tp;
+    if (c->timing) {
+        c->tm.tau_pairs += tp;
+        c->tm.kick_pairs += tp - inner;
+    }
+    c->st.components += nc;
+    c->st.kick_pairs += tp - inner;
+    c->st.drifts += 2 * (all - memb);
+    return CC_OK;
+}
+
+static int dkd(cc_ctx *c, LevelAlloc &a, double h)
+{
+    const cudaStream_t s = c->stream;
+    long long nit = 0;
+    for (int32_t n : a.h_set_n) nit += (n + KICK_TILE - 1) / KICK_TILE;
+    launch_drift(a.L, a.root, 0.5 * h, s);
+    const int ev = ev_begin(c, 1);
+    launch_kick(a.L, a.root, (int)nit, c->p.G, c->p.eps * c->p.eps, h, c->p.precision, c->d_ctr, nullptr, s);
+    ev_end(c, ev);
+    launch_drift(a.L, a.root, 0.5 * h, s);
+    return CC_OK;
+}
+
+static int process(cc_ctx *c, int d, double h)
+{
+    if (d > c->p.max_depth) return fail(c, CC_E_DEPTH, "recursion deeper than max_depth");
+    if (d > c->st.max_depth_seen) c->st.max_depth_seen = d;
+    // lv is sized once at init (max_depth + 2 levels) and never reallocates,
+    // so references into it stay valid across the recursion
+    LevelAlloc &a = c->lv[d];
+    int ncomp = 0;
+    CC_TRY(split_level(c, a, h, ncomp));
+    // classify the components (host, sizes are known)
+    std::vector<int32_t> kl, lstart, lsize;
+    for (int q = 0; q < ncomp; ++q) {
+        const int sz = a.h_size[q];
+        if (c->p.kepler && sz == 2) kl.push_back(q);
+        else {
+            lstart.push_back(a.h_start[q]);
+            lsize.push_back(sz);
+        }
+    }
+    const int nk = (int)kl.size(), nl = (int)lsize.size();
+    if (nk) CC_CUDA(c, cudaMemcpyAsync(a.klist, kl.data(), nk * 4, cudaMemcpyHostToDevice, c->stream));
+    c->st.kepler_calls += 2ull * nk;
+    int nmem = 0;
+    if (nl) {
+        SetLayout S;
+        make_layout(lsize, S);
+        std::vector<int32_t> pref(nl + 1, 0);
+        for (int q = 0; q < nl; ++q) pref[q + 1] = pref[q] + lsize[q];
+        nmem = pref[nl];
+        CC_CUDA(c, cudaMemcpyAsync(a.lcomp_start, lstart.data(), nl * 4, cudaMemcpyHostToDevice, c->stream));
+        CC_CUDA(c, cudaMemcpyAsync(a.lpref, pref.data(), (nl + 1) * 4, cudaMemcpyHostToDevice, c->stream));
+        CC_CUDA(c, cudaMemcpyAsync(a.ldst, S.start.data(), nl * 4, cudaMemcpyHostToDevice, c->stream));
+        CC_TRY(upload_layout(c, c->lv[d + 1], S));
+    }
+    LevelAlloc &a2 = a;
+    for (int half = 0; half < 2; ++half) {
+        if (half == 1) CC_TRY(dkd(c, a2, h));
+        if (nk) launch_kepler(a2.L, a2.members, a2.comp_start, a2.klist, nk, c->p.G, 0.5 * h, c->d_ctr, c->stream);
+        if (nl) {
+            LevelAlloc &ch = c->lv[d + 1];
+            launch_gather(a2.L, ch.L, a2.members, a2.lcomp_start, a2.lpref, a2.ldst, nl, nmem, nl, c->stream);
+            CC_TRY(process(c, d + 1, 0.5 * h));
+            launch_scatter(a2.L, ch.L, c->stream);
+        }
+    }
+    return CC_OK;
+}
+
+// level-0 layout of the systems
+static int setup_systems(cc_ctx *c)
+{
+    std::vector<int32_t> sizes;
+    for (size_t q = 0; q + 1 < c->sys_off.size(); ++q) sizes.push_back((int32_t)(c->sys_off[q + 1] - c->sys_off[q]));
+    SetLayout S;
+    make_layout(sizes, S);
+    CC_TRY(upload_layout(c, c->lv[0], S));
+    if (c->d_sys_off) cudaFree(c->d_sys_off);
+    c->d_sys_off = nullptr;
+    std::vector<int32_t> off(c->sys_off.begin(), c->sys_off.end());
+    CC_CUDA(c, cudaMalloc(&c->d_sys_off, off.size() * 4));
+    CC_CUDA(c, cudaMemcpyAsync(c->d_sys_off, off.data(), off.size() * 4, cudaMemcpyHostToDevice, c->stream));
+    CC_CUDA(c, cudaStreamSynchronize(c->stream));
+    return CC_OK;
+}
+
+static int reset_call_counters(cc_ctx *c)
+{
+    c->launch_mark = g_launches;
+    CC_CUDA(c, cudaMemsetAsync(&c->d_ctr->edges, 0, sizeof(unsigned long long) * 2, c->stream));
+    return CC_OK;
+}
+
+static int harvest_counters(cc_ctx *c)
+{
+    c->st.launches += g_launches - c->launch_mark;
+    c->launch_mark = g_launches;
+    DevCounters h;
+    CC_CUDA(c, cudaMemcpyAsync(&h, c->d_ctr, sizeof(DevCounters), cudaMemcpyDeviceToHost, c->stream));
+    CC_CUDA(c, cudaStreamSynchronize(c->stream));
+    c->st.edges += h.edges;
+    c->st.near_pairs += h.near_pairs;
+    return CC_OK;
+}
+
+// ------------------------------------------------------------ C ABI
+extern "C" {
+
+int cc_default_params(cc_params *p)
+{
+    if (!p) return CC_E_ARG;
+    std::memset(p, 0, sizeof(*p));
+    p->G = 1.0;
+    p->eps = 0.0;
+    p->eta = 0.03;
+    p->dt = 1.0 / 64.0;
+    p->h_fp64 = 0.0;
+    p->near_tol = 1e-12;
+    p->precision = CC_PREC_FP64;
+    p->kepler = 0;
+    p->max_depth = 64;
+    p->s_small = 32;
+    p->eta_outside = 0;
+    return CC_OK;
+}
+
+static bool finite_pos(double v) { return std::isfinite(v) && v > 0.0; }
+
+int cc_init(cc_ctx **out, int64_t n, const double *m, const double *x3, const double *v3, const cc_params *p,
+            void *stream)
+{
+    g_init_err.clear();
+    if (!out || n < 1 || n > (1 << 28) || !m || !x3 || !v3 || !p) {
+        g_init_err = "cc_init: invalid argument";
+        return CC_E_ARG;
+    }
+    *out = nullptr;
+    if (!(p->G > 0.0) || !(p->eps >= 0.0) || !finite_pos(p->eta) || !finite_pos(p->dt) || p->max_depth < 0 ||
+        p->max_depth > 200 || (p->precision != CC_PREC_FP64 && p->precision != CC_PREC_MIXED) ||
+        (p->kepler && p->eps != 0.0) || p->s_small < 0 || p->s_small > 32) {
+        g_init_err = "cc_init: invalid parameters";
+        return CC_E_ARG;
+    }
+    cc_ctx *c = new cc_ctx();
+    c->n = n;
+    c->p = *p;
+    c->eta_run = p->eta;
+    c->stream = (cudaStream_t)stream;
+    auto bail = [&](int code) {
+        g_init_err = c->err;
+        cc_destroy(c);
+        return code;
+    };
+    if (cudaMalloc(&c->d_x3, 3 * n * 8) != cudaSuccess || cudaMalloc(&c->d_v3, 3 * n * 8) != cudaSuccess ||
+        cudaMalloc(&c->d_m, n * 8) != cudaSuccess || cudaMalloc(&c->d_ctr, sizeof(DevCounters)) != cudaSuccess ||
+        cudaMalloc(&c->d_near_ij, c->near_cap * 8) != cudaSuccess ||
+        cudaMalloc(&c->d_near_tau, c->near_cap * 8) != cudaSuccess ||
+        cudaMalloc(&c->d_bad, 16) != cudaSuccess) {
+        cudaGetLastError();
+        c->err = "cc_init: device allocation failed";
+        return bail(CC_E_NOMEM);
+    }
+    cudaMemsetAsync(c->d_ctr, 0, sizeof(DevCounters), c->stream);
+    c->lv.resize(p->max_depth + 2);
+    int rc = cc_set_state(c, 0.0, m, x3, v3);
+    if (rc) return bail(rc);
+    c->sys_off = {0, n};
+    rc = setup_systems(c);
+    if (rc) return bail(rc);
+    *out = c;
+    return CC_OK;
+}
+
+int cc_set_systems(cc_ctx *c, const int64_t *sys_off, int64_t nsys)
+{
+    if (!c || !sys_off || nsys < 1) return c ? fail(c, CC_E_ARG, "cc_set_systems: invalid argument") : CC_E_ARG;
+    if (sys_off[0] != 0 || sys_off[nsys] != c->n) return fail(c, CC_E_ARG, "cc_set_systems: bad offsets");
+    for (int64_t q = 0; q < nsys; ++q)
+        if (sys_off[q + 1] <= sys_off[q]) return fail(c, CC_E_ARG, "cc_set_systems: empty or decreasing system");
+    c->sys_off.assign(sys_off, sys_off + nsys + 1);
+    return setup_systems(c);
+}
+
+int cc_set_stream(cc_ctx *c, void *stream)
+{
+    if (!c) return CC_E_ARG;
+    c->stream = (cudaStream_t)stream;
+    return CC_OK;
+}
+
+int cc_set_state(cc_ctx *c, double t, const double *m, const double *x3, const double *v3)
+{
+    if (!c) return CC_E_ARG;
+    const int64_t n = c->n;
+    if (!std::isfinite(t)) return fail(c, CC_E_NONFINITE, "non-finite time");
+    // stage into scratch, validate on the device, then commit
+    CC_TRY(ensure_tmp(c, (size_t)n * 8 * 7 + 64));
+    double *sm = (double *)c->tmp, *sx = sm + n, *sv = sx + 3 * n;
+    if (m) CC_TRY(copy_in(c, sm, m, n * 8));
+    if (x3) CC_TRY(copy_in(c, sx, x3, 3 * n * 8));
+    if (v3) CC_TRY(copy_in(c, sv, v3, 3 * n * 8));
+    CC_CUDA(c, cudaMemsetAsync(c->d_bad, 0, 4, c->stream));
+    launch_check_state(m ? sm : nullptr, x3 ? sx : nullptr, v3 ? sv : nullptr, n, c->d_bad, c->stream);
+    unsigned bad = 0;
+    CC_CUDA(c, cudaMemcpyAsync(&bad, c->d_bad, 4, cudaMemcpyDeviceToHost, c->stream));
+    CC_CUDA(c, cudaStreamSynchronize(c->stream));
+    if (bad & 2u) return fail(c, CC_E_NONFINITE, "masses must be finite and > 0");
+    if (bad) return fail(c, CC_E_NONFINITE, "non-finite position or velocity");
+    if (m) CC_CUDA(c, cudaMemcpyAsync(c->d_m, sm, n * 8, cudaMemcpyDeviceToDevice, c->stream));
+    if (x3) CC_CUDA(c, cudaMemcpyAsync(c->d_x3, sx, 3 * n * 8, cudaMemcpyDeviceToDevice, c->stream));
+    if (v3) CC_CUDA(c, cudaMemcpyAsync(c->d_v3, sv, 3 * n * 8, cudaMemcpyDeviceToDevice, c->stream));
+    c->t = t;
+    return CC_OK;
+}
+
+int cc_get_state(cc_ctx *c, double *t, double *m, double *x3, double *v3)
+{
+    if (!c) return CC_E_ARG;
+    const int64_t n = c->n;
+    if (t) *t = c->t;
+    CC_TRY(copy_out(c, m, c->d_m, n * 8));
+    CC_TRY(copy_out(c, x3, c->d_x3, 3 * n * 8));
+    CC_TRY(copy_out(c, v3, c->d_v3, 3 * n * 8));
+    CC_CUDA(c, cudaStreamSynchronize(c->stream));
+    return CC_OK;
+}
+
+int cc_evolve(cc_ctx *c, double t_end, double eta)
+{
+    if (!c) return CC_E_ARG;
+    if (eta > 0.0) c->eta_run = eta;
+    const double span = t_end - c->t;
+    if (!(span >= -1e-15)) return fail(c, CC_E_ARG, "cc_evolve: t_end before current time");
+    const double q = span / c->p.dt;
+    const long long nsteps = std::llround(q);
+    if (std::fabs(q - (double)nsteps) > 1e-9 * std::max(1.0, std::fabs(q)))
+        return fail(c, CC_E_ARG, "cc_evolve: t_end - t is not a whole number of steps dt");
+    CC_TRY(reset_call_counters(c));
+    const double t0 = c->t;
+    for (long long k = 0; k < nsteps; ++k) {
+        launch_pack_state(c->d_x3, c->d_v3, c->d_m, c->n, c->lv[0].L, c->d_sys_off, c->stream);
+        int rc = process(c, 0, c->p.dt);
+        if (rc) return rc;
+        launch_unpack_state(c->d_x3, c->d_v3, c->n, c->lv[0].L, c->stream);
+        CC_TRY(check_device_error(c));
+        ev_resolve(c);
+        c->t = t0 + (double)(k + 1) * c->p.dt;
+    }
+    CC_CUDA(c, cudaGetLastError());
+    CC_TRY(harvest_counters(c));
+    return CC_OK;
+}
+
+// stage a caller set (ascending ids) into the unit level as one set
+static int stage_set(cc_ctx *c, const int32_t *set, int64_t n_set, const int32_t **dset_out)
+{
+    if (n_set < 1 || n_set > c->n) return fail(c, CC_E_ARG, "set size out of range");
+    SetLayout S;
+    make_layout(std::vector<int32_t>(1, (int32_t)n_set), S);
+    CC_TRY(upload_layout(c, c->unit, S));
+    CC_TRY(ensure_tmp(c, (size_t)n_set * 4 * 4 + 64));
+    int32_t *dset = (int32_t *)c->tmp;
+    if (set) {
+        CC_TRY(copy_in(c, dset, set, n_set * 4));
+    } else {
+        if (n_set != c->n) return fail(c, CC_E_ARG, "NULL set requires n_set == n");
+        std::vector<int32_t> all(n_set);
+        for (int64_t k = 0; k < n_set; ++k) all[k] = (int32_t)k;
+        CC_CUDA(c, cudaMemcpyAsync(dset, all.data(), n_set * 4, cudaMemcpyHostToDevice, c->stream));
+        CC_CUDA(c, cudaStreamSynchronize(c->stream));
+    }
+    CC_CUDA(c, cudaMemsetAsync(c->d_bad, 0, 4, c->stream));
+    launch_gather_set(c->d_x3, c->d_v3, c->d_m, c->n, dset, (int)n_set, c->unit.L, c->d_bad, c->stream);
+    unsigned bad = 0;
+    CC_CUDA(c, cudaMemcpyAsync(&bad, c->d_bad, 4, cudaMemcpyDeviceToHost, c->stream));
+    CC_CUDA(c, cudaStreamSynchronize(c->stream));
+    if (bad) return fail(c, CC_E_ARG, "set ids must be distinct, ascending and in [0, n)");
+    if (dset_out) *dset_out = dset;
+    return CC_OK;
+}
+
+int cc_components(cc_ctx *c, const int32_t *set, int64_t n_set, double h, int32_t *labels_out, int64_t *n_comp)
+{
+    if (!c || !(h > 0.0) || !std::isfinite(h)) return c ? fail(c, CC_E_ARG, "cc_components: bad argument") : CC_E_ARG;
+    CC_TRY(stage_set(c, set, n_set, nullptr));
+    CC_TRY(reset_call_counters(c));
+    int nc = 0;
+    CC_TRY(split_level(c, c->unit, h, nc));
+    if (labels_out) {
+        int32_t *dl = (int32_t *)c->tmp + n_set;
+        launch_label_canon(c->unit.L, c->unit.root, dl, (int)n_set, c->stream);
+        CC_TRY(copy_out(c, labels_out, dl, n_set * 4));
+    }
+    if (n_comp) *n_comp = nc;
+    CC_TRY(check_device_error(c));
+    CC_TRY(harvest_counters(c));
+    return CC_OK;
+}
+
+int cc_timestep_graph(cc_ctx *c, const int32_t *set, int64_t n_set, double h, int64_t *n_edges, int32_t *edges_out,
+                      int64_t cap, int64_t *n_near)
+{
+    if (!c || !(h > 0.0) || !std::isfinite(h) || cap < 0)
+        return c ? fail(c, CC_E_ARG, "cc_timestep_graph: bad argument") : CC_E_ARG;
+    CC_TRY(stage_set(c, set, n_set, nullptr));
+    // pass 1: count edges (and split, which also fills the union-find)
+    CC_TRY(reset_call_counters(c));
+    LevelAlloc &u = c->unit;
+    const TauParams P = tau_params(c, h);
+    const long long nt = (n_set + TAU_TILE - 1) / TAU_TILE;
+    launch_init_parent(u.L, c->stream);
+    launch_tau_hook(u.L, (int)(nt * (nt + 1) / 2), P, c->p.precision, c->d_ctr, nullptr, 0, c->d_near_ij,
+                    c->d_near_tau, c->near_cap, c->stream);
+    DevCounters h1;
+    CC_CUDA(c, cudaMemcpyAsync(&h1, c->d_ctr, sizeof(h1), cudaMemcpyDeviceToHost, c->stream));
+    CC_CUDA(c, cudaStreamSynchronize(c->stream));
+    const long long ne = (long long)h1.edges;
+    if (n_edges) *n_edges = ne;
+    if (n_near) *n_near = (long long)h1.near_pairs;
+    c->st.edges += h1.edges;
+    c->st.near_pairs += h1.near_pairs;
+    c->st.tau_pairs += (unsigned long long)n_set * (n_set - 1) / 2;
+    CC_TRY(check_device_error(c));
+    if (edges_out && ne > 0) {
+        // pass 2: write the edges, then sort them lexicographically
+        const size_t need = (size_t)ne * 8 + edge_sort_scratch_bytes(ne) + (size_t)n_set * 16 + 1024;
+        CC_TRY(ensure_tmp(c, need));
+        int32_t *de = (int32_t *)((char *)c->tmp + (size_t)n_set * 16);
+        void *ss = (void *)(de + 2 * ne);
+        CC_TRY(reset_call_counters(c));
+        launch_init_parent(u.L, c->stream);
+        launch_tau_hook(u.L, (int)(nt * (nt + 1) / 2), P, c->p.precision, c->d_ctr, de, ne, c->d_near_ij,
+                        c->d_near_tau, c->near_cap, c->stream);
+        int bits = 0;
+        while (bits < 31 && (1ll << bits) <= c->n) ++bits;
+        launch_sort_edges(de, ne, bits, ss, c->stream);
+        CC_TRY(copy_out(c, edges_out, de, (size_t)std::min<long long>(ne, cap) * 8));
+        CC_CUDA(c, cudaStreamSynchronize(c->stream));
+        CC_TRY(check_device_error(c));
+        if (ne > cap) return fail(c, CC_E_CAPACITY, "edges_out too small");
+    }
+    return CC_OK;
+}
+
+int cc_kick(cc_ctx *c, const int32_t *set, int64_t n_set, const int32_t *labels, double h)
+{
+    if (!c || !labels || !std::isfinite(h)) return c ? fail(c, CC_E_ARG, "cc_kick: bad argument") : CC_E_ARG;
+    CC_TRY(stage_set(c, set, n_set, nullptr));
+    int32_t *dl = (int32_t *)c->tmp + 2 * n_set + 8;
+    dl = (int32_t *)(((uintptr_t)dl + 15) & ~(uintptr_t)15);
+    CC_TRY(copy_in(c, dl, labels, n_set * 4));
+    LevelAlloc &u = c->unit;
+    const int nit = (int)((n_set + KICK_TILE - 1) / KICK_TILE);
+    launch_kick(u.L, dl, nit, c->p.G, c->p.eps * c->p.eps, h, c->p.precision, c->d_ctr, nullptr, c->stream);
+    launch_scatter_set(c->d_x3, c->d_v3, c->n, u.L, (int)n_set, false, true, c->stream);
+    CC_CUDA(c, cudaStreamSynchronize(c->stream));
+    return check_device_error(c);
+}
+
+int cc_drift(cc_ctx *c, const int32_t *set, int64_t n_set, const int32_t *labels, double h)
+{
+    if (!c || !labels || !std::isfinite(h)) return c ? fail(c, CC_E_ARG, "cc_drift: bad argument") : CC_E_ARG;
+    CC_TRY(stage_set(c, set, n_set, nullptr));
+    LevelAlloc &u = c->unit;
+    // labels, singleton flags and sort scratch live after the staged set
+    int32_t *dl = (int32_t *)c->tmp + 2 * n_set + 8;
+    dl = (int32_t *)(((uintptr_t)dl + 15) & ~(uintptr_t)15);
+    int32_t *single = dl + n_set + 4;
+    void *ss = (void *)(single + n_set + 4);
+    const size_t need = (size_t)((char *)ss - (char *)c->tmp) + sort_scratch_bytes(n_set) + (size_t)n_set * 8 + 256;
+    if (need > c->tmp_sz) {
+        // grow the staging buffer and restage (the set copy lives there)
+        CC_TRY(ensure_tmp(c, need));
+        CC_TRY(stage_set(c, set, n_set, nullptr));
+        dl = (int32_t *)c->tmp + 2 * n_set + 8;
+        dl = (int32_t *)(((uintptr_t)dl + 15) & ~(uintptr_t)15);
+        single = dl + n_set + 4;
+        ss = (void *)(single + n_set + 4);
+    }
+    CC_TRY(copy_in(c, dl, labels, n_set * 4));
+    launch_singleton_from_labels(dl, (int)n_set, single, ss, c->stream);
+    launch_drift_labels(u.L, single, h, c->stream);
+    launch_scatter_set(c->d_x3, c->d_v3, c->n, u.L, (int)n_set, true, false, c->stream);
+    CC_CUDA(c, cudaStreamSynchronize(c->stream));
+    return check_device_error(c);
+}
+
+int cc_stats(cc_ctx *c, cc_stats_t *out)
+{
+    if (!c || !out) return CC_E_ARG;
+    *out = c->st;
+    return CC_OK;
+}
+
+int cc_reset_stats(cc_ctx *c)
+{
+    if (!c) return CC_E_ARG;
+    std::memset(&c->st, 0, sizeof(c->st));
+    return CC_OK;
+}
+
+int cc_energy(cc_ctx *c, double *E, double *P3, double *L3)
+{
+    if (!c) return CC_E_ARG;
+    const int nb = energy_blocks(c->n);
+    if (nb > c->partial_cap) {
+        if (c->d_partial) cudaFree(c->d_partial);
+        c->d_partial = nullptr;
+        CC_CUDA(c, cudaMalloc(&c->d_partial, (size_t)nb * 8 * 8));
+        c->partial_cap = nb;
+    }
+    launch_energy(c->d_x3, c->d_v3, c->d_m, c->n, c->p.G, c->p.eps * c->p.eps, c->d_partial, nb, c->stream);
+    std::vector<double> h((size_t)nb * 8);
+    CC_CUDA(c, cudaMemcpyAsync(h.data(), c->d_partial, h.size() * 8, cudaMemcpyDeviceToHost, c->stream));
+    CC_CUDA(c, cudaStreamSynchronize(c->stream));
+    double acc[8] = {0, 0, 0, 0, 0, 0, 0, 0};
+    for (int b = 0; b < nb; ++b)
+        for (int k = 0; k < 8; ++k) acc[k] += h[(size_t)b * 8 + k];
+    if (E) *E = acc[0] + acc[1];
+    if (P3) { P3[0] = acc[2]; P3[1] = acc[3]; P3[2] = acc[4]; }
+    if (L3) { L3[0] = acc[5]; L3[1] = acc[6]; L3[2] = acc[7]; }
+    return CC_OK;
+}
+
+int cc_near_pairs(cc_ctx *c, int32_t *pairs, double *tau, int64_t cap, int64_t *n)
+{
+    if (!c || cap < 0) return CC_E_ARG;
+    unsigned long long cnt = 0;
+    CC_CUDA(c, cudaMemcpyAsync(&cnt, &c->d_ctr->near_pairs, 8, cudaMemcpyDeviceToHost, c->stream));
+    CC_CUDA(c, cudaStreamSynchronize(c->stream));
+    if (n) *n = (int64_t)cnt;
+    const long long k = std::min<long long>(std::min<long long>((long long)cnt, cap), c->near_cap);
+    if (pairs) CC_TRY(copy_out(c, pairs, c->d_near_ij, (size_t)k * 8));
+    if (tau) CC_TRY(copy_out(c, tau, c->d_near_tau, (size_t)k * 8));
+    CC_CUDA(c, cudaStreamSynchronize(c->stream));
+    return CC_OK;
+}
+
+int cc_set_timing(cc_ctx *c, int on)
+{
+    if (!c) return CC_E_ARG;
+    CC_CUDA(c, cudaStreamSynchronize(c->stream));
+    ev_resolve(c);
+    c->timing = on != 0;
+    std::memset(&c->tm, 0, sizeof(c->tm));
+    return CC_OK;
+}
+
+int cc_timing(cc_ctx *c, cc_timing_t *out)
+{
+    if (!c || !out) return CC_E_ARG;
+    CC_CUDA(c, cudaStreamSynchronize(c->stream));
+    ev_resolve(c);
+    *out = c->tm;
+    return CC_OK;
+}
+
+int cc_destroy(cc_ctx *c)
+{
+    if (!c) return CC_OK;
+    if (c->stream) cudaStreamSynchronize(c->stream);
+    for (cudaEvent_t e : c->evs) cudaEventDestroy(e);
+    for (auto &a : c->lv) free_level(a);
+    free_level(c->unit);
+    void *ptrs[] = {c->d_x3, c->d_v3, c->d_m, c->d_ctr, c->d_near_ij, c->d_near_tau, c->d_partial,
+                    c->tmp, c->seg_scratch, c->d_sys_off, c->d_bad};
+    for (void *q : ptrs)
+        if (q) cudaFree(q);
+    delete c;
+    return CC_OK;
+}
+
+int cc_probe_peaks(void *stream, double *fp64_flops, double *fp32_flops)
+{
+    int dev = 0, nsm = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev) !=
+                                                 cudaSuccess) {
+        cudaGetLastError();
+        g_init_err = "cc_probe_peaks: no CUDA device";
+        return CC_E_CUDA;
+    }
+    if (fp64_flops) *fp64_flops = probe_fma(1, nsm, (cudaStream_t)stream);
+    if (fp32_flops) *fp32_flops = probe_fma(0, nsm, (cudaStream_t)stream);
+    if (cudaGetLastError() != cudaSuccess) {
+        g_init_err = "cc_probe_peaks: kernel failed";
+        return CC_E_CUDA;
+    }
+    return CC_OK;
+}
+
+const char *cc_last_error(cc_ctx *c)
+{
+    if (!c) return g_init_err.c_str();
+    return c->err.c_str();
+}
+
+}  // extern "C"

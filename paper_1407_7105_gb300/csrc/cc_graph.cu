@@ -1,0 +1,623 @@
+// cc_graph.cu -- graph and data-movement kernels of the CC split
+// (arXiv:1407.7105 Sec. 2.2-2.3):
+//   * union-find compression: root[k] = smallest packed index of k's
+//     component, sizes by root;
+//   * segmentation: a stable sort of component members by root, so every
+//     non-trivial component C_i is a contiguous run of ascending members
+//     (the paper's particle reshuffle into start/end ranges, Sec. 2.3);
+//   * gathering components into the next level's packed buffer and back;
+//   * the drift D_{h,T_i} of Eq. (drift) for rest-set members.
+// Scans and the radix sort are written here (no library kernels).
+#include "cc_internal.cuh"
+
+namespace cc {
+
+// ------------------------------------------------------------ scan
+constexpr int SCAN_T = 512;
+constexpr int SCAN_ITEMS = 4;
+constexpr int SCAN_TILE = SCAN_T * SCAN_ITEMS;
+
+__device__ __forceinline__ int block_exclusive_scan(int v, int *tmp, int &total)
+{
+    // tmp: SCAN_T/32 ints
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    int x = v;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        int y = __shfl_up_sync(0xffffffffu, x, o);
+        if (lane >= o) x += y;
+    }
+    if (lane == 31) tmp[w] = x;
+    __syncthreads();
+    if (w == 0) {
+        int t = lane < (int)(blockDim.x >> 5) ? tmp[lane] : 0;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            int y = __shfl_up_sync(0xffffffffu, t, o);
+            if (lane >= o) t += y;
+        }
+        if (lane < (int)(blockDim.x >> 5)) tmp[lane] = t;
+    }
+    __syncthreads();
+    total = tmp[(blockDim.x >> 5) - 1];
+    int base = w > 0 ? tmp[w - 1] : 0;
+    __syncthreads();
+    return base + x - v;
+}
+
+// out[k] = sum of in[0..k); block sums to bsum
+__global__ void __launch_bounds__(SCAN_T) k_scan_tiles(const int *in, int *out, int n, int *bsum)
+{
+    __shared__ int tmp[SCAN_T / 32];
+    const int base = blockIdx.x * SCAN_TILE + threadIdx.x * SCAN_ITEMS;
+    int v[SCAN_ITEMS], s = 0;
+#pragma unroll
+    for (int k = 0; k < SCAN_ITEMS; ++k) {
+        v[k] = base + k < n ? in[base + k] : 0;
+        s += v[k];
+    }
+    int total;
+    int ex = block_exclusive_scan(s, tmp, total);
+#pragma unroll
+    for (int k = 0; k < SCAN_ITEMS; ++k) {
+        if (base + k < n) out[base + k] = ex;
+        ex += v[k];
+    }
+    if (threadIdx.x == 0) bsum[blockIdx.x] = total;
+}
+
+// single block: exclusive scan of bsum[0..nb) in place, chunked
+__global__ void __launch_bounds__(SCAN_T) k_scan_sums(int *bsum, int nb, int *grand)
+{
+    __shared__ int tmp[SCAN_T / 32];
+    __shared__ int carry;
+    if (threadIdx.x == 0) carry = 0;
+    __syncthreads();
+    for (int c0 = 0; c0 < nb; c0 += SCAN_T) {
+        const int k = c0 + threadIdx.x;
+        int v = k < nb ? bsum[k] : 0, total;
+        int ex = block_exclusive_scan(v, tmp, total);
+        if (k < nb) bsum[k] = ex + carry;
+        __syncthreads();
+        if (threadIdx.x == 0) carry += total;
+        __syncthreads();
+    }
+    if (threadIdx.x == 0 && grand) *grand = carry;
+}
+
+__global__ void k_scan_add(int *out, int n, const int *bsum)
+{
+    const int k = blockIdx.x * SCAN_TILE + threadIdx.x;
+    const int add = bsum[blockIdx.x];
+    for (int q = 0; q < SCAN_ITEMS; ++q) {
+        const int idx = k + q * SCAN_T;
+        if (idx < n && idx < (int)(blockIdx.x + 1) * SCAN_TILE) out[idx] += add;
+    }
+}
+
+static int scan_blocks(int n) { return (n + SCAN_TILE - 1) / SCAN_TILE; }
+
+// exclusive scan of n ints; scratch needs scan_blocks(n) ints; *grand = total
+static void device_scan(const int *in, int *out, int n, int *bsum, int *grand, cudaStream_t s)
+{
+    if (n <= 0) return;
+    const int nb = scan_blocks(n);
+    k_scan_tiles<<<nb, SCAN_T, 0, s>>>(in, out, n, bsum);
+    CC_COUNT_LAUNCH(1);
+    k_scan_sums<<<1, SCAN_T, 0, s>>>(bsum, nb, grand);
+    CC_COUNT_LAUNCH(1);
+    if (nb > 1) {
+        k_scan_add<<<nb, SCAN_T, 0, s>>>(out, n, bsum);
+        CC_COUNT_LAUNCH(1);
+    }
+}
+
+// ------------------------------------------------------------ radix sort
+// Stable LSD radix sort of (key, val) pairs, 8-bit digits.  Per pass:
+// per-tile digit histograms, one exclusive scan over [digit][tile], and a
+// stable scatter whose in-tile ranks come from warp match + per-warp
+// digit counts combined in warp order.
+constexpr int RS_T = 256;
+constexpr int RS_ROUNDS = 8;
+constexpr int RS_TILE = RS_T * RS_ROUNDS;
+
+__global__ void __launch_bounds__(RS_T) k_rs_hist(const uint32_t *keys, int n, int shift, int *hist, int ntiles)
+{
+    __shared__ int h[256];
+    h[threadIdx.x] = 0;
+    __syncthreads();
+    const int b = blockIdx.x * RS_TILE;
+    for (int r = 0; r < RS_ROUNDS; ++r) {
+        const int i = b + r * RS_T + threadIdx.x;
+        if (i < n) atomicAdd(&h[(keys[i] >> shift) & 255u], 1);
+    }
+    __syncthreads();
+    hist[threadIdx.x * ntiles + blockIdx.x] = h[threadIdx.x];
+}
+
+__global__ void __launch_bounds__(RS_T) k_rs_scatter(const uint32_t *kin, const int32_t *vin, uint32_t *kout,
+                                                      int32_t *vout, int n, int shift, const int *offs,
+                                                      int ntiles)
+{
+    __shared__ int base[256];
+    __shared__ int wc[RS_T / 32][257];
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    base[threadIdx.x] = offs[threadIdx.x * ntiles + blockIdx.x];
+    const unsigned lt = (1u << lane) - 1u;
+    for (int r = 0; r < RS_ROUNDS; ++r) {
+        for (int q = threadIdx.x; q < (RS_T / 32) * 257; q += RS_T) (&wc[0][0])[q] = 0;
+        __syncthreads();
+        const int i = blockIdx.x * RS_TILE + r * RS_T + threadIdx.x;
+        const bool valid = i < n;
+        uint32_t key = 0;
+        int32_t val = 0;
+        int d = 256;
+        if (valid) {
+            key = kin[i];
+            val = vin[i];
+            d = (key >> shift) & 255u;
+        }
+        const unsigned peers = __match_any_sync(0xffffffffu, d);
+        const int rank = __popc(peers & lt);
+        if (valid && rank == 0) wc[w][d] = __popc(peers);
+        __syncthreads();
+        int run = 0;
+        for (int ww = 0; ww < RS_T / 32; ++ww) {
+            const int c = wc[ww][threadIdx.x];
+            wc[ww][threadIdx.x] = run;
+            run += c;
+        }
+        __syncthreads();
+        if (valid) {
+            const int pos = base[d] + wc[w][d] + rank;
+            kout[pos] = key;
+            vout[pos] = val;
+        }
+        __syncthreads();
+        base[threadIdx.x] += run;
+        __syncthreads();
+    }
+}
+
+static int rs_tiles(long long n) { return (int)((n + RS_TILE - 1) / RS_TILE); }
+
+size_t sort_scratch_bytes(long long n)
+{
+    const long long nt = rs_tiles(n);
+    const long long hist = 256 * nt;
+    return (size_t)(4 * n + hist + scan_blocks((int)hist) + 16) * 4 + 256;
+}
+
+// sorts (k, v) in place by the low `bits` bits of k; scratch >= sort_scratch_bytes(n)
+static void radix_sort(uint32_t *k, int32_t *v, int n, int bits, void *scratch, cudaStream_t s)
+{
+    if (n <= 1 || bits <= 0) return;
+    const int nt = rs_tiles(n);
+    uint32_t *k2 = (uint32_t *)scratch;
+    int32_t *v2 = (int32_t *)(k2 + n);
+    int *hist = (int *)(v2 + n);
+    int *bsum = hist + 256 * nt;
+    uint32_t *ka = k, *kb = k2;
+    int32_t *va = v, *vb = v2;
+    int passes = (bits + 7) / 8;
+    for (int p = 0; p < passes; ++p) {
+        const int shift = 8 * p;
+        k_rs_hist<<<nt, RS_T, 0, s>>>(ka, n, shift, hist, nt);
+        CC_COUNT_LAUNCH(1);
+        device_scan(hist, hist, 256 * nt, bsum, nullptr, s);
+        k_rs_scatter<<<nt, RS_T, 0, s>>>(ka, va, kb, vb, n, shift, hist, nt);
+        CC_COUNT_LAUNCH(1);
+        uint32_t *tk = ka; ka = kb; kb = tk;
+        int32_t *tv = va; va = vb; vb = tv;
+    }
+    if (ka != k) {
+        cudaMemcpyAsync(k, ka, sizeof(uint32_t) * n, cudaMemcpyDeviceToDevice, s);
+        cudaMemcpyAsync(v, va, sizeof(int32_t) * n, cudaMemcpyDeviceToDevice, s);
+    }
+}
+
+static int bits_for(long long maxval)
+{
+    int b = 0;
+    while (b < 32 && (1ll << b) <= maxval) ++b;
+    return b;
+}
+
+// ------------------------------------------------------------ compress
+__global__ void k_compress(Level L, int32_t *root)
+{
+    const int k = blockIdx.x * blockDim.x + threadIdx.x;
+    if (k >= L.total) return;
+    if (L.gid[k] < 0) {
+        root[k] = k;
+        return;
+    }
+    const int r = uf_find(L.parent, k);
+    root[k] = r;
+    atomicAdd(&L.cnt[r], 1);
+}
+
+void launch_compress(const Level &L, int32_t *root, cudaStream_t s)
+{
+    if (L.total <= 0) return;
+    k_compress<<<(L.total + 255) / 256, 256, 0, s>>>(L, root);
+    CC_COUNT_LAUNCH(1);
+}
+
+// ------------------------------------------------------------ segment
+__global__ void k_seg_keys(Level L, const int32_t *root, uint32_t *key, int32_t *val)
+{
+    const int k = blockIdx.x * blockDim.x + threadIdx.x;
+    if (k >= L.total) return;
+    const bool mem = L.gid[k] >= 0 && L.cnt[root[k]] >= 2;
+    key[k] = mem ? (uint32_t)root[k] : (uint32_t)L.total;
+    val[k] = k;
+}
+
+__global__ void k_seg_heads(const uint32_t *key, int n, uint32_t sentinel, int *flag)
+{
+    const int t = blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= n) return;
+    flag[t] = key[t] < sentinel && (t == 0 || key[t] != key[t - 1]) ? 1 : 0;
+}
+
+__global__ void k_seg_bounds(Level L, const uint32_t *key, const int32_t *val, const int *flag, const int *cidx,
+                             int n, int32_t *members, int32_t *comp_start, int32_t *comp_size, int32_t *ncomp)
+{
+    const int t = blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= n) return;
+    const bool mem = key[t] < (uint32_t)L.total;
+    if (mem) members[t] = val[t];
+    if (flag[t]) {
+        comp_start[cidx[t]] = t;
+        comp_size[cidx[t]] = L.cnt[key[t]];
+    }
+    if (t == n - 1) *ncomp = cidx[t] + flag[t];
+}
+
+size_t seg_scratch_bytes(int cap)
+{
+    return (size_t)cap * 4 * 4 + sort_scratch_bytes(cap) + (size_t)(scan_blocks(cap) + 16) * 4 + 1024;
+}
+
+void launch_segment(const Level &L, const int32_t *root, int32_t *members, int32_t *comp_start,
+                    int32_t *comp_size, int32_t *d_ncomp, void *scratch, cudaStream_t s)
+{
+    const int n = L.total;
+    if (n <= 0) {
+        cudaMemsetAsync(d_ncomp, 0, sizeof(int32_t), s);
+        return;
+    }
+    uint32_t *key = (uint32_t *)scratch;
+    int32_t *val = (int32_t *)(key + n);
+    int *flag = (int *)(val + n);
+    int *cidx = flag + n;
+    int *bsum = cidx + n;
+    void *sort_scratch = (void *)(bsum + scan_blocks(n) + 16);
+    const int g = (n + 255) / 256;
+    k_seg_keys<<<g, 256, 0, s>>>(L, root, key, val);
+    CC_COUNT_LAUNCH(1);
+    radix_sort(key, val, n, bits_for(n), sort_scratch, s);
+    k_seg_heads<<<g, 256, 0, s>>>(key, n, (uint32_t)n, flag);
+    CC_COUNT_LAUNCH(1);
+    device_scan(flag, cidx, n, bsum, nullptr, s);
+    k_seg_bounds<<<g, 256, 0, s>>>(L, key, val, flag, cidx, n, members, comp_start, comp_size, d_ncomp);
+    CC_COUNT_LAUNCH(1);
+}
+
+// ------------------------------------------------------------ movement
+__global__ void k_fill_pad(Level L)
+{
+    const int k = blockIdx.x * blockDim.x + threadIdx.x;
+    if (k >= L.total) return;
+    L.gid[k] = -1;
+    L.sidx[k] = -1;
+}
+
+static void fill_pad(const Level &L, cudaStream_t s)
+{
+    if (L.total > 0) {
+        k_fill_pad<<<(L.total + 255) / 256, 256, 0, s>>>(L);
+        CC_COUNT_LAUNCH(1);
+    }
+}
+
+__device__ __forceinline__ int upper_find(const int32_t *off, int nsets, int t)
+{
+    int lo = 0, hi = nsets;
+    while (hi - lo > 1) {
+        int mid = (lo + hi) >> 1;
+        if (off[mid] <= t) lo = mid; else hi = mid;
+    }
+    return lo;
+}
+
+__global__ void k_gather(Level P, Level C, const int32_t *members, const int32_t *lcomp_start,
+                         const int32_t *lpref, const int32_t *ldst, int nl, int nmem)
+{
+    const int t = blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= nmem) return;
+    const int c = upper_find(lpref, nl, t);
+    const int w = t - lpref[c];
+    const int k = members[lcomp_start[c] + w];
+    const int d = ldst[c] + w;
+    C.x[d] = P.x[k]; C.y[d] = P.y[k]; C.z[d] = P.z[k];
+    C.vx[d] = P.vx[k]; C.vy[d] = P.vy[k]; C.vz[d] = P.vz[k];
+    C.m[d] = P.m[k];
+    C.gid[d] = P.gid[k];
+    C.src[d] = k;
+    C.sidx[d] = c;
+}
+
+void launch_gather(const Level &P, const Level &C, const int32_t *members, const int32_t *lcomp_start,
+                   const int32_t *lpref, const int32_t *ldst, int nl, int nmem, int nsets_child, cudaStream_t s)
+{
+    (void)nsets_child;
+    fill_pad(C, s);
+    if (nmem > 0) {
+        k_gather<<<(nmem + 255) / 256, 256, 0, s>>>(P, C, members, lcomp_start, lpref, ldst, nl, nmem);
+        CC_COUNT_LAUNCH(1);
+    }
+}
+
+__global__ void k_scatter(Level P, Level C)
+{
+    const int d = blockIdx.x * blockDim.x + threadIdx.x;
+    if (d >= C.total || C.gid[d] < 0) return;
+    const int k = C.src[d];
+    P.x[k] = C.x[d]; P.y[k] = C.y[d]; P.z[k] = C.z[d];
+    P.vx[k] = C.vx[d]; P.vy[k] = C.vy[d]; P.vz[k] = C.vz[d];
+}
+
+void launch_scatter(const Level &P, const Level &C, cudaStream_t s)
+{
+    if (C.total > 0) {
+        k_scatter<<<(C.total + 255) / 256, 256, 0, s>>>(P, C);
+        CC_COUNT_LAUNCH(1);
+    }
+}
+
+// state (id order) -> level 0, system q at set_start[q]
+__global__ void k_pack_state(const double *x3, const double *v3, const double *m, long long n, Level L,
+                             const int32_t *sys_off)
+{
+    const long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= n) return;
+    const int q = upper_find(sys_off, L.nsets, (int)t);
+    const int d = L.set_start[q] + (int)(t - sys_off[q]);
+    L.x[d] = x3[t]; L.y[d] = x3[n + t]; L.z[d] = x3[2 * n + t];
+    L.vx[d] = v3[t]; L.vy[d] = v3[n + t]; L.vz[d] = v3[2 * n + t];
+    L.m[d] = m[t];
+    L.gid[d] = (int)t;
+    L.src[d] = (int)t;
+    L.sidx[d] = q;
+}
+
+void launch_pack_state(const double *x3, const double *v3, const double *m, long long n, const Level &L,
+                       const int32_t *sys_off, cudaStream_t s)
+{
+    fill_pad(L, s);
+    if (n > 0) {
+        k_pack_state<<<(int)((n + 255) / 256), 256, 0, s>>>(x3, v3, m, n, L, sys_off);
+        CC_COUNT_LAUNCH(1);
+    }
+}
+
+__global__ void k_unpack_state(double *x3, double *v3, long long n, Level L)
+{
+    const int d = blockIdx.x * blockDim.x + threadIdx.x;
+    if (d >= L.total) return;
+    const int g = L.gid[d];
+    if (g < 0) return;
+    x3[g] = L.x[d]; x3[n + g] = L.y[d]; x3[2 * n + g] = L.z[d];
+    v3[g] = L.vx[d]; v3[n + g] = L.vy[d]; v3[2 * n + g] = L.vz[d];
+}
+
+void launch_unpack_state(double *x3, double *v3, long long n, const Level &L, cudaStream_t s)
+{
+    if (L.total > 0) {
+        k_unpack_state<<<(L.total + 255) / 256, 256, 0, s>>>(x3, v3, n, L);
+        CC_COUNT_LAUNCH(1);
+    }
+}
+
+// a caller set (ids, ascending) -> one packed set at 0; flags bad ids
+__global__ void k_gather_set(const double *x3, const double *v3, const double *m, long long n,
+                             const int32_t *set, int nset, Level L, unsigned *bad)
+{
+    const int k = blockIdx.x * blockDim.x + threadIdx.x;
+    if (k >= nset) return;
+    const int g = set[k];
+    if (g < 0 || g >= n || (k > 0 && set[k - 1] >= g)) {
+        atomicExch(bad, 1u);
+        L.gid[k] = -1;
+        return;
+    }
+    L.x[k] = x3[g]; L.y[k] = x3[n + g]; L.z[k] = x3[2 * n + g];
+    L.vx[k] = v3[g]; L.vy[k] = v3[n + g]; L.vz[k] = v3[2 * n + g];
+    L.m[k] = m[g];
+    L.gid[k] = g;
+    L.src[k] = g;
+    L.sidx[k] = 0;
+}
+
+void launch_gather_set(const double *x3, const double *v3, const double *m, long long n, const int32_t *set,
+                       int nset, const Level &L, unsigned *bad, cudaStream_t s)
+{
+    fill_pad(L, s);
+    if (nset > 0) {
+        k_gather_set<<<(nset + 255) / 256, 256, 0, s>>>(x3, v3, m, n, set, nset, L, bad);
+        CC_COUNT_LAUNCH(1);
+    }
+}
+
+__global__ void k_scatter_set(double *x3, double *v3, long long n, Level L, int nset, int wx, int wv)
+{
+    const int k = blockIdx.x * blockDim.x + threadIdx.x;
+    if (k >= nset) return;
+    const int g = L.gid[k];
+    if (g < 0) return;
+    if (wx) { x3[g] = L.x[k]; x3[n + g] = L.y[k]; x3[2 * n + g] = L.z[k]; }
+    if (wv) { v3[g] = L.vx[k]; v3[n + g] = L.vy[k]; v3[2 * n + g] = L.vz[k]; }
+}
+
+void launch_scatter_set(double *x3, double *v3, long long n, const Level &L, int nset, bool write_x,
+                        bool write_v, cudaStream_t s)
+{
+    if (nset > 0) {
+        k_scatter_set<<<(nset + 255) / 256, 256, 0, s>>>(x3, v3, n, L, nset, write_x, write_v);
+        CC_COUNT_LAUNCH(1);
+    }
+}
+
+// labels_out[k] = particle id of the root of k (the smallest id of its
+// component, since the set is ascending)
+__global__ void k_label_canon(Level L, const int32_t *root, int32_t *labels_out, int nset)
+{
+    const int k = blockIdx.x * blockDim.x + threadIdx.x;
+    if (k >= nset) return;
+    labels_out[k] = L.gid[root[k]];
+}
+
+void launch_label_canon(const Level &L, const int32_t *root, int32_t *labels_out, int nset, cudaStream_t s)
+{
+    if (nset > 0) {
+        k_label_canon<<<(nset + 255) / 256, 256, 0, s>>>(L, root, labels_out, nset);
+        CC_COUNT_LAUNCH(1);
+    }
+}
+
+// ------------------------------------------------------------ drift
+// x_i += dt * v_i (Eq. drift) for rest-set members: component size 1
+__global__ void k_drift_root(Level L, const int32_t *root, double dt)
+{
+    const int k = blockIdx.x * blockDim.x + threadIdx.x;
+    if (k >= L.total || L.gid[k] < 0 || L.cnt[root[k]] != 1) return;
+    L.x[k] = __dadd_rn(L.x[k], __dmul_rn(dt, L.vx[k]));
+    L.y[k] = __dadd_rn(L.y[k], __dmul_rn(dt, L.vy[k]));
+    L.z[k] = __dadd_rn(L.z[k], __dmul_rn(dt, L.vz[k]));
+}
+
+void launch_drift(const Level &L, const int32_t *root, double dt, cudaStream_t s)
+{
+    if (L.total > 0) {
+        k_drift_root<<<(L.total + 255) / 256, 256, 0, s>>>(L, root, dt);
+        CC_COUNT_LAUNCH(1);
+    }
+}
+
+__global__ void k_drift_flag(Level L, const int32_t *single, double dt, int nset)
+{
+    const int k = blockIdx.x * blockDim.x + threadIdx.x;
+    if (k >= nset || L.gid[k] < 0 || !single[k]) return;
+    L.x[k] = __dadd_rn(L.x[k], __dmul_rn(dt, L.vx[k]));
+    L.y[k] = __dadd_rn(L.y[k], __dmul_rn(dt, L.vy[k]));
+    L.z[k] = __dadd_rn(L.z[k], __dmul_rn(dt, L.vz[k]));
+}
+
+void launch_drift_labels(const Level &L, const int32_t *singleton, double dt, cudaStream_t s)
+{
+    if (L.total > 0) {
+        k_drift_flag<<<(L.total + 255) / 256, 256, 0, s>>>(L, singleton, dt, L.total);
+        CC_COUNT_LAUNCH(1);
+    }
+}
+
+// singleton[k] = 1 iff no other entry of labels[0..n) equals labels[k]
+__global__ void k_lab_keys(const int32_t *labels, int n, uint32_t *key, int32_t *val)
+{
+    const int k = blockIdx.x * blockDim.x + threadIdx.x;
+    if (k >= n) return;
+    key[k] = (uint32_t)labels[k] ^ 0x80000000u;
+    val[k] = k;
+}
+
+__global__ void k_lab_single(const uint32_t *key, const int32_t *val, int n, int32_t *single)
+{
+    const int t = blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= n) return;
+    const bool a = t > 0 && key[t - 1] == key[t];
+    const bool b = t + 1 < n && key[t + 1] == key[t];
+    single[val[t]] = (a || b) ? 0 : 1;
+}
+
+void launch_singleton_from_labels(const int32_t *labels, int n, int32_t *singleton, void *scratch,
+                                  cudaStream_t s)
+{
+    if (n <= 0) return;
+    uint32_t *key = (uint32_t *)scratch;
+    int32_t *val = (int32_t *)(key + n);
+    void *ss = (void *)(val + n);
+    k_lab_keys<<<(n + 255) / 256, 256, 0, s>>>(labels, n, key, val);
+    CC_COUNT_LAUNCH(1);
+    radix_sort(key, val, n, 32, ss, s);
+    k_lab_single<<<(n + 255) / 256, 256, 0, s>>>(key, val, n, singleton);
+    CC_COUNT_LAUNCH(1);
+}
+
+// ------------------------------------------------------------ validation
+// bad |= 1 if any value is non-finite; |= 2 if a mass is not > 0
+__global__ void k_check_state(const double *m, const double *x3, const double *v3, long long n, unsigned *bad)
+{
+    const long long k = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (k >= n) return;
+    unsigned b = 0;
+    if (m && !(isfinite(m[k]) && m[k] > 0.0)) b |= 2u;
+    if (x3 && !(isfinite(x3[k]) && isfinite(x3[n + k]) && isfinite(x3[2 * n + k]))) b |= 1u;
+    if (v3 && !(isfinite(v3[k]) && isfinite(v3[n + k]) && isfinite(v3[2 * n + k]))) b |= 1u;
+    if (b) atomicOr(bad, b);
+}
+
+void launch_check_state(const double *m, const double *x3, const double *v3, long long n, unsigned *bad,
+                        cudaStream_t s)
+{
+    if (n > 0) {
+        k_check_state<<<(int)((n + 255) / 256), 256, 0, s>>>(m, x3, v3, n, bad);
+        CC_COUNT_LAUNCH(1);
+    }
+}
+
+// ------------------------------------------------------------ edge order
+__global__ void k_edge_keys(const int32_t *edges, long long ne, int col, const int32_t *perm, uint32_t *key,
+                            int32_t *val)
+{
+    const long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= ne) return;
+    const int e = perm ? perm[t] : (int)t;
+    key[t] = (uint32_t)edges[2 * e + col];
+    val[t] = e;
+}
+
+__global__ void k_edge_apply(const int32_t *edges, long long ne, const int32_t *perm, int32_t *out)
+{
+    const long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= ne) return;
+    out[2 * t] = edges[2 * perm[t]];
+    out[2 * t + 1] = edges[2 * perm[t] + 1];
+}
+
+// lexicographic (i, j) order: stable sort by j, then by i
+void launch_sort_edges(int32_t *edges, long long ne, int bits, void *scratch, cudaStream_t s)
+{
+    if (ne <= 1) return;
+    const int n = (int)ne;
+    uint32_t *key = (uint32_t *)scratch;
+    int32_t *val = (int32_t *)(key + n);
+    int32_t *tmp = val + n;  // 2n
+    void *ss = (void *)(tmp + 2 * n);
+    const int g = (n + 255) / 256;
+    k_edge_keys<<<g, 256, 0, s>>>(edges, ne, 1, nullptr, key, val);
+    CC_COUNT_LAUNCH(1);
+    radix_sort(key, val, n, bits, ss, s);
+    cudaMemcpyAsync(tmp, val, sizeof(int32_t) * n, cudaMemcpyDeviceToDevice, s);
+    k_edge_keys<<<g, 256, 0, s>>>(edges, ne, 0, tmp, key, val);
+    CC_COUNT_LAUNCH(1);
+    radix_sort(key, val, n, bits, ss, s);
+    k_edge_apply<<<g, 256, 0, s>>>(edges, ne, val, tmp);
+    CC_COUNT_LAUNCH(1);
+    cudaMemcpyAsync(edges, tmp, sizeof(int32_t) * 2 * n, cudaMemcpyDeviceToDevice, s);
+}
+
+size_t edge_sort_scratch_bytes(long long ne) { return (size_t)ne * 16 + sort_scratch_bytes(ne) + 256; }
+
+}  // namespace cc

@@ -1,0 +1,247 @@
+// cc_internal.cuh -- device helpers and kernel launchers shared by the
+// translation units of libcc.so (CC split integrator, arXiv:1407.7105).
+#pragma once
+#include <cuda_runtime.h>
+#include <math_constants.h>
+#include <stdint.h>
+
+#include "../../include/cc.h"
+
+namespace cc {
+
+// ---------------------------------------------------------------- layout
+// A level buffer holds one batch of disjoint sets packed contiguously in
+// SoA form.  Every set starts at a multiple of SET_ALIGN elements so that
+// j-tiles of the double and int32 arrays start on 16-byte boundaries (TMA
+// bulk copies).  Padding elements carry gid = -1.
+constexpr int SET_ALIGN = 4;
+constexpr int PAD_TAIL = 256;  // slack past the last element (tile over-reads)
+
+struct Level {
+    double *x, *y, *z, *vx, *vy, *vz, *m;  // packed state, cap entries each
+    int32_t *gid;      // particle id, -1 = padding
+    int32_t *sidx;     // set index of the element, -1 = padding
+    int32_t *src;      // index in the parent level the element came from
+    int32_t *parent;   // union-find forest over packed indices
+    int32_t *cnt;      // component size, indexed by root
+    int32_t *set_start, *set_n;      // [nsets]
+    int32_t *tile_off;               // [nsets+1] triangular tau tiles prefix
+    int32_t *itile_off;              // [nsets+1] i-tiles prefix (kick)
+    int32_t total;                   // packed length including padding
+    int32_t nsets;
+};
+
+// bounded-wait error codes written to the device error word
+enum DevErr : unsigned {
+    DERR_NONE = 0,
+    DERR_TMA_TIMEOUT = 1,
+    DERR_UF_RETRY = 2,
+    DERR_KEPLER = 3,
+    DERR_DEPTH = 4,
+    DERR_SMALL_OVERFLOW = 5,
+};
+
+struct DevCounters {
+    unsigned long long edges;
+    unsigned long long near_pairs;
+    unsigned long long tau_fp64;
+    unsigned long long near_logged;
+    unsigned long long small_tau_pairs;
+    unsigned long long small_kick_pairs;
+    unsigned long long small_drifts;
+    unsigned long long small_kepler;
+    unsigned long long small_splits;
+    unsigned long long small_components;
+    unsigned int err;
+    int max_depth_seen;
+};
+
+struct TauParams {
+    double G, eps2, eta_in, eta, h, near_tol;
+    int eta_outside;
+};
+
+// --------------------------------------------------------------- helpers
+__device__ __forceinline__ unsigned smem_u32(const void *p)
+{
+    return static_cast<unsigned>(__cvta_generic_to_shared(p));
+}
+
+__device__ __forceinline__ void raise_err(DevCounters *c, unsigned code)
+{
+    atomicCAS(&c->err, 0u, code);
+}
+
+// mbarrier + TMA bulk copy (sm_90+ PTX, used unchanged on sm_103a)
+__device__ __forceinline__ void mbar_init(uint64_t *bar, unsigned count)
+{
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count) : "memory");
+}
+__device__ __forceinline__ void fence_mbar_init()
+{
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+}
+__device__ __forceinline__ void fence_proxy_async_smem()
+{
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+}
+__device__ __forceinline__ void mbar_expect_tx(uint64_t *bar, unsigned bytes)
+{
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)), "r"(bytes)
+                 : "memory");
+}
+// global -> shared bulk copy; dst, src 16-byte aligned, bytes % 16 == 0
+__device__ __forceinline__ void tma_load_1d(void *dst, const void *src, unsigned bytes, uint64_t *bar)
+{
+    asm volatile(
+        "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+            smem_u32(dst)),
+        "l"(src), "r"(bytes), "r"(smem_u32(bar))
+        : "memory");
+}
+// wait for the phase with the given parity; gives up after ~limit cycles
+__device__ __forceinline__ bool mbar_wait(uint64_t *bar, unsigned parity, long long limit_cycles)
+{
+    unsigned a = smem_u32(bar);
+    long long t0 = clock64();
+    while (true) {
+        unsigned done;
+        asm volatile(
+            "{\n\t.reg .pred p;\n\t"
+            "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+            "selp.u32 %0, 1, 0, p;\n\t}"
+            : "=r"(done) : "r"(a), "r"(parity) : "memory");
+        if (done) return true;
+        if (clock64() - t0 > limit_cycles) return false;
+    }
+}
+constexpr long long TMA_WAIT_CYCLES = 4000000000LL;  // ~2 s at 2 GHz
+
+// ------------------------------------------------- FP64 tau(i,j), exact
+// Eq. (tauij) with the free-fall / flyby reading stated in the design doc; the
+// operations and their order are fixed (no FMA: explicit _rn intrinsics)
+// so that the predicate tau < h is bit-identical to a plain IEEE-754
+// evaluation of:
+//   r2 = ((dx0*dx0 + dx1*dx1) + dx2*dx2) + eps2;  r = sqrt(r2)
+//   v2 = (dv0*dv0 + dv1*dv1) + dv2*dv2;  rv = (dx0*dv0 + dx1*dv1) + dx2*dv2
+//   mu = G*(mi + mj)
+//   Tff = eta_in*sqrt((r2*r)/mu);  dTff = ((1.5*Tff)*rv)/r2
+//   Tfb = eta_in*(r/sqrt(v2));  dTfb = (Tfb*(rv/r2))*(1 + mu/(r*v2))   [v2 > 0]
+//   tau_x = T_x/(1 - 0.5*min(dT_x, 1));  tau = min(tau_ff, tau_fb) [* eta]
+__device__ __forceinline__ double tau_fp64(double dx0, double dx1, double dx2, double dv0, double dv1,
+                                           double dv2, double mi, double mj, const TauParams &P)
+{
+    double r2 = __dadd_rn(__dadd_rn(__dadd_rn(__dmul_rn(dx0, dx0), __dmul_rn(dx1, dx1)), __dmul_rn(dx2, dx2)),
+                          P.eps2);
+    double r = __dsqrt_rn(r2);
+    double v2 = __dadd_rn(__dadd_rn(__dmul_rn(dv0, dv0), __dmul_rn(dv1, dv1)), __dmul_rn(dv2, dv2));
+    double rv = __dadd_rn(__dadd_rn(__dmul_rn(dx0, dv0), __dmul_rn(dx1, dv1)), __dmul_rn(dx2, dv2));
+    double mu = __dmul_rn(P.G, __dadd_rn(mi, mj));
+    double Tff = __dmul_rn(P.eta_in, __dsqrt_rn(__ddiv_rn(__dmul_rn(r2, r), mu)));
+    double dTff = __ddiv_rn(__dmul_rn(__dmul_rn(1.5, Tff), rv), r2);
+    double c1 = dTff < 1.0 ? dTff : 1.0;
+    double tff = __ddiv_rn(Tff, __dsub_rn(1.0, __dmul_rn(0.5, c1)));
+    double tfb = CUDART_INF;
+    if (v2 > 0.0) {
+        double Tfb = __dmul_rn(P.eta_in, __ddiv_rn(r, __dsqrt_rn(v2)));
+        double dTfb = __dmul_rn(__dmul_rn(Tfb, __ddiv_rn(rv, r2)), __dadd_rn(1.0, __ddiv_rn(mu, __dmul_rn(r, v2))));
+        double c2 = dTfb < 1.0 ? dTfb : 1.0;
+        tfb = __ddiv_rn(Tfb, __dsub_rn(1.0, __dmul_rn(0.5, c2)));
+    }
+    double t = tff < tfb ? tff : tfb;
+    if (P.eta_outside) t = __dmul_rn(P.eta, t);
+    return t;
+}
+
+// -------------------------------------------------------- union-find
+// Forest over packed indices; every link goes from a larger root to a
+// smaller one, so parent[x] <= x and a root is the smallest index of its
+// tree.  find() halves paths; the halving stores only ever point a node
+// to one of its own ancestors, so racing finds stay correct.
+__device__ __forceinline__ int uf_find(int32_t *parent, int x)
+{
+    volatile int32_t *par = parent;
+    int p = par[x];
+    if (p != x) {
+        int prev = x, nx;
+        while (p > (nx = par[p])) {
+            par[prev] = nx;
+            prev = p;
+            p = nx;
+        }
+    }
+    return p;
+}
+
+// Union of the trees of a and b: link the larger root under the smaller one
+// with compare-and-swap, retrying from the new parent on contention.
+__device__ __forceinline__ bool uf_union(int32_t *parent, int a, int b)
+{
+    int ra = uf_find(parent, a), rb = uf_find(parent, b);
+    for (int it = 0; it < (1 << 24); ++it) {
+        if (ra == rb) return true;
+        if (ra < rb) {
+            int old = atomicCAS(&parent[rb], rb, ra);
+            if (old == rb) return true;
+            rb = uf_find(parent, old);
+        } else {
+            int old = atomicCAS(&parent[ra], ra, rb);
+            if (old == ra) return true;
+            ra = uf_find(parent, old);
+        }
+    }
+    return false;
+}
+
+// ----------------------------------------------------------- launchers
+// Every launcher adds the number of kernels it launched to g_launches.
+extern unsigned long long g_launches;
+#define CC_COUNT_LAUNCH(k) (::cc::g_launches += (k))
+
+// cc_pair.cu
+void launch_init_parent(const Level &L, cudaStream_t s);
+void launch_tau_hook(const Level &L, int ntiles, const TauParams &P, int precision, DevCounters *ctr,
+                     int32_t *edges, long long edge_cap, int32_t *near_ij, double *near_tau, long long near_cap,
+                     cudaStream_t s);
+void launch_kick(const Level &L, const int32_t *label, int nitiles, double G, double eps2, double h,
+                 int precision, DevCounters *ctr, float *scratch, cudaStream_t s);
+void launch_energy(const double *x3, const double *v3, const double *m, long long n, double G, double eps2,
+                   double *partial /*[nblk*8]*/, int nblk, cudaStream_t s);
+int energy_blocks(long long n);
+
+// cc_graph.cu
+void launch_compress(const Level &L, int32_t *root, cudaStream_t s);
+void launch_drift(const Level &L, const int32_t *root, double dt, cudaStream_t s);
+void launch_drift_labels(const Level &L, const int32_t *singleton, double dt, cudaStream_t s);
+// stable segmentation of the components of a level; returns via device
+// arrays: comp_start/comp_size (ncomp on device at *d_ncomp) and the sorted
+// member list (packed indices).  scratch must hold seg_scratch_bytes(cap).
+size_t seg_scratch_bytes(int cap);
+void launch_segment(const Level &L, const int32_t *root, int32_t *members, int32_t *comp_start,
+                    int32_t *comp_size, int32_t *d_ncomp, void *scratch, cudaStream_t s);
+void launch_gather(const Level &P, const Level &C, const int32_t *members, const int32_t *lcomp_start,
+                   const int32_t *lpref, const int32_t *ldst, int nl, int nmem, int nsets_child, cudaStream_t s);
+void launch_scatter(const Level &P, const Level &C, cudaStream_t s);
+void launch_pack_state(const double *x3, const double *v3, const double *m, long long n, const Level &L,
+                       const int32_t *sys_src_start, cudaStream_t s);
+void launch_unpack_state(double *x3, double *v3, long long n, const Level &L, cudaStream_t s);
+void launch_gather_set(const double *x3, const double *v3, const double *m, long long n, const int32_t *set,
+                       int nset, const Level &L, unsigned *bad, cudaStream_t s);
+void launch_scatter_set(double *x3, double *v3, long long n, const Level &L, int nset, bool write_x,
+                        bool write_v, cudaStream_t s);
+void launch_label_canon(const Level &L, const int32_t *root, int32_t *labels_out, int nset, cudaStream_t s);
+void launch_singleton_from_labels(const int32_t *labels, int n, int32_t *singleton, void *scratch,
+                                  cudaStream_t s);
+void launch_sort_edges(int32_t *edges, long long ne, int bits, void *scratch, cudaStream_t s);
+size_t edge_sort_scratch_bytes(long long ne);
+void launch_check_state(const double *m, const double *x3, const double *v3, long long n, unsigned *bad,
+                        cudaStream_t s);
+size_t sort_scratch_bytes(long long n);
+
+double probe_fma(int fp64, int nsm, cudaStream_t s);
+
+// cc_kepler.cu
+void launch_kepler(const Level &L, const int32_t *members, const int32_t *comp_start, const int32_t *klist,
+                   int nk, double G, double dt, DevCounters *ctr, cudaStream_t s);
+
+}  // namespace cc

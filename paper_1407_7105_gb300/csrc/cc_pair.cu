@@ -1,0 +1,440 @@
+// cc_pair.cu -- pairwise kernels of the CC split (arXiv:1407.7105):
+//   * tau(i,j) over all pairs of each set fused with the edge test
+//     tau < h (Sec. 2.2) and union-find hooking of every edge;
+//   * the kick K_{h,V_ij} between members of different components
+//     (Eqs. kickij, kickji; Sec. 2.2 K_{h, V_R + V_CC + V_CR});
+//   * the energy diagnostic H (Eq. Hamiltonian).
+// j-tiles are staged in shared memory by TMA bulk copies (cp.async.bulk)
+// completing on an mbarrier; every wait is bounded.
+#include "cc_internal.cuh"
+
+namespace cc {
+
+// ------------------------------------------------------------ helpers
+__device__ __forceinline__ int find_set(const int32_t *off, int nsets, int b)
+{
+    int lo = 0, hi = nsets;  // off[lo] <= b < off[hi]
+    while (hi - lo > 1) {
+        int mid = (lo + hi) >> 1;
+        if (off[mid] <= b) lo = mid; else hi = mid;
+    }
+    return lo;
+}
+
+__global__ void k_init_parent(int32_t *parent, int32_t *cnt, int total)
+{
+    int k = blockIdx.x * blockDim.x + threadIdx.x;
+    if (k < total) {
+        parent[k] = k;
+        cnt[k] = 0;
+    }
+}
+
+void launch_init_parent(const Level &L, cudaStream_t s)
+{
+    if (L.total <= 0) return;
+    k_init_parent<<<(L.total + 255) / 256, 256, 0, s>>>(L.parent, L.cnt, L.total);
+    CC_COUNT_LAUNCH(1);
+}
+
+// ------------------------------------------------------------ tau + hook
+// One CTA per (set, i-tile, j-tile) with i-tile <= j-tile: TAU_T threads,
+// thread r owns particle i = i-tile*TAU_T + r and tests it against the
+// j-tile staged in shared memory (pairs i < j only).
+constexpr int TAU_T = 128;
+
+struct TauSmem {
+    double col[7][TAU_T + 4];  // x y z vx vy vz m of the j-tile
+    uint64_t bar;
+};
+
+__device__ __forceinline__ void log_pair(const TauParams &P, double tau, int gi, int gj, DevCounters *ctr,
+                                         int32_t *near_ij, double *near_tau, long long near_cap)
+{
+    if (fabs(tau - P.h) < P.near_tol * P.h) {
+        unsigned long long k = atomicAdd(&ctr->near_pairs, 1ull);
+        if ((long long)k < near_cap) {
+            near_ij[2 * k] = gi < gj ? gi : gj;
+            near_ij[2 * k + 1] = gi < gj ? gj : gi;
+            near_tau[k] = tau;
+        }
+    }
+}
+
+template <int PREC>
+__global__ void __launch_bounds__(TAU_T) k_tau_hook(Level L, TauParams P, DevCounters *ctr, int32_t *near_ij,
+                                                     double *near_tau, long long near_cap)
+{
+    __shared__ TauSmem sm;
+    const int tid = threadIdx.x;
+    const int s = find_set(L.tile_off, L.nsets, blockIdx.x);
+    int t = blockIdx.x - L.tile_off[s];
+    const int n = L.set_n[s], start = L.set_start[s];
+    const int nt = (n + TAU_T - 1) / TAU_T;
+    int ti = 0;
+    while (t >= nt - ti) {
+        t -= nt - ti;
+        ++ti;
+    }
+    const int tj = ti + t;
+    const int j0 = start + tj * TAU_T;
+    const int jn = min(TAU_T, n - tj * TAU_T);
+
+    if (tid == 0) {
+        mbar_init(&sm.bar, 1);
+        fence_mbar_init();
+    }
+    __syncthreads();
+    if (tid == 0) {
+        const unsigned bytes = (unsigned)((jn + 3) & ~3) * 8u;
+        mbar_expect_tx(&sm.bar, 7u * bytes);
+        const double *src[7] = {L.x, L.y, L.z, L.vx, L.vy, L.vz, L.m};
+#pragma unroll
+        for (int c = 0; c < 7; ++c) tma_load_1d(sm.col[c], src[c] + j0, bytes, &sm.bar);
+    }
+    const int il = ti * TAU_T + tid;
+    const bool iv = il < n;
+    const int i = start + il;
+    double xi = 0, yi = 0, zi = 0, vxi = 0, vyi = 0, vzi = 0, mi = 0;
+    int gi = -1;
+    if (iv) {
+        xi = L.x[i]; yi = L.y[i]; zi = L.z[i];
+        vxi = L.vx[i]; vyi = L.vy[i]; vzi = L.vz[i];
+        mi = L.m[i];
+        gi = L.gid[i];
+    }
+    if (!mbar_wait(&sm.bar, 0, TMA_WAIT_CYCLES)) {
+        raise_err(ctr, DERR_TMA_TIMEOUT);
+        mbar_wait(&sm.bar, 0, TMA_WAIT_CYCLES);
+        return;
+    }
+    unsigned long long my_edges = 0;
+    if (iv) {
+        const int kbeg = (ti == tj) ? tid + 1 : 0;
+        for (int k = kbeg; k < jn; ++k) {
+            const double dx0 = __dsub_rn(xi, sm.col[0][k]);
+            const double dx1 = __dsub_rn(yi, sm.col[1][k]);
+            const double dx2 = __dsub_rn(zi, sm.col[2][k]);
+            const double dv0 = __dsub_rn(vxi, sm.col[3][k]);
+            const double dv1 = __dsub_rn(vyi, sm.col[4][k]);
+            const double dv2 = __dsub_rn(vzi, sm.col[5][k]);
+            const double tau = tau_fp64(dx0, dx1, dx2, dv0, dv1, dv2, mi, sm.col[6][k], P);
+            const int j = j0 + k;
+            log_pair(P, tau, gi, L.gid[j], ctr, near_ij, near_tau, near_cap);
+            if (tau < P.h) {
+                ++my_edges;
+                if (!uf_union(L.parent, i, j)) raise_err(ctr, DERR_UF_RETRY);
+            }
+        }
+    }
+    // warp-aggregated edge count: one atomic per warp
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) my_edges += __shfl_down_sync(0xffffffffu, my_edges, o);
+    if ((tid & 31) == 0 && my_edges) atomicAdd(&ctr->edges, my_edges);
+}
+
+// Edge-list variant for the time-step-graph entry point: same predicate,
+// each edge written as (gid_i, gid_j), gid_i < gid_j, at an atomically
+// reserved slot (order fixed afterwards by a sort).
+__global__ void __launch_bounds__(TAU_T) k_tau_edges(Level L, TauParams P, DevCounters *ctr, int32_t *edges,
+                                                      long long edge_cap, int32_t *near_ij, double *near_tau,
+                                                      long long near_cap)
+{
+    __shared__ TauSmem sm;
+    const int tid = threadIdx.x;
+    const int s = find_set(L.tile_off, L.nsets, blockIdx.x);
+    int t = blockIdx.x - L.tile_off[s];
+    const int n = L.set_n[s], start = L.set_start[s];
+    const int nt = (n + TAU_T - 1) / TAU_T;
+    int ti = 0;
+    while (t >= nt - ti) {
+        t -= nt - ti;
+        ++ti;
+    }
+    const int tj = ti + t;
+    const int j0 = start + tj * TAU_T;
+    const int jn = min(TAU_T, n - tj * TAU_T);
+    if (tid == 0) {
+        mbar_init(&sm.bar, 1);
+        fence_mbar_init();
+    }
+    __syncthreads();
+    if (tid == 0) {
+        const unsigned bytes = (unsigned)((jn + 3) & ~3) * 8u;
+        mbar_expect_tx(&sm.bar, 7u * bytes);
+        const double *src[7] = {L.x, L.y, L.z, L.vx, L.vy, L.vz, L.m};
+#pragma unroll
+        for (int c = 0; c < 7; ++c) tma_load_1d(sm.col[c], src[c] + j0, bytes, &sm.bar);
+    }
+    const int il = ti * TAU_T + tid;
+    const bool iv = il < n;
+    const int i = start + il;
+    double xi = 0, yi = 0, zi = 0, vxi = 0, vyi = 0, vzi = 0, mi = 0;
+    int gi = -1;
+    if (iv) {
+        xi = L.x[i]; yi = L.y[i]; zi = L.z[i];
+        vxi = L.vx[i]; vyi = L.vy[i]; vzi = L.vz[i];
+        mi = L.m[i];
+        gi = L.gid[i];
+    }
+    if (!mbar_wait(&sm.bar, 0, TMA_WAIT_CYCLES)) {
+        raise_err(ctr, DERR_TMA_TIMEOUT);
+        mbar_wait(&sm.bar, 0, TMA_WAIT_CYCLES);
+        return;
+    }
+    if (!iv) return;
+    const int kbeg = (ti == tj) ? tid + 1 : 0;
+    for (int k = kbeg; k < jn; ++k) {
+        const double tau = tau_fp64(__dsub_rn(xi, sm.col[0][k]), __dsub_rn(yi, sm.col[1][k]),
+                                    __dsub_rn(zi, sm.col[2][k]), __dsub_rn(vxi, sm.col[3][k]),
+                                    __dsub_rn(vyi, sm.col[4][k]), __dsub_rn(vzi, sm.col[5][k]), mi,
+                                    sm.col[6][k], P);
+        const int j = j0 + k;
+        const int gj = L.gid[j];
+        log_pair(P, tau, gi, gj, ctr, near_ij, near_tau, near_cap);
+        if (tau < P.h) {
+            if (!uf_union(L.parent, i, j)) raise_err(ctr, DERR_UF_RETRY);
+            unsigned long long e = atomicAdd(&ctr->edges, 1ull);
+            if ((long long)e < edge_cap) {
+                edges[2 * e] = gi < gj ? gi : gj;
+                edges[2 * e + 1] = gi < gj ? gj : gi;
+            }
+        }
+    }
+}
+
+void launch_tau_hook(const Level &L, int ntiles, const TauParams &P, int precision, DevCounters *ctr,
+                     int32_t *edges, long long edge_cap, int32_t *near_ij, double *near_tau, long long near_cap,
+                     cudaStream_t s)
+{
+    if (ntiles <= 0) return;
+    if (edges) {
+        k_tau_edges<<<ntiles, TAU_T, 0, s>>>(L, P, ctr, edges, edge_cap, near_ij, near_tau, near_cap);
+        CC_COUNT_LAUNCH(1);
+        return;
+    }
+    (void)precision;
+    k_tau_hook<0><<<ntiles, TAU_T, 0, s>>>(L, P, ctr, near_ij, near_tau, near_cap);
+    CC_COUNT_LAUNCH(1);
+}
+
+// ------------------------------------------------------------ kick (FP64)
+// One CTA per (set, i-tile); thread r accumulates a_i over every j-tile of
+// its set in ascending order (pairs with equal labels skipped), so the sum
+// runs over j in ascending packed index = ascending particle id, the
+// order of the plain definition; then v_i += h a_i.  Two-stage TMA ring.
+constexpr int KICK_T = 64;
+
+struct KickSmem {
+    double col[2][4][KICK_T];  // x y z m per stage
+    int32_t lab[2][KICK_T];
+    uint64_t bar[2];
+};
+
+__device__ __forceinline__ void kick_issue(KickSmem &sm, int st, const Level &L, const int32_t *label, int j0,
+                                           int jn)
+{
+    const unsigned cnt = (unsigned)((jn + 3) & ~3);
+    fence_proxy_async_smem();
+    mbar_expect_tx(&sm.bar[st], cnt * (4u * 8u + 4u));
+    tma_load_1d(sm.col[st][0], L.x + j0, cnt * 8u, &sm.bar[st]);
+    tma_load_1d(sm.col[st][1], L.y + j0, cnt * 8u, &sm.bar[st]);
+    tma_load_1d(sm.col[st][2], L.z + j0, cnt * 8u, &sm.bar[st]);
+    tma_load_1d(sm.col[st][3], L.m + j0, cnt * 8u, &sm.bar[st]);
+    tma_load_1d(sm.lab[st], label + j0, cnt * 4u, &sm.bar[st]);
+}
+
+__global__ void __launch_bounds__(KICK_T) k_kick64(Level L, const int32_t *label, double G, double eps2,
+                                                    double h, DevCounters *ctr)
+{
+    __shared__ __align__(16) KickSmem sm;
+    const int tid = threadIdx.x;
+    const int s = find_set(L.itile_off, L.nsets, blockIdx.x);
+    const int ti = blockIdx.x - L.itile_off[s];
+    const int n = L.set_n[s], start = L.set_start[s];
+    const int nt = (n + KICK_T - 1) / KICK_T;
+    const int il = ti * KICK_T + tid;
+    const bool iv = il < n;
+    const int i = start + il;
+    if (tid == 0) {
+        mbar_init(&sm.bar[0], 1);
+        mbar_init(&sm.bar[1], 1);
+        fence_mbar_init();
+    }
+    __syncthreads();
+    if (tid == 0) kick_issue(sm, 0, L, label, start, min(KICK_T, n));
+    double xi = 0, yi = 0, zi = 0;
+    int li = 0;
+    if (iv) {
+        xi = L.x[i]; yi = L.y[i]; zi = L.z[i];
+        li = label[i];
+    }
+    double ax = 0.0, ay = 0.0, az = 0.0;
+    bool ok = true;
+    for (int tj = 0; tj < nt; ++tj) {
+        const int st = tj & 1;
+        if (tid == 0 && tj + 1 < nt)
+            kick_issue(sm, st ^ 1, L, label, start + (tj + 1) * KICK_T, min(KICK_T, n - (tj + 1) * KICK_T));
+        if (!mbar_wait(&sm.bar[st], (tj >> 1) & 1, TMA_WAIT_CYCLES)) {
+            ok = false;
+            break;
+        }
+        const int jn = min(KICK_T, n - tj * KICK_T);
+        const int j0l = tj * KICK_T;
+        if (iv) {
+            for (int k = 0; k < jn; ++k) {
+                if (j0l + k == il || sm.lab[st][k] == li) continue;
+                const double dx0 = __dsub_rn(sm.col[st][0][k], xi);
+                const double dx1 = __dsub_rn(sm.col[st][1][k], yi);
+                const double dx2 = __dsub_rn(sm.col[st][2][k], zi);
+                const double r2 = __dadd_rn(
+                    __dadd_rn(__dadd_rn(__dmul_rn(dx0, dx0), __dmul_rn(dx1, dx1)), __dmul_rn(dx2, dx2)), eps2);
+                const double rinv3 = __ddiv_rn(1.0, __dmul_rn(r2, __dsqrt_rn(r2)));
+                const double w = __dmul_rn(__dmul_rn(G, sm.col[st][3][k]), rinv3);
+                ax = __dadd_rn(ax, __dmul_rn(w, dx0));
+                ay = __dadd_rn(ay, __dmul_rn(w, dx1));
+                az = __dadd_rn(az, __dmul_rn(w, dx2));
+            }
+        }
+        __syncthreads();
+    }
+    if (!ok) {
+        raise_err(ctr, DERR_TMA_TIMEOUT);
+        // let any copy still in flight land before the CTA exits
+        mbar_wait(&sm.bar[0], 0, TMA_WAIT_CYCLES);
+        mbar_wait(&sm.bar[1], 0, TMA_WAIT_CYCLES);
+        return;
+    }
+    if (iv) {
+        L.vx[i] = __dadd_rn(L.vx[i], __dmul_rn(h, ax));
+        L.vy[i] = __dadd_rn(L.vy[i], __dmul_rn(h, ay));
+        L.vz[i] = __dadd_rn(L.vz[i], __dmul_rn(h, az));
+    }
+}
+
+void launch_kick(const Level &L, const int32_t *label, int nitiles, double G, double eps2, double h,
+                 int precision, DevCounters *ctr, float *scratch, cudaStream_t s)
+{
+    (void)precision;
+    (void)scratch;
+    if (nitiles <= 0) return;
+    k_kick64<<<nitiles, KICK_T, 0, s>>>(L, label, G, eps2, h, ctr);
+    CC_COUNT_LAUNCH(1);
+}
+
+// ------------------------------------------------------------ energy
+constexpr int EN_T = 128;
+
+int energy_blocks(long long n) { return (int)((n + EN_T - 1) / EN_T); }
+
+__global__ void __launch_bounds__(EN_T) k_energy(const double *x3, const double *v3, const double *m,
+                                                  long long n, double G, double eps2, double *partial)
+{
+    __shared__ double sx[EN_T], sy[EN_T], sz[EN_T], smm[EN_T];
+    __shared__ double red[8][EN_T / 32];
+    const long long i = (long long)blockIdx.x * EN_T + threadIdx.x;
+    const bool iv = i < n;
+    double xi = 0, yi = 0, zi = 0, mi = 0, vx = 0, vy = 0, vz = 0;
+    if (iv) {
+        xi = x3[i]; yi = x3[n + i]; zi = x3[2 * n + i];
+        vx = v3[i]; vy = v3[n + i]; vz = v3[2 * n + i];
+        mi = m[i];
+    }
+    double V = 0.0;
+    for (long long j0 = (long long)blockIdx.x * EN_T; j0 < n; j0 += EN_T) {
+        const long long j = j0 + threadIdx.x;
+        __syncthreads();
+        if (j < n) {
+            sx[threadIdx.x] = x3[j]; sy[threadIdx.x] = x3[n + j]; sz[threadIdx.x] = x3[2 * n + j];
+            smm[threadIdx.x] = m[j];
+        }
+        __syncthreads();
+        if (iv) {
+            const int jn = (int)min((long long)EN_T, n - j0);
+            for (int k = 0; k < jn; ++k) {
+                if (j0 + k <= i) continue;
+                const double dx = sx[k] - xi, dy = sy[k] - yi, dz = sz[k] - zi;
+                V -= G * mi * smm[k] / sqrt(dx * dx + dy * dy + dz * dz + eps2);
+            }
+        }
+    }
+    double q[8];
+    q[0] = iv ? 0.5 * mi * (vx * vx + vy * vy + vz * vz) : 0.0;
+    q[1] = V;
+    q[2] = mi * vx; q[3] = mi * vy; q[4] = mi * vz;
+    q[5] = mi * (yi * vz - zi * vy);
+    q[6] = mi * (zi * vx - xi * vz);
+    q[7] = mi * (xi * vy - yi * vx);
+#pragma unroll
+    for (int c = 0; c < 8; ++c) {
+        double val = q[c];
+        for (int o = 16; o > 0; o >>= 1) val += __shfl_down_sync(0xffffffffu, val, o);
+        if ((threadIdx.x & 31) == 0) red[c][threadIdx.x >> 5] = val;
+    }
+    __syncthreads();
+    if (threadIdx.x < 8) {
+        double acc = 0.0;
+        for (int w = 0; w < EN_T / 32; ++w) acc += red[threadIdx.x][w];
+        partial[blockIdx.x * 8 + threadIdx.x] = acc;
+    }
+}
+
+void launch_energy(const double *x3, const double *v3, const double *m, long long n, double G, double eps2,
+                   double *partial, int nblk, cudaStream_t s)
+{
+    if (n <= 0) return;
+    k_energy<<<nblk, EN_T, 0, s>>>(x3, v3, m, n, G, eps2, partial);
+    CC_COUNT_LAUNCH(1);
+}
+
+}  // namespace cc
+
+// ------------------------------------------------------------ peak probe
+// FMA throughput microbenchmarks (the ALU roofline denominators): every
+// thread advances 8 independent FMA chains; flops = 2 per FMA.
+namespace cc {
+
+template <typename T>
+__global__ void __launch_bounds__(256) k_probe_fma(T b, T c, int iters, T *out)
+{
+    T a0 = (T)threadIdx.x, a1 = a0 + (T)1, a2 = a0 + (T)2, a3 = a0 + (T)3;
+    T a4 = a0 + (T)4, a5 = a0 + (T)5, a6 = a0 + (T)6, a7 = a0 + (T)7;
+    for (int i = 0; i < iters; ++i) {
+        a0 = fma(a0, b, c); a1 = fma(a1, b, c); a2 = fma(a2, b, c); a3 = fma(a3, b, c);
+        a4 = fma(a4, b, c); a5 = fma(a5, b, c); a6 = fma(a6, b, c); a7 = fma(a7, b, c);
+    }
+    const T r = ((a0 + a1) + (a2 + a3)) + ((a4 + a5) + (a6 + a7));
+    if (r == (T)-12345.678) out[blockIdx.x] = r;  // keeps the chains live
+}
+
+double probe_fma(int fp64, int nsm, cudaStream_t s)
+{
+    const int blocks = nsm * 8, threads = 256;
+    const int iters = fp64 ? 512 : 16384;
+    void *out = nullptr;
+    cudaMalloc(&out, blocks * 8);
+    cudaEvent_t e0, e1;
+    cudaEventCreate(&e0);
+    cudaEventCreate(&e1);
+    float best = 1e30f;
+    for (int rep = 0; rep < 4; ++rep) {
+        cudaEventRecord(e0, s);
+        if (fp64)
+            k_probe_fma<double><<<blocks, threads, 0, s>>>(0.999999, 1e-7, iters, (double *)out);
+        else
+            k_probe_fma<float><<<blocks, threads, 0, s>>>(0.999999f, 1e-7f, iters, (float *)out);
+        CC_COUNT_LAUNCH(1);
+        cudaEventRecord(e1, s);
+        cudaEventSynchronize(e1);
+        float ms = 0.f;
+        cudaEventElapsedTime(&ms, e0, e1);
+        if (rep > 0 && ms < best) best = ms;
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    cudaFree(out);
+    const double flops = 2.0 * 8.0 * (double)iters * blocks * threads;
+    return flops / (best * 1e-3);
+}
+
+}  // namespace cc

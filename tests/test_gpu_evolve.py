@@ -1,0 +1,138 @@
+"""GPU parity of the kick, the drift and the recursive CC integrator
+(Sec. 2.2-2.3, CC pseudocode figure) against the FP64 oracle."""
+import numpy as np
+import pytest
+
+from oracle import oracle as O
+from paper_1407_7105_gb300 import ics
+
+pytestmark = pytest.mark.gpu
+
+
+def _rel_ok(a, b, rtol=1e-12):
+    scale = np.abs(b).max()
+    return np.all(np.abs(a - b) <= rtol * np.abs(b) + 1e-15 * scale)
+
+
+def test_kick_bit_exact(cclib, plummer_ic):
+    m, x, v = plummer_ic(300, seed=4)
+    rng = np.random.default_rng(0)
+    labels = rng.integers(0, 40, 300).astype(np.int32)
+    c = cclib.Context(m, x, v)
+    c.kick(labels, 1 / 64)
+    _, _, gx, gv = c.get_state()
+    s = O.State(m, x, v)
+    O.kick(s, O.params(), np.arange(300), labels, 1 / 64)
+    assert np.array_equal(gv, s.v3) and np.array_equal(gx, s.x3)
+    c.close()
+
+
+def test_drift_bit_exact_subset(cclib, plummer_ic):
+    m, x, v = plummer_ic(300, seed=4)
+    sub = np.arange(5, 300, 3, dtype=np.int32)
+    labels = (sub // 7).astype(np.int32)
+    c = cclib.Context(m, x, v)
+    c.drift(labels, 1 / 128, set_ids=sub)
+    _, _, gx, gv = c.get_state()
+    s = O.State(m, x, v)
+    O.drift(s, sub, labels, 1 / 128)
+    assert np.array_equal(gx, s.x3) and np.array_equal(gv, s.v3)
+    c.close()
+
+
+@pytest.mark.parametrize("n,dt", [(256, 1 / 64), (1000, 1 / 128)])
+def test_one_outer_step(cclib, plummer_ic, n, dt):
+    m, x, v = plummer_ic(n)
+    c = cclib.Context(m, x, v, dt=dt)
+    c.evolve(dt)
+    t, _, gx, gv = c.get_state()
+    s = O.State(m, x, v)
+    st = O.evolve(s, O.params(dt=dt), 1)
+    assert t == dt
+    assert _rel_ok(gx, s.x3) and _rel_ok(gv, s.v3)
+    g = c.stats()
+    for k in ("tau_pairs", "kick_pairs", "drifts", "splits", "components"):
+        assert g[k] == getattr(st, k), k
+    assert g["max_depth_seen"] == st.max_depth_seen
+    c.close()
+
+
+def test_eight_steps_and_conservation(cclib, plummer_ic):
+    m, x, v = plummer_ic(256)
+    c = cclib.Context(m, x, v, dt=1 / 64)
+    E0, P0, L0 = c.energy()
+    c.evolve(8 / 64)
+    _, _, gx, gv = c.get_state()
+    s = O.State(m, x, v)
+    O.evolve(s, O.params(dt=1 / 64), 8)
+    assert _rel_ok(gx, s.x3, 1e-10) and _rel_ok(gv, s.v3, 1e-10)
+    E1, P1, L1 = c.energy()
+    oE0, _, _ = O.energy(O.State(m, x, v))
+    assert abs(E0 - oE0) < 1e-14
+    assert np.abs(P1 - P0).max() < 1e-15 and np.abs(L1 - L0).max() < 1e-14
+    assert abs((E1 - E0) / E0) < 1e-5
+    c.close()
+
+
+def test_full_size_one_step(cclib, plummer_ic):
+    """The 16384-body Plummer sphere at dt = 1/256 (the benchmark workload):
+    one outer step against the oracle on every particle."""
+    m, x, v = plummer_ic(16384)
+    c = cclib.Context(m, x, v, dt=1 / 256)
+    c.evolve(1 / 256)
+    _, _, gx, gv = c.get_state()
+    s = O.State(m, x, v)
+    st = O.evolve(s, O.params(dt=1 / 256), 1)
+    assert _rel_ok(gx, s.x3) and _rel_ok(gv, s.v3)
+    g = c.stats()
+    assert g["tau_pairs"] == st.tau_pairs and g["kick_pairs"] == st.kick_pairs
+    c.close()
+
+
+def test_independent_systems(cclib):
+    parts = [ics.plummer(k, seed=10 + k) for k in (37, 64, 5)]
+    m = np.concatenate([p[0] for p in parts])
+    x = np.ascontiguousarray(np.concatenate([p[1] + 10.0 * i for i, p in enumerate(parts)], axis=1))
+    v = np.ascontiguousarray(np.concatenate([p[2] for p in parts], axis=1))
+    off = np.array([0, 37, 101, 106], dtype=np.int64)
+    c = cclib.Context(m, x, v, dt=1 / 32)
+    c.set_systems(off)
+    c.evolve(2 / 32)
+    _, _, gx, gv = c.get_state()
+    s = O.State(m, x, v)
+    O.evolve(s, O.params(dt=1 / 32), 2, sys_off=off)
+    assert _rel_ok(gx, s.x3) and _rel_ok(gv, s.v3)
+    c.close()
+
+
+def test_kepler_mode_binaries(cclib):
+    m, x, v = ics.plummer_with_binaries(512, seed=3)
+    c = cclib.Context(m, x, v, dt=1 / 256, kepler=1)
+    c.evolve(1 / 256)
+    _, _, gx, gv = c.get_state()
+    s = O.State(m, x, v)
+    st = O.evolve(s, O.params(dt=1 / 256, kepler=True), 1)
+    assert c.stats()["kepler_calls"] == st.kepler_calls > 0
+    assert _rel_ok(gx, s.x3, 1e-9)
+    # velocities of hard binaries are large: compare relative to each one
+    assert np.all(np.abs(gv - s.v3) <= 1e-8 * np.abs(s.v3) + 1e-12)
+    c.close()
+
+
+def test_errors_are_reported(cclib, plummer_ic):
+    m, x, v = plummer_ic(256)
+    c = cclib.Context(m, x, v, dt=1 / 64)
+    with pytest.raises(cclib.CCError) as e:
+        c.evolve(0.01)
+    assert e.value.code == -1
+    c.close()
+    c = cclib.Context(m, x, v, dt=1 / 64, max_depth=1)
+    with pytest.raises(cclib.CCError) as e:
+        c.evolve(1 / 64)
+    assert e.value.code == -3
+    c.close()
+    bad = x.copy()
+    bad[0, 0] = np.nan
+    with pytest.raises(cclib.CCError) as e:
+        cclib.Context(m, bad, v)
+    assert e.value.code == -5
