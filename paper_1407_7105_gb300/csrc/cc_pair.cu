@@ -43,7 +43,7 @@ void launch_init_parent(const Level &L, cudaStream_t s)
 // j-tile staged in shared memory (pairs i < j only).
 constexpr int TAU_T = 128;
 
-struct TauSmem {
+struct __align__(16) TauSmem {
     double col[7][TAU_T + 4];  // x y z vx vy vz m of the j-tile
     uint64_t bar;
 };
@@ -225,7 +225,7 @@ void launch_tau_hook(const Level &L, int ntiles, const TauParams &P, int precisi
 // order of the plain definition; then v_i += h a_i.  Two-stage TMA ring.
 constexpr int KICK_T = 64;
 
-struct KickSmem {
+struct __align__(16) KickSmem {
     double col[2][4][KICK_T];  // x y z m per stage
     int32_t lab[2][KICK_T];
     uint64_t bar[2];
@@ -275,7 +275,8 @@ __global__ void __launch_bounds__(KICK_T) k_kick64(Level L, const int32_t *label
         const int st = tj & 1;
         if (tid == 0 && tj + 1 < nt)
             kick_issue(sm, st ^ 1, L, label, start + (tj + 1) * KICK_T, min(KICK_T, n - (tj + 1) * KICK_T));
-        if (!mbar_wait(&sm.bar[st], (tj >> 1) & 1, TMA_WAIT_CYCLES)) {
+        const bool got = mbar_wait(&sm.bar[st], (tj >> 1) & 1, TMA_WAIT_CYCLES);
+        if (__syncthreads_or(!got)) {  // uniform exit: no thread is left at a barrier
             ok = false;
             break;
         }
