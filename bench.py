@@ -39,8 +39,8 @@ TAU_FLOPS = 47   # Eq. tauij as evaluated: 3 sqrt, 6 div, 38 add/sub/mul
 KICK_FLOPS = 28  # one pair force applied to both bodies (Eqs. kickij/kickji)
 
 
-def workload_name():
-    return (f"Plummer N={N_BODY}, equal masses, N-body units, eps=0, eta={ETA}, outer step dt=1/256 "
+def workload_name(n=N_BODY):
+    return (f"Plummer N={n}, equal masses, N-body units, eps=0, eta={ETA}, outer step dt=1/256 "
             f"(one evolve_cc step per bench step)")
 
 
@@ -168,7 +168,8 @@ def run_gpu(args, rank, world):
     dev = torch.device("cuda", local)
     build.build()
     seed = args.seed + rank
-    m, x, v = ics.plummer(N_BODY, seed=seed)
+    N = args.n
+    m, x, v = ics.plummer(N, seed=seed)
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
@@ -199,6 +200,7 @@ def run_gpu(args, rank, world):
         dist.barrier()
     torch.cuda.synchronize()
     sampler.start()
+    torch.cuda.nvtx.range_push("timed_region")
     total_ms = 0.0
     for _ in range(args.steps):
         l2_flush.fill_(1)
@@ -212,6 +214,7 @@ def run_gpu(args, rank, world):
         e1.synchronize()
         total_ms += e0.elapsed_time(e1)
     torch.cuda.synchronize()
+    torch.cuda.nvtx.range_pop()
     clocks = sampler.stop()
     st1 = ctx.stats()
     tm = ctx.timing()
@@ -221,9 +224,9 @@ def run_gpu(args, rank, world):
     E1, _, _ = ctx.energy()
 
     # end to end through the C ABI with host buffers (pinned)
-    hm = torch.empty(N_BODY, dtype=torch.float64).pin_memory()
-    hx = torch.empty(3, N_BODY, dtype=torch.float64).pin_memory()
-    hv = torch.empty(3, N_BODY, dtype=torch.float64).pin_memory()
+    hm = torch.empty(N, dtype=torch.float64).pin_memory()
+    hx = torch.empty(3, N, dtype=torch.float64).pin_memory()
+    hv = torch.empty(3, N, dtype=torch.float64).pin_memory()
     ctx.get_state(hm, hx, hv)
     e2e_steps = max(1, min(args.steps, 3))
     st2 = ctx.stats()
@@ -269,10 +272,10 @@ def run_gpu(args, rank, world):
             "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": total_ms / args.steps, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-            "config": {"workload": workload_name(), "form": args.form, "l2": "flushed (256 MB write) before each step",
+            "config": {"workload": workload_name(N), "form": args.form, "l2": "flushed (256 MB write) before each step",
                        "parallelism": "replicas" if world > 1 else "single GPU"},
-            "e2e": {"value": e2e_inter / e2e_sec, "unit": UNIT, "h2d_bytes_per_step": 7 * N_BODY * 8,
-                    "d2h_bytes_per_step": 6 * N_BODY * 8, "steps": e2e_steps},
+            "e2e": {"value": e2e_inter / e2e_sec, "unit": UNIT, "h2d_bytes_per_step": 7 * N * 8,
+                    "d2h_bytes_per_step": 6 * N * 8, "steps": e2e_steps},
             "gpu_launches": launches,
             "roofline": roof,
             "cpu_baseline": cpu,
@@ -293,6 +296,7 @@ def main():
     ap.add_argument("--impl", default="cc", choices=["cc", "reference"])
     ap.add_argument("--form", default="fp64", choices=["fp64", "mixed"])
     ap.add_argument("--seed", type=int, default=1)
+    ap.add_argument("--n", type=int, default=N_BODY, help="bodies (smaller cases are for profiling only)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     args = ap.parse_args()
     world = int(os.environ.get("WORLD_SIZE", "1"))
