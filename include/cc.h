@@ -173,6 +173,32 @@ int cc_timing(cc_ctx *ctx, cc_timing_t *out);
  * CC_E_CUDA. */
 int cc_probe_peaks(void *stream, double *fp64_flops, double *fp32_flops);
 
+/* Component labels of a caller-held state without any device allocation.
+ * No counterpart in the paper: it is cc_components over all n particles
+ * for callers that cannot let this library call cudaMalloc -- their device
+ * memory belongs to another allocator (a framework pool that has reserved
+ * the GPU, or a fixed budget) or their loop cannot take the device-wide
+ * synchronisation cudaMalloc/cudaFree imply.  Scratch lives in a fixed
+ * file-scope device array of CC_NOALLOC_MAX_N entries (512 KiB held on
+ * every GPU that loads libcc.so, until exit), so n <= CC_NOALLOC_MAX_N.
+ *   m[n], x3[3n], v3[3n]: device-accessible state, SoA as above (read only)
+ *   p: G, eps, eta, eta_outside are used; h: threshold of tau(i,j) < h
+ *   labels_out[n] (device-accessible int32): smallest particle index of
+ *     each particle's component, identical to cc_components on all n
+ *   n_comp_out (device-accessible int64): number of components >= 2
+ * The first call on a device looks up the array's device address with
+ * that device current; make that first call before any stream capture.
+ * Calls share the one array per device: calls whose work overlaps on the
+ * GPU race and give wrong labels, so serialise them (one stream, or
+ * synchronise between calls).  The call synchronises `stream` before it
+ * returns.  Errors: CC_E_ARG (NULL pointer, n < 1, h not > 0),
+ * CC_E_CAPACITY (n > CC_NOALLOC_MAX_N), CC_E_CUDA (a CUDA call failed),
+ * CC_E_TIMEOUT (union-find retry limit reached). */
+#define CC_NOALLOC_MAX_N 65536
+int cc_components_noalloc(const double *m, const double *x3, const double *v3,
+                          int64_t n, const cc_params *p, double h,
+                          int32_t *labels_out, int64_t *n_comp_out, void *stream);
+
 /* Release the context and all its device memory. */
 int cc_destroy(cc_ctx *ctx);
 

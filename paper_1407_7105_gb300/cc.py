@@ -59,7 +59,7 @@ _lib = None
 EXPORTS = ["cc_default_params", "cc_init", "cc_set_systems", "cc_set_stream", "cc_timestep_graph",
            "cc_components", "cc_kick", "cc_drift", "cc_evolve", "cc_get_state", "cc_set_state", "cc_stats",
            "cc_reset_stats", "cc_energy", "cc_near_pairs", "cc_set_timing", "cc_timing", "cc_probe_peaks",
-           "cc_destroy", "cc_last_error"]
+           "cc_components_noalloc", "cc_destroy", "cc_last_error"]
 
 
 def lib():
@@ -89,6 +89,7 @@ def lib():
         L.cc_set_timing.argtypes = [vp, C.c_int]
         L.cc_timing.argtypes = [vp, C.POINTER(Timing)]
         L.cc_probe_peaks.argtypes = [vp, C.POINTER(C.c_double), C.POINTER(C.c_double)]
+        L.cc_components_noalloc.argtypes = [dp, dp, dp, i64, C.POINTER(Params), C.c_double, i32p, vp, vp]
         L.cc_destroy.argtypes = [vp]
         L.cc_last_error.argtypes = [vp]
         L.cc_last_error.restype = C.c_char_p
@@ -141,6 +142,18 @@ def probe_peaks(stream=None):
     if rc:
         raise CCError(rc, lib().cc_last_error(None).decode())
     return float(f64.value), float(f32.value)
+
+
+def components_noalloc(m, x3, v3, h: float, labels_out, n_comp_out, params: Params | None = None, stream=None):
+    """cc_components_noalloc: labels of all particles of a device-resident
+    state into caller-provided device buffers (labels_out int32[n],
+    n_comp_out int64[1]); the library allocates nothing."""
+    p = params if params is not None else default_params()
+    rc = lib().cc_components_noalloc(_ptr(m), _ptr(x3), _ptr(v3), int(m.shape[0]), C.byref(p), float(h),
+                                     _ptr(labels_out), _ptr(n_comp_out),
+                                     stream if stream is not None else _stream())
+    if rc:
+        raise CCError(rc, "cc_components_noalloc")
 
 
 class Context:
