@@ -181,47 +181,65 @@ def run_gpu(args, rank, world):
                          "drift-kick-drift, single thread, same initial state"}
 
     stream = torch.cuda.current_stream(dev)
-    prec = cc.PREC_MIXED if args.form == "mixed" else cc.PREC_FP64
-    dm, dx, dv = (torch.tensor(a, device=dev) for a in (m, x, v))
-    ctx = cc.Context(dm, dx, dv, dt=DT, eta=ETA, precision=prec)
-    E0, _, _ = ctx.energy()
     f64_peak, f32_peak = cc.probe_peaks()
     l2_flush = torch.empty(64 * 1024 * 1024, dtype=torch.int32, device=dev)  # 256 MB > L2
+    dm, dx, dv = (torch.tensor(a, device=dev) for a in (m, x, v))
 
-    t = 0.0
-    for _ in range(args.warmup):
-        t += DT
-        ctx.evolve(t)
-    torch.cuda.synchronize()
-    st0 = ctx.stats()
-    ctx.set_timing(True)
-    sampler = ClockSampler(local)
-    if dist.is_initialized():
-        dist.barrier()
-    torch.cuda.synchronize()
-    sampler.start()
-    torch.cuda.nvtx.range_push("timed_region")
-    total_ms = 0.0
-    for _ in range(args.steps):
-        l2_flush.fill_(1)
+    def make_ctx(form):
+        prec = cc.PREC_MIXED if form == "mixed" else cc.PREC_FP64
+        return cc.Context(dm, dx, dv, dt=DT, eta=ETA, precision=prec, h_fp64=args.h_fp64 * DT)
+
+    def time_form(form, steps, warmup, clocks_too):
+        ctx = make_ctx(form)
+        E0, _, _ = ctx.energy()
+        t = 0.0
+        for _ in range(warmup):
+            t += DT
+            ctx.evolve(t)
         torch.cuda.synchronize()
-        e0 = torch.cuda.Event(enable_timing=True)
-        e1 = torch.cuda.Event(enable_timing=True)
-        e0.record(stream)
-        t += DT
-        ctx.evolve(t)
-        e1.record(stream)
-        e1.synchronize()
-        total_ms += e0.elapsed_time(e1)
-    torch.cuda.synchronize()
-    torch.cuda.nvtx.range_pop()
-    clocks = sampler.stop()
-    st1 = ctx.stats()
-    tm = ctx.timing()
-    ctx.set_timing(False)
-    inter = (st1["tau_pairs"] - st0["tau_pairs"]) + (st1["kick_pairs"] - st0["kick_pairs"])
-    launches = st1["launches"] - st0["launches"]
-    E1, _, _ = ctx.energy()
+        st0 = ctx.stats()
+        ctx.set_timing(True)
+        sampler = ClockSampler(local) if clocks_too else None
+        if dist.is_initialized():
+            dist.barrier()
+        torch.cuda.synchronize()
+        if sampler:
+            sampler.start()
+        torch.cuda.nvtx.range_push("timed_region")
+        total_ms = 0.0
+        for _ in range(steps):
+            l2_flush.fill_(1)
+            torch.cuda.synchronize()
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            t += DT
+            ctx.evolve(t)
+            e1.record(stream)
+            e1.synchronize()
+            total_ms += e0.elapsed_time(e1)
+        torch.cuda.synchronize()
+        torch.cuda.nvtx.range_pop()
+        clocks = sampler.stop() if sampler else None
+        st1 = ctx.stats()
+        tm = ctx.timing()
+        ctx.set_timing(False)
+        E1, _, _ = ctx.energy()
+        res = {"ctx": ctx, "t": t, "total_ms": total_ms, "clocks": clocks, "timing": tm,
+               "inter": (st1["tau_pairs"] - st0["tau_pairs"]) + (st1["kick_pairs"] - st0["kick_pairs"]),
+               "launches": st1["launches"] - st0["launches"],
+               "tau_fp64": st1["tau_fp64"] - st0["tau_fp64"], "tau_pairs": st1["tau_pairs"] - st0["tau_pairs"],
+               "dE": (E1 - E0) / abs(E0)}
+        return res
+
+    head = time_form(args.form, args.steps, args.warmup, True)
+    other_form = "fp64" if args.form == "mixed" else "mixed"
+    other = None if args.single_form else time_form(other_form, max(1, min(args.steps, 3)), 1, False)
+    if other:
+        other["ctx"].close()
+    ctx, t = head["ctx"], head["t"]
+    total_ms, clocks, tm, inter, launches = (head["total_ms"], head["clocks"], head["timing"], head["inter"],
+                                             head["launches"])
 
     # end to end through the C ABI with host buffers (pinned)
     hm = torch.empty(N, dtype=torch.float64).pin_memory()
@@ -254,25 +272,37 @@ def run_gpu(args, rank, world):
     value = inter / sec
 
     # roofline of the dominant pairwise kernel (measured live above)
+    fp32 = args.form == "mixed"
     if tm["tau_ms"] >= tm["kick_ms"]:
-        kname, kms, kl, flops = "tau_hook", tm["tau_ms"], tm["tau_launches"], TAU_FLOPS * tm["tau_pairs"]
+        kname, kms, kl, flops = "tau", tm["tau_ms"], tm["tau_launches"], TAU_FLOPS * tm["tau_pairs"]
     else:
         kname, kms, kl, flops = "kick", tm["kick_ms"], tm["kick_launches"], KICK_FLOPS * tm["kick_pairs"]
+    kname = ("k_tau_mixed" if kname == "tau" else "k_kick_mixed") if fp32 else \
+            ("k_tau_hook" if kname == "tau" else "k_kick64")
     achieved = flops / (kms * 1e-3) / 1e12 if kms > 0 else None
-    peak = f64_peak / 1e12
+    peak = (f32_peak if fp32 else f64_peak) / 1e12
     roof = {"bound": "alu", "kernel": kname, "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
             "frac": (achieved / peak) if achieved else None, "traffic": None,
-            "peak_source": "FP64 FMA throughput measured by cc_probe_peaks on this GPU",
+            "peak_source": ("FP32" if fp32 else "FP64") + " FMA throughput measured by cc_probe_peaks on this GPU",
+            "algorithmic_flops_per_pair": TAU_FLOPS if kname.startswith("k_tau") else KICK_FLOPS,
             "kernel_ms_per_step": kms / args.steps, "launches_per_step": kl / args.steps,
             "tau_ms_per_step": tm["tau_ms"] / args.steps, "kick_ms_per_step": tm["kick_ms"] / args.steps,
-            "fp32_peak_tflops": f32_peak / 1e12}
-
+            "small_kernel_ms_per_step": tm["small_ms"] / args.steps,
+            "fp64_peak_tflops": f64_peak / 1e12, "fp32_peak_tflops": f32_peak / 1e12}
+    other_line = None
+    if other:
+        other_line = {"form": other_form, "value": other["inter"] / (other["total_ms"] * 1e-3),
+                      "ms_per_step": other["total_ms"] / max(1, min(args.steps, 3)), "dE_over_E": other["dE"],
+                      "tau_ms_per_step": other["timing"]["tau_ms"] / max(1, min(args.steps, 3)),
+                      "kick_ms_per_step": other["timing"]["kick_ms"] / max(1, min(args.steps, 3)),
+                      "small_kernel_ms_per_step": other["timing"]["small_ms"] / max(1, min(args.steps, 3))}
     if rank == 0:
         line = {
             "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": total_ms / args.steps, "higher_is_better": True,
-            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-            "config": {"workload": workload_name(N), "form": args.form, "l2": "flushed (256 MB write) before each step",
+            "scaling": "weak", "vs_baseline": None, "dtype": "f32/f64" if fp32 else "f64", "data": "synthetic",
+            "config": {"workload": workload_name(N), "form": args.form, "h_fp64": f"{args.h_fp64}*dt",
+                       "l2": "flushed (256 MB write) before each step",
                        "parallelism": "replicas" if world > 1 else "single GPU"},
             "e2e": {"value": e2e_inter / e2e_sec, "unit": UNIT, "h2d_bytes_per_step": 7 * N * 8,
                     "d2h_bytes_per_step": 6 * N * 8, "steps": e2e_steps},
@@ -280,8 +310,10 @@ def run_gpu(args, rank, world):
             "roofline": roof,
             "cpu_baseline": cpu,
             "clocks": clocks,
-            "dE_over_E": (E1 - E0) / abs(E0),
+            "dE_over_E": head["dE"],
+            "tau_fp64_fraction": head["tau_fp64"] / max(1, head["tau_pairs"]),
             "interactions_per_step": inter / args.steps / world,
+            "other_form": other_line,
         }
         print(json.dumps(line), flush=True)
     ctx.close()
@@ -294,7 +326,10 @@ def main():
     ap.add_argument("--steps", type=int, default=5)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="cc", choices=["cc", "reference"])
-    ap.add_argument("--form", default="fp64", choices=["fp64", "mixed"])
+    ap.add_argument("--form", default="mixed", choices=["fp64", "mixed"])
+    ap.add_argument("--h-fp64", type=float, default=0.0,
+                    help="mixed form: sets split at h < h_fp64*dt take FP64 forces")
+    ap.add_argument("--single-form", action="store_true", help="skip timing the other form")
     ap.add_argument("--seed", type=int, default=1)
     ap.add_argument("--n", type=int, default=N_BODY, help="bodies (smaller cases are for profiling only)")
     ap.add_argument("--no-cpu-baseline", action="store_true")

@@ -75,12 +75,14 @@ typedef struct {
 } cc_stats_t;
 
 /* Device time of the pairwise kernels, measured with CUDA events on the
- * context's stream while timing is on (cc_set_timing).  pairs = unordered
- * pairs those launches covered (tau: n(n-1)/2 per set; kick: cross-
- * component pairs). */
+ * context's stream while timing is on (cc_set_timing): the tau kernels of
+ * the level splits, the kick kernels of the level DKDs, and the
+ * small-component kernel (which runs whole sub-recursions).  pairs =
+ * unordered pairs the tau and kick launches covered (tau: n(n-1)/2 per
+ * set; kick: cross-component pairs). */
 typedef struct {
-    double   tau_ms, kick_ms;
-    int64_t  tau_launches, kick_launches;
+    double   tau_ms, kick_ms, small_ms;
+    int64_t  tau_launches, kick_launches, small_launches;
     uint64_t tau_pairs, kick_pairs;
 } cc_timing_t;
 

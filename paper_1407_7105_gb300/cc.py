@@ -41,8 +41,9 @@ class Stats(C.Structure):
 
 
 class Timing(C.Structure):
-    _fields_ = [("tau_ms", C.c_double), ("kick_ms", C.c_double), ("tau_launches", C.c_int64),
-                ("kick_launches", C.c_int64), ("tau_pairs", C.c_uint64), ("kick_pairs", C.c_uint64)]
+    _fields_ = [("tau_ms", C.c_double), ("kick_ms", C.c_double), ("small_ms", C.c_double),
+                ("tau_launches", C.c_int64), ("kick_launches", C.c_int64), ("small_launches", C.c_int64),
+                ("tau_pairs", C.c_uint64), ("kick_pairs", C.c_uint64)]
 
     def as_dict(self):
         return {k: getattr(self, k) for k, _ in self._fields_}

@@ -37,6 +37,9 @@ thread_local std::string g_init_err;
 
 struct LevelAlloc {
     Level L{};
+    FFView F{};
+    long long kblocks = 0;   // mixed-kick blocks of the current layout
+    int kchunks_max = 0;     // largest j-chunk count of a set
     int cap = 0;      // element capacity (excluding PAD_TAIL)
     int set_cap = 0;  // set-array capacity
     void *block = nullptr;
@@ -49,6 +52,9 @@ struct LevelAlloc {
     int list_cap = 0;
     std::vector<int32_t> h_size, h_start;
     std::vector<int32_t> h_set_n;  // set sizes of this level (host copy)
+    int32_t *h_info = nullptr;     // pinned: ncomp, sizes, starts (one D2H per split)
+    int info_cap = 0;
+    cudaEvent_t ev_ready = nullptr, ev_small = nullptr;  // side-stream joins
 };
 
 }  // namespace
@@ -74,6 +80,11 @@ struct cc_ctx {
     void *tmp = nullptr;  // staging for caller buffers
     size_t tmp_sz = 0;
     unsigned *d_bad = nullptr;
+    int *d_queue = nullptr;     // work queue of the small-component kernel
+    cudaStream_t side = nullptr;  // small-component kernels overlap the level recursion
+    int nsm = 152;
+    double *d_kpart = nullptr;  // mixed-kick chunk partials
+    size_t kpart_sz = 0;
     cc_stats_t st{};
     std::string err;
     double eta_run = 0.03;
@@ -87,8 +98,9 @@ struct cc_ctx {
 };
 
 // record the start of a timed launch; returns the pair index or -1
-static int ev_begin(cc_ctx *c, int kind)
+static int ev_begin(cc_ctx *c, int kind, cudaStream_t st = nullptr)
 {
+    if (!st) st = c->stream;
     if (!c->timing) return -1;
     if (c->ev_used + 2 > c->evs.size()) {
         for (int k = 0; k < 64; ++k) {
@@ -100,14 +112,14 @@ static int ev_begin(cc_ctx *c, int kind)
     }
     const int pair = (int)(c->ev_used / 2);
     c->ev_kind[pair] = kind;
-    cudaEventRecord(c->evs[c->ev_used], c->stream);
+    cudaEventRecord(c->evs[c->ev_used], st);
     c->ev_used += 2;
     return pair;
 }
 
-static void ev_end(cc_ctx *c, int pair)
+static void ev_end(cc_ctx *c, int pair, cudaStream_t st = nullptr)
 {
-    if (pair >= 0) cudaEventRecord(c->evs[2 * pair + 1], c->stream);
+    if (pair >= 0) cudaEventRecord(c->evs[2 * pair + 1], st ? st : c->stream);
 }
 
 // fold the recorded event pairs into the totals (stream must be idle)
@@ -119,9 +131,12 @@ static void ev_resolve(cc_ctx *c)
         if (c->ev_kind[q] == 0) {
             c->tm.tau_ms += ms;
             c->tm.tau_launches++;
-        } else {
+        } else if (c->ev_kind[q] == 1) {
             c->tm.kick_ms += ms;
             c->tm.kick_launches++;
+        } else {
+            c->tm.small_ms += ms;
+            c->tm.small_launches++;
         }
     }
     c->ev_used = 0;
@@ -183,6 +198,12 @@ static int align_up(int v, int a) { return (v + a - 1) / a * a; }
 
 static void free_level(LevelAlloc &a)
 {
+    if (a.h_info) cudaFreeHost(a.h_info);
+    if (a.ev_ready) cudaEventDestroy(a.ev_ready);
+    if (a.ev_small) cudaEventDestroy(a.ev_small);
+    a.h_info = nullptr;
+    a.info_cap = 0;
+    a.ev_ready = a.ev_small = nullptr;
     if (a.block) cudaFree(a.block);
     if (a.setblock) cudaFree(a.setblock);
     if (a.listblock) cudaFree(a.listblock);
@@ -196,9 +217,12 @@ static int ensure_level(cc_ctx *c, LevelAlloc &a, int need, int nsets)
     if (need > a.cap) {
         if (a.block) cudaFree(a.block);
         a.block = nullptr;
-        int cap = align_up(std::max(need, 64), 64);
+        // sized once for the worst batch (every set padded): no reallocation,
+        // and no cudaFree stall, once a level has been reached
+        const long long worst = std::min<long long>(2 * (long long)c->n + 64, 0x3fffffff);
+        int cap = align_up(std::max<int>(need, (int)std::max<long long>(64, worst)), 64);
         size_t nd = (size_t)cap + PAD_TAIL;
-        size_t bytes = nd * 8 * 7 + nd * 4 * 10 + 4096;
+        size_t bytes = nd * 8 * 7 + nd * 4 * 10 + nd * 4 * 13 + 4096;
         if (cudaMalloc(&a.block, bytes) != cudaSuccess) {
             cudaGetLastError();
             return fail(c, CC_E_NOMEM, "device allocation failed (level buffer)");
@@ -210,6 +234,11 @@ static int ensure_level(cc_ctx *c, LevelAlloc &a, int need, int nsets)
         int32_t **ip[10] = {&a.L.gid, &a.L.sidx, &a.L.src, &a.L.parent, &a.L.cnt,
                             &a.root, &a.members, &a.comp_start, &a.comp_size, &a.d_ncomp};
         for (int k = 0; k < 10; ++k) { *ip[k] = (int32_t *)q; q += nd * 4; }
+        float **fp[13] = {&a.F.ph[0], &a.F.ph[1], &a.F.ph[2], &a.F.pl[0], &a.F.pl[1], &a.F.pl[2],
+                          &a.F.vh[0], &a.F.vh[1], &a.F.vh[2], &a.F.vl[0], &a.F.vl[1], &a.F.vl[2], &a.F.m};
+        for (int k = 0; k < 13; ++k) { *fp[k] = (float *)q; q += nd * 4; }
+        a.F.maxes = (float *)q;
+        a.F.cap = (int)nd;
         a.cap = cap;
         // lists: at most cap/2 components
         if (a.listblock) cudaFree(a.listblock);
@@ -230,7 +259,7 @@ static int ensure_level(cc_ctx *c, LevelAlloc &a, int need, int nsets)
         if (a.setblock) cudaFree(a.setblock);
         a.setblock = nullptr;
         int sc = align_up(nsets + 2, 256);
-        if (cudaMalloc(&a.setblock, (size_t)sc * 4 * 4) != cudaSuccess) {
+        if (cudaMalloc(&a.setblock, (size_t)sc * 4 * 5) != cudaSuccess) {
             cudaGetLastError();
             return fail(c, CC_E_NOMEM, "device allocation failed (set arrays)");
         }
@@ -238,7 +267,8 @@ static int ensure_level(cc_ctx *c, LevelAlloc &a, int need, int nsets)
         a.L.set_start = sq; sq += sc;
         a.L.set_n = sq; sq += sc;
         a.L.tile_off = sq; sq += sc;
-        a.L.itile_off = sq;
+        a.L.itile_off = sq; sq += sc;
+        a.L.koff = sq;
         a.set_cap = sc;
     }
     // the segmentation scratch is shared by all levels: size for the largest
@@ -258,9 +288,10 @@ static int ensure_level(cc_ctx *c, LevelAlloc &a, int need, int nsets)
 // upload the set layout (sizes -> aligned starts, tile prefixes); returns
 // the packed total through L.total
 struct SetLayout {
-    std::vector<int32_t> start, n, toff, ioff;
+    std::vector<int32_t> start, n, toff, ioff, koff;
     int total = 0;
-    long long tiles = 0, itiles = 0;
+    long long tiles = 0, itiles = 0, kblocks = 0;
+    int kchunks_max = 0;
 };
 
 static void make_layout(const std::vector<int32_t> &sizes, SetLayout &S)
@@ -270,22 +301,28 @@ static void make_layout(const std::vector<int32_t> &sizes, SetLayout &S)
     S.n = sizes;
     S.toff.resize(ns + 1);
     S.ioff.resize(ns + 1);
+    S.koff.resize(ns + 1);
     int pos = 0;
-    long long tt = 0, it = 0;
+    long long tt = 0, it = 0, kb = 0;
     for (size_t s = 0; s < ns; ++s) {
         S.start[s] = pos;
         pos += align_up(sizes[s], SET_ALIGN);
         S.toff[s] = (int32_t)tt;
         S.ioff[s] = (int32_t)it;
+        S.koff[s] = (int32_t)kb;
         const long long nt = (sizes[s] + TAU_TILE - 1) / TAU_TILE;
         tt += nt * (nt + 1) / 2;
         it += (sizes[s] + KICK_TILE - 1) / KICK_TILE;
+        kb += mixed_kick_blocks(sizes[s]);
+        S.kchunks_max = std::max(S.kchunks_max, mixed_kick_chunks(sizes[s]));
     }
     S.toff[ns] = (int32_t)tt;
     S.ioff[ns] = (int32_t)it;
+    S.koff[ns] = (int32_t)kb;
     S.total = pos;
     S.tiles = tt;
     S.itiles = it;
+    S.kblocks = kb;
 }
 
 static int upload_layout(cc_ctx *c, LevelAlloc &a, const SetLayout &S)
@@ -296,6 +333,9 @@ static int upload_layout(cc_ctx *c, LevelAlloc &a, const SetLayout &S)
     CC_CUDA(c, cudaMemcpyAsync(a.L.set_n, S.n.data(), ns * 4, cudaMemcpyHostToDevice, c->stream));
     CC_CUDA(c, cudaMemcpyAsync(a.L.tile_off, S.toff.data(), (ns + 1) * 4, cudaMemcpyHostToDevice, c->stream));
     CC_CUDA(c, cudaMemcpyAsync(a.L.itile_off, S.ioff.data(), (ns + 1) * 4, cudaMemcpyHostToDevice, c->stream));
+    CC_CUDA(c, cudaMemcpyAsync(a.L.koff, S.koff.data(), (ns + 1) * 4, cudaMemcpyHostToDevice, c->stream));
+    a.kblocks = S.kblocks;
+    a.kchunks_max = S.kchunks_max;
     a.L.total = S.total;
     a.L.nsets = ns;
     a.h_set_n = S.n;
@@ -351,23 +391,36 @@ static int split_level(cc_ctx *c, LevelAlloc &a, double h, int &ncomp)
         }
     }
     if (ntiles > 0x7fffffff) return fail(c, CC_E_ARG, "set too large for the tile grid");
-    const int ev = ev_begin(c, 0);
-    launch_tau_hook(a.L, (int)ntiles, P, c->p.precision, c->d_ctr, nullptr, 0, c->d_near_ij, c->d_near_tau,
-                    c->near_cap, s);
+    int ev;
+    if (c->p.precision == CC_PREC_MIXED) {
+        launch_prep_ff(a.L, a.F, true, s);
+        ev = ev_begin(c, 0);
+        launch_tau_mixed(a.L, a.F, (int)ntiles, P, c->d_ctr, c->d_near_ij, c->d_near_tau, c->near_cap, s);
+    } else {
+        ev = ev_begin(c, 0);
+        launch_tau_hook(a.L, (int)ntiles, P, c->p.precision, c->d_ctr, nullptr, 0, c->d_near_ij, c->d_near_tau,
+                        c->near_cap, s);
+    }
     ev_end(c, ev);
     launch_compress(a.L, a.root, s);
     launch_segment(a.L, a.root, a.members, a.comp_start, a.comp_size, a.d_ncomp, c->seg_scratch, s);
-    int32_t nc = 0;
-    CC_CUDA(c, cudaMemcpyAsync(&nc, a.d_ncomp, 4, cudaMemcpyDeviceToHost, s));
-    CC_CUDA(c, cudaStreamSynchronize(s));
-    ncomp = nc;
-    a.h_size.resize(nc);
-    a.h_start.resize(nc);
-    if (nc > 0) {
-        CC_CUDA(c, cudaMemcpyAsync(a.h_size.data(), a.comp_size, nc * 4, cudaMemcpyDeviceToHost, s));
-        CC_CUDA(c, cudaMemcpyAsync(a.h_start.data(), a.comp_start, nc * 4, cudaMemcpyDeviceToHost, s));
-        CC_CUDA(c, cudaStreamSynchronize(s));
+    // one round trip: the count and, bounded by total/2, sizes and starts
+    const int maxc = a.L.total / 2 + 1;
+    if (maxc > a.info_cap) {
+        if (a.h_info) cudaFreeHost(a.h_info);
+        a.h_info = nullptr;
+        const int cap2 = std::max(maxc, a.cap / 2 + 8);
+        CC_CUDA(c, cudaMallocHost(&a.h_info, (size_t)(2 * cap2 + 4) * 4));
+        a.info_cap = cap2;
     }
+    CC_CUDA(c, cudaMemcpyAsync(a.h_info, a.d_ncomp, 4, cudaMemcpyDeviceToHost, s));
+    CC_CUDA(c, cudaMemcpyAsync(a.h_info + 4, a.comp_size, (size_t)maxc * 4, cudaMemcpyDeviceToHost, s));
+    CC_CUDA(c, cudaMemcpyAsync(a.h_info + 4 + a.info_cap, a.comp_start, (size_t)maxc * 4, cudaMemcpyDeviceToHost, s));
+    CC_CUDA(c, cudaStreamSynchronize(s));
+    const int32_t nc = a.h_info[0];
+    ncomp = nc;
+    a.h_size.assign(a.h_info + 4, a.h_info + 4 + nc);
+    a.h_start.assign(a.h_info + 4 + a.info_cap, a.h_info + 4 + a.info_cap + nc);
     // statistics: n(n-1)/2 tau pairs per set, cross-component kick pairs
     unsigned long long tp = 0, inner = 0, memb = 0, all = 0;
     for (int32_t n : a.h_set_n) {
@@ -380,6 +433,7 @@ static int split_level(cc_ctx *c, LevelAlloc &a, double h, int &ncomp)
     }
     c->st.splits += a.h_set_n.size();
     c->st.tau_pairs += tp;
+    if (c->p.precision != CC_PREC_MIXED) c->st.tau_fp64 += tp;
     if (c->timing) {
         c->tm.tau_pairs += tp;
         c->tm.kick_pairs += tp - inner;
@@ -396,9 +450,29 @@ static int dkd(cc_ctx *c, LevelAlloc &a, double h)
     long long nit = 0;
     for (int32_t n : a.h_set_n) nit += (n + KICK_TILE - 1) / KICK_TILE;
     launch_drift(a.L, a.root, 0.5 * h, s);
-    const int ev = ev_begin(c, 1);
-    launch_kick(a.L, a.root, (int)nit, c->p.G, c->p.eps * c->p.eps, h, c->p.precision, c->d_ctr, nullptr, s);
-    ev_end(c, ev);
+    if (c->p.precision == CC_PREC_MIXED && !(h < c->p.h_fp64)) {
+        // FP32 pair forces between components; partials of multi-chunk sets
+        const size_t need = (size_t)a.kchunks_max * 3 * (size_t)a.F.cap * sizeof(double);
+        if (a.kchunks_max > 1 && need > c->kpart_sz) {
+            if (c->d_kpart) cudaFree(c->d_kpart);
+            c->d_kpart = nullptr;
+            c->kpart_sz = 0;
+            if (cudaMalloc(&c->d_kpart, need) != cudaSuccess) {
+                cudaGetLastError();
+                return fail(c, CC_E_NOMEM, "device allocation failed (kick partials)");
+            }
+            c->kpart_sz = need;
+        }
+        launch_prep_ff(a.L, a.F, false, s);
+        const int ev = ev_begin(c, 1);
+        launch_kick_mixed(a.L, a.F, a.root, a.L.koff, (int)a.kblocks, a.kchunks_max > 1, c->p.G,
+                          c->p.eps * c->p.eps, h, c->d_ctr, c->d_kpart, s);
+        ev_end(c, ev);
+    } else {
+        const int ev = ev_begin(c, 1);
+        launch_kick(a.L, a.root, (int)nit, c->p.G, c->p.eps * c->p.eps, h, c->p.precision, c->d_ctr, nullptr, s);
+        ev_end(c, ev);
+    }
     launch_drift(a.L, a.root, 0.5 * h, s);
     return CC_OK;
 }
@@ -413,17 +487,35 @@ static int process(cc_ctx *c, int d, double h)
     int ncomp = 0;
     CC_TRY(split_level(c, a, h, ncomp));
     // classify the components (host, sizes are known)
-    std::vector<int32_t> kl, lstart, lsize;
+    std::vector<int32_t> kl, sl, lstart, lsize;
     for (int q = 0; q < ncomp; ++q) {
         const int sz = a.h_size[q];
         if (c->p.kepler && sz == 2) kl.push_back(q);
+        else if (sz <= c->p.s_small) sl.push_back(q);
         else {
             lstart.push_back(a.h_start[q]);
             lsize.push_back(sz);
         }
     }
-    const int nk = (int)kl.size(), nl = (int)lsize.size();
+    // small components largest first: the longest sub-recursions start early
+    std::stable_sort(sl.begin(), sl.end(), [&](int32_t u, int32_t v) { return a.h_size[u] > a.h_size[v]; });
+    const int nk = (int)kl.size(), nl = (int)lsize.size(), ns = (int)sl.size();
     if (nk) CC_CUDA(c, cudaMemcpyAsync(a.klist, kl.data(), nk * 4, cudaMemcpyHostToDevice, c->stream));
+    if (ns) CC_CUDA(c, cudaMemcpyAsync(a.slist, sl.data(), ns * 4, cudaMemcpyHostToDevice, c->stream));
+    SmallParams SP;
+    SP.G = c->p.G;
+    SP.eps2 = c->p.eps * c->p.eps;
+    SP.eta = c->eta_run;
+    SP.eta_in = c->p.eta_outside ? 1.0 : c->eta_run;
+    SP.h0 = 0.5 * h;
+    SP.near_tol = c->p.near_tol;
+    SP.h_fp64 = c->p.h_fp64;
+    SP.eta_outside = c->p.eta_outside;
+    SP.kepler = c->p.kepler;
+    SP.precision = c->p.precision;
+    SP.depth0 = d + 1;
+    SP.max_depth = c->p.max_depth;
+    if (ns && d + 1 > c->p.max_depth) return fail(c, CC_E_DEPTH, "recursion deeper than max_depth");
     c->st.kepler_calls += 2ull * nk;
     int nmem = 0;
     if (nl) {
@@ -438,8 +530,27 @@ static int process(cc_ctx *c, int d, double h)
         CC_TRY(upload_layout(c, c->lv[d + 1], S));
     }
     LevelAlloc &a2 = a;
+    if (ns && !a2.ev_ready) {
+        CC_CUDA(c, cudaEventCreateWithFlags(&a2.ev_ready, cudaEventDisableTiming));
+        CC_CUDA(c, cudaEventCreateWithFlags(&a2.ev_small, cudaEventDisableTiming));
+    }
     for (int half = 0; half < 2; ++half) {
-        if (half == 1) CC_TRY(dkd(c, a2, h));
+        if (half == 1) {
+            if (ns) CC_CUDA(c, cudaStreamWaitEvent(c->stream, a2.ev_small, 0));
+            CC_TRY(dkd(c, a2, h));
+        }
+        if (ns) {
+            // the small components run on the side stream, overlapping the
+            // Kepler pairs and the recursion of the large components (they
+            // touch disjoint particles); the DKD and the return join them
+            CC_CUDA(c, cudaEventRecord(a2.ev_ready, c->stream));
+            CC_CUDA(c, cudaStreamWaitEvent(c->side, a2.ev_ready, 0));
+            const int ev = ev_begin(c, 2, c->side);
+            launch_small(a2.L, a2.members, a2.comp_start, a2.comp_size, a2.slist, ns, SP, c->d_ctr,
+                         c->d_queue + 4 * (d & 1), c->d_near_ij, c->d_near_tau, c->near_cap, c->nsm, c->side);
+            ev_end(c, ev, c->side);
+            CC_CUDA(c, cudaEventRecord(a2.ev_small, c->side));
+        }
         if (nk) launch_kepler(a2.L, a2.members, a2.comp_start, a2.klist, nk, c->p.G, 0.5 * h, c->d_ctr, c->stream);
         if (nl) {
             LevelAlloc &ch = c->lv[d + 1];
@@ -448,6 +559,7 @@ static int process(cc_ctx *c, int d, double h)
             launch_scatter(a2.L, ch.L, c->stream);
         }
     }
+    if (ns) CC_CUDA(c, cudaStreamWaitEvent(c->stream, a2.ev_small, 0));
     return CC_OK;
 }
 
@@ -484,6 +596,20 @@ static int harvest_counters(cc_ctx *c)
     CC_CUDA(c, cudaStreamSynchronize(c->stream));
     c->st.edges += h.edges;
     c->st.near_pairs += h.near_pairs;
+    c->st.tau_fp64 += h.tau_fp64;
+    // sub-recursions run by the small-component kernel
+    c->st.tau_pairs += h.small_tau_pairs;
+    c->st.kick_pairs += h.small_kick_pairs;
+    c->st.drifts += h.small_drifts;
+    c->st.splits += h.small_splits;
+    c->st.components += h.small_components;
+    c->st.kepler_calls += h.small_kepler;
+    if (c->timing) {
+        c->tm.tau_pairs += h.small_tau_pairs;
+        c->tm.kick_pairs += h.small_kick_pairs;
+    }
+    if (h.max_depth_seen > c->st.max_depth_seen) c->st.max_depth_seen = h.max_depth_seen;
+    CC_CUDA(c, cudaMemsetAsync(&c->d_ctr->tau_fp64, 0, sizeof(unsigned long long) * 8, c->stream));
     return CC_OK;
 }
 
@@ -539,12 +665,19 @@ int cc_init(cc_ctx **out, int64_t n, const double *m, const double *x3, const do
         cudaMalloc(&c->d_m, n * 8) != cudaSuccess || cudaMalloc(&c->d_ctr, sizeof(DevCounters)) != cudaSuccess ||
         cudaMalloc(&c->d_near_ij, c->near_cap * 8) != cudaSuccess ||
         cudaMalloc(&c->d_near_tau, c->near_cap * 8) != cudaSuccess ||
-        cudaMalloc(&c->d_bad, 16) != cudaSuccess) {
+        cudaMalloc(&c->d_bad, 16) != cudaSuccess || cudaMalloc(&c->d_queue, 64) != cudaSuccess ||
+        cudaStreamCreateWithFlags(&c->side, cudaStreamNonBlocking) != cudaSuccess) {
         cudaGetLastError();
         c->err = "cc_init: device allocation failed";
         return bail(CC_E_NOMEM);
     }
     cudaMemsetAsync(c->d_ctr, 0, sizeof(DevCounters), c->stream);
+    {
+        int dev = 0;
+        cudaGetDevice(&dev);
+        cudaDeviceGetAttribute(&c->nsm, cudaDevAttrMultiProcessorCount, dev);
+        if (c->nsm <= 0) c->nsm = 1;
+    }
     c->lv.resize(p->max_depth + 2);
     int rc = cc_set_state(c, 0.0, m, x3, v3);
     if (rc) return bail(rc);
@@ -843,11 +976,15 @@ int cc_destroy(cc_ctx *c)
 {
     if (!c) return CC_OK;
     if (c->stream) cudaStreamSynchronize(c->stream);
+    if (c->side) {
+        cudaStreamSynchronize(c->side);
+        cudaStreamDestroy(c->side);
+    }
     for (cudaEvent_t e : c->evs) cudaEventDestroy(e);
     for (auto &a : c->lv) free_level(a);
     free_level(c->unit);
     void *ptrs[] = {c->d_x3, c->d_v3, c->d_m, c->d_ctr, c->d_near_ij, c->d_near_tau, c->d_partial,
-                    c->tmp, c->seg_scratch, c->d_sys_off, c->d_bad};
+                    c->tmp, c->seg_scratch, c->d_sys_off, c->d_bad, c->d_kpart, c->d_queue};
     for (void *q : ptrs)
         if (q) cudaFree(q);
     delete c;

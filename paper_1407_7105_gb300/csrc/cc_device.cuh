@@ -1,0 +1,200 @@
+// cc_device.cuh -- device functions shared by several kernels of libcc.so:
+// the certified FP32 decision of the edge predicate tau(i,j) < h
+// (arXiv:1407.7105 Eq. tauij), compensated summation, and the universal-
+// variable two-body flow of the CC_KEPLER variant (Sec. 3.2).
+#pragma once
+#include "cc_internal.cuh"
+
+namespace cc {
+
+// ------------------------------------------------------------ tau, FP32 certified
+// Error model (u = 2^-24; +,-,*,fma round to nearest: u each; rsqrtf within
+// 2 ulp, budgeted 8u; every bound below is budgeted generously):
+//   |dx~ - dx| <= er r,  er = 2.05u + 11u^2 X / r      (float-float difference)
+//   |dv~ - dv| <= ev |dv|, ev = 2.05u + 11u^2 V / |dv|
+//   rinv = rsqrt(r2), s1 = rsqrt(r mu), s2 = rsqrt(v2)
+//   T_ff = eta r2 s1          (= eta sqrt(r^3/mu)),      rel. error <= 40u + 3er
+//   T_fb = eta r s2           (= eta r/|dv|),            rel. error <= 40u + 3er + 3ev
+//   dT_ff = 1.5 eta rv s1,  dT_fb = eta rv s2 rinv (1 + mu s2^2 rinv)
+//   rv = dx.dv has no relative bound (cancellation): |drv| <= (er+ev+4u) r |dv|,
+//   so |d dT| <= 32u|dT_ff| + 1.5 eta s1 |drv|   (ff)
+//              80u|dT_fb| + eta s2 rinv (1 + mu s2^2 rinv) |drv|   (fb)
+//   D = 1 - min(dT,1)/2 >= 1/2,  |dD| <= |d dT|/2 + 2u D
+// tau_x = T_x / D_x < h is certain when T~(1+eT)(1+s) < h (D~ - dD), and
+// certainly false when T~(1-eT)(1-s) >= h (D~ + dD); the slack s = 2e-6
+// covers the FP32 evaluation of the bounds and the FP64 predicate's own
+// rounding.  Any NaN/Inf fails both tests: the pair is undecided.
+constexpr float U32 = 5.9604645e-8f;  // 2^-24
+constexpr float SLACK = 2e-6f;
+
+struct MixedTauParams {
+    float eta, h, eps2, G;
+};
+
+__device__ __forceinline__ int tau_decide_fp32(float dx0, float dx1, float dx2, float dv0, float dv1, float dv2,
+                                               float mu, float X, float V, const MixedTauParams &Q)
+{
+    // returns 1 = edge certain, 0 = no edge certain, -1 = undecided
+    const float r2 = fmaf(dx2, dx2, fmaf(dx1, dx1, fmaf(dx0, dx0, Q.eps2)));
+    const float v2 = fmaf(dv2, dv2, fmaf(dv1, dv1, dv0 * dv0));
+    const float rv = fmaf(dx2, dv2, fmaf(dx1, dv1, dx0 * dv0));
+    const float rinv = rsqrtf(r2);
+    const float r = r2 * rinv;
+    const float er = 2.05f * U32 + 11.f * U32 * U32 * X * rinv;
+    const float s1 = rsqrtf(r * mu);
+    const float Tff = Q.eta * r2 * s1;
+    const float dTff = 1.5f * Q.eta * rv * s1;
+    // velocity-dependent pieces (v2 == 0: flyby time infinite)
+    const bool has_v = v2 > 0.f;
+    const float s2 = has_v ? rsqrtf(v2) : 0.f;
+    const float vn = v2 * s2;  // |dv|
+    const float ev = has_v ? 2.05f * U32 + 11.f * U32 * U32 * V * s2 : 0.f;
+    const float drv = (er + ev + 4.f * U32) * r * vn;
+    // free-fall branch
+    const float ddff = 32.f * U32 * fabsf(dTff) + 1.5f * Q.eta * s1 * drv;
+    const float Dff = 1.f - 0.5f * fminf(dTff, 1.f);
+    const float dDff = 0.5f * ddff + 2.f * U32 * Dff;
+    const float eff = 40.f * U32 + 3.f * er;
+    const bool ff_yes = Tff * (1.f + eff) * (1.f + SLACK) < Q.h * (Dff - dDff);
+    const bool ff_no = Tff * (1.f - eff) * (1.f - SLACK) >= Q.h * (Dff + dDff);
+    // an exactly zero (or unresolved) FP32 velocity difference may hide a
+    // tiny nonzero FP64 one, whose flyby term can be small: only a certain
+    // free-fall edge decides such a pair
+    if (!has_v || vn < 64.f * U32 * U32 * V) return ff_yes ? 1 : -1;
+    const float Tfb = Q.eta * r * s2;
+    const float g = 1.f + mu * s2 * s2 * rinv;
+    const float dTfb = Q.eta * rv * s2 * rinv * g;
+    const float ddfb = 80.f * U32 * fabsf(dTfb) + Q.eta * s2 * rinv * g * drv;
+    const float Dfb = 1.f - 0.5f * fminf(dTfb, 1.f);
+    const float dDfb = 0.5f * ddfb + 2.f * U32 * Dfb;
+    const float efb = 40.f * U32 + 3.f * er + 3.f * ev;
+    const bool fb_yes = Tfb * (1.f + efb) * (1.f + SLACK) < Q.h * (Dfb - dDfb);
+    const bool fb_no = Tfb * (1.f - efb) * (1.f - SLACK) >= Q.h * (Dfb + dDfb);
+    if (ff_yes || fb_yes) return 1;
+    if (ff_no && fb_no) return 0;
+    return -1;
+}
+
+// Kahan-compensated accumulation: s + (-c) carries the running sum
+__device__ __forceinline__ void kahan_add(float &s, float &c, float x)
+{
+    const float y = x - c;
+    const float t = s + y;
+    c = (t - s) - y;
+    s = t;
+}
+
+// ------------------------------------------------------------ Kepler
+// Stumpff functions c2(z) = (1 - cos sqrt z)/z, c3(z) = (sqrt z - sin sqrt z)/z^{3/2}
+// (hyperbolic continuation for z < 0), by their Taylor series near 0.
+__device__ __forceinline__ void stumpff(double z, double &c2, double &c3)
+{
+    if (fabs(z) < 0.1) {
+        // c2 = sum (-z)^k/(2k+2)!, c3 = sum (-z)^k/(2k+3)!
+        double t2 = 0.5, t3 = 1.0 / 6.0;
+        c2 = 0.0;
+        c3 = 0.0;
+#pragma unroll
+        for (int k = 0; k < 10; ++k) {
+            c2 += t2;
+            c3 += t3;
+            t2 *= -z / ((2.0 * k + 3.0) * (2.0 * k + 4.0));
+            t3 *= -z / ((2.0 * k + 4.0) * (2.0 * k + 5.0));
+        }
+    } else if (z > 0.0) {
+        const double s = sqrt(z);
+        double sn, cs;
+        sincos(s, &sn, &cs);
+        c2 = (1.0 - cs) / z;
+        c3 = (s - sn) / (z * s);
+    } else {
+        const double s = sqrt(-z);
+        c2 = (cosh(s) - 1.0) / (-z);
+        c3 = (sinh(s) - s) / (-z * s);
+    }
+}
+
+// Advance the relative orbit (r0, v0) under mu by dt; returns false when
+// the iteration does not converge.
+__device__ __forceinline__ bool kepler_universal(const double r0[3], const double v0[3], double mu, double dt, double r1[3],
+                                 double v1[3])
+{
+    const double r0n = sqrt(r0[0] * r0[0] + r0[1] * r0[1] + r0[2] * r0[2]);
+    const double v0s = v0[0] * v0[0] + v0[1] * v0[1] + v0[2] * v0[2];
+    const double sig = r0[0] * v0[0] + r0[1] * v0[1] + r0[2] * v0[2];
+    const double smu = sqrt(mu);
+    const double alpha = 2.0 / r0n - v0s / mu;
+    if (!(r0n > 0.0) || !(mu > 0.0) || !isfinite(alpha)) return false;
+    // whole periods of a bound orbit are the identity: reduce dt
+    if (alpha > 0.0) {
+        const double P = 2.0 * CUDART_PI * sqrt(1.0 / (mu * alpha * alpha * alpha));
+        if (fabs(dt) > P) dt = dt - P * trunc(dt / P);
+    }
+    const double a1 = sig / smu, a2 = 1.0 - alpha * r0n;
+    double chi = (alpha > 0.0) ? smu * alpha * dt : smu * dt / r0n;
+    if (alpha > 0.0 && fabs(alpha * r0n) < 1e-3) chi = smu * dt / r0n;
+    double c2 = 0.5, c3 = 1.0 / 6.0, F1 = r0n;
+    bool conv = false;
+    // Laguerre-Conway iteration (order n = 5) on the universal Kepler equation
+    for (int it = 0; it < 200; ++it) {
+        const double x2 = chi * chi, z = alpha * x2;
+        stumpff(z, c2, c3);
+        const double F = a1 * x2 * c2 + a2 * x2 * chi * c3 + r0n * chi - smu * dt;
+        F1 = a1 * chi * (1.0 - z * c3) + a2 * x2 * c2 + r0n;
+        const double F2 = a1 * (1.0 - z * c2) + a2 * chi * (1.0 - z * c3);
+        const double disc = sqrt(fabs(16.0 * F1 * F1 - 20.0 * F * F2));
+        const double den = F1 + copysign(disc, F1);
+        const double d = (den != 0.0) ? 5.0 * F / den : F / F1;
+        chi -= d;
+        if (fabs(d) <= 1e-15 * fmax(1.0, fabs(chi))) {
+            conv = true;
+            break;
+        }
+    }
+    if (!conv) return false;
+    // one Newton polish at the converged point
+    {
+        const double x2 = chi * chi, z = alpha * x2;
+        stumpff(z, c2, c3);
+        const double F = a1 * x2 * c2 + a2 * x2 * chi * c3 + r0n * chi - smu * dt;
+        F1 = a1 * chi * (1.0 - z * c3) + a2 * x2 * c2 + r0n;
+        chi -= F / F1;
+    }
+    const double x2 = chi * chi, z = alpha * x2;
+    stumpff(z, c2, c3);
+    const double f = 1.0 - x2 * c2 / r0n;
+    const double g = dt - x2 * chi * c3 / smu;
+    for (int k = 0; k < 3; ++k) r1[k] = f * r0[k] + g * v0[k];
+    const double r = sqrt(r1[0] * r1[0] + r1[1] * r1[1] + r1[2] * r1[2]);
+    const double fd = smu / (r * r0n) * chi * (z * c3 - 1.0);
+    const double gd = 1.0 - x2 * c2 / r;
+    for (int k = 0; k < 3; ++k) v1[k] = fd * r0[k] + gd * v0[k];
+    return isfinite(r);
+}
+
+// Two-body flow of particles a and b over dt (Eq. kepler, eps = 0): the
+// centre of mass moves uniformly, the relative orbit r = x_a - x_b follows
+// kepler_universal.  xa.. are updated in place; false if unconverged.
+__device__ __forceinline__ bool kepler_pair(double ma, double mb, double xa[3], double xb[3], double va[3],
+                                            double vb[3], double G, double dt)
+{
+    const double M = ma + mb;
+    double r0[3], v0[3], xc[3], vc[3], r1[3], v1[3];
+    for (int k = 0; k < 3; ++k) {
+        xc[k] = (ma * xa[k] + mb * xb[k]) / M;
+        vc[k] = (ma * va[k] + mb * vb[k]) / M;
+        r0[k] = xa[k] - xb[k];
+        v0[k] = va[k] - vb[k];
+    }
+    if (!kepler_universal(r0, v0, G * M, dt, r1, v1)) return false;
+    for (int k = 0; k < 3; ++k) {
+        const double xcn = xc[k] + vc[k] * dt;
+        xa[k] = xcn + (mb / M) * r1[k];
+        xb[k] = xcn - (ma / M) * r1[k];
+        va[k] = vc[k] + (mb / M) * v1[k];
+        vb[k] = vc[k] - (ma / M) * v1[k];
+    }
+    return true;
+}
+
+}  // namespace cc

@@ -27,8 +27,18 @@ struct Level {
     int32_t *set_start, *set_n;      // [nsets]
     int32_t *tile_off;               // [nsets+1] triangular tau tiles prefix
     int32_t *itile_off;              // [nsets+1] i-tiles prefix (kick)
+    int32_t *koff;                   // [nsets+1] mixed-kick blocks prefix
     int32_t total;                   // packed length including padding
     int32_t nsets;
+};
+
+// float-float copy of a level (mixed-precision kernels): hi = fl32(x),
+// lo = fl32(x - hi) for positions and velocities, FP32 masses, and the
+// level's max |x|, max |v| (float bit patterns, for the error bounds)
+struct FFView {
+    float *ph[3], *pl[3], *vh[3], *vl[3], *m;
+    float *maxes;
+    int cap;
 };
 
 // bounded-wait error codes written to the device error word
@@ -54,6 +64,13 @@ struct DevCounters {
     unsigned long long small_components;
     unsigned int err;
     int max_depth_seen;
+};
+
+// parameters of the small-component kernel: h0 is the pivot of the
+// components it receives (half the parent's), depth0 their recursion depth
+struct SmallParams {
+    double G, eps2, eta, eta_in, h0, near_tol, h_fp64;
+    int eta_outside, kepler, precision, depth0, max_depth;
 };
 
 struct TauParams {
@@ -239,6 +256,21 @@ void launch_check_state(const double *m, const double *x3, const double *v3, lon
 size_t sort_scratch_bytes(long long n);
 
 double probe_fma(int fp64, int nsm, cudaStream_t s);
+
+// cc_mixed.cu
+void launch_prep_ff(const Level &L, const FFView &F, bool with_v, cudaStream_t s);
+void launch_tau_mixed(const Level &L, const FFView &F, int ntiles, const TauParams &P, DevCounters *ctr,
+                      int32_t *near_ij, double *near_tau, long long near_cap, cudaStream_t s);
+int mixed_kick_blocks(int n);
+int mixed_kick_chunks(int n);
+void launch_kick_mixed(const Level &L, const FFView &F, const int32_t *label, const int32_t *koff, int nblocks,
+                       bool multi_chunk, double G, double eps2, double h, DevCounters *ctr, double *partial,
+                       cudaStream_t s);
+
+// cc_small.cu
+void launch_small(const Level &L, const int32_t *members, const int32_t *comp_start, const int32_t *comp_size,
+                  const int32_t *slist, int ns, const SmallParams &SP, DevCounters *ctr, int *queue,
+                  int32_t *near_ij, double *near_tau, long long near_cap, int nsm, cudaStream_t s);
 
 // cc_kepler.cu
 void launch_kepler(const Level &L, const int32_t *members, const int32_t *comp_start, const int32_t *klist,

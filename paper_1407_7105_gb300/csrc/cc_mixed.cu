@@ -1,0 +1,394 @@
+// cc_mixed.cu -- mixed-precision forms of the two pair kernels of the CC
+// split (arXiv:1407.7105, Eqs. tauij, kickij/kickji):
+//
+//  * k_tau_mixed: the edge predicate tau(i,j) < h decided in FP32 with a
+//    rigorous per-pair error bound; a pair whose FP32 value is too close to
+//    h for the bound to decide is re-evaluated with the exact FP64
+//    predicate (tau_fp64), so the edge set is identical to the FP64 one.
+//  * k_kick_mixed: pair forces in FP32 from float-float position
+//    differences, rsqrt plus one Newton step, Kahan-compensated FP32 sums,
+//    partial sums over j-chunks combined in FP64; v stays FP64.
+//
+// Positions and velocities are carried as float pairs (hi = fl32(x),
+// lo = fl32(x - hi)), so x_j - x_i = (hi_j - hi_i) + (lo_j - lo_i) is formed
+// with relative error <= 2u + 11 u^2 X / r (u = 2^-24, X = max |x|),
+// the accuracy of an FP64 difference rounded to FP32 up to one more
+// rounding, at three FP32 additions instead of three FP64 subtractions
+// (GB300 issues FP64 at 1/58 of the FP32 rate).
+#include "cc_device.cuh"
+
+namespace cc {
+
+// ------------------------------------------------------------ prep
+// float-float copy of the packed state; per-level maxima of |x| and |v|
+__global__ void k_prep_ff(Level L, FFView F, int with_v)
+{
+    const int k = blockIdx.x * blockDim.x + threadIdx.x;
+    float ax = 0.f, av = 0.f;
+    if (k < L.total && L.gid[k] >= 0) {
+        const double xs[3] = {L.x[k], L.y[k], L.z[k]};
+#pragma unroll
+        for (int c = 0; c < 3; ++c) {
+            const float hi = __double2float_rn(xs[c]);
+            F.ph[c][k] = hi;
+            F.pl[c][k] = __double2float_rn(xs[c] - (double)hi);
+            ax = fmaxf(ax, fabsf(hi));
+        }
+        F.m[k] = __double2float_rn(L.m[k]);
+        if (with_v) {
+            const double vs[3] = {L.vx[k], L.vy[k], L.vz[k]};
+#pragma unroll
+            for (int c = 0; c < 3; ++c) {
+                const float hi = __double2float_rn(vs[c]);
+                F.vh[c][k] = hi;
+                F.vl[c][k] = __double2float_rn(vs[c] - (double)hi);
+                av = fmaxf(av, fabsf(hi));
+            }
+        }
+    }
+    // positive floats order like their bit patterns
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        ax = fmaxf(ax, __shfl_xor_sync(0xffffffffu, ax, o));
+        av = fmaxf(av, __shfl_xor_sync(0xffffffffu, av, o));
+    }
+    if ((threadIdx.x & 31) == 0) {
+        if (ax > 0.f) atomicMax((int *)&F.maxes[0], __float_as_int(ax));
+        if (av > 0.f) atomicMax((int *)&F.maxes[1], __float_as_int(av));
+    }
+}
+
+void launch_prep_ff(const Level &L, const FFView &F, bool with_v, cudaStream_t s)
+{
+    if (L.total <= 0) return;
+    cudaMemsetAsync(F.maxes, 0, 2 * sizeof(float), s);
+    k_prep_ff<<<(L.total + 255) / 256, 256, 0, s>>>(L, F, with_v ? 1 : 0);
+    CC_COUNT_LAUNCH(1);
+}
+
+constexpr int MT_T = 128;
+
+struct __align__(16) MixedTauSmem {
+    float col[13][MT_T + 4];  // ph[3] pl[3] vh[3] vl[3] m
+    int32_t lp[2 * MT_T];     // local union-find over the tile's particles
+    uint64_t bar;
+};
+
+// local union-find in shared memory (indices 0..2T-1, links to the smaller)
+__device__ __forceinline__ int luf_find(volatile int32_t *p, int x)
+{
+    while (true) {
+        const int q = p[x];
+        if (q == x) return x;
+        const int g = p[q];
+        if (g != q) p[x] = g;
+        x = q;
+    }
+}
+
+__device__ __forceinline__ bool luf_union(int32_t *p, int a, int b)
+{
+    volatile int32_t *vp = p;
+    for (int it = 0; it < (1 << 20); ++it) {
+        a = luf_find(vp, a);
+        b = luf_find(vp, b);
+        if (a == b) return true;
+        if (a > b) {
+            const int t = a; a = b; b = t;
+        }
+        if (atomicCAS(&p[b], b, a) == b) return true;
+    }
+    return false;
+}
+
+__global__ void __launch_bounds__(MT_T) k_tau_mixed(Level L, FFView F, TauParams P, MixedTauParams Q,
+                                                     DevCounters *ctr, int32_t *near_ij, double *near_tau,
+                                                     long long near_cap)
+{
+    __shared__ MixedTauSmem sm;
+    const int tid = threadIdx.x;
+    int lo = 0, hi = L.nsets;
+    while (hi - lo > 1) {
+        const int mid = (lo + hi) >> 1;
+        if (L.tile_off[mid] <= (int)blockIdx.x) lo = mid; else hi = mid;
+    }
+    const int s = lo;
+    int t = blockIdx.x - L.tile_off[s];
+    const int n = L.set_n[s], start = L.set_start[s];
+    const int nt = (n + MT_T - 1) / MT_T;
+    int ti = 0;
+    while (t >= nt - ti) {
+        t -= nt - ti;
+        ++ti;
+    }
+    const int tj = ti + t;
+    const bool diag = ti == tj;
+    const int j0 = start + tj * MT_T;
+    const int jn = min(MT_T, n - tj * MT_T);
+    if (tid == 0) {
+        mbar_init(&sm.bar, 1);
+        fence_mbar_init();
+    }
+    sm.lp[tid] = tid;
+    sm.lp[MT_T + tid] = MT_T + tid;
+    __syncthreads();
+    if (tid == 0) {
+        const unsigned bytes = (unsigned)((jn + 3) & ~3) * 4u;
+        mbar_expect_tx(&sm.bar, 13u * bytes);
+        const float *src[13] = {F.ph[0], F.ph[1], F.ph[2], F.pl[0], F.pl[1], F.pl[2], F.vh[0],
+                                F.vh[1], F.vh[2], F.vl[0], F.vl[1], F.vl[2], F.m};
+#pragma unroll
+        for (int c = 0; c < 13; ++c) tma_load_1d(sm.col[c], src[c] + j0, bytes, &sm.bar);
+    }
+    const int il = ti * MT_T + tid;
+    const bool iv = il < n;
+    const int i = start + il;
+    float xh = 0, yh = 0, zh = 0, xl = 0, yl = 0, zl = 0, uh = 0, vh = 0, wh = 0, ul = 0, vl = 0, wl = 0, mi = 0;
+    if (iv) {
+        xh = F.ph[0][i]; yh = F.ph[1][i]; zh = F.ph[2][i];
+        xl = F.pl[0][i]; yl = F.pl[1][i]; zl = F.pl[2][i];
+        uh = F.vh[0][i]; vh = F.vh[1][i]; wh = F.vh[2][i];
+        ul = F.vl[0][i]; vl = F.vl[1][i]; wl = F.vl[2][i];
+        mi = F.m[i];
+    }
+    const float X = F.maxes[0], V = F.maxes[1];
+    const bool got = mbar_wait(&sm.bar, 0, TMA_WAIT_CYCLES);
+    if (__syncthreads_or(!got)) {
+        raise_err(ctr, DERR_TMA_TIMEOUT);
+        mbar_wait(&sm.bar, 0, TMA_WAIT_CYCLES);
+        return;
+    }
+    unsigned long long my_edges = 0, my_fp64 = 0;
+    const int joff = diag ? 0 : MT_T;  // local index base of the j-tile
+    if (iv) {
+        const float Gf = Q.G;
+        for (int k = diag ? tid + 1 : 0; k < jn; ++k) {
+            const float dx0 = (sm.col[0][k] - xh) + (sm.col[3][k] - xl);
+            const float dx1 = (sm.col[1][k] - yh) + (sm.col[4][k] - yl);
+            const float dx2 = (sm.col[2][k] - zh) + (sm.col[5][k] - zl);
+            const float dv0 = (sm.col[6][k] - uh) + (sm.col[9][k] - ul);
+            const float dv1 = (sm.col[7][k] - vh) + (sm.col[10][k] - vl);
+            const float dv2 = (sm.col[8][k] - wh) + (sm.col[11][k] - wl);
+            const float mu = Gf * (mi + sm.col[12][k]);
+            int dec = tau_decide_fp32(dx0, dx1, dx2, dv0, dv1, dv2, mu, X, V, Q);
+            if (dec < 0) {
+                // undecided: the exact FP64 predicate of the FP64 form
+                const int j = j0 + k;
+                const double tau = tau_fp64(__dsub_rn(L.x[i], L.x[j]), __dsub_rn(L.y[i], L.y[j]),
+                                            __dsub_rn(L.z[i], L.z[j]), __dsub_rn(L.vx[i], L.vx[j]),
+                                            __dsub_rn(L.vy[i], L.vy[j]), __dsub_rn(L.vz[i], L.vz[j]), L.m[i],
+                                            L.m[j], P);
+                ++my_fp64;
+                if (fabs(tau - P.h) < P.near_tol * P.h) {
+                    unsigned long long q = atomicAdd(&ctr->near_pairs, 1ull);
+                    if ((long long)q < near_cap) {
+                        const int gi = L.gid[i], gj = L.gid[j];
+                        near_ij[2 * q] = gi < gj ? gi : gj;
+                        near_ij[2 * q + 1] = gi < gj ? gj : gi;
+                        near_tau[q] = tau;
+                    }
+                }
+                dec = tau < P.h ? 1 : 0;
+            }
+            if (dec) {
+                ++my_edges;
+                if (!luf_union(sm.lp, tid, joff + k)) raise_err(ctr, DERR_UF_RETRY);
+            }
+        }
+    }
+    __syncthreads();
+    // merge the tile's local components into the global forest: one union
+    // per local non-root element instead of one per edge
+    for (int e = tid; e < (diag ? MT_T : 2 * MT_T); e += MT_T) {
+        const int r = luf_find(sm.lp, e);
+        if (r != e) {
+            const int ge = (e < MT_T) ? start + ti * MT_T + e : j0 + (e - MT_T);
+            const int gr = (r < MT_T) ? start + ti * MT_T + r : j0 + (r - MT_T);
+            if (!uf_union(L.parent, ge, gr)) raise_err(ctr, DERR_UF_RETRY);
+        }
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        my_edges += __shfl_down_sync(0xffffffffu, my_edges, o);
+        my_fp64 += __shfl_down_sync(0xffffffffu, my_fp64, o);
+    }
+    if ((tid & 31) == 0) {
+        if (my_edges) atomicAdd(&ctr->edges, my_edges);
+        if (my_fp64) atomicAdd(&ctr->tau_fp64, my_fp64);
+    }
+}
+
+void launch_tau_mixed(const Level &L, const FFView &F, int ntiles, const TauParams &P, DevCounters *ctr,
+                      int32_t *near_ij, double *near_tau, long long near_cap, cudaStream_t s)
+{
+    if (ntiles <= 0) return;
+    MixedTauParams Q;
+    Q.eta = (float)P.eta_in;
+    Q.h = (float)(P.eta_outside ? P.h / P.eta : P.h);
+    Q.eps2 = (float)P.eps2;
+    Q.G = (float)P.G;
+    k_tau_mixed<<<ntiles, MT_T, 0, s>>>(L, F, P, Q, ctr, near_ij, near_tau, near_cap);
+    CC_COUNT_LAUNCH(1);
+}
+
+// ------------------------------------------------------------ kick, FP32
+// Grid: (set, i-tile, j-chunk).  Thread r of an i-tile accumulates
+// sum_j m_j (x_j - x_i) |x_j - x_i|^-3 over the chunk's j (labels differ)
+// in compensated FP32; the chunk's partial goes to scratch in FP64 unless
+// the set has a single chunk, in which case v is updated directly.
+constexpr int MK_T = 128;
+constexpr int MK_CHUNK_TILES = 8;  // j-tiles per chunk (1024 j)
+
+struct __align__(16) MixedKickSmem {
+    float col[2][7][MK_T];  // ph[3] pl[3] m
+    int32_t lab[2][MK_T];
+    uint64_t bar[2];
+};
+
+__device__ __forceinline__ void mk_issue(MixedKickSmem &sm, int st, const FFView &F, const int32_t *label,
+                                         int j0, int jn)
+{
+    const unsigned cnt = (unsigned)((jn + 3) & ~3);
+    fence_proxy_async_smem();
+    mbar_expect_tx(&sm.bar[st], cnt * (7u * 4u + 4u));
+    tma_load_1d(sm.col[st][0], F.ph[0] + j0, cnt * 4u, &sm.bar[st]);
+    tma_load_1d(sm.col[st][1], F.ph[1] + j0, cnt * 4u, &sm.bar[st]);
+    tma_load_1d(sm.col[st][2], F.ph[2] + j0, cnt * 4u, &sm.bar[st]);
+    tma_load_1d(sm.col[st][3], F.pl[0] + j0, cnt * 4u, &sm.bar[st]);
+    tma_load_1d(sm.col[st][4], F.pl[1] + j0, cnt * 4u, &sm.bar[st]);
+    tma_load_1d(sm.col[st][5], F.pl[2] + j0, cnt * 4u, &sm.bar[st]);
+    tma_load_1d(sm.col[st][6], F.m + j0, cnt * 4u, &sm.bar[st]);
+    tma_load_1d(sm.lab[st], label + j0, cnt * 4u, &sm.bar[st]);
+}
+
+__global__ void __launch_bounds__(MK_T) k_kick_mixed(Level L, FFView F, const int32_t *label, const int32_t *koff,
+                                                      float eps2, double Gh, DevCounters *ctr, double *partial)
+{
+    __shared__ MixedKickSmem sm;
+    const int tid = threadIdx.x;
+    int lo = 0, hi = L.nsets;
+    while (hi - lo > 1) {
+        const int mid = (lo + hi) >> 1;
+        if (koff[mid] <= (int)blockIdx.x) lo = mid; else hi = mid;
+    }
+    const int s = lo;
+    const int b = blockIdx.x - koff[s];
+    const int n = L.set_n[s], start = L.set_start[s];
+    const int ntile = (n + MK_T - 1) / MK_T;
+    const int nchunk = (ntile + MK_CHUNK_TILES - 1) / MK_CHUNK_TILES;
+    const int ti = b / nchunk, ch = b % nchunk;
+    const int tj0 = ch * MK_CHUNK_TILES, tj1 = min(ntile, tj0 + MK_CHUNK_TILES);
+    const int il = ti * MK_T + tid;
+    const bool iv = il < n;
+    const int i = start + il;
+    if (tid == 0) {
+        mbar_init(&sm.bar[0], 1);
+        mbar_init(&sm.bar[1], 1);
+        fence_mbar_init();
+    }
+    __syncthreads();
+    if (tid == 0) mk_issue(sm, 0, F, label, start + tj0 * MK_T, min(MK_T, n - tj0 * MK_T));
+    float xh = 0, yh = 0, zh = 0, xl = 0, yl = 0, zl = 0;
+    int li = 0;
+    if (iv) {
+        xh = F.ph[0][i]; yh = F.ph[1][i]; zh = F.ph[2][i];
+        xl = F.pl[0][i]; yl = F.pl[1][i]; zl = F.pl[2][i];
+        li = label[i];
+    }
+    float sx = 0.f, sy = 0.f, sz = 0.f, cx = 0.f, cy = 0.f, cz = 0.f;
+    bool ok = true;
+    for (int tj = tj0; tj < tj1; ++tj) {
+        const int q = tj - tj0, st = q & 1;
+        if (tid == 0 && tj + 1 < tj1)
+            mk_issue(sm, st ^ 1, F, label, start + (tj + 1) * MK_T, min(MK_T, n - (tj + 1) * MK_T));
+        const bool got = mbar_wait(&sm.bar[st], (q >> 1) & 1, TMA_WAIT_CYCLES);
+        if (__syncthreads_or(!got)) {
+            ok = false;
+            break;
+        }
+        const int jn = min(MK_T, n - tj * MK_T);
+        if (iv) {
+#pragma unroll 4
+            for (int k = 0; k < jn; ++k) {
+                if (sm.lab[st][k] == li || tj * MK_T + k == il) continue;
+                const float dx = (sm.col[st][0][k] - xh) + (sm.col[st][3][k] - xl);
+                const float dy = (sm.col[st][1][k] - yh) + (sm.col[st][4][k] - yl);
+                const float dz = (sm.col[st][2][k] - zh) + (sm.col[st][5][k] - zl);
+                const float r2 = fmaf(dz, dz, fmaf(dy, dy, fmaf(dx, dx, eps2)));
+                float ri = rsqrtf(r2);
+                ri = ri * fmaf(-0.5f * r2, ri * ri, 1.5f);  // one Newton step
+                const float w = sm.col[st][6][k] * (ri * ri * ri);
+                kahan_add(sx, cx, w * dx);
+                kahan_add(sy, cy, w * dy);
+                kahan_add(sz, cz, w * dz);
+            }
+        }
+        __syncthreads();
+    }
+    if (!ok) {
+        raise_err(ctr, DERR_TMA_TIMEOUT);
+        mbar_wait(&sm.bar[0], 0, TMA_WAIT_CYCLES);
+        mbar_wait(&sm.bar[1], 0, TMA_WAIT_CYCLES);
+        return;
+    }
+    if (!iv) return;
+    const double ax = (double)sx - (double)cx, ay = (double)sy - (double)cy, az = (double)sz - (double)cz;
+    if (nchunk == 1) {
+        L.vx[i] += Gh * ax;
+        L.vy[i] += Gh * ay;
+        L.vz[i] += Gh * az;
+    } else {
+        // partial[(chunk * 3 + c) * cap + i]
+        const size_t cap = (size_t)F.cap;
+        partial[((size_t)ch * 3 + 0) * cap + i] = ax;
+        partial[((size_t)ch * 3 + 1) * cap + i] = ay;
+        partial[((size_t)ch * 3 + 2) * cap + i] = az;
+    }
+}
+
+// sum the chunk partials of multi-chunk sets in chunk order (FP64), v += G h a
+__global__ void k_kick_reduce(Level L, FFView F, double Gh, const double *partial)
+{
+    const int k = blockIdx.x * blockDim.x + threadIdx.x;
+    if (k >= L.total || L.sidx[k] < 0) return;
+    const int n = L.set_n[L.sidx[k]];
+    const int nchunk = ((n + MK_T - 1) / MK_T + MK_CHUNK_TILES - 1) / MK_CHUNK_TILES;
+    if (nchunk == 1) return;
+    const size_t cap = (size_t)F.cap;
+    double ax = 0.0, ay = 0.0, az = 0.0;
+    for (int c = 0; c < nchunk; ++c) {
+        ax += partial[((size_t)c * 3 + 0) * cap + k];
+        ay += partial[((size_t)c * 3 + 1) * cap + k];
+        az += partial[((size_t)c * 3 + 2) * cap + k];
+    }
+    L.vx[k] += Gh * ax;
+    L.vy[k] += Gh * ay;
+    L.vz[k] += Gh * az;
+}
+
+int mixed_kick_blocks(int n)
+{
+    const int ntile = (n + MK_T - 1) / MK_T;
+    return ntile * ((ntile + MK_CHUNK_TILES - 1) / MK_CHUNK_TILES);
+}
+
+int mixed_kick_chunks(int n)
+{
+    const int ntile = (n + MK_T - 1) / MK_T;
+    return (ntile + MK_CHUNK_TILES - 1) / MK_CHUNK_TILES;
+}
+
+void launch_kick_mixed(const Level &L, const FFView &F, const int32_t *label, const int32_t *koff, int nblocks,
+                       bool multi_chunk, double G, double eps2, double h, DevCounters *ctr, double *partial,
+                       cudaStream_t s)
+{
+    if (nblocks <= 0) return;
+    k_kick_mixed<<<nblocks, MK_T, 0, s>>>(L, F, label, koff, (float)eps2, G * h, ctr, partial);
+    CC_COUNT_LAUNCH(1);
+    if (multi_chunk) {
+        k_kick_reduce<<<(L.total + 255) / 256, 256, 0, s>>>(L, F, G * h, partial);
+        CC_COUNT_LAUNCH(1);
+    }
+}
+
+}  // namespace cc

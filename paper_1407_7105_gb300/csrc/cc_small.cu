@@ -1,0 +1,319 @@
+// cc_small.cu -- persistent small-component integrator: one warp evolves a
+// whole connected component of at most 32 bodies through the recursion of
+// evolve_cc (arXiv:1407.7105 Sec. 2.3, CC pseudocode figure) on-chip.
+//
+// Lane l holds body l of the component (members are in ascending particle
+// id, so lane order is id order).  A set at recursion level k is a lane mask;
+// all sets of the same level are advanced in lockstep (they are independent
+// closed Hamiltonians, Sec. 2.2), level by level with an explicit stack:
+//   phase 0: split the lane's set at h_k: tau(i,j) < h_k over the set (the
+//            exact FP64 predicate, or the certified FP32 decision with FP64
+//            fallback), components by mask closure; push level k+1 with
+//            the non-trivial components (first half)
+//   phase 1: Kepler half step of two-body components (CC_KEPLER), the DKD
+//            of level k, the second Kepler half step; push level k+1 again
+//   phase 2: pop
+// Warps take components from a queue (largest first) until it is empty.
+// The arithmetic of every step is the same as the level kernels', so the
+// FP64 form stays bit-identical to the oracle.
+#include "cc_device.cuh"
+
+namespace cc {
+
+constexpr int K8_WARPS = 4;
+constexpr int K8_MAXD = 64;
+constexpr unsigned FULL = 0xffffffffu;
+
+struct __align__(16) K8Warp {
+    double d[7][32];  // x y z vx vy vz m
+    float f[13][32];  // hi/lo of x y z vx vy vz, m (FP32 decision)
+};
+
+__device__ __forceinline__ void k8_publish(K8Warp &S, int lane, const double st[7], bool ff)
+{
+    __syncwarp();  // every lane is done reading the previous contents
+#pragma unroll
+    for (int c = 0; c < 7; ++c) S.d[c][lane] = st[c];
+    if (ff) {
+#pragma unroll
+        for (int c = 0; c < 6; ++c) {
+            const float hi = __double2float_rn(st[c]);
+            S.f[c][lane] = hi;
+            S.f[6 + c][lane] = __double2float_rn(st[c] - (double)hi);
+        }
+        S.f[12][lane] = __double2float_rn(st[6]);
+    }
+    __syncwarp();
+}
+
+__global__ void __launch_bounds__(K8_WARPS * 32) k_small(Level L, const int32_t *members, const int32_t *comp_start,
+                                                          const int32_t *comp_size, const int32_t *slist, int ns,
+                                                          SmallParams SP, DevCounters *ctr, int *queue,
+                                                          int32_t *near_ij, double *near_tau, long long near_cap)
+{
+    __shared__ K8Warp sw[K8_WARPS];
+    const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    K8Warp &S = sw[w];
+    const uint32_t me = 1u << lane;
+    uint32_t mk[K8_MAXD], cmk[K8_MAXD];
+    unsigned char ph[K8_MAXD];
+    unsigned long long c_tau = 0, c_kick = 0, c_drift = 0, c_split = 0, c_comp = 0, c_kep = 0, c_fp64 = 0;
+    int maxd = 0;
+    const bool mixed = SP.precision == CC_PREC_MIXED;
+    TauParams P;
+    P.G = SP.G; P.eps2 = SP.eps2; P.eta = SP.eta; P.eta_in = SP.eta_in; P.eta_outside = SP.eta_outside;
+    P.near_tol = SP.near_tol;
+    MixedTauParams Q;
+    Q.eta = (float)SP.eta_in; Q.eps2 = (float)SP.eps2; Q.G = (float)SP.G;
+    for (;;) {
+        int q = 0;
+        if (lane == 0) q = atomicAdd(queue, 1);
+        q = __shfl_sync(FULL, q, 0);
+        if (q >= ns) break;
+        const int c = slist[q], n = comp_size[c], base = comp_start[c];
+        const bool act = lane < n;
+        const int p = act ? members[base + lane] : -1;
+        double st[7] = {0, 0, 0, 0, 0, 0, 0};
+        if (act) {
+            st[0] = L.x[p]; st[1] = L.y[p]; st[2] = L.z[p];
+            st[3] = L.vx[p]; st[4] = L.vy[p]; st[5] = L.vz[p];
+            st[6] = L.m[p];
+        }
+        const uint32_t all = (n >= 32) ? FULL : ((1u << n) - 1u);
+        int k = 0;
+        mk[0] = act ? all : 0u;
+        ph[0] = 0;
+        bool bad = false;
+        if (SP.depth0 > maxd) maxd = SP.depth0;
+        while (k >= 0 && !bad) {
+            const double h = ldexp(SP.h0, -k);
+            const uint32_t mine = mk[k];
+            if (ph[k] == 0) {
+                // ---------------- split at h: tau(i,j) < h inside the lane's set
+                k8_publish(S, lane, st, mixed);
+                float X = 0.f, V = 0.f;
+                if (mixed) {
+                    X = fmaxf(fabsf(S.f[0][lane]), fmaxf(fabsf(S.f[1][lane]), fabsf(S.f[2][lane])));
+                    V = fmaxf(fabsf(S.f[3][lane]), fmaxf(fabsf(S.f[4][lane]), fabsf(S.f[5][lane])));
+#pragma unroll
+                    for (int o = 16; o > 0; o >>= 1) {
+                        X = fmaxf(X, __shfl_xor_sync(FULL, X, o));
+                        V = fmaxf(V, __shfl_xor_sync(FULL, V, o));
+                    }
+                }
+                P.h = h;
+                Q.h = (float)(SP.eta_outside ? h / SP.eta : h);
+                uint32_t adj = 0;
+                if (mine) {
+                    for (int j = 0; j < n; ++j) {
+                        if (j == lane || !((mine >> j) & 1u)) continue;
+                        int dec = -1;
+                        if (mixed) {
+                            dec = tau_decide_fp32((S.f[0][j] - S.f[0][lane]) + (S.f[6][j] - S.f[6][lane]),
+                                                  (S.f[1][j] - S.f[1][lane]) + (S.f[7][j] - S.f[7][lane]),
+                                                  (S.f[2][j] - S.f[2][lane]) + (S.f[8][j] - S.f[8][lane]),
+                                                  (S.f[3][j] - S.f[3][lane]) + (S.f[9][j] - S.f[9][lane]),
+                                                  (S.f[4][j] - S.f[4][lane]) + (S.f[10][j] - S.f[10][lane]),
+                                                  (S.f[5][j] - S.f[5][lane]) + (S.f[11][j] - S.f[11][lane]),
+                                                  Q.G * (S.f[12][lane] + S.f[12][j]), X, V, Q);
+                        }
+                        if (dec < 0) {
+                            const int lo = lane < j ? lane : j, hi = lane < j ? j : lane;
+                            const double tau = tau_fp64(
+                                __dsub_rn(S.d[0][lo], S.d[0][hi]), __dsub_rn(S.d[1][lo], S.d[1][hi]),
+                                __dsub_rn(S.d[2][lo], S.d[2][hi]), __dsub_rn(S.d[3][lo], S.d[3][hi]),
+                                __dsub_rn(S.d[4][lo], S.d[4][hi]), __dsub_rn(S.d[5][lo], S.d[5][hi]),
+                                S.d[6][lo], S.d[6][hi], P);
+                            if (lane < j) {
+                                ++c_fp64;
+                                if (fabs(tau - h) < P.near_tol * h) {
+                                    const unsigned long long z = atomicAdd(&ctr->near_pairs, 1ull);
+                                    if ((long long)z < near_cap) {
+                                        const int ga = L.gid[members[base + lane]], gb = L.gid[members[base + j]];
+                                        near_ij[2 * z] = ga < gb ? ga : gb;
+                                        near_ij[2 * z + 1] = ga < gb ? gb : ga;
+                                        near_tau[z] = tau;
+                                    }
+                                }
+                            }
+                            dec = tau < h ? 1 : 0;
+                        }
+                        if (dec) adj |= 1u << j;
+                    }
+                }
+                // components: closure of the adjacency by mask doubling
+                uint32_t cm = mine ? (adj | me) : 0u;
+                for (int it = 0; it < 6; ++it) {
+                    uint32_t nx = cm;
+                    for (int j = 0; j < n; ++j) {
+                        const uint32_t cj = __shfl_sync(FULL, cm, j);
+                        if ((cm >> j) & 1u) nx |= cj;
+                    }
+                    const bool same = __all_sync(FULL, nx == cm);
+                    cm = nx;
+                    if (same) break;
+                }
+                cmk[k] = cm;
+                const int csz = __popc(cm);
+                if (mine && lane == __ffs(mine) - 1) {
+                    const unsigned long long ms = __popc(mine);
+                    ++c_split;
+                    c_tau += ms * (ms - 1) / 2;
+                }
+                if (csz >= 2 && lane == __ffs(cm) - 1) {
+                    ++c_comp;
+                    if (SP.kepler && csz == 2) c_kep += 2;
+                }
+                ph[k] = 1;
+                const bool sub = csz >= 2 && !(SP.kepler && csz == 2);
+                if (__any_sync(FULL, sub)) {
+                    if (SP.depth0 + k + 1 > SP.max_depth || k + 1 >= K8_MAXD) {
+                        bad = true;
+                        raise_err(ctr, DERR_DEPTH);
+                        break;
+                    }
+                    mk[k + 1] = sub ? cm : 0u;
+                    ph[k + 1] = 0;
+                    ++k;
+                    if (SP.depth0 + k > maxd) maxd = SP.depth0 + k;
+                    continue;
+                }
+            }
+            const uint32_t cm = cmk[k];
+            const int csz = __popc(cm);
+            const bool sub = csz >= 2 && !(SP.kepler && csz == 2);
+            if (ph[k] == 1) {
+                const bool kep = mine && SP.kepler && csz == 2;
+                for (int half = 0; half < 2; ++half) {
+                    if (half == 1) {
+                        // ------------- D_{h/2,T_R} K_{h,V} D_{h/2,T_R} on the lane's set
+                        const bool single = mine && cm == me;
+                        const double hd = 0.5 * h;
+                        if (single) {
+                            st[0] = __dadd_rn(st[0], __dmul_rn(hd, st[3]));
+                            st[1] = __dadd_rn(st[1], __dmul_rn(hd, st[4]));
+                            st[2] = __dadd_rn(st[2], __dmul_rn(hd, st[5]));
+                            c_drift += 2;
+                        }
+                        const bool fp64_kick = !mixed || h < SP.h_fp64;
+                        k8_publish(S, lane, st, !fp64_kick);
+                        if (mine) {
+                            const uint32_t others = mine & ~cm;
+                            c_kick += __popc(others & ~((me << 1) - 1u));
+                            if (fp64_kick) {
+                                double ax = 0.0, ay = 0.0, az = 0.0;
+                                for (int j = 0; j < n; ++j) {
+                                    if (!((others >> j) & 1u)) continue;
+                                    const double dx0 = __dsub_rn(S.d[0][j], st[0]);
+                                    const double dx1 = __dsub_rn(S.d[1][j], st[1]);
+                                    const double dx2 = __dsub_rn(S.d[2][j], st[2]);
+                                    const double r2 = __dadd_rn(__dadd_rn(__dadd_rn(__dmul_rn(dx0, dx0),
+                                                                                    __dmul_rn(dx1, dx1)),
+                                                                          __dmul_rn(dx2, dx2)),
+                                                                SP.eps2);
+                                    const double rinv3 = __ddiv_rn(1.0, __dmul_rn(r2, __dsqrt_rn(r2)));
+                                    const double ww = __dmul_rn(__dmul_rn(SP.G, S.d[6][j]), rinv3);
+                                    ax = __dadd_rn(ax, __dmul_rn(ww, dx0));
+                                    ay = __dadd_rn(ay, __dmul_rn(ww, dx1));
+                                    az = __dadd_rn(az, __dmul_rn(ww, dx2));
+                                }
+                                st[3] = __dadd_rn(st[3], __dmul_rn(h, ax));
+                                st[4] = __dadd_rn(st[4], __dmul_rn(h, ay));
+                                st[5] = __dadd_rn(st[5], __dmul_rn(h, az));
+                            } else {
+                                // FP32 pair forces from float-float differences
+                                const float xh = S.f[0][lane], yh = S.f[1][lane], zh = S.f[2][lane];
+                                const float xl = S.f[6][lane], yl = S.f[7][lane], zl = S.f[8][lane];
+                                float sx = 0.f, sy = 0.f, sz = 0.f, cx = 0.f, cy = 0.f, cz = 0.f;
+                                const float e2 = (float)SP.eps2;
+                                for (int j = 0; j < n; ++j) {
+                                    if (!((others >> j) & 1u)) continue;
+                                    const float dx = (S.f[0][j] - xh) + (S.f[6][j] - xl);
+                                    const float dy = (S.f[1][j] - yh) + (S.f[7][j] - yl);
+                                    const float dz = (S.f[2][j] - zh) + (S.f[8][j] - zl);
+                                    const float r2 = fmaf(dz, dz, fmaf(dy, dy, fmaf(dx, dx, e2)));
+                                    float ri = rsqrtf(r2);
+                                    ri = ri * fmaf(-0.5f * r2, ri * ri, 1.5f);
+                                    const float ww = S.f[12][j] * (ri * ri * ri);
+                                    kahan_add(sx, cx, ww * dx);
+                                    kahan_add(sy, cy, ww * dy);
+                                    kahan_add(sz, cz, ww * dz);
+                                }
+                                const double gh = SP.G * h;
+                                st[3] += gh * ((double)sx - (double)cx);
+                                st[4] += gh * ((double)sy - (double)cy);
+                                st[5] += gh * ((double)sz - (double)cz);
+                            }
+                        }
+                        __syncwarp();
+                        if (single) {
+                            st[0] = __dadd_rn(st[0], __dmul_rn(hd, st[3]));
+                            st[1] = __dadd_rn(st[1], __dmul_rn(hd, st[4]));
+                            st[2] = __dadd_rn(st[2], __dmul_rn(hd, st[5]));
+                        }
+                    }
+                    // two-body components: the Kepler flow over h/2
+                    k8_publish(S, lane, st, false);
+                    if (kep) {
+                        const int other = __ffs(cm & ~me) - 1;
+                        const int a = lane < other ? lane : other, b = lane < other ? other : lane;
+                        double xa[3] = {S.d[0][a], S.d[1][a], S.d[2][a]}, xb[3] = {S.d[0][b], S.d[1][b], S.d[2][b]};
+                        double va[3] = {S.d[3][a], S.d[4][a], S.d[5][a]}, vb[3] = {S.d[3][b], S.d[4][b], S.d[5][b]};
+                        if (!kepler_pair(S.d[6][a], S.d[6][b], xa, xb, va, vb, SP.G, 0.5 * h)) {
+                            raise_err(ctr, DERR_KEPLER);
+                        } else if (lane == a) {
+                            st[0] = xa[0]; st[1] = xa[1]; st[2] = xa[2]; st[3] = va[0]; st[4] = va[1]; st[5] = va[2];
+                        } else {
+                            st[0] = xb[0]; st[1] = xb[1]; st[2] = xb[2]; st[3] = vb[0]; st[4] = vb[1]; st[5] = vb[2];
+                        }
+                    }
+                    __syncwarp();
+                }
+                ph[k] = 2;
+                if (__any_sync(FULL, sub)) {
+                    mk[k + 1] = sub ? cm : 0u;
+                    ph[k + 1] = 0;
+                    ++k;
+                    continue;
+                }
+            }
+            --k;
+        }
+        if (act) {
+            L.x[p] = st[0]; L.y[p] = st[1]; L.z[p] = st[2];
+            L.vx[p] = st[3]; L.vy[p] = st[4]; L.vz[p] = st[5];
+        }
+        __syncwarp();
+    }
+    // per-lane counters -> one atomic per warp and counter
+    unsigned long long v[7] = {c_tau, c_kick, c_drift, c_split, c_comp, c_kep, c_fp64};
+#pragma unroll
+    for (int i = 0; i < 7; ++i)
+        for (int o = 16; o > 0; o >>= 1) v[i] += __shfl_down_sync(FULL, v[i], o);
+    for (int o = 16; o > 0; o >>= 1) maxd = max(maxd, __shfl_down_sync(FULL, maxd, o));
+    if (lane == 0) {
+        if (v[0]) atomicAdd(&ctr->small_tau_pairs, v[0]);
+        if (v[1]) atomicAdd(&ctr->small_kick_pairs, v[1]);
+        if (v[2]) atomicAdd(&ctr->small_drifts, v[2]);
+        if (v[3]) atomicAdd(&ctr->small_splits, v[3]);
+        if (v[4]) atomicAdd(&ctr->small_components, v[4]);
+        if (v[5]) atomicAdd(&ctr->small_kepler, v[5]);
+        if (v[6]) atomicAdd(&ctr->tau_fp64, v[6]);
+        atomicMax(&ctr->max_depth_seen, maxd);
+    }
+}
+
+void launch_small(const Level &L, const int32_t *members, const int32_t *comp_start, const int32_t *comp_size,
+                  const int32_t *slist, int ns, const SmallParams &SP, DevCounters *ctr, int *queue,
+                  int32_t *near_ij, double *near_tau, long long near_cap, int nsm, cudaStream_t s)
+{
+    if (ns <= 0) return;
+    cudaMemsetAsync(queue, 0, sizeof(int), s);
+    const int want = (ns + K8_WARPS - 1) / K8_WARPS;
+    const int grid = want < nsm * 8 ? want : nsm * 8;
+    k_small<<<grid, K8_WARPS * 32, 0, s>>>(L, members, comp_start, comp_size, slist, ns, SP, ctr, queue, near_ij,
+                                           near_tau, near_cap);
+    CC_COUNT_LAUNCH(1);
+}
+
+}  // namespace cc

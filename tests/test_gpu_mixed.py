@@ -1,0 +1,100 @@
+"""GPU checks of the mixed-precision form (CC_PREC_MIXED).
+
+The certified FP32 tau pre-filter must leave the edge predicate exactly
+the FP64 one: labels equal the oracle's bit for bit, including thresholds
+placed within 1e-7 .. 1e-3 (relative) of individual pair time steps.  The
+FP32 kick is judged by its error against the FP64 kick on the same state.
+"""
+import numpy as np
+import pytest
+
+from oracle import oracle as O
+from paper_1407_7105_gb300 import ics
+
+pytestmark = pytest.mark.gpu
+
+
+def _mixed(cclib, m, x, v, **kw):
+    return cclib.Context(m, x, v, precision=cclib.PREC_MIXED, **kw)
+
+
+@pytest.mark.parametrize("n", [1000, 16384])
+def test_mixed_components_equal_fp64(cclib, plummer_ic, n):
+    m, x, v = plummer_ic(n)
+    s = O.State(m, x, v)
+    c = _mixed(cclib, m, x, v)
+    for h in (1 / 64, 1 / 256, 1 / 2048):
+        if n > 2000 and h != 1 / 256:
+            continue
+        lab, k = c.components(h)
+        olab, ok = O.components(s, O.params(), h)
+        assert k == ok and np.array_equal(lab, olab), h
+    st = c.stats()
+    assert st["tau_fp64"] < 1e-3 * st["tau_pairs"] + 100, st
+    c.close()
+
+
+@pytest.mark.parametrize("rel", [1e-7, -1e-7, 1e-5, -1e-5, 1e-3, -1e-3, 0.0])
+def test_mixed_threshold_at_pair_tau(cclib, plummer_ic, rel):
+    """Thresholds a hair above / below / at individual tau(i,j): the
+    pre-filter must hand every such pair to the FP64 predicate."""
+    m, x, v = plummer_ic(300, seed=9)
+    s = O.State(m, x, v)
+    p = O.params()
+    T = O.tau_matrix(s, p)
+    vals = np.sort(T[np.triu_indices(300, 1)])
+    c = _mixed(cclib, m, x, v)
+    for q in (0.001, 0.01, 0.1, 0.5):
+        h = float(vals[int(q * (vals.size - 1))]) * (1.0 + rel)
+        lab, k = c.components(h)
+        olab, ok = O.components(s, p, h)
+        assert k == ok and np.array_equal(lab, olab), (q, rel)
+    c.close()
+
+
+def test_mixed_kick_error(cclib, plummer_ic):
+    m, x, v = plummer_ic(4096, seed=3)
+    rng = np.random.default_rng(1)
+    labels = np.arange(4096, dtype=np.int32)
+    labels[rng.choice(4096, 600, replace=False)] = 7  # one 600-member group
+    h = 1 / 256
+    c = _mixed(cclib, m, x, v)
+    c.kick(labels, h)
+    _, _, _, gv = c.get_state()
+    c.close()
+    s = O.State(m, x, v)
+    O.kick(s, O.params(), np.arange(4096), labels, h)
+    da_ref = (s.v3 - v) / h
+    da_gpu = (gv - v) / h
+    err = np.linalg.norm(da_gpu - da_ref, axis=0) / np.linalg.norm(da_ref, axis=0)
+    assert np.median(err) < 2e-7 and err.max() < 1e-5, (np.median(err), err.max())
+
+
+def test_mixed_energy_matches_fp64(cclib, plummer_ic):
+    m, x, v = plummer_ic(1024, seed=5)
+    out = {}
+    for name, prec in (("fp64", cclib.PREC_FP64), ("mixed", cclib.PREC_MIXED)):
+        c = cclib.Context(m, x, v, dt=1 / 128, precision=prec)
+        E0, P0, _ = c.energy()
+        c.evolve(16 / 128)
+        E1, P1, _ = c.energy()
+        out[name] = ((E1 - E0) / abs(E0), np.abs(P1 - P0).max())
+        c.close()
+    assert abs(out["mixed"][0]) < 1e-6 and abs(out["fp64"][0]) < 1e-6, out
+    assert abs(out["mixed"][0] - out["fp64"][0]) < 1e-7, out
+    # FP32 pair forces are not exactly antisymmetric: momentum is kept to
+    # the FP32 rounding of the forces, not to FP64 machine precision
+    assert out["fp64"][1] < 1e-15 and out["mixed"][1] < 1e-10, out
+
+
+def test_mixed_one_step_close_to_oracle(cclib, plummer_ic):
+    m, x, v = plummer_ic(16384)
+    c = _mixed(cclib, m, x, v, dt=1 / 256)
+    c.evolve(1 / 256)
+    _, _, gx, gv = c.get_state()
+    c.close()
+    s = O.State(m, x, v)
+    O.evolve(s, O.params(dt=1 / 256), 1)
+    dv = np.linalg.norm(gv - s.v3, axis=0) / np.linalg.norm(s.v3, axis=0)
+    dx = np.linalg.norm(gx - s.x3, axis=0) / np.linalg.norm(s.x3, axis=0)
+    assert np.median(dv) < 1e-8 and np.median(dx) < 1e-9, (np.median(dv), np.median(dx))
