@@ -320,6 +320,39 @@ def run_gpu(args, rank, world):
     return 0
 
 
+def run_accuracy(args):
+    """The accuracy gate of the metric: both forms integrate the workload to
+    t = 1 (256 outer steps) from the same state; |dE/E|, momentum drift and
+    time to solution are reported per form (JSON lines, not the bench line)."""
+    import torch
+
+    from paper_1407_7105_gb300 import build, cc, ics
+    build.build()
+    m, x, v = ics.plummer(args.n, seed=args.seed)
+    dev = torch.device("cuda", 0)
+    dm, dx, dv = (torch.tensor(a, device=dev) for a in (m, x, v))
+    steps = int(round(args.t_end / DT))
+    for form, hf in (("mixed", 0.0), ("mixed", args.h_fp64 or 1.0 / 16), ("fp64", 0.0)):
+        prec = cc.PREC_MIXED if form == "mixed" else cc.PREC_FP64
+        ctx = cc.Context(dm, dx, dv, dt=DT, eta=ETA, precision=prec, h_fp64=hf * DT)
+        E0, P0, L0 = ctx.energy()
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        ctx.evolve(steps * DT)
+        torch.cuda.synchronize()
+        sec = time.perf_counter() - t0
+        E1, P1, L1 = ctx.energy()
+        st = ctx.stats()
+        ctx.close()
+        inter = st["tau_pairs"] + st["kick_pairs"]
+        print(json.dumps({"accuracy": True, "form": form, "h_fp64": f"{hf}*dt", "t_end": steps * DT,
+                          "steps": steps, "seconds": sec, "interactions": inter, "interactions_per_s": inter / sec,
+                          "dE_over_E": (E1 - E0) / abs(E0), "dP": float(np.abs(P1 - P0).max()),
+                          "dL": float(np.abs(L1 - L0).max()), "max_depth": st["max_depth_seen"],
+                          "tau_fp64_fraction": st["tau_fp64"] / max(1, st["tau_pairs"])}), flush=True)
+    return 0
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -330,6 +363,8 @@ def main():
     ap.add_argument("--h-fp64", type=float, default=0.0,
                     help="mixed form: sets split at h < h_fp64*dt take FP64 forces")
     ap.add_argument("--single-form", action="store_true", help="skip timing the other form")
+    ap.add_argument("--accuracy", action="store_true", help="integrate both forms to --t-end and report dE/E")
+    ap.add_argument("--t-end", type=float, default=1.0)
     ap.add_argument("--seed", type=int, default=1)
     ap.add_argument("--n", type=int, default=N_BODY, help="bodies (smaller cases are for profiling only)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
@@ -338,6 +373,8 @@ def main():
     rank = int(os.environ.get("RANK", "0"))
     if args.impl == "reference":
         return run_reference(args, rank, world)
+    if args.accuracy:
+        return run_accuracy(args)
     if world > 1:
         import torch.distributed as dist
         dist.init_process_group("nccl")

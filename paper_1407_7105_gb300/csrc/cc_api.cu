@@ -53,6 +53,8 @@ struct LevelAlloc {
     std::vector<int32_t> h_size, h_start;
     std::vector<int32_t> h_set_n;  // set sizes of this level (host copy)
     int32_t *h_info = nullptr;     // pinned: ncomp, sizes, starts (one D2H per split)
+    int32_t *h_sets = nullptr;     // pinned staging of the set arrays (one H2D)
+    int32_t *h_lists = nullptr;    // pinned staging of the component lists (one H2D)
     int info_cap = 0;
     cudaEvent_t ev_ready = nullptr, ev_small = nullptr;  // side-stream joins
 };
@@ -199,6 +201,9 @@ static int align_up(int v, int a) { return (v + a - 1) / a * a; }
 static void free_level(LevelAlloc &a)
 {
     if (a.h_info) cudaFreeHost(a.h_info);
+    if (a.h_sets) cudaFreeHost(a.h_sets);
+    if (a.h_lists) cudaFreeHost(a.h_lists);
+    a.h_sets = a.h_lists = nullptr;
     if (a.ev_ready) cudaEventDestroy(a.ev_ready);
     if (a.ev_small) cudaEventDestroy(a.ev_small);
     a.h_info = nullptr;
@@ -222,7 +227,7 @@ static int ensure_level(cc_ctx *c, LevelAlloc &a, int need, int nsets)
         const long long worst = std::min<long long>(2 * (long long)c->n + 64, 0x3fffffff);
         int cap = align_up(std::max<int>(need, (int)std::max<long long>(64, worst)), 64);
         size_t nd = (size_t)cap + PAD_TAIL;
-        size_t bytes = nd * 8 * 7 + nd * 4 * 10 + nd * 4 * 13 + 4096;
+        size_t bytes = nd * 8 * 7 + nd * 4 * 10 + nd * 64 + 4096;
         if (cudaMalloc(&a.block, bytes) != cudaSuccess) {
             cudaGetLastError();
             return fail(c, CC_E_NOMEM, "device allocation failed (level buffer)");
@@ -234,9 +239,8 @@ static int ensure_level(cc_ctx *c, LevelAlloc &a, int need, int nsets)
         int32_t **ip[10] = {&a.L.gid, &a.L.sidx, &a.L.src, &a.L.parent, &a.L.cnt,
                             &a.root, &a.members, &a.comp_start, &a.comp_size, &a.d_ncomp};
         for (int k = 0; k < 10; ++k) { *ip[k] = (int32_t *)q; q += nd * 4; }
-        float **fp[13] = {&a.F.ph[0], &a.F.ph[1], &a.F.ph[2], &a.F.pl[0], &a.F.pl[1], &a.F.pl[2],
-                          &a.F.vh[0], &a.F.vh[1], &a.F.vh[2], &a.F.vl[0], &a.F.vl[1], &a.F.vl[2], &a.F.m};
-        for (int k = 0; k < 13; ++k) { *fp[k] = (float *)q; q += nd * 4; }
+        a.F.pq = (float4 *)q; q += nd * 32;
+        a.F.vq = (float4 *)q; q += nd * 32;
         a.F.maxes = (float *)q;
         a.F.cap = (int)nd;
         a.cap = cap;
@@ -247,6 +251,12 @@ static int ensure_level(cc_ctx *c, LevelAlloc &a, int need, int nsets)
         if (cudaMalloc(&a.listblock, (size_t)a.list_cap * 4 * 5 + 1024) != cudaSuccess) {
             cudaGetLastError();
             return fail(c, CC_E_NOMEM, "device allocation failed (component lists)");
+        }
+        if (a.h_lists) cudaFreeHost(a.h_lists);
+        a.h_lists = nullptr;
+        if (cudaMallocHost(&a.h_lists, (size_t)a.list_cap * 4 * 5 + 1024) != cudaSuccess) {
+            cudaGetLastError();
+            return fail(c, CC_E_NOMEM, "pinned host allocation failed (component lists)");
         }
         int32_t *lq = (int32_t *)a.listblock;
         a.klist = lq; lq += a.list_cap;
@@ -262,6 +272,12 @@ static int ensure_level(cc_ctx *c, LevelAlloc &a, int need, int nsets)
         if (cudaMalloc(&a.setblock, (size_t)sc * 4 * 5) != cudaSuccess) {
             cudaGetLastError();
             return fail(c, CC_E_NOMEM, "device allocation failed (set arrays)");
+        }
+        if (a.h_sets) cudaFreeHost(a.h_sets);
+        a.h_sets = nullptr;
+        if (cudaMallocHost(&a.h_sets, (size_t)sc * 4 * 5) != cudaSuccess) {
+            cudaGetLastError();
+            return fail(c, CC_E_NOMEM, "pinned host allocation failed (set arrays)");
         }
         int32_t *sq = (int32_t *)a.setblock;
         a.L.set_start = sq; sq += sc;
@@ -329,11 +345,16 @@ static int upload_layout(cc_ctx *c, LevelAlloc &a, const SetLayout &S)
 {
     const int ns = (int)S.n.size();
     CC_TRY(ensure_level(c, a, std::max(S.total, 1), ns));
-    CC_CUDA(c, cudaMemcpyAsync(a.L.set_start, S.start.data(), ns * 4, cudaMemcpyHostToDevice, c->stream));
-    CC_CUDA(c, cudaMemcpyAsync(a.L.set_n, S.n.data(), ns * 4, cudaMemcpyHostToDevice, c->stream));
-    CC_CUDA(c, cudaMemcpyAsync(a.L.tile_off, S.toff.data(), (ns + 1) * 4, cudaMemcpyHostToDevice, c->stream));
-    CC_CUDA(c, cudaMemcpyAsync(a.L.itile_off, S.ioff.data(), (ns + 1) * 4, cudaMemcpyHostToDevice, c->stream));
-    CC_CUDA(c, cudaMemcpyAsync(a.L.koff, S.koff.data(), (ns + 1) * 4, cudaMemcpyHostToDevice, c->stream));
+    // one pinned staging block laid out like the device set arrays (stride
+    // set_cap), copied in one asynchronous transfer
+    const int sc = a.set_cap;
+    std::memcpy(a.h_sets, S.start.data(), ns * 4);
+    std::memcpy(a.h_sets + sc, S.n.data(), ns * 4);
+    std::memcpy(a.h_sets + 2 * sc, S.toff.data(), (ns + 1) * 4);
+    std::memcpy(a.h_sets + 3 * sc, S.ioff.data(), (ns + 1) * 4);
+    std::memcpy(a.h_sets + 4 * sc, S.koff.data(), (ns + 1) * 4);
+    CC_CUDA(c, cudaMemcpyAsync(a.L.set_start, a.h_sets, (size_t)(4 * sc + ns + 1) * 4, cudaMemcpyHostToDevice,
+                               c->stream));
     a.kblocks = S.kblocks;
     a.kchunks_max = S.kchunks_max;
     a.L.total = S.total;
@@ -393,7 +414,7 @@ static int split_level(cc_ctx *c, LevelAlloc &a, double h, int &ncomp)
     if (ntiles > 0x7fffffff) return fail(c, CC_E_ARG, "set too large for the tile grid");
     int ev;
     if (c->p.precision == CC_PREC_MIXED) {
-        launch_prep_ff(a.L, a.F, true, s);
+        launch_prep_ff(a.L, a.F, c->p.G, true, s);
         ev = ev_begin(c, 0);
         launch_tau_mixed(a.L, a.F, (int)ntiles, P, c->d_ctr, c->d_near_ij, c->d_near_tau, c->near_cap, s);
     } else {
@@ -402,8 +423,7 @@ static int split_level(cc_ctx *c, LevelAlloc &a, double h, int &ncomp)
                         c->near_cap, s);
     }
     ev_end(c, ev);
-    launch_compress(a.L, a.root, s);
-    launch_segment(a.L, a.root, a.members, a.comp_start, a.comp_size, a.d_ncomp, c->seg_scratch, s);
+    launch_compress_segment(a.L, a.root, a.members, a.comp_start, a.comp_size, a.d_ncomp, c->seg_scratch, s);
     // one round trip: the count and, bounded by total/2, sizes and starts
     const int maxc = a.L.total / 2 + 1;
     if (maxc > a.info_cap) {
@@ -463,7 +483,7 @@ static int dkd(cc_ctx *c, LevelAlloc &a, double h)
             }
             c->kpart_sz = need;
         }
-        launch_prep_ff(a.L, a.F, false, s);
+        launch_prep_ff(a.L, a.F, c->p.G, false, s);
         const int ev = ev_begin(c, 1);
         launch_kick_mixed(a.L, a.F, a.root, a.L.koff, (int)a.kblocks, a.kchunks_max > 1, c->p.G,
                           c->p.eps * c->p.eps, h, c->d_ctr, c->d_kpart, s);
@@ -500,8 +520,11 @@ static int process(cc_ctx *c, int d, double h)
     // small components largest first: the longest sub-recursions start early
     std::stable_sort(sl.begin(), sl.end(), [&](int32_t u, int32_t v) { return a.h_size[u] > a.h_size[v]; });
     const int nk = (int)kl.size(), nl = (int)lsize.size(), ns = (int)sl.size();
-    if (nk) CC_CUDA(c, cudaMemcpyAsync(a.klist, kl.data(), nk * 4, cudaMemcpyHostToDevice, c->stream));
-    if (ns) CC_CUDA(c, cudaMemcpyAsync(a.slist, sl.data(), ns * 4, cudaMemcpyHostToDevice, c->stream));
+    // all component lists of this split travel in one pinned transfer
+    const int lc = a.list_cap;
+    int32_t *hl = a.h_lists;
+    if (nk) std::memcpy(hl, kl.data(), nk * 4);
+    if (ns) std::memcpy(hl + lc, sl.data(), ns * 4);
     SmallParams SP;
     SP.G = c->p.G;
     SP.eps2 = c->p.eps * c->p.eps;
@@ -524,10 +547,14 @@ static int process(cc_ctx *c, int d, double h)
         std::vector<int32_t> pref(nl + 1, 0);
         for (int q = 0; q < nl; ++q) pref[q + 1] = pref[q] + lsize[q];
         nmem = pref[nl];
-        CC_CUDA(c, cudaMemcpyAsync(a.lcomp_start, lstart.data(), nl * 4, cudaMemcpyHostToDevice, c->stream));
-        CC_CUDA(c, cudaMemcpyAsync(a.lpref, pref.data(), (nl + 1) * 4, cudaMemcpyHostToDevice, c->stream));
-        CC_CUDA(c, cudaMemcpyAsync(a.ldst, S.start.data(), nl * 4, cudaMemcpyHostToDevice, c->stream));
+        std::memcpy(hl + 2 * lc, lstart.data(), nl * 4);
+        std::memcpy(hl + 3 * lc, pref.data(), (nl + 1) * 4);
+        std::memcpy(hl + 4 * lc + 1, S.start.data(), nl * 4);
         CC_TRY(upload_layout(c, c->lv[d + 1], S));
+    }
+    if (nk || ns || nl) {
+        const size_t words = nl ? (size_t)(4 * lc + 1 + nl) : ns ? (size_t)(lc + ns) : (size_t)nk;
+        CC_CUDA(c, cudaMemcpyAsync(a.klist, hl, words * 4, cudaMemcpyHostToDevice, c->stream));
     }
     LevelAlloc &a2 = a;
     if (ns && !a2.ev_ready) {

@@ -27,49 +27,50 @@ namespace cc {
 constexpr float U32 = 5.9604645e-8f;  // 2^-24
 constexpr float SLACK = 2e-6f;
 
+// eta and eta/h in float (the decision compares T/h with D); c_x = 11 u^2 X
+// and c_v = 11 u^2 V carry the float-float rounding of the differences
 struct MixedTauParams {
-    float eta, h, eps2, G;
+    float eta, etah, eps2, G;
 };
 
 __device__ __forceinline__ int tau_decide_fp32(float dx0, float dx1, float dx2, float dv0, float dv1, float dv2,
-                                               float mu, float X, float V, const MixedTauParams &Q)
+                                               float mu, float c_x, float c_v, const MixedTauParams &Q)
 {
     // returns 1 = edge certain, 0 = no edge certain, -1 = undecided
+    const float A = 1.f + SLACK, B = 1.f - SLACK;
     const float r2 = fmaf(dx2, dx2, fmaf(dx1, dx1, fmaf(dx0, dx0, Q.eps2)));
     const float v2 = fmaf(dv2, dv2, fmaf(dv1, dv1, dv0 * dv0));
     const float rv = fmaf(dx2, dv2, fmaf(dx1, dv1, dx0 * dv0));
     const float rinv = rsqrtf(r2);
     const float r = r2 * rinv;
-    const float er = 2.05f * U32 + 11.f * U32 * U32 * X * rinv;
     const float s1 = rsqrtf(r * mu);
-    const float Tff = Q.eta * r2 * s1;
-    const float dTff = 1.5f * Q.eta * rv * s1;
-    // velocity-dependent pieces (v2 == 0: flyby time infinite)
-    const bool has_v = v2 > 0.f;
-    const float s2 = has_v ? rsqrtf(v2) : 0.f;
+    const float er = fmaf(c_x, rinv, 2.05f * U32);
+    const float s2 = v2 > 0.f ? rsqrtf(v2) : 0.f;
     const float vn = v2 * s2;  // |dv|
-    const float ev = has_v ? 2.05f * U32 + 11.f * U32 * U32 * V * s2 : 0.f;
-    const float drv = (er + ev + 4.f * U32) * r * vn;
-    // free-fall branch
-    const float ddff = 32.f * U32 * fabsf(dTff) + 1.5f * Q.eta * s1 * drv;
-    const float Dff = 1.f - 0.5f * fminf(dTff, 1.f);
-    const float dDff = 0.5f * ddff + 2.f * U32 * Dff;
-    const float eff = 40.f * U32 + 3.f * er;
-    const bool ff_yes = Tff * (1.f + eff) * (1.f + SLACK) < Q.h * (Dff - dDff);
-    const bool ff_no = Tff * (1.f - eff) * (1.f - SLACK) >= Q.h * (Dff + dDff);
+    const float ev = fmaf(c_v, s2, 2.05f * U32);
+    const float drv = (er + ev + 4.f * U32) * (r * vn);
+    // free fall: T/h = (eta/h) r2 s1, dT/dt = 1.5 eta rv s1
+    const float Tff = Q.etah * r2 * s1;
+    const float dTff = 1.5f * Q.eta * rv * s1;
+    const float Dff = fmaf(-0.5f, fminf(dTff, 1.f), 1.f);
+    const float dDff = fmaf(0.5f, fmaf(32.f * U32, fabsf(dTff), 1.5f * Q.eta * s1 * drv), 2.f * U32 * Dff);
+    const float eff = fmaf(3.f, er, 40.f * U32);
+    const bool ff_yes = Tff * fmaf(eff, A, A) < Dff - dDff;
+    const bool ff_no = Tff * fmaf(-eff, B, B) >= Dff + dDff;
     // an exactly zero (or unresolved) FP32 velocity difference may hide a
     // tiny nonzero FP64 one, whose flyby term can be small: only a certain
     // free-fall edge decides such a pair
-    if (!has_v || vn < 64.f * U32 * U32 * V) return ff_yes ? 1 : -1;
-    const float Tfb = Q.eta * r * s2;
-    const float g = 1.f + mu * s2 * s2 * rinv;
-    const float dTfb = Q.eta * rv * s2 * rinv * g;
-    const float ddfb = 80.f * U32 * fabsf(dTfb) + Q.eta * s2 * rinv * g * drv;
-    const float Dfb = 1.f - 0.5f * fminf(dTfb, 1.f);
-    const float dDfb = 0.5f * ddfb + 2.f * U32 * Dfb;
-    const float efb = 40.f * U32 + 3.f * er + 3.f * ev;
-    const bool fb_yes = Tfb * (1.f + efb) * (1.f + SLACK) < Q.h * (Dfb - dDfb);
-    const bool fb_no = Tfb * (1.f - efb) * (1.f - SLACK) >= Q.h * (Dfb + dDfb);
+    if (!(v2 > 0.f) || vn < 6.f * c_v) return ff_yes ? 1 : -1;
+    // flyby: T/h = (eta/h) r s2, dT/dt = eta rv s2 rinv (1 + mu s2^2 rinv)
+    const float g = fmaf(mu * s2 * s2, rinv, 1.f);
+    const float k = s2 * rinv * g;
+    const float Tfb = Q.etah * r * s2;
+    const float dTfb = Q.eta * rv * k;
+    const float Dfb = fmaf(-0.5f, fminf(dTfb, 1.f), 1.f);
+    const float dDfb = fmaf(0.5f, fmaf(80.f * U32, fabsf(dTfb), Q.eta * k * drv), 2.f * U32 * Dfb);
+    const float efb = fmaf(3.f, er + ev, 40.f * U32);
+    const bool fb_yes = Tfb * fmaf(efb, A, A) < Dfb - dDfb;
+    const bool fb_no = Tfb * fmaf(-efb, B, B) >= Dfb + dDfb;
     if (ff_yes || fb_yes) return 1;
     if (ff_no && fb_no) return 0;
     return -1;

@@ -305,6 +305,97 @@ void launch_segment(const Level &L, const int32_t *root, int32_t *members, int32
     CC_COUNT_LAUNCH(1);
 }
 
+// ------------------------------------------------------------ fused small path
+// For a batch of at most SEG1_MAX packed elements one CTA does what the
+// general path spreads over ~15 launches: union-find compression, sizes,
+// component heads and offsets (block scans), and the stable, ordered
+// scatter of members (one warp walks the indices in order; lanes with the
+// same root are ranked by warp match).
+constexpr int SEG1_T = 1024;
+constexpr int SEG1_MAX = 4096;
+
+__global__ void __launch_bounds__(SEG1_T) k_segment_small(Level L, int32_t *root_out, int32_t *members,
+                                                          int32_t *comp_start, int32_t *comp_size, int32_t *ncomp)
+{
+    __shared__ int s_root[SEG1_MAX];
+    __shared__ int s_cnt[SEG1_MAX];  // size by root; for heads then -(cursor + 1)
+    __shared__ int tmp[32];
+    const int n = L.total, tid = threadIdx.x;
+    for (int k = tid; k < n; k += SEG1_T) s_cnt[k] = 0;
+    __syncthreads();
+    for (int k = tid; k < n; k += SEG1_T) {
+        const bool valid = L.gid[k] >= 0;
+        const int r = valid ? uf_find(L.parent, k) : k;
+        s_root[k] = r;
+        root_out[k] = r;
+        if (valid) atomicAdd(&s_cnt[r], 1);
+    }
+    __syncthreads();
+    for (int k = tid; k < n; k += SEG1_T) L.cnt[k] = s_cnt[k];
+    // heads (roots of non-trivial components) in index order: component
+    // index and member offset by two block scans over 4 items per thread
+    int hc[4], hsz[4];
+    int sc = 0, ss = 0;
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+        const int k = 4 * tid + q;
+        const bool head = k < n && L.gid[k] >= 0 && s_root[k] == k && s_cnt[k] >= 2;
+        hc[q] = head ? 1 : 0;
+        hsz[q] = head ? s_cnt[k] : 0;
+        sc += hc[q];
+        ss += hsz[q];
+    }
+    __syncthreads();
+    int tot_c, tot_s;
+    int ec = block_exclusive_scan(sc, tmp, tot_c);
+    int es = block_exclusive_scan(ss, tmp, tot_s);
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+        const int k = 4 * tid + q;
+        if (hc[q]) {
+            comp_start[ec] = es;
+            comp_size[ec] = hsz[q];
+            s_cnt[k] = -(es + 1);
+        }
+        ec += hc[q];
+        es += hsz[q];
+    }
+    if (tid == 0) *ncomp = tot_c;
+    __syncthreads();
+    if (tid < 32) {
+        const unsigned lt = (1u << tid) - 1u;
+        for (int base = 0; base < n; base += 32) {
+            const int k = base + tid;
+            const int r = k < n ? s_root[k] : 0;
+            const bool mem = k < n && L.gid[k] >= 0 && s_cnt[r] < 0;
+            const int key = mem ? r : -1 - tid;
+            const unsigned peers = __match_any_sync(0xffffffffu, key);
+            const int rank = __popc(peers & lt);
+            const int lead = __ffs(peers) - 1;
+            int pos = 0;
+            if (mem && rank == 0) {
+                pos = -s_cnt[r] - 1;
+                s_cnt[r] -= __popc(peers);
+            }
+            pos = __shfl_sync(0xffffffffu, pos, lead) + rank;
+            if (mem) members[pos] = k;
+            __syncwarp();
+        }
+    }
+}
+
+void launch_compress_segment(const Level &L, int32_t *root, int32_t *members, int32_t *comp_start,
+                             int32_t *comp_size, int32_t *d_ncomp, void *scratch, cudaStream_t s)
+{
+    if (L.total > 0 && L.total <= SEG1_MAX) {
+        k_segment_small<<<1, SEG1_T, 0, s>>>(L, root, members, comp_start, comp_size, d_ncomp);
+        CC_COUNT_LAUNCH(1);
+        return;
+    }
+    launch_compress(L, root, s);
+    launch_segment(L, root, members, comp_start, comp_size, d_ncomp, scratch, s);
+}
+
 // ------------------------------------------------------------ movement
 __global__ void k_fill_pad(Level L)
 {

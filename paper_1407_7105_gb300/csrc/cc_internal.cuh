@@ -32,11 +32,14 @@ struct Level {
     int32_t nsets;
 };
 
-// float-float copy of a level (mixed-precision kernels): hi = fl32(x),
-// lo = fl32(x - hi) for positions and velocities, FP32 masses, and the
-// level's max |x|, max |v| (float bit patterns, for the error bounds)
+// float-float copy of a level (mixed-precision kernels), two float4 per
+// particle and quantity so that one j costs four 16-byte shared loads:
+//   pq[2k] = (x_hi, y_hi, z_hi, G m),  pq[2k+1] = (x_lo, y_lo, z_lo, 0)
+//   vq[2k] = (vx_hi, vy_hi, vz_hi, 0), vq[2k+1] = (vx_lo, vy_lo, vz_lo, 0)
+// with hi = fl32(x), lo = fl32(x - hi); maxes = max |x|, max |v| of the
+// level (float bit patterns, for the error bounds)
 struct FFView {
-    float *ph[3], *pl[3], *vh[3], *vl[3], *m;
+    float4 *pq, *vq;
     float *maxes;
     int cap;
 };
@@ -236,6 +239,8 @@ void launch_drift_labels(const Level &L, const int32_t *singleton, double dt, cu
 size_t seg_scratch_bytes(int cap);
 void launch_segment(const Level &L, const int32_t *root, int32_t *members, int32_t *comp_start,
                     int32_t *comp_size, int32_t *d_ncomp, void *scratch, cudaStream_t s);
+void launch_compress_segment(const Level &L, int32_t *root, int32_t *members, int32_t *comp_start,
+                             int32_t *comp_size, int32_t *d_ncomp, void *scratch, cudaStream_t s);
 void launch_gather(const Level &P, const Level &C, const int32_t *members, const int32_t *lcomp_start,
                    const int32_t *lpref, const int32_t *ldst, int nl, int nmem, int nsets_child, cudaStream_t s);
 void launch_scatter(const Level &P, const Level &C, cudaStream_t s);
@@ -258,7 +263,7 @@ size_t sort_scratch_bytes(long long n);
 double probe_fma(int fp64, int nsm, cudaStream_t s);
 
 // cc_mixed.cu
-void launch_prep_ff(const Level &L, const FFView &F, bool with_v, cudaStream_t s);
+void launch_prep_ff(const Level &L, const FFView &F, double G, bool with_v, cudaStream_t s);
 void launch_tau_mixed(const Level &L, const FFView &F, int ntiles, const TauParams &P, DevCounters *ctr,
                       int32_t *near_ij, double *near_tau, long long near_cap, cudaStream_t s);
 int mixed_kick_blocks(int n);

@@ -21,29 +21,31 @@ namespace cc {
 
 // ------------------------------------------------------------ prep
 // float-float copy of the packed state; per-level maxima of |x| and |v|
-__global__ void k_prep_ff(Level L, FFView F, int with_v)
+__global__ void k_prep_ff(Level L, FFView F, float G, int with_v)
 {
     const int k = blockIdx.x * blockDim.x + threadIdx.x;
     float ax = 0.f, av = 0.f;
     if (k < L.total && L.gid[k] >= 0) {
         const double xs[3] = {L.x[k], L.y[k], L.z[k]};
+        float hi[3], lo[3];
 #pragma unroll
         for (int c = 0; c < 3; ++c) {
-            const float hi = __double2float_rn(xs[c]);
-            F.ph[c][k] = hi;
-            F.pl[c][k] = __double2float_rn(xs[c] - (double)hi);
-            ax = fmaxf(ax, fabsf(hi));
+            hi[c] = __double2float_rn(xs[c]);
+            lo[c] = __double2float_rn(xs[c] - (double)hi[c]);
+            ax = fmaxf(ax, fabsf(hi[c]));
         }
-        F.m[k] = __double2float_rn(L.m[k]);
+        F.pq[2 * k] = make_float4(hi[0], hi[1], hi[2], G * __double2float_rn(L.m[k]));
+        F.pq[2 * k + 1] = make_float4(lo[0], lo[1], lo[2], 0.f);
         if (with_v) {
             const double vs[3] = {L.vx[k], L.vy[k], L.vz[k]};
 #pragma unroll
             for (int c = 0; c < 3; ++c) {
-                const float hi = __double2float_rn(vs[c]);
-                F.vh[c][k] = hi;
-                F.vl[c][k] = __double2float_rn(vs[c] - (double)hi);
-                av = fmaxf(av, fabsf(hi));
+                hi[c] = __double2float_rn(vs[c]);
+                lo[c] = __double2float_rn(vs[c] - (double)hi[c]);
+                av = fmaxf(av, fabsf(hi[c]));
             }
+            F.vq[2 * k] = make_float4(hi[0], hi[1], hi[2], 0.f);
+            F.vq[2 * k + 1] = make_float4(lo[0], lo[1], lo[2], 0.f);
         }
     }
     // positive floats order like their bit patterns
@@ -58,19 +60,20 @@ __global__ void k_prep_ff(Level L, FFView F, int with_v)
     }
 }
 
-void launch_prep_ff(const Level &L, const FFView &F, bool with_v, cudaStream_t s)
+void launch_prep_ff(const Level &L, const FFView &F, double G, bool with_v, cudaStream_t s)
 {
     if (L.total <= 0) return;
     cudaMemsetAsync(F.maxes, 0, 2 * sizeof(float), s);
-    k_prep_ff<<<(L.total + 255) / 256, 256, 0, s>>>(L, F, with_v ? 1 : 0);
+    k_prep_ff<<<(L.total + 255) / 256, 256, 0, s>>>(L, F, (float)G, with_v ? 1 : 0);
     CC_COUNT_LAUNCH(1);
 }
 
 constexpr int MT_T = 128;
 
 struct __align__(16) MixedTauSmem {
-    float col[13][MT_T + 4];  // ph[3] pl[3] vh[3] vl[3] m
-    int32_t lp[2 * MT_T];     // local union-find over the tile's particles
+    float4 pq[2 * MT_T];   // positions (hi, Gm), (lo) of the j-tile
+    float4 vq[2 * MT_T];   // velocities (hi), (lo)
+    int32_t lp[2 * MT_T];  // local union-find over the tile's particles
     uint64_t bar;
 };
 
@@ -133,25 +136,20 @@ __global__ void __launch_bounds__(MT_T) k_tau_mixed(Level L, FFView F, TauParams
     sm.lp[MT_T + tid] = MT_T + tid;
     __syncthreads();
     if (tid == 0) {
-        const unsigned bytes = (unsigned)((jn + 3) & ~3) * 4u;
-        mbar_expect_tx(&sm.bar, 13u * bytes);
-        const float *src[13] = {F.ph[0], F.ph[1], F.ph[2], F.pl[0], F.pl[1], F.pl[2], F.vh[0],
-                                F.vh[1], F.vh[2], F.vl[0], F.vl[1], F.vl[2], F.m};
-#pragma unroll
-        for (int c = 0; c < 13; ++c) tma_load_1d(sm.col[c], src[c] + j0, bytes, &sm.bar);
+        const unsigned bytes = (unsigned)jn * 32u;
+        mbar_expect_tx(&sm.bar, 2u * bytes);
+        tma_load_1d(sm.pq, F.pq + 2 * (size_t)j0, bytes, &sm.bar);
+        tma_load_1d(sm.vq, F.vq + 2 * (size_t)j0, bytes, &sm.bar);
     }
     const int il = ti * MT_T + tid;
     const bool iv = il < n;
     const int i = start + il;
-    float xh = 0, yh = 0, zh = 0, xl = 0, yl = 0, zl = 0, uh = 0, vh = 0, wh = 0, ul = 0, vl = 0, wl = 0, mi = 0;
+    float4 ip0 = make_float4(0, 0, 0, 0), ip1 = ip0, iv0 = ip0, iv1 = ip0;
     if (iv) {
-        xh = F.ph[0][i]; yh = F.ph[1][i]; zh = F.ph[2][i];
-        xl = F.pl[0][i]; yl = F.pl[1][i]; zl = F.pl[2][i];
-        uh = F.vh[0][i]; vh = F.vh[1][i]; wh = F.vh[2][i];
-        ul = F.vl[0][i]; vl = F.vl[1][i]; wl = F.vl[2][i];
-        mi = F.m[i];
+        ip0 = F.pq[2 * i]; ip1 = F.pq[2 * i + 1];
+        iv0 = F.vq[2 * i]; iv1 = F.vq[2 * i + 1];
     }
-    const float X = F.maxes[0], V = F.maxes[1];
+    const float cX = 11.f * U32 * U32 * F.maxes[0], cV = 11.f * U32 * U32 * F.maxes[1];
     const bool got = mbar_wait(&sm.bar, 0, TMA_WAIT_CYCLES);
     if (__syncthreads_or(!got)) {
         raise_err(ctr, DERR_TMA_TIMEOUT);
@@ -161,16 +159,16 @@ __global__ void __launch_bounds__(MT_T) k_tau_mixed(Level L, FFView F, TauParams
     unsigned long long my_edges = 0, my_fp64 = 0;
     const int joff = diag ? 0 : MT_T;  // local index base of the j-tile
     if (iv) {
-        const float Gf = Q.G;
         for (int k = diag ? tid + 1 : 0; k < jn; ++k) {
-            const float dx0 = (sm.col[0][k] - xh) + (sm.col[3][k] - xl);
-            const float dx1 = (sm.col[1][k] - yh) + (sm.col[4][k] - yl);
-            const float dx2 = (sm.col[2][k] - zh) + (sm.col[5][k] - zl);
-            const float dv0 = (sm.col[6][k] - uh) + (sm.col[9][k] - ul);
-            const float dv1 = (sm.col[7][k] - vh) + (sm.col[10][k] - vl);
-            const float dv2 = (sm.col[8][k] - wh) + (sm.col[11][k] - wl);
-            const float mu = Gf * (mi + sm.col[12][k]);
-            int dec = tau_decide_fp32(dx0, dx1, dx2, dv0, dv1, dv2, mu, X, V, Q);
+            const float4 jp0 = sm.pq[2 * k], jp1 = sm.pq[2 * k + 1];
+            const float4 jv0 = sm.vq[2 * k], jv1 = sm.vq[2 * k + 1];
+            const float dx0 = (jp0.x - ip0.x) + (jp1.x - ip1.x);
+            const float dx1 = (jp0.y - ip0.y) + (jp1.y - ip1.y);
+            const float dx2 = (jp0.z - ip0.z) + (jp1.z - ip1.z);
+            const float dv0 = (jv0.x - iv0.x) + (jv1.x - iv1.x);
+            const float dv1 = (jv0.y - iv0.y) + (jv1.y - iv1.y);
+            const float dv2 = (jv0.z - iv0.z) + (jv1.z - iv1.z);
+            int dec = tau_decide_fp32(dx0, dx1, dx2, dv0, dv1, dv2, ip0.w + jp0.w, cX, cV, Q);
             if (dec < 0) {
                 // undecided: the exact FP64 predicate of the FP64 form
                 const int j = j0 + k;
@@ -224,7 +222,7 @@ void launch_tau_mixed(const Level &L, const FFView &F, int ntiles, const TauPara
     if (ntiles <= 0) return;
     MixedTauParams Q;
     Q.eta = (float)P.eta_in;
-    Q.h = (float)(P.eta_outside ? P.h / P.eta : P.h);
+    Q.etah = (float)(P.eta_outside ? P.eta_in * P.eta / P.h : P.eta_in / P.h);
     Q.eps2 = (float)P.eps2;
     Q.G = (float)P.G;
     k_tau_mixed<<<ntiles, MT_T, 0, s>>>(L, F, P, Q, ctr, near_ij, near_tau, near_cap);
@@ -240,7 +238,7 @@ constexpr int MK_T = 128;
 constexpr int MK_CHUNK_TILES = 8;  // j-tiles per chunk (1024 j)
 
 struct __align__(16) MixedKickSmem {
-    float col[2][7][MK_T];  // ph[3] pl[3] m
+    float4 pq[2][2 * MK_T];  // (hi, Gm), (lo) per j, two stages
     int32_t lab[2][MK_T];
     uint64_t bar[2];
 };
@@ -250,19 +248,13 @@ __device__ __forceinline__ void mk_issue(MixedKickSmem &sm, int st, const FFView
 {
     const unsigned cnt = (unsigned)((jn + 3) & ~3);
     fence_proxy_async_smem();
-    mbar_expect_tx(&sm.bar[st], cnt * (7u * 4u + 4u));
-    tma_load_1d(sm.col[st][0], F.ph[0] + j0, cnt * 4u, &sm.bar[st]);
-    tma_load_1d(sm.col[st][1], F.ph[1] + j0, cnt * 4u, &sm.bar[st]);
-    tma_load_1d(sm.col[st][2], F.ph[2] + j0, cnt * 4u, &sm.bar[st]);
-    tma_load_1d(sm.col[st][3], F.pl[0] + j0, cnt * 4u, &sm.bar[st]);
-    tma_load_1d(sm.col[st][4], F.pl[1] + j0, cnt * 4u, &sm.bar[st]);
-    tma_load_1d(sm.col[st][5], F.pl[2] + j0, cnt * 4u, &sm.bar[st]);
-    tma_load_1d(sm.col[st][6], F.m + j0, cnt * 4u, &sm.bar[st]);
+    mbar_expect_tx(&sm.bar[st], (unsigned)jn * 32u + cnt * 4u);
+    tma_load_1d(sm.pq[st], F.pq + 2 * (size_t)j0, (unsigned)jn * 32u, &sm.bar[st]);
     tma_load_1d(sm.lab[st], label + j0, cnt * 4u, &sm.bar[st]);
 }
 
 __global__ void __launch_bounds__(MK_T) k_kick_mixed(Level L, FFView F, const int32_t *label, const int32_t *koff,
-                                                      float eps2, double Gh, DevCounters *ctr, double *partial)
+                                                      float eps2, double h, DevCounters *ctr, double *partial)
 {
     __shared__ MixedKickSmem sm;
     const int tid = threadIdx.x;
@@ -288,11 +280,11 @@ __global__ void __launch_bounds__(MK_T) k_kick_mixed(Level L, FFView F, const in
     }
     __syncthreads();
     if (tid == 0) mk_issue(sm, 0, F, label, start + tj0 * MK_T, min(MK_T, n - tj0 * MK_T));
-    float xh = 0, yh = 0, zh = 0, xl = 0, yl = 0, zl = 0;
+    float4 ip0 = make_float4(0, 0, 0, 0), ip1 = ip0;
     int li = 0;
     if (iv) {
-        xh = F.ph[0][i]; yh = F.ph[1][i]; zh = F.ph[2][i];
-        xl = F.pl[0][i]; yl = F.pl[1][i]; zl = F.pl[2][i];
+        ip0 = F.pq[2 * i];
+        ip1 = F.pq[2 * i + 1];
         li = label[i];
     }
     float sx = 0.f, sy = 0.f, sz = 0.f, cx = 0.f, cy = 0.f, cz = 0.f;
@@ -311,13 +303,14 @@ __global__ void __launch_bounds__(MK_T) k_kick_mixed(Level L, FFView F, const in
 #pragma unroll 4
             for (int k = 0; k < jn; ++k) {
                 if (sm.lab[st][k] == li || tj * MK_T + k == il) continue;
-                const float dx = (sm.col[st][0][k] - xh) + (sm.col[st][3][k] - xl);
-                const float dy = (sm.col[st][1][k] - yh) + (sm.col[st][4][k] - yl);
-                const float dz = (sm.col[st][2][k] - zh) + (sm.col[st][5][k] - zl);
+                const float4 jp0 = sm.pq[st][2 * k], jp1 = sm.pq[st][2 * k + 1];
+                const float dx = (jp0.x - ip0.x) + (jp1.x - ip1.x);
+                const float dy = (jp0.y - ip0.y) + (jp1.y - ip1.y);
+                const float dz = (jp0.z - ip0.z) + (jp1.z - ip1.z);
                 const float r2 = fmaf(dz, dz, fmaf(dy, dy, fmaf(dx, dx, eps2)));
                 float ri = rsqrtf(r2);
                 ri = ri * fmaf(-0.5f * r2, ri * ri, 1.5f);  // one Newton step
-                const float w = sm.col[st][6][k] * (ri * ri * ri);
+                const float w = jp0.w * (ri * ri * ri);      // G m_j / r^3
                 kahan_add(sx, cx, w * dx);
                 kahan_add(sy, cy, w * dy);
                 kahan_add(sz, cz, w * dz);
@@ -334,9 +327,9 @@ __global__ void __launch_bounds__(MK_T) k_kick_mixed(Level L, FFView F, const in
     if (!iv) return;
     const double ax = (double)sx - (double)cx, ay = (double)sy - (double)cy, az = (double)sz - (double)cz;
     if (nchunk == 1) {
-        L.vx[i] += Gh * ax;
-        L.vy[i] += Gh * ay;
-        L.vz[i] += Gh * az;
+        L.vx[i] += h * ax;
+        L.vy[i] += h * ay;
+        L.vz[i] += h * az;
     } else {
         // partial[(chunk * 3 + c) * cap + i]
         const size_t cap = (size_t)F.cap;
@@ -346,8 +339,8 @@ __global__ void __launch_bounds__(MK_T) k_kick_mixed(Level L, FFView F, const in
     }
 }
 
-// sum the chunk partials of multi-chunk sets in chunk order (FP64), v += G h a
-__global__ void k_kick_reduce(Level L, FFView F, double Gh, const double *partial)
+// sum the chunk partials of multi-chunk sets in chunk order (FP64), v += h a
+__global__ void k_kick_reduce(Level L, FFView F, double h, const double *partial)
 {
     const int k = blockIdx.x * blockDim.x + threadIdx.x;
     if (k >= L.total || L.sidx[k] < 0) return;
@@ -361,9 +354,9 @@ __global__ void k_kick_reduce(Level L, FFView F, double Gh, const double *partia
         ay += partial[((size_t)c * 3 + 1) * cap + k];
         az += partial[((size_t)c * 3 + 2) * cap + k];
     }
-    L.vx[k] += Gh * ax;
-    L.vy[k] += Gh * ay;
-    L.vz[k] += Gh * az;
+    L.vx[k] += h * ax;
+    L.vy[k] += h * ay;
+    L.vz[k] += h * az;
 }
 
 int mixed_kick_blocks(int n)
@@ -383,10 +376,11 @@ void launch_kick_mixed(const Level &L, const FFView &F, const int32_t *label, co
                        cudaStream_t s)
 {
     if (nblocks <= 0) return;
-    k_kick_mixed<<<nblocks, MK_T, 0, s>>>(L, F, label, koff, (float)eps2, G * h, ctr, partial);
+    (void)G;  // folded into the float masses (G m) by the prep kernel
+    k_kick_mixed<<<nblocks, MK_T, 0, s>>>(L, F, label, koff, (float)eps2, h, ctr, partial);
     CC_COUNT_LAUNCH(1);
     if (multi_chunk) {
-        k_kick_reduce<<<(L.total + 255) / 256, 256, 0, s>>>(L, F, G * h, partial);
+        k_kick_reduce<<<(L.total + 255) / 256, 256, 0, s>>>(L, F, h, partial);
         CC_COUNT_LAUNCH(1);
     }
 }

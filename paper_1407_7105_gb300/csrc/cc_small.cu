@@ -27,6 +27,7 @@ constexpr unsigned FULL = 0xffffffffu;
 struct __align__(16) K8Warp {
     double d[7][32];  // x y z vx vy vz m
     float f[13][32];  // hi/lo of x y z vx vy vz, m (FP32 decision)
+    float xm[32], vm[32];  // per body max |x_hi|, max |v_hi| (error bounds)
 };
 
 __device__ __forceinline__ void k8_publish(K8Warp &S, int lane, const double st[7], bool ff)
@@ -42,8 +43,25 @@ __device__ __forceinline__ void k8_publish(K8Warp &S, int lane, const double st[
             S.f[6 + c][lane] = __double2float_rn(st[c] - (double)hi);
         }
         S.f[12][lane] = __double2float_rn(st[6]);
+        S.xm[lane] = fmaxf(fabsf(S.f[0][lane]), fmaxf(fabsf(S.f[1][lane]), fabsf(S.f[2][lane])));
+        S.vm[lane] = fmaxf(fabsf(S.f[3][lane]), fmaxf(fabsf(S.f[4][lane]), fabsf(S.f[5][lane])));
     }
     __syncwarp();
+}
+
+// x += dt v: exact IEEE operations in the FP64 form (bit-identical to the
+// oracle), fused multiply-add in the mixed form
+__device__ __forceinline__ void k8_drift(double st[7], double dt, bool exact)
+{
+    if (exact) {
+        st[0] = __dadd_rn(st[0], __dmul_rn(dt, st[3]));
+        st[1] = __dadd_rn(st[1], __dmul_rn(dt, st[4]));
+        st[2] = __dadd_rn(st[2], __dmul_rn(dt, st[5]));
+    } else {
+        st[0] = fma(dt, st[3], st[0]);
+        st[1] = fma(dt, st[4], st[1]);
+        st[2] = fma(dt, st[5], st[2]);
+    }
 }
 
 __global__ void __launch_bounds__(K8_WARPS * 32) k_small(Level L, const int32_t *members, const int32_t *comp_start,
@@ -91,18 +109,9 @@ __global__ void __launch_bounds__(K8_WARPS * 32) k_small(Level L, const int32_t 
             if (ph[k] == 0) {
                 // ---------------- split at h: tau(i,j) < h inside the lane's set
                 k8_publish(S, lane, st, mixed);
-                float X = 0.f, V = 0.f;
-                if (mixed) {
-                    X = fmaxf(fabsf(S.f[0][lane]), fmaxf(fabsf(S.f[1][lane]), fabsf(S.f[2][lane])));
-                    V = fmaxf(fabsf(S.f[3][lane]), fmaxf(fabsf(S.f[4][lane]), fabsf(S.f[5][lane])));
-#pragma unroll
-                    for (int o = 16; o > 0; o >>= 1) {
-                        X = fmaxf(X, __shfl_xor_sync(FULL, X, o));
-                        V = fmaxf(V, __shfl_xor_sync(FULL, V, o));
-                    }
-                }
                 P.h = h;
-                Q.h = (float)(SP.eta_outside ? h / SP.eta : h);
+                Q.etah = (float)(SP.eta_outside ? SP.eta_in * SP.eta / h : SP.eta_in / h);
+                const float c11 = 11.f * U32 * U32;
                 uint32_t adj = 0;
                 if (mine) {
                     for (int j = 0; j < n; ++j) {
@@ -115,7 +124,9 @@ __global__ void __launch_bounds__(K8_WARPS * 32) k_small(Level L, const int32_t 
                                                   (S.f[3][j] - S.f[3][lane]) + (S.f[9][j] - S.f[9][lane]),
                                                   (S.f[4][j] - S.f[4][lane]) + (S.f[10][j] - S.f[10][lane]),
                                                   (S.f[5][j] - S.f[5][lane]) + (S.f[11][j] - S.f[11][lane]),
-                                                  Q.G * (S.f[12][lane] + S.f[12][j]), X, V, Q);
+                                                  Q.G * (S.f[12][lane] + S.f[12][j]),
+                                                  c11 * fmaxf(S.xm[lane], S.xm[j]), c11 * fmaxf(S.vm[lane], S.vm[j]),
+                                                  Q);
                         }
                         if (dec < 0) {
                             const int lo = lane < j ? lane : j, hi = lane < j ? j : lane;
@@ -184,15 +195,17 @@ __global__ void __launch_bounds__(K8_WARPS * 32) k_small(Level L, const int32_t 
             const bool sub = csz >= 2 && !(SP.kepler && csz == 2);
             if (ph[k] == 1) {
                 const bool kep = mine && SP.kepler && csz == 2;
+                const bool any_kep = __any_sync(FULL, kep);
+                // the level's DKD has work only where the lane's set holds a
+                // rest-set member or more than one component
+                const bool any_dkd = __any_sync(FULL, mine && (cm != mine || cm == me));
                 for (int half = 0; half < 2; ++half) {
-                    if (half == 1) {
+                    if (half == 1 && any_dkd) {
                         // ------------- D_{h/2,T_R} K_{h,V} D_{h/2,T_R} on the lane's set
                         const bool single = mine && cm == me;
                         const double hd = 0.5 * h;
                         if (single) {
-                            st[0] = __dadd_rn(st[0], __dmul_rn(hd, st[3]));
-                            st[1] = __dadd_rn(st[1], __dmul_rn(hd, st[4]));
-                            st[2] = __dadd_rn(st[2], __dmul_rn(hd, st[5]));
+                            k8_drift(st, hd, !mixed);
                             c_drift += 2;
                         }
                         const bool fp64_kick = !mixed || h < SP.h_fp64;
@@ -240,18 +253,14 @@ __global__ void __launch_bounds__(K8_WARPS * 32) k_small(Level L, const int32_t 
                                     kahan_add(sz, cz, ww * dz);
                                 }
                                 const double gh = SP.G * h;
-                                st[3] += gh * ((double)sx - (double)cx);
-                                st[4] += gh * ((double)sy - (double)cy);
-                                st[5] += gh * ((double)sz - (double)cz);
+                                st[3] = fma(gh, (double)sx - (double)cx, st[3]);
+                                st[4] = fma(gh, (double)sy - (double)cy, st[4]);
+                                st[5] = fma(gh, (double)sz - (double)cz, st[5]);
                             }
                         }
-                        __syncwarp();
-                        if (single) {
-                            st[0] = __dadd_rn(st[0], __dmul_rn(hd, st[3]));
-                            st[1] = __dadd_rn(st[1], __dmul_rn(hd, st[4]));
-                            st[2] = __dadd_rn(st[2], __dmul_rn(hd, st[5]));
-                        }
+                        if (single) k8_drift(st, hd, !mixed);
                     }
+                    if (!any_kep) continue;
                     // two-body components: the Kepler flow over h/2
                     k8_publish(S, lane, st, false);
                     if (kep) {
@@ -267,7 +276,6 @@ __global__ void __launch_bounds__(K8_WARPS * 32) k_small(Level L, const int32_t 
                             st[0] = xb[0]; st[1] = xb[1]; st[2] = xb[2]; st[3] = vb[0]; st[4] = vb[1]; st[5] = vb[2];
                         }
                     }
-                    __syncwarp();
                 }
                 ph[k] = 2;
                 if (__any_sync(FULL, sub)) {
