@@ -39,9 +39,50 @@ TAU_FLOPS = 47   # Eq. tauij as evaluated: 3 sqrt, 6 div, 38 add/sub/mul
 KICK_FLOPS = 28  # one pair force applied to both bodies (Eqs. kickij/kickji)
 
 
-def workload_name(n=N_BODY):
-    return (f"Plummer N={n}, equal masses, N-body units, eps=0, eta={ETA}, outer step dt=1/256 "
-            f"(one evolve_cc step per bench step)")
+WORKLOADS = {
+    # the configuration the metric is quoted on (default)
+    "plummer": dict(dt=1.0 / 256, kepler=False,
+                    name="Plummer N={n}, equal masses, N-body units, eps=0, eta=0.03, outer step dt=1/256 "
+                         "(one evolve_cc step per bench step)"),
+    "fractal": dict(dt=1.0 / 256, kepler=False,
+                    name="box fractal N={n}, D=1.6, Salpeter IMF 0.1-100 (total M=1), Q=0.3, N-body units, "
+                         "eps=0, eta=0.03, outer step dt=1/256"),
+    "binaries": dict(dt=1.0 / 256, kepler=True,
+                     name="Plummer N={n} with 50% of bodies in binaries (a log-uniform 1e-5..1e-2, thermal e, "
+                          "q~U(0.1,1]), CC_KEPLER, eta=0.03, outer step dt=1/256"),
+    "systems": dict(dt=1.0 / 64, kepler=False,
+                    name="{nsys} independent systems (triples, or Plummer clumps of logU[3,512] bodies), "
+                         "each in its own N-body units, eta=0.03, outer step dt=1/64"),
+}
+
+
+def workload_name(n=N_BODY, workload="plummer", nsys=4096):
+    return WORKLOADS[workload]["name"].format(n=n, nsys=nsys)
+
+
+def make_workload(args, seed, dev=None):
+    """Seeded synthetic state (m, x3, v3, sys_off or None) of the workload."""
+    from paper_1407_7105_gb300 import ics
+    w = args.workload
+    if w == "plummer":
+        return (*ics.plummer(args.n, seed=seed), None)
+    if w == "binaries":
+        return (*ics.plummer_with_binaries(args.n, seed=seed), None)
+    if w == "systems":
+        return ics.small_systems(args.nsys, seed=seed)
+    # fractal: the potential energy of the unscaled cluster is summed on the
+    # GPU by the library's energy diagnostic (velocities zero: E = W)
+    from paper_1407_7105_gb300 import cc
+    import torch
+    x0, v0 = ics.box_fractal_raw(args.n, seed=seed)
+    m = ics.salpeter_masses(args.n, seed, 9100)
+    x0, v0 = ics._com_frame(m, x0, v0)
+    ctx = cc.Context(torch.tensor(m, device=dev), torch.tensor(x0, device=dev),
+                     torch.zeros((3, args.n), dtype=torch.float64, device=dev))
+    W, _, _ = ctx.energy()
+    ctx.close()
+    x3, v3 = ics.scale_to_nbody_units(m, x0, v0, Q=0.3, exact=False, W=W)
+    return m, x3, v3, None
 
 
 # ------------------------------------------------------------------ clocks
@@ -168,11 +209,13 @@ def run_gpu(args, rank, world):
     dev = torch.device("cuda", local)
     build.build()
     seed = args.seed + rank
-    N = args.n
-    m, x, v = ics.plummer(N, seed=seed)
+    m, x, v, sys_off = make_workload(args, seed, dev)
+    N = int(m.shape[0])
+    W = WORKLOADS[args.workload]
+    DTW = W["dt"]
 
     cpu = None
-    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+    if rank == 0 and world == 1 and not args.no_cpu_baseline and args.workload == "plummer":
         from oracle import oracle as O
         O.build()
         inter, sec = oracle_sample(m, x, v)
@@ -187,14 +230,18 @@ def run_gpu(args, rank, world):
 
     def make_ctx(form):
         prec = cc.PREC_MIXED if form == "mixed" else cc.PREC_FP64
-        return cc.Context(dm, dx, dv, dt=DT, eta=ETA, precision=prec, h_fp64=args.h_fp64 * DT)
+        ctx = cc.Context(dm, dx, dv, dt=DTW, eta=ETA, precision=prec, h_fp64=args.h_fp64 * DTW,
+                         s_small=args.s_small, kepler=int(W["kepler"]))
+        if sys_off is not None:
+            ctx.set_systems(sys_off)
+        return ctx
 
     def time_form(form, steps, warmup, clocks_too):
         ctx = make_ctx(form)
         E0, _, _ = ctx.energy()
         t = 0.0
         for _ in range(warmup):
-            t += DT
+            t += DTW
             ctx.evolve(t)
         torch.cuda.synchronize()
         st0 = ctx.stats()
@@ -213,7 +260,7 @@ def run_gpu(args, rank, world):
             e0 = torch.cuda.Event(enable_timing=True)
             e1 = torch.cuda.Event(enable_timing=True)
             e0.record(stream)
-            t += DT
+            t += DTW
             ctx.evolve(t)
             e1.record(stream)
             e1.synchronize()
@@ -252,7 +299,7 @@ def run_gpu(args, rank, world):
     w0 = time.perf_counter()
     for _ in range(e2e_steps):
         ctx.set_state(t, hm, hx, hv)
-        t += DT
+        t += DTW
         ctx.evolve(t)
         ctx.get_state(None, hx, hv, alloc=False)
     torch.cuda.synchronize()
@@ -301,7 +348,8 @@ def run_gpu(args, rank, world):
             "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": total_ms / args.steps, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f32/f64" if fp32 else "f64", "data": "synthetic",
-            "config": {"workload": workload_name(N), "form": args.form, "h_fp64": f"{args.h_fp64}*dt",
+            "config": {"workload": workload_name(N, args.workload, args.nsys), "form": args.form, "h_fp64": f"{args.h_fp64}*dt",
+                       "s_small": args.s_small,
                        "l2": "flushed (256 MB write) before each step",
                        "parallelism": "replicas" if world > 1 else "single GPU"},
             "e2e": {"value": e2e_inter / e2e_sec, "unit": UNIT, "h2d_bytes_per_step": 7 * N * 8,
@@ -363,12 +411,19 @@ def main():
     ap.add_argument("--h-fp64", type=float, default=0.0,
                     help="mixed form: sets split at h < h_fp64*dt take FP64 forces")
     ap.add_argument("--single-form", action="store_true", help="skip timing the other form")
+    ap.add_argument("--s-small", type=int, default=32,
+                    help="components of at most this many bodies run in the small-component kernel (0: none)")
     ap.add_argument("--accuracy", action="store_true", help="integrate both forms to --t-end and report dE/E")
     ap.add_argument("--t-end", type=float, default=1.0)
     ap.add_argument("--seed", type=int, default=1)
-    ap.add_argument("--n", type=int, default=N_BODY, help="bodies (smaller cases are for profiling only)")
+    ap.add_argument("--n", type=int, default=None, help="bodies (default per workload)")
+    ap.add_argument("--workload", default="plummer", choices=sorted(WORKLOADS),
+                    help="plummer (the metric's configuration), fractal, binaries, systems")
+    ap.add_argument("--nsys", type=int, default=4096, help="systems of the 'systems' workload")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     args = ap.parse_args()
+    if args.n is None:
+        args.n = {"plummer": N_BODY, "fractal": 65536, "binaries": 32768, "systems": 0}[args.workload]
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
     if args.impl == "reference":

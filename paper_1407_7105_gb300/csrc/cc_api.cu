@@ -227,7 +227,7 @@ static int ensure_level(cc_ctx *c, LevelAlloc &a, int need, int nsets)
         const long long worst = std::min<long long>(2 * (long long)c->n + 64, 0x3fffffff);
         int cap = align_up(std::max<int>(need, (int)std::max<long long>(64, worst)), 64);
         size_t nd = (size_t)cap + PAD_TAIL;
-        size_t bytes = nd * 8 * 7 + nd * 4 * 10 + nd * 64 + 4096;
+        size_t bytes = nd * 8 * 7 + nd * 4 * 11 + nd * 64 + 4096;
         if (cudaMalloc(&a.block, bytes) != cudaSuccess) {
             cudaGetLastError();
             return fail(c, CC_E_NOMEM, "device allocation failed (level buffer)");
@@ -236,9 +236,9 @@ static int ensure_level(cc_ctx *c, LevelAlloc &a, int need, int nsets)
         char *q = (char *)a.block;
         double **dp[7] = {&a.L.x, &a.L.y, &a.L.z, &a.L.vx, &a.L.vy, &a.L.vz, &a.L.m};
         for (int k = 0; k < 7; ++k) { *dp[k] = (double *)q; q += nd * 8; }
-        int32_t **ip[10] = {&a.L.gid, &a.L.sidx, &a.L.src, &a.L.parent, &a.L.cnt,
+        int32_t **ip[11] = {&a.L.gid, &a.L.sidx, &a.L.src, &a.L.parent, &a.L.cnt, &a.L.klab,
                             &a.root, &a.members, &a.comp_start, &a.comp_size, &a.d_ncomp};
-        for (int k = 0; k < 10; ++k) { *ip[k] = (int32_t *)q; q += nd * 4; }
+        for (int k = 0; k < 11; ++k) { *ip[k] = (int32_t *)q; q += nd * 4; }
         a.F.pq = (float4 *)q; q += nd * 32;
         a.F.vq = (float4 *)q; q += nd * 32;
         a.F.maxes = (float *)q;
@@ -483,10 +483,12 @@ static int dkd(cc_ctx *c, LevelAlloc &a, double h)
             }
             c->kpart_sz = need;
         }
-        launch_prep_ff(a.L, a.F, c->p.G, false, s);
+        // positions in the root-sorted order of the split: members of one
+        // component are adjacent, so tiles inside one component are skipped
+        launch_prep_kick(a.L, a.F, a.members, a.root, c->p.G, s);
         const int ev = ev_begin(c, 1);
-        launch_kick_mixed(a.L, a.F, a.root, a.L.koff, (int)a.kblocks, a.kchunks_max > 1, c->p.G,
-                          c->p.eps * c->p.eps, h, c->d_ctr, c->d_kpart, s);
+        launch_kick_mixed(a.L, a.F, a.members, a.L.koff, (int)a.kblocks, a.kchunks_max > 1, c->p.eps * c->p.eps,
+                          h, c->d_ctr, c->d_kpart, s);
         ev_end(c, ev);
     } else {
         const int ev = ev_begin(c, 1);
@@ -692,13 +694,24 @@ int cc_init(cc_ctx **out, int64_t n, const double *m, const double *x3, const do
         cudaMalloc(&c->d_m, n * 8) != cudaSuccess || cudaMalloc(&c->d_ctr, sizeof(DevCounters)) != cudaSuccess ||
         cudaMalloc(&c->d_near_ij, c->near_cap * 8) != cudaSuccess ||
         cudaMalloc(&c->d_near_tau, c->near_cap * 8) != cudaSuccess ||
-        cudaMalloc(&c->d_bad, 16) != cudaSuccess || cudaMalloc(&c->d_queue, 64) != cudaSuccess ||
-        cudaStreamCreateWithFlags(&c->side, cudaStreamNonBlocking) != cudaSuccess) {
+        cudaMalloc(&c->d_bad, 16) != cudaSuccess || cudaMalloc(&c->d_queue, 64) != cudaSuccess) {
         cudaGetLastError();
         c->err = "cc_init: device allocation failed";
         return bail(CC_E_NOMEM);
     }
     cudaMemsetAsync(c->d_ctr, 0, sizeof(DevCounters), c->stream);
+    {
+        // the side stream of the small-component kernel gets the highest
+        // priority: its few long-running blocks take SM slots as soon as the
+        // pair kernels' short blocks retire, instead of queueing behind them
+        int least = 0, greatest = 0;
+        cudaDeviceGetStreamPriorityRange(&least, &greatest);
+        if (cudaStreamCreateWithPriority(&c->side, cudaStreamNonBlocking, greatest) != cudaSuccess) {
+            cudaGetLastError();
+            c->err = "cc_init: stream creation failed";
+            return bail(CC_E_CUDA);
+        }
+    }
     {
         int dev = 0;
         cudaGetDevice(&dev);
@@ -894,8 +907,28 @@ int cc_kick(cc_ctx *c, const int32_t *set, int64_t n_set, const int32_t *labels,
     dl = (int32_t *)(((uintptr_t)dl + 15) & ~(uintptr_t)15);
     CC_TRY(copy_in(c, dl, labels, n_set * 4));
     LevelAlloc &u = c->unit;
-    const int nit = (int)((n_set + KICK_TILE - 1) / KICK_TILE);
-    launch_kick(u.L, dl, nit, c->p.G, c->p.eps * c->p.eps, h, c->p.precision, c->d_ctr, nullptr, c->stream);
+    if (c->p.precision == CC_PREC_MIXED && !(h < c->p.h_fp64)) {
+        // the mixed kick works in label-sorted order (members of a group adjacent)
+        int32_t *order = u.members;
+        launch_label_order(dl, (int)n_set, u.L.total, order, c->seg_scratch, c->stream);
+        const size_t need = (size_t)std::max(1, u.kchunks_max) * 3 * (size_t)u.F.cap * sizeof(double);
+        if (u.kchunks_max > 1 && need > c->kpart_sz) {
+            if (c->d_kpart) cudaFree(c->d_kpart);
+            c->d_kpart = nullptr;
+            c->kpart_sz = 0;
+            if (cudaMalloc(&c->d_kpart, need) != cudaSuccess) {
+                cudaGetLastError();
+                return fail(c, CC_E_NOMEM, "device allocation failed (kick partials)");
+            }
+            c->kpart_sz = need;
+        }
+        launch_prep_kick(u.L, u.F, order, dl, c->p.G, c->stream);
+        launch_kick_mixed(u.L, u.F, order, u.L.koff, (int)u.kblocks, u.kchunks_max > 1, c->p.eps * c->p.eps, h,
+                          c->d_ctr, c->d_kpart, c->stream);
+    } else {
+        const int nit = (int)((n_set + KICK_TILE - 1) / KICK_TILE);
+        launch_kick(u.L, dl, nit, c->p.G, c->p.eps * c->p.eps, h, c->p.precision, c->d_ctr, nullptr, c->stream);
+    }
     launch_scatter_set(c->d_x3, c->d_v3, c->n, u.L, (int)n_set, false, true, c->stream);
     CC_CUDA(c, cudaStreamSynchronize(c->stream));
     return check_device_error(c);

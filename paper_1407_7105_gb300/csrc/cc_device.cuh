@@ -76,6 +76,34 @@ __device__ __forceinline__ int tau_decide_fp32(float dx0, float dx1, float dx2, 
     return -1;
 }
 
+// Float-float split of a double: hi = fl32(x) (round to nearest even),
+// lo = fl32(x - hi).  For |x| in [2^-74, 2^127) it is computed with integer
+// operations and int->float conversions (the significand rounded to 24
+// bits by integer arithmetic, the remainder converted exactly-then-rounded),
+// giving the same two floats as the FP64 route at a fraction of its cost on
+// a part whose FP64 pipe is 1/58 of the FP32 rate; outside that range it
+// takes the FP64 route.
+__device__ __forceinline__ void ff_split(double x, float &hi, float &lo)
+{
+    const unsigned long long b = (unsigned long long)__double_as_longlong(x);
+    const int e = (int)((b >> 52) & 0x7FFull);
+    if (e < 949 || e > 1150) {
+        hi = __double2float_rn(x);
+        lo = __double2float_rn(x - (double)hi);
+        return;
+    }
+    const long long F = (long long)((b & 0xFFFFFFFFFFFFFull) | 0x10000000000000ull);  // 53-bit significand
+    const long long Fr = (F + 0x0FFFFFFFll + ((F >> 29) & 1ll)) >> 29;             // 24 bits, nearest even
+    const int d = (int)(F - (Fr << 29));                                           // |d| <= 2^28
+    const float s_hi = __int_as_float((e - 1046 + 127) << 23);                     // 2^(e-1046)
+    const float s_lo = __int_as_float((e - 1075 + 127) << 23);                     // 2^(e-1075)
+    const float h = __int2float_rn((int)Fr) * s_hi;
+    const float l = __int2float_rn(d) * s_lo;
+    const bool neg = (b >> 63) != 0ull;
+    hi = neg ? -h : h;
+    lo = neg ? -l : l;
+}
+
 // Kahan-compensated accumulation: s + (-c) carries the running sum
 __device__ __forceinline__ void kahan_add(float &s, float &c, float x)
 {

@@ -245,20 +245,23 @@ void launch_compress(const Level &L, int32_t *root, cudaStream_t s)
 }
 
 // ------------------------------------------------------------ segment
+// The order produced here ("members") is every packed element stably sorted
+// by root (padding keyed by its own index): each set keeps its range, each
+// component is a contiguous run of ascending members, and rest-set members
+// sit between runs in ascending order.  comp_start indexes this order.
 __global__ void k_seg_keys(Level L, const int32_t *root, uint32_t *key, int32_t *val)
 {
     const int k = blockIdx.x * blockDim.x + threadIdx.x;
     if (k >= L.total) return;
-    const bool mem = L.gid[k] >= 0 && L.cnt[root[k]] >= 2;
-    key[k] = mem ? (uint32_t)root[k] : (uint32_t)L.total;
+    key[k] = L.gid[k] >= 0 ? (uint32_t)root[k] : (uint32_t)k;
     val[k] = k;
 }
 
-__global__ void k_seg_heads(const uint32_t *key, int n, uint32_t sentinel, int *flag)
+__global__ void k_seg_heads(Level L, const uint32_t *key, int n, int *flag)
 {
     const int t = blockIdx.x * blockDim.x + threadIdx.x;
     if (t >= n) return;
-    flag[t] = key[t] < sentinel && (t == 0 || key[t] != key[t - 1]) ? 1 : 0;
+    flag[t] = L.cnt[key[t]] >= 2 && (t == 0 || key[t] != key[t - 1]) ? 1 : 0;
 }
 
 __global__ void k_seg_bounds(Level L, const uint32_t *key, const int32_t *val, const int *flag, const int *cidx,
@@ -266,8 +269,7 @@ __global__ void k_seg_bounds(Level L, const uint32_t *key, const int32_t *val, c
 {
     const int t = blockIdx.x * blockDim.x + threadIdx.x;
     if (t >= n) return;
-    const bool mem = key[t] < (uint32_t)L.total;
-    if (mem) members[t] = val[t];
+    members[t] = val[t];
     if (flag[t]) {
         comp_start[cidx[t]] = t;
         comp_size[cidx[t]] = L.cnt[key[t]];
@@ -298,7 +300,7 @@ void launch_segment(const Level &L, const int32_t *root, int32_t *members, int32
     k_seg_keys<<<g, 256, 0, s>>>(L, root, key, val);
     CC_COUNT_LAUNCH(1);
     radix_sort(key, val, n, bits_for(n), sort_scratch, s);
-    k_seg_heads<<<g, 256, 0, s>>>(key, n, (uint32_t)n, flag);
+    k_seg_heads<<<g, 256, 0, s>>>(L, key, n, flag);
     CC_COUNT_LAUNCH(1);
     device_scan(flag, cidx, n, bsum, nullptr, s);
     k_seg_bounds<<<g, 256, 0, s>>>(L, key, val, flag, cidx, n, members, comp_start, comp_size, d_ncomp);
@@ -318,7 +320,7 @@ __global__ void __launch_bounds__(SEG1_T) k_segment_small(Level L, int32_t *root
                                                           int32_t *comp_start, int32_t *comp_size, int32_t *ncomp)
 {
     __shared__ int s_root[SEG1_MAX];
-    __shared__ int s_cnt[SEG1_MAX];  // size by root; for heads then -(cursor + 1)
+    __shared__ int s_cnt[SEG1_MAX];  // size by root, then run start / cursor by key
     __shared__ int tmp[32];
     const int n = L.total, tid = threadIdx.x;
     for (int k = tid; k < n; k += SEG1_T) s_cnt[k] = 0;
@@ -332,33 +334,36 @@ __global__ void __launch_bounds__(SEG1_T) k_segment_small(Level L, int32_t *root
     }
     __syncthreads();
     for (int k = tid; k < n; k += SEG1_T) L.cnt[k] = s_cnt[k];
-    // heads (roots of non-trivial components) in index order: component
-    // index and member offset by two block scans over 4 items per thread
-    int hc[4], hsz[4];
-    int sc = 0, ss = 0;
+    // runs in key order: key = root for valid elements, own index for
+    // padding; w[k] = number of elements keyed k.  Run starts by a block scan
+    // (4 items per thread), component index by a second scan over heads.
+    int wv[4], hc[4];
+    int sw = 0, sc = 0;
 #pragma unroll
     for (int q = 0; q < 4; ++q) {
         const int k = 4 * tid + q;
-        const bool head = k < n && L.gid[k] >= 0 && s_root[k] == k && s_cnt[k] >= 2;
-        hc[q] = head ? 1 : 0;
-        hsz[q] = head ? s_cnt[k] : 0;
+        const bool valid_root = k < n && L.gid[k] >= 0 && s_root[k] == k;
+        const bool pad = k < n && L.gid[k] < 0;
+        wv[q] = valid_root ? s_cnt[k] : (pad ? 1 : 0);
+        hc[q] = valid_root && s_cnt[k] >= 2 ? 1 : 0;
+        sw += wv[q];
         sc += hc[q];
-        ss += hsz[q];
     }
     __syncthreads();
-    int tot_c, tot_s;
+    int tot_w, tot_c;
+    int ew = block_exclusive_scan(sw, tmp, tot_w);
     int ec = block_exclusive_scan(sc, tmp, tot_c);
-    int es = block_exclusive_scan(ss, tmp, tot_s);
+    __syncthreads();
 #pragma unroll
     for (int q = 0; q < 4; ++q) {
         const int k = 4 * tid + q;
         if (hc[q]) {
-            comp_start[ec] = es;
-            comp_size[ec] = hsz[q];
-            s_cnt[k] = -(es + 1);
+            comp_start[ec] = ew;
+            comp_size[ec] = wv[q];
         }
+        if (k < n) s_cnt[k] = ew;  // run start of key k (cursor)
         ec += hc[q];
-        es += hsz[q];
+        ew += wv[q];
     }
     if (tid == 0) *ncomp = tot_c;
     __syncthreads();
@@ -366,19 +371,18 @@ __global__ void __launch_bounds__(SEG1_T) k_segment_small(Level L, int32_t *root
         const unsigned lt = (1u << tid) - 1u;
         for (int base = 0; base < n; base += 32) {
             const int k = base + tid;
-            const int r = k < n ? s_root[k] : 0;
-            const bool mem = k < n && L.gid[k] >= 0 && s_cnt[r] < 0;
-            const int key = mem ? r : -1 - tid;
+            const bool in = k < n;
+            const int key = in ? (L.gid[k] >= 0 ? s_root[k] : k) : -1 - tid;
             const unsigned peers = __match_any_sync(0xffffffffu, key);
             const int rank = __popc(peers & lt);
             const int lead = __ffs(peers) - 1;
             int pos = 0;
-            if (mem && rank == 0) {
-                pos = -s_cnt[r] - 1;
-                s_cnt[r] -= __popc(peers);
+            if (in && rank == 0) {
+                pos = s_cnt[key];
+                s_cnt[key] += __popc(peers);
             }
             pos = __shfl_sync(0xffffffffu, pos, lead) + rank;
-            if (mem) members[pos] = k;
+            if (in) members[pos] = k;
             __syncwarp();
         }
     }
@@ -666,6 +670,29 @@ void launch_check_state(const double *m, const double *x3, const double *v3, lon
         k_check_state<<<(int)((n + 255) / 256), 256, 0, s>>>(m, x3, v3, n, bad);
         CC_COUNT_LAUNCH(1);
     }
+}
+
+// order[0..n) = indices of labels[0..n) stably sorted by label;
+// order[t] = t for the padding positions n <= t < total
+__global__ void k_order_from_sorted(const int32_t *val, int n, int total, int32_t *order)
+{
+    const int t = blockIdx.x * blockDim.x + threadIdx.x;
+    if (t < total) order[t] = t < n ? val[t] : t;
+}
+
+void launch_label_order(const int32_t *labels, int n, int total, int32_t *order, void *scratch, cudaStream_t s)
+{
+    if (total <= 0) return;
+    uint32_t *key = (uint32_t *)scratch;
+    int32_t *val = (int32_t *)(key + n);
+    void *ss = (void *)(val + n);
+    if (n > 0) {
+        k_lab_keys<<<(n + 255) / 256, 256, 0, s>>>(labels, n, key, val);
+        CC_COUNT_LAUNCH(1);
+        radix_sort(key, val, n, 32, ss, s);
+    }
+    k_order_from_sorted<<<(total + 255) / 256, 256, 0, s>>>(val, n, total, order);
+    CC_COUNT_LAUNCH(1);
 }
 
 // ------------------------------------------------------------ edge order

@@ -24,6 +24,7 @@ struct Level {
     int32_t *src;      // index in the parent level the element came from
     int32_t *parent;   // union-find forest over packed indices
     int32_t *cnt;      // component size, indexed by root
+    int32_t *klab;     // mixed kick: label (root) by position of the root-sorted order
     int32_t *set_start, *set_n;      // [nsets]
     int32_t *tile_off;               // [nsets+1] triangular tau tiles prefix
     int32_t *itile_off;              // [nsets+1] i-tiles prefix (kick)
@@ -254,6 +255,7 @@ void launch_scatter_set(double *x3, double *v3, long long n, const Level &L, int
 void launch_label_canon(const Level &L, const int32_t *root, int32_t *labels_out, int nset, cudaStream_t s);
 void launch_singleton_from_labels(const int32_t *labels, int n, int32_t *singleton, void *scratch,
                                   cudaStream_t s);
+void launch_label_order(const int32_t *labels, int n, int total, int32_t *order, void *scratch, cudaStream_t s);
 void launch_sort_edges(int32_t *edges, long long ne, int bits, void *scratch, cudaStream_t s);
 size_t edge_sort_scratch_bytes(long long ne);
 void launch_check_state(const double *m, const double *x3, const double *v3, long long n, unsigned *bad,
@@ -268,9 +270,10 @@ void launch_tau_mixed(const Level &L, const FFView &F, int ntiles, const TauPara
                       int32_t *near_ij, double *near_tau, long long near_cap, cudaStream_t s);
 int mixed_kick_blocks(int n);
 int mixed_kick_chunks(int n);
-void launch_kick_mixed(const Level &L, const FFView &F, const int32_t *label, const int32_t *koff, int nblocks,
-                       bool multi_chunk, double G, double eps2, double h, DevCounters *ctr, double *partial,
-                       cudaStream_t s);
+void launch_prep_kick(const Level &L, const FFView &F, const int32_t *order, const int32_t *root, double G,
+                      cudaStream_t s);
+void launch_kick_mixed(const Level &L, const FFView &F, const int32_t *order, const int32_t *koff, int nblocks,
+                       bool multi_chunk, double eps2, double h, DevCounters *ctr, double *partial, cudaStream_t s);
 
 // cc_small.cu
 void launch_small(const Level &L, const int32_t *members, const int32_t *comp_start, const int32_t *comp_size,

@@ -30,8 +30,7 @@ __global__ void k_prep_ff(Level L, FFView F, float G, int with_v)
         float hi[3], lo[3];
 #pragma unroll
         for (int c = 0; c < 3; ++c) {
-            hi[c] = __double2float_rn(xs[c]);
-            lo[c] = __double2float_rn(xs[c] - (double)hi[c]);
+            ff_split(xs[c], hi[c], lo[c]);
             ax = fmaxf(ax, fabsf(hi[c]));
         }
         F.pq[2 * k] = make_float4(hi[0], hi[1], hi[2], G * __double2float_rn(L.m[k]));
@@ -40,8 +39,7 @@ __global__ void k_prep_ff(Level L, FFView F, float G, int with_v)
             const double vs[3] = {L.vx[k], L.vy[k], L.vz[k]};
 #pragma unroll
             for (int c = 0; c < 3; ++c) {
-                hi[c] = __double2float_rn(vs[c]);
-                lo[c] = __double2float_rn(vs[c] - (double)hi[c]);
+                ff_split(vs[c], hi[c], lo[c]);
                 av = fmaxf(av, fabsf(hi[c]));
             }
             F.vq[2 * k] = make_float4(hi[0], hi[1], hi[2], 0.f);
@@ -65,6 +63,34 @@ void launch_prep_ff(const Level &L, const FFView &F, double G, bool with_v, cuda
     if (L.total <= 0) return;
     cudaMemsetAsync(F.maxes, 0, 2 * sizeof(float), s);
     k_prep_ff<<<(L.total + 255) / 256, 256, 0, s>>>(L, F, (float)G, with_v ? 1 : 0);
+    CC_COUNT_LAUNCH(1);
+}
+
+// positions (hi, G m), (lo) and labels in the root-sorted order of the
+// split: position t holds packed element order[t]
+__global__ void k_prep_kick(Level L, FFView F, const int32_t *order, const int32_t *root, float G)
+{
+    const int t = blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= L.total) return;
+    const int k = order[t];
+    if (L.gid[k] < 0) {
+        L.klab[t] = -1 - t;
+        return;
+    }
+    const double xs[3] = {L.x[k], L.y[k], L.z[k]};
+    float hi[3], lo[3];
+#pragma unroll
+    for (int c = 0; c < 3; ++c) ff_split(xs[c], hi[c], lo[c]);
+    F.pq[2 * t] = make_float4(hi[0], hi[1], hi[2], G * __double2float_rn(L.m[k]));
+    F.pq[2 * t + 1] = make_float4(lo[0], lo[1], lo[2], 0.f);
+    L.klab[t] = root[k];
+}
+
+void launch_prep_kick(const Level &L, const FFView &F, const int32_t *order, const int32_t *root, double G,
+                      cudaStream_t s)
+{
+    if (L.total <= 0) return;
+    k_prep_kick<<<(L.total + 255) / 256, 256, 0, s>>>(L, F, order, root, (float)G);
     CC_COUNT_LAUNCH(1);
 }
 
@@ -230,16 +256,22 @@ void launch_tau_mixed(const Level &L, const FFView &F, int ntiles, const TauPara
 }
 
 // ------------------------------------------------------------ kick, FP32
-// Grid: (set, i-tile, j-chunk).  Thread r of an i-tile accumulates
-// sum_j m_j (x_j - x_i) |x_j - x_i|^-3 over the chunk's j (labels differ)
-// in compensated FP32; the chunk's partial goes to scratch in FP64 unless
-// the set has a single chunk, in which case v is updated directly.
+// Works in the root-sorted order of the split (members of a component are
+// adjacent; rest-set members are their own components).  Grid: (set,
+// i-tile, j-chunk).  Thread r of an i-tile accumulates
+// sum_j G m_j (x_j - x_i) |x_j - x_i|^-3 over the chunk's j whose label
+// differs, in compensated FP32; a j-tile whose labels and the i-tile's are
+// all one component is skipped whole (sorted order: first == last label
+// means a uniform tile).  Partials go to scratch in FP64 unless the set has
+// a single chunk, in which case v is updated directly.
 constexpr int MK_T = 128;
 constexpr int MK_CHUNK_TILES = 8;  // j-tiles per chunk (1024 j)
 
 struct __align__(16) MixedKickSmem {
     float4 pq[2][2 * MK_T];  // (hi, Gm), (lo) per j, two stages
     int32_t lab[2][MK_T];
+    int32_t tiles[MK_CHUNK_TILES];
+    int32_t ntiles;
     uint64_t bar[2];
 };
 
@@ -253,7 +285,7 @@ __device__ __forceinline__ void mk_issue(MixedKickSmem &sm, int st, const FFView
     tma_load_1d(sm.lab[st], label + j0, cnt * 4u, &sm.bar[st]);
 }
 
-__global__ void __launch_bounds__(MK_T) k_kick_mixed(Level L, FFView F, const int32_t *label, const int32_t *koff,
+__global__ void __launch_bounds__(MK_T) k_kick_mixed(Level L, FFView F, const int32_t *order, const int32_t *koff,
                                                       float eps2, double h, DevCounters *ctr, double *partial)
 {
     __shared__ MixedKickSmem sm;
@@ -272,27 +304,41 @@ __global__ void __launch_bounds__(MK_T) k_kick_mixed(Level L, FFView F, const in
     const int tj0 = ch * MK_CHUNK_TILES, tj1 = min(ntile, tj0 + MK_CHUNK_TILES);
     const int il = ti * MK_T + tid;
     const bool iv = il < n;
-    const int i = start + il;
+    const int t = start + il;  // position in the sorted order
+    const int32_t *label = L.klab;
     if (tid == 0) {
         mbar_init(&sm.bar[0], 1);
         mbar_init(&sm.bar[1], 1);
         fence_mbar_init();
+        // tiles with at least one cross-component pair
+        const int ia = start + ti * MK_T, ib = start + min(n, (ti + 1) * MK_T) - 1;
+        const bool iu = label[ia] == label[ib];
+        int q = 0;
+        for (int tj = tj0; tj < tj1; ++tj) {
+            const int ja = start + tj * MK_T, jb = start + min(n, (tj + 1) * MK_T) - 1;
+            if (iu && label[ja] == label[jb] && label[ja] == label[ia]) continue;
+            sm.tiles[q++] = tj;
+        }
+        sm.ntiles = q;
     }
     __syncthreads();
-    if (tid == 0) mk_issue(sm, 0, F, label, start + tj0 * MK_T, min(MK_T, n - tj0 * MK_T));
+    const int nt = sm.ntiles;
+    if (tid == 0 && nt > 0) mk_issue(sm, 0, F, label, start + sm.tiles[0] * MK_T, min(MK_T, n - sm.tiles[0] * MK_T));
     float4 ip0 = make_float4(0, 0, 0, 0), ip1 = ip0;
     int li = 0;
     if (iv) {
-        ip0 = F.pq[2 * i];
-        ip1 = F.pq[2 * i + 1];
-        li = label[i];
+        ip0 = F.pq[2 * t];
+        ip1 = F.pq[2 * t + 1];
+        li = label[t];
     }
     float sx = 0.f, sy = 0.f, sz = 0.f, cx = 0.f, cy = 0.f, cz = 0.f;
     bool ok = true;
-    for (int tj = tj0; tj < tj1; ++tj) {
-        const int q = tj - tj0, st = q & 1;
-        if (tid == 0 && tj + 1 < tj1)
-            mk_issue(sm, st ^ 1, F, label, start + (tj + 1) * MK_T, min(MK_T, n - (tj + 1) * MK_T));
+    for (int q = 0; q < nt; ++q) {
+        const int tj = sm.tiles[q], st = q & 1;
+        if (tid == 0 && q + 1 < nt) {
+            const int tn = sm.tiles[q + 1];
+            mk_issue(sm, st ^ 1, F, label, start + tn * MK_T, min(MK_T, n - tn * MK_T));
+        }
         const bool got = mbar_wait(&sm.bar[st], (q >> 1) & 1, TMA_WAIT_CYCLES);
         if (__syncthreads_or(!got)) {
             ok = false;
@@ -302,7 +348,7 @@ __global__ void __launch_bounds__(MK_T) k_kick_mixed(Level L, FFView F, const in
         if (iv) {
 #pragma unroll 4
             for (int k = 0; k < jn; ++k) {
-                if (sm.lab[st][k] == li || tj * MK_T + k == il) continue;
+                if (sm.lab[st][k] == li) continue;  // same component (and self)
                 const float4 jp0 = sm.pq[st][2 * k], jp1 = sm.pq[st][2 * k + 1];
                 const float dx = (jp0.x - ip0.x) + (jp1.x - ip1.x);
                 const float dy = (jp0.y - ip0.y) + (jp1.y - ip1.y);
@@ -327,32 +373,35 @@ __global__ void __launch_bounds__(MK_T) k_kick_mixed(Level L, FFView F, const in
     if (!iv) return;
     const double ax = (double)sx - (double)cx, ay = (double)sy - (double)cy, az = (double)sz - (double)cz;
     if (nchunk == 1) {
-        L.vx[i] += h * ax;
-        L.vy[i] += h * ay;
-        L.vz[i] += h * az;
+        const int k = order[t];
+        L.vx[k] += h * ax;
+        L.vy[k] += h * ay;
+        L.vz[k] += h * az;
     } else {
-        // partial[(chunk * 3 + c) * cap + i]
+        // partial[(chunk * 3 + c) * cap + t]
         const size_t cap = (size_t)F.cap;
-        partial[((size_t)ch * 3 + 0) * cap + i] = ax;
-        partial[((size_t)ch * 3 + 1) * cap + i] = ay;
-        partial[((size_t)ch * 3 + 2) * cap + i] = az;
+        partial[((size_t)ch * 3 + 0) * cap + t] = ax;
+        partial[((size_t)ch * 3 + 1) * cap + t] = ay;
+        partial[((size_t)ch * 3 + 2) * cap + t] = az;
     }
 }
 
 // sum the chunk partials of multi-chunk sets in chunk order (FP64), v += h a
-__global__ void k_kick_reduce(Level L, FFView F, double h, const double *partial)
+__global__ void k_kick_reduce(Level L, FFView F, const int32_t *order, double h, const double *partial)
 {
-    const int k = blockIdx.x * blockDim.x + threadIdx.x;
-    if (k >= L.total || L.sidx[k] < 0) return;
+    const int t = blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= L.total) return;
+    const int k = order[t];
+    if (L.sidx[k] < 0) return;
     const int n = L.set_n[L.sidx[k]];
     const int nchunk = ((n + MK_T - 1) / MK_T + MK_CHUNK_TILES - 1) / MK_CHUNK_TILES;
     if (nchunk == 1) return;
     const size_t cap = (size_t)F.cap;
     double ax = 0.0, ay = 0.0, az = 0.0;
     for (int c = 0; c < nchunk; ++c) {
-        ax += partial[((size_t)c * 3 + 0) * cap + k];
-        ay += partial[((size_t)c * 3 + 1) * cap + k];
-        az += partial[((size_t)c * 3 + 2) * cap + k];
+        ax += partial[((size_t)c * 3 + 0) * cap + t];
+        ay += partial[((size_t)c * 3 + 1) * cap + t];
+        az += partial[((size_t)c * 3 + 2) * cap + t];
     }
     L.vx[k] += h * ax;
     L.vy[k] += h * ay;
@@ -371,16 +420,14 @@ int mixed_kick_chunks(int n)
     return (ntile + MK_CHUNK_TILES - 1) / MK_CHUNK_TILES;
 }
 
-void launch_kick_mixed(const Level &L, const FFView &F, const int32_t *label, const int32_t *koff, int nblocks,
-                       bool multi_chunk, double G, double eps2, double h, DevCounters *ctr, double *partial,
-                       cudaStream_t s)
+void launch_kick_mixed(const Level &L, const FFView &F, const int32_t *order, const int32_t *koff, int nblocks,
+                       bool multi_chunk, double eps2, double h, DevCounters *ctr, double *partial, cudaStream_t s)
 {
     if (nblocks <= 0) return;
-    (void)G;  // folded into the float masses (G m) by the prep kernel
-    k_kick_mixed<<<nblocks, MK_T, 0, s>>>(L, F, label, koff, (float)eps2, h, ctr, partial);
+    k_kick_mixed<<<nblocks, MK_T, 0, s>>>(L, F, order, koff, (float)eps2, h, ctr, partial);
     CC_COUNT_LAUNCH(1);
     if (multi_chunk) {
-        k_kick_reduce<<<(L.total + 255) / 256, 256, 0, s>>>(L, F, h, partial);
+        k_kick_reduce<<<(L.total + 255) / 256, 256, 0, s>>>(L, F, order, h, partial);
         CC_COUNT_LAUNCH(1);
     }
 }

@@ -38,9 +38,10 @@ __device__ __forceinline__ void k8_publish(K8Warp &S, int lane, const double st[
     if (ff) {
 #pragma unroll
         for (int c = 0; c < 6; ++c) {
-            const float hi = __double2float_rn(st[c]);
+            float hi, lo;
+            ff_split(st[c], hi, lo);
             S.f[c][lane] = hi;
-            S.f[6 + c][lane] = __double2float_rn(st[c] - (double)hi);
+            S.f[6 + c][lane] = lo;
         }
         S.f[12][lane] = __double2float_rn(st[6]);
         S.xm[lane] = fmaxf(fabsf(S.f[0][lane]), fmaxf(fabsf(S.f[1][lane]), fabsf(S.f[2][lane])));
@@ -64,6 +65,161 @@ __device__ __forceinline__ void k8_drift(double st[7], double dt, bool exact)
     }
 }
 
+// ------------------------------------------------------------ pair path
+// evolve_cc({a, b}, h0) of a two-body set in one thread.  The recursion of a
+// pair is a binary tree: a node at pivot h splits {a,b} (one tau); an edge
+// makes it a component visited twice at h/2 (its DKD is empty: no rest set,
+// no cross pair); no edge makes it a leaf, where both bodies form the rest
+// set: drift h/2, pair kick h, drift h/2.  The tree is walked with a bit
+// stack (bit d: the node at depth d has finished its first child).  a has the
+// smaller id, and the arithmetic is that of the level kernels, so the FP64
+// form is bit-identical to the oracle.
+struct PairCounters {
+    unsigned long long tau = 0, kick = 0, drift = 0, split = 0, comp = 0, fp64 = 0;
+    int maxd = 0;
+};
+
+constexpr long long PAIR_VISIT_LIMIT = 1ll << 26;  // work cap per pair path (error beyond)
+
+__device__ __forceinline__ bool pair_edge(const double A[7], const double B[7], double h, bool mixed,
+                                          const TauParams &P0, const MixedTauParams &Q0, PairCounters &pc,
+                                          DevCounters *ctr, int ga, int gb, int32_t *near_ij, double *near_tau,
+                                          long long near_cap)
+{
+    const double dx0 = __dsub_rn(A[0], B[0]), dx1 = __dsub_rn(A[1], B[1]), dx2 = __dsub_rn(A[2], B[2]);
+    const double dv0 = __dsub_rn(A[3], B[3]), dv1 = __dsub_rn(A[4], B[4]), dv2 = __dsub_rn(A[5], B[5]);
+    if (mixed) {
+        // FP64-formed differences rounded to FP32: relative error <= u
+        MixedTauParams Q = Q0;
+        Q.etah = (float)(P0.eta_outside ? P0.eta_in * P0.eta / h : P0.eta_in / h);
+        const int dec = tau_decide_fp32((float)dx0, (float)dx1, (float)dx2, (float)dv0, (float)dv1, (float)dv2,
+                                        Q.G * ((float)A[6] + (float)B[6]), 0.f, 0.f, Q);
+        if (dec >= 0) return dec == 1;
+    }
+    TauParams P = P0;
+    P.h = h;
+    const double tau = tau_fp64(dx0, dx1, dx2, dv0, dv1, dv2, A[6], B[6], P);
+    ++pc.fp64;
+    if (fabs(tau - h) < P.near_tol * h) {
+        const unsigned long long z = atomicAdd(&ctr->near_pairs, 1ull);
+        if ((long long)z < near_cap) {
+            near_ij[2 * z] = ga < gb ? ga : gb;
+            near_ij[2 * z + 1] = ga < gb ? gb : ga;
+            near_tau[z] = tau;
+        }
+    }
+    return tau < h;
+}
+
+__device__ __forceinline__ void pair_leaf(double A[7], double B[7], double h, bool mixed, const SmallParams &SP)
+{
+    const double hd = 0.5 * h;
+    k8_drift(A, hd, !mixed);
+    k8_drift(B, hd, !mixed);
+    if (!mixed || h < SP.h_fp64) {
+        // the oracle's row sums: a_a = (G m_b) r^-3 (x_b - x_a), a_b with -dx
+        const double dx0 = __dsub_rn(B[0], A[0]), dx1 = __dsub_rn(B[1], A[1]), dx2 = __dsub_rn(B[2], A[2]);
+        const double r2 = __dadd_rn(__dadd_rn(__dadd_rn(__dmul_rn(dx0, dx0), __dmul_rn(dx1, dx1)),
+                                              __dmul_rn(dx2, dx2)), SP.eps2);
+        const double rinv3 = __ddiv_rn(1.0, __dmul_rn(r2, __dsqrt_rn(r2)));
+        const double wa = __dmul_rn(__dmul_rn(SP.G, B[6]), rinv3), wb = __dmul_rn(__dmul_rn(SP.G, A[6]), rinv3);
+        A[3] = __dadd_rn(A[3], __dmul_rn(h, __dmul_rn(wa, dx0)));
+        A[4] = __dadd_rn(A[4], __dmul_rn(h, __dmul_rn(wa, dx1)));
+        A[5] = __dadd_rn(A[5], __dmul_rn(h, __dmul_rn(wa, dx2)));
+        B[3] = __dadd_rn(B[3], __dmul_rn(h, __dmul_rn(wb, -dx0)));
+        B[4] = __dadd_rn(B[4], __dmul_rn(h, __dmul_rn(wb, -dx1)));
+        B[5] = __dadd_rn(B[5], __dmul_rn(h, __dmul_rn(wb, -dx2)));
+    } else {
+        // FP32 pair force from the FP64-formed difference, rsqrt + one Newton step
+        const float fx = (float)(B[0] - A[0]), fy = (float)(B[1] - A[1]), fz = (float)(B[2] - A[2]);
+        const float r2 = fmaf(fz, fz, fmaf(fy, fy, fmaf(fx, fx, (float)SP.eps2)));
+        float ri = rsqrtf(r2);
+        ri = ri * fmaf(-0.5f * r2, ri * ri, 1.5f);
+        const float r3 = ri * ri * ri;
+        const double ga = SP.G * h * B[6], gb = SP.G * h * A[6];
+        const double ux = (double)(r3 * fx), uy = (double)(r3 * fy), uz = (double)(r3 * fz);
+        A[3] = fma(ga, ux, A[3]);
+        A[4] = fma(ga, uy, A[4]);
+        A[5] = fma(ga, uz, A[5]);
+        B[3] = fma(-gb, ux, B[3]);
+        B[4] = fma(-gb, uy, B[4]);
+        B[5] = fma(-gb, uz, B[5]);
+    }
+    k8_drift(A, hd, !mixed);
+    k8_drift(B, hd, !mixed);
+}
+
+// returns 0 = ok, DERR_DEPTH or DERR_SMALL_OVERFLOW (work cap)
+__device__ unsigned pair_path(double A[7], double B[7], double h0, int depth0, const SmallParams &SP,
+                              const TauParams &P, const MixedTauParams &Q, bool mixed, PairCounters &pc,
+                              DevCounters *ctr, int ga, int gb, int32_t *near_ij, double *near_tau,
+                              long long near_cap)
+{
+    unsigned long long pend = 0ull;
+    int d = 0;
+    for (long long visit = 0; visit < PAIR_VISIT_LIMIT; ++visit) {
+        const double h = ldexp(h0, -d);
+        ++pc.split;
+        ++pc.tau;
+        if (depth0 + d > pc.maxd) pc.maxd = depth0 + d;
+        if (pair_edge(A, B, h, mixed, P, Q, pc, ctr, ga, gb, near_ij, near_tau, near_cap)) {
+            ++pc.comp;
+            if (depth0 + d + 1 > SP.max_depth || d + 1 >= 62) return DERR_DEPTH;
+            ++d;
+            continue;
+        }
+        pair_leaf(A, B, h, mixed, SP);
+        ++pc.kick;
+        pc.drift += 4;
+        bool done = true;
+        while (d > 0) {
+            --d;
+            if (!((pend >> d) & 1ull)) {
+                pend |= 1ull << d;
+                ++d;
+                done = false;
+                break;
+            }
+            pend &= ~(1ull << d);
+        }
+        if (done) return 0u;
+    }
+    return DERR_SMALL_OVERFLOW;
+}
+
+// Hand every two-body set {lane, partner} (leader = the lower lane) to the
+// pair path for its sub-recursion at pivot hsub; states move through shared
+// memory.  Returns a device error code (0 = ok) uniform over the warp.
+__device__ __forceinline__ unsigned k8_pair_handoff(K8Warp &S, int lane, double st[7], uint32_t cm, bool is_sub,
+                                                    double hsub, int dsub, const SmallParams &SP,
+                                                    const TauParams &P, const MixedTauParams &Q, bool mixed,
+                                                    PairCounters &pc, DevCounters *ctr, const Level &L,
+                                                    const int32_t *members, int base, int32_t *near_ij,
+                                                    double *near_tau, long long near_cap)
+{
+    k8_publish(S, lane, st, false);
+    const uint32_t me = 1u << lane;
+    const bool leader = is_sub && lane == __ffs(cm) - 1;
+    unsigned err = 0u;
+    if (leader) {
+        const int j = __ffs(cm & ~me) - 1;
+        double B[7];
+#pragma unroll
+        for (int c = 0; c < 7; ++c) B[c] = S.d[c][j];
+        err = pair_path(st, B, hsub, dsub, SP, P, Q, mixed, pc, ctr, L.gid[members[base + lane]],
+                        L.gid[members[base + j]], near_ij, near_tau, near_cap);
+#pragma unroll
+        for (int c = 0; c < 6; ++c) S.d[c][j] = B[c];
+    }
+    __syncwarp();
+    if (is_sub && !leader) {
+#pragma unroll
+        for (int c = 0; c < 6; ++c) st[c] = S.d[c][lane];
+    }
+    const unsigned e = __reduce_or_sync(0xffffffffu, err);
+    return e;
+}
+
 __global__ void __launch_bounds__(K8_WARPS * 32) k_small(Level L, const int32_t *members, const int32_t *comp_start,
                                                           const int32_t *comp_size, const int32_t *slist, int ns,
                                                           SmallParams SP, DevCounters *ctr, int *queue,
@@ -74,7 +230,8 @@ __global__ void __launch_bounds__(K8_WARPS * 32) k_small(Level L, const int32_t 
     K8Warp &S = sw[w];
     const uint32_t me = 1u << lane;
     uint32_t mk[K8_MAXD], cmk[K8_MAXD];
-    unsigned char ph[K8_MAXD];
+    unsigned char ph[K8_MAXD], pm[K8_MAXD];
+    PairCounters pc;
     unsigned long long c_tau = 0, c_kick = 0, c_drift = 0, c_split = 0, c_comp = 0, c_kep = 0, c_fp64 = 0;
     int maxd = 0;
     const bool mixed = SP.precision == CC_PREC_MIXED;
@@ -103,6 +260,16 @@ __global__ void __launch_bounds__(K8_WARPS * 32) k_small(Level L, const int32_t 
         ph[0] = 0;
         bool bad = false;
         if (SP.depth0 > maxd) maxd = SP.depth0;
+        if (n == 2) {
+            // a two-body component: its whole recursion on the pair path
+            const unsigned e = k8_pair_handoff(S, lane, st, 3u, act, SP.h0, SP.depth0, SP, P, Q, mixed, pc, ctr, L,
+                                               members, base, near_ij, near_tau, near_cap);
+            if (e) {
+                raise_err(ctr, e);
+                bad = true;
+            }
+            k = -1;
+        }
         while (k >= 0 && !bad) {
             const double h = ldexp(SP.h0, -k);
             const uint32_t mine = mk[k];
@@ -177,7 +344,20 @@ __global__ void __launch_bounds__(K8_WARPS * 32) k_small(Level L, const int32_t 
                 }
                 ph[k] = 1;
                 const bool sub = csz >= 2 && !(SP.kepler && csz == 2);
-                if (__any_sync(FULL, sub)) {
+                // every sub-recursion at this level is a pair: run them on the
+                // pair path (first half now, second half after the DKD)
+                pm[k] = __all_sync(FULL, !sub || csz == 2) ? 1 : 0;
+                if (pm[k] && __any_sync(FULL, sub)) {
+                    const unsigned e = k8_pair_handoff(S, lane, st, cm, sub, 0.5 * h, SP.depth0 + k + 1, SP, P, Q,
+                                                       mixed, pc, ctr, L, members, base, near_ij, near_tau,
+                                                       near_cap);
+                    if (e) {
+                        raise_err(ctr, e);
+                        bad = true;
+                        break;
+                    }
+                } else if (__any_sync(FULL, sub)) {
+                    pm[k] = 0;
                     if (SP.depth0 + k + 1 > SP.max_depth || k + 1 >= K8_MAXD) {
                         bad = true;
                         raise_err(ctr, DERR_DEPTH);
@@ -279,10 +459,21 @@ __global__ void __launch_bounds__(K8_WARPS * 32) k_small(Level L, const int32_t 
                 }
                 ph[k] = 2;
                 if (__any_sync(FULL, sub)) {
-                    mk[k + 1] = sub ? cm : 0u;
-                    ph[k + 1] = 0;
-                    ++k;
-                    continue;
+                    if (pm[k]) {
+                        const unsigned e = k8_pair_handoff(S, lane, st, cm, sub, 0.5 * h, SP.depth0 + k + 1, SP, P,
+                                                           Q, mixed, pc, ctr, L, members, base, near_ij, near_tau,
+                                                           near_cap);
+                        if (e) {
+                            raise_err(ctr, e);
+                            bad = true;
+                            break;
+                        }
+                    } else {
+                        mk[k + 1] = sub ? cm : 0u;
+                        ph[k + 1] = 0;
+                        ++k;
+                        continue;
+                    }
                 }
             }
             --k;
@@ -293,8 +484,10 @@ __global__ void __launch_bounds__(K8_WARPS * 32) k_small(Level L, const int32_t 
         }
         __syncwarp();
     }
-    // per-lane counters -> one atomic per warp and counter
-    unsigned long long v[7] = {c_tau, c_kick, c_drift, c_split, c_comp, c_kep, c_fp64};
+    // per-lane counters (lockstep levels + pair paths) -> one atomic per warp
+    if (pc.maxd > maxd) maxd = pc.maxd;
+    unsigned long long v[7] = {c_tau + pc.tau, c_kick + pc.kick, c_drift + pc.drift, c_split + pc.split,
+                               c_comp + pc.comp, c_kep, c_fp64 + pc.fp64};
 #pragma unroll
     for (int i = 0; i < 7; ++i)
         for (int o = 16; o > 0; o >>= 1) v[i] += __shfl_down_sync(FULL, v[i], o);

@@ -216,55 +216,126 @@ def salpeter_masses(n: int, seed: int, stream: int, lo: float = 0.1, hi: float =
     return mm / mm.sum()
 
 
-def box_fractal(n: int, seed: int = 1, D: float = 1.6, Q: float = 0.3, imf: bool = True,
-                exact_scale: bool | None = None):
-    """Box-fractal cluster in the manner of Goodwin & Whitworth (2004).
+def _gauss(seed: int, stream: int, n: int) -> np.ndarray:
+    """n standard normal deviates (Box-Muller on two uniform streams)."""
+    u1 = uniform(seed, stream, n)
+    u2 = uniform(seed, stream + 1, n)
+    return np.sqrt(-2.0 * np.log(1.0 - u1)) * np.cos(2.0 * math.pi * u2)
 
-    A cube of side 2 is divided into 2^3 sub-cubes; each child survives as
-    a parent of the next generation with probability 2^(D-3), is jittered
-    by noise of a tenth of its cell size, and inherits its parent's
-    velocity plus a Gaussian component whose scale halves per generation.
-    Generations continue until enough leaves exist inside the unit sphere;
-    n of them are drawn, masses follow a Salpeter IMF (0.1-100, total 1),
-    and the result is scaled to virial ratio Q (sub-virial, clumpy velocities).
-    """
-    keep = 2.0 ** (D - 3.0)
-    pos = np.zeros((1, 3))
-    vel = np.zeros((1, 3))
-    side = 2.0
-    gen = 0
+
+def box_fractal_raw(n: int, seed: int = 1, D: float = 1.6, max_gen: int = 16):
+    """Unscaled box fractal in the manner of Goodwin & Whitworth (2004).
+
+    A cube of side 2 centred on the origin holds the first parent.  Each
+    generation halves the cell size: every parent gets 2^3 children at the
+    centres of its sub-cubes, displaced by uniform noise of a tenth of the
+    new cell size; a child survives as a parent of the next generation with
+    probability 2^(D-3).  Velocities: the first generation draws a Gaussian
+    velocity, every later child inherits its parent's velocity plus a
+    Gaussian component whose scale halves each generation (correlated
+    clump velocities).  Generations continue until the children inside the
+    unit sphere number at least 1.5 n; n of them are drawn at random.
+    Returns positions (3, n) and velocities (3, n), not yet scaled."""
     offs = np.array([[i, j, k] for i in (-1, 1) for j in (-1, 1) for k in (-1, 1)], dtype=float)
-    while True:
-        gen += 1
-        side *= 0.5
-        npar = pos.shape[0]
-        child = (pos[:, None, :] + 0.5 * side * offs[None, :, :]).reshape(-1, 3)
-        cvel = np.repeat(vel, 8, axis=0)
-        nc = child.shape[0]
-        u = uniform(seed, 100 + 10 * gen, 7 * nc).reshape(7, nc)
-        child = child + 0.1 * side * (u[0:3].T - 0.5)
-        g = np.sqrt(-2.0 * np.log(1.0 - u[3:6])) * np.cos(2.0 * math.pi * u[6])[None, :]
-        cvel = cvel + (0.5 ** gen) * g.T
-        inside = (child * child).sum(axis=1) < 1.0
-        if inside.sum() >= 1.5 * n or gen > 12:
-            pos, vel = child[inside], cvel[inside]
-            break
-        alive = u[3] < keep if gen > 1 else np.ones(nc, dtype=bool)
-        # keep one parent at least so the tree never dies out
-        if not alive.any():
-            alive[0] = True
-        pos, vel = child[alive], cvel[alive]
-        if npar == 0:
-            break
-    if pos.shape[0] < n:
-        raise ValueError("fractal tree too small for n")
-    pick = np.argsort(uniform(seed, 9000, pos.shape[0]), kind="stable")[:n]
-    x3 = np.ascontiguousarray(pos[pick].T)
-    v3 = np.ascontiguousarray(vel[pick].T)
+    keep = 2.0 ** (D - 3.0)
+    for attempt in range(50):
+        pos = np.zeros((1, 3))
+        vel = np.zeros((1, 3))
+        side = 2.0
+        leaves = None
+        for gen in range(1, max_gen + 1):
+            side *= 0.5
+            child = (pos[:, None, :] + 0.5 * side * offs[None, :, :]).reshape(-1, 3)
+            cvel = np.repeat(vel, 8, axis=0)
+            nc = child.shape[0]
+            st = 100 * attempt + 10 * gen
+            jit = np.stack([uniform(seed, st + q, nc) for q in range(3)], axis=1) - 0.5
+            child = child + 0.1 * side * jit
+            g = np.stack([_gauss(seed, 5000 + st + 2 * q, nc) for q in range(3)], axis=1)
+            cvel = cvel + (0.5 ** (gen - 1)) * g
+            inside = (child * child).sum(axis=1) < 1.0
+            if inside.sum() >= 1.5 * n:
+                leaves = (child[inside], cvel[inside])
+                break
+            alive = uniform(seed, 9000 + st, nc) < keep if gen > 1 else np.ones(nc, dtype=bool)
+            if not alive.any():
+                break
+            pos, vel = child[alive], cvel[alive]
+        if leaves is not None:
+            pick = np.argsort(uniform(seed, 777 + attempt, leaves[0].shape[0]), kind="stable")[:n]
+            return np.ascontiguousarray(leaves[0][pick].T), np.ascontiguousarray(leaves[1][pick].T)
+    raise ValueError("box fractal: branching process died out repeatedly")
+
+
+def box_fractal(n: int, seed: int = 1, D: float = 1.6, Q: float = 0.3, imf: bool = True,
+                W: float | None = None):
+    """Box-fractal cluster (Goodwin & Whitworth 2004 recipe, box_fractal_raw)
+    with Salpeter masses (0.1-100, total 1) in the centre-of-mass frame,
+    scaled to virial ratio Q and E = -1/4.  W, the potential energy of the
+    unscaled configuration with these masses, may be passed in (computed
+    elsewhere for large n); otherwise it is summed exactly here."""
+    x3, v3 = box_fractal_raw(n, seed=seed, D=D)
     m = salpeter_masses(n, seed, 9100) if imf else np.full(n, 1.0 / n)
     x3, v3 = _com_frame(m, x3, v3)
-    if exact_scale is None:
-        exact_scale = n <= 20000
-    W = None if exact_scale else -0.5 * float(m.sum()) ** 2 / 0.6
-    x3, v3 = scale_to_nbody_units(m, x3, v3, Q=Q, exact=exact_scale, W=W)
+    x3, v3 = scale_to_nbody_units(m, x3, v3, Q=Q, exact=W is None, W=W)
     return m, x3, v3
+
+
+def hierarchical_triple(seed: int, stream: int, G: float = 1.0):
+    """A hierarchical triple in its own N-body units (M = 1): inner binary
+    (a_in = 1, e_in ~ U[0, 0.5]) orbited by a third body with outer-to-inner
+    period ratio ~ logU[10, 1000], e_out ~ U[0, 0.5], isotropic mutual
+    inclination, uniform mean anomalies; masses (0.4, 0.3, 0.3)."""
+    u = uniform(seed, stream, 12)
+    m1, m2, m3 = 0.4, 0.3, 0.3
+    e_in, e_out = 0.5 * u[0], 0.5 * u[1]
+    ratio = math.exp(math.log(10.0) + (math.log(1000.0) - math.log(10.0)) * u[2])
+    a_in = 1.0
+    # P ~ sqrt(a^3 / M): a_out from the period ratio
+    a_out = a_in * (ratio ** 2 * (m1 + m2 + m3) / (m1 + m2)) ** (1.0 / 3.0)
+    Ei = _mean_anomaly_E(seed, stream + 1000, np.array([e_in]))[0]
+    Eo = _mean_anomaly_E(seed, stream + 2000, np.array([e_out]))[0]
+    r_in, v_in = orbit_state(m1, m2, a_in, e_in, Ei, inc=math.acos(2 * u[3] - 1), node=2 * math.pi * u[4],
+                             peri=2 * math.pi * u[5], G=G)
+    r_out, v_out = orbit_state(m1 + m2, m3, a_out, e_out, Eo, inc=math.acos(2 * u[6] - 1),
+                               node=2 * math.pi * u[7], peri=2 * math.pi * u[8], G=G)
+    mi = m1 + m2
+    M = mi + m3
+    x = np.zeros((3, 3))
+    v = np.zeros((3, 3))
+    # inner COM at (m3/M) r_out, third body at -(mi/M) r_out
+    ci, cv = (m3 / M) * r_out, (m3 / M) * v_out
+    x[:, 0] = ci + (m2 / mi) * r_in
+    x[:, 1] = ci - (m1 / mi) * r_in
+    x[:, 2] = -(mi / M) * r_out
+    v[:, 0] = cv + (m2 / mi) * v_in
+    v[:, 1] = cv - (m1 / mi) * v_in
+    v[:, 2] = -(mi / M) * v_out
+    m = np.array([m1, m2, m3])
+    x, v = _com_frame(m, x, v)
+    # N-body units: scale lengths so E = -1/4 (virial ratio is what it is)
+    T = 0.5 * float((m * (v * v).sum(axis=0)).sum())
+    Wt = potential_energy(m, x)
+    beta = (T + Wt) / -0.25
+    return m, np.ascontiguousarray(x * beta), np.ascontiguousarray(v / math.sqrt(beta))
+
+
+def small_systems(nsys: int = 4096, seed: int = 1, n_min: int = 3, n_max: int = 512):
+    """A batch of independent small systems, each in its own N-body units:
+    a fair coin picks a hierarchical triple or an equal-mass Plummer clump
+    with round(logU[n_min, n_max]) bodies.  Returns (m, x3, v3, sys_off)
+    with system s occupying ids [sys_off[s], sys_off[s+1])."""
+    coin = uniform(seed, 31, nsys)
+    sizes = np.rint(np.exp(np.log(n_min) + (np.log(n_max) - np.log(n_min)) * uniform(seed, 32, nsys))).astype(int)
+    ms, xs, vs, off = [], [], [], [0]
+    for s in range(nsys):
+        if coin[s] < 0.5:
+            m, x, v = hierarchical_triple(seed, 100000 + 37 * s)
+        else:
+            m, x, v = plummer(int(sizes[s]), seed=seed * 100003 + s, exact_scale=True)
+        ms.append(m)
+        xs.append(x)
+        vs.append(v)
+        off.append(off[-1] + m.shape[0])
+    return (np.concatenate(ms), np.ascontiguousarray(np.concatenate(xs, axis=1)),
+            np.ascontiguousarray(np.concatenate(vs, axis=1)), np.array(off, dtype=np.int64))
