@@ -55,7 +55,9 @@ typedef struct {
                           the persistent small-component kernel; 0 disables it         */
     int    eta_outside;/* 0: eta inside T and dT/dt (default reading); 1: eta
                           multiplies the min of Eq. (tauij) literally                  */
-    int    reserved[5];
+    int    autotune;   /* 1: launch shapes tuned online per size bin (default); 0: a
+                          fixed rule (run-to-run identical rounding in mixed mode)   */
+    int    reserved[4];
 } cc_params;
 
 typedef struct {
@@ -89,7 +91,7 @@ typedef struct {
 typedef struct cc_ctx cc_ctx;
 
 /* Fill *p with defaults: G=1, eps=0, eta=0.03, dt=1/64, h_fp64=0,
- * near_tol=1e-12, FP64, kepler off, max_depth=64, s_small=32. */
+ * near_tol=1e-12, FP64, kepler off, max_depth=64, s_small=32, autotune on. */
 int cc_default_params(cc_params *p);
 
 /* Create a context holding n particles (Sec. 2.1: masses m_i, positions q_i,

@@ -26,7 +26,7 @@ class Params(C.Structure):
     _fields_ = [("G", C.c_double), ("eps", C.c_double), ("eta", C.c_double), ("dt", C.c_double),
                 ("h_fp64", C.c_double), ("near_tol", C.c_double), ("precision", C.c_int),
                 ("kepler", C.c_int), ("max_depth", C.c_int), ("s_small", C.c_int),
-                ("eta_outside", C.c_int), ("reserved", C.c_int * 5)]
+                ("eta_outside", C.c_int), ("autotune", C.c_int), ("reserved", C.c_int * 4)]
 
 
 class Stats(C.Structure):

@@ -38,8 +38,12 @@ thread_local std::string g_init_err;
 struct LevelAlloc {
     Level L{};
     FFView F{};
-    long long kblocks = 0;   // mixed-kick blocks of the current layout
-    int kchunks_max = 0;     // largest j-chunk count of a set
+    // launch-shape variants: block prefixes over the sets (device) and the
+    // total blocks (host) of every tunable shape, for the current layout
+    int32_t *tau_off[N_TAU_VAR] = {}, *k64_off[N_K64_VAR] = {}, *mk_off[N_MK_VAR] = {};
+    long long tau_blocks[N_TAU_VAR] = {}, k64_blocks[N_K64_VAR] = {}, mk_blocks[N_MK_VAR] = {};
+    int mk_chunks_max[N_MK_VAR] = {};
+    long long pairs = 0;     // sum n(n-1)/2 over the sets (work unit of the tuner)
     int cap = 0;      // element capacity (excluding PAD_TAIL)
     int set_cap = 0;  // set-array capacity
     void *block = nullptr;
@@ -58,6 +62,33 @@ struct LevelAlloc {
     int info_cap = 0;
     cudaEvent_t ev_ready = nullptr, ev_small = nullptr;  // side-stream joins
 };
+
+// ------------------------------------------------------------ autotuner
+// Online tuner of launch shapes per (kernel, size bin): the first launches
+// of a bin try each variant (preference order first) while CUDA events time
+// them; once every variant has TUNE_TRIALS timed launches, the one with the
+// least time per pair is kept for the bin.  Results do not depend on the
+// choice except through the rounding order of the mixed kick's j-chunks.
+enum TuneKind { TK_TAU64 = 0, TK_TAUMIX = 1, TK_K64 = 2, TK_MK = 3, TK_N = 4 };
+constexpr int TUNE_BINS = 40, TUNE_MAXV = 3, TUNE_TRIALS = 1;
+constexpr int TUNE_NVAR[TK_N] = {N_TAU_VAR, N_TAU_VAR, N_K64_VAR, N_MK_VAR};
+
+struct TuneCell {
+    double ms[TUNE_MAXV] = {0, 0, 0}, work[TUNE_MAXV] = {0, 0, 0};
+    int picked[TUNE_MAXV] = {0, 0, 0}, timed[TUNE_MAXV] = {0, 0, 0};
+    int best = -1;
+};
+
+struct Tuner {
+    TuneCell cell[TK_N][TUNE_BINS];
+};
+
+static int tune_bin(long long work)
+{
+    int b = 0;
+    while (b < TUNE_BINS - 1 && (2ll << b) <= work) ++b;
+    return b;
+}
 
 }  // namespace
 
@@ -93,27 +124,37 @@ struct cc_ctx {
     // optional per-launch event timing of the tau and kick kernels
     bool timing = false;
     std::vector<cudaEvent_t> evs;
-    std::vector<int> ev_kind;  // 0 = tau, 1 = kick, per event pair
+    struct EvRec {
+        int kind;   // 0 = tau, 1 = kick, 2 = small-component kernel
+        int tkind;  // tuner kernel (-1 = none)
+        int bin, var;
+        double work;
+    };
+    std::vector<EvRec> ev_rec;  // one per event pair
+    Tuner tuner;
+    bool p_autotune = true;
     size_t ev_used = 0;
     cc_timing_t tm{};
     unsigned long long launch_mark = 0;
 };
 
-// record the start of a timed launch; returns the pair index or -1
-static int ev_begin(cc_ctx *c, int kind, cudaStream_t st = nullptr)
+// record the start of a timed launch (user timing on, or a tuner sample);
+// returns the pair index or -1
+static int ev_begin(cc_ctx *c, int kind, cudaStream_t st = nullptr, int tkind = -1, int bin = 0, int var = 0,
+                    double work = 0.0)
 {
     if (!st) st = c->stream;
-    if (!c->timing) return -1;
+    if (!c->timing && tkind < 0) return -1;
     if (c->ev_used + 2 > c->evs.size()) {
         for (int k = 0; k < 64; ++k) {
             cudaEvent_t e;
             cudaEventCreate(&e);
             c->evs.push_back(e);
         }
-        c->ev_kind.resize(c->evs.size() / 2);
+        c->ev_rec.resize(c->evs.size() / 2);
     }
     const int pair = (int)(c->ev_used / 2);
-    c->ev_kind[pair] = kind;
+    c->ev_rec[pair] = {kind, tkind, bin, var, work};
     cudaEventRecord(c->evs[c->ev_used], st);
     c->ev_used += 2;
     return pair;
@@ -130,10 +171,18 @@ static void ev_resolve(cc_ctx *c)
     for (size_t q = 0; q < c->ev_used / 2; ++q) {
         float ms = 0.f;
         cudaEventElapsedTime(&ms, c->evs[2 * q], c->evs[2 * q + 1]);
-        if (c->ev_kind[q] == 0) {
+        const cc_ctx::EvRec &r = c->ev_rec[q];
+        if (r.tkind >= 0) {
+            TuneCell &t = c->tuner.cell[r.tkind][r.bin];
+            t.ms[r.var] += ms;
+            t.work[r.var] += r.work;
+            t.timed[r.var]++;
+        }
+        if (!c->timing) continue;
+        if (r.kind == 0) {
             c->tm.tau_ms += ms;
             c->tm.tau_launches++;
-        } else if (c->ev_kind[q] == 1) {
+        } else if (r.kind == 1) {
             c->tm.kick_ms += ms;
             c->tm.kick_launches++;
         } else {
@@ -197,6 +246,52 @@ static int copy_out(cc_ctx *c, void *dst, const void *src, size_t bytes)
 }
 
 static int align_up(int v, int a) { return (v + a - 1) / a * a; }
+
+// Launch shape for a kernel of the given kind on a level.  Returns the
+// variant; *timed tells whether this launch is a tuner sample.  Without
+// autotuning (or before any sample) a rule picks the largest shape that
+// still gives every SM a few blocks.
+static int tune_pick(cc_ctx *c, int tkind, const long long *blocks, long long work, int *bin_out, bool *timed)
+{
+    const int nv = TUNE_NVAR[tkind];
+    int rule = 0;
+    for (int v = nv - 1; v >= 0; --v)
+        if (blocks[v] >= 3ll * c->nsm) {
+            rule = v;
+            break;
+        }
+    const int bin = tune_bin(work);
+    *bin_out = bin;
+    *timed = false;
+    if (!c->p_autotune) return rule;
+    TuneCell &t = c->tuner.cell[tkind][bin];
+    if (t.best >= 0) return t.best;
+    bool all = true;
+    for (int v = 0; v < nv; ++v) all = all && t.timed[v] >= TUNE_TRIALS;
+    if (all) {
+        int best = 0;
+        double bq = 1e300;
+        for (int v = 0; v < nv; ++v) {
+            const double q = t.ms[v] / (t.work[v] > 0 ? t.work[v] : 1.0);
+            if (q < bq) {
+                bq = q;
+                best = v;
+            }
+        }
+        t.best = best;
+        return best;
+    }
+    // explore: the rule's choice first, then the others, fewest picks first
+    int pick = rule, fewest = t.picked[rule];
+    for (int v = 0; v < nv; ++v)
+        if (t.picked[v] < fewest) {
+            fewest = t.picked[v];
+            pick = v;
+        }
+    t.picked[pick]++;
+    *timed = true;
+    return pick;
+}
 
 static void free_level(LevelAlloc &a)
 {
@@ -269,22 +364,25 @@ static int ensure_level(cc_ctx *c, LevelAlloc &a, int need, int nsets)
         if (a.setblock) cudaFree(a.setblock);
         a.setblock = nullptr;
         int sc = align_up(nsets + 2, 256);
-        if (cudaMalloc(&a.setblock, (size_t)sc * 4 * 5) != cudaSuccess) {
+        if (cudaMalloc(&a.setblock, (size_t)sc * 4 * (2 + N_TAU_VAR + N_K64_VAR + N_MK_VAR)) != cudaSuccess) {
             cudaGetLastError();
             return fail(c, CC_E_NOMEM, "device allocation failed (set arrays)");
         }
         if (a.h_sets) cudaFreeHost(a.h_sets);
         a.h_sets = nullptr;
-        if (cudaMallocHost(&a.h_sets, (size_t)sc * 4 * 5) != cudaSuccess) {
+        if (cudaMallocHost(&a.h_sets, (size_t)sc * 4 * (2 + N_TAU_VAR + N_K64_VAR + N_MK_VAR)) != cudaSuccess) {
             cudaGetLastError();
             return fail(c, CC_E_NOMEM, "pinned host allocation failed (set arrays)");
         }
         int32_t *sq = (int32_t *)a.setblock;
         a.L.set_start = sq; sq += sc;
         a.L.set_n = sq; sq += sc;
-        a.L.tile_off = sq; sq += sc;
-        a.L.itile_off = sq; sq += sc;
-        a.L.koff = sq;
+        for (int v = 0; v < N_TAU_VAR; ++v) { a.tau_off[v] = sq; sq += sc; }
+        for (int v = 0; v < N_K64_VAR; ++v) { a.k64_off[v] = sq; sq += sc; }
+        for (int v = 0; v < N_MK_VAR; ++v) { a.mk_off[v] = sq; sq += sc; }
+        a.L.tile_off = a.tau_off[N_TAU_VAR - 1];
+        a.L.itile_off = a.k64_off[1];
+        a.L.koff = a.mk_off[1];
         a.set_cap = sc;
     }
     // the segmentation scratch is shared by all levels: size for the largest
@@ -304,41 +402,51 @@ static int ensure_level(cc_ctx *c, LevelAlloc &a, int need, int nsets)
 // upload the set layout (sizes -> aligned starts, tile prefixes); returns
 // the packed total through L.total
 struct SetLayout {
-    std::vector<int32_t> start, n, toff, ioff, koff;
+    std::vector<int32_t> start, n;
+    std::vector<int32_t> tau_off[N_TAU_VAR], k64_off[N_K64_VAR], mk_off[N_MK_VAR];
+    long long tau_blocks[N_TAU_VAR] = {}, k64_blocks[N_K64_VAR] = {}, mk_blocks[N_MK_VAR] = {};
+    int mk_chunks_max[N_MK_VAR] = {};
+    long long pairs = 0;
     int total = 0;
-    long long tiles = 0, itiles = 0, kblocks = 0;
-    int kchunks_max = 0;
 };
 
+// block prefixes of every launch-shape variant: triangular tau tiles,
+// FP64-kick i-tiles, mixed-kick (i-tile, j-chunk) blocks
 static void make_layout(const std::vector<int32_t> &sizes, SetLayout &S)
 {
     const size_t ns = sizes.size();
     S.start.resize(ns);
     S.n = sizes;
-    S.toff.resize(ns + 1);
-    S.ioff.resize(ns + 1);
-    S.koff.resize(ns + 1);
+    for (auto &v : S.tau_off) v.assign(ns + 1, 0);
+    for (auto &v : S.k64_off) v.assign(ns + 1, 0);
+    for (auto &v : S.mk_off) v.assign(ns + 1, 0);
     int pos = 0;
-    long long tt = 0, it = 0, kb = 0;
+    long long tb[N_TAU_VAR] = {}, kb[N_K64_VAR] = {}, mb[N_MK_VAR] = {};
+    S.pairs = 0;
     for (size_t s = 0; s < ns; ++s) {
         S.start[s] = pos;
         pos += align_up(sizes[s], SET_ALIGN);
-        S.toff[s] = (int32_t)tt;
-        S.ioff[s] = (int32_t)it;
-        S.koff[s] = (int32_t)kb;
-        const long long nt = (sizes[s] + TAU_TILE - 1) / TAU_TILE;
-        tt += nt * (nt + 1) / 2;
-        it += (sizes[s] + KICK_TILE - 1) / KICK_TILE;
-        kb += mixed_kick_blocks(sizes[s]);
-        S.kchunks_max = std::max(S.kchunks_max, mixed_kick_chunks(sizes[s]));
+        const long long n = sizes[s];
+        S.pairs += n * (n - 1) / 2;
+        for (int v = 0; v < N_TAU_VAR; ++v) {
+            S.tau_off[v][s] = (int32_t)tb[v];
+            const long long nt = (n + TAU_VAR_T[v] - 1) / TAU_VAR_T[v];
+            tb[v] += nt * (nt + 1) / 2;
+        }
+        for (int v = 0; v < N_K64_VAR; ++v) {
+            S.k64_off[v][s] = (int32_t)kb[v];
+            kb[v] += (n + K64_VAR_T[v] - 1) / K64_VAR_T[v];
+        }
+        for (int v = 0; v < N_MK_VAR; ++v) {
+            S.mk_off[v][s] = (int32_t)mb[v];
+            mb[v] += mixed_kick_blocks((int)n, MK_VAR_CHUNK[v]);
+            S.mk_chunks_max[v] = std::max(S.mk_chunks_max[v], mixed_kick_chunks((int)n, MK_VAR_CHUNK[v]));
+        }
     }
-    S.toff[ns] = (int32_t)tt;
-    S.ioff[ns] = (int32_t)it;
-    S.koff[ns] = (int32_t)kb;
+    for (int v = 0; v < N_TAU_VAR; ++v) { S.tau_off[v][ns] = (int32_t)tb[v]; S.tau_blocks[v] = tb[v]; }
+    for (int v = 0; v < N_K64_VAR; ++v) { S.k64_off[v][ns] = (int32_t)kb[v]; S.k64_blocks[v] = kb[v]; }
+    for (int v = 0; v < N_MK_VAR; ++v) { S.mk_off[v][ns] = (int32_t)mb[v]; S.mk_blocks[v] = mb[v]; }
     S.total = pos;
-    S.tiles = tt;
-    S.itiles = it;
-    S.kblocks = kb;
 }
 
 static int upload_layout(cc_ctx *c, LevelAlloc &a, const SetLayout &S)
@@ -348,15 +456,24 @@ static int upload_layout(cc_ctx *c, LevelAlloc &a, const SetLayout &S)
     // one pinned staging block laid out like the device set arrays (stride
     // set_cap), copied in one asynchronous transfer
     const int sc = a.set_cap;
-    std::memcpy(a.h_sets, S.start.data(), ns * 4);
-    std::memcpy(a.h_sets + sc, S.n.data(), ns * 4);
-    std::memcpy(a.h_sets + 2 * sc, S.toff.data(), (ns + 1) * 4);
-    std::memcpy(a.h_sets + 3 * sc, S.ioff.data(), (ns + 1) * 4);
-    std::memcpy(a.h_sets + 4 * sc, S.koff.data(), (ns + 1) * 4);
-    CC_CUDA(c, cudaMemcpyAsync(a.L.set_start, a.h_sets, (size_t)(4 * sc + ns + 1) * 4, cudaMemcpyHostToDevice,
-                               c->stream));
-    a.kblocks = S.kblocks;
-    a.kchunks_max = S.kchunks_max;
+    int32_t *hq = a.h_sets;
+    std::memcpy(hq, S.start.data(), ns * 4);
+    hq += sc;
+    std::memcpy(hq, S.n.data(), ns * 4);
+    hq += sc;
+    for (int v = 0; v < N_TAU_VAR; ++v, hq += sc) std::memcpy(hq, S.tau_off[v].data(), (ns + 1) * 4);
+    for (int v = 0; v < N_K64_VAR; ++v, hq += sc) std::memcpy(hq, S.k64_off[v].data(), (ns + 1) * 4);
+    for (int v = 0; v < N_MK_VAR; ++v, hq += sc) std::memcpy(hq, S.mk_off[v].data(), (ns + 1) * 4);
+    const int narr = 2 + N_TAU_VAR + N_K64_VAR + N_MK_VAR;
+    CC_CUDA(c, cudaMemcpyAsync(a.L.set_start, a.h_sets, (size_t)((narr - 1) * sc + ns + 1) * 4,
+                               cudaMemcpyHostToDevice, c->stream));
+    for (int v = 0; v < N_TAU_VAR; ++v) a.tau_blocks[v] = S.tau_blocks[v];
+    for (int v = 0; v < N_K64_VAR; ++v) a.k64_blocks[v] = S.k64_blocks[v];
+    for (int v = 0; v < N_MK_VAR; ++v) {
+        a.mk_blocks[v] = S.mk_blocks[v];
+        a.mk_chunks_max[v] = S.mk_chunks_max[v];
+    }
+    a.pairs = S.pairs;
     a.L.total = S.total;
     a.L.nsets = ns;
     a.h_set_n = S.n;
@@ -403,24 +520,23 @@ static int split_level(cc_ctx *c, LevelAlloc &a, double h, int &ncomp)
     const cudaStream_t s = c->stream;
     const TauParams P = tau_params(c, h);
     launch_init_parent(a.L, s);
-    long long ntiles = 0;
-    {
-        // number of tau tiles of this level = last prefix entry (host copy)
-        for (int32_t n : a.h_set_n) {
-            const long long nt = (n + TAU_TILE - 1) / TAU_TILE;
-            ntiles += nt * (nt + 1) / 2;
-        }
-    }
+    const bool mixed = c->p.precision == CC_PREC_MIXED;
+    const int tk = mixed ? TK_TAUMIX : TK_TAU64;
+    int bin;
+    bool timed;
+    const int var = tune_pick(c, tk, a.tau_blocks, a.pairs, &bin, &timed);
+    const long long ntiles = a.tau_blocks[var];
     if (ntiles > 0x7fffffff) return fail(c, CC_E_ARG, "set too large for the tile grid");
+    Level L = a.L;
+    L.tile_off = a.tau_off[var];
     int ev;
-    if (c->p.precision == CC_PREC_MIXED) {
+    if (mixed) {
         launch_prep_ff(a.L, a.F, c->p.G, true, s);
-        ev = ev_begin(c, 0);
-        launch_tau_mixed(a.L, a.F, (int)ntiles, P, c->d_ctr, c->d_near_ij, c->d_near_tau, c->near_cap, s);
+        ev = ev_begin(c, 0, nullptr, timed ? tk : -1, bin, var, (double)a.pairs);
+        launch_tau_mixed(L, a.F, (int)ntiles, P, var, c->d_ctr, c->d_near_ij, c->d_near_tau, c->near_cap, s);
     } else {
-        ev = ev_begin(c, 0);
-        launch_tau_hook(a.L, (int)ntiles, P, c->p.precision, c->d_ctr, nullptr, 0, c->d_near_ij, c->d_near_tau,
-                        c->near_cap, s);
+        ev = ev_begin(c, 0, nullptr, timed ? tk : -1, bin, var, (double)a.pairs);
+        launch_tau_hook(L, (int)ntiles, P, var, c->d_ctr, nullptr, 0, c->d_near_ij, c->d_near_tau, c->near_cap, s);
     }
     ev_end(c, ev);
     launch_compress_segment(a.L, a.root, a.members, a.comp_start, a.comp_size, a.d_ncomp, c->seg_scratch, s);
@@ -464,37 +580,57 @@ static int split_level(cc_ctx *c, LevelAlloc &a, double h, int &ncomp)
     return CC_OK;
 }
 
+static int ensure_kpart(cc_ctx *c, int chunks, int fcap)
+{
+    const size_t need = (size_t)std::max(1, chunks) * 3 * (size_t)fcap * sizeof(double);
+    if (chunks > 1 && need > c->kpart_sz) {
+        if (c->d_kpart) cudaFree(c->d_kpart);
+        c->d_kpart = nullptr;
+        c->kpart_sz = 0;
+        if (cudaMalloc(&c->d_kpart, need) != cudaSuccess) {
+            cudaGetLastError();
+            return fail(c, CC_E_NOMEM, "device allocation failed (kick partials)");
+        }
+        c->kpart_sz = need;
+    }
+    return CC_OK;
+}
+
+// K_{h,V} on a level: labels lab (packed order); order = the root-sorted
+// order of the mixed kick (its labels at L.klab, prepared by the caller)
+static int level_kick(cc_ctx *c, LevelAlloc &a, const int32_t *lab, const int32_t *order, double h)
+{
+    const cudaStream_t s = c->stream;
+    int bin;
+    bool timed;
+    Level L = a.L;
+    if (c->p.precision == CC_PREC_MIXED && !(h < c->p.h_fp64)) {
+        const int var = tune_pick(c, TK_MK, a.mk_blocks, a.pairs, &bin, &timed);
+        CC_TRY(ensure_kpart(c, a.mk_chunks_max[var], a.F.cap));
+        const int ev = ev_begin(c, 1, nullptr, timed ? TK_MK : -1, bin, var, (double)a.pairs);
+        launch_kick_mixed(L, a.F, order, a.mk_off[var], (int)a.mk_blocks[var], MK_VAR_CHUNK[var],
+                          a.mk_chunks_max[var] > 1, c->p.eps * c->p.eps, h, c->d_ctr, c->d_kpart, s);
+        ev_end(c, ev);
+    } else {
+        const int var = tune_pick(c, TK_K64, a.k64_blocks, a.pairs, &bin, &timed);
+        L.itile_off = a.k64_off[var];
+        const int ev = ev_begin(c, 1, nullptr, timed ? TK_K64 : -1, bin, var, (double)a.pairs);
+        launch_kick(L, lab, (int)a.k64_blocks[var], c->p.G, c->p.eps * c->p.eps, h, var, c->d_ctr, s);
+        ev_end(c, ev);
+    }
+    return CC_OK;
+}
+
 static int dkd(cc_ctx *c, LevelAlloc &a, double h)
 {
     const cudaStream_t s = c->stream;
-    long long nit = 0;
-    for (int32_t n : a.h_set_n) nit += (n + KICK_TILE - 1) / KICK_TILE;
     launch_drift(a.L, a.root, 0.5 * h, s);
     if (c->p.precision == CC_PREC_MIXED && !(h < c->p.h_fp64)) {
-        // FP32 pair forces between components; partials of multi-chunk sets
-        const size_t need = (size_t)a.kchunks_max * 3 * (size_t)a.F.cap * sizeof(double);
-        if (a.kchunks_max > 1 && need > c->kpart_sz) {
-            if (c->d_kpart) cudaFree(c->d_kpart);
-            c->d_kpart = nullptr;
-            c->kpart_sz = 0;
-            if (cudaMalloc(&c->d_kpart, need) != cudaSuccess) {
-                cudaGetLastError();
-                return fail(c, CC_E_NOMEM, "device allocation failed (kick partials)");
-            }
-            c->kpart_sz = need;
-        }
         // positions in the root-sorted order of the split: members of one
         // component are adjacent, so tiles inside one component are skipped
         launch_prep_kick(a.L, a.F, a.members, a.root, c->p.G, s);
-        const int ev = ev_begin(c, 1);
-        launch_kick_mixed(a.L, a.F, a.members, a.L.koff, (int)a.kblocks, a.kchunks_max > 1, c->p.eps * c->p.eps,
-                          h, c->d_ctr, c->d_kpart, s);
-        ev_end(c, ev);
-    } else {
-        const int ev = ev_begin(c, 1);
-        launch_kick(a.L, a.root, (int)nit, c->p.G, c->p.eps * c->p.eps, h, c->p.precision, c->d_ctr, nullptr, s);
-        ev_end(c, ev);
     }
+    CC_TRY(level_kick(c, a, a.root, a.members, h));
     launch_drift(a.L, a.root, 0.5 * h, s);
     return CC_OK;
 }
@@ -660,6 +796,7 @@ int cc_default_params(cc_params *p)
     p->max_depth = 64;
     p->s_small = 32;
     p->eta_outside = 0;
+    p->autotune = 1;
     return CC_OK;
 }
 
@@ -684,6 +821,7 @@ int cc_init(cc_ctx **out, int64_t n, const double *m, const double *x3, const do
     c->n = n;
     c->p = *p;
     c->eta_run = p->eta;
+    c->p_autotune = p->autotune != 0;
     c->stream = (cudaStream_t)stream;
     auto bail = [&](int code) {
         g_init_err = c->err;
@@ -865,8 +1003,10 @@ int cc_timestep_graph(cc_ctx *c, const int32_t *set, int64_t n_set, double h, in
     LevelAlloc &u = c->unit;
     const TauParams P = tau_params(c, h);
     const long long nt = (n_set + TAU_TILE - 1) / TAU_TILE;
+    Level UL = u.L;
+    UL.tile_off = u.tau_off[N_TAU_VAR - 1];  // 128-wide tiles
     launch_init_parent(u.L, c->stream);
-    launch_tau_hook(u.L, (int)(nt * (nt + 1) / 2), P, c->p.precision, c->d_ctr, nullptr, 0, c->d_near_ij,
+    launch_tau_hook(UL, (int)(nt * (nt + 1) / 2), P, N_TAU_VAR - 1, c->d_ctr, nullptr, 0, c->d_near_ij,
                     c->d_near_tau, c->near_cap, c->stream);
     DevCounters h1;
     CC_CUDA(c, cudaMemcpyAsync(&h1, c->d_ctr, sizeof(h1), cudaMemcpyDeviceToHost, c->stream));
@@ -886,7 +1026,7 @@ int cc_timestep_graph(cc_ctx *c, const int32_t *set, int64_t n_set, double h, in
         void *ss = (void *)(de + 2 * ne);
         CC_TRY(reset_call_counters(c));
         launch_init_parent(u.L, c->stream);
-        launch_tau_hook(u.L, (int)(nt * (nt + 1) / 2), P, c->p.precision, c->d_ctr, de, ne, c->d_near_ij,
+        launch_tau_hook(UL, (int)(nt * (nt + 1) / 2), P, N_TAU_VAR - 1, c->d_ctr, de, ne, c->d_near_ij,
                         c->d_near_tau, c->near_cap, c->stream);
         int bits = 0;
         while (bits < 31 && (1ll << bits) <= c->n) ++bits;
@@ -907,28 +1047,15 @@ int cc_kick(cc_ctx *c, const int32_t *set, int64_t n_set, const int32_t *labels,
     dl = (int32_t *)(((uintptr_t)dl + 15) & ~(uintptr_t)15);
     CC_TRY(copy_in(c, dl, labels, n_set * 4));
     LevelAlloc &u = c->unit;
+    int32_t *order = u.members;
     if (c->p.precision == CC_PREC_MIXED && !(h < c->p.h_fp64)) {
         // the mixed kick works in label-sorted order (members of a group adjacent)
-        int32_t *order = u.members;
         launch_label_order(dl, (int)n_set, u.L.total, order, c->seg_scratch, c->stream);
-        const size_t need = (size_t)std::max(1, u.kchunks_max) * 3 * (size_t)u.F.cap * sizeof(double);
-        if (u.kchunks_max > 1 && need > c->kpart_sz) {
-            if (c->d_kpart) cudaFree(c->d_kpart);
-            c->d_kpart = nullptr;
-            c->kpart_sz = 0;
-            if (cudaMalloc(&c->d_kpart, need) != cudaSuccess) {
-                cudaGetLastError();
-                return fail(c, CC_E_NOMEM, "device allocation failed (kick partials)");
-            }
-            c->kpart_sz = need;
-        }
         launch_prep_kick(u.L, u.F, order, dl, c->p.G, c->stream);
-        launch_kick_mixed(u.L, u.F, order, u.L.koff, (int)u.kblocks, u.kchunks_max > 1, c->p.eps * c->p.eps, h,
-                          c->d_ctr, c->d_kpart, c->stream);
-    } else {
-        const int nit = (int)((n_set + KICK_TILE - 1) / KICK_TILE);
-        launch_kick(u.L, dl, nit, c->p.G, c->p.eps * c->p.eps, h, c->p.precision, c->d_ctr, nullptr, c->stream);
     }
+    CC_TRY(level_kick(c, u, dl, order, h));
+    CC_CUDA(c, cudaStreamSynchronize(c->stream));
+    ev_resolve(c);
     launch_scatter_set(c->d_x3, c->d_v3, c->n, u.L, (int)n_set, false, true, c->stream);
     CC_CUDA(c, cudaStreamSynchronize(c->stream));
     return check_device_error(c);

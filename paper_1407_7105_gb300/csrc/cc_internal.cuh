@@ -221,11 +221,18 @@ extern unsigned long long g_launches;
 
 // cc_pair.cu
 void launch_init_parent(const Level &L, cudaStream_t s);
-void launch_tau_hook(const Level &L, int ntiles, const TauParams &P, int precision, DevCounters *ctr,
+// tunable launch shapes (variant index): tau tiles {64, 128}; FP64 kick
+// tiles {32, 64, 128}; mixed kick j-chunks {1, 4, 16} tiles of 128
+constexpr int N_TAU_VAR = 2, N_K64_VAR = 3, N_MK_VAR = 3;
+constexpr int TAU_VAR_T[N_TAU_VAR] = {64, 128};
+constexpr int K64_VAR_T[N_K64_VAR] = {32, 64, 128};
+constexpr int MK_VAR_CHUNK[N_MK_VAR] = {1, 4, 16};
+constexpr int MK_TILE = 128;
+void launch_tau_hook(const Level &L, int ntiles, const TauParams &P, int variant, DevCounters *ctr,
                      int32_t *edges, long long edge_cap, int32_t *near_ij, double *near_tau, long long near_cap,
                      cudaStream_t s);
 void launch_kick(const Level &L, const int32_t *label, int nitiles, double G, double eps2, double h,
-                 int precision, DevCounters *ctr, float *scratch, cudaStream_t s);
+                 int variant, DevCounters *ctr, cudaStream_t s);
 void launch_energy(const double *x3, const double *v3, const double *m, long long n, double G, double eps2,
                    double *partial /*[nblk*8]*/, int nblk, cudaStream_t s);
 int energy_blocks(long long n);
@@ -266,14 +273,15 @@ double probe_fma(int fp64, int nsm, cudaStream_t s);
 
 // cc_mixed.cu
 void launch_prep_ff(const Level &L, const FFView &F, double G, bool with_v, cudaStream_t s);
-void launch_tau_mixed(const Level &L, const FFView &F, int ntiles, const TauParams &P, DevCounters *ctr,
-                      int32_t *near_ij, double *near_tau, long long near_cap, cudaStream_t s);
-int mixed_kick_blocks(int n);
-int mixed_kick_chunks(int n);
+void launch_tau_mixed(const Level &L, const FFView &F, int ntiles, const TauParams &P, int variant,
+                      DevCounters *ctr, int32_t *near_ij, double *near_tau, long long near_cap, cudaStream_t s);
+int mixed_kick_blocks(int n, int chunk);
+int mixed_kick_chunks(int n, int chunk);
 void launch_prep_kick(const Level &L, const FFView &F, const int32_t *order, const int32_t *root, double G,
                       cudaStream_t s);
 void launch_kick_mixed(const Level &L, const FFView &F, const int32_t *order, const int32_t *koff, int nblocks,
-                       bool multi_chunk, double eps2, double h, DevCounters *ctr, double *partial, cudaStream_t s);
+                       int chunk, bool multi_chunk, double eps2, double h, DevCounters *ctr, double *partial,
+                       cudaStream_t s);
 
 // cc_small.cu
 void launch_small(const Level &L, const int32_t *members, const int32_t *comp_start, const int32_t *comp_size,

@@ -94,12 +94,12 @@ void launch_prep_kick(const Level &L, const FFView &F, const int32_t *order, con
     CC_COUNT_LAUNCH(1);
 }
 
-constexpr int MT_T = 128;
 
+template <int T>
 struct __align__(16) MixedTauSmem {
-    float4 pq[2 * MT_T];   // positions (hi, Gm), (lo) of the j-tile
-    float4 vq[2 * MT_T];   // velocities (hi), (lo)
-    int32_t lp[2 * MT_T];  // local union-find over the tile's particles
+    float4 pq[2 * T];   // positions (hi, Gm), (lo) of the j-tile
+    float4 vq[2 * T];   // velocities (hi), (lo)
+    int32_t lp[2 * T];  // local union-find over the tile's particles
     uint64_t bar;
 };
 
@@ -130,11 +130,12 @@ __device__ __forceinline__ bool luf_union(int32_t *p, int a, int b)
     return false;
 }
 
-__global__ void __launch_bounds__(MT_T) k_tau_mixed(Level L, FFView F, TauParams P, MixedTauParams Q,
+template <int T>
+__global__ void __launch_bounds__(T) k_tau_mixed(Level L, FFView F, TauParams P, MixedTauParams Q,
                                                      DevCounters *ctr, int32_t *near_ij, double *near_tau,
                                                      long long near_cap)
 {
-    __shared__ MixedTauSmem sm;
+    __shared__ MixedTauSmem<T> sm;
     const int tid = threadIdx.x;
     int lo = 0, hi = L.nsets;
     while (hi - lo > 1) {
@@ -144,7 +145,7 @@ __global__ void __launch_bounds__(MT_T) k_tau_mixed(Level L, FFView F, TauParams
     const int s = lo;
     int t = blockIdx.x - L.tile_off[s];
     const int n = L.set_n[s], start = L.set_start[s];
-    const int nt = (n + MT_T - 1) / MT_T;
+    const int nt = (n + T - 1) / T;
     int ti = 0;
     while (t >= nt - ti) {
         t -= nt - ti;
@@ -152,14 +153,14 @@ __global__ void __launch_bounds__(MT_T) k_tau_mixed(Level L, FFView F, TauParams
     }
     const int tj = ti + t;
     const bool diag = ti == tj;
-    const int j0 = start + tj * MT_T;
-    const int jn = min(MT_T, n - tj * MT_T);
+    const int j0 = start + tj * T;
+    const int jn = min(T, n - tj * T);
     if (tid == 0) {
         mbar_init(&sm.bar, 1);
         fence_mbar_init();
     }
     sm.lp[tid] = tid;
-    sm.lp[MT_T + tid] = MT_T + tid;
+    sm.lp[T + tid] = T + tid;
     __syncthreads();
     if (tid == 0) {
         const unsigned bytes = (unsigned)jn * 32u;
@@ -167,7 +168,7 @@ __global__ void __launch_bounds__(MT_T) k_tau_mixed(Level L, FFView F, TauParams
         tma_load_1d(sm.pq, F.pq + 2 * (size_t)j0, bytes, &sm.bar);
         tma_load_1d(sm.vq, F.vq + 2 * (size_t)j0, bytes, &sm.bar);
     }
-    const int il = ti * MT_T + tid;
+    const int il = ti * T + tid;
     const bool iv = il < n;
     const int i = start + il;
     float4 ip0 = make_float4(0, 0, 0, 0), ip1 = ip0, iv0 = ip0, iv1 = ip0;
@@ -183,7 +184,7 @@ __global__ void __launch_bounds__(MT_T) k_tau_mixed(Level L, FFView F, TauParams
         return;
     }
     unsigned long long my_edges = 0, my_fp64 = 0;
-    const int joff = diag ? 0 : MT_T;  // local index base of the j-tile
+    const int joff = diag ? 0 : T;  // local index base of the j-tile
     if (iv) {
         for (int k = diag ? tid + 1 : 0; k < jn; ++k) {
             const float4 jp0 = sm.pq[2 * k], jp1 = sm.pq[2 * k + 1];
@@ -223,11 +224,11 @@ __global__ void __launch_bounds__(MT_T) k_tau_mixed(Level L, FFView F, TauParams
     __syncthreads();
     // merge the tile's local components into the global forest: one union
     // per local non-root element instead of one per edge
-    for (int e = tid; e < (diag ? MT_T : 2 * MT_T); e += MT_T) {
+    for (int e = tid; e < (diag ? T : 2 * T); e += T) {
         const int r = luf_find(sm.lp, e);
         if (r != e) {
-            const int ge = (e < MT_T) ? start + ti * MT_T + e : j0 + (e - MT_T);
-            const int gr = (r < MT_T) ? start + ti * MT_T + r : j0 + (r - MT_T);
+            const int ge = (e < T) ? start + ti * T + e : j0 + (e - T);
+            const int gr = (r < T) ? start + ti * T + r : j0 + (r - T);
             if (!uf_union(L.parent, ge, gr)) raise_err(ctr, DERR_UF_RETRY);
         }
     }
@@ -242,8 +243,8 @@ __global__ void __launch_bounds__(MT_T) k_tau_mixed(Level L, FFView F, TauParams
     }
 }
 
-void launch_tau_mixed(const Level &L, const FFView &F, int ntiles, const TauParams &P, DevCounters *ctr,
-                      int32_t *near_ij, double *near_tau, long long near_cap, cudaStream_t s)
+void launch_tau_mixed(const Level &L, const FFView &F, int ntiles, const TauParams &P, int variant,
+                      DevCounters *ctr, int32_t *near_ij, double *near_tau, long long near_cap, cudaStream_t s)
 {
     if (ntiles <= 0) return;
     MixedTauParams Q;
@@ -251,7 +252,10 @@ void launch_tau_mixed(const Level &L, const FFView &F, int ntiles, const TauPara
     Q.etah = (float)(P.eta_outside ? P.eta_in * P.eta / P.h : P.eta_in / P.h);
     Q.eps2 = (float)P.eps2;
     Q.G = (float)P.G;
-    k_tau_mixed<<<ntiles, MT_T, 0, s>>>(L, F, P, Q, ctr, near_ij, near_tau, near_cap);
+    if (variant == 0)
+        k_tau_mixed<64><<<ntiles, 64, 0, s>>>(L, F, P, Q, ctr, near_ij, near_tau, near_cap);
+    else
+        k_tau_mixed<128><<<ntiles, 128, 0, s>>>(L, F, P, Q, ctr, near_ij, near_tau, near_cap);
     CC_COUNT_LAUNCH(1);
 }
 
@@ -265,12 +269,12 @@ void launch_tau_mixed(const Level &L, const FFView &F, int ntiles, const TauPara
 // means a uniform tile).  Partials go to scratch in FP64 unless the set has
 // a single chunk, in which case v is updated directly.
 constexpr int MK_T = 128;
-constexpr int MK_CHUNK_TILES = 8;  // j-tiles per chunk (1024 j)
+constexpr int MK_CHUNK_MAX = 16;  // j-tiles per chunk: 1, 4 or 16 (tuned per size bin)
 
 struct __align__(16) MixedKickSmem {
     float4 pq[2][2 * MK_T];  // (hi, Gm), (lo) per j, two stages
     int32_t lab[2][MK_T];
-    int32_t tiles[MK_CHUNK_TILES];
+    int32_t tiles[MK_CHUNK_MAX];
     int32_t ntiles;
     uint64_t bar[2];
 };
@@ -286,7 +290,8 @@ __device__ __forceinline__ void mk_issue(MixedKickSmem &sm, int st, const FFView
 }
 
 __global__ void __launch_bounds__(MK_T) k_kick_mixed(Level L, FFView F, const int32_t *order, const int32_t *koff,
-                                                      float eps2, double h, DevCounters *ctr, double *partial)
+                                                      int chunk, float eps2, double h, DevCounters *ctr,
+                                                      double *partial)
 {
     __shared__ MixedKickSmem sm;
     const int tid = threadIdx.x;
@@ -299,9 +304,9 @@ __global__ void __launch_bounds__(MK_T) k_kick_mixed(Level L, FFView F, const in
     const int b = blockIdx.x - koff[s];
     const int n = L.set_n[s], start = L.set_start[s];
     const int ntile = (n + MK_T - 1) / MK_T;
-    const int nchunk = (ntile + MK_CHUNK_TILES - 1) / MK_CHUNK_TILES;
+    const int nchunk = (ntile + chunk - 1) / chunk;
     const int ti = b / nchunk, ch = b % nchunk;
-    const int tj0 = ch * MK_CHUNK_TILES, tj1 = min(ntile, tj0 + MK_CHUNK_TILES);
+    const int tj0 = ch * chunk, tj1 = min(ntile, tj0 + chunk);
     const int il = ti * MK_T + tid;
     const bool iv = il < n;
     const int t = start + il;  // position in the sorted order
@@ -387,14 +392,14 @@ __global__ void __launch_bounds__(MK_T) k_kick_mixed(Level L, FFView F, const in
 }
 
 // sum the chunk partials of multi-chunk sets in chunk order (FP64), v += h a
-__global__ void k_kick_reduce(Level L, FFView F, const int32_t *order, double h, const double *partial)
+__global__ void k_kick_reduce(Level L, FFView F, const int32_t *order, int chunk, double h, const double *partial)
 {
     const int t = blockIdx.x * blockDim.x + threadIdx.x;
     if (t >= L.total) return;
     const int k = order[t];
     if (L.sidx[k] < 0) return;
     const int n = L.set_n[L.sidx[k]];
-    const int nchunk = ((n + MK_T - 1) / MK_T + MK_CHUNK_TILES - 1) / MK_CHUNK_TILES;
+    const int nchunk = ((n + MK_T - 1) / MK_T + chunk - 1) / chunk;
     if (nchunk == 1) return;
     const size_t cap = (size_t)F.cap;
     double ax = 0.0, ay = 0.0, az = 0.0;
@@ -408,26 +413,27 @@ __global__ void k_kick_reduce(Level L, FFView F, const int32_t *order, double h,
     L.vz[k] += h * az;
 }
 
-int mixed_kick_blocks(int n)
+int mixed_kick_blocks(int n, int chunk)
 {
     const int ntile = (n + MK_T - 1) / MK_T;
-    return ntile * ((ntile + MK_CHUNK_TILES - 1) / MK_CHUNK_TILES);
+    return ntile * ((ntile + chunk - 1) / chunk);
 }
 
-int mixed_kick_chunks(int n)
+int mixed_kick_chunks(int n, int chunk)
 {
     const int ntile = (n + MK_T - 1) / MK_T;
-    return (ntile + MK_CHUNK_TILES - 1) / MK_CHUNK_TILES;
+    return (ntile + chunk - 1) / chunk;
 }
 
 void launch_kick_mixed(const Level &L, const FFView &F, const int32_t *order, const int32_t *koff, int nblocks,
-                       bool multi_chunk, double eps2, double h, DevCounters *ctr, double *partial, cudaStream_t s)
+                       int chunk, bool multi_chunk, double eps2, double h, DevCounters *ctr, double *partial,
+                       cudaStream_t s)
 {
     if (nblocks <= 0) return;
-    k_kick_mixed<<<nblocks, MK_T, 0, s>>>(L, F, order, koff, (float)eps2, h, ctr, partial);
+    k_kick_mixed<<<nblocks, MK_T, 0, s>>>(L, F, order, koff, chunk, (float)eps2, h, ctr, partial);
     CC_COUNT_LAUNCH(1);
     if (multi_chunk) {
-        k_kick_reduce<<<(L.total + 255) / 256, 256, 0, s>>>(L, F, order, h, partial);
+        k_kick_reduce<<<(L.total + 255) / 256, 256, 0, s>>>(L, F, order, chunk, h, partial);
         CC_COUNT_LAUNCH(1);
     }
 }

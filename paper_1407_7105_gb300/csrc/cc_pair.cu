@@ -41,10 +41,11 @@ void launch_init_parent(const Level &L, cudaStream_t s)
 // One CTA per (set, i-tile, j-tile) with i-tile <= j-tile: TAU_T threads,
 // thread r owns particle i = i-tile*TAU_T + r and tests it against the
 // j-tile staged in shared memory (pairs i < j only).
-constexpr int TAU_T = 128;
+constexpr int TAU_T = 128;  // tile of the edge-list variant
 
+template <int T>
 struct __align__(16) TauSmem {
-    double col[7][TAU_T + 4];  // x y z vx vy vz m of the j-tile
+    double col[7][T + 4];  // x y z vx vy vz m of the j-tile
     uint64_t bar;
 };
 
@@ -61,24 +62,24 @@ __device__ __forceinline__ void log_pair(const TauParams &P, double tau, int gi,
     }
 }
 
-template <int PREC>
-__global__ void __launch_bounds__(TAU_T) k_tau_hook(Level L, TauParams P, DevCounters *ctr, int32_t *near_ij,
+template <int T>
+__global__ void __launch_bounds__(T) k_tau_hook(Level L, TauParams P, DevCounters *ctr, int32_t *near_ij,
                                                      double *near_tau, long long near_cap)
 {
-    __shared__ TauSmem sm;
+    __shared__ TauSmem<T> sm;
     const int tid = threadIdx.x;
     const int s = find_set(L.tile_off, L.nsets, blockIdx.x);
     int t = blockIdx.x - L.tile_off[s];
     const int n = L.set_n[s], start = L.set_start[s];
-    const int nt = (n + TAU_T - 1) / TAU_T;
+    const int nt = (n + T - 1) / T;
     int ti = 0;
     while (t >= nt - ti) {
         t -= nt - ti;
         ++ti;
     }
     const int tj = ti + t;
-    const int j0 = start + tj * TAU_T;
-    const int jn = min(TAU_T, n - tj * TAU_T);
+    const int j0 = start + tj * T;
+    const int jn = min(T, n - tj * T);
 
     if (tid == 0) {
         mbar_init(&sm.bar, 1);
@@ -92,7 +93,7 @@ __global__ void __launch_bounds__(TAU_T) k_tau_hook(Level L, TauParams P, DevCou
 #pragma unroll
         for (int c = 0; c < 7; ++c) tma_load_1d(sm.col[c], src[c] + j0, bytes, &sm.bar);
     }
-    const int il = ti * TAU_T + tid;
+    const int il = ti * T + tid;
     const bool iv = il < n;
     const int i = start + il;
     double xi = 0, yi = 0, zi = 0, vxi = 0, vyi = 0, vzi = 0, mi = 0;
@@ -140,7 +141,7 @@ __global__ void __launch_bounds__(TAU_T) k_tau_edges(Level L, TauParams P, DevCo
                                                       long long edge_cap, int32_t *near_ij, double *near_tau,
                                                       long long near_cap)
 {
-    __shared__ TauSmem sm;
+    __shared__ TauSmem<TAU_T> sm;
     const int tid = threadIdx.x;
     const int s = find_set(L.tile_off, L.nsets, blockIdx.x);
     int t = blockIdx.x - L.tile_off[s];
@@ -203,7 +204,7 @@ __global__ void __launch_bounds__(TAU_T) k_tau_edges(Level L, TauParams P, DevCo
     }
 }
 
-void launch_tau_hook(const Level &L, int ntiles, const TauParams &P, int precision, DevCounters *ctr,
+void launch_tau_hook(const Level &L, int ntiles, const TauParams &P, int variant, DevCounters *ctr,
                      int32_t *edges, long long edge_cap, int32_t *near_ij, double *near_tau, long long near_cap,
                      cudaStream_t s)
 {
@@ -213,8 +214,10 @@ void launch_tau_hook(const Level &L, int ntiles, const TauParams &P, int precisi
         CC_COUNT_LAUNCH(1);
         return;
     }
-    (void)precision;
-    k_tau_hook<0><<<ntiles, TAU_T, 0, s>>>(L, P, ctr, near_ij, near_tau, near_cap);
+    if (variant == 0)
+        k_tau_hook<64><<<ntiles, 64, 0, s>>>(L, P, ctr, near_ij, near_tau, near_cap);
+    else
+        k_tau_hook<128><<<ntiles, 128, 0, s>>>(L, P, ctr, near_ij, near_tau, near_cap);
     CC_COUNT_LAUNCH(1);
 }
 
@@ -223,15 +226,16 @@ void launch_tau_hook(const Level &L, int ntiles, const TauParams &P, int precisi
 // its set in ascending order (pairs with equal labels skipped), so the sum
 // runs over j in ascending packed index = ascending particle id, the
 // order of the plain definition; then v_i += h a_i.  Two-stage TMA ring.
-constexpr int KICK_T = 64;
 
+template <int T>
 struct __align__(16) KickSmem {
-    double col[2][4][KICK_T];  // x y z m per stage
-    int32_t lab[2][KICK_T];
+    double col[2][4][T];  // x y z m per stage
+    int32_t lab[2][T];
     uint64_t bar[2];
 };
 
-__device__ __forceinline__ void kick_issue(KickSmem &sm, int st, const Level &L, const int32_t *label, int j0,
+template <int T>
+__device__ __forceinline__ void kick_issue(KickSmem<T> &sm, int st, const Level &L, const int32_t *label, int j0,
                                            int jn)
 {
     const unsigned cnt = (unsigned)((jn + 3) & ~3);
@@ -244,16 +248,17 @@ __device__ __forceinline__ void kick_issue(KickSmem &sm, int st, const Level &L,
     tma_load_1d(sm.lab[st], label + j0, cnt * 4u, &sm.bar[st]);
 }
 
-__global__ void __launch_bounds__(KICK_T) k_kick64(Level L, const int32_t *label, double G, double eps2,
+template <int T>
+__global__ void __launch_bounds__(T) k_kick64(Level L, const int32_t *label, double G, double eps2,
                                                     double h, DevCounters *ctr)
 {
-    __shared__ __align__(16) KickSmem sm;
+    __shared__ __align__(16) KickSmem<T> sm;
     const int tid = threadIdx.x;
     const int s = find_set(L.itile_off, L.nsets, blockIdx.x);
     const int ti = blockIdx.x - L.itile_off[s];
     const int n = L.set_n[s], start = L.set_start[s];
-    const int nt = (n + KICK_T - 1) / KICK_T;
-    const int il = ti * KICK_T + tid;
+    const int nt = (n + T - 1) / T;
+    const int il = ti * T + tid;
     const bool iv = il < n;
     const int i = start + il;
     if (tid == 0) {
@@ -262,7 +267,7 @@ __global__ void __launch_bounds__(KICK_T) k_kick64(Level L, const int32_t *label
         fence_mbar_init();
     }
     __syncthreads();
-    if (tid == 0) kick_issue(sm, 0, L, label, start, min(KICK_T, n));
+    if (tid == 0) kick_issue(sm, 0, L, label, start, min(T, n));
     double xi = 0, yi = 0, zi = 0;
     int li = 0;
     if (iv) {
@@ -274,14 +279,14 @@ __global__ void __launch_bounds__(KICK_T) k_kick64(Level L, const int32_t *label
     for (int tj = 0; tj < nt; ++tj) {
         const int st = tj & 1;
         if (tid == 0 && tj + 1 < nt)
-            kick_issue(sm, st ^ 1, L, label, start + (tj + 1) * KICK_T, min(KICK_T, n - (tj + 1) * KICK_T));
+            kick_issue(sm, st ^ 1, L, label, start + (tj + 1) * T, min(T, n - (tj + 1) * T));
         const bool got = mbar_wait(&sm.bar[st], (tj >> 1) & 1, TMA_WAIT_CYCLES);
         if (__syncthreads_or(!got)) {  // uniform exit: no thread is left at a barrier
             ok = false;
             break;
         }
-        const int jn = min(KICK_T, n - tj * KICK_T);
-        const int j0l = tj * KICK_T;
+        const int jn = min(T, n - tj * T);
+        const int j0l = tj * T;
         if (iv) {
             for (int k = 0; k < jn; ++k) {
                 if (j0l + k == il || sm.lab[st][k] == li) continue;
@@ -314,12 +319,15 @@ __global__ void __launch_bounds__(KICK_T) k_kick64(Level L, const int32_t *label
 }
 
 void launch_kick(const Level &L, const int32_t *label, int nitiles, double G, double eps2, double h,
-                 int precision, DevCounters *ctr, float *scratch, cudaStream_t s)
+                 int variant, DevCounters *ctr, cudaStream_t s)
 {
-    (void)precision;
-    (void)scratch;
     if (nitiles <= 0) return;
-    k_kick64<<<nitiles, KICK_T, 0, s>>>(L, label, G, eps2, h, ctr);
+    if (variant == 0)
+        k_kick64<32><<<nitiles, 32, 0, s>>>(L, label, G, eps2, h, ctr);
+    else if (variant == 1)
+        k_kick64<64><<<nitiles, 64, 0, s>>>(L, label, G, eps2, h, ctr);
+    else
+        k_kick64<128><<<nitiles, 128, 0, s>>>(L, label, G, eps2, h, ctr);
     CC_COUNT_LAUNCH(1);
 }
 

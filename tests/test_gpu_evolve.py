@@ -179,3 +179,21 @@ def test_errors_are_reported(cclib, plummer_ic):
     with pytest.raises(cclib.CCError) as e:
         cclib.Context(m, bad, v)
     assert e.value.code == -5
+
+
+def test_launch_shapes_do_not_change_fp64_results(cclib, plummer_ic):
+    """The autotuner tries several tile shapes for the tau and FP64 kick
+    kernels; in the FP64 form every shape computes the same arithmetic in
+    the same order, so tuned and untuned runs agree bit for bit."""
+    m, x, v = plummer_ic(1000)
+    out = []
+    for tune in (0, 1):
+        c = cclib.Context(m, x, v, dt=1 / 128, autotune=tune)
+        c.evolve(6 / 128)
+        _, _, gx, gv = c.get_state()
+        out.append((gx, gv))
+        c.close()
+    assert np.array_equal(out[0][0], out[1][0]) and np.array_equal(out[0][1], out[1][1])
+    s = O.State(m, x, v)
+    O.evolve(s, O.params(dt=1 / 128), 6)
+    assert _rel_ok(out[1][0], s.x3, 1e-10) and _rel_ok(out[1][1], s.v3, 1e-10)
