@@ -33,10 +33,22 @@ struct MixedTauParams {
     float eta, etah, eps2, G;
 };
 
-__device__ __forceinline__ int tau_decide_fp32(float dx0, float dx1, float dx2, float dv0, float dv1, float dv2,
-                                               float mu, float c_x, float c_v, const MixedTauParams &Q)
+// The h-independent part of the decision: everything except T/h.  The
+// decision at a threshold h then costs two products and four comparisons,
+// and since eta/h doubles exactly when h halves, T/h at h 2^-m is T/h at h
+// times 2^m bit for bit: decide(prep, etah * 2^m) is the decision the full
+// evaluation would take at h 2^-m for the same state.
+struct TauPrep32 {
+    float r2, s1, r, s2;         // Tff/h = (etah r2) s1, Tfb/h = (etah r) s2
+    float ffA, ffB, ffLo, ffHi;  // ff edge certain: Tff ffA < ffLo; no edge certain: Tff ffB >= ffHi
+    float fbA, fbB, fbLo, fbHi;  // the same for the flyby term
+    bool fb;                     // flyby term usable (else only a certain ff edge decides)
+};
+
+__device__ __forceinline__ TauPrep32 tau_prep_fp32(float dx0, float dx1, float dx2, float dv0, float dv1, float dv2,
+                                                   float mu, float c_x, float c_v, const MixedTauParams &Q)
 {
-    // returns 1 = edge certain, 0 = no edge certain, -1 = undecided
+    TauPrep32 t;
     const float A = 1.f + SLACK, B = 1.f - SLACK;
     const float r2 = fmaf(dx2, dx2, fmaf(dx1, dx1, fmaf(dx0, dx0, Q.eps2)));
     const float v2 = fmaf(dv2, dv2, fmaf(dv1, dv1, dv0 * dv0));
@@ -50,30 +62,82 @@ __device__ __forceinline__ int tau_decide_fp32(float dx0, float dx1, float dx2, 
     const float ev = fmaf(c_v, s2, 2.05f * U32);
     const float drv = (er + ev + 4.f * U32) * (r * vn);
     // free fall: T/h = (eta/h) r2 s1, dT/dt = 1.5 eta rv s1
-    const float Tff = Q.etah * r2 * s1;
     const float dTff = 1.5f * Q.eta * rv * s1;
     const float Dff = fmaf(-0.5f, fminf(dTff, 1.f), 1.f);
     const float dDff = fmaf(0.5f, fmaf(32.f * U32, fabsf(dTff), 1.5f * Q.eta * s1 * drv), 2.f * U32 * Dff);
     const float eff = fmaf(3.f, er, 40.f * U32);
-    const bool ff_yes = Tff * fmaf(eff, A, A) < Dff - dDff;
-    const bool ff_no = Tff * fmaf(-eff, B, B) >= Dff + dDff;
+    t.r2 = r2;
+    t.s1 = s1;
+    t.r = r;
+    t.s2 = s2;
+    t.ffA = fmaf(eff, A, A);
+    t.ffB = fmaf(-eff, B, B);
+    t.ffLo = Dff - dDff;
+    t.ffHi = Dff + dDff;
     // an exactly zero (or unresolved) FP32 velocity difference may hide a
     // tiny nonzero FP64 one, whose flyby term can be small: only a certain
     // free-fall edge decides such a pair
-    if (!(v2 > 0.f) || vn < 6.f * c_v) return ff_yes ? 1 : -1;
+    t.fb = (v2 > 0.f) && !(vn < 6.f * c_v);
     // flyby: T/h = (eta/h) r s2, dT/dt = eta rv s2 rinv (1 + mu s2^2 rinv)
     const float g = fmaf(mu * s2 * s2, rinv, 1.f);
     const float k = s2 * rinv * g;
-    const float Tfb = Q.etah * r * s2;
     const float dTfb = Q.eta * rv * k;
     const float Dfb = fmaf(-0.5f, fminf(dTfb, 1.f), 1.f);
     const float dDfb = fmaf(0.5f, fmaf(80.f * U32, fabsf(dTfb), Q.eta * k * drv), 2.f * U32 * Dfb);
     const float efb = fmaf(3.f, er + ev, 40.f * U32);
-    const bool fb_yes = Tfb * fmaf(efb, A, A) < Dfb - dDfb;
-    const bool fb_no = Tfb * fmaf(-efb, B, B) >= Dfb + dDfb;
+    t.fbA = fmaf(efb, A, A);
+    t.fbB = fmaf(-efb, B, B);
+    t.fbLo = Dfb - dDfb;
+    t.fbHi = Dfb + dDfb;
+    return t;
+}
+
+// returns 1 = edge certain, 0 = no edge certain, -1 = undecided; etah =
+// eta/h in float
+__device__ __forceinline__ int tau_decide_at(const TauPrep32 &t, float etah)
+{
+    const float Tff = etah * t.r2 * t.s1;
+    const bool ff_yes = Tff * t.ffA < t.ffLo;
+    if (!t.fb) return ff_yes ? 1 : -1;
+    const bool ff_no = Tff * t.ffB >= t.ffHi;
+    const float Tfb = etah * t.r * t.s2;
+    const bool fb_yes = Tfb * t.fbA < t.fbLo;
+    const bool fb_no = Tfb * t.fbB >= t.fbHi;
     if (ff_yes || fb_yes) return 1;
     if (ff_no && fb_no) return 0;
     return -1;
+}
+
+__device__ __forceinline__ int tau_decide_fp32(float dx0, float dx1, float dx2, float dv0, float dv1, float dv2,
+                                               float mu, float c_x, float c_v, const MixedTauParams &Q)
+{
+    return tau_decide_at(tau_prep_fp32(dx0, dx1, dx2, dv0, dv1, dv2, mu, c_x, c_v, Q), Q.etah);
+}
+
+// 2^k as a float (0 <= k <= 127); 2^-k as a double (0 <= k <= 1022)
+__device__ __forceinline__ float pow2f(int k) { return __int_as_float((127 + k) << 23); }
+__device__ __forceinline__ double pow2m(int k) { return __longlong_as_double((long long)(1023 - k) << 52); }
+
+// x 2^-k for a normal x whose result stays normal: an exponent-field
+// subtraction (exact, and no FP64 instruction)
+__device__ __forceinline__ double scale2m(double x, int k)
+{
+    return __longlong_as_double(__double_as_longlong(x) - ((long long)k << 52));
+}
+
+// The first m >= 0 with h 2^-m <= tau (the first threshold of the sequence
+// h, h/2, h/4, ... at which tau < threshold fails), at most `levels`.  h is
+// positive and normal; the comparison is exact: (exponent, significand) of
+// h 2^-m against those of tau.  NaN tau: 0 (the predicate is false).
+__device__ __forceinline__ int first_level_at_or_below(double tau, double h, int levels)
+{
+    if (!(tau < h)) return 0;
+    if (!(tau >= 2.2250738585072014e-308)) return levels;  // 0, negative or subnormal: below every threshold
+    const long long bt = __double_as_longlong(tau), bh = __double_as_longlong(h);
+    const int et = (int)(bt >> 52), eh = (int)(bh >> 52);
+    const long long mt = bt & 0xFFFFFFFFFFFFFll, mh = bh & 0xFFFFFFFFFFFFFll;
+    const int m = eh - et + (mh <= mt ? 0 : 1);
+    return m < levels ? m : levels;
 }
 
 // Float-float split of a double: hi = fl32(x) (round to nearest even),
@@ -102,6 +166,34 @@ __device__ __forceinline__ void ff_split(double x, float &hi, float &lo)
     const bool neg = (b >> 63) != 0ull;
     hi = neg ? -h : h;
     lo = neg ? -l : l;
+}
+
+// fl32(x) = round-to-nearest-even double -> float, by integer arithmetic for
+// results in the normal float range (same value as __double2float_rn); the
+// conversion instruction costs ~180 cycles per warp on GB300.
+__device__ __forceinline__ float fl32(double x)
+{
+    const unsigned long long b = (unsigned long long)__double_as_longlong(x);
+    const int e = (int)((b >> 52) & 0x7FFull);
+    if (e < 1023 - 126 || e > 1023 + 126) return __double2float_rn(x);
+    const unsigned long long mag = b & 0x7FFFFFFFFFFFFFFFull;
+    const unsigned long long r = mag + 0x0FFFFFFFull + ((mag >> 29) & 1ull);  // drop 29 bits, nearest even
+    const unsigned int fb = (unsigned int)((r >> 29) - (896ull << 23)) | ((unsigned int)(b >> 32) & 0x80000000u);
+    return __uint_as_float(fb);
+}
+
+// f2d(f) = the exact double of a float, by integer arithmetic for normal
+// floats and zeros (the conversion instruction costs ~140 cycles per warp)
+__device__ __forceinline__ double f2d(float f)
+{
+    const unsigned int u = __float_as_uint(f);
+    const unsigned int ex = (u >> 23) & 0xFFu;
+    if ((u & 0x7FFFFFFFu) == 0u) return __longlong_as_double((long long)((unsigned long long)u << 32));
+    if (ex == 0u || ex == 255u) return (double)f;
+    const unsigned long long b = ((unsigned long long)(u & 0x80000000u) << 32) |
+                                 ((unsigned long long)(ex + 896u) << 52) |
+                                 ((unsigned long long)(u & 0x7FFFFFu) << 29);
+    return __longlong_as_double((long long)b);
 }
 
 // Kahan-compensated accumulation: s + (-c) carries the running sum

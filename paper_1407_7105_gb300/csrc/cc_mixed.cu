@@ -33,7 +33,7 @@ __global__ void k_prep_ff(Level L, FFView F, float G, int with_v)
             ff_split(xs[c], hi[c], lo[c]);
             ax = fmaxf(ax, fabsf(hi[c]));
         }
-        F.pq[2 * k] = make_float4(hi[0], hi[1], hi[2], G * __double2float_rn(L.m[k]));
+        F.pq[2 * k] = make_float4(hi[0], hi[1], hi[2], G * fl32(L.m[k]));
         F.pq[2 * k + 1] = make_float4(lo[0], lo[1], lo[2], 0.f);
         if (with_v) {
             const double vs[3] = {L.vx[k], L.vy[k], L.vz[k]};
@@ -81,7 +81,7 @@ __global__ void k_prep_kick(Level L, FFView F, const int32_t *order, const int32
     float hi[3], lo[3];
 #pragma unroll
     for (int c = 0; c < 3; ++c) ff_split(xs[c], hi[c], lo[c]);
-    F.pq[2 * t] = make_float4(hi[0], hi[1], hi[2], G * __double2float_rn(L.m[k]));
+    F.pq[2 * t] = make_float4(hi[0], hi[1], hi[2], G * fl32(L.m[k]));
     F.pq[2 * t + 1] = make_float4(lo[0], lo[1], lo[2], 0.f);
     L.klab[t] = root[k];
 }

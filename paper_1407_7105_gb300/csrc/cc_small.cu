@@ -28,6 +28,8 @@ struct __align__(16) K8Warp {
     double d[7][32];  // x y z vx vy vz m
     float f[13][32];  // hi/lo of x y z vx vy vz, m (FP32 decision)
     float xm[32], vm[32];  // per body max |x_hi|, max |v_hi| (error bounds)
+    int gid[32];           // particle ids (near-threshold log)
+    unsigned char e[32][32];  // e[j][l]: edge depth of pair (l, j) at the level the state was split fresh
 };
 
 __device__ __forceinline__ void k8_publish(K8Warp &S, int lane, const double st[7], bool ff)
@@ -43,7 +45,7 @@ __device__ __forceinline__ void k8_publish(K8Warp &S, int lane, const double st[
             S.f[c][lane] = hi;
             S.f[6 + c][lane] = lo;
         }
-        S.f[12][lane] = __double2float_rn(st[6]);
+        S.f[12][lane] = fl32(st[6]);
         S.xm[lane] = fmaxf(fabsf(S.f[0][lane]), fmaxf(fabsf(S.f[1][lane]), fabsf(S.f[2][lane])));
         S.vm[lane] = fmaxf(fabsf(S.f[3][lane]), fmaxf(fabsf(S.f[4][lane]), fabsf(S.f[5][lane])));
     }
@@ -65,42 +67,21 @@ __device__ __forceinline__ void k8_drift(double st[7], double dt, bool exact)
     }
 }
 
-// ------------------------------------------------------------ pair path
-// evolve_cc({a, b}, h0) of a two-body set in one thread.  The recursion of a
-// pair is a binary tree: a node at pivot h splits {a,b} (one tau); an edge
-// makes it a component visited twice at h/2 (its DKD is empty: no rest set,
-// no cross pair); no edge makes it a leaf, where both bodies form the rest
-// set: drift h/2, pair kick h, drift h/2.  The tree is walked with a bit
-// stack (bit d: the node at depth d has finished its first child).  a has the
-// smaller id, and the arithmetic is that of the level kernels, so the FP64
-// form is bit-identical to the oracle.
-struct PairCounters {
-    unsigned long long tau = 0, kick = 0, drift = 0, split = 0, comp = 0, fp64 = 0;
-    int maxd = 0;
-};
+// ------------------------------------------------------------ edge depth
+// A split at pivot h and the first split of each component's first half
+// (pivot h/2) see the same state, so tau(i,j) is the same number and only
+// the threshold halves.  The kernels therefore take, for each pair of a
+// fresh state, its edge depth e: the pair is an edge at h 2^-m for
+// m = 0 .. e-1 and not at h 2^-e (tau < h 2^-m is monotone in m).  The
+// decisions are the ones a node-by-node evaluation takes: the FP64
+// predicate compares one tau with each threshold, and the FP32 decision at
+// h 2^-m is tau_decide_at(prep, (eta/h) 2^m) exactly.
 
-constexpr long long PAIR_VISIT_LIMIT = 1ll << 26;  // work cap per pair path (error beyond)
-
-__device__ __forceinline__ bool pair_edge(const double A[7], const double B[7], double h, bool mixed,
-                                          const TauParams &P0, const MixedTauParams &Q0, PairCounters &pc,
-                                          DevCounters *ctr, int ga, int gb, int32_t *near_ij, double *near_tau,
-                                          long long near_cap)
+// log (i, j, tau) when |tau - h| < near_tol h (FP64-decided pairs only)
+__device__ __forceinline__ void near_log(double tau, double h, double near_tol, DevCounters *ctr, int ga, int gb,
+                                         int32_t *near_ij, double *near_tau, long long near_cap)
 {
-    const double dx0 = __dsub_rn(A[0], B[0]), dx1 = __dsub_rn(A[1], B[1]), dx2 = __dsub_rn(A[2], B[2]);
-    const double dv0 = __dsub_rn(A[3], B[3]), dv1 = __dsub_rn(A[4], B[4]), dv2 = __dsub_rn(A[5], B[5]);
-    if (mixed) {
-        // FP64-formed differences rounded to FP32: relative error <= u
-        MixedTauParams Q = Q0;
-        Q.etah = (float)(P0.eta_outside ? P0.eta_in * P0.eta / h : P0.eta_in / h);
-        const int dec = tau_decide_fp32((float)dx0, (float)dx1, (float)dx2, (float)dv0, (float)dv1, (float)dv2,
-                                        Q.G * ((float)A[6] + (float)B[6]), 0.f, 0.f, Q);
-        if (dec >= 0) return dec == 1;
-    }
-    TauParams P = P0;
-    P.h = h;
-    const double tau = tau_fp64(dx0, dx1, dx2, dv0, dv1, dv2, A[6], B[6], P);
-    ++pc.fp64;
-    if (fabs(tau - h) < P.near_tol * h) {
+    if (fabs(tau - h) < near_tol * h) {
         const unsigned long long z = atomicAdd(&ctr->near_pairs, 1ull);
         if ((long long)z < near_cap) {
             near_ij[2 * z] = ga < gb ? ga : gb;
@@ -108,16 +89,113 @@ __device__ __forceinline__ bool pair_edge(const double A[7], const double B[7], 
             near_tau[z] = tau;
         }
     }
-    return tau < h;
 }
 
-__device__ __forceinline__ void pair_leaf(double A[7], double B[7], double h, bool mixed, const SmallParams &SP)
+struct NearLog {
+    DevCounters *ctr;
+    int32_t *ij;
+    double *tau;
+    long long cap;
+    double tol;
+};
+
+// FP64 form: edge depth over `levels` thresholds h 2^-m (returns levels when
+// every one is an edge).  log(tau, h_m) runs at the thresholds next to tau
+// (h_m just above and at or below it): the only ones a near-threshold pair
+// can sit at.
+template <class LogF>
+__device__ __forceinline__ int edge_depth_fp64(double tau, double h, int levels, LogF log)
 {
-    const double hd = 0.5 * h;
-    k8_drift(A, hd, !mixed);
-    k8_drift(B, hd, !mixed);
-    if (!mixed || h < SP.h_fp64) {
-        // the oracle's row sums: a_a = (G m_b) r^-3 (x_b - x_a), a_b with -dx
+    const int e = first_level_at_or_below(tau, h, levels);
+    if (e >= 1) log(tau, scale2m(h, e - 1));
+    if (e < levels) log(tau, scale2m(h, e));
+    return e;
+}
+
+// mixed form: certified FP32 decisions from one prep (etah = eta/h) while
+// they settle the threshold; at the first undecided threshold the FP64 tau
+// (tau64(), evaluated once) settles the rest.  used64 reports whether it ran.
+// The FP32 decisions agree with the FP64 predicate wherever they are taken,
+// so the result is the FP64 predicate's edge depth.
+template <class TauF, class LogF>
+__device__ __forceinline__ int edge_depth_mixed(const TauPrep32 &t, float etah, double h, int levels, TauF tau64,
+                                                LogF log, bool &used64)
+{
+    used64 = false;
+    for (int m = 0; m < levels; ++m) {
+        const int dec = tau_decide_at(t, etah * pow2f(m));
+        if (dec > 0) continue;
+        if (dec == 0) return m;
+        used64 = true;
+        const int e = edge_depth_fp64(tau64(), h, levels, log);
+        return e > m ? e : m;
+    }
+    return levels;
+}
+
+// ------------------------------------------------------------ pair path
+// evolve_cc({a, b}, h0) of a two-body set in one thread.  The recursion of a
+// pair is a binary tree: a node at pivot h splits {a,b} (one tau); an edge
+// makes it a component visited twice at h/2 (its DKD is empty: no rest set,
+// no cross pair); no edge makes it a leaf, where both bodies form the rest
+// set: drift h/2, pair kick h, drift h/2.  The tree is walked with a bit
+// stack (bit d: the node at depth d has finished its first child); from a
+// fresh state the walk goes straight down to the leaf through the state's
+// edge depth.  e0 = the edge depth of the initial state if the caller knows
+// it, else -1.
+struct PairCounters {
+    unsigned long long tau = 0, kick = 0, drift = 0, split = 0, comp = 0, fp64 = 0;
+    int maxd = 0;
+};
+
+constexpr long long PAIR_VISIT_LIMIT = 1ll << 26;  // work cap per pair path (error beyond)
+
+// after a leaf at depth d: the next node is the second child of the deepest
+// node whose first child is finishing; returns false when the tree is done
+__device__ __forceinline__ bool pair_next(unsigned long long &pend, int &d)
+{
+    while (d > 0) {
+        --d;
+        if (!((pend >> d) & 1ull)) {
+            pend |= 1ull << d;
+            ++d;
+            return true;
+        }
+        pend &= ~(1ull << d);
+    }
+    return false;
+}
+
+// FP64 form, in the bodies' own coordinates with the level kernels'
+// arithmetic (bit-identical to the oracle): the leaf's row sums are
+// a_a = (G m_b) r^-3 (x_b - x_a) and a_b with -dx.
+// Returns 0, DERR_DEPTH or DERR_SMALL_OVERFLOW (work cap).
+__device__ unsigned pair_path(double A[7], double B[7], double h0, int depth0, int e0, const SmallParams &SP,
+                              const TauParams &P, PairCounters &pc, const NearLog &nl, int ga, int gb)
+{
+    const int dmax = min(SP.max_depth - depth0, 61);  // an edge at node d needs d + 1 <= dmax
+    unsigned long long pend = 0ull;
+    int d = 0, e = e0;
+    for (long long work = 0; work < PAIR_VISIT_LIMIT;) {
+        if (e < 0) {
+            const double tau = tau_fp64(__dsub_rn(A[0], B[0]), __dsub_rn(A[1], B[1]), __dsub_rn(A[2], B[2]),
+                                        __dsub_rn(A[3], B[3]), __dsub_rn(A[4], B[4]), __dsub_rn(A[5], B[5]), A[6],
+                                        B[6], P);
+            ++pc.fp64;
+            e = edge_depth_fp64(tau, scale2m(h0, d), max(dmax - d + 1, 1), [&](double tv, double hm) {
+                near_log(tv, hm, nl.tol, nl.ctr, ga, gb, nl.ij, nl.tau, nl.cap);
+            });
+        }
+        if (e > 0 && d + e > dmax) return DERR_DEPTH;  // an edge at a node below the cap
+        pc.split += e + 1;
+        pc.tau += e + 1;
+        pc.comp += e;
+        work += e + 1;
+        d += e;
+        if (depth0 + d > pc.maxd) pc.maxd = depth0 + d;
+        const double h = scale2m(h0, d), hd = scale2m(h0, d + 1);
+        k8_drift(A, hd, true);
+        k8_drift(B, hd, true);
         const double dx0 = __dsub_rn(B[0], A[0]), dx1 = __dsub_rn(B[1], A[1]), dx2 = __dsub_rn(B[2], A[2]);
         const double r2 = __dadd_rn(__dadd_rn(__dadd_rn(__dmul_rn(dx0, dx0), __dmul_rn(dx1, dx1)),
                                               __dmul_rn(dx2, dx2)), SP.eps2);
@@ -129,73 +207,121 @@ __device__ __forceinline__ void pair_leaf(double A[7], double B[7], double h, bo
         B[3] = __dadd_rn(B[3], __dmul_rn(h, __dmul_rn(wb, -dx0)));
         B[4] = __dadd_rn(B[4], __dmul_rn(h, __dmul_rn(wb, -dx1)));
         B[5] = __dadd_rn(B[5], __dmul_rn(h, __dmul_rn(wb, -dx2)));
-    } else {
-        // FP32 pair force from the FP64-formed difference, rsqrt + one Newton step
-        const float fx = (float)(B[0] - A[0]), fy = (float)(B[1] - A[1]), fz = (float)(B[2] - A[2]);
-        const float r2 = fmaf(fz, fz, fmaf(fy, fy, fmaf(fx, fx, (float)SP.eps2)));
-        float ri = rsqrtf(r2);
-        ri = ri * fmaf(-0.5f * r2, ri * ri, 1.5f);
-        const float r3 = ri * ri * ri;
-        const double ga = SP.G * h * B[6], gb = SP.G * h * A[6];
-        const double ux = (double)(r3 * fx), uy = (double)(r3 * fy), uz = (double)(r3 * fz);
-        A[3] = fma(ga, ux, A[3]);
-        A[4] = fma(ga, uy, A[4]);
-        A[5] = fma(ga, uz, A[5]);
-        B[3] = fma(-gb, ux, B[3]);
-        B[4] = fma(-gb, uy, B[4]);
-        B[5] = fma(-gb, uz, B[5]);
-    }
-    k8_drift(A, hd, !mixed);
-    k8_drift(B, hd, !mixed);
-}
-
-// returns 0 = ok, DERR_DEPTH or DERR_SMALL_OVERFLOW (work cap)
-__device__ unsigned pair_path(double A[7], double B[7], double h0, int depth0, const SmallParams &SP,
-                              const TauParams &P, const MixedTauParams &Q, bool mixed, PairCounters &pc,
-                              DevCounters *ctr, int ga, int gb, int32_t *near_ij, double *near_tau,
-                              long long near_cap)
-{
-    unsigned long long pend = 0ull;
-    int d = 0;
-    for (long long visit = 0; visit < PAIR_VISIT_LIMIT; ++visit) {
-        const double h = ldexp(h0, -d);
-        ++pc.split;
-        ++pc.tau;
-        if (depth0 + d > pc.maxd) pc.maxd = depth0 + d;
-        if (pair_edge(A, B, h, mixed, P, Q, pc, ctr, ga, gb, near_ij, near_tau, near_cap)) {
-            ++pc.comp;
-            if (depth0 + d + 1 > SP.max_depth || d + 1 >= 62) return DERR_DEPTH;
-            ++d;
-            continue;
-        }
-        pair_leaf(A, B, h, mixed, SP);
+        k8_drift(A, hd, true);
+        k8_drift(B, hd, true);
         ++pc.kick;
         pc.drift += 4;
-        bool done = true;
-        while (d > 0) {
-            --d;
-            if (!((pend >> d) & 1ull)) {
-                pend |= 1ull << d;
-                ++d;
-                done = false;
-                break;
-            }
-            pend &= ~(1ull << d);
+        e = -1;
+        if (!pair_next(pend, d)) return 0u;
+    }
+    return DERR_SMALL_OVERFLOW;
+}
+
+// Mixed form, in the pair's own coordinates: inside evolve_cc({a,b}, .)
+// only the pair's mutual force acts, so the centre of mass moves uniformly
+// and the relative state (r = x_a - x_b, u = v_a - v_b, FP64) carries
+// everything.  A leaf is r += h/2 u; u -= h G M r/|r|^3 (FP32 force from
+// fl32(r), rsqrt + Newton); r += h/2 u: nine FP64 FMAs.  The edge decision
+// takes fl32(r), fl32(u) (relative error u) and falls back to the exact
+// FP64 predicate on (r, u); below h_fp64 the force is FP64 as well.
+// Returns 0, DERR_DEPTH or DERR_SMALL_OVERFLOW.
+__device__ unsigned pair_path_rel(double A[7], double B[7], double h0, int depth0, int e0, const SmallParams &SP,
+                                  const TauParams &P, const MixedTauParams &Q, PairCounters &pc, const NearLog &nl,
+                                  int ga, int gb)
+{
+    const double ma = A[6], mb = B[6], M = ma + mb;
+    double R[3], V[3], r[3], u[3];
+    for (int k = 0; k < 3; ++k) {
+        R[k] = (ma * A[k] + mb * B[k]) / M;
+        V[k] = (ma * A[3 + k] + mb * B[3 + k]) / M;
+        r[k] = A[k] - B[k];
+        u[k] = A[3 + k] - B[3 + k];
+    }
+    const float muf = Q.G * (fl32(ma) + fl32(mb));
+    const double GM = SP.G * M;
+    const float e2 = fl32(SP.eps2);
+    const float etah0 = (float)(P.eta_outside ? P.eta_in * P.eta / h0 : P.eta_in / h0);
+    const int dmax = min(SP.max_depth - depth0, 61);
+    const double c0 = -GM * h0;
+    // depths whose pivot h0 2^-d is below h_fp64 take FP64 forces
+    int d64 = 64;
+    if (SP.h_fp64 > 0.0) {
+        d64 = first_level_at_or_below(SP.h_fp64, h0, 64);
+        if (d64 < 64 && scale2m(h0, d64) == SP.h_fp64) ++d64;
+    }
+    unsigned long long pend = 0ull;
+    int d = 0, e = e0;
+    for (long long work = 0; work < PAIR_VISIT_LIMIT;) {
+        if (e < 0) {
+            const TauPrep32 t = tau_prep_fp32(fl32(r[0]), fl32(r[1]), fl32(r[2]), fl32(u[0]), fl32(u[1]),
+                                              fl32(u[2]), muf, 0.f, 0.f, Q);
+            bool used64;
+            e = edge_depth_mixed(
+                t, etah0 * pow2f(d), scale2m(h0, d), max(dmax - d + 1, 1),
+                [&]() { return tau_fp64(r[0], r[1], r[2], u[0], u[1], u[2], ma, mb, P); },
+                [&](double tv, double hm) { near_log(tv, hm, nl.tol, nl.ctr, ga, gb, nl.ij, nl.tau, nl.cap); },
+                used64);
+            pc.fp64 += used64 ? 1 : 0;
         }
-        if (done) return 0u;
+        if (e > 0 && d + e > dmax) return DERR_DEPTH;  // an edge at a node below the cap
+        pc.split += e + 1;
+        pc.tau += e + 1;
+        pc.comp += e;
+        work += e + 1;
+        d += e;
+        if (depth0 + d > pc.maxd) pc.maxd = depth0 + d;
+        const double hd = scale2m(h0, d + 1);
+        r[0] = fma(hd, u[0], r[0]);
+        r[1] = fma(hd, u[1], r[1]);
+        r[2] = fma(hd, u[2], r[2]);
+        const double c = scale2m(c0, d);  // -G M h
+        if (d >= d64) {
+            // below the FP64-force threshold: the force in FP64
+            const double q2 = fma(r[2], r[2], fma(r[1], r[1], fma(r[0], r[0], SP.eps2)));
+            const double w = c / (q2 * sqrt(q2));
+            u[0] = fma(w, r[0], u[0]);
+            u[1] = fma(w, r[1], u[1]);
+            u[2] = fma(w, r[2], u[2]);
+        } else {
+            const float gx = fl32(r[0]), gy = fl32(r[1]), gz = fl32(r[2]);
+            const float q2 = fmaf(gz, gz, fmaf(gy, gy, fmaf(gx, gx, e2)));
+            float ri = rsqrtf(q2);
+            ri = ri * fmaf(-0.5f * q2, ri * ri, 1.5f);
+            const float r3 = ri * ri * ri;
+            u[0] = fma(c, f2d(r3 * gx), u[0]);
+            u[1] = fma(c, f2d(r3 * gy), u[1]);
+            u[2] = fma(c, f2d(r3 * gz), u[2]);
+        }
+        r[0] = fma(hd, u[0], r[0]);
+        r[1] = fma(hd, u[1], r[1]);
+        r[2] = fma(hd, u[2], r[2]);
+        ++pc.kick;
+        pc.drift += 4;
+        e = -1;
+        if (!pair_next(pend, d)) {
+            for (int k = 0; k < 3; ++k) {
+                const double Rk = fma(h0, V[k], R[k]);
+                A[k] = Rk + (mb / M) * r[k];
+                B[k] = Rk - (ma / M) * r[k];
+                A[3 + k] = V[k] + (mb / M) * u[k];
+                B[3 + k] = V[k] - (ma / M) * u[k];
+            }
+            return 0u;
+        }
     }
     return DERR_SMALL_OVERFLOW;
 }
 
 // Hand every two-body set {lane, partner} (leader = the lower lane) to the
 // pair path for its sub-recursion at pivot hsub; states move through shared
-// memory.  Returns a device error code (0 = ok) uniform over the warp.
+// memory.  First halves (eoff >= 0) start from the edge depths of the
+// split just taken: the pair's depth at hsub is S.e - eoff unless the stored
+// value hit its scan cap ecap.  Returns a device error code (0 = ok)
+// uniform over the warp.
 __device__ __forceinline__ unsigned k8_pair_handoff(K8Warp &S, int lane, double st[7], uint32_t cm, bool is_sub,
-                                                    double hsub, int dsub, const SmallParams &SP,
+                                                    double hsub, int dsub, int eoff, int ecap, const SmallParams &SP,
                                                     const TauParams &P, const MixedTauParams &Q, bool mixed,
-                                                    PairCounters &pc, DevCounters *ctr, const Level &L,
-                                                    const int32_t *members, int base, int32_t *near_ij,
-                                                    double *near_tau, long long near_cap)
+                                                    PairCounters &pc, const NearLog &nl)
 {
     k8_publish(S, lane, st, false);
     const uint32_t me = 1u << lane;
@@ -206,8 +332,13 @@ __device__ __forceinline__ unsigned k8_pair_handoff(K8Warp &S, int lane, double 
         double B[7];
 #pragma unroll
         for (int c = 0; c < 7; ++c) B[c] = S.d[c][j];
-        err = pair_path(st, B, hsub, dsub, SP, P, Q, mixed, pc, ctr, L.gid[members[base + lane]],
-                        L.gid[members[base + j]], near_ij, near_tau, near_cap);
+        const int ga = S.gid[lane], gb = S.gid[j];
+        const int ec = S.e[j][lane];
+        const int e0 = (eoff >= 0 && ec < ecap) ? ec - eoff : -1;
+        if (mixed)
+            err = pair_path_rel(st, B, hsub, dsub, e0, SP, P, Q, pc, nl, ga, gb);
+        else
+            err = pair_path(st, B, hsub, dsub, e0, SP, P, pc, nl, ga, gb);
 #pragma unroll
         for (int c = 0; c < 6; ++c) S.d[c][j] = B[c];
     }
@@ -231,6 +362,7 @@ __global__ void __launch_bounds__(K8_WARPS * 32) k_small(Level L, const int32_t 
     const uint32_t me = 1u << lane;
     uint32_t mk[K8_MAXD], cmk[K8_MAXD];
     unsigned char ph[K8_MAXD], pm[K8_MAXD];
+    signed char cf[K8_MAXD];  // level whose fresh split filled S.e for level k's state (-1: none)
     PairCounters pc;
     unsigned long long c_tau = 0, c_kick = 0, c_drift = 0, c_split = 0, c_comp = 0, c_kep = 0, c_fp64 = 0;
     int maxd = 0;
@@ -240,6 +372,7 @@ __global__ void __launch_bounds__(K8_WARPS * 32) k_small(Level L, const int32_t 
     P.near_tol = SP.near_tol;
     MixedTauParams Q;
     Q.eta = (float)SP.eta_in; Q.eps2 = (float)SP.eps2; Q.G = (float)SP.G;
+    const NearLog nl = {ctr, near_ij, near_tau, near_cap, SP.near_tol};
     for (;;) {
         int q = 0;
         if (lane == 0) q = atomicAdd(queue, 1);
@@ -258,12 +391,15 @@ __global__ void __launch_bounds__(K8_WARPS * 32) k_small(Level L, const int32_t 
         int k = 0;
         mk[0] = act ? all : 0u;
         ph[0] = 0;
+        cf[0] = -1;
+        __syncwarp();
+        S.gid[lane] = act ? L.gid[p] : -1;
+        __syncwarp();
         bool bad = false;
         if (SP.depth0 > maxd) maxd = SP.depth0;
         if (n == 2) {
             // a two-body component: its whole recursion on the pair path
-            const unsigned e = k8_pair_handoff(S, lane, st, 3u, act, SP.h0, SP.depth0, SP, P, Q, mixed, pc, ctr, L,
-                                               members, base, near_ij, near_tau, near_cap);
+            const unsigned e = k8_pair_handoff(S, lane, st, 3u, act, SP.h0, SP.depth0, -1, 0, SP, P, Q, mixed, pc, nl);
             if (e) {
                 raise_err(ctr, e);
                 bad = true;
@@ -274,50 +410,59 @@ __global__ void __launch_bounds__(K8_WARPS * 32) k_small(Level L, const int32_t 
             const double h = ldexp(SP.h0, -k);
             const uint32_t mine = mk[k];
             if (ph[k] == 0) {
-                // ---------------- split at h: tau(i,j) < h inside the lane's set
-                k8_publish(S, lane, st, mixed);
-                P.h = h;
-                Q.etah = (float)(SP.eta_outside ? SP.eta_in * SP.eta / h : SP.eta_in / h);
-                const float c11 = 11.f * U32 * U32;
+                // ---------------- split at h: tau(i,j) < h inside the lane's set.
+                // A fresh state (the component's start, a second half) takes
+                // every pair's edge depth; a first half reads them, since its
+                // state is the one its parent split.
+                if (cf[k] < 0) {
+                    k8_publish(S, lane, st, mixed);
+                    P.h = h;
+                    const float etah = (float)(SP.eta_outside ? SP.eta_in * SP.eta / h : SP.eta_in / h);
+                    const float c11 = 11.f * U32 * U32;
+                    const int levels = K8_MAXD - k;
+                    if (mine) {
+                        for (int j = 0; j < n; ++j) {
+                            if (j == lane || !((mine >> j) & 1u)) continue;
+                            const int lo = lane < j ? lane : j, hi = lane < j ? j : lane;
+                            // FP64 tau, in the pair's fixed order (symmetric bit for bit)
+                            auto tau64 = [&]() {
+                                return tau_fp64(__dsub_rn(S.d[0][lo], S.d[0][hi]), __dsub_rn(S.d[1][lo], S.d[1][hi]),
+                                                __dsub_rn(S.d[2][lo], S.d[2][hi]), __dsub_rn(S.d[3][lo], S.d[3][hi]),
+                                                __dsub_rn(S.d[4][lo], S.d[4][hi]), __dsub_rn(S.d[5][lo], S.d[5][hi]),
+                                                S.d[6][lo], S.d[6][hi], P);
+                            };
+                            auto log = [&](double tv, double hm) {
+                                if (lane < j)
+                                    near_log(tv, hm, nl.tol, nl.ctr, S.gid[lane], S.gid[j], nl.ij, nl.tau, nl.cap);
+                            };
+                            int e;
+                            if (mixed) {
+                                const TauPrep32 t = tau_prep_fp32(
+                                    (S.f[0][j] - S.f[0][lane]) + (S.f[6][j] - S.f[6][lane]),
+                                    (S.f[1][j] - S.f[1][lane]) + (S.f[7][j] - S.f[7][lane]),
+                                    (S.f[2][j] - S.f[2][lane]) + (S.f[8][j] - S.f[8][lane]),
+                                    (S.f[3][j] - S.f[3][lane]) + (S.f[9][j] - S.f[9][lane]),
+                                    (S.f[4][j] - S.f[4][lane]) + (S.f[10][j] - S.f[10][lane]),
+                                    (S.f[5][j] - S.f[5][lane]) + (S.f[11][j] - S.f[11][lane]),
+                                    Q.G * (S.f[12][lane] + S.f[12][j]), c11 * fmaxf(S.xm[lane], S.xm[j]),
+                                    c11 * fmaxf(S.vm[lane], S.vm[j]), Q);
+                                bool used64;
+                                e = edge_depth_mixed(t, etah, h, levels, tau64, log, used64);
+                                if (used64 && lane < j) ++c_fp64;
+                            } else {
+                                e = edge_depth_fp64(tau64(), h, levels, log);
+                                if (lane < j) ++c_fp64;
+                            }
+                            S.e[j][lane] = (unsigned char)e;
+                        }
+                    }
+                    cf[k] = (signed char)k;
+                }
+                const int eoff = k - cf[k];
                 uint32_t adj = 0;
                 if (mine) {
-                    for (int j = 0; j < n; ++j) {
-                        if (j == lane || !((mine >> j) & 1u)) continue;
-                        int dec = -1;
-                        if (mixed) {
-                            dec = tau_decide_fp32((S.f[0][j] - S.f[0][lane]) + (S.f[6][j] - S.f[6][lane]),
-                                                  (S.f[1][j] - S.f[1][lane]) + (S.f[7][j] - S.f[7][lane]),
-                                                  (S.f[2][j] - S.f[2][lane]) + (S.f[8][j] - S.f[8][lane]),
-                                                  (S.f[3][j] - S.f[3][lane]) + (S.f[9][j] - S.f[9][lane]),
-                                                  (S.f[4][j] - S.f[4][lane]) + (S.f[10][j] - S.f[10][lane]),
-                                                  (S.f[5][j] - S.f[5][lane]) + (S.f[11][j] - S.f[11][lane]),
-                                                  Q.G * (S.f[12][lane] + S.f[12][j]),
-                                                  c11 * fmaxf(S.xm[lane], S.xm[j]), c11 * fmaxf(S.vm[lane], S.vm[j]),
-                                                  Q);
-                        }
-                        if (dec < 0) {
-                            const int lo = lane < j ? lane : j, hi = lane < j ? j : lane;
-                            const double tau = tau_fp64(
-                                __dsub_rn(S.d[0][lo], S.d[0][hi]), __dsub_rn(S.d[1][lo], S.d[1][hi]),
-                                __dsub_rn(S.d[2][lo], S.d[2][hi]), __dsub_rn(S.d[3][lo], S.d[3][hi]),
-                                __dsub_rn(S.d[4][lo], S.d[4][hi]), __dsub_rn(S.d[5][lo], S.d[5][hi]),
-                                S.d[6][lo], S.d[6][hi], P);
-                            if (lane < j) {
-                                ++c_fp64;
-                                if (fabs(tau - h) < P.near_tol * h) {
-                                    const unsigned long long z = atomicAdd(&ctr->near_pairs, 1ull);
-                                    if ((long long)z < near_cap) {
-                                        const int ga = L.gid[members[base + lane]], gb = L.gid[members[base + j]];
-                                        near_ij[2 * z] = ga < gb ? ga : gb;
-                                        near_ij[2 * z + 1] = ga < gb ? gb : ga;
-                                        near_tau[z] = tau;
-                                    }
-                                }
-                            }
-                            dec = tau < h ? 1 : 0;
-                        }
-                        if (dec) adj |= 1u << j;
-                    }
+                    for (int j = 0; j < n; ++j)
+                        if (j != lane && ((mine >> j) & 1u) && S.e[j][lane] > eoff) adj |= 1u << j;
                 }
                 // components: closure of the adjacency by mask doubling
                 uint32_t cm = mine ? (adj | me) : 0u;
@@ -348,9 +493,8 @@ __global__ void __launch_bounds__(K8_WARPS * 32) k_small(Level L, const int32_t 
                 // pair path (first half now, second half after the DKD)
                 pm[k] = __all_sync(FULL, !sub || csz == 2) ? 1 : 0;
                 if (pm[k] && __any_sync(FULL, sub)) {
-                    const unsigned e = k8_pair_handoff(S, lane, st, cm, sub, 0.5 * h, SP.depth0 + k + 1, SP, P, Q,
-                                                       mixed, pc, ctr, L, members, base, near_ij, near_tau,
-                                                       near_cap);
+                    const unsigned e = k8_pair_handoff(S, lane, st, cm, sub, 0.5 * h, SP.depth0 + k + 1,
+                                                       k + 1 - cf[k], K8_MAXD - cf[k], SP, P, Q, mixed, pc, nl);
                     if (e) {
                         raise_err(ctr, e);
                         bad = true;
@@ -365,6 +509,7 @@ __global__ void __launch_bounds__(K8_WARPS * 32) k_small(Level L, const int32_t 
                     }
                     mk[k + 1] = sub ? cm : 0u;
                     ph[k + 1] = 0;
+                    cf[k + 1] = cf[k];  // first half: the state this split saw
                     ++k;
                     if (SP.depth0 + k > maxd) maxd = SP.depth0 + k;
                     continue;
@@ -433,9 +578,9 @@ __global__ void __launch_bounds__(K8_WARPS * 32) k_small(Level L, const int32_t 
                                     kahan_add(sz, cz, ww * dz);
                                 }
                                 const double gh = SP.G * h;
-                                st[3] = fma(gh, (double)sx - (double)cx, st[3]);
-                                st[4] = fma(gh, (double)sy - (double)cy, st[4]);
-                                st[5] = fma(gh, (double)sz - (double)cz, st[5]);
+                                st[3] = fma(gh, f2d(sx) - f2d(cx), st[3]);
+                                st[4] = fma(gh, f2d(sy) - f2d(cy), st[4]);
+                                st[5] = fma(gh, f2d(sz) - f2d(cz), st[5]);
                             }
                         }
                         if (single) k8_drift(st, hd, !mixed);
@@ -460,9 +605,8 @@ __global__ void __launch_bounds__(K8_WARPS * 32) k_small(Level L, const int32_t 
                 ph[k] = 2;
                 if (__any_sync(FULL, sub)) {
                     if (pm[k]) {
-                        const unsigned e = k8_pair_handoff(S, lane, st, cm, sub, 0.5 * h, SP.depth0 + k + 1, SP, P,
-                                                           Q, mixed, pc, ctr, L, members, base, near_ij, near_tau,
-                                                           near_cap);
+                        const unsigned e = k8_pair_handoff(S, lane, st, cm, sub, 0.5 * h, SP.depth0 + k + 1, -1, 0,
+                                                           SP, P, Q, mixed, pc, nl);
                         if (e) {
                             raise_err(ctr, e);
                             bad = true;
@@ -471,6 +615,7 @@ __global__ void __launch_bounds__(K8_WARPS * 32) k_small(Level L, const int32_t 
                     } else {
                         mk[k + 1] = sub ? cm : 0u;
                         ph[k + 1] = 0;
+                        cf[k + 1] = -1;  // second half: the DKD moved the state
                         ++k;
                         continue;
                     }
