@@ -276,6 +276,8 @@ def run_gpu(args, rank, world):
                "inter": (st1["tau_pairs"] - st0["tau_pairs"]) + (st1["kick_pairs"] - st0["kick_pairs"]),
                "launches": st1["launches"] - st0["launches"],
                "tau_fp64": st1["tau_fp64"] - st0["tau_fp64"], "tau_pairs": st1["tau_pairs"] - st0["tau_pairs"],
+               "tau_evaluated": st1["tau_evaluated"] - st0["tau_evaluated"],
+               "kick_pairs": st1["kick_pairs"] - st0["kick_pairs"],
                "dE": (E1 - E0) / abs(E0)}
         return res
 
@@ -361,6 +363,12 @@ def run_gpu(args, rank, world):
             "dE_over_E": head["dE"],
             "tau_fp64_fraction": head["tau_fp64"] / max(1, head["tau_pairs"]),
             "interactions_per_step": inter / args.steps / world,
+            # interactions = tau pairs decided by the splits + kick pairs; a
+            # first-half split decides its pairs from the tau values its
+            # parent split computed, so fewer pairs are evaluated than decided
+            "tau_pairs_per_step": head["tau_pairs"] / args.steps,
+            "tau_pairs_evaluated_per_step": head["tau_evaluated"] / args.steps,
+            "kick_pairs_per_step": head["kick_pairs"] / args.steps,
             "other_form": other_line,
         }
         print(json.dumps(line), flush=True)

@@ -72,6 +72,10 @@ typedef struct {
     uint64_t near_pairs;    /* pairs with |tau-h| < near_tol*h                        */
     uint64_t small_tasks;   /* components run by the small-component kernel          */
     uint64_t launches;      /* kernels this context launched                          */
+    uint64_t tau_evaluated; /* pairs whose tau a kernel computed: tau_pairs counts every
+                               pair a split decides, but the split of a component's
+                               first half sees the state its parent split saw, and
+                               takes the edges from the parent's tau values instead  */
     int32_t  max_depth_seen;
     int32_t  reserved;
 } cc_stats_t;

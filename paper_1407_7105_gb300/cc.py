@@ -33,7 +33,8 @@ class Stats(C.Structure):
     _fields_ = [("tau_pairs", C.c_uint64), ("tau_fp64", C.c_uint64), ("kick_pairs", C.c_uint64),
                 ("drifts", C.c_uint64), ("kepler_calls", C.c_uint64), ("splits", C.c_uint64),
                 ("components", C.c_uint64), ("edges", C.c_uint64), ("near_pairs", C.c_uint64),
-                ("small_tasks", C.c_uint64), ("launches", C.c_uint64), ("max_depth_seen", C.c_int32),
+                ("small_tasks", C.c_uint64), ("launches", C.c_uint64), ("tau_evaluated", C.c_uint64),
+                ("max_depth_seen", C.c_int32),
                 ("reserved", C.c_int32)]
 
     def as_dict(self):

@@ -61,6 +61,12 @@ struct LevelAlloc {
     int32_t *h_lists = nullptr;    // pinned staging of the component lists (one H2D)
     int info_cap = 0;
     cudaEvent_t ev_ready = nullptr, ev_small = nullptr;  // side-stream joins
+    // edge records of this level's last split (read by the first-half split
+    // of the next level) and the parent -> child index map of the gather
+    int32_t *inv = nullptr;
+    EdgeList E{nullptr, nullptr, 0};
+    void *eblock = nullptr;
+    long long ecount = 0;  // records the last split offered (complete if <= E.cap)
 };
 
 // ------------------------------------------------------------ autotuner
@@ -307,7 +313,9 @@ static void free_level(LevelAlloc &a)
     if (a.block) cudaFree(a.block);
     if (a.setblock) cudaFree(a.setblock);
     if (a.listblock) cudaFree(a.listblock);
-    a.block = a.setblock = a.listblock = nullptr;
+    if (a.eblock) cudaFree(a.eblock);
+    a.block = a.setblock = a.listblock = a.eblock = nullptr;
+    a.E = EdgeList{nullptr, nullptr, 0};
     a.cap = a.set_cap = a.list_cap = 0;
 }
 
@@ -322,7 +330,7 @@ static int ensure_level(cc_ctx *c, LevelAlloc &a, int need, int nsets)
         const long long worst = std::min<long long>(2 * (long long)c->n + 64, 0x3fffffff);
         int cap = align_up(std::max<int>(need, (int)std::max<long long>(64, worst)), 64);
         size_t nd = (size_t)cap + PAD_TAIL;
-        size_t bytes = nd * 8 * 7 + nd * 4 * 11 + nd * 64 + 4096;
+        size_t bytes = nd * 8 * 7 + nd * 4 * 12 + nd * 64 + 4096;
         if (cudaMalloc(&a.block, bytes) != cudaSuccess) {
             cudaGetLastError();
             return fail(c, CC_E_NOMEM, "device allocation failed (level buffer)");
@@ -331,9 +339,9 @@ static int ensure_level(cc_ctx *c, LevelAlloc &a, int need, int nsets)
         char *q = (char *)a.block;
         double **dp[7] = {&a.L.x, &a.L.y, &a.L.z, &a.L.vx, &a.L.vy, &a.L.vz, &a.L.m};
         for (int k = 0; k < 7; ++k) { *dp[k] = (double *)q; q += nd * 8; }
-        int32_t **ip[11] = {&a.L.gid, &a.L.sidx, &a.L.src, &a.L.parent, &a.L.cnt, &a.L.klab,
-                            &a.root, &a.members, &a.comp_start, &a.comp_size, &a.d_ncomp};
-        for (int k = 0; k < 11; ++k) { *ip[k] = (int32_t *)q; q += nd * 4; }
+        int32_t **ip[12] = {&a.L.gid, &a.L.sidx, &a.L.src, &a.L.parent, &a.L.cnt, &a.L.klab,
+                            &a.root, &a.members, &a.comp_start, &a.comp_size, &a.d_ncomp, &a.inv};
+        for (int k = 0; k < 12; ++k) { *ip[k] = (int32_t *)q; q += nd * 4; }
         a.F.pq = (float4 *)q; q += nd * 32;
         a.F.vq = (float4 *)q; q += nd * 32;
         a.F.maxes = (float *)q;
@@ -396,6 +404,32 @@ static int ensure_level(cc_ctx *c, LevelAlloc &a, int need, int nsets)
         }
         c->seg_scratch_sz = need_seg;
     }
+    return CC_OK;
+}
+
+// Edge-record list of a level: 4 records per element at first, grown to
+// twice the last count when a split overflowed it (up to EDGE_CAP_MAX); an
+// incomplete list only means the next first-half split evaluates tau itself.
+constexpr long long EDGE_CAP_MAX = 1ll << 22;
+
+static int ensure_edges(cc_ctx *c, LevelAlloc &a)
+{
+    long long want = std::max<long long>(4096, 4ll * a.cap);
+    if (a.ecount > a.E.cap) want = std::max(want, 2 * a.ecount);
+    want = std::min(want, EDGE_CAP_MAX);
+    if (a.eblock && want <= a.E.cap) return CC_OK;
+    if (a.eblock && a.E.cap >= EDGE_CAP_MAX) return CC_OK;
+    if (a.eblock) cudaFree(a.eblock);
+    a.eblock = nullptr;
+    a.E = EdgeList{nullptr, nullptr, 0};
+    if (cudaMalloc(&a.eblock, 256 + (size_t)want * sizeof(EdgeRec)) != cudaSuccess) {
+        cudaGetLastError();
+        return fail(c, CC_E_NOMEM, "device allocation failed (edge records)");
+    }
+    a.E.count = (unsigned long long *)a.eblock;
+    a.E.rec = (EdgeRec *)((char *)a.eblock + 256);
+    a.E.cap = want;
+    CC_CUDA(c, cudaMemsetAsync(a.eblock, 0, 256, c->stream));
     return CC_OK;
 }
 
@@ -512,33 +546,44 @@ static int check_device_error(cc_ctx *c)
 }
 
 // ------------------------------------------------------------ recursion
-static int process(cc_ctx *c, int d, double h);
+static int process(cc_ctx *c, int d, double h, const LevelAlloc *parent);
 
-// split the batch of level d at h: union-find components and segments
-static int split_level(cc_ctx *c, LevelAlloc &a, double h, int &ncomp)
+// split the batch of level d at h: union-find components and segments.
+// parent != null: this is the first half of the parent's components, whose
+// split saw the same state at 2h, so the edges come from the parent's
+// edge records (a pass over the records instead of all pairs).
+static int split_level(cc_ctx *c, LevelAlloc &a, double h, int &ncomp, const LevelAlloc *parent)
 {
     const cudaStream_t s = c->stream;
     const TauParams P = tau_params(c, h);
-    launch_init_parent(a.L, s);
+    CC_TRY(ensure_edges(c, a));
+    launch_init_parent(a.L, a.E.count, s);
     const bool mixed = c->p.precision == CC_PREC_MIXED;
-    const int tk = mixed ? TK_TAUMIX : TK_TAU64;
-    int bin;
-    bool timed;
-    const int var = tune_pick(c, tk, a.tau_blocks, a.pairs, &bin, &timed);
-    const long long ntiles = a.tau_blocks[var];
-    if (ntiles > 0x7fffffff) return fail(c, CC_E_ARG, "set too large for the tile grid");
-    Level L = a.L;
-    L.tile_off = a.tau_off[var];
-    int ev;
-    if (mixed) {
-        launch_prep_ff(a.L, a.F, c->p.G, true, s);
-        ev = ev_begin(c, 0, nullptr, timed ? tk : -1, bin, var, (double)a.pairs);
-        launch_tau_mixed(L, a.F, (int)ntiles, P, var, c->d_ctr, c->d_near_ij, c->d_near_tau, c->near_cap, s);
+    if (parent) {
+        launch_edges_reuse(parent->E, parent->ecount, parent->L, parent->inv, a.L, a.E, P, c->d_ctr, c->d_near_ij,
+                           c->d_near_tau, c->near_cap, s);
     } else {
-        ev = ev_begin(c, 0, nullptr, timed ? tk : -1, bin, var, (double)a.pairs);
-        launch_tau_hook(L, (int)ntiles, P, var, c->d_ctr, nullptr, 0, c->d_near_ij, c->d_near_tau, c->near_cap, s);
+        const int tk = mixed ? TK_TAUMIX : TK_TAU64;
+        int bin;
+        bool timed;
+        const int var = tune_pick(c, tk, a.tau_blocks, a.pairs, &bin, &timed);
+        const long long ntiles = a.tau_blocks[var];
+        if (ntiles > 0x7fffffff) return fail(c, CC_E_ARG, "set too large for the tile grid");
+        Level L = a.L;
+        L.tile_off = a.tau_off[var];
+        int ev;
+        if (mixed) {
+            launch_prep_ff(a.L, a.F, c->p.G, true, s);
+            ev = ev_begin(c, 0, nullptr, timed ? tk : -1, bin, var, (double)a.pairs);
+            launch_tau_mixed(L, a.F, (int)ntiles, P, var, c->d_ctr, c->d_near_ij, c->d_near_tau, c->near_cap, a.E,
+                             s);
+        } else {
+            ev = ev_begin(c, 0, nullptr, timed ? tk : -1, bin, var, (double)a.pairs);
+            launch_tau_hook(L, (int)ntiles, P, var, c->d_ctr, nullptr, 0, c->d_near_ij, c->d_near_tau, c->near_cap,
+                            s, &a.E);
+        }
+        ev_end(c, ev);
     }
-    ev_end(c, ev);
     launch_compress_segment(a.L, a.root, a.members, a.comp_start, a.comp_size, a.d_ncomp, c->seg_scratch, s);
     // one round trip: the count and, bounded by total/2, sizes and starts
     const int maxc = a.L.total / 2 + 1;
@@ -550,11 +595,13 @@ static int split_level(cc_ctx *c, LevelAlloc &a, double h, int &ncomp)
         a.info_cap = cap2;
     }
     CC_CUDA(c, cudaMemcpyAsync(a.h_info, a.d_ncomp, 4, cudaMemcpyDeviceToHost, s));
+    CC_CUDA(c, cudaMemcpyAsync(a.h_info + 2, a.E.count, 8, cudaMemcpyDeviceToHost, s));
     CC_CUDA(c, cudaMemcpyAsync(a.h_info + 4, a.comp_size, (size_t)maxc * 4, cudaMemcpyDeviceToHost, s));
     CC_CUDA(c, cudaMemcpyAsync(a.h_info + 4 + a.info_cap, a.comp_start, (size_t)maxc * 4, cudaMemcpyDeviceToHost, s));
     CC_CUDA(c, cudaStreamSynchronize(s));
     const int32_t nc = a.h_info[0];
     ncomp = nc;
+    std::memcpy(&a.ecount, a.h_info + 2, 8);
     a.h_size.assign(a.h_info + 4, a.h_info + 4 + nc);
     a.h_start.assign(a.h_info + 4 + a.info_cap, a.h_info + 4 + a.info_cap + nc);
     // statistics: n(n-1)/2 tau pairs per set, cross-component kick pairs
@@ -570,8 +617,9 @@ static int split_level(cc_ctx *c, LevelAlloc &a, double h, int &ncomp)
     c->st.splits += a.h_set_n.size();
     c->st.tau_pairs += tp;
     if (c->p.precision != CC_PREC_MIXED) c->st.tau_fp64 += tp;
+    if (!parent) c->st.tau_evaluated += tp;
     if (c->timing) {
-        c->tm.tau_pairs += tp;
+        if (!parent) c->tm.tau_pairs += tp;
         c->tm.kick_pairs += tp - inner;
     }
     c->st.components += nc;
@@ -635,7 +683,7 @@ static int dkd(cc_ctx *c, LevelAlloc &a, double h)
     return CC_OK;
 }
 
-static int process(cc_ctx *c, int d, double h)
+static int process(cc_ctx *c, int d, double h, const LevelAlloc *parent)
 {
     if (d > c->p.max_depth) return fail(c, CC_E_DEPTH, "recursion deeper than max_depth");
     if (d > c->st.max_depth_seen) c->st.max_depth_seen = d;
@@ -643,7 +691,7 @@ static int process(cc_ctx *c, int d, double h)
     // so references into it stay valid across the recursion
     LevelAlloc &a = c->lv[d];
     int ncomp = 0;
-    CC_TRY(split_level(c, a, h, ncomp));
+    CC_TRY(split_level(c, a, h, ncomp, parent));
     // classify the components (host, sizes are known)
     std::vector<int32_t> kl, sl, lstart, lsize;
     for (int q = 0; q < ncomp; ++q) {
@@ -719,8 +767,11 @@ static int process(cc_ctx *c, int d, double h)
         if (nk) launch_kepler(a2.L, a2.members, a2.comp_start, a2.klist, nk, c->p.G, 0.5 * h, c->d_ctr, c->stream);
         if (nl) {
             LevelAlloc &ch = c->lv[d + 1];
-            launch_gather(a2.L, ch.L, a2.members, a2.lcomp_start, a2.lpref, a2.ldst, nl, nmem, nl, c->stream);
-            CC_TRY(process(c, d + 1, 0.5 * h));
+            launch_gather(a2.L, ch.L, a2.members, a2.lcomp_start, a2.lpref, a2.ldst, nl, nmem, a2.inv, c->stream);
+            // first half: the state this split saw, so its edge records
+            // (when complete) give the child's split; second half: fresh
+            const bool reuse = half == 0 && a2.ecount <= a2.E.cap;
+            CC_TRY(process(c, d + 1, 0.5 * h, reuse ? &a2 : nullptr));
             launch_scatter(a2.L, ch.L, c->stream);
         }
     }
@@ -769,12 +820,10 @@ static int harvest_counters(cc_ctx *c)
     c->st.splits += h.small_splits;
     c->st.components += h.small_components;
     c->st.kepler_calls += h.small_kepler;
-    if (c->timing) {
-        c->tm.tau_pairs += h.small_tau_pairs;
-        c->tm.kick_pairs += h.small_kick_pairs;
-    }
+    c->st.tau_evaluated += h.tau_evals;
     if (h.max_depth_seen > c->st.max_depth_seen) c->st.max_depth_seen = h.max_depth_seen;
-    CC_CUDA(c, cudaMemsetAsync(&c->d_ctr->tau_fp64, 0, sizeof(unsigned long long) * 8, c->stream));
+    // tau_fp64 .. tau_evals
+    CC_CUDA(c, cudaMemsetAsync(&c->d_ctr->tau_fp64, 0, sizeof(unsigned long long) * 9, c->stream));
     return CC_OK;
 }
 
@@ -934,7 +983,7 @@ int cc_evolve(cc_ctx *c, double t_end, double eta)
     const double t0 = c->t;
     for (long long k = 0; k < nsteps; ++k) {
         launch_pack_state(c->d_x3, c->d_v3, c->d_m, c->n, c->lv[0].L, c->d_sys_off, c->stream);
-        int rc = process(c, 0, c->p.dt);
+        int rc = process(c, 0, c->p.dt, nullptr);
         if (rc) return rc;
         launch_unpack_state(c->d_x3, c->d_v3, c->n, c->lv[0].L, c->stream);
         CC_TRY(check_device_error(c));
@@ -980,7 +1029,7 @@ int cc_components(cc_ctx *c, const int32_t *set, int64_t n_set, double h, int32_
     CC_TRY(stage_set(c, set, n_set, nullptr));
     CC_TRY(reset_call_counters(c));
     int nc = 0;
-    CC_TRY(split_level(c, c->unit, h, nc));
+    CC_TRY(split_level(c, c->unit, h, nc, nullptr));
     if (labels_out) {
         int32_t *dl = (int32_t *)c->tmp + n_set;
         launch_label_canon(c->unit.L, c->unit.root, dl, (int)n_set, c->stream);
@@ -1005,7 +1054,7 @@ int cc_timestep_graph(cc_ctx *c, const int32_t *set, int64_t n_set, double h, in
     const long long nt = (n_set + TAU_TILE - 1) / TAU_TILE;
     Level UL = u.L;
     UL.tile_off = u.tau_off[N_TAU_VAR - 1];  // 128-wide tiles
-    launch_init_parent(u.L, c->stream);
+    launch_init_parent(u.L, nullptr, c->stream);
     launch_tau_hook(UL, (int)(nt * (nt + 1) / 2), P, N_TAU_VAR - 1, c->d_ctr, nullptr, 0, c->d_near_ij,
                     c->d_near_tau, c->near_cap, c->stream);
     DevCounters h1;
@@ -1025,7 +1074,7 @@ int cc_timestep_graph(cc_ctx *c, const int32_t *set, int64_t n_set, double h, in
         int32_t *de = (int32_t *)((char *)c->tmp + (size_t)n_set * 16);
         void *ss = (void *)(de + 2 * ne);
         CC_TRY(reset_call_counters(c));
-        launch_init_parent(u.L, c->stream);
+        launch_init_parent(u.L, nullptr, c->stream);
         launch_tau_hook(UL, (int)(nt * (nt + 1) / 2), P, N_TAU_VAR - 1, c->d_ctr, de, ne, c->d_near_ij,
                         c->d_near_tau, c->near_cap, c->stream);
         int bits = 0;

@@ -196,6 +196,20 @@ __device__ __forceinline__ double f2d(float f)
     return __longlong_as_double((long long)b);
 }
 
+// one edge record at an atomically reserved slot (dropped past cap; the
+// count still tells the host the list is incomplete)
+__device__ __forceinline__ void record_edge(const EdgeList &E, int a, int b, double tau)
+{
+    const unsigned long long q = atomicAdd(E.count, 1ull);
+    if ((long long)q < E.cap) {
+        EdgeRec r;
+        r.a = a;
+        r.b = b;
+        r.tau = tau;
+        E.rec[q] = r;
+    }
+}
+
 // Kahan-compensated accumulation: s + (-c) carries the running sum
 __device__ __forceinline__ void kahan_add(float &s, float &c, float x)
 {

@@ -428,7 +428,7 @@ __device__ __forceinline__ int upper_find(const int32_t *off, int nsets, int t)
 }
 
 __global__ void k_gather(Level P, Level C, const int32_t *members, const int32_t *lcomp_start,
-                         const int32_t *lpref, const int32_t *ldst, int nl, int nmem)
+                         const int32_t *lpref, const int32_t *ldst, int nl, int nmem, int32_t *inv)
 {
     const int t = blockIdx.x * blockDim.x + threadIdx.x;
     if (t >= nmem) return;
@@ -442,15 +442,17 @@ __global__ void k_gather(Level P, Level C, const int32_t *members, const int32_t
     C.gid[d] = P.gid[k];
     C.src[d] = k;
     C.sidx[d] = c;
+    inv[k] = d;
 }
 
+// inv[k] = the child index of parent element k (written for the gathered
+// elements only; a reader checks C.src[inv[k]] == k)
 void launch_gather(const Level &P, const Level &C, const int32_t *members, const int32_t *lcomp_start,
-                   const int32_t *lpref, const int32_t *ldst, int nl, int nmem, int nsets_child, cudaStream_t s)
+                   const int32_t *lpref, const int32_t *ldst, int nl, int nmem, int32_t *inv, cudaStream_t s)
 {
-    (void)nsets_child;
     fill_pad(C, s);
     if (nmem > 0) {
-        k_gather<<<(nmem + 255) / 256, 256, 0, s>>>(P, C, members, lcomp_start, lpref, ldst, nl, nmem);
+        k_gather<<<(nmem + 255) / 256, 256, 0, s>>>(P, C, members, lcomp_start, lpref, ldst, nl, nmem, inv);
         CC_COUNT_LAUNCH(1);
     }
 }

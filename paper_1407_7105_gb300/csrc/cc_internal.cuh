@@ -45,6 +45,22 @@ struct FFView {
     int cap;
 };
 
+// Edge record of a split at pivot h: packed indices a < b of the level
+// (tau(a,b) < h) and tau in FP64 when the split evaluated it (NaN when the
+// certified FP32 decision settled the edge).  The first-half split of a
+// component at h/2 sees the same state, so its edges are the records with
+// tau < h/2, and its near-threshold pairs (tau within near_tol of h/2) are
+// records too (tau < h).
+struct EdgeRec {
+    int32_t a, b;
+    double tau;
+};
+struct EdgeList {
+    EdgeRec *rec;                  // [cap]
+    unsigned long long *count;     // records offered (may exceed cap: list incomplete)
+    long long cap;
+};
+
 // bounded-wait error codes written to the device error word
 enum DevErr : unsigned {
     DERR_NONE = 0,
@@ -66,6 +82,7 @@ struct DevCounters {
     unsigned long long small_kepler;
     unsigned long long small_splits;
     unsigned long long small_components;
+    unsigned long long tau_evals;  // pairs whose tau the small kernel or the edge-record pass evaluated
     unsigned int err;
     int max_depth_seen;
 };
@@ -220,7 +237,7 @@ extern unsigned long long g_launches;
 #define CC_COUNT_LAUNCH(k) (::cc::g_launches += (k))
 
 // cc_pair.cu
-void launch_init_parent(const Level &L, cudaStream_t s);
+void launch_init_parent(const Level &L, unsigned long long *edge_count, cudaStream_t s);
 // tunable launch shapes (variant index): tau tiles {64, 128}; FP64 kick
 // tiles {32, 64, 128}; mixed kick j-chunks {1, 4, 16} tiles of 128
 constexpr int N_TAU_VAR = 2, N_K64_VAR = 3, N_MK_VAR = 3;
@@ -230,7 +247,14 @@ constexpr int MK_VAR_CHUNK[N_MK_VAR] = {1, 4, 16};
 constexpr int MK_TILE = 128;
 void launch_tau_hook(const Level &L, int ntiles, const TauParams &P, int variant, DevCounters *ctr,
                      int32_t *edges, long long edge_cap, int32_t *near_ij, double *near_tau, long long near_cap,
-                     cudaStream_t s);
+                     cudaStream_t s, const EdgeList *rec = nullptr);
+// first-half split from the parent split's edge records: the records with
+// tau < P.h whose endpoints the gather moved to this level (inv = parent
+// index -> child index) are hooked and recorded for this split; the FP64
+// tau of a record that lacks it is evaluated from the parent level's state
+void launch_edges_reuse(const EdgeList &parent, long long pcount, const Level &PL, const int32_t *inv,
+                        const Level &C, const EdgeList &child, const TauParams &P, DevCounters *ctr,
+                        int32_t *near_ij, double *near_tau, long long near_cap, cudaStream_t s);
 void launch_kick(const Level &L, const int32_t *label, int nitiles, double G, double eps2, double h,
                  int variant, DevCounters *ctr, cudaStream_t s);
 void launch_energy(const double *x3, const double *v3, const double *m, long long n, double G, double eps2,
@@ -250,7 +274,7 @@ void launch_segment(const Level &L, const int32_t *root, int32_t *members, int32
 void launch_compress_segment(const Level &L, int32_t *root, int32_t *members, int32_t *comp_start,
                              int32_t *comp_size, int32_t *d_ncomp, void *scratch, cudaStream_t s);
 void launch_gather(const Level &P, const Level &C, const int32_t *members, const int32_t *lcomp_start,
-                   const int32_t *lpref, const int32_t *ldst, int nl, int nmem, int nsets_child, cudaStream_t s);
+                   const int32_t *lpref, const int32_t *ldst, int nl, int nmem, int32_t *inv, cudaStream_t s);
 void launch_scatter(const Level &P, const Level &C, cudaStream_t s);
 void launch_pack_state(const double *x3, const double *v3, const double *m, long long n, const Level &L,
                        const int32_t *sys_src_start, cudaStream_t s);
@@ -274,7 +298,8 @@ double probe_fma(int fp64, int nsm, cudaStream_t s);
 // cc_mixed.cu
 void launch_prep_ff(const Level &L, const FFView &F, double G, bool with_v, cudaStream_t s);
 void launch_tau_mixed(const Level &L, const FFView &F, int ntiles, const TauParams &P, int variant,
-                      DevCounters *ctr, int32_t *near_ij, double *near_tau, long long near_cap, cudaStream_t s);
+                      DevCounters *ctr, int32_t *near_ij, double *near_tau, long long near_cap, const EdgeList &rec,
+                      cudaStream_t s);
 int mixed_kick_blocks(int n, int chunk);
 int mixed_kick_chunks(int n, int chunk);
 void launch_prep_kick(const Level &L, const FFView &F, const int32_t *order, const int32_t *root, double G,

@@ -133,7 +133,7 @@ __device__ __forceinline__ bool luf_union(int32_t *p, int a, int b)
 template <int T>
 __global__ void __launch_bounds__(T) k_tau_mixed(Level L, FFView F, TauParams P, MixedTauParams Q,
                                                      DevCounters *ctr, int32_t *near_ij, double *near_tau,
-                                                     long long near_cap)
+                                                     long long near_cap, EdgeList E)
 {
     __shared__ MixedTauSmem<T> sm;
     const int tid = threadIdx.x;
@@ -196,10 +196,11 @@ __global__ void __launch_bounds__(T) k_tau_mixed(Level L, FFView F, TauParams P,
             const float dv1 = (jv0.y - iv0.y) + (jv1.y - iv1.y);
             const float dv2 = (jv0.z - iv0.z) + (jv1.z - iv1.z);
             int dec = tau_decide_fp32(dx0, dx1, dx2, dv0, dv1, dv2, ip0.w + jp0.w, cX, cV, Q);
+            double tau = CUDART_NAN;
             if (dec < 0) {
                 // undecided: the exact FP64 predicate of the FP64 form
                 const int j = j0 + k;
-                const double tau = tau_fp64(__dsub_rn(L.x[i], L.x[j]), __dsub_rn(L.y[i], L.y[j]),
+                tau = tau_fp64(__dsub_rn(L.x[i], L.x[j]), __dsub_rn(L.y[i], L.y[j]),
                                             __dsub_rn(L.z[i], L.z[j]), __dsub_rn(L.vx[i], L.vx[j]),
                                             __dsub_rn(L.vy[i], L.vy[j]), __dsub_rn(L.vz[i], L.vz[j]), L.m[i],
                                             L.m[j], P);
@@ -218,6 +219,7 @@ __global__ void __launch_bounds__(T) k_tau_mixed(Level L, FFView F, TauParams P,
             if (dec) {
                 ++my_edges;
                 if (!luf_union(sm.lp, tid, joff + k)) raise_err(ctr, DERR_UF_RETRY);
+                if (E.rec) record_edge(E, i, j0 + k, tau);
             }
         }
     }
@@ -244,7 +246,8 @@ __global__ void __launch_bounds__(T) k_tau_mixed(Level L, FFView F, TauParams P,
 }
 
 void launch_tau_mixed(const Level &L, const FFView &F, int ntiles, const TauParams &P, int variant,
-                      DevCounters *ctr, int32_t *near_ij, double *near_tau, long long near_cap, cudaStream_t s)
+                      DevCounters *ctr, int32_t *near_ij, double *near_tau, long long near_cap, const EdgeList &E,
+                      cudaStream_t s)
 {
     if (ntiles <= 0) return;
     MixedTauParams Q;
@@ -253,9 +256,9 @@ void launch_tau_mixed(const Level &L, const FFView &F, int ntiles, const TauPara
     Q.eps2 = (float)P.eps2;
     Q.G = (float)P.G;
     if (variant == 0)
-        k_tau_mixed<64><<<ntiles, 64, 0, s>>>(L, F, P, Q, ctr, near_ij, near_tau, near_cap);
+        k_tau_mixed<64><<<ntiles, 64, 0, s>>>(L, F, P, Q, ctr, near_ij, near_tau, near_cap, E);
     else
-        k_tau_mixed<128><<<ntiles, 128, 0, s>>>(L, F, P, Q, ctr, near_ij, near_tau, near_cap);
+        k_tau_mixed<128><<<ntiles, 128, 0, s>>>(L, F, P, Q, ctr, near_ij, near_tau, near_cap, E);
     CC_COUNT_LAUNCH(1);
 }
 

@@ -6,7 +6,7 @@
 //   * the energy diagnostic H (Eq. Hamiltonian).
 // j-tiles are staged in shared memory by TMA bulk copies (cp.async.bulk)
 // completing on an mbarrier; every wait is bounded.
-#include "cc_internal.cuh"
+#include "cc_device.cuh"
 
 namespace cc {
 
@@ -21,19 +21,20 @@ __device__ __forceinline__ int find_set(const int32_t *off, int nsets, int b)
     return lo;
 }
 
-__global__ void k_init_parent(int32_t *parent, int32_t *cnt, int total)
+__global__ void k_init_parent(int32_t *parent, int32_t *cnt, int total, unsigned long long *edge_count)
 {
     int k = blockIdx.x * blockDim.x + threadIdx.x;
     if (k < total) {
         parent[k] = k;
         cnt[k] = 0;
     }
+    if (k == 0 && edge_count) *edge_count = 0ull;
 }
 
-void launch_init_parent(const Level &L, cudaStream_t s)
+void launch_init_parent(const Level &L, unsigned long long *edge_count, cudaStream_t s)
 {
     if (L.total <= 0) return;
-    k_init_parent<<<(L.total + 255) / 256, 256, 0, s>>>(L.parent, L.cnt, L.total);
+    k_init_parent<<<(L.total + 255) / 256, 256, 0, s>>>(L.parent, L.cnt, L.total, edge_count);
     CC_COUNT_LAUNCH(1);
 }
 
@@ -64,7 +65,7 @@ __device__ __forceinline__ void log_pair(const TauParams &P, double tau, int gi,
 
 template <int T>
 __global__ void __launch_bounds__(T) k_tau_hook(Level L, TauParams P, DevCounters *ctr, int32_t *near_ij,
-                                                     double *near_tau, long long near_cap)
+                                                     double *near_tau, long long near_cap, EdgeList E)
 {
     __shared__ TauSmem<T> sm;
     const int tid = threadIdx.x;
@@ -125,6 +126,7 @@ __global__ void __launch_bounds__(T) k_tau_hook(Level L, TauParams P, DevCounter
             if (tau < P.h) {
                 ++my_edges;
                 if (!uf_union(L.parent, i, j)) raise_err(ctr, DERR_UF_RETRY);
+                if (E.rec) record_edge(E, i, j, tau);
             }
         }
     }
@@ -132,6 +134,66 @@ __global__ void __launch_bounds__(T) k_tau_hook(Level L, TauParams P, DevCounter
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) my_edges += __shfl_down_sync(0xffffffffu, my_edges, o);
     if ((tid & 31) == 0 && my_edges) atomicAdd(&ctr->edges, my_edges);
+}
+
+// ------------------------------------------------------------ first-half split
+// The split of a component's first half (pivot h) sees the state its
+// parent split saw at 2h, so tau(i,j) is unchanged: the edges are the
+// parent's records with tau < h, and every pair near h is a parent record
+// too (tau < 2h).  One thread per parent record; records of components the
+// gather did not move to this level (small, Kepler) are skipped (inv[a] is
+// only meaningful where this level's src points back to a).  A record
+// without its FP64 tau (an FP32-certified edge of the mixed form) gets it
+// here, from the parent level's state, which the first half has not moved.
+__global__ void k_edges_reuse(EdgeList PE, long long pcount, Level PL, const int32_t *inv, Level C, EdgeList CE,
+                              TauParams P, DevCounters *ctr, int32_t *near_ij, double *near_tau, long long near_cap)
+{
+    const long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    unsigned long long my_edges = 0, my_evals = 0;
+    if (t < pcount) {
+        const EdgeRec r = PE.rec[t];
+        const int a = inv[r.a], b = inv[r.b];
+        const bool in = a >= 0 && a < C.total && b >= 0 && b < C.total && C.src[a] == r.a && C.src[b] == r.b &&
+                        C.gid[a] >= 0 && C.gid[b] >= 0;
+        if (in) {
+            double tau = r.tau;
+            if (!(tau == tau)) {
+                const int i = r.a, j = r.b;
+                tau = tau_fp64(__dsub_rn(PL.x[i], PL.x[j]), __dsub_rn(PL.y[i], PL.y[j]), __dsub_rn(PL.z[i], PL.z[j]),
+                               __dsub_rn(PL.vx[i], PL.vx[j]), __dsub_rn(PL.vy[i], PL.vy[j]),
+                               __dsub_rn(PL.vz[i], PL.vz[j]), PL.m[i], PL.m[j], P);
+                ++my_evals;
+            }
+            log_pair(P, tau, C.gid[a], C.gid[b], ctr, near_ij, near_tau, near_cap);
+            if (tau < P.h) {
+                ++my_edges;
+                if (!uf_union(C.parent, a, b)) raise_err(ctr, DERR_UF_RETRY);
+                record_edge(CE, min(a, b), max(a, b), tau);
+            }
+        }
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        my_edges += __shfl_down_sync(0xffffffffu, my_edges, o);
+        my_evals += __shfl_down_sync(0xffffffffu, my_evals, o);
+    }
+    if ((threadIdx.x & 31) == 0) {
+        if (my_edges) atomicAdd(&ctr->edges, my_edges);
+        if (my_evals) {
+            atomicAdd(&ctr->tau_fp64, my_evals);
+            atomicAdd(&ctr->tau_evals, my_evals);
+        }
+    }
+}
+
+void launch_edges_reuse(const EdgeList &parent, long long pcount, const Level &PL, const int32_t *inv,
+                        const Level &C, const EdgeList &child, const TauParams &P, DevCounters *ctr,
+                        int32_t *near_ij, double *near_tau, long long near_cap, cudaStream_t s)
+{
+    if (pcount <= 0) return;
+    k_edges_reuse<<<(unsigned)((pcount + 255) / 256), 256, 0, s>>>(parent, pcount, PL, inv, C, child, P, ctr,
+                                                                    near_ij, near_tau, near_cap);
+    CC_COUNT_LAUNCH(1);
 }
 
 // Edge-list variant for the time-step-graph entry point: same predicate,
@@ -206,18 +268,19 @@ __global__ void __launch_bounds__(TAU_T) k_tau_edges(Level L, TauParams P, DevCo
 
 void launch_tau_hook(const Level &L, int ntiles, const TauParams &P, int variant, DevCounters *ctr,
                      int32_t *edges, long long edge_cap, int32_t *near_ij, double *near_tau, long long near_cap,
-                     cudaStream_t s)
+                     cudaStream_t s, const EdgeList *rec)
 {
     if (ntiles <= 0) return;
+    const EdgeList E = rec ? *rec : EdgeList{nullptr, nullptr, 0};
     if (edges) {
         k_tau_edges<<<ntiles, TAU_T, 0, s>>>(L, P, ctr, edges, edge_cap, near_ij, near_tau, near_cap);
         CC_COUNT_LAUNCH(1);
         return;
     }
     if (variant == 0)
-        k_tau_hook<64><<<ntiles, 64, 0, s>>>(L, P, ctr, near_ij, near_tau, near_cap);
+        k_tau_hook<64><<<ntiles, 64, 0, s>>>(L, P, ctr, near_ij, near_tau, near_cap, E);
     else
-        k_tau_hook<128><<<ntiles, 128, 0, s>>>(L, P, ctr, near_ij, near_tau, near_cap);
+        k_tau_hook<128><<<ntiles, 128, 0, s>>>(L, P, ctr, near_ij, near_tau, near_cap, E);
     CC_COUNT_LAUNCH(1);
 }
 

@@ -144,7 +144,7 @@ __device__ __forceinline__ int edge_depth_mixed(const TauPrep32 &t, float etah, 
 // edge depth.  e0 = the edge depth of the initial state if the caller knows
 // it, else -1.
 struct PairCounters {
-    unsigned long long tau = 0, kick = 0, drift = 0, split = 0, comp = 0, fp64 = 0;
+    unsigned long long tau = 0, kick = 0, drift = 0, split = 0, comp = 0, fp64 = 0, evals = 0;
     int maxd = 0;
 };
 
@@ -182,6 +182,7 @@ __device__ unsigned pair_path(double A[7], double B[7], double h0, int depth0, i
                                         __dsub_rn(A[3], B[3]), __dsub_rn(A[4], B[4]), __dsub_rn(A[5], B[5]), A[6],
                                         B[6], P);
             ++pc.fp64;
+            ++pc.evals;
             e = edge_depth_fp64(tau, scale2m(h0, d), max(dmax - d + 1, 1), [&](double tv, double hm) {
                 near_log(tv, hm, nl.tol, nl.ctr, ga, gb, nl.ij, nl.tau, nl.cap);
             });
@@ -255,6 +256,7 @@ __device__ unsigned pair_path_rel(double A[7], double B[7], double h0, int depth
         if (e < 0) {
             const TauPrep32 t = tau_prep_fp32(fl32(r[0]), fl32(r[1]), fl32(r[2]), fl32(u[0]), fl32(u[1]),
                                               fl32(u[2]), muf, 0.f, 0.f, Q);
+            ++pc.evals;
             bool used64;
             e = edge_depth_mixed(
                 t, etah0 * pow2f(d), scale2m(h0, d), max(dmax - d + 1, 1),
@@ -364,7 +366,8 @@ __global__ void __launch_bounds__(K8_WARPS * 32) k_small(Level L, const int32_t 
     unsigned char ph[K8_MAXD], pm[K8_MAXD];
     signed char cf[K8_MAXD];  // level whose fresh split filled S.e for level k's state (-1: none)
     PairCounters pc;
-    unsigned long long c_tau = 0, c_kick = 0, c_drift = 0, c_split = 0, c_comp = 0, c_kep = 0, c_fp64 = 0;
+    unsigned long long c_tau = 0, c_kick = 0, c_drift = 0, c_split = 0, c_comp = 0, c_kep = 0, c_fp64 = 0,
+                       c_eval = 0;
     int maxd = 0;
     const bool mixed = SP.precision == CC_PREC_MIXED;
     TauParams P;
@@ -454,6 +457,7 @@ __global__ void __launch_bounds__(K8_WARPS * 32) k_small(Level L, const int32_t 
                                 if (lane < j) ++c_fp64;
                             }
                             S.e[j][lane] = (unsigned char)e;
+                            if (lane < j) ++c_eval;
                         }
                     }
                     cf[k] = (signed char)k;
@@ -631,10 +635,10 @@ __global__ void __launch_bounds__(K8_WARPS * 32) k_small(Level L, const int32_t 
     }
     // per-lane counters (lockstep levels + pair paths) -> one atomic per warp
     if (pc.maxd > maxd) maxd = pc.maxd;
-    unsigned long long v[7] = {c_tau + pc.tau, c_kick + pc.kick, c_drift + pc.drift, c_split + pc.split,
-                               c_comp + pc.comp, c_kep, c_fp64 + pc.fp64};
+    unsigned long long v[8] = {c_tau + pc.tau, c_kick + pc.kick, c_drift + pc.drift, c_split + pc.split,
+                               c_comp + pc.comp, c_kep, c_fp64 + pc.fp64, c_eval + pc.evals};
 #pragma unroll
-    for (int i = 0; i < 7; ++i)
+    for (int i = 0; i < 8; ++i)
         for (int o = 16; o > 0; o >>= 1) v[i] += __shfl_down_sync(FULL, v[i], o);
     for (int o = 16; o > 0; o >>= 1) maxd = max(maxd, __shfl_down_sync(FULL, maxd, o));
     if (lane == 0) {
@@ -645,6 +649,7 @@ __global__ void __launch_bounds__(K8_WARPS * 32) k_small(Level L, const int32_t 
         if (v[4]) atomicAdd(&ctr->small_components, v[4]);
         if (v[5]) atomicAdd(&ctr->small_kepler, v[5]);
         if (v[6]) atomicAdd(&ctr->tau_fp64, v[6]);
+        if (v[7]) atomicAdd(&ctr->tau_evals, v[7]);
         atomicMax(&ctr->max_depth_seen, maxd);
     }
 }

@@ -197,3 +197,26 @@ def test_launch_shapes_do_not_change_fp64_results(cclib, plummer_ic):
     s = O.State(m, x, v)
     O.evolve(s, O.params(dt=1 / 128), 6)
     assert _rel_ok(out[1][0], s.x3, 1e-10) and _rel_ok(out[1][1], s.v3, 1e-10)
+
+
+@pytest.mark.parametrize("s_small", [0, 32])
+def test_first_half_splits_from_parent_records(cclib, plummer_ic, s_small):
+    """A first-half split takes its edges from the parent split's tau values
+    (the state is the one the parent saw).  With the small-component kernel
+    off every component recurses level by level, so most splits below the
+    top are first halves: the result must still be the oracle's, with the
+    same split and pair counts, and fewer pairs evaluated than decided."""
+    m, x, v = plummer_ic(2000, seed=9)
+    c = cclib.Context(m, x, v, dt=1 / 32, s_small=s_small)
+    c.evolve(1 / 32)
+    _, _, gx, gv = c.get_state()
+    s = O.State(m, x, v)
+    st = O.evolve(s, O.params(dt=1 / 32), 1)
+    assert _rel_ok(gx, s.x3) and _rel_ok(gv, s.v3)
+    g = c.stats()
+    for k in ("tau_pairs", "kick_pairs", "drifts", "splits", "components"):
+        assert g[k] == getattr(st, k), k
+    assert g["max_depth_seen"] == st.max_depth_seen
+    assert st.max_depth_seen >= 3
+    assert 0 < g["tau_evaluated"] < g["tau_pairs"]
+    c.close()
