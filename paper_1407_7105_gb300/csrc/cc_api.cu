@@ -560,8 +560,8 @@ static int split_level(cc_ctx *c, LevelAlloc &a, double h, int &ncomp, const Lev
     launch_init_parent(a.L, a.E.count, s);
     const bool mixed = c->p.precision == CC_PREC_MIXED;
     if (parent) {
-        launch_edges_reuse(parent->E, parent->ecount, parent->L, parent->inv, a.L, a.E, P, c->d_ctr, c->d_near_ij,
-                           c->d_near_tau, c->near_cap, s);
+        launch_edges_reuse(parent->E, parent->ecount, parent->L, parent->F, mixed, parent->inv, a.L, a.E, P, c->d_ctr,
+                           c->d_near_ij, c->d_near_tau, c->near_cap, s);
     } else {
         const int tk = mixed ? TK_TAUMIX : TK_TAU64;
         int bin;

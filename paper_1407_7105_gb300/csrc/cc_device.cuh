@@ -198,13 +198,15 @@ __device__ __forceinline__ double f2d(float f)
 
 // one edge record at an atomically reserved slot (dropped past cap; the
 // count still tells the host the list is incomplete)
-__device__ __forceinline__ void record_edge(const EdgeList &E, int a, int b, double tau)
+__device__ __forceinline__ void record_edge(const EdgeList &E, int a, int b, int e, double tau)
 {
     const unsigned long long q = atomicAdd(E.count, 1ull);
     if ((long long)q < E.cap) {
         EdgeRec r;
         r.a = a;
         r.b = b;
+        r.e = e;
+        r.pad = 0;
         r.tau = tau;
         E.rec[q] = r;
     }

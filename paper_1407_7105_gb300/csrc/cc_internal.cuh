@@ -46,13 +46,15 @@ struct FFView {
 };
 
 // Edge record of a split at pivot h: packed indices a < b of the level
-// (tau(a,b) < h) and tau in FP64 when the split evaluated it (NaN when the
-// certified FP32 decision settled the edge).  The first-half split of a
-// component at h/2 sees the same state, so its edges are the records with
-// tau < h/2, and its near-threshold pairs (tau within near_tol of h/2) are
-// records too (tau < h).
+// (tau(a,b) < h); tau in FP64 when it was evaluated (NaN when a certified
+// FP32 decision settled the edge); e = the edge depth when known (the pair
+// is an edge at h 2^-m exactly for m < e, saturating at EDGE_E_INF), -1
+// when not.  The first-half split of a component at h/2 sees the same
+// state, so its edges are the records that are edges at h/2, and its
+// near-threshold pairs (tau within near_tol of h/2) are records too.
+constexpr int EDGE_E_INF = 1 << 20;
 struct EdgeRec {
-    int32_t a, b;
+    int32_t a, b, e, pad;
     double tau;
 };
 struct EdgeList {
@@ -248,13 +250,14 @@ constexpr int MK_TILE = 128;
 void launch_tau_hook(const Level &L, int ntiles, const TauParams &P, int variant, DevCounters *ctr,
                      int32_t *edges, long long edge_cap, int32_t *near_ij, double *near_tau, long long near_cap,
                      cudaStream_t s, const EdgeList *rec = nullptr);
-// first-half split from the parent split's edge records: the records with
-// tau < P.h whose endpoints the gather moved to this level (inv = parent
-// index -> child index) are hooked and recorded for this split; the FP64
-// tau of a record that lacks it is evaluated from the parent level's state
-void launch_edges_reuse(const EdgeList &parent, long long pcount, const Level &PL, const int32_t *inv,
-                        const Level &C, const EdgeList &child, const TauParams &P, DevCounters *ctr,
-                        int32_t *near_ij, double *near_tau, long long near_cap, cudaStream_t s);
+// first-half split from the parent split's edge records: the records that
+// are edges at P.h and whose endpoints the gather moved to this level (inv =
+// parent index -> child index) are hooked and recorded for this split
+// (PF = the parent's float-float view, valid for records of a fresh mixed
+// split: their FP32 decisions at h/2, h/4, ... are taken from it)
+void launch_edges_reuse(const EdgeList &parent, long long pcount, const Level &PL, const FFView &PF, bool mixed,
+                        const int32_t *inv, const Level &C, const EdgeList &child, const TauParams &P,
+                        DevCounters *ctr, int32_t *near_ij, double *near_tau, long long near_cap, cudaStream_t s);
 void launch_kick(const Level &L, const int32_t *label, int nitiles, double G, double eps2, double h,
                  int variant, DevCounters *ctr, cudaStream_t s);
 void launch_energy(const double *x3, const double *v3, const double *m, long long n, double G, double eps2,

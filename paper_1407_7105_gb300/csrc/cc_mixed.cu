@@ -200,10 +200,9 @@ __global__ void __launch_bounds__(T) k_tau_mixed(Level L, FFView F, TauParams P,
             if (dec < 0) {
                 // undecided: the exact FP64 predicate of the FP64 form
                 const int j = j0 + k;
-                tau = tau_fp64(__dsub_rn(L.x[i], L.x[j]), __dsub_rn(L.y[i], L.y[j]),
-                                            __dsub_rn(L.z[i], L.z[j]), __dsub_rn(L.vx[i], L.vx[j]),
-                                            __dsub_rn(L.vy[i], L.vy[j]), __dsub_rn(L.vz[i], L.vz[j]), L.m[i],
-                                            L.m[j], P);
+                tau = tau_fp64(__dsub_rn(L.x[i], L.x[j]), __dsub_rn(L.y[i], L.y[j]), __dsub_rn(L.z[i], L.z[j]),
+                               __dsub_rn(L.vx[i], L.vx[j]), __dsub_rn(L.vy[i], L.vy[j]), __dsub_rn(L.vz[i], L.vz[j]),
+                               L.m[i], L.m[j], P);
                 ++my_fp64;
                 if (fabs(tau - P.h) < P.near_tol * P.h) {
                     unsigned long long q = atomicAdd(&ctr->near_pairs, 1ull);
@@ -219,7 +218,10 @@ __global__ void __launch_bounds__(T) k_tau_mixed(Level L, FFView F, TauParams P,
             if (dec) {
                 ++my_edges;
                 if (!luf_union(sm.lp, tid, joff + k)) raise_err(ctr, DERR_UF_RETRY);
-                if (E.rec) record_edge(E, i, j0 + k, tau);
+                // every edge is recorded (the decision at h/2 is left to the
+                // first half's pass: taking it here costs the pair loop
+                // registers); tau = the FP64 value or NaN
+                if (E.rec) record_edge(E, i, j0 + k, -1, tau);
             }
         }
     }
@@ -394,26 +396,46 @@ __global__ void __launch_bounds__(MK_T) k_kick_mixed(Level L, FFView F, const in
     }
 }
 
-// sum the chunk partials of multi-chunk sets in chunk order (FP64), v += h a
+// Sum the chunk partials of multi-chunk sets (FP64), v += h a.  KR_LANES
+// lanes per body: lane s sums chunks s, s + KR_LANES, ... in order, then a
+// fixed butterfly combines the lanes, so the rounding order is fixed (run to
+// run identical) and the dependent FP64 chain is nchunk/KR_LANES + 3 adds
+// long instead of nchunk (an FP64 add's latency dominates this kernel).
+constexpr int KR_LANES = 8;
+
 __global__ void k_kick_reduce(Level L, FFView F, const int32_t *order, int chunk, double h, const double *partial)
 {
-    const int t = blockIdx.x * blockDim.x + threadIdx.x;
-    if (t >= L.total) return;
-    const int k = order[t];
-    if (L.sidx[k] < 0) return;
-    const int n = L.set_n[L.sidx[k]];
-    const int nchunk = ((n + MK_T - 1) / MK_T + chunk - 1) / chunk;
-    if (nchunk == 1) return;
+    const long long g = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    const int t = (int)(g / KR_LANES), sub = (int)(g % KR_LANES);
+    int k = -1, nchunk = 1;
+    if (t < L.total) {
+        k = order[t];
+        if (L.sidx[k] >= 0) {
+            const int n = L.set_n[L.sidx[k]];
+            nchunk = ((n + MK_T - 1) / MK_T + chunk - 1) / chunk;
+        }
+    }
+    const bool on = k >= 0 && L.sidx[k] >= 0 && nchunk > 1;
     const size_t cap = (size_t)F.cap;
     double ax = 0.0, ay = 0.0, az = 0.0;
-    for (int c = 0; c < nchunk; ++c) {
-        ax += partial[((size_t)c * 3 + 0) * cap + t];
-        ay += partial[((size_t)c * 3 + 1) * cap + t];
-        az += partial[((size_t)c * 3 + 2) * cap + t];
+    if (on) {
+        for (int c = sub; c < nchunk; c += KR_LANES) {
+            ax += partial[((size_t)c * 3 + 0) * cap + t];
+            ay += partial[((size_t)c * 3 + 1) * cap + t];
+            az += partial[((size_t)c * 3 + 2) * cap + t];
+        }
     }
-    L.vx[k] += h * ax;
-    L.vy[k] += h * ay;
-    L.vz[k] += h * az;
+#pragma unroll
+    for (int o = KR_LANES / 2; o > 0; o >>= 1) {
+        ax += __shfl_xor_sync(0xffffffffu, ax, o);
+        ay += __shfl_xor_sync(0xffffffffu, ay, o);
+        az += __shfl_xor_sync(0xffffffffu, az, o);
+    }
+    if (on && sub == 0) {
+        L.vx[k] += h * ax;
+        L.vy[k] += h * ay;
+        L.vz[k] += h * az;
+    }
 }
 
 int mixed_kick_blocks(int n, int chunk)
@@ -436,7 +458,8 @@ void launch_kick_mixed(const Level &L, const FFView &F, const int32_t *order, co
     k_kick_mixed<<<nblocks, MK_T, 0, s>>>(L, F, order, koff, chunk, (float)eps2, h, ctr, partial);
     CC_COUNT_LAUNCH(1);
     if (multi_chunk) {
-        k_kick_reduce<<<(L.total + 255) / 256, 256, 0, s>>>(L, F, order, chunk, h, partial);
+        const long long threads = (long long)L.total * KR_LANES;
+        k_kick_reduce<<<(unsigned)((threads + 255) / 256), 256, 0, s>>>(L, F, order, chunk, h, partial);
         CC_COUNT_LAUNCH(1);
     }
 }

@@ -126,7 +126,10 @@ __global__ void __launch_bounds__(T) k_tau_hook(Level L, TauParams P, DevCounter
             if (tau < P.h) {
                 ++my_edges;
                 if (!uf_union(L.parent, i, j)) raise_err(ctr, DERR_UF_RETRY);
-                if (E.rec) record_edge(E, i, j, tau);
+                // a record serves the first half at h/2: kept when the pair
+                // is an edge there or near h/2
+                if (E.rec && (tau < 0.5 * P.h || fabs(tau - 0.5 * P.h) < P.near_tol * 0.5 * P.h))
+                    record_edge(E, i, j, -1, tau);
             }
         }
     }
@@ -139,14 +142,19 @@ __global__ void __launch_bounds__(T) k_tau_hook(Level L, TauParams P, DevCounter
 // ------------------------------------------------------------ first-half split
 // The split of a component's first half (pivot h) sees the state its
 // parent split saw at 2h, so tau(i,j) is unchanged: the edges are the
-// parent's records with tau < h, and every pair near h is a parent record
-// too (tau < 2h).  One thread per parent record; records of components the
-// gather did not move to this level (small, Kepler) are skipped (inv[a] is
-// only meaningful where this level's src points back to a).  A record
-// without its FP64 tau (an FP32-certified edge of the mixed form) gets it
-// here, from the parent level's state, which the first half has not moved.
-__global__ void k_edges_reuse(EdgeList PE, long long pcount, Level PL, const int32_t *inv, Level C, EdgeList CE,
-                              TauParams P, DevCounters *ctr, int32_t *near_ij, double *near_tau, long long near_cap)
+// parent's records that are edges at h, and every pair near h is a parent
+// record too (tau < 2h).  One thread per parent record; records of
+// components the gather did not move to this level (small, Kepler) are
+// skipped (inv[a] is only meaningful where this level's src points back to
+// a).  A record's edge depth comes from its e, else its FP64 tau, else (an
+// FP32-certified edge of a fresh mixed split) from certified FP32
+// decisions at h, h/2, ... on the parent's float-float copy, which the
+// first half leaves untouched, with the FP64 tau from the parent level's
+// state at the first undecided threshold.  The child's record carries the
+// depth on, so deeper first halves never need the float-float copy.
+__global__ void k_edges_reuse(EdgeList PE, long long pcount, Level PL, FFView PF, MixedTauParams Q, int mixed,
+                              const int32_t *inv, Level C, EdgeList CE, TauParams P, DevCounters *ctr,
+                              int32_t *near_ij, double *near_tau, long long near_cap)
 {
     const long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
     unsigned long long my_edges = 0, my_evals = 0;
@@ -156,20 +164,53 @@ __global__ void k_edges_reuse(EdgeList PE, long long pcount, Level PL, const int
         const bool in = a >= 0 && a < C.total && b >= 0 && b < C.total && C.src[a] == r.a && C.src[b] == r.b &&
                         C.gid[a] >= 0 && C.gid[b] >= 0;
         if (in) {
+            const double hp = 2.0 * P.h;  // the parent's pivot
             double tau = r.tau;
-            if (!(tau == tau)) {
-                const int i = r.a, j = r.b;
-                tau = tau_fp64(__dsub_rn(PL.x[i], PL.x[j]), __dsub_rn(PL.y[i], PL.y[j]), __dsub_rn(PL.z[i], PL.z[j]),
-                               __dsub_rn(PL.vx[i], PL.vx[j]), __dsub_rn(PL.vy[i], PL.vy[j]),
-                               __dsub_rn(PL.vz[i], PL.vz[j]), PL.m[i], PL.m[j], P);
-                ++my_evals;
+            int e = r.e;
+            if (e < 0 && tau == tau) e = first_level_at_or_below(tau, hp, EDGE_E_INF);
+            if (e < 0) {
+                int m = 1, dec = 1;
+                if (mixed) {
+                    // the tau kernel's decision at hp, restated at hp 2^-m
+                    const float4 ip0 = PF.pq[2 * r.a], ip1 = PF.pq[2 * r.a + 1];
+                    const float4 iv0 = PF.vq[2 * r.a], iv1 = PF.vq[2 * r.a + 1];
+                    const float4 jp0 = PF.pq[2 * r.b], jp1 = PF.pq[2 * r.b + 1];
+                    const float4 jv0 = PF.vq[2 * r.b], jv1 = PF.vq[2 * r.b + 1];
+                    const float cX = 11.f * U32 * U32 * PF.maxes[0];
+                    const float cV = 11.f * U32 * U32 * PF.maxes[1];
+                    const TauPrep32 tp = tau_prep_fp32(
+                        (jp0.x - ip0.x) + (jp1.x - ip1.x), (jp0.y - ip0.y) + (jp1.y - ip1.y),
+                        (jp0.z - ip0.z) + (jp1.z - ip1.z), (jv0.x - iv0.x) + (jv1.x - iv1.x),
+                        (jv0.y - iv0.y) + (jv1.y - iv1.y), (jv0.z - iv0.z) + (jv1.z - iv1.z), ip0.w + jp0.w, cX, cV,
+                        Q);
+                    while (m < 100) {
+                        dec = tau_decide_at(tp, Q.etah * pow2f(m));
+                        if (dec != 1) break;
+                        ++m;
+                    }
+                }
+                if (mixed && dec == 0) {
+                    e = m;
+                } else {
+                    const int i = r.a, j = r.b;
+                    tau = tau_fp64(__dsub_rn(PL.x[i], PL.x[j]), __dsub_rn(PL.y[i], PL.y[j]),
+                                   __dsub_rn(PL.z[i], PL.z[j]), __dsub_rn(PL.vx[i], PL.vx[j]),
+                                   __dsub_rn(PL.vy[i], PL.vy[j]), __dsub_rn(PL.vz[i], PL.vz[j]), PL.m[i], PL.m[j], P);
+                    ++my_evals;
+                    const int e64 = first_level_at_or_below(tau, hp, EDGE_E_INF);
+                    e = e64 > m ? e64 : m;
+                }
             }
-            log_pair(P, tau, C.gid[a], C.gid[b], ctr, near_ij, near_tau, near_cap);
-            if (tau < P.h) {
+            if (tau == tau) log_pair(P, tau, C.gid[a], C.gid[b], ctr, near_ij, near_tau, near_cap);
+            if (e >= 2) {
                 ++my_edges;
                 if (!uf_union(C.parent, a, b)) raise_err(ctr, DERR_UF_RETRY);
-                record_edge(CE, min(a, b), max(a, b), tau);
             }
+            // this split's record serves the next first half (pivot h/2):
+            // an edge there (e >= 3), or a known tau that may be near h/2
+            const double hc = 0.5 * P.h;
+            if (e >= 3 || (e == 2 && tau == tau && fabs(tau - hc) < P.near_tol * hc))
+                record_edge(CE, min(a, b), max(a, b), e >= EDGE_E_INF ? EDGE_E_INF : e - 1, tau);
         }
     }
 #pragma unroll
@@ -186,13 +227,19 @@ __global__ void k_edges_reuse(EdgeList PE, long long pcount, Level PL, const int
     }
 }
 
-void launch_edges_reuse(const EdgeList &parent, long long pcount, const Level &PL, const int32_t *inv,
-                        const Level &C, const EdgeList &child, const TauParams &P, DevCounters *ctr,
-                        int32_t *near_ij, double *near_tau, long long near_cap, cudaStream_t s)
+void launch_edges_reuse(const EdgeList &parent, long long pcount, const Level &PL, const FFView &PF, bool mixed,
+                        const int32_t *inv, const Level &C, const EdgeList &child, const TauParams &P,
+                        DevCounters *ctr, int32_t *near_ij, double *near_tau, long long near_cap, cudaStream_t s)
 {
     if (pcount <= 0) return;
-    k_edges_reuse<<<(unsigned)((pcount + 255) / 256), 256, 0, s>>>(parent, pcount, PL, inv, C, child, P, ctr,
-                                                                    near_ij, near_tau, near_cap);
+    const double hp = 2.0 * P.h;
+    MixedTauParams Q;
+    Q.eta = (float)P.eta_in;
+    Q.etah = (float)(P.eta_outside ? P.eta_in * P.eta / hp : P.eta_in / hp);
+    Q.eps2 = (float)P.eps2;
+    Q.G = (float)P.G;
+    k_edges_reuse<<<(unsigned)((pcount + 255) / 256), 256, 0, s>>>(parent, pcount, PL, PF, Q, mixed ? 1 : 0, inv, C,
+                                                                    child, P, ctr, near_ij, near_tau, near_cap);
     CC_COUNT_LAUNCH(1);
 }
 

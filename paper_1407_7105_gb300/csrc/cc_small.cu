@@ -230,18 +230,20 @@ __device__ unsigned pair_path_rel(double A[7], double B[7], double h0, int depth
                                   const TauParams &P, const MixedTauParams &Q, PairCounters &pc, const NearLog &nl,
                                   int ga, int gb)
 {
-    const double ma = A[6], mb = B[6], M = ma + mb;
+    // mass fractions from one reciprocal (an FP64 division is a chain of
+    // ~10 dependent FP64 operations on this part)
+    const double ma = A[6], mb = B[6], M = ma + mb, iM = 1.0 / M, wa = ma * iM, wb = mb * iM;
     double R[3], V[3], r[3], u[3];
     for (int k = 0; k < 3; ++k) {
-        R[k] = (ma * A[k] + mb * B[k]) / M;
-        V[k] = (ma * A[3 + k] + mb * B[3 + k]) / M;
+        R[k] = fma(wa, A[k], wb * B[k]);
+        V[k] = fma(wa, A[3 + k], wb * B[3 + k]);
         r[k] = A[k] - B[k];
         u[k] = A[3 + k] - B[3 + k];
     }
     const float muf = Q.G * (fl32(ma) + fl32(mb));
     const double GM = SP.G * M;
     const float e2 = fl32(SP.eps2);
-    const float etah0 = (float)(P.eta_outside ? P.eta_in * P.eta / h0 : P.eta_in / h0);
+    const float etah0 = Q.etah;  // eta/h0 in float (the caller's, exact power-of-two scaling of its own)
     const int dmax = min(SP.max_depth - depth0, 61);
     const double c0 = -GM * h0;
     // depths whose pivot h0 2^-d is below h_fp64 take FP64 forces
@@ -303,10 +305,10 @@ __device__ unsigned pair_path_rel(double A[7], double B[7], double h0, int depth
         if (!pair_next(pend, d)) {
             for (int k = 0; k < 3; ++k) {
                 const double Rk = fma(h0, V[k], R[k]);
-                A[k] = Rk + (mb / M) * r[k];
-                B[k] = Rk - (ma / M) * r[k];
-                A[3 + k] = V[k] + (mb / M) * u[k];
-                B[3 + k] = V[k] - (ma / M) * u[k];
+                A[k] = fma(wb, r[k], Rk);
+                B[k] = fma(-wa, r[k], Rk);
+                A[3 + k] = fma(wb, u[k], V[k]);
+                B[3 + k] = fma(-wa, u[k], V[k]);
             }
             return 0u;
         }
@@ -321,7 +323,8 @@ __device__ unsigned pair_path_rel(double A[7], double B[7], double h0, int depth
 // value hit its scan cap ecap.  Returns a device error code (0 = ok)
 // uniform over the warp.
 __device__ __forceinline__ unsigned k8_pair_handoff(K8Warp &S, int lane, double st[7], uint32_t cm, bool is_sub,
-                                                    double hsub, int dsub, int eoff, int ecap, const SmallParams &SP,
+                                                    double hsub, float etah_sub, int dsub, int eoff, int ecap,
+                                                    const SmallParams &SP,
                                                     const TauParams &P, const MixedTauParams &Q, bool mixed,
                                                     PairCounters &pc, const NearLog &nl)
 {
@@ -337,9 +340,11 @@ __device__ __forceinline__ unsigned k8_pair_handoff(K8Warp &S, int lane, double 
         const int ga = S.gid[lane], gb = S.gid[j];
         const int ec = S.e[j][lane];
         const int e0 = (eoff >= 0 && ec < ecap) ? ec - eoff : -1;
-        if (mixed)
-            err = pair_path_rel(st, B, hsub, dsub, e0, SP, P, Q, pc, nl, ga, gb);
-        else
+        if (mixed) {
+            MixedTauParams Qs = Q;
+            Qs.etah = etah_sub;  // eta/hsub
+            err = pair_path_rel(st, B, hsub, dsub, e0, SP, P, Qs, pc, nl, ga, gb);
+        } else
             err = pair_path(st, B, hsub, dsub, e0, SP, P, pc, nl, ga, gb);
 #pragma unroll
         for (int c = 0; c < 6; ++c) S.d[c][j] = B[c];
@@ -376,6 +381,8 @@ __global__ void __launch_bounds__(K8_WARPS * 32) k_small(Level L, const int32_t 
     MixedTauParams Q;
     Q.eta = (float)SP.eta_in; Q.eps2 = (float)SP.eps2; Q.G = (float)SP.G;
     const NearLog nl = {ctr, near_ij, near_tau, near_cap, SP.near_tol};
+    // eta/h0 in float, once: eta/(h0 2^-k) is this times 2^k exactly
+    const float etah_c = (float)(SP.eta_outside ? SP.eta_in * SP.eta / SP.h0 : SP.eta_in / SP.h0);
     for (;;) {
         int q = 0;
         if (lane == 0) q = atomicAdd(queue, 1);
@@ -402,7 +409,8 @@ __global__ void __launch_bounds__(K8_WARPS * 32) k_small(Level L, const int32_t 
         if (SP.depth0 > maxd) maxd = SP.depth0;
         if (n == 2) {
             // a two-body component: its whole recursion on the pair path
-            const unsigned e = k8_pair_handoff(S, lane, st, 3u, act, SP.h0, SP.depth0, -1, 0, SP, P, Q, mixed, pc, nl);
+            const unsigned e = k8_pair_handoff(S, lane, st, 3u, act, SP.h0, etah_c, SP.depth0, -1, 0, SP, P, Q, mixed, pc,
+                                               nl);
             if (e) {
                 raise_err(ctr, e);
                 bad = true;
@@ -410,7 +418,7 @@ __global__ void __launch_bounds__(K8_WARPS * 32) k_small(Level L, const int32_t 
             k = -1;
         }
         while (k >= 0 && !bad) {
-            const double h = ldexp(SP.h0, -k);
+            const double h = scale2m(SP.h0, k);
             const uint32_t mine = mk[k];
             if (ph[k] == 0) {
                 // ---------------- split at h: tau(i,j) < h inside the lane's set.
@@ -420,42 +428,60 @@ __global__ void __launch_bounds__(K8_WARPS * 32) k_small(Level L, const int32_t 
                 if (cf[k] < 0) {
                     k8_publish(S, lane, st, mixed);
                     P.h = h;
-                    const float etah = (float)(SP.eta_outside ? SP.eta_in * SP.eta / h : SP.eta_in / h);
+                    const float etah = etah_c * pow2f(k);
                     const float c11 = 11.f * U32 * U32;
                     const int levels = K8_MAXD - k;
-                    if (mine) {
+                    // FP64 tau of pair (lane, j), in the pair's fixed order
+                    // (symmetric bit for bit)
+                    auto tau64_of = [&](int j) {
+                        const int lo = lane < j ? lane : j, hi = lane < j ? j : lane;
+                        return tau_fp64(__dsub_rn(S.d[0][lo], S.d[0][hi]), __dsub_rn(S.d[1][lo], S.d[1][hi]),
+                                        __dsub_rn(S.d[2][lo], S.d[2][hi]), __dsub_rn(S.d[3][lo], S.d[3][hi]),
+                                        __dsub_rn(S.d[4][lo], S.d[4][hi]), __dsub_rn(S.d[5][lo], S.d[5][hi]),
+                                        S.d[6][lo], S.d[6][hi], P);
+                    };
+                    auto log_of = [&](int j, double tv, double hm) {
+                        if (lane < j) near_log(tv, hm, nl.tol, nl.ctr, S.gid[lane], S.gid[j], nl.ij, nl.tau, nl.cap);
+                    };
+                    if (mine && mixed) {
+                        auto prep = [&](int j) {
+                            return tau_prep_fp32((S.f[0][j] - S.f[0][lane]) + (S.f[6][j] - S.f[6][lane]),
+                                                 (S.f[1][j] - S.f[1][lane]) + (S.f[7][j] - S.f[7][lane]),
+                                                 (S.f[2][j] - S.f[2][lane]) + (S.f[8][j] - S.f[8][lane]),
+                                                 (S.f[3][j] - S.f[3][lane]) + (S.f[9][j] - S.f[9][lane]),
+                                                 (S.f[4][j] - S.f[4][lane]) + (S.f[10][j] - S.f[10][lane]),
+                                                 (S.f[5][j] - S.f[5][lane]) + (S.f[11][j] - S.f[11][lane]),
+                                                 Q.G * (S.f[12][lane] + S.f[12][j]), c11 * fmaxf(S.xm[lane], S.xm[j]),
+                                                 c11 * fmaxf(S.vm[lane], S.vm[j]), Q);
+                        };
+                        auto finish = [&](int j, const TauPrep32 &t) {
+                            if (j == lane || !((mine >> j) & 1u)) return;
+                            int e = 0;
+                            if (tau_decide_at(t, etah) != 0) {
+                                bool used64;
+                                e = edge_depth_mixed(
+                                    t, etah, h, levels, [&]() { return tau64_of(j); },
+                                    [&](double tv, double hm) { log_of(j, tv, hm); }, used64);
+                                if (used64 && lane < j) ++c_fp64;
+                            }
+                            S.e[j][lane] = (unsigned char)e;
+                            if (lane < j) ++c_eval;
+                        };
+                        // two preps in flight: a lone warp's latency, not its
+                        // issue rate, bounds this loop (excluded j are computed
+                        // and dropped)
+                        for (int j = 0; j < n; j += 2) {
+                            const int j1 = j + 1 < n ? j + 1 : j;
+                            const TauPrep32 t0 = prep(j), t1 = prep(j1);
+                            finish(j, t0);
+                            if (j + 1 < n) finish(j + 1, t1);
+                        }
+                    } else if (mine) {
                         for (int j = 0; j < n; ++j) {
                             if (j == lane || !((mine >> j) & 1u)) continue;
-                            const int lo = lane < j ? lane : j, hi = lane < j ? j : lane;
-                            // FP64 tau, in the pair's fixed order (symmetric bit for bit)
-                            auto tau64 = [&]() {
-                                return tau_fp64(__dsub_rn(S.d[0][lo], S.d[0][hi]), __dsub_rn(S.d[1][lo], S.d[1][hi]),
-                                                __dsub_rn(S.d[2][lo], S.d[2][hi]), __dsub_rn(S.d[3][lo], S.d[3][hi]),
-                                                __dsub_rn(S.d[4][lo], S.d[4][hi]), __dsub_rn(S.d[5][lo], S.d[5][hi]),
-                                                S.d[6][lo], S.d[6][hi], P);
-                            };
-                            auto log = [&](double tv, double hm) {
-                                if (lane < j)
-                                    near_log(tv, hm, nl.tol, nl.ctr, S.gid[lane], S.gid[j], nl.ij, nl.tau, nl.cap);
-                            };
-                            int e;
-                            if (mixed) {
-                                const TauPrep32 t = tau_prep_fp32(
-                                    (S.f[0][j] - S.f[0][lane]) + (S.f[6][j] - S.f[6][lane]),
-                                    (S.f[1][j] - S.f[1][lane]) + (S.f[7][j] - S.f[7][lane]),
-                                    (S.f[2][j] - S.f[2][lane]) + (S.f[8][j] - S.f[8][lane]),
-                                    (S.f[3][j] - S.f[3][lane]) + (S.f[9][j] - S.f[9][lane]),
-                                    (S.f[4][j] - S.f[4][lane]) + (S.f[10][j] - S.f[10][lane]),
-                                    (S.f[5][j] - S.f[5][lane]) + (S.f[11][j] - S.f[11][lane]),
-                                    Q.G * (S.f[12][lane] + S.f[12][j]), c11 * fmaxf(S.xm[lane], S.xm[j]),
-                                    c11 * fmaxf(S.vm[lane], S.vm[j]), Q);
-                                bool used64;
-                                e = edge_depth_mixed(t, etah, h, levels, tau64, log, used64);
-                                if (used64 && lane < j) ++c_fp64;
-                            } else {
-                                e = edge_depth_fp64(tau64(), h, levels, log);
-                                if (lane < j) ++c_fp64;
-                            }
+                            const int e = edge_depth_fp64(tau64_of(j), h, levels,
+                                                          [&](double tv, double hm) { log_of(j, tv, hm); });
+                            if (lane < j) ++c_fp64;
                             S.e[j][lane] = (unsigned char)e;
                             if (lane < j) ++c_eval;
                         }
@@ -497,8 +523,9 @@ __global__ void __launch_bounds__(K8_WARPS * 32) k_small(Level L, const int32_t 
                 // pair path (first half now, second half after the DKD)
                 pm[k] = __all_sync(FULL, !sub || csz == 2) ? 1 : 0;
                 if (pm[k] && __any_sync(FULL, sub)) {
-                    const unsigned e = k8_pair_handoff(S, lane, st, cm, sub, 0.5 * h, SP.depth0 + k + 1,
-                                                       k + 1 - cf[k], K8_MAXD - cf[k], SP, P, Q, mixed, pc, nl);
+                    const unsigned e = k8_pair_handoff(S, lane, st, cm, sub, 0.5 * h, etah_c * pow2f(k + 1),
+                                                       SP.depth0 + k + 1, k + 1 - cf[k], K8_MAXD - cf[k], SP, P, Q,
+                                                       mixed, pc, nl);
                     if (e) {
                         raise_err(ctr, e);
                         bad = true;
@@ -566,25 +593,33 @@ __global__ void __launch_bounds__(K8_WARPS * 32) k_small(Level L, const int32_t 
                                 // FP32 pair forces from float-float differences
                                 const float xh = S.f[0][lane], yh = S.f[1][lane], zh = S.f[2][lane];
                                 const float xl = S.f[6][lane], yl = S.f[7][lane], zl = S.f[8][lane];
-                                float sx = 0.f, sy = 0.f, sz = 0.f, cx = 0.f, cy = 0.f, cz = 0.f;
+                                // two compensated accumulators (even and odd j): two
+                                // independent dependency chains for one warp that runs
+                                // alone on its scheduler; excluded j contribute an exact 0
+                                float sx0 = 0.f, sy0 = 0.f, sz0 = 0.f, cx0 = 0.f, cy0 = 0.f, cz0 = 0.f;
+                                float sx1 = 0.f, sy1 = 0.f, sz1 = 0.f, cx1 = 0.f, cy1 = 0.f, cz1 = 0.f;
                                 const float e2 = (float)SP.eps2;
-                                for (int j = 0; j < n; ++j) {
-                                    if (!((others >> j) & 1u)) continue;
+                                auto term = [&](int j, float &sx, float &sy, float &sz, float &cx, float &cy,
+                                                float &cz) {
                                     const float dx = (S.f[0][j] - xh) + (S.f[6][j] - xl);
                                     const float dy = (S.f[1][j] - yh) + (S.f[7][j] - yl);
                                     const float dz = (S.f[2][j] - zh) + (S.f[8][j] - zl);
                                     const float r2 = fmaf(dz, dz, fmaf(dy, dy, fmaf(dx, dx, e2)));
                                     float ri = rsqrtf(r2);
                                     ri = ri * fmaf(-0.5f * r2, ri * ri, 1.5f);
-                                    const float ww = S.f[12][j] * (ri * ri * ri);
+                                    const float ww = ((others >> j) & 1u) ? S.f[12][j] * (ri * ri * ri) : 0.f;
                                     kahan_add(sx, cx, ww * dx);
                                     kahan_add(sy, cy, ww * dy);
                                     kahan_add(sz, cz, ww * dz);
+                                };
+                                for (int j = 0; j < n; j += 2) {
+                                    term(j, sx0, sy0, sz0, cx0, cy0, cz0);
+                                    if (j + 1 < n) term(j + 1, sx1, sy1, sz1, cx1, cy1, cz1);
                                 }
                                 const double gh = SP.G * h;
-                                st[3] = fma(gh, f2d(sx) - f2d(cx), st[3]);
-                                st[4] = fma(gh, f2d(sy) - f2d(cy), st[4]);
-                                st[5] = fma(gh, f2d(sz) - f2d(cz), st[5]);
+                                st[3] = fma(gh, (f2d(sx0) - f2d(cx0)) + (f2d(sx1) - f2d(cx1)), st[3]);
+                                st[4] = fma(gh, (f2d(sy0) - f2d(cy0)) + (f2d(sy1) - f2d(cy1)), st[4]);
+                                st[5] = fma(gh, (f2d(sz0) - f2d(cz0)) + (f2d(sz1) - f2d(cz1)), st[5]);
                             }
                         }
                         if (single) k8_drift(st, hd, !mixed);
@@ -609,8 +644,8 @@ __global__ void __launch_bounds__(K8_WARPS * 32) k_small(Level L, const int32_t 
                 ph[k] = 2;
                 if (__any_sync(FULL, sub)) {
                     if (pm[k]) {
-                        const unsigned e = k8_pair_handoff(S, lane, st, cm, sub, 0.5 * h, SP.depth0 + k + 1, -1, 0,
-                                                           SP, P, Q, mixed, pc, nl);
+                        const unsigned e = k8_pair_handoff(S, lane, st, cm, sub, 0.5 * h, etah_c * pow2f(k + 1),
+                                                           SP.depth0 + k + 1, -1, 0, SP, P, Q, mixed, pc, nl);
                         if (e) {
                             raise_err(ctr, e);
                             bad = true;
