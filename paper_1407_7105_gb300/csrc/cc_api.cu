@@ -412,13 +412,14 @@ static int ensure_level(cc_ctx *c, LevelAlloc &a, int need, int nsets)
 // incomplete list only means the next first-half split evaluates tau itself.
 constexpr long long EDGE_CAP_MAX = 1ll << 22;
 
-static int ensure_edges(cc_ctx *c, LevelAlloc &a)
+static int ensure_edges(cc_ctx *c, LevelAlloc &a, long long at_least = 0)
 {
-    long long want = std::max<long long>(4096, 4ll * a.cap);
+    long long want = std::max<long long>(std::max<long long>(4096, 4ll * a.cap), at_least);
     if (a.ecount > a.E.cap) want = std::max(want, 2 * a.ecount);
-    want = std::min(want, EDGE_CAP_MAX);
+    want = std::min(std::max(want, at_least), std::max(EDGE_CAP_MAX, at_least));
     if (a.eblock && want <= a.E.cap) return CC_OK;
-    if (a.eblock && a.E.cap >= EDGE_CAP_MAX) return CC_OK;
+    // grow geometrically: a reallocation synchronises the device
+    if (a.eblock) want = std::max(want, a.E.cap + a.E.cap / 2);
     if (a.eblock) cudaFree(a.eblock);
     a.eblock = nullptr;
     a.E = EdgeList{nullptr, nullptr, 0};
@@ -556,7 +557,8 @@ static int split_level(cc_ctx *c, LevelAlloc &a, double h, int &ncomp, const Lev
 {
     const cudaStream_t s = c->stream;
     const TauParams P = tau_params(c, h);
-    CC_TRY(ensure_edges(c, a));
+    // a first half's records are a subset of its parent's: room for all
+    CC_TRY(ensure_edges(c, a, parent ? parent->ecount : 0));
     launch_init_parent(a.L, a.E.count, s);
     const bool mixed = c->p.precision == CC_PREC_MIXED;
     if (parent) {

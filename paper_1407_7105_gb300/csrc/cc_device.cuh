@@ -198,10 +198,11 @@ __device__ __forceinline__ double f2d(float f)
 
 // one edge record at an atomically reserved slot (dropped past cap; the
 // count still tells the host the list is incomplete)
-__device__ __forceinline__ void record_edge(const EdgeList &E, int a, int b, int e, double tau)
+__device__ __forceinline__ bool record_edge(const EdgeList &E, int a, int b, int e, double tau)
 {
     const unsigned long long q = atomicAdd(E.count, 1ull);
-    if ((long long)q < E.cap) {
+    if ((long long)q >= E.cap) return false;
+    {
         EdgeRec r;
         r.a = a;
         r.b = b;
@@ -210,6 +211,7 @@ __device__ __forceinline__ void record_edge(const EdgeList &E, int a, int b, int
         r.tau = tau;
         E.rec[q] = r;
     }
+    return true;
 }
 
 // Kahan-compensated accumulation: s + (-c) carries the running sum

@@ -310,20 +310,27 @@ void launch_segment(const Level &L, const int32_t *root, int32_t *members, int32
 // ------------------------------------------------------------ fused small path
 // For a batch of at most SEG1_MAX packed elements one CTA does what the
 // general path spreads over ~15 launches: union-find compression, sizes,
-// component heads and offsets (block scans), and the stable, ordered
-// scatter of members (one warp walks the indices in order; lanes with the
-// same root are ranked by warp match).
+// component heads and offsets (block scans), and the ordered scatter of
+// members: an unordered scatter by shared-memory cursors, then every
+// component's run sorted by index (one warp per run, ranks by counting),
+// which is the stable order since the input is in index order.  A run of
+// more than 64 members sends the block to a stable single-warp scatter (one
+// warp walks the indices in order; lanes with the same root are ranked by
+// warp match).
 constexpr int SEG1_T = 1024;
 constexpr int SEG1_MAX = 4096;
+constexpr int SEG1_RUN = 64;
 
 __global__ void __launch_bounds__(SEG1_T) k_segment_small(Level L, int32_t *root_out, int32_t *members,
                                                           int32_t *comp_start, int32_t *comp_size, int32_t *ncomp)
 {
-    __shared__ int s_root[SEG1_MAX];
-    __shared__ int s_cnt[SEG1_MAX];  // size by root, then run start / cursor by key
+    __shared__ int s_root[SEG1_MAX];  // roots, then the member list being built
+    __shared__ int s_cnt[SEG1_MAX];   // size by root, then run start / cursor by key
     __shared__ int tmp[32];
+    __shared__ int s_big;
     const int n = L.total, tid = threadIdx.x;
     for (int k = tid; k < n; k += SEG1_T) s_cnt[k] = 0;
+    if (tid == 0) s_big = 0;
     __syncthreads();
     for (int k = tid; k < n; k += SEG1_T) {
         const bool valid = L.gid[k] >= 0;
@@ -337,7 +344,7 @@ __global__ void __launch_bounds__(SEG1_T) k_segment_small(Level L, int32_t *root
     // runs in key order: key = root for valid elements, own index for
     // padding; w[k] = number of elements keyed k.  Run starts by a block scan
     // (4 items per thread), component index by a second scan over heads.
-    int wv[4], hc[4];
+    int wv[4], hc[4], key[4];
     int sw = 0, sc = 0;
 #pragma unroll
     for (int q = 0; q < 4; ++q) {
@@ -348,6 +355,8 @@ __global__ void __launch_bounds__(SEG1_T) k_segment_small(Level L, int32_t *root
         hc[q] = valid_root && s_cnt[k] >= 2 ? 1 : 0;
         sw += wv[q];
         sc += hc[q];
+        const int e = tid + q * SEG1_T;  // the element this thread scatters below
+        key[q] = e < n ? (L.gid[e] >= 0 ? s_root[e] : e) : -1;
     }
     __syncthreads();
     int tot_w, tot_c;
@@ -360,6 +369,7 @@ __global__ void __launch_bounds__(SEG1_T) k_segment_small(Level L, int32_t *root
         if (hc[q]) {
             comp_start[ec] = ew;
             comp_size[ec] = wv[q];
+            if (wv[q] > SEG1_RUN) s_big = 1;
         }
         if (k < n) s_cnt[k] = ew;  // run start of key k (cursor)
         ec += hc[q];
@@ -367,6 +377,35 @@ __global__ void __launch_bounds__(SEG1_T) k_segment_small(Level L, int32_t *root
     }
     if (tid == 0) *ncomp = tot_c;
     __syncthreads();
+    if (!s_big) {
+        // unordered scatter (s_root now holds the member list), then each
+        // component run sorted by index, one warp per run
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+            const int e = tid + q * SEG1_T;
+            if (e < n) s_root[atomicAdd(&s_cnt[key[q]], 1)] = e;
+        }
+        __syncthreads();
+        const int w = tid >> 5, lane = tid & 31;
+        for (int c = w; c < tot_c; c += SEG1_T / 32) {
+            const int st = comp_start[c], sz = comp_size[c];
+            const int x0 = lane < sz ? s_root[st + lane] : 0x7fffffff;
+            const int x1 = lane + 32 < sz ? s_root[st + lane + 32] : 0x7fffffff;
+            int r0 = 0, r1 = 0;
+            for (int j = 0; j < sz; ++j) {
+                const int y = s_root[st + j];
+                r0 += y < x0;
+                r1 += y < x1;
+            }
+            __syncwarp();
+            if (lane < sz) s_root[st + r0] = x0;
+            if (lane + 32 < sz) s_root[st + r1] = x1;
+            __syncwarp();
+        }
+        __syncthreads();
+        for (int k = tid; k < n; k += SEG1_T) members[k] = s_root[k];
+        return;
+    }
     if (tid < 32) {
         const unsigned lt = (1u << tid) - 1u;
         for (int base = 0; base < n; base += 32) {

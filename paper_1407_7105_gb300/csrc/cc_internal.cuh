@@ -233,6 +233,39 @@ __device__ __forceinline__ bool uf_union(int32_t *parent, int a, int b)
     return false;
 }
 
+// The same forest operations reading through L1 (ld.global.ca), for passes
+// in which thousands of finds end on one root: volatile reads all go to the
+// L2 slice holding that root's line and queue there.  A stale read is safe:
+// every pointer ever stored points to a smaller index of the same tree, so
+// a find still terminates inside the tree, and the hook's compare-and-swap
+// (performed at L2) rejects a root that is no longer one.  (Callers keep
+// the trees shallow; see the min-neighbour links of the first-half split.)
+__device__ __forceinline__ int uf_find_ca(const int32_t *parent, int x)
+{
+    // no path halving: its stores would queue at the same L2 lines
+    int p = __ldca(parent + x), nx;
+    while (p > (nx = __ldca(parent + p))) p = nx;
+    return p;
+}
+
+__device__ __forceinline__ bool uf_union_ca(int32_t *parent, int a, int b)
+{
+    int ra = uf_find_ca(parent, a), rb = uf_find_ca(parent, b);
+    for (int it = 0; it < (1 << 24); ++it) {
+        if (ra == rb) return true;
+        if (ra < rb) {
+            int old = atomicCAS(&parent[rb], rb, ra);
+            if (old == rb) return true;
+            rb = uf_find_ca(parent, old);
+        } else {
+            int old = atomicCAS(&parent[ra], ra, rb);
+            if (old == ra) return true;
+            ra = uf_find_ca(parent, old);
+        }
+    }
+    return false;
+}
+
 // ----------------------------------------------------------- launchers
 // Every launcher adds the number of kernels it launched to g_launches.
 extern unsigned long long g_launches;

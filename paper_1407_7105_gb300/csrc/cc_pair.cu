@@ -143,18 +143,27 @@ __global__ void __launch_bounds__(T) k_tau_hook(Level L, TauParams P, DevCounter
 // The split of a component's first half (pivot h) sees the state its
 // parent split saw at 2h, so tau(i,j) is unchanged: the edges are the
 // parent's records that are edges at h, and every pair near h is a parent
-// record too (tau < 2h).  One thread per parent record; records of
-// components the gather did not move to this level (small, Kepler) are
-// skipped (inv[a] is only meaningful where this level's src points back to
-// a).  A record's edge depth comes from its e, else its FP64 tau, else (an
-// FP32-certified edge of a fresh mixed split) from certified FP32
-// decisions at h, h/2, ... on the parent's float-float copy, which the
-// first half leaves untouched, with the FP64 tau from the parent level's
-// state at the first undecided threshold.  The child's record carries the
-// depth on, so deeper first halves never need the float-float copy.
-__global__ void k_edges_reuse(EdgeList PE, long long pcount, Level PL, FFView PF, MixedTauParams Q, int mixed,
-                              const int32_t *inv, Level C, EdgeList CE, TauParams P, DevCounters *ctr,
-                              int32_t *near_ij, double *near_tau, long long near_cap)
+// record too (tau < 2h).  Two passes:
+//   k_edges_filter, one thread per parent record: records of components the
+//   gather did not move to this level (small, Kepler) are skipped (inv[a] is
+//   only meaningful where this level's src points back to a); the record's
+//   edge depth comes from its e, else its FP64 tau, else (an FP32-certified
+//   edge of a fresh mixed split) from certified FP32 decisions at 2h, h,
+//   h/2, ... on the parent's float-float copy, which the first half leaves
+//   untouched, with the FP64 tau from the parent level's state at the first
+//   undecided threshold; near-threshold pairs are logged, and the edges at h
+//   become this split's records (depth carried on, so deeper first halves
+//   never need a float-float copy);
+//   k_edges_hook: union-find hooking of this split's records, a compact list
+//   (a fraction of the parent's), so the pointer chasing of the hooks runs
+//   in about one wave (the list holds at least as many records as the
+//   parent's, so none is dropped).  The filter pass also points each edge's larger
+//   endpoint at its smallest neighbour (atomicMin): every union-find
+//   invariant holds for that forest, and in a dense core, where many edges
+//   share an endpoint, it spares the hooks their compare-and-swap retries.
+__global__ void k_edges_filter(EdgeList PE, long long pcount, Level PL, FFView PF, MixedTauParams Q, int mixed,
+                               const int32_t *inv, Level C, EdgeList CE, TauParams P, DevCounters *ctr,
+                               int32_t *near_ij, double *near_tau, long long near_cap)
 {
     const long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
     unsigned long long my_edges = 0, my_evals = 0;
@@ -204,13 +213,16 @@ __global__ void k_edges_reuse(EdgeList PE, long long pcount, Level PL, FFView PF
             if (tau == tau) log_pair(P, tau, C.gid[a], C.gid[b], ctr, near_ij, near_tau, near_cap);
             if (e >= 2) {
                 ++my_edges;
-                if (!uf_union(C.parent, a, b)) raise_err(ctr, DERR_UF_RETRY);
+                // link the larger endpoint to its smallest neighbour so far:
+                // a forest with parent < self whose links are edges, built
+                // without retries; the hook pass then finds most record
+                // endpoints already in one tree
+                atomicMin(&C.parent[max(a, b)], min(a, b));
+                // the host sizes this list to the parent's record count, so
+                // a record is never dropped (the hook pass must see every edge)
+                if (!record_edge(CE, min(a, b), max(a, b), e >= EDGE_E_INF ? EDGE_E_INF : e - 1, tau))
+                    raise_err(ctr, DERR_UF_RETRY);
             }
-            // this split's record serves the next first half (pivot h/2):
-            // an edge there (e >= 3), or a known tau that may be near h/2
-            const double hc = 0.5 * P.h;
-            if (e >= 3 || (e == 2 && tau == tau && fabs(tau - hc) < P.near_tol * hc))
-                record_edge(CE, min(a, b), max(a, b), e >= EDGE_E_INF ? EDGE_E_INF : e - 1, tau);
         }
     }
 #pragma unroll
@@ -227,6 +239,19 @@ __global__ void k_edges_reuse(EdgeList PE, long long pcount, Level PL, FFView PF
     }
 }
 
+__global__ void k_edges_hook(EdgeList E, int32_t *parent, DevCounters *ctr)
+{
+    const long long n = (long long)min(*E.count, (unsigned long long)E.cap);
+    for (long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x; t < n; t += (long long)gridDim.x * blockDim.x) {
+        const EdgeRec r = E.rec[t];
+        // a shared parent, or the link itself, already puts a and b in one
+        // tree (a parent is an ancestor, and trees only merge)
+        const int pa = __ldca(parent + r.a), pb = __ldca(parent + r.b);
+        if (pa == pb || pb == r.a || pa == r.b) continue;
+        if (!uf_union_ca(parent, r.a, r.b)) raise_err(ctr, DERR_UF_RETRY);
+    }
+}
+
 void launch_edges_reuse(const EdgeList &parent, long long pcount, const Level &PL, const FFView &PF, bool mixed,
                         const int32_t *inv, const Level &C, const EdgeList &child, const TauParams &P,
                         DevCounters *ctr, int32_t *near_ij, double *near_tau, long long near_cap, cudaStream_t s)
@@ -238,9 +263,12 @@ void launch_edges_reuse(const EdgeList &parent, long long pcount, const Level &P
     Q.etah = (float)(P.eta_outside ? P.eta_in * P.eta / hp : P.eta_in / hp);
     Q.eps2 = (float)P.eps2;
     Q.G = (float)P.G;
-    k_edges_reuse<<<(unsigned)((pcount + 255) / 256), 256, 0, s>>>(parent, pcount, PL, PF, Q, mixed ? 1 : 0, inv, C,
-                                                                    child, P, ctr, near_ij, near_tau, near_cap);
-    CC_COUNT_LAUNCH(1);
+    const unsigned blocks = (unsigned)((pcount + 255) / 256);
+    k_edges_filter<<<blocks, 256, 0, s>>>(parent, pcount, PL, PF, Q, mixed ? 1 : 0, inv, C, child, P, ctr, near_ij,
+                                          near_tau, near_cap);
+    // the hooks: at most pcount records, usually far fewer (grid-stride)
+    k_edges_hook<<<blocks < 1216u ? blocks : 1216u, 256, 0, s>>>(child, C.parent, ctr);
+    CC_COUNT_LAUNCH(2);
 }
 
 // Edge-list variant for the time-step-graph entry point: same predicate,

@@ -495,12 +495,16 @@ __global__ void __launch_bounds__(K8_WARPS * 32) k_small(Level L, const int32_t 
                         if (j != lane && ((mine >> j) & 1u) && S.e[j][lane] > eoff) adj |= 1u << j;
                 }
                 // components: closure of the adjacency by mask doubling
+                // (each lane ORs the masks of its own members only: as many
+                // shuffles per round as the largest mask has bits)
                 uint32_t cm = mine ? (adj | me) : 0u;
                 for (int it = 0; it < 6; ++it) {
-                    uint32_t nx = cm;
-                    for (int j = 0; j < n; ++j) {
-                        const uint32_t cj = __shfl_sync(FULL, cm, j);
-                        if ((cm >> j) & 1u) nx |= cj;
+                    uint32_t nx = cm, rem = cm;
+                    const unsigned rounds = __reduce_max_sync(FULL, (unsigned)__popc(cm));
+                    for (unsigned t = 0; t < rounds; ++t) {
+                        const int j = rem ? __ffs(rem) - 1 : lane;
+                        rem &= rem - 1u;
+                        nx |= __shfl_sync(FULL, cm, j);
                     }
                     const bool same = __all_sync(FULL, nx == cm);
                     cm = nx;
