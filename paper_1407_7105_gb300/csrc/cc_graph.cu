@@ -224,17 +224,19 @@ static int bits_for(long long maxval)
 }
 
 // ------------------------------------------------------------ compress
+// root of every element (the forest is final: finds read through L1, since
+// thousands of them end on one root) and component sizes by root, with one
+// atomic per distinct root in each warp (members of a giant component would
+// otherwise queue on one counter)
 __global__ void k_compress(Level L, int32_t *root)
 {
     const int k = blockIdx.x * blockDim.x + threadIdx.x;
-    if (k >= L.total) return;
-    if (L.gid[k] < 0) {
-        root[k] = k;
-        return;
-    }
-    const int r = uf_find(L.parent, k);
-    root[k] = r;
-    atomicAdd(&L.cnt[r], 1);
+    const bool in = k < L.total;
+    const bool valid = in && L.gid[k] >= 0;
+    const int r = valid ? uf_find_ca(L.parent, k) : (in ? k : -1);
+    if (in) root[k] = r;
+    const unsigned peers = __match_any_sync(0xffffffffu, valid ? r : -2 - (int)(threadIdx.x & 31));
+    if (valid && (threadIdx.x & 31) == __ffs(peers) - 1) atomicAdd(&L.cnt[r], __popc(peers));
 }
 
 void launch_compress(const Level &L, int32_t *root, cudaStream_t s)
@@ -334,7 +336,7 @@ __global__ void __launch_bounds__(SEG1_T) k_segment_small(Level L, int32_t *root
     __syncthreads();
     for (int k = tid; k < n; k += SEG1_T) {
         const bool valid = L.gid[k] >= 0;
-        const int r = valid ? uf_find(L.parent, k) : k;
+        const int r = valid ? uf_find_ca(L.parent, k) : k;
         s_root[k] = r;
         root_out[k] = r;
         if (valid) atomicAdd(&s_cnt[r], 1);
