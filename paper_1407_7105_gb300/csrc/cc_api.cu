@@ -35,6 +35,17 @@ constexpr int KICK_TILE = 64;   // must match the kick kernel
 
 thread_local std::string g_init_err;
 
+// set layout of a level batch: sizes -> aligned starts, the block
+// prefixes of every launch-shape variant, the packed total
+struct SetLayout {
+    std::vector<int32_t> start, n;
+    std::vector<int32_t> tau_off[N_TAU_VAR], k64_off[N_K64_VAR], mk_off[N_MK_VAR];
+    long long tau_blocks[N_TAU_VAR] = {}, k64_blocks[N_K64_VAR] = {}, mk_blocks[N_MK_VAR] = {};
+    int mk_chunks_max[N_MK_VAR] = {};
+    long long pairs = 0;
+    int total = 0;
+};
+
 struct LevelAlloc {
     Level L{};
     FFView F{};
@@ -51,12 +62,16 @@ struct LevelAlloc {
     // split products of this level
     int32_t *root = nullptr, *members = nullptr, *comp_start = nullptr, *comp_size = nullptr, *d_ncomp = nullptr;
     // component lists handed to the children
-    int32_t *klist = nullptr, *slist = nullptr, *lcomp_start = nullptr, *lpref = nullptr, *ldst = nullptr;
+    // (kqueue: the work-queue counters of the two small-kernel launches of a
+    // split, zeroed by the same upload as the lists)
+    int32_t *kqueue = nullptr, *klist = nullptr, *slist = nullptr, *lcomp_start = nullptr;
     void *listblock = nullptr;
     int list_cap = 0;
     std::vector<int32_t> h_size, h_start;
     std::vector<int32_t> h_set_n;  // set sizes of this level (host copy)
-    int32_t *h_info = nullptr;     // pinned: ncomp, sizes, starts (one D2H per split)
+    // device split summary, one block: [ncomp, -, edge-record count (8 B), sizes[nd], starts[nd]];
+    // h_info is its pinned host copy (one D2H per split)
+    int32_t *h_info = nullptr;
     int32_t *h_sets = nullptr;     // pinned staging of the set arrays (one H2D)
     int32_t *h_lists = nullptr;    // pinned staging of the component lists (one H2D)
     int info_cap = 0;
@@ -67,6 +82,9 @@ struct LevelAlloc {
     EdgeList E{nullptr, nullptr, 0};
     void *eblock = nullptr;
     long long ecount = 0;  // records the last split offered (complete if <= E.cap)
+    // host scratch of the classification, kept between splits (no reallocation)
+    std::vector<int32_t> v_kl, v_sl, v_lstart, v_lsize;
+    SetLayout child_layout;
 };
 
 // ------------------------------------------------------------ autotuner
@@ -119,7 +137,6 @@ struct cc_ctx {
     void *tmp = nullptr;  // staging for caller buffers
     size_t tmp_sz = 0;
     unsigned *d_bad = nullptr;
-    int *d_queue = nullptr;     // work queue of the small-component kernel
     cudaStream_t side = nullptr;  // small-component kernels overlap the level recursion
     int nsm = 152;
     double *d_kpart = nullptr;  // mixed-kick chunk partials
@@ -330,7 +347,7 @@ static int ensure_level(cc_ctx *c, LevelAlloc &a, int need, int nsets)
         const long long worst = std::min<long long>(2 * (long long)c->n + 64, 0x3fffffff);
         int cap = align_up(std::max<int>(need, (int)std::max<long long>(64, worst)), 64);
         size_t nd = (size_t)cap + PAD_TAIL;
-        size_t bytes = nd * 8 * 7 + nd * 4 * 12 + nd * 64 + 4096;
+        size_t bytes = nd * 8 * 7 + (nd * 11 + 4) * 4 + nd * 64 + 4096;
         if (cudaMalloc(&a.block, bytes) != cudaSuccess) {
             cudaGetLastError();
             return fail(c, CC_E_NOMEM, "device allocation failed (level buffer)");
@@ -339,9 +356,20 @@ static int ensure_level(cc_ctx *c, LevelAlloc &a, int need, int nsets)
         char *q = (char *)a.block;
         double **dp[7] = {&a.L.x, &a.L.y, &a.L.z, &a.L.vx, &a.L.vy, &a.L.vz, &a.L.m};
         for (int k = 0; k < 7; ++k) { *dp[k] = (double *)q; q += nd * 8; }
-        int32_t **ip[12] = {&a.L.gid, &a.L.sidx, &a.L.src, &a.L.parent, &a.L.cnt, &a.L.klab,
-                            &a.root, &a.members, &a.comp_start, &a.comp_size, &a.d_ncomp, &a.inv};
-        for (int k = 0; k < 12; ++k) { *ip[k] = (int32_t *)q; q += nd * 4; }
+        int32_t **ip[9] = {&a.L.gid, &a.L.sidx, &a.L.src, &a.L.parent, &a.L.cnt, &a.L.klab,
+                           &a.root, &a.members, &a.inv};
+        for (int k = 0; k < 9; ++k) { *ip[k] = (int32_t *)q; q += nd * 4; }
+        a.d_ncomp = (int32_t *)q;
+        a.comp_size = a.d_ncomp + 4;
+        a.comp_start = a.d_ncomp + 4 + nd;
+        q += (2 * nd + 4) * 4;
+        if (a.h_info) cudaFreeHost(a.h_info);
+        a.h_info = nullptr;
+        if (cudaMallocHost(&a.h_info, (2 * nd + 4) * 4) != cudaSuccess) {
+            cudaGetLastError();
+            return fail(c, CC_E_NOMEM, "pinned host allocation failed (split summary)");
+        }
+        a.info_cap = (int)nd;
         a.F.pq = (float4 *)q; q += nd * 32;
         a.F.vq = (float4 *)q; q += nd * 32;
         a.F.maxes = (float *)q;
@@ -362,11 +390,10 @@ static int ensure_level(cc_ctx *c, LevelAlloc &a, int need, int nsets)
             return fail(c, CC_E_NOMEM, "pinned host allocation failed (component lists)");
         }
         int32_t *lq = (int32_t *)a.listblock;
+        a.kqueue = lq; lq += 4;
         a.klist = lq; lq += a.list_cap;
         a.slist = lq; lq += a.list_cap;
-        a.lcomp_start = lq; lq += a.list_cap;
-        a.lpref = lq; lq += a.list_cap + 1;
-        a.ldst = lq;
+        a.lcomp_start = lq;
     }
     if (nsets + 2 > a.set_cap) {
         if (a.setblock) cudaFree(a.setblock);
@@ -414,6 +441,7 @@ constexpr long long EDGE_CAP_MAX = 1ll << 22;
 
 static int ensure_edges(cc_ctx *c, LevelAlloc &a, long long at_least = 0)
 {
+    a.E.count = (unsigned long long *)(a.d_ncomp + 2);  // in the split summary block
     long long want = std::max<long long>(std::max<long long>(4096, 4ll * a.cap), at_least);
     if (a.ecount > a.E.cap) want = std::max(want, 2 * a.ecount);
     want = std::min(std::max(want, at_least), std::max(EDGE_CAP_MAX, at_least));
@@ -427,23 +455,11 @@ static int ensure_edges(cc_ctx *c, LevelAlloc &a, long long at_least = 0)
         cudaGetLastError();
         return fail(c, CC_E_NOMEM, "device allocation failed (edge records)");
     }
-    a.E.count = (unsigned long long *)a.eblock;
     a.E.rec = (EdgeRec *)((char *)a.eblock + 256);
     a.E.cap = want;
-    CC_CUDA(c, cudaMemsetAsync(a.eblock, 0, 256, c->stream));
+    a.E.count = (unsigned long long *)(a.d_ncomp + 2);
     return CC_OK;
 }
-
-// upload the set layout (sizes -> aligned starts, tile prefixes); returns
-// the packed total through L.total
-struct SetLayout {
-    std::vector<int32_t> start, n;
-    std::vector<int32_t> tau_off[N_TAU_VAR], k64_off[N_K64_VAR], mk_off[N_MK_VAR];
-    long long tau_blocks[N_TAU_VAR] = {}, k64_blocks[N_K64_VAR] = {}, mk_blocks[N_MK_VAR] = {};
-    int mk_chunks_max[N_MK_VAR] = {};
-    long long pairs = 0;
-    int total = 0;
-};
 
 // block prefixes of every launch-shape variant: triangular tau tiles,
 // FP64-kick i-tiles, mixed-kick (i-tile, j-chunk) blocks
@@ -458,6 +474,7 @@ static void make_layout(const std::vector<int32_t> &sizes, SetLayout &S)
     int pos = 0;
     long long tb[N_TAU_VAR] = {}, kb[N_K64_VAR] = {}, mb[N_MK_VAR] = {};
     S.pairs = 0;
+    for (int v = 0; v < N_MK_VAR; ++v) S.mk_chunks_max[v] = 0;
     for (size_t s = 0; s < ns; ++s) {
         S.start[s] = pos;
         pos += align_up(sizes[s], SET_ALIGN);
@@ -587,19 +604,9 @@ static int split_level(cc_ctx *c, LevelAlloc &a, double h, int &ncomp, const Lev
         ev_end(c, ev);
     }
     launch_compress_segment(a.L, a.root, a.members, a.comp_start, a.comp_size, a.d_ncomp, c->seg_scratch, s);
-    // one round trip: the count and, bounded by total/2, sizes and starts
+    // one round trip: count, record count, sizes and (bounded by total/2) starts
     const int maxc = a.L.total / 2 + 1;
-    if (maxc > a.info_cap) {
-        if (a.h_info) cudaFreeHost(a.h_info);
-        a.h_info = nullptr;
-        const int cap2 = std::max(maxc, a.cap / 2 + 8);
-        CC_CUDA(c, cudaMallocHost(&a.h_info, (size_t)(2 * cap2 + 4) * 4));
-        a.info_cap = cap2;
-    }
-    CC_CUDA(c, cudaMemcpyAsync(a.h_info, a.d_ncomp, 4, cudaMemcpyDeviceToHost, s));
-    CC_CUDA(c, cudaMemcpyAsync(a.h_info + 2, a.E.count, 8, cudaMemcpyDeviceToHost, s));
-    CC_CUDA(c, cudaMemcpyAsync(a.h_info + 4, a.comp_size, (size_t)maxc * 4, cudaMemcpyDeviceToHost, s));
-    CC_CUDA(c, cudaMemcpyAsync(a.h_info + 4 + a.info_cap, a.comp_start, (size_t)maxc * 4, cudaMemcpyDeviceToHost, s));
+    CC_CUDA(c, cudaMemcpyAsync(a.h_info, a.d_ncomp, (size_t)(4 + a.info_cap + maxc) * 4, cudaMemcpyDeviceToHost, s));
     CC_CUDA(c, cudaStreamSynchronize(s));
     const int32_t nc = a.h_info[0];
     ncomp = nc;
@@ -648,7 +655,8 @@ static int ensure_kpart(cc_ctx *c, int chunks, int fcap)
 
 // K_{h,V} on a level: labels lab (packed order); order = the root-sorted
 // order of the mixed kick (its labels at L.klab, prepared by the caller)
-static int level_kick(cc_ctx *c, LevelAlloc &a, const int32_t *lab, const int32_t *order, double h)
+static int level_kick(cc_ctx *c, LevelAlloc &a, const int32_t *lab, const int32_t *order, double h,
+                      double drift_dt = 0.0)
 {
     const cudaStream_t s = c->stream;
     int bin;
@@ -659,7 +667,7 @@ static int level_kick(cc_ctx *c, LevelAlloc &a, const int32_t *lab, const int32_
         CC_TRY(ensure_kpart(c, a.mk_chunks_max[var], a.F.cap));
         const int ev = ev_begin(c, 1, nullptr, timed ? TK_MK : -1, bin, var, (double)a.pairs);
         launch_kick_mixed(L, a.F, order, a.mk_off[var], (int)a.mk_blocks[var], MK_VAR_CHUNK[var],
-                          a.mk_chunks_max[var] > 1, c->p.eps * c->p.eps, h, c->d_ctr, c->d_kpart, s);
+                          a.mk_chunks_max[var] > 1, c->p.eps * c->p.eps, h, c->d_ctr, c->d_kpart, lab, drift_dt, s);
         ev_end(c, ev);
     } else {
         const int var = tune_pick(c, TK_K64, a.k64_blocks, a.pairs, &bin, &timed);
@@ -674,12 +682,15 @@ static int level_kick(cc_ctx *c, LevelAlloc &a, const int32_t *lab, const int32_
 static int dkd(cc_ctx *c, LevelAlloc &a, double h)
 {
     const cudaStream_t s = c->stream;
-    launch_drift(a.L, a.root, 0.5 * h, s);
     if (c->p.precision == CC_PREC_MIXED && !(h < c->p.h_fp64)) {
-        // positions in the root-sorted order of the split: members of one
-        // component are adjacent, so tiles inside one component are skipped
-        launch_prep_kick(a.L, a.F, a.members, a.root, c->p.G, s);
+        // positions in the root-sorted order of the split (members of one
+        // component adjacent: tiles inside one component are skipped); both
+        // drifts ride on the copy and on the partial reduce
+        launch_prep_kick(a.L, a.F, a.members, a.root, c->p.G, 0.5 * h, s);
+        CC_TRY(level_kick(c, a, a.root, a.members, h, 0.5 * h));
+        return CC_OK;
     }
+    launch_drift(a.L, a.root, 0.5 * h, s);
     CC_TRY(level_kick(c, a, a.root, a.members, h));
     launch_drift(a.L, a.root, 0.5 * h, s);
     return CC_OK;
@@ -695,24 +706,43 @@ static int process(cc_ctx *c, int d, double h, const LevelAlloc *parent)
     int ncomp = 0;
     CC_TRY(split_level(c, a, h, ncomp, parent));
     // classify the components (host, sizes are known)
-    std::vector<int32_t> kl, sl, lstart, lsize;
+    std::vector<int32_t> &kl = a.v_kl, &sl = a.v_sl, &lstart = a.v_lstart, &lsize = a.v_lsize;
+    kl.clear();
+    sl.clear();
+    lstart.clear();
+    lsize.clear();
+    // small components largest first (the longest sub-recursions start
+    // early): a counting sort by size, stable within a size
+    int bucket[34] = {0};
+    const int smax = std::min(c->p.s_small, 32);
     for (int q = 0; q < ncomp; ++q) {
         const int sz = a.h_size[q];
         if (c->p.kepler && sz == 2) kl.push_back(q);
-        else if (sz <= c->p.s_small) sl.push_back(q);
+        else if (sz <= smax) ++bucket[sz];
         else {
             lstart.push_back(a.h_start[q]);
             lsize.push_back(sz);
         }
     }
-    // small components largest first: the longest sub-recursions start early
-    std::stable_sort(sl.begin(), sl.end(), [&](int32_t u, int32_t v) { return a.h_size[u] > a.h_size[v]; });
+    int nsmall = 0;
+    for (int z = smax; z >= 0; --z) {
+        const int k = bucket[z];
+        bucket[z] = nsmall;
+        nsmall += k;
+    }
+    sl.resize(nsmall);
+    for (int q = 0; q < ncomp; ++q) {
+        const int sz = a.h_size[q];
+        if (!(c->p.kepler && sz == 2) && sz <= smax) sl[bucket[sz]++] = q;
+    }
     const int nk = (int)kl.size(), nl = (int)lsize.size(), ns = (int)sl.size();
-    // all component lists of this split travel in one pinned transfer
+    // all component lists of this split (and the zeroed queue counters of
+    // its small-kernel launches) travel in one pinned transfer
     const int lc = a.list_cap;
     int32_t *hl = a.h_lists;
-    if (nk) std::memcpy(hl, kl.data(), nk * 4);
-    if (ns) std::memcpy(hl + lc, sl.data(), ns * 4);
+    hl[0] = hl[1] = hl[2] = hl[3] = 0;
+    if (nk) std::memcpy(hl + 4, kl.data(), nk * 4);
+    if (ns) std::memcpy(hl + 4 + lc, sl.data(), ns * 4);
     SmallParams SP;
     SP.G = c->p.G;
     SP.eps2 = c->p.eps * c->p.eps;
@@ -728,21 +758,15 @@ static int process(cc_ctx *c, int d, double h, const LevelAlloc *parent)
     SP.max_depth = c->p.max_depth;
     if (ns && d + 1 > c->p.max_depth) return fail(c, CC_E_DEPTH, "recursion deeper than max_depth");
     c->st.kepler_calls += 2ull * nk;
-    int nmem = 0;
     if (nl) {
-        SetLayout S;
+        SetLayout &S = c->lv[d + 1].child_layout;
         make_layout(lsize, S);
-        std::vector<int32_t> pref(nl + 1, 0);
-        for (int q = 0; q < nl; ++q) pref[q + 1] = pref[q] + lsize[q];
-        nmem = pref[nl];
-        std::memcpy(hl + 2 * lc, lstart.data(), nl * 4);
-        std::memcpy(hl + 3 * lc, pref.data(), (nl + 1) * 4);
-        std::memcpy(hl + 4 * lc + 1, S.start.data(), nl * 4);
+        std::memcpy(hl + 4 + 2 * lc, lstart.data(), nl * 4);
         CC_TRY(upload_layout(c, c->lv[d + 1], S));
     }
     if (nk || ns || nl) {
-        const size_t words = nl ? (size_t)(4 * lc + 1 + nl) : ns ? (size_t)(lc + ns) : (size_t)nk;
-        CC_CUDA(c, cudaMemcpyAsync(a.klist, hl, words * 4, cudaMemcpyHostToDevice, c->stream));
+        const size_t words = nl ? (size_t)(4 + 2 * lc + nl) : ns ? (size_t)(4 + lc + ns) : (size_t)(4 + nk);
+        CC_CUDA(c, cudaMemcpyAsync(a.kqueue, hl, words * 4, cudaMemcpyHostToDevice, c->stream));
     }
     LevelAlloc &a2 = a;
     if (ns && !a2.ev_ready) {
@@ -762,14 +786,14 @@ static int process(cc_ctx *c, int d, double h, const LevelAlloc *parent)
             CC_CUDA(c, cudaStreamWaitEvent(c->side, a2.ev_ready, 0));
             const int ev = ev_begin(c, 2, c->side);
             launch_small(a2.L, a2.members, a2.comp_start, a2.comp_size, a2.slist, ns, SP, c->d_ctr,
-                         c->d_queue + 4 * (d & 1), c->d_near_ij, c->d_near_tau, c->near_cap, c->nsm, c->side);
+                         a2.kqueue + half, c->d_near_ij, c->d_near_tau, c->near_cap, c->nsm, c->side);
             ev_end(c, ev, c->side);
             CC_CUDA(c, cudaEventRecord(a2.ev_small, c->side));
         }
         if (nk) launch_kepler(a2.L, a2.members, a2.comp_start, a2.klist, nk, c->p.G, 0.5 * h, c->d_ctr, c->stream);
         if (nl) {
             LevelAlloc &ch = c->lv[d + 1];
-            launch_gather(a2.L, ch.L, a2.members, a2.lcomp_start, a2.lpref, a2.ldst, nl, nmem, a2.inv, c->stream);
+            launch_gather(a2.L, ch.L, a2.members, a2.lcomp_start, a2.inv, c->stream);
             // first half: the state this split saw, so its edge records
             // (when complete) give the child's split; second half: fresh
             const bool reuse = half == 0 && a2.ecount <= a2.E.cap;
@@ -883,7 +907,7 @@ int cc_init(cc_ctx **out, int64_t n, const double *m, const double *x3, const do
         cudaMalloc(&c->d_m, n * 8) != cudaSuccess || cudaMalloc(&c->d_ctr, sizeof(DevCounters)) != cudaSuccess ||
         cudaMalloc(&c->d_near_ij, c->near_cap * 8) != cudaSuccess ||
         cudaMalloc(&c->d_near_tau, c->near_cap * 8) != cudaSuccess ||
-        cudaMalloc(&c->d_bad, 16) != cudaSuccess || cudaMalloc(&c->d_queue, 64) != cudaSuccess) {
+        cudaMalloc(&c->d_bad, 16) != cudaSuccess) {
         cudaGetLastError();
         c->err = "cc_init: device allocation failed";
         return bail(CC_E_NOMEM);
@@ -1102,7 +1126,7 @@ int cc_kick(cc_ctx *c, const int32_t *set, int64_t n_set, const int32_t *labels,
     if (c->p.precision == CC_PREC_MIXED && !(h < c->p.h_fp64)) {
         // the mixed kick works in label-sorted order (members of a group adjacent)
         launch_label_order(dl, (int)n_set, u.L.total, order, c->seg_scratch, c->stream);
-        launch_prep_kick(u.L, u.F, order, dl, c->p.G, c->stream);
+        launch_prep_kick(u.L, u.F, order, dl, c->p.G, 0.0, c->stream);
     }
     CC_TRY(level_kick(c, u, dl, order, h));
     CC_CUDA(c, cudaStreamSynchronize(c->stream));
@@ -1222,7 +1246,7 @@ int cc_destroy(cc_ctx *c)
     for (auto &a : c->lv) free_level(a);
     free_level(c->unit);
     void *ptrs[] = {c->d_x3, c->d_v3, c->d_m, c->d_ctr, c->d_near_ij, c->d_near_tau, c->d_partial,
-                    c->tmp, c->seg_scratch, c->d_sys_off, c->d_bad, c->d_kpart, c->d_queue};
+                    c->tmp, c->seg_scratch, c->d_sys_off, c->d_bad, c->d_kpart};
     for (void *q : ptrs)
         if (q) cudaFree(q);
     delete c;

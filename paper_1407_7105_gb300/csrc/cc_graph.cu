@@ -468,15 +468,22 @@ __device__ __forceinline__ int upper_find(const int32_t *off, int nsets, int t)
     return lo;
 }
 
-__global__ void k_gather(Level P, Level C, const int32_t *members, const int32_t *lcomp_start,
-                         const int32_t *lpref, const int32_t *ldst, int nl, int nmem, int32_t *inv)
+// One thread per position of the child level: a member of large component
+// c (child set c) copies its state from the parent, a padding slot is
+// marked (gid = -1); inv[k] = the child index of parent element k (written
+// for the gathered elements only; a reader checks C.src[inv[k]] == k)
+__global__ void k_gather(Level P, Level C, const int32_t *members, const int32_t *lcomp_start, int32_t *inv)
 {
-    const int t = blockIdx.x * blockDim.x + threadIdx.x;
-    if (t >= nmem) return;
-    const int c = upper_find(lpref, nl, t);
-    const int w = t - lpref[c];
+    const int d = blockIdx.x * blockDim.x + threadIdx.x;
+    if (d >= C.total) return;
+    const int c = upper_find(C.set_start, C.nsets, d);
+    const int w = d - C.set_start[c];
+    if (w >= C.set_n[c]) {
+        C.gid[d] = -1;
+        C.sidx[d] = -1;
+        return;
+    }
     const int k = members[lcomp_start[c] + w];
-    const int d = ldst[c] + w;
     C.x[d] = P.x[k]; C.y[d] = P.y[k]; C.z[d] = P.z[k];
     C.vx[d] = P.vx[k]; C.vy[d] = P.vy[k]; C.vz[d] = P.vz[k];
     C.m[d] = P.m[k];
@@ -486,14 +493,11 @@ __global__ void k_gather(Level P, Level C, const int32_t *members, const int32_t
     inv[k] = d;
 }
 
-// inv[k] = the child index of parent element k (written for the gathered
-// elements only; a reader checks C.src[inv[k]] == k)
-void launch_gather(const Level &P, const Level &C, const int32_t *members, const int32_t *lcomp_start,
-                   const int32_t *lpref, const int32_t *ldst, int nl, int nmem, int32_t *inv, cudaStream_t s)
+void launch_gather(const Level &P, const Level &C, const int32_t *members, const int32_t *lcomp_start, int32_t *inv,
+                   cudaStream_t s)
 {
-    fill_pad(C, s);
-    if (nmem > 0) {
-        k_gather<<<(nmem + 255) / 256, 256, 0, s>>>(P, C, members, lcomp_start, lpref, ldst, nl, nmem, inv);
+    if (C.total > 0) {
+        k_gather<<<(C.total + 255) / 256, 256, 0, s>>>(P, C, members, lcomp_start, inv);
         CC_COUNT_LAUNCH(1);
     }
 }

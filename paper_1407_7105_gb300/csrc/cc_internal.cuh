@@ -309,8 +309,8 @@ void launch_segment(const Level &L, const int32_t *root, int32_t *members, int32
                     int32_t *comp_size, int32_t *d_ncomp, void *scratch, cudaStream_t s);
 void launch_compress_segment(const Level &L, int32_t *root, int32_t *members, int32_t *comp_start,
                              int32_t *comp_size, int32_t *d_ncomp, void *scratch, cudaStream_t s);
-void launch_gather(const Level &P, const Level &C, const int32_t *members, const int32_t *lcomp_start,
-                   const int32_t *lpref, const int32_t *ldst, int nl, int nmem, int32_t *inv, cudaStream_t s);
+void launch_gather(const Level &P, const Level &C, const int32_t *members, const int32_t *lcomp_start, int32_t *inv,
+                   cudaStream_t s);
 void launch_scatter(const Level &P, const Level &C, cudaStream_t s);
 void launch_pack_state(const double *x3, const double *v3, const double *m, long long n, const Level &L,
                        const int32_t *sys_src_start, cudaStream_t s);
@@ -338,11 +338,14 @@ void launch_tau_mixed(const Level &L, const FFView &F, int ntiles, const TauPara
                       cudaStream_t s);
 int mixed_kick_blocks(int n, int chunk);
 int mixed_kick_chunks(int n, int chunk);
+// drift_dt > 0: the level's drift of rest-set members (component size 1 by
+// root) fused in: before the positions are copied (prep), after the kick
+// (the partial reduce, launched for it even without multi-chunk sets)
 void launch_prep_kick(const Level &L, const FFView &F, const int32_t *order, const int32_t *root, double G,
-                      cudaStream_t s);
+                      double drift_dt, cudaStream_t s);
 void launch_kick_mixed(const Level &L, const FFView &F, const int32_t *order, const int32_t *koff, int nblocks,
                        int chunk, bool multi_chunk, double eps2, double h, DevCounters *ctr, double *partial,
-                       cudaStream_t s);
+                       const int32_t *root, double drift_dt, cudaStream_t s);
 
 // cc_small.cu
 void launch_small(const Level &L, const int32_t *members, const int32_t *comp_start, const int32_t *comp_size,

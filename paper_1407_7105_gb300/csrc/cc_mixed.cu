@@ -67,8 +67,10 @@ void launch_prep_ff(const Level &L, const FFView &F, double G, bool with_v, cuda
 }
 
 // positions (hi, G m), (lo) and labels in the root-sorted order of the
-// split: position t holds packed element order[t]
-__global__ void k_prep_kick(Level L, FFView F, const int32_t *order, const int32_t *root, float G)
+// split: position t holds packed element order[t].  dt > 0: the level's
+// first drift D_{h/2,T_R} of rest-set members (component size 1, Eq. drift,
+// exact IEEE operations) is applied first, in the same pass.
+__global__ void k_prep_kick(Level L, FFView F, const int32_t *order, const int32_t *root, float G, double dt)
 {
     const int t = blockIdx.x * blockDim.x + threadIdx.x;
     if (t >= L.total) return;
@@ -76,6 +78,11 @@ __global__ void k_prep_kick(Level L, FFView F, const int32_t *order, const int32
     if (L.gid[k] < 0) {
         L.klab[t] = -1 - t;
         return;
+    }
+    if (dt > 0.0 && L.cnt[root[k]] == 1) {
+        L.x[k] = __dadd_rn(L.x[k], __dmul_rn(dt, L.vx[k]));
+        L.y[k] = __dadd_rn(L.y[k], __dmul_rn(dt, L.vy[k]));
+        L.z[k] = __dadd_rn(L.z[k], __dmul_rn(dt, L.vz[k]));
     }
     const double xs[3] = {L.x[k], L.y[k], L.z[k]};
     float hi[3], lo[3];
@@ -87,10 +94,10 @@ __global__ void k_prep_kick(Level L, FFView F, const int32_t *order, const int32
 }
 
 void launch_prep_kick(const Level &L, const FFView &F, const int32_t *order, const int32_t *root, double G,
-                      cudaStream_t s)
+                      double drift_dt, cudaStream_t s)
 {
     if (L.total <= 0) return;
-    k_prep_kick<<<(L.total + 255) / 256, 256, 0, s>>>(L, F, order, root, (float)G);
+    k_prep_kick<<<(L.total + 255) / 256, 256, 0, s>>>(L, F, order, root, (float)G, drift_dt);
     CC_COUNT_LAUNCH(1);
 }
 
@@ -403,7 +410,8 @@ __global__ void __launch_bounds__(MK_T) k_kick_mixed(Level L, FFView F, const in
 // long instead of nchunk (an FP64 add's latency dominates this kernel).
 constexpr int KR_LANES = 8;
 
-__global__ void k_kick_reduce(Level L, FFView F, const int32_t *order, int chunk, double h, const double *partial)
+__global__ void k_kick_reduce(Level L, FFView F, const int32_t *order, int chunk, double h, const double *partial,
+                              const int32_t *root, double drift_dt)
 {
     const long long g = (long long)blockIdx.x * blockDim.x + threadIdx.x;
     const int t = (int)(g / KR_LANES), sub = (int)(g % KR_LANES);
@@ -436,6 +444,13 @@ __global__ void k_kick_reduce(Level L, FFView F, const int32_t *order, int chunk
         L.vy[k] += h * ay;
         L.vz[k] += h * az;
     }
+    // drift_dt > 0: the level's second drift of rest-set members, after their
+    // kick (the kick kernels read the float-float copy, never x)
+    if (drift_dt > 0.0 && sub == 0 && k >= 0 && L.gid[k] >= 0 && L.cnt[root[k]] == 1) {
+        L.x[k] = __dadd_rn(L.x[k], __dmul_rn(drift_dt, L.vx[k]));
+        L.y[k] = __dadd_rn(L.y[k], __dmul_rn(drift_dt, L.vy[k]));
+        L.z[k] = __dadd_rn(L.z[k], __dmul_rn(drift_dt, L.vz[k]));
+    }
 }
 
 int mixed_kick_blocks(int n, int chunk)
@@ -452,14 +467,16 @@ int mixed_kick_chunks(int n, int chunk)
 
 void launch_kick_mixed(const Level &L, const FFView &F, const int32_t *order, const int32_t *koff, int nblocks,
                        int chunk, bool multi_chunk, double eps2, double h, DevCounters *ctr, double *partial,
-                       cudaStream_t s)
+                       const int32_t *root, double drift_dt, cudaStream_t s)
 {
-    if (nblocks <= 0) return;
-    k_kick_mixed<<<nblocks, MK_T, 0, s>>>(L, F, order, koff, chunk, (float)eps2, h, ctr, partial);
-    CC_COUNT_LAUNCH(1);
-    if (multi_chunk) {
+    if (nblocks > 0) {
+        k_kick_mixed<<<nblocks, MK_T, 0, s>>>(L, F, order, koff, chunk, (float)eps2, h, ctr, partial);
+        CC_COUNT_LAUNCH(1);
+    }
+    if ((multi_chunk && nblocks > 0) || (drift_dt > 0.0 && L.total > 0)) {
         const long long threads = (long long)L.total * KR_LANES;
-        k_kick_reduce<<<(unsigned)((threads + 255) / 256), 256, 0, s>>>(L, F, order, chunk, h, partial);
+        k_kick_reduce<<<(unsigned)((threads + 255) / 256), 256, 0, s>>>(L, F, order, multi_chunk ? chunk : 1 << 30, h,
+                                                                        partial, root, drift_dt);
         CC_COUNT_LAUNCH(1);
     }
 }

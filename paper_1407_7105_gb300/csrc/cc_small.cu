@@ -698,7 +698,7 @@ void launch_small(const Level &L, const int32_t *members, const int32_t *comp_st
                   int32_t *near_ij, double *near_tau, long long near_cap, int nsm, cudaStream_t s)
 {
     if (ns <= 0) return;
-    cudaMemsetAsync(queue, 0, sizeof(int), s);
+    // *queue is zero on entry (the caller uploads it with the component list)
     const int want = (ns + K8_WARPS - 1) / K8_WARPS;
     const int grid = want < nsm * 8 ? want : nsm * 8;
     k_small<<<grid, K8_WARPS * 32, 0, s>>>(L, members, comp_start, comp_size, slist, ns, SP, ctr, queue, near_ij,
