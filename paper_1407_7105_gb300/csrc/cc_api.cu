@@ -76,6 +76,7 @@ struct LevelAlloc {
     int32_t *h_lists = nullptr;    // pinned staging of the component lists (one H2D)
     int info_cap = 0;
     cudaEvent_t ev_ready = nullptr, ev_small = nullptr;  // side-stream joins
+    cudaEvent_t ev_info = nullptr;                       // split summary copied
     // edge records of this level's last split (read by the first-half split
     // of the next level) and the parent -> child index map of the gather
     int32_t *inv = nullptr;
@@ -83,7 +84,7 @@ struct LevelAlloc {
     void *eblock = nullptr;
     long long ecount = 0;  // records the last split offered (complete if <= E.cap)
     // host scratch of the classification, kept between splits (no reallocation)
-    std::vector<int32_t> v_kl, v_sl, v_lstart, v_lsize;
+    std::vector<int32_t> v_lstart, v_lsize;
     SetLayout child_layout;
 };
 
@@ -324,6 +325,8 @@ static void free_level(LevelAlloc &a)
     a.h_sets = a.h_lists = nullptr;
     if (a.ev_ready) cudaEventDestroy(a.ev_ready);
     if (a.ev_small) cudaEventDestroy(a.ev_small);
+    if (a.ev_info) cudaEventDestroy(a.ev_info);
+    a.ev_info = nullptr;
     a.h_info = nullptr;
     a.info_cap = 0;
     a.ev_ready = a.ev_small = nullptr;
@@ -570,7 +573,7 @@ static int process(cc_ctx *c, int d, double h, const LevelAlloc *parent);
 // parent != null: this is the first half of the parent's components, whose
 // split saw the same state at 2h, so the edges come from the parent's
 // edge records (a pass over the records instead of all pairs).
-static int split_level(cc_ctx *c, LevelAlloc &a, double h, int &ncomp, const LevelAlloc *parent)
+static int split_launch(cc_ctx *c, LevelAlloc &a, double h, const LevelAlloc *parent)
 {
     const cudaStream_t s = c->stream;
     const TauParams P = tau_params(c, h);
@@ -607,7 +610,16 @@ static int split_level(cc_ctx *c, LevelAlloc &a, double h, int &ncomp, const Lev
     // one round trip: count, record count, sizes and (bounded by total/2) starts
     const int maxc = a.L.total / 2 + 1;
     CC_CUDA(c, cudaMemcpyAsync(a.h_info, a.d_ncomp, (size_t)(4 + a.info_cap + maxc) * 4, cudaMemcpyDeviceToHost, s));
-    CC_CUDA(c, cudaStreamSynchronize(s));
+    if (!a.ev_info) CC_CUDA(c, cudaEventCreateWithFlags(&a.ev_info, cudaEventDisableTiming));
+    CC_CUDA(c, cudaEventRecord(a.ev_info, s));
+    return CC_OK;
+}
+
+// wait for the split summary (only it: kernels queued after it keep
+// running) and account the split
+static int split_finish(cc_ctx *c, LevelAlloc &a, const LevelAlloc *parent, int &ncomp)
+{
+    CC_CUDA(c, cudaEventSynchronize(a.ev_info));
     const int32_t nc = a.h_info[0];
     ncomp = nc;
     std::memcpy(&a.ecount, a.h_info + 2, 8);
@@ -703,46 +715,12 @@ static int process(cc_ctx *c, int d, double h, const LevelAlloc *parent)
     // lv is sized once at init (max_depth + 2 levels) and never reallocates,
     // so references into it stay valid across the recursion
     LevelAlloc &a = c->lv[d];
-    int ncomp = 0;
-    CC_TRY(split_level(c, a, h, ncomp, parent));
-    // classify the components (host, sizes are known)
-    std::vector<int32_t> &kl = a.v_kl, &sl = a.v_sl, &lstart = a.v_lstart, &lsize = a.v_lsize;
-    kl.clear();
-    sl.clear();
-    lstart.clear();
-    lsize.clear();
-    // small components largest first (the longest sub-recursions start
-    // early): a counting sort by size, stable within a size
-    int bucket[34] = {0};
-    const int smax = std::min(c->p.s_small, 32);
-    for (int q = 0; q < ncomp; ++q) {
-        const int sz = a.h_size[q];
-        if (c->p.kepler && sz == 2) kl.push_back(q);
-        else if (sz <= smax) ++bucket[sz];
-        else {
-            lstart.push_back(a.h_start[q]);
-            lsize.push_back(sz);
-        }
-    }
-    int nsmall = 0;
-    for (int z = smax; z >= 0; --z) {
-        const int k = bucket[z];
-        bucket[z] = nsmall;
-        nsmall += k;
-    }
-    sl.resize(nsmall);
-    for (int q = 0; q < ncomp; ++q) {
-        const int sz = a.h_size[q];
-        if (!(c->p.kepler && sz == 2) && sz <= smax) sl[bucket[sz]++] = q;
-    }
-    const int nk = (int)kl.size(), nl = (int)lsize.size(), ns = (int)sl.size();
-    // all component lists of this split (and the zeroed queue counters of
-    // its small-kernel launches) travel in one pinned transfer
-    const int lc = a.list_cap;
-    int32_t *hl = a.h_lists;
-    hl[0] = hl[1] = hl[2] = hl[3] = 0;
-    if (nk) std::memcpy(hl + 4, kl.data(), nk * 4);
-    if (ns) std::memcpy(hl + 4 + lc, sl.data(), ns * 4);
+    const cudaStream_t s = c->stream;
+    CC_TRY(split_launch(c, a, h, parent));
+    // The integrator lists of the components are built on the device, so the
+    // small components' first half (side stream) and the Kepler pairs start
+    // while the host waits for the split summary and lays out the large
+    // components; they touch disjoint particles.
     SmallParams SP;
     SP.G = c->p.G;
     SP.eps2 = c->p.eps * c->p.eps;
@@ -756,52 +734,79 @@ static int process(cc_ctx *c, int d, double h, const LevelAlloc *parent)
     SP.precision = c->p.precision;
     SP.depth0 = d + 1;
     SP.max_depth = c->p.max_depth;
-    if (ns && d + 1 > c->p.max_depth) return fail(c, CC_E_DEPTH, "recursion deeper than max_depth");
+    const int bound = a.L.total / 2 + 1;  // components of a split, at most
+    const bool small_on = c->p.s_small >= 2 && d + 1 <= c->p.max_depth;
+    launch_classify(a.comp_size, a.d_ncomp, c->p.s_small, c->p.kepler, a.kqueue, a.kqueue + 2, a.klist, a.slist, s);
+    if (small_on) {
+        if (!a.ev_ready) {
+            CC_CUDA(c, cudaEventCreateWithFlags(&a.ev_ready, cudaEventDisableTiming));
+            CC_CUDA(c, cudaEventCreateWithFlags(&a.ev_small, cudaEventDisableTiming));
+        }
+        CC_CUDA(c, cudaEventRecord(a.ev_ready, s));
+        CC_CUDA(c, cudaStreamWaitEvent(c->side, a.ev_ready, 0));
+        const int ev = ev_begin(c, 2, c->side);
+        launch_small(a.L, a.members, a.comp_start, a.comp_size, a.slist, a.kqueue + 3, bound, SP, c->d_ctr,
+                     a.kqueue + 0, c->d_near_ij, c->d_near_tau, c->near_cap, c->nsm, c->side);
+        ev_end(c, ev, c->side);
+        CC_CUDA(c, cudaEventRecord(a.ev_small, c->side));
+    }
+    if (c->p.kepler) launch_kepler(a.L, a.members, a.comp_start, a.klist, a.kqueue + 2, bound, c->p.G, 0.5 * h, c->d_ctr, s);
+    int ncomp = 0;
+    CC_TRY(split_finish(c, a, parent, ncomp));
+    // the host's part: counts, and the layout of the large components
+    std::vector<int32_t> &lstart = a.v_lstart, &lsize = a.v_lsize;
+    lstart.clear();
+    lsize.clear();
+    int nk = 0, ns = 0;
+    const int smax = std::min(c->p.s_small, 32);
+    for (int q = 0; q < ncomp; ++q) {
+        const int sz = a.h_size[q];
+        if (c->p.kepler && sz == 2) ++nk;
+        else if (sz <= smax) ++ns;
+        else {
+            lstart.push_back(a.h_start[q]);
+            lsize.push_back(sz);
+        }
+    }
+    const int nl = (int)lsize.size();
+    if (ns && !small_on) return fail(c, CC_E_DEPTH, "recursion deeper than max_depth");
     c->st.kepler_calls += 2ull * nk;
+    c->st.small_tasks += 2ull * ns;
     if (nl) {
         SetLayout &S = c->lv[d + 1].child_layout;
         make_layout(lsize, S);
-        std::memcpy(hl + 4 + 2 * lc, lstart.data(), nl * 4);
+        std::memcpy(a.h_lists, lstart.data(), nl * 4);
+        CC_CUDA(c, cudaMemcpyAsync(a.lcomp_start, a.h_lists, (size_t)nl * 4, cudaMemcpyHostToDevice, s));
         CC_TRY(upload_layout(c, c->lv[d + 1], S));
-    }
-    if (nk || ns || nl) {
-        const size_t words = nl ? (size_t)(4 + 2 * lc + nl) : ns ? (size_t)(4 + lc + ns) : (size_t)(4 + nk);
-        CC_CUDA(c, cudaMemcpyAsync(a.kqueue, hl, words * 4, cudaMemcpyHostToDevice, c->stream));
-    }
-    LevelAlloc &a2 = a;
-    if (ns && !a2.ev_ready) {
-        CC_CUDA(c, cudaEventCreateWithFlags(&a2.ev_ready, cudaEventDisableTiming));
-        CC_CUDA(c, cudaEventCreateWithFlags(&a2.ev_small, cudaEventDisableTiming));
     }
     for (int half = 0; half < 2; ++half) {
         if (half == 1) {
-            if (ns) CC_CUDA(c, cudaStreamWaitEvent(c->stream, a2.ev_small, 0));
-            CC_TRY(dkd(c, a2, h));
+            if (small_on) CC_CUDA(c, cudaStreamWaitEvent(s, a.ev_small, 0));
+            CC_TRY(dkd(c, a, h));
+            if (ns) {
+                // second half of the small components on the side stream,
+                // overlapping the large components' second half
+                CC_CUDA(c, cudaEventRecord(a.ev_ready, s));
+                CC_CUDA(c, cudaStreamWaitEvent(c->side, a.ev_ready, 0));
+                const int ev = ev_begin(c, 2, c->side);
+                launch_small(a.L, a.members, a.comp_start, a.comp_size, a.slist, a.kqueue + 3, ns, SP, c->d_ctr,
+                             a.kqueue + 1, c->d_near_ij, c->d_near_tau, c->near_cap, c->nsm, c->side);
+                ev_end(c, ev, c->side);
+                CC_CUDA(c, cudaEventRecord(a.ev_small, c->side));
+            }
+            if (nk) launch_kepler(a.L, a.members, a.comp_start, a.klist, a.kqueue + 2, nk, c->p.G, 0.5 * h, c->d_ctr, s);
         }
-        if (ns) {
-            // the small components run on the side stream, overlapping the
-            // Kepler pairs and the recursion of the large components (they
-            // touch disjoint particles); the DKD and the return join them
-            CC_CUDA(c, cudaEventRecord(a2.ev_ready, c->stream));
-            CC_CUDA(c, cudaStreamWaitEvent(c->side, a2.ev_ready, 0));
-            const int ev = ev_begin(c, 2, c->side);
-            launch_small(a2.L, a2.members, a2.comp_start, a2.comp_size, a2.slist, ns, SP, c->d_ctr,
-                         a2.kqueue + half, c->d_near_ij, c->d_near_tau, c->near_cap, c->nsm, c->side);
-            ev_end(c, ev, c->side);
-            CC_CUDA(c, cudaEventRecord(a2.ev_small, c->side));
-        }
-        if (nk) launch_kepler(a2.L, a2.members, a2.comp_start, a2.klist, nk, c->p.G, 0.5 * h, c->d_ctr, c->stream);
         if (nl) {
             LevelAlloc &ch = c->lv[d + 1];
-            launch_gather(a2.L, ch.L, a2.members, a2.lcomp_start, a2.inv, c->stream);
+            launch_gather(a.L, ch.L, a.members, a.lcomp_start, a.inv, s);
             // first half: the state this split saw, so its edge records
             // (when complete) give the child's split; second half: fresh
-            const bool reuse = half == 0 && a2.ecount <= a2.E.cap;
-            CC_TRY(process(c, d + 1, 0.5 * h, reuse ? &a2 : nullptr));
-            launch_scatter(a2.L, ch.L, c->stream);
+            const bool reuse = half == 0 && a.ecount <= a.E.cap;
+            CC_TRY(process(c, d + 1, 0.5 * h, reuse ? &a : nullptr));
+            launch_scatter(a.L, ch.L, s);
         }
     }
-    if (ns) CC_CUDA(c, cudaStreamWaitEvent(c->stream, a2.ev_small, 0));
+    if (small_on) CC_CUDA(c, cudaStreamWaitEvent(s, a.ev_small, 0));
     return CC_OK;
 }
 
@@ -1055,7 +1060,8 @@ int cc_components(cc_ctx *c, const int32_t *set, int64_t n_set, double h, int32_
     CC_TRY(stage_set(c, set, n_set, nullptr));
     CC_TRY(reset_call_counters(c));
     int nc = 0;
-    CC_TRY(split_level(c, c->unit, h, nc, nullptr));
+    CC_TRY(split_launch(c, c->unit, h, nullptr));
+    CC_TRY(split_finish(c, c->unit, nullptr, nc));
     if (labels_out) {
         int32_t *dl = (int32_t *)c->tmp + n_set;
         launch_label_canon(c->unit.L, c->unit.root, dl, (int)n_set, c->stream);

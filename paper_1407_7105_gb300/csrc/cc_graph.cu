@@ -441,6 +441,58 @@ void launch_compress_segment(const Level &L, int32_t *root, int32_t *members, in
     launch_segment(L, root, members, comp_start, comp_size, d_ncomp, scratch, s);
 }
 
+// ------------------------------------------------------------ classification
+// Sorts the components of a split for their integrators (one CTA, after the
+// segmentation): two-body components go to klist when Kepler mode is on,
+// components of at most s_small members to slist, largest first (a counting
+// sort by size; order within one size is immaterial: components are
+// independent), larger ones stay for the next level.  Writes counts[0] =
+// nk, counts[1] = ns and zeroes the two work-queue counters of the small
+// kernel (queue[0..1]), so the kernels that read them can be launched
+// before the host learns the sizes.
+constexpr int CLS_T = 1024;
+
+__global__ void __launch_bounds__(CLS_T) k_classify(const int32_t *comp_size, const int32_t *ncomp, int s_small,
+                                                    int kepler, int32_t *queue, int32_t *counts, int32_t *klist,
+                                                    int32_t *slist)
+{
+    __shared__ int s_cnt[34], s_pos[34], s_nk;
+    const int tid = threadIdx.x, nc = *ncomp;
+    if (tid < 34) s_cnt[tid] = 0;
+    if (tid == 0) s_nk = 0;
+    __syncthreads();
+    for (int q = tid; q < nc; q += CLS_T) {
+        const int sz = comp_size[q];
+        if (kepler && sz == 2) klist[atomicAdd(&s_nk, 1)] = q;
+        else if (sz <= s_small) atomicAdd(&s_cnt[sz], 1);
+    }
+    __syncthreads();
+    if (tid == 0) {
+        int pos = 0;
+        for (int z = s_small; z >= 0; --z) {
+            s_pos[z] = pos;
+            pos += s_cnt[z];
+        }
+        counts[0] = s_nk;
+        counts[1] = pos;
+        queue[0] = 0;
+        queue[1] = 0;
+    }
+    __syncthreads();
+    for (int q = tid; q < nc; q += CLS_T) {
+        const int sz = comp_size[q];
+        if (!(kepler && sz == 2) && sz <= s_small) slist[atomicAdd(&s_pos[sz], 1)] = q;
+    }
+}
+
+void launch_classify(const int32_t *comp_size, const int32_t *ncomp, int s_small, int kepler, int32_t *queue,
+                     int32_t *counts, int32_t *klist, int32_t *slist, cudaStream_t s)
+{
+    k_classify<<<1, CLS_T, 0, s>>>(comp_size, ncomp, s_small < 32 ? s_small : 32, kepler, queue, counts, klist,
+                                   slist);
+    CC_COUNT_LAUNCH(1);
+}
+
 // ------------------------------------------------------------ movement
 __global__ void k_fill_pad(Level L)
 {

@@ -312,6 +312,11 @@ void launch_compress_segment(const Level &L, int32_t *root, int32_t *members, in
 void launch_gather(const Level &P, const Level &C, const int32_t *members, const int32_t *lcomp_start, int32_t *inv,
                    cudaStream_t s);
 void launch_scatter(const Level &P, const Level &C, cudaStream_t s);
+// integrator lists of a split's components on the device (Kepler pairs,
+// small components largest first), their counts and the small kernel's
+// zeroed queue counters
+void launch_classify(const int32_t *comp_size, const int32_t *ncomp, int s_small, int kepler, int32_t *queue,
+                     int32_t *counts, int32_t *klist, int32_t *slist, cudaStream_t s);
 void launch_pack_state(const double *x3, const double *v3, const double *m, long long n, const Level &L,
                        const int32_t *sys_src_start, cudaStream_t s);
 void launch_unpack_state(double *x3, double *v3, long long n, const Level &L, cudaStream_t s);
@@ -349,11 +354,11 @@ void launch_kick_mixed(const Level &L, const FFView &F, const int32_t *order, co
 
 // cc_small.cu
 void launch_small(const Level &L, const int32_t *members, const int32_t *comp_start, const int32_t *comp_size,
-                  const int32_t *slist, int ns, const SmallParams &SP, DevCounters *ctr, int *queue,
-                  int32_t *near_ij, double *near_tau, long long near_cap, int nsm, cudaStream_t s);
+                  const int32_t *slist, const int32_t *ns_ptr, int ns_bound, const SmallParams &SP, DevCounters *ctr,
+                  int *queue, int32_t *near_ij, double *near_tau, long long near_cap, int nsm, cudaStream_t s);
 
 // cc_kepler.cu
 void launch_kepler(const Level &L, const int32_t *members, const int32_t *comp_start, const int32_t *klist,
-                   int nk, double G, double dt, DevCounters *ctr, cudaStream_t s);
+                   const int32_t *nk_ptr, int nk_bound, double G, double dt, DevCounters *ctr, cudaStream_t s);
 
 }  // namespace cc

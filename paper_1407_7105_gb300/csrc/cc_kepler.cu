@@ -7,11 +7,11 @@
 
 namespace cc {
 
-__global__ void k_kepler(Level L, const int32_t *members, const int32_t *comp_start, const int32_t *klist, int nk,
-                         double G, double dt, DevCounters *ctr)
+__global__ void k_kepler(Level L, const int32_t *members, const int32_t *comp_start, const int32_t *klist,
+                         const int32_t *nk_ptr, double G, double dt, DevCounters *ctr)
 {
     const int t = blockIdx.x * blockDim.x + threadIdx.x;
-    if (t >= nk) return;
+    if (t >= *nk_ptr) return;
     const int c = klist[t];
     const int a = members[comp_start[c]], b = members[comp_start[c] + 1];
     double xa[3] = {L.x[a], L.y[a], L.z[a]}, xb[3] = {L.x[b], L.y[b], L.z[b]};
@@ -27,10 +27,10 @@ __global__ void k_kepler(Level L, const int32_t *members, const int32_t *comp_st
 }
 
 void launch_kepler(const Level &L, const int32_t *members, const int32_t *comp_start, const int32_t *klist,
-                   int nk, double G, double dt, DevCounters *ctr, cudaStream_t s)
+                   const int32_t *nk_ptr, int nk_bound, double G, double dt, DevCounters *ctr, cudaStream_t s)
 {
-    if (nk > 0) {
-        k_kepler<<<(nk + 127) / 128, 128, 0, s>>>(L, members, comp_start, klist, nk, G, dt, ctr);
+    if (nk_bound > 0) {
+        k_kepler<<<(nk_bound + 127) / 128, 128, 0, s>>>(L, members, comp_start, klist, nk_ptr, G, dt, ctr);
         CC_COUNT_LAUNCH(1);
     }
 }

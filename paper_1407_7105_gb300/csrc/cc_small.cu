@@ -359,11 +359,13 @@ __device__ __forceinline__ unsigned k8_pair_handoff(K8Warp &S, int lane, double 
 }
 
 __global__ void __launch_bounds__(K8_WARPS * 32) k_small(Level L, const int32_t *members, const int32_t *comp_start,
-                                                          const int32_t *comp_size, const int32_t *slist, int ns,
+                                                          const int32_t *comp_size, const int32_t *slist,
+                                                          const int32_t *ns_ptr,
                                                           SmallParams SP, DevCounters *ctr, int *queue,
                                                           int32_t *near_ij, double *near_tau, long long near_cap)
 {
     __shared__ K8Warp sw[K8_WARPS];
+    const int ns = *ns_ptr;
     const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
     K8Warp &S = sw[w];
     const uint32_t me = 1u << lane;
@@ -694,14 +696,15 @@ __global__ void __launch_bounds__(K8_WARPS * 32) k_small(Level L, const int32_t 
 }
 
 void launch_small(const Level &L, const int32_t *members, const int32_t *comp_start, const int32_t *comp_size,
-                  const int32_t *slist, int ns, const SmallParams &SP, DevCounters *ctr, int *queue,
-                  int32_t *near_ij, double *near_tau, long long near_cap, int nsm, cudaStream_t s)
+                  const int32_t *slist, const int32_t *ns_ptr, int ns_bound, const SmallParams &SP, DevCounters *ctr,
+                  int *queue, int32_t *near_ij, double *near_tau, long long near_cap, int nsm, cudaStream_t s)
 {
-    if (ns <= 0) return;
-    // *queue is zero on entry (the caller uploads it with the component list)
-    const int want = (ns + K8_WARPS - 1) / K8_WARPS;
+    if (ns_bound <= 0) return;
+    // *queue is zero on entry and *ns_ptr the component count (k_classify);
+    // warps of blocks beyond the work exit at the first queue read
+    const int want = (ns_bound + K8_WARPS - 1) / K8_WARPS;
     const int grid = want < nsm * 8 ? want : nsm * 8;
-    k_small<<<grid, K8_WARPS * 32, 0, s>>>(L, members, comp_start, comp_size, slist, ns, SP, ctr, queue, near_ij,
+    k_small<<<grid, K8_WARPS * 32, 0, s>>>(L, members, comp_start, comp_size, slist, ns_ptr, SP, ctr, queue, near_ij,
                                            near_tau, near_cap);
     CC_COUNT_LAUNCH(1);
 }
