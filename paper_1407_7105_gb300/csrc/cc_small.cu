@@ -77,8 +77,52 @@ __device__ __forceinline__ void k8_drift(double st[7], double dt, bool exact)
 // predicate compares one tau with each threshold, and the FP32 decision at
 // h 2^-m is tau_decide_at(prep, (eta/h) 2^m) exactly.
 
+// Out-of-line copies of the FP64 work a mixed-form component rarely needs
+// (undecided tau, Kepler pairs, FP64 kicks): kept out of the lockstep loop
+// so that its hot code stays compact in the instruction cache (a warp of
+// this kernel mostly runs alone on its scheduler and waits on fetches).
+__device__ __noinline__ double tau_fp64_ool(double dx0, double dx1, double dx2, double dv0, double dv1, double dv2,
+                                            double mi, double mj, const TauParams &P)
+{
+    return tau_fp64(dx0, dx1, dx2, dv0, dv1, dv2, mi, mj, P);
+}
+
+struct K8Acc {
+    double x, y, z;
+};
+
+// the FP64 row sum of one lane (the level kernels' arithmetic): a_i =
+// sum over j in `others`, ascending, of (G m_j) r^-3 (x_j - x_i)
+__device__ __noinline__ K8Acc k8_kick64(const K8Warp &S, int n, uint32_t others, double xi, double yi, double zi,
+                                        double G, double eps2)
+{
+    double ax = 0.0, ay = 0.0, az = 0.0;
+    for (int j = 0; j < n; ++j) {
+        if (!((others >> j) & 1u)) continue;
+        const double dx0 = __dsub_rn(S.d[0][j], xi);
+        const double dx1 = __dsub_rn(S.d[1][j], yi);
+        const double dx2 = __dsub_rn(S.d[2][j], zi);
+        const double r2 = __dadd_rn(__dadd_rn(__dadd_rn(__dmul_rn(dx0, dx0), __dmul_rn(dx1, dx1)),
+                                              __dmul_rn(dx2, dx2)), eps2);
+        const double rinv3 = __ddiv_rn(1.0, __dmul_rn(r2, __dsqrt_rn(r2)));
+        const double ww = __dmul_rn(__dmul_rn(G, S.d[6][j]), rinv3);
+        ax = __dadd_rn(ax, __dmul_rn(ww, dx0));
+        ay = __dadd_rn(ay, __dmul_rn(ww, dx1));
+        az = __dadd_rn(az, __dmul_rn(ww, dx2));
+    }
+    return K8Acc{ax, ay, az};
+}
+
+// the Kepler flow of a two-body component over dt (positions and
+// velocities of both bodies in place)
+__device__ __noinline__ bool k8_kepler(double ma, double mb, double *xa, double *xb, double *va, double *vb, double G,
+                                       double dt)
+{
+    return kepler_pair(ma, mb, xa, xb, va, vb, G, dt);
+}
+
 // log (i, j, tau) when |tau - h| < near_tol h (FP64-decided pairs only)
-__device__ __forceinline__ void near_log(double tau, double h, double near_tol, DevCounters *ctr, int ga, int gb,
+__device__ __noinline__ void near_log(double tau, double h, double near_tol, DevCounters *ctr, int ga, int gb,
                                          int32_t *near_ij, double *near_tau, long long near_cap)
 {
     if (fabs(tau - h) < near_tol * h) {
@@ -178,7 +222,7 @@ __device__ unsigned pair_path(double A[7], double B[7], double h0, int depth0, i
     int d = 0, e = e0;
     for (long long work = 0; work < PAIR_VISIT_LIMIT;) {
         if (e < 0) {
-            const double tau = tau_fp64(__dsub_rn(A[0], B[0]), __dsub_rn(A[1], B[1]), __dsub_rn(A[2], B[2]),
+            const double tau = tau_fp64_ool(__dsub_rn(A[0], B[0]), __dsub_rn(A[1], B[1]), __dsub_rn(A[2], B[2]),
                                         __dsub_rn(A[3], B[3]), __dsub_rn(A[4], B[4]), __dsub_rn(A[5], B[5]), A[6],
                                         B[6], P);
             ++pc.fp64;
@@ -262,7 +306,7 @@ __device__ unsigned pair_path_rel(double A[7], double B[7], double h0, int depth
             bool used64;
             e = edge_depth_mixed(
                 t, etah0 * pow2f(d), scale2m(h0, d), max(dmax - d + 1, 1),
-                [&]() { return tau_fp64(r[0], r[1], r[2], u[0], u[1], u[2], ma, mb, P); },
+                [&]() { return tau_fp64_ool(r[0], r[1], r[2], u[0], u[1], u[2], ma, mb, P); },
                 [&](double tv, double hm) { near_log(tv, hm, nl.tol, nl.ctr, ga, gb, nl.ij, nl.tau, nl.cap); },
                 used64);
             pc.fp64 += used64 ? 1 : 0;
@@ -437,7 +481,7 @@ __global__ void __launch_bounds__(K8_WARPS * 32) k_small(Level L, const int32_t 
                     // (symmetric bit for bit)
                     auto tau64_of = [&](int j) {
                         const int lo = lane < j ? lane : j, hi = lane < j ? j : lane;
-                        return tau_fp64(__dsub_rn(S.d[0][lo], S.d[0][hi]), __dsub_rn(S.d[1][lo], S.d[1][hi]),
+                        return tau_fp64_ool(__dsub_rn(S.d[0][lo], S.d[0][hi]), __dsub_rn(S.d[1][lo], S.d[1][hi]),
                                         __dsub_rn(S.d[2][lo], S.d[2][hi]), __dsub_rn(S.d[3][lo], S.d[3][hi]),
                                         __dsub_rn(S.d[4][lo], S.d[4][hi]), __dsub_rn(S.d[5][lo], S.d[5][hi]),
                                         S.d[6][lo], S.d[6][hi], P);
@@ -446,15 +490,22 @@ __global__ void __launch_bounds__(K8_WARPS * 32) k_small(Level L, const int32_t 
                         if (lane < j) near_log(tv, hm, nl.tol, nl.ctr, S.gid[lane], S.gid[j], nl.ij, nl.tau, nl.cap);
                     };
                     if (mine && mixed) {
+                        // the lane's own float-float state in registers (the
+                        // byte stores of the edge depths below may alias any
+                        // shared word, so reads from S would be repeated)
+                        float me_f[13];
+#pragma unroll
+                        for (int q = 0; q < 13; ++q) me_f[q] = S.f[q][lane];
+                        const float me_xm = S.xm[lane], me_vm = S.vm[lane];
                         auto prep = [&](int j) {
-                            return tau_prep_fp32((S.f[0][j] - S.f[0][lane]) + (S.f[6][j] - S.f[6][lane]),
-                                                 (S.f[1][j] - S.f[1][lane]) + (S.f[7][j] - S.f[7][lane]),
-                                                 (S.f[2][j] - S.f[2][lane]) + (S.f[8][j] - S.f[8][lane]),
-                                                 (S.f[3][j] - S.f[3][lane]) + (S.f[9][j] - S.f[9][lane]),
-                                                 (S.f[4][j] - S.f[4][lane]) + (S.f[10][j] - S.f[10][lane]),
-                                                 (S.f[5][j] - S.f[5][lane]) + (S.f[11][j] - S.f[11][lane]),
-                                                 Q.G * (S.f[12][lane] + S.f[12][j]), c11 * fmaxf(S.xm[lane], S.xm[j]),
-                                                 c11 * fmaxf(S.vm[lane], S.vm[j]), Q);
+                            return tau_prep_fp32((S.f[0][j] - me_f[0]) + (S.f[6][j] - me_f[6]),
+                                                 (S.f[1][j] - me_f[1]) + (S.f[7][j] - me_f[7]),
+                                                 (S.f[2][j] - me_f[2]) + (S.f[8][j] - me_f[8]),
+                                                 (S.f[3][j] - me_f[3]) + (S.f[9][j] - me_f[9]),
+                                                 (S.f[4][j] - me_f[4]) + (S.f[10][j] - me_f[10]),
+                                                 (S.f[5][j] - me_f[5]) + (S.f[11][j] - me_f[11]),
+                                                 Q.G * (me_f[12] + S.f[12][j]), c11 * fmaxf(me_xm, S.xm[j]),
+                                                 c11 * fmaxf(me_vm, S.vm[j]), Q);
                         };
                         auto finish = [&](int j, const TauPrep32 &t) {
                             if (j == lane || !((mine >> j) & 1u)) return;
@@ -469,9 +520,8 @@ __global__ void __launch_bounds__(K8_WARPS * 32) k_small(Level L, const int32_t 
                             S.e[j][lane] = (unsigned char)e;
                             if (lane < j) ++c_eval;
                         };
-                        // two preps in flight: a lone warp's latency, not its
-                        // issue rate, bounds this loop (excluded j are computed
-                        // and dropped)
+                        // two preps in flight (excluded j are computed and
+                        // dropped)
                         for (int j = 0; j < n; j += 2) {
                             const int j1 = j + 1 < n ? j + 1 : j;
                             const TauPrep32 t0 = prep(j), t1 = prep(j1);
@@ -576,25 +626,10 @@ __global__ void __launch_bounds__(K8_WARPS * 32) k_small(Level L, const int32_t 
                             const uint32_t others = mine & ~cm;
                             c_kick += __popc(others & ~((me << 1) - 1u));
                             if (fp64_kick) {
-                                double ax = 0.0, ay = 0.0, az = 0.0;
-                                for (int j = 0; j < n; ++j) {
-                                    if (!((others >> j) & 1u)) continue;
-                                    const double dx0 = __dsub_rn(S.d[0][j], st[0]);
-                                    const double dx1 = __dsub_rn(S.d[1][j], st[1]);
-                                    const double dx2 = __dsub_rn(S.d[2][j], st[2]);
-                                    const double r2 = __dadd_rn(__dadd_rn(__dadd_rn(__dmul_rn(dx0, dx0),
-                                                                                    __dmul_rn(dx1, dx1)),
-                                                                          __dmul_rn(dx2, dx2)),
-                                                                SP.eps2);
-                                    const double rinv3 = __ddiv_rn(1.0, __dmul_rn(r2, __dsqrt_rn(r2)));
-                                    const double ww = __dmul_rn(__dmul_rn(SP.G, S.d[6][j]), rinv3);
-                                    ax = __dadd_rn(ax, __dmul_rn(ww, dx0));
-                                    ay = __dadd_rn(ay, __dmul_rn(ww, dx1));
-                                    az = __dadd_rn(az, __dmul_rn(ww, dx2));
-                                }
-                                st[3] = __dadd_rn(st[3], __dmul_rn(h, ax));
-                                st[4] = __dadd_rn(st[4], __dmul_rn(h, ay));
-                                st[5] = __dadd_rn(st[5], __dmul_rn(h, az));
+                                const K8Acc a = k8_kick64(S, n, others, st[0], st[1], st[2], SP.G, SP.eps2);
+                                st[3] = __dadd_rn(st[3], __dmul_rn(h, a.x));
+                                st[4] = __dadd_rn(st[4], __dmul_rn(h, a.y));
+                                st[5] = __dadd_rn(st[5], __dmul_rn(h, a.z));
                             } else {
                                 // FP32 pair forces from float-float differences
                                 const float xh = S.f[0][lane], yh = S.f[1][lane], zh = S.f[2][lane];
@@ -638,7 +673,7 @@ __global__ void __launch_bounds__(K8_WARPS * 32) k_small(Level L, const int32_t 
                         const int a = lane < other ? lane : other, b = lane < other ? other : lane;
                         double xa[3] = {S.d[0][a], S.d[1][a], S.d[2][a]}, xb[3] = {S.d[0][b], S.d[1][b], S.d[2][b]};
                         double va[3] = {S.d[3][a], S.d[4][a], S.d[5][a]}, vb[3] = {S.d[3][b], S.d[4][b], S.d[5][b]};
-                        if (!kepler_pair(S.d[6][a], S.d[6][b], xa, xb, va, vb, SP.G, 0.5 * h)) {
+                        if (!k8_kepler(S.d[6][a], S.d[6][b], xa, xb, va, vb, SP.G, 0.5 * h)) {
                             raise_err(ctr, DERR_KEPLER);
                         } else if (lane == a) {
                             st[0] = xa[0]; st[1] = xa[1]; st[2] = xa[2]; st[3] = va[0]; st[4] = va[1]; st[5] = va[2];
