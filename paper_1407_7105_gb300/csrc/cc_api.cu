@@ -138,7 +138,11 @@ struct cc_ctx {
     void *tmp = nullptr;  // staging for caller buffers
     size_t tmp_sz = 0;
     unsigned *d_bad = nullptr;
-    cudaStream_t side = nullptr;  // small-component kernels overlap the level recursion
+    // small-component kernels overlap the level recursion, one stream per
+    // depth (a level's launch must not queue behind its parent level's:
+    // they touch disjoint particles), highest priority, created on first use
+    std::vector<cudaStream_t> sides;
+    int prio_high = 0;
     int nsm = 152;
     double *d_kpart = nullptr;  // mixed-kick chunk partials
     size_t kpart_sz = 0;
@@ -708,6 +712,14 @@ static int dkd(cc_ctx *c, LevelAlloc &a, double h)
     return CC_OK;
 }
 
+static int side_stream(cc_ctx *c, int d, cudaStream_t *out)
+{
+    cudaStream_t &st = c->sides[d];
+    if (!st) CC_CUDA(c, cudaStreamCreateWithPriority(&st, cudaStreamNonBlocking, c->prio_high));
+    *out = st;
+    return CC_OK;
+}
+
 static int process(cc_ctx *c, int d, double h, const LevelAlloc *parent)
 {
     if (d > c->p.max_depth) return fail(c, CC_E_DEPTH, "recursion deeper than max_depth");
@@ -736,6 +748,8 @@ static int process(cc_ctx *c, int d, double h, const LevelAlloc *parent)
     SP.max_depth = c->p.max_depth;
     const int bound = a.L.total / 2 + 1;  // components of a split, at most
     const bool small_on = c->p.s_small >= 2 && d + 1 <= c->p.max_depth;
+    cudaStream_t side = nullptr;
+    if (small_on) CC_TRY(side_stream(c, d, &side));
     launch_classify(a.comp_size, a.d_ncomp, c->p.s_small, c->p.kepler, a.kqueue, a.kqueue + 2, a.klist, a.slist, s);
     if (small_on) {
         if (!a.ev_ready) {
@@ -743,12 +757,12 @@ static int process(cc_ctx *c, int d, double h, const LevelAlloc *parent)
             CC_CUDA(c, cudaEventCreateWithFlags(&a.ev_small, cudaEventDisableTiming));
         }
         CC_CUDA(c, cudaEventRecord(a.ev_ready, s));
-        CC_CUDA(c, cudaStreamWaitEvent(c->side, a.ev_ready, 0));
-        const int ev = ev_begin(c, 2, c->side);
+        CC_CUDA(c, cudaStreamWaitEvent(side, a.ev_ready, 0));
+        const int ev = ev_begin(c, 2, side);
         launch_small(a.L, a.members, a.comp_start, a.comp_size, a.slist, a.kqueue + 3, bound, SP, c->d_ctr,
-                     a.kqueue + 0, c->d_near_ij, c->d_near_tau, c->near_cap, c->nsm, c->side);
-        ev_end(c, ev, c->side);
-        CC_CUDA(c, cudaEventRecord(a.ev_small, c->side));
+                     a.kqueue + 0, c->d_near_ij, c->d_near_tau, c->near_cap, c->nsm, side);
+        ev_end(c, ev, side);
+        CC_CUDA(c, cudaEventRecord(a.ev_small, side));
     }
     if (c->p.kepler) launch_kepler(a.L, a.members, a.comp_start, a.klist, a.kqueue + 2, bound, c->p.G, 0.5 * h, c->d_ctr, s);
     int ncomp = 0;
@@ -787,12 +801,12 @@ static int process(cc_ctx *c, int d, double h, const LevelAlloc *parent)
                 // second half of the small components on the side stream,
                 // overlapping the large components' second half
                 CC_CUDA(c, cudaEventRecord(a.ev_ready, s));
-                CC_CUDA(c, cudaStreamWaitEvent(c->side, a.ev_ready, 0));
-                const int ev = ev_begin(c, 2, c->side);
+                CC_CUDA(c, cudaStreamWaitEvent(side, a.ev_ready, 0));
+                const int ev = ev_begin(c, 2, side);
                 launch_small(a.L, a.members, a.comp_start, a.comp_size, a.slist, a.kqueue + 3, ns, SP, c->d_ctr,
-                             a.kqueue + 1, c->d_near_ij, c->d_near_tau, c->near_cap, c->nsm, c->side);
-                ev_end(c, ev, c->side);
-                CC_CUDA(c, cudaEventRecord(a.ev_small, c->side));
+                             a.kqueue + 1, c->d_near_ij, c->d_near_tau, c->near_cap, c->nsm, side);
+                ev_end(c, ev, side);
+                CC_CUDA(c, cudaEventRecord(a.ev_small, side));
             }
             if (nk) launch_kepler(a.L, a.members, a.comp_start, a.klist, a.kqueue + 2, nk, c->p.G, 0.5 * h, c->d_ctr, s);
         }
@@ -919,16 +933,13 @@ int cc_init(cc_ctx **out, int64_t n, const double *m, const double *x3, const do
     }
     cudaMemsetAsync(c->d_ctr, 0, sizeof(DevCounters), c->stream);
     {
-        // the side stream of the small-component kernel gets the highest
+        // the side streams of the small-component kernel get the highest
         // priority: its few long-running blocks take SM slots as soon as the
         // pair kernels' short blocks retire, instead of queueing behind them
         int least = 0, greatest = 0;
         cudaDeviceGetStreamPriorityRange(&least, &greatest);
-        if (cudaStreamCreateWithPriority(&c->side, cudaStreamNonBlocking, greatest) != cudaSuccess) {
-            cudaGetLastError();
-            c->err = "cc_init: stream creation failed";
-            return bail(CC_E_CUDA);
-        }
+        c->prio_high = greatest;
+        c->sides.assign((size_t)p->max_depth + 2, nullptr);
     }
     {
         int dev = 0;
@@ -1244,10 +1255,11 @@ int cc_destroy(cc_ctx *c)
 {
     if (!c) return CC_OK;
     if (c->stream) cudaStreamSynchronize(c->stream);
-    if (c->side) {
-        cudaStreamSynchronize(c->side);
-        cudaStreamDestroy(c->side);
-    }
+    for (cudaStream_t st : c->sides)
+        if (st) {
+            cudaStreamSynchronize(st);
+            cudaStreamDestroy(st);
+        }
     for (cudaEvent_t e : c->evs) cudaEventDestroy(e);
     for (auto &a : c->lv) free_level(a);
     free_level(c->unit);
