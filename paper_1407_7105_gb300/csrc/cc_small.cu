@@ -489,6 +489,10 @@ __global__ void __launch_bounds__(K8_WARPS * 32) k_small(Level L, const int32_t 
                     auto log_of = [&](int j, double tv, double hm) {
                         if (lane < j) near_log(tv, hm, nl.tol, nl.ctr, S.gid[lane], S.gid[j], nl.ij, nl.tau, nl.cap);
                     };
+                    // the warp's active lanes at this level: a lane's set is a
+                    // subset, so its pairs are among these (deep levels of a
+                    // big component leave few)
+                    const uint32_t act = __reduce_or_sync(FULL, mine);
                     if (mine && mixed) {
                         // the lane's own float-float state in registers (the
                         // byte stores of the edge depths below may alias any
@@ -520,13 +524,17 @@ __global__ void __launch_bounds__(K8_WARPS * 32) k_small(Level L, const int32_t 
                             S.e[j][lane] = (unsigned char)e;
                             if (lane < j) ++c_eval;
                         };
-                        // two preps in flight (excluded j are computed and
-                        // dropped)
-                        for (int j = 0; j < n; j += 2) {
-                            const int j1 = j + 1 < n ? j + 1 : j;
-                            const TauPrep32 t0 = prep(j), t1 = prep(j1);
-                            finish(j, t0);
-                            if (j + 1 < n) finish(j + 1, t1);
+                        // two preps in flight, over the active lanes (pairs
+                        // outside the lane's set are computed and dropped)
+                        for (uint32_t rem = act; rem;) {
+                            const int j0 = __ffs(rem) - 1;
+                            rem &= rem - 1u;
+                            const bool two = rem != 0u;
+                            const int j1 = two ? __ffs(rem) - 1 : j0;
+                            if (two) rem &= rem - 1u;
+                            const TauPrep32 t0 = prep(j0), t1 = prep(j1);
+                            finish(j0, t0);
+                            if (two) finish(j1, t1);
                         }
                     } else if (mine) {
                         for (int j = 0; j < n; ++j) {
@@ -622,6 +630,7 @@ __global__ void __launch_bounds__(K8_WARPS * 32) k_small(Level L, const int32_t 
                         }
                         const bool fp64_kick = !mixed || h < SP.h_fp64;
                         k8_publish(S, lane, st, !fp64_kick);
+                        const uint32_t act = __reduce_or_sync(FULL, mine);
                         if (mine) {
                             const uint32_t others = mine & ~cm;
                             c_kick += __popc(others & ~((me << 1) - 1u));
@@ -634,9 +643,10 @@ __global__ void __launch_bounds__(K8_WARPS * 32) k_small(Level L, const int32_t 
                                 // FP32 pair forces from float-float differences
                                 const float xh = S.f[0][lane], yh = S.f[1][lane], zh = S.f[2][lane];
                                 const float xl = S.f[6][lane], yl = S.f[7][lane], zl = S.f[8][lane];
-                                // two compensated accumulators (even and odd j): two
-                                // independent dependency chains for one warp that runs
-                                // alone on its scheduler; excluded j contribute an exact 0
+                                // two compensated accumulators: two independent
+                                // dependency chains for one warp that runs alone on
+                                // its scheduler; j outside the lane's others add an
+                                // exact 0
                                 float sx0 = 0.f, sy0 = 0.f, sz0 = 0.f, cx0 = 0.f, cy0 = 0.f, cz0 = 0.f;
                                 float sx1 = 0.f, sy1 = 0.f, sz1 = 0.f, cx1 = 0.f, cy1 = 0.f, cz1 = 0.f;
                                 const float e2 = (float)SP.eps2;
@@ -653,9 +663,15 @@ __global__ void __launch_bounds__(K8_WARPS * 32) k_small(Level L, const int32_t 
                                     kahan_add(sy, cy, ww * dy);
                                     kahan_add(sz, cz, ww * dz);
                                 };
-                                for (int j = 0; j < n; j += 2) {
-                                    term(j, sx0, sy0, sz0, cx0, cy0, cz0);
-                                    if (j + 1 < n) term(j + 1, sx1, sy1, sz1, cx1, cy1, cz1);
+                                // over the warp's active lanes, two terms per round
+                                for (uint32_t rem = act; rem;) {
+                                    const int j0 = __ffs(rem) - 1;
+                                    rem &= rem - 1u;
+                                    term(j0, sx0, sy0, sz0, cx0, cy0, cz0);
+                                    if (rem) {
+                                        term(__ffs(rem) - 1, sx1, sy1, sz1, cx1, cy1, cz1);
+                                        rem &= rem - 1u;
+                                    }
                                 }
                                 const double gh = SP.G * h;
                                 st[3] = fma(gh, (f2d(sx0) - f2d(cx0)) + (f2d(sx1) - f2d(cx1)), st[3]);
