@@ -309,30 +309,47 @@ void launch_segment(const Level &L, const int32_t *root, int32_t *members, int32
     CC_COUNT_LAUNCH(1);
 }
 
-// ------------------------------------------------------------ fused small path
+// ------------------------------------------------------------ one-CTA path
 // For a batch of at most SEG1_MAX packed elements one CTA does what the
 // general path spreads over ~15 launches: union-find compression, sizes,
-// component heads and offsets (block scans), and the ordered scatter of
-// members: an unordered scatter by shared-memory cursors, then every
-// component's run sorted by index (one warp per run, ranks by counting),
-// which is the stable order since the input is in index order.  A run of
-// more than 64 members sends the block to a stable single-warp scatter (one
-// warp walks the indices in order; lanes with the same root are ranked by
-// warp match).
+// run starts and component offsets (block scans over contiguous chunks),
+// and the ordered scatter of members.  Order within a run must be index
+// order (the input order): runs of at most SEG1_RUN members are scattered
+// by shared-memory cursors and then sorted by index, one warp per run (ranks
+// by counting); each larger run (up to SEG1_BIG of them; the giant
+// component of a dense cluster is one) is written by a stable compaction,
+// a block scan of "key == its root" over the batch.  More large runs than
+// that send the block to a stable single-warp scatter (one warp walks the
+// indices in order; lanes with the same root are ranked by warp match).
+// Shared memory: 8 bytes per element (dynamic).
 constexpr int SEG1_T = 1024;
-constexpr int SEG1_MAX = 4096;
+constexpr int SEG1_MAX = 16384;
 constexpr int SEG1_RUN = 64;
+constexpr int SEG1_BIG = 8;
+
+// exclusive block scan of the per-thread value v; *total = the sum
+__device__ __forceinline__ int seg1_scan(int v, int *tmp, int *total)
+{
+    int t;
+    const int e = block_exclusive_scan(v, tmp, t);
+    *total = t;
+    return e;
+}
 
 __global__ void __launch_bounds__(SEG1_T) k_segment_small(Level L, int32_t *root_out, int32_t *members,
                                                           int32_t *comp_start, int32_t *comp_size, int32_t *ncomp)
 {
-    __shared__ int s_root[SEG1_MAX];  // roots, then the member list being built
-    __shared__ int s_cnt[SEG1_MAX];   // size by root, then run start / cursor by key
-    __shared__ int tmp[32];
-    __shared__ int s_big;
+    extern __shared__ int seg1_smem[];
     const int n = L.total, tid = threadIdx.x;
+    int *s_root = seg1_smem;      // roots, then the member list being built
+    int *s_cnt = seg1_smem + n;   // size by root, then run start / cursor by key
+    __shared__ int tmp[32];
+    __shared__ int s_nbig, s_big_root[SEG1_BIG], s_big_start[SEG1_BIG], s_big_size[SEG1_BIG];
+    // each thread owns the contiguous chunk [c0, c1) of the batch (scans)
+    const int per = (n + SEG1_T - 1) / SEG1_T;
+    const int c0 = min(n, tid * per), c1 = min(n, c0 + per);
     for (int k = tid; k < n; k += SEG1_T) s_cnt[k] = 0;
-    if (tid == 0) s_big = 0;
+    if (tid == 0) s_nbig = 0;
     __syncthreads();
     for (int k = tid; k < n; k += SEG1_T) {
         const bool valid = L.gid[k] >= 0;
@@ -343,54 +360,79 @@ __global__ void __launch_bounds__(SEG1_T) k_segment_small(Level L, int32_t *root
     }
     __syncthreads();
     for (int k = tid; k < n; k += SEG1_T) L.cnt[k] = s_cnt[k];
-    // runs in key order: key = root for valid elements, own index for
-    // padding; w[k] = number of elements keyed k.  Run starts by a block scan
-    // (4 items per thread), component index by a second scan over heads.
-    int wv[4], hc[4], key[4];
+    // run of key k: w = elements keyed k (key = root for valid elements, own
+    // index for padding); a component head has w >= 2
+    auto weight = [&](int k) {
+        return L.gid[k] < 0 ? 1 : (s_root[k] == k ? s_cnt[k] : 0);
+    };
     int sw = 0, sc = 0;
-#pragma unroll
-    for (int q = 0; q < 4; ++q) {
-        const int k = 4 * tid + q;
-        const bool valid_root = k < n && L.gid[k] >= 0 && s_root[k] == k;
-        const bool pad = k < n && L.gid[k] < 0;
-        wv[q] = valid_root ? s_cnt[k] : (pad ? 1 : 0);
-        hc[q] = valid_root && s_cnt[k] >= 2 ? 1 : 0;
-        sw += wv[q];
-        sc += hc[q];
-        const int e = tid + q * SEG1_T;  // the element this thread scatters below
-        key[q] = e < n ? (L.gid[e] >= 0 ? s_root[e] : e) : -1;
+    for (int k = c0; k < c1; ++k) {
+        const int w = weight(k);
+        sw += w;
+        sc += (L.gid[k] >= 0 && w >= 2) ? 1 : 0;
     }
     __syncthreads();
     int tot_w, tot_c;
-    int ew = block_exclusive_scan(sw, tmp, tot_w);
-    int ec = block_exclusive_scan(sc, tmp, tot_c);
+    int ew = seg1_scan(sw, tmp, &tot_w);
+    int ec = seg1_scan(sc, tmp, &tot_c);
     __syncthreads();
-#pragma unroll
-    for (int q = 0; q < 4; ++q) {
-        const int k = 4 * tid + q;
-        if (hc[q]) {
+    // (weights are read before the cursors overwrite s_cnt: one chunk per
+    // thread, and a key's cursor lives at the key's own index)
+    for (int k = c0; k < c1; ++k) {
+        const int w = weight(k);
+        if (L.gid[k] >= 0 && w >= 2) {
             comp_start[ec] = ew;
-            comp_size[ec] = wv[q];
-            if (wv[q] > SEG1_RUN) s_big = 1;
+            comp_size[ec] = w;
+            if (w > SEG1_RUN) {
+                const int b = atomicAdd(&s_nbig, 1);
+                if (b < SEG1_BIG) {
+                    s_big_root[b] = k;
+                    s_big_start[b] = ew;
+                    s_big_size[b] = w;
+                }
+            }
+            ++ec;
         }
-        if (k < n) s_cnt[k] = ew;  // run start of key k (cursor)
-        ec += hc[q];
-        ew += wv[q];
+        s_cnt[k] = ew;  // run start of key k (cursor)
+        ew += w;
     }
     if (tid == 0) *ncomp = tot_c;
     __syncthreads();
-    if (!s_big) {
-        // unordered scatter (s_root now holds the member list), then each
-        // component run sorted by index, one warp per run
+    const int nbig = s_nbig;
+    if (nbig <= SEG1_BIG) {
+        // keys of the thread's strided elements, read before s_root turns
+        // into the member list
+        auto key_of = [&](int k) { return L.gid[k] >= 0 ? s_root[k] : k; };
+        auto is_big = [&](int key) { return L.gid[key] >= 0 && s_root[key] == key && L.cnt[key] > SEG1_RUN; };
+        // large runs first: stable compaction per run (reads s_root only)
+        for (int b = 0; b < nbig; ++b) {
+            const int rb = s_big_root[b];
+            int cnt = 0;
+            for (int k = c0; k < c1; ++k) cnt += (L.gid[k] >= 0 && s_root[k] == rb) ? 1 : 0;
+            int tot;
+            int pos = s_big_start[b] + seg1_scan(cnt, tmp, &tot);
+            for (int k = c0; k < c1; ++k)
+                if (L.gid[k] >= 0 && s_root[k] == rb) members[pos++] = k;
+            __syncthreads();
+        }
+        // small runs: unordered scatter into shared memory
+        int kk[SEG1_MAX / SEG1_T];
 #pragma unroll
-        for (int q = 0; q < 4; ++q) {
-            const int e = tid + q * SEG1_T;
-            if (e < n) s_root[atomicAdd(&s_cnt[key[q]], 1)] = e;
+        for (int q = 0; q < SEG1_MAX / SEG1_T; ++q) {
+            const int k = tid + q * SEG1_T;
+            kk[q] = (k < n && !is_big(key_of(k))) ? key_of(k) : -1;
+        }
+        __syncthreads();
+#pragma unroll
+        for (int q = 0; q < SEG1_MAX / SEG1_T; ++q) {
+            const int k = tid + q * SEG1_T;
+            if (kk[q] >= 0) s_root[atomicAdd(&s_cnt[kk[q]], 1)] = k;
         }
         __syncthreads();
         const int w = tid >> 5, lane = tid & 31;
         for (int c = w; c < tot_c; c += SEG1_T / 32) {
             const int st = comp_start[c], sz = comp_size[c];
+            if (sz > SEG1_RUN) continue;
             const int x0 = lane < sz ? s_root[st + lane] : 0x7fffffff;
             const int x1 = lane + 32 < sz ? s_root[st + lane + 32] : 0x7fffffff;
             int r0 = 0, r1 = 0;
@@ -405,7 +447,12 @@ __global__ void __launch_bounds__(SEG1_T) k_segment_small(Level L, int32_t *root
             __syncwarp();
         }
         __syncthreads();
-        for (int k = tid; k < n; k += SEG1_T) members[k] = s_root[k];
+        // copy out everything but the large runs (already in place)
+        for (int k = tid; k < n; k += SEG1_T) {
+            bool in_big = false;
+            for (int b = 0; b < nbig; ++b) in_big |= (k >= s_big_start[b] && k < s_big_start[b] + s_big_size[b]);
+            if (!in_big) members[k] = s_root[k];
+        }
         return;
     }
     if (tid < 32) {
@@ -433,7 +480,15 @@ void launch_compress_segment(const Level &L, int32_t *root, int32_t *members, in
                              int32_t *comp_size, int32_t *d_ncomp, void *scratch, cudaStream_t s)
 {
     if (L.total > 0 && L.total <= SEG1_MAX) {
-        k_segment_small<<<1, SEG1_T, 0, s>>>(L, root, members, comp_start, comp_size, d_ncomp);
+        // opt in to the dynamic shared memory once per device
+        static bool attr_set[64] = {};
+        int dev = 0;
+        cudaGetDevice(&dev);
+        if (dev >= 0 && dev < 64 && !attr_set[dev]) {
+            cudaFuncSetAttribute(k_segment_small, cudaFuncAttributeMaxDynamicSharedMemorySize, SEG1_MAX * 8);
+            attr_set[dev] = true;
+        }
+        k_segment_small<<<1, SEG1_T, (size_t)L.total * 8, s>>>(L, root, members, comp_start, comp_size, d_ncomp);
         CC_COUNT_LAUNCH(1);
         return;
     }

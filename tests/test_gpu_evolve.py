@@ -220,3 +220,28 @@ def test_first_half_splits_from_parent_records(cclib, plummer_ic, s_small):
     assert st.max_depth_seen >= 3
     assert 0 < g["tau_evaluated"] < g["tau_pairs"]
     c.close()
+
+
+@pytest.mark.parametrize("nsys", [5, 12])
+def test_batches_of_large_components(cclib, nsys):
+    """A batch whose sets are each one large component (100 bodies at a long
+    step): the one-CTA segmentation writes runs of more than 64 members by
+    a stable compaction when there are at most 8 of them and falls back to a
+    serial stable scatter beyond that; both must give the oracle's state."""
+    parts = [ics.plummer(100, seed=40 + k) for k in range(nsys)]
+    m = np.concatenate([p[0] for p in parts])
+    x = np.ascontiguousarray(np.concatenate([p[1] for p in parts], axis=1))
+    v = np.ascontiguousarray(np.concatenate([p[2] for p in parts], axis=1))
+    off = np.arange(nsys + 1, dtype=np.int64) * 100
+    dt = 1 / 4
+    c = cclib.Context(m, x, v, dt=dt)
+    c.set_systems(off)
+    c.evolve(dt)
+    _, _, gx, gv = c.get_state()
+    s = O.State(m, x, v)
+    st = O.evolve(s, O.params(dt=dt), 1, sys_off=off)
+    assert _rel_ok(gx, s.x3) and _rel_ok(gv, s.v3)
+    g = c.stats()
+    for k in ("tau_pairs", "kick_pairs", "splits", "components"):
+        assert g[k] == getattr(st, k), k
+    c.close()
