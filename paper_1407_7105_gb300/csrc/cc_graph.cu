@@ -337,39 +337,50 @@ __device__ __forceinline__ int seg1_scan(int v, int *tmp, int *total)
 }
 
 __global__ void __launch_bounds__(SEG1_T) k_segment_small(Level L, int32_t *root_out, int32_t *members,
-                                                          int32_t *comp_start, int32_t *comp_size, int32_t *ncomp)
+                                                          int32_t *comp_start, int32_t *comp_size, int32_t *ncomp,
+                                                          int roots_ready)
 {
     extern __shared__ int seg1_smem[];
     const int n = L.total, tid = threadIdx.x;
-    int *s_root = seg1_smem;      // roots, then the member list being built
+    int *s_root = seg1_smem;      // roots (-1: padding), then the member list being built
     int *s_cnt = seg1_smem + n;   // size by root, then run start / cursor by key
     __shared__ int tmp[32];
     __shared__ int s_nbig, s_big_root[SEG1_BIG], s_big_start[SEG1_BIG], s_big_size[SEG1_BIG];
     // each thread owns the contiguous chunk [c0, c1) of the batch (scans)
     const int per = (n + SEG1_T - 1) / SEG1_T;
     const int c0 = min(n, tid * per), c1 = min(n, c0 + per);
-    for (int k = tid; k < n; k += SEG1_T) s_cnt[k] = 0;
     if (tid == 0) s_nbig = 0;
-    __syncthreads();
-    for (int k = tid; k < n; k += SEG1_T) {
-        const bool valid = L.gid[k] >= 0;
-        const int r = valid ? uf_find_ca(L.parent, k) : k;
-        s_root[k] = r;
-        root_out[k] = r;
-        if (valid) atomicAdd(&s_cnt[r], 1);
+    if (roots_ready) {
+        // roots and sizes from the multi-block compress pass (k_compress)
+        for (int k = tid; k < n; k += SEG1_T) {
+            s_root[k] = L.gid[k] >= 0 ? root_out[k] : -1;
+            s_cnt[k] = L.cnt[k];
+        }
+        __syncthreads();
+    } else {
+        for (int k = tid; k < n; k += SEG1_T) s_cnt[k] = 0;
+        __syncthreads();
+        for (int k = tid; k < n; k += SEG1_T) {
+            const bool valid = L.gid[k] >= 0;
+            const int r = valid ? uf_find_ca(L.parent, k) : k;
+            s_root[k] = valid ? r : -1;
+            root_out[k] = r;
+            if (valid) atomicAdd(&s_cnt[r], 1);
+        }
+        __syncthreads();
+        for (int k = tid; k < n; k += SEG1_T) L.cnt[k] = s_cnt[k];
     }
-    __syncthreads();
-    for (int k = tid; k < n; k += SEG1_T) L.cnt[k] = s_cnt[k];
     // run of key k: w = elements keyed k (key = root for valid elements, own
     // index for padding); a component head has w >= 2
     auto weight = [&](int k) {
-        return L.gid[k] < 0 ? 1 : (s_root[k] == k ? s_cnt[k] : 0);
+        const int r = s_root[k];
+        return r < 0 ? 1 : (r == k ? s_cnt[k] : 0);
     };
     int sw = 0, sc = 0;
     for (int k = c0; k < c1; ++k) {
         const int w = weight(k);
         sw += w;
-        sc += (L.gid[k] >= 0 && w >= 2) ? 1 : 0;
+        sc += (s_root[k] >= 0 && w >= 2) ? 1 : 0;
     }
     __syncthreads();
     int tot_w, tot_c;
@@ -380,7 +391,7 @@ __global__ void __launch_bounds__(SEG1_T) k_segment_small(Level L, int32_t *root
     // thread, and a key's cursor lives at the key's own index)
     for (int k = c0; k < c1; ++k) {
         const int w = weight(k);
-        if (L.gid[k] >= 0 && w >= 2) {
+        if (s_root[k] >= 0 && w >= 2) {
             comp_start[ec] = ew;
             comp_size[ec] = w;
             if (w > SEG1_RUN) {
@@ -402,17 +413,17 @@ __global__ void __launch_bounds__(SEG1_T) k_segment_small(Level L, int32_t *root
     if (nbig <= SEG1_BIG) {
         // keys of the thread's strided elements, read before s_root turns
         // into the member list
-        auto key_of = [&](int k) { return L.gid[k] >= 0 ? s_root[k] : k; };
-        auto is_big = [&](int key) { return L.gid[key] >= 0 && s_root[key] == key && L.cnt[key] > SEG1_RUN; };
+        auto key_of = [&](int k) { return s_root[k] >= 0 ? s_root[k] : k; };
+        auto is_big = [&](int key) { return s_root[key] == key && L.cnt[key] > SEG1_RUN; };
         // large runs first: stable compaction per run (reads s_root only)
         for (int b = 0; b < nbig; ++b) {
             const int rb = s_big_root[b];
             int cnt = 0;
-            for (int k = c0; k < c1; ++k) cnt += (L.gid[k] >= 0 && s_root[k] == rb) ? 1 : 0;
+            for (int k = c0; k < c1; ++k) cnt += s_root[k] == rb ? 1 : 0;
             int tot;
             int pos = s_big_start[b] + seg1_scan(cnt, tmp, &tot);
             for (int k = c0; k < c1; ++k)
-                if (L.gid[k] >= 0 && s_root[k] == rb) members[pos++] = k;
+                if (s_root[k] == rb) members[pos++] = k;
             __syncthreads();
         }
         // small runs: unordered scatter into shared memory
@@ -460,7 +471,7 @@ __global__ void __launch_bounds__(SEG1_T) k_segment_small(Level L, int32_t *root
         for (int base = 0; base < n; base += 32) {
             const int k = base + tid;
             const bool in = k < n;
-            const int key = in ? (L.gid[k] >= 0 ? s_root[k] : k) : -1 - tid;
+            const int key = in ? (s_root[k] >= 0 ? s_root[k] : k) : -1 - tid;
             const unsigned peers = __match_any_sync(0xffffffffu, key);
             const int rank = __popc(peers & lt);
             const int lead = __ffs(peers) - 1;
@@ -488,7 +499,12 @@ void launch_compress_segment(const Level &L, int32_t *root, int32_t *members, in
             cudaFuncSetAttribute(k_segment_small, cudaFuncAttributeMaxDynamicSharedMemorySize, SEG1_MAX * 8);
             attr_set[dev] = true;
         }
-        k_segment_small<<<1, SEG1_T, (size_t)L.total * 8, s>>>(L, root, members, comp_start, comp_size, d_ncomp);
+        // past a few thousand elements the finds run faster spread over the
+        // GPU (k_compress) than in the one CTA
+        const bool spread = L.total > 4096;
+        if (spread) launch_compress(L, root, s);  // (sizes start at zero: k_init_parent)
+        k_segment_small<<<1, SEG1_T, (size_t)L.total * 8, s>>>(L, root, members, comp_start, comp_size, d_ncomp,
+                                                               spread ? 1 : 0);
         CC_COUNT_LAUNCH(1);
         return;
     }
