@@ -113,14 +113,22 @@ __global__ void __launch_bounds__(T) k_tau_hook(Level L, TauParams P, DevCounter
     unsigned long long my_edges = 0;
     if (iv) {
         const int kbeg = (ti == tj) ? tid + 1 : 0;
+        auto tau_of = [&](int k) {
+            return tau_fp64(__dsub_rn(xi, sm.col[0][k]), __dsub_rn(yi, sm.col[1][k]), __dsub_rn(zi, sm.col[2][k]),
+                            __dsub_rn(vxi, sm.col[3][k]), __dsub_rn(vyi, sm.col[4][k]), __dsub_rn(vzi, sm.col[5][k]),
+                            mi, sm.col[6][k], P);
+        };
+        // two pairs' tau in flight (its square roots and divisions are long
+        // dependent chains); the second of the last pair may be a repeat
+        double tnext = 0.0;
         for (int k = kbeg; k < jn; ++k) {
-            const double dx0 = __dsub_rn(xi, sm.col[0][k]);
-            const double dx1 = __dsub_rn(yi, sm.col[1][k]);
-            const double dx2 = __dsub_rn(zi, sm.col[2][k]);
-            const double dv0 = __dsub_rn(vxi, sm.col[3][k]);
-            const double dv1 = __dsub_rn(vyi, sm.col[4][k]);
-            const double dv2 = __dsub_rn(vzi, sm.col[5][k]);
-            const double tau = tau_fp64(dx0, dx1, dx2, dv0, dv1, dv2, mi, sm.col[6][k], P);
+            double tau;
+            if (((k - kbeg) & 1) == 0) {
+                tau = tau_of(k);
+                tnext = tau_of(k + 1 < jn ? k + 1 : k);
+            } else {
+                tau = tnext;
+            }
             const int j = j0 + k;
             log_pair(P, tau, gi, L.gid[j], ctr, near_ij, near_tau, near_cap);
             if (tau < P.h) {
@@ -426,8 +434,12 @@ __global__ void __launch_bounds__(T) k_kick64(Level L, const int32_t *label, dou
         const int jn = min(T, n - tj * T);
         const int j0l = tj * T;
         if (iv) {
-            for (int k = 0; k < jn; ++k) {
-                if (j0l + k == il || sm.lab[st][k] == li) continue;
+            // the pair force of j (exactly +0 for j = i or the same label,
+            // which leaves the sum unchanged bit for bit); the square root
+            // and division of several j are in flight at once, while the
+            // sums still take the terms in ascending j
+            auto term = [&](int k, double &fx, double &fy, double &fz) {
+                const bool use = j0l + k != il && sm.lab[st][k] != li;
                 const double dx0 = __dsub_rn(sm.col[st][0][k], xi);
                 const double dx1 = __dsub_rn(sm.col[st][1][k], yi);
                 const double dx2 = __dsub_rn(sm.col[st][2][k], zi);
@@ -435,9 +447,25 @@ __global__ void __launch_bounds__(T) k_kick64(Level L, const int32_t *label, dou
                     __dadd_rn(__dadd_rn(__dmul_rn(dx0, dx0), __dmul_rn(dx1, dx1)), __dmul_rn(dx2, dx2)), eps2);
                 const double rinv3 = __ddiv_rn(1.0, __dmul_rn(r2, __dsqrt_rn(r2)));
                 const double w = __dmul_rn(__dmul_rn(G, sm.col[st][3][k]), rinv3);
-                ax = __dadd_rn(ax, __dmul_rn(w, dx0));
-                ay = __dadd_rn(ay, __dmul_rn(w, dx1));
-                az = __dadd_rn(az, __dmul_rn(w, dx2));
+                fx = use ? __dmul_rn(w, dx0) : 0.0;
+                fy = use ? __dmul_rn(w, dx1) : 0.0;
+                fz = use ? __dmul_rn(w, dx2) : 0.0;
+            };
+            int k = 0;
+            for (; k + 1 < jn; k += 2) {
+                double f0x, f0y, f0z, f1x, f1y, f1z;
+                term(k, f0x, f0y, f0z);
+                term(k + 1, f1x, f1y, f1z);
+                ax = __dadd_rn(__dadd_rn(ax, f0x), f1x);
+                ay = __dadd_rn(__dadd_rn(ay, f0y), f1y);
+                az = __dadd_rn(__dadd_rn(az, f0z), f1z);
+            }
+            if (k < jn) {
+                double fx, fy, fz;
+                term(k, fx, fy, fz);
+                ax = __dadd_rn(ax, fx);
+                ay = __dadd_rn(ay, fy);
+                az = __dadd_rn(az, fz);
             }
         }
         __syncthreads();
