@@ -686,10 +686,10 @@ static int level_kick(cc_ctx *c, LevelAlloc &a, const int32_t *lab, const int32_
                           a.mk_chunks_max[var] > 1, c->p.eps * c->p.eps, h, c->d_ctr, c->d_kpart, lab, drift_dt, s);
         ev_end(c, ev);
     } else {
-        const int var = tune_pick(c, TK_K64, a.k64_blocks, a.pairs, &bin, &timed);
-        L.itile_off = a.k64_off[var];
-        const int ev = ev_begin(c, 1, nullptr, timed ? TK_K64 : -1, bin, var, (double)a.pairs);
-        launch_kick(L, lab, (int)a.k64_blocks[var], c->p.G, c->p.eps * c->p.eps, h, var, c->d_ctr, s);
+        // FP64: one shape (32-body i-tiles; the row order fixes the rounding)
+        L.itile_off = a.k64_off[0];
+        const int ev = ev_begin(c, 1, nullptr, -1, 0, 0, (double)a.pairs);
+        launch_kick(L, lab, (int)a.k64_blocks[0], c->p.G, c->p.eps * c->p.eps, h, 0, c->d_ctr, s);
         ev_end(c, ev);
     }
     return CC_OK;

@@ -394,106 +394,103 @@ __device__ __forceinline__ void kick_issue(KickSmem<T> &sm, int st, const Level 
     tma_load_1d(sm.lab[st], label + j0, cnt * 4u, &sm.bar[st]);
 }
 
-template <int T>
-__global__ void __launch_bounds__(T) k_kick64(Level L, const int32_t *label, double G, double eps2,
-                                                    double h, DevCounters *ctr)
+// One CTA (256 threads) per 32-body i-tile of a set.  For each 32-body
+// j-tile (TMA, double-buffered) all threads first compute the tile's 1024
+// pair forces (the square roots and divisions, the bulk of the FP64 work,
+// spread over eight warps) into shared memory, then 96 threads each add one
+// (row, component) over the tile in ascending j: a_i is still the sum over
+// j in ascending id, term by term as in the plain definition (a skipped
+// pair is an exact +0), so the result is the oracle's bit for bit, while the
+// FP64 pipe sees eight warps per block instead of one thread per body.
+constexpr int KB_T = 32;        // i-tile and j-tile
+constexpr int KB_THREADS = 256;
+static_assert(K64_VAR_T[0] == KB_T, "the FP64 kick runs on the 32-body i-tile prefix");
+
+struct __align__(16) KickBSmem {
+    KickSmem<KB_T> j;                // j tiles: x y z m, labels
+    double f[3][KB_T][KB_T + 1];     // pair forces of the current tile (padded rows)
+    double xi[3][KB_T];              // the i-tile
+    int32_t li[KB_T];
+};
+
+__global__ void __launch_bounds__(KB_THREADS) k_kick64(Level L, const int32_t *label, double G, double eps2, double h,
+                                                       DevCounters *ctr)
 {
-    __shared__ __align__(16) KickSmem<T> sm;
+    __shared__ KickBSmem sm;
     const int tid = threadIdx.x;
     const int s = find_set(L.itile_off, L.nsets, blockIdx.x);
     const int ti = blockIdx.x - L.itile_off[s];
     const int n = L.set_n[s], start = L.set_start[s];
-    const int nt = (n + T - 1) / T;
-    const int il = ti * T + tid;
-    const bool iv = il < n;
-    const int i = start + il;
+    const int nt = (n + KB_T - 1) / KB_T;
+    const int il0 = ti * KB_T, ni = min(KB_T, n - il0);
     if (tid == 0) {
-        mbar_init(&sm.bar[0], 1);
-        mbar_init(&sm.bar[1], 1);
+        mbar_init(&sm.j.bar[0], 1);
+        mbar_init(&sm.j.bar[1], 1);
         fence_mbar_init();
     }
-    __syncthreads();
-    if (tid == 0) kick_issue(sm, 0, L, label, start, min(T, n));
-    double xi = 0, yi = 0, zi = 0;
-    int li = 0;
-    if (iv) {
-        xi = L.x[i]; yi = L.y[i]; zi = L.z[i];
-        li = label[i];
+    if (tid < KB_T) {
+        const bool v = tid < ni;
+        const int i = start + il0 + tid;
+        sm.xi[0][tid] = v ? L.x[i] : 0.0;
+        sm.xi[1][tid] = v ? L.y[i] : 0.0;
+        sm.xi[2][tid] = v ? L.z[i] : 0.0;
+        sm.li[tid] = v ? label[i] : 0;
     }
-    double ax = 0.0, ay = 0.0, az = 0.0;
+    __syncthreads();
+    if (tid == 0) kick_issue(sm.j, 0, L, label, start, min(KB_T, n));
+    const int r = tid & 31, c = tid >> 5;  // summing threads: row r, component c (tid < 96)
+    double acc = 0.0;
     bool ok = true;
     for (int tj = 0; tj < nt; ++tj) {
         const int st = tj & 1;
         if (tid == 0 && tj + 1 < nt)
-            kick_issue(sm, st ^ 1, L, label, start + (tj + 1) * T, min(T, n - (tj + 1) * T));
-        const bool got = mbar_wait(&sm.bar[st], (tj >> 1) & 1, TMA_WAIT_CYCLES);
+            kick_issue(sm.j, st ^ 1, L, label, start + (tj + 1) * KB_T, min(KB_T, n - (tj + 1) * KB_T));
+        const bool got = mbar_wait(&sm.j.bar[st], (tj >> 1) & 1, TMA_WAIT_CYCLES);
         if (__syncthreads_or(!got)) {  // uniform exit: no thread is left at a barrier
             ok = false;
             break;
         }
-        const int jn = min(T, n - tj * T);
-        const int j0l = tj * T;
-        if (iv) {
-            // the pair force of j (exactly +0 for j = i or the same label,
-            // which leaves the sum unchanged bit for bit); the square root
-            // and division of several j are in flight at once, while the
-            // sums still take the terms in ascending j
-            auto term = [&](int k, double &fx, double &fy, double &fz) {
-                const bool use = j0l + k != il && sm.lab[st][k] != li;
-                const double dx0 = __dsub_rn(sm.col[st][0][k], xi);
-                const double dx1 = __dsub_rn(sm.col[st][1][k], yi);
-                const double dx2 = __dsub_rn(sm.col[st][2][k], zi);
-                const double r2 = __dadd_rn(
-                    __dadd_rn(__dadd_rn(__dmul_rn(dx0, dx0), __dmul_rn(dx1, dx1)), __dmul_rn(dx2, dx2)), eps2);
-                const double rinv3 = __ddiv_rn(1.0, __dmul_rn(r2, __dsqrt_rn(r2)));
-                const double w = __dmul_rn(__dmul_rn(G, sm.col[st][3][k]), rinv3);
-                fx = use ? __dmul_rn(w, dx0) : 0.0;
-                fy = use ? __dmul_rn(w, dx1) : 0.0;
-                fz = use ? __dmul_rn(w, dx2) : 0.0;
-            };
-            int k = 0;
-            for (; k + 1 < jn; k += 2) {
-                double f0x, f0y, f0z, f1x, f1y, f1z;
-                term(k, f0x, f0y, f0z);
-                term(k + 1, f1x, f1y, f1z);
-                ax = __dadd_rn(__dadd_rn(ax, f0x), f1x);
-                ay = __dadd_rn(__dadd_rn(ay, f0y), f1y);
-                az = __dadd_rn(__dadd_rn(az, f0z), f1z);
-            }
-            if (k < jn) {
-                double fx, fy, fz;
-                term(k, fx, fy, fz);
-                ax = __dadd_rn(ax, fx);
-                ay = __dadd_rn(ay, fy);
-                az = __dadd_rn(az, fz);
-            }
+        const int jn = min(KB_T, n - tj * KB_T), jl0 = tj * KB_T;
+#pragma unroll
+        for (int q = 0; q < KB_T * KB_T / KB_THREADS; ++q) {
+            const int pidx = tid + q * KB_THREADS, ii = pidx >> 5, jj = pidx & 31;
+            const bool use = ii < ni && jj < jn && il0 + ii != jl0 + jj && sm.li[ii] != sm.j.lab[st][jj];
+            const double dx0 = __dsub_rn(sm.j.col[st][0][jj], sm.xi[0][ii]);
+            const double dx1 = __dsub_rn(sm.j.col[st][1][jj], sm.xi[1][ii]);
+            const double dx2 = __dsub_rn(sm.j.col[st][2][jj], sm.xi[2][ii]);
+            const double r2 = __dadd_rn(
+                __dadd_rn(__dadd_rn(__dmul_rn(dx0, dx0), __dmul_rn(dx1, dx1)), __dmul_rn(dx2, dx2)), eps2);
+            const double rinv3 = __ddiv_rn(1.0, __dmul_rn(r2, __dsqrt_rn(r2)));
+            const double w = __dmul_rn(__dmul_rn(G, sm.j.col[st][3][jj]), rinv3);
+            sm.f[0][ii][jj] = use ? __dmul_rn(w, dx0) : 0.0;
+            sm.f[1][ii][jj] = use ? __dmul_rn(w, dx1) : 0.0;
+            sm.f[2][ii][jj] = use ? __dmul_rn(w, dx2) : 0.0;
         }
+        __syncthreads();
+        if (tid < 3 * KB_T)
+            for (int jj = 0; jj < jn; ++jj) acc = __dadd_rn(acc, sm.f[c][r][jj]);
         __syncthreads();
     }
     if (!ok) {
         raise_err(ctr, DERR_TMA_TIMEOUT);
         // let any copy still in flight land before the CTA exits
-        mbar_wait(&sm.bar[0], 0, TMA_WAIT_CYCLES);
-        mbar_wait(&sm.bar[1], 0, TMA_WAIT_CYCLES);
+        mbar_wait(&sm.j.bar[0], 0, TMA_WAIT_CYCLES);
+        mbar_wait(&sm.j.bar[1], 0, TMA_WAIT_CYCLES);
         return;
     }
-    if (iv) {
-        L.vx[i] = __dadd_rn(L.vx[i], __dmul_rn(h, ax));
-        L.vy[i] = __dadd_rn(L.vy[i], __dmul_rn(h, ay));
-        L.vz[i] = __dadd_rn(L.vz[i], __dmul_rn(h, az));
+    if (tid < 3 * KB_T && r < ni) {
+        const int i = start + il0 + r;
+        double *v = c == 0 ? L.vx : (c == 1 ? L.vy : L.vz);
+        v[i] = __dadd_rn(v[i], __dmul_rn(h, acc));
     }
 }
 
 void launch_kick(const Level &L, const int32_t *label, int nitiles, double G, double eps2, double h,
                  int variant, DevCounters *ctr, cudaStream_t s)
 {
+    (void)variant;  // one shape: 32-body tiles (the prefix of variant 0)
     if (nitiles <= 0) return;
-    if (variant == 0)
-        k_kick64<32><<<nitiles, 32, 0, s>>>(L, label, G, eps2, h, ctr);
-    else if (variant == 1)
-        k_kick64<64><<<nitiles, 64, 0, s>>>(L, label, G, eps2, h, ctr);
-    else
-        k_kick64<128><<<nitiles, 128, 0, s>>>(L, label, G, eps2, h, ctr);
+    k_kick64<<<nitiles, KB_THREADS, 0, s>>>(L, label, G, eps2, h, ctr);
     CC_COUNT_LAUNCH(1);
 }
 
