@@ -287,6 +287,7 @@ struct __align__(16) MixedKickSmem {
     float4 pq[2][2 * MK_T];  // (hi, Gm), (lo) per j, two stages
     int32_t lab[2][MK_T];
     int32_t tiles[MK_CHUNK_MAX];
+    int32_t apart[MK_CHUNK_MAX];  // 1: no label of the j-tile is one of the i-tile's
     int32_t ntiles;
     uint64_t bar[2];
 };
@@ -334,6 +335,8 @@ __global__ void __launch_bounds__(MK_T) k_kick_mixed(Level L, FFView F, const in
         for (int tj = tj0; tj < tj1; ++tj) {
             const int ja = start + tj * MK_T, jb = start + min(n, (tj + 1) * MK_T) - 1;
             if (iu && label[ja] == label[jb] && label[ja] == label[ia]) continue;
+            // labels ascend within a set: disjoint ranges share no component
+            sm.apart[q] = (label[jb] < label[ia] || label[ib] < label[ja]) ? 1 : 0;
             sm.tiles[q++] = tj;
         }
         sm.ntiles = q;
@@ -363,9 +366,7 @@ __global__ void __launch_bounds__(MK_T) k_kick_mixed(Level L, FFView F, const in
         }
         const int jn = min(MK_T, n - tj * MK_T);
         if (iv) {
-#pragma unroll 4
-            for (int k = 0; k < jn; ++k) {
-                if (sm.lab[st][k] == li) continue;  // same component (and self)
+            auto term = [&](int k) {
                 const float4 jp0 = sm.pq[st][2 * k], jp1 = sm.pq[st][2 * k + 1];
                 const float dx = (jp0.x - ip0.x) + (jp1.x - ip1.x);
                 const float dy = (jp0.y - ip0.y) + (jp1.y - ip1.y);
@@ -377,6 +378,14 @@ __global__ void __launch_bounds__(MK_T) k_kick_mixed(Level L, FFView F, const in
                 kahan_add(sx, cx, w * dx);
                 kahan_add(sy, cy, w * dy);
                 kahan_add(sz, cz, w * dz);
+            };
+            if (sm.apart[q]) {
+#pragma unroll 4
+                for (int k = 0; k < jn; ++k) term(k);
+            } else {
+#pragma unroll 4
+                for (int k = 0; k < jn; ++k)
+                    if (sm.lab[st][k] != li) term(k);  // same component (and self) skipped
             }
         }
         __syncthreads();
