@@ -31,6 +31,7 @@ constexpr float SLACK = 2e-6f;
 // and c_v = 11 u^2 V carry the float-float rounding of the differences
 struct MixedTauParams {
     float eta, etah, eps2, G;
+    float hq;  // eta/etah (h, or h/eta when eta multiplies the min): the pre-test's q = hq |dv|/r
 };
 
 // The h-independent part of the decision: everything except T/h.  The
@@ -106,6 +107,40 @@ __device__ __forceinline__ int tau_decide_at(const TauPrep32 &t, float etah)
     if (ff_yes || fb_yes) return 1;
     if (ff_no && fb_no) return 0;
     return -1;
+}
+
+// A sufficient test for "no edge" that skips the certified evaluation for
+// the great majority of pairs (those whose tau is well above h).  With T =
+// T_ff or T_fb and D = 1 - min(dT/dt, 1)/2, tau_x = T/D and D <= 1 + |dT/dt|/2:
+//   free fall: |dT_ff/dt| = 1.5 T_ff |rv|/r^2 <= 1.5 T_ff |dv|/r, so
+//     tau_ff >= h  if  (T_ff/h) (1 - 0.75 q) >= 1,  q = h|dv|/r (q < 4/3);
+//   flyby:     |dT_fb/dt| <= eta (1 + mu/(r v^2))  (T_fb = eta r/|dv|), so
+//     tau_fb >= h  if  T_fb/h >= 1 + eta (1 + mu/(r v^2))/2.
+// (eta is the factor inside T: Q.eta; hq = h/eta_in, the same as
+// eta/etah in both readings of the eta placement.)  The differences may be
+// formed from the rounded high parts alone: then |dx~ - dx| <= u r + c_x
+// with c_x = 3.5 u X (X = max |x|), likewise c_v for the velocities.  Once
+// c_x/r and c_v/|dv| are below 1e-4, every FP32 quantity used has relative
+// error below 1e-3 (the error model above: 40u + 3(er + ev) plus the rsqrt
+// budget), so a 2 % margin on each inequality makes the test rigorous; a
+// pair it does not settle goes to the certified decision.
+__device__ __forceinline__ bool tau_quick_apart(float dx0, float dx1, float dx2, float dv0, float dv1, float dv2,
+                                                float mu, float c_x, float c_v, const MixedTauParams &Q)
+{
+    const float r2 = fmaf(dx2, dx2, fmaf(dx1, dx1, fmaf(dx0, dx0, Q.eps2)));
+    const float v2 = fmaf(dv2, dv2, fmaf(dv1, dv1, dv0 * dv0));
+    const float rinv = rsqrtf(r2);
+    const float r = r2 * rinv;
+    const float s1 = rsqrtf(r * mu);
+    const float s2 = rsqrtf(v2);      // inf for v2 = 0: rejected below
+    const float vn = v2 * s2;         // |dv|
+    const float Tff = Q.etah * r2 * s1;                  // T_ff / h
+    const float q = Q.hq * vn * rinv;                    // h |dv| / r
+    const float Tfb = Q.etah * r * s2;                   // T_fb / h
+    const float g = mu * rinv * s2 * s2;                 // mu / (r v^2)
+    const float M = 1.02f;
+    return c_x * rinv <= 1e-4f && v2 > 0.f && c_v * s2 <= 1e-4f && 0.75f * M * q < 1.f &&
+           Tff * fmaf(-0.75f * M, q, 1.f) >= M && Tfb >= M * fmaf(0.5f * Q.eta, 1.f + g, 1.f);
 }
 
 __device__ __forceinline__ int tau_decide_fp32(float dx0, float dx1, float dx2, float dv0, float dv1, float dv2,

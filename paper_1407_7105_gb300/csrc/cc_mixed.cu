@@ -137,6 +137,12 @@ __device__ __forceinline__ bool luf_union(int32_t *p, int a, int b)
     return false;
 }
 
+__device__ __noinline__ int tau_decide_fp32_ool(float dx0, float dx1, float dx2, float dv0, float dv1, float dv2,
+                                                float mu, float c_x, float c_v, MixedTauParams Q)
+{
+    return tau_decide_fp32(dx0, dx1, dx2, dv0, dv1, dv2, mu, c_x, c_v, Q);
+}
+
 template <int T>
 __global__ void __launch_bounds__(T) k_tau_mixed(Level L, FFView F, TauParams P, MixedTauParams Q,
                                                      DevCounters *ctr, int32_t *near_ij, double *near_tau,
@@ -184,6 +190,7 @@ __global__ void __launch_bounds__(T) k_tau_mixed(Level L, FFView F, TauParams P,
         iv0 = F.vq[2 * i]; iv1 = F.vq[2 * i + 1];
     }
     const float cX = 11.f * U32 * U32 * F.maxes[0], cV = 11.f * U32 * U32 * F.maxes[1];
+    const float cXh = 3.5f * U32 * F.maxes[0], cVh = 3.5f * U32 * F.maxes[1];  // high parts alone
     const bool got = mbar_wait(&sm.bar, 0, TMA_WAIT_CYCLES);
     if (__syncthreads_or(!got)) {
         raise_err(ctr, DERR_TMA_TIMEOUT);
@@ -194,15 +201,20 @@ __global__ void __launch_bounds__(T) k_tau_mixed(Level L, FFView F, TauParams P,
     const int joff = diag ? 0 : T;  // local index base of the j-tile
     if (iv) {
         for (int k = diag ? tid + 1 : 0; k < jn; ++k) {
-            const float4 jp0 = sm.pq[2 * k], jp1 = sm.pq[2 * k + 1];
-            const float4 jv0 = sm.vq[2 * k], jv1 = sm.vq[2 * k + 1];
-            const float dx0 = (jp0.x - ip0.x) + (jp1.x - ip1.x);
-            const float dx1 = (jp0.y - ip0.y) + (jp1.y - ip1.y);
-            const float dx2 = (jp0.z - ip0.z) + (jp1.z - ip1.z);
-            const float dv0 = (jv0.x - iv0.x) + (jv1.x - iv1.x);
-            const float dv1 = (jv0.y - iv0.y) + (jv1.y - iv1.y);
-            const float dv2 = (jv0.z - iv0.z) + (jv1.z - iv1.z);
-            int dec = tau_decide_fp32(dx0, dx1, dx2, dv0, dv1, dv2, ip0.w + jp0.w, cX, cV, Q);
+            // most pairs: certainly apart by the cheap bound on the high
+            // parts; the rest take the certified decision on the float-float
+            // differences (out of line, so that the common path stays
+            // short) and, if it is undecided, FP64
+            const float4 jp0 = sm.pq[2 * k], jv0 = sm.vq[2 * k];
+            int dec = 0;
+            if (!tau_quick_apart(jp0.x - ip0.x, jp0.y - ip0.y, jp0.z - ip0.z, jv0.x - iv0.x, jv0.y - iv0.y,
+                                 jv0.z - iv0.z, ip0.w + jp0.w, cXh, cVh, Q)) {
+                const float4 jp1 = sm.pq[2 * k + 1], jv1 = sm.vq[2 * k + 1];
+                dec = tau_decide_fp32_ool((jp0.x - ip0.x) + (jp1.x - ip1.x), (jp0.y - ip0.y) + (jp1.y - ip1.y),
+                                          (jp0.z - ip0.z) + (jp1.z - ip1.z), (jv0.x - iv0.x) + (jv1.x - iv1.x),
+                                          (jv0.y - iv0.y) + (jv1.y - iv1.y), (jv0.z - iv0.z) + (jv1.z - iv1.z),
+                                          ip0.w + jp0.w, cX, cV, Q);
+            }
             double tau = CUDART_NAN;
             if (dec < 0) {
                 // undecided: the exact FP64 predicate of the FP64 form
@@ -264,6 +276,7 @@ void launch_tau_mixed(const Level &L, const FFView &F, int ntiles, const TauPara
     Q.etah = (float)(P.eta_outside ? P.eta_in * P.eta / P.h : P.eta_in / P.h);
     Q.eps2 = (float)P.eps2;
     Q.G = (float)P.G;
+    Q.hq = (float)(P.eta_outside ? P.h / P.eta : P.h);  // h/eta_in in the units of T: eta_in/etah
     if (variant == 0)
         k_tau_mixed<64><<<ntiles, 64, 0, s>>>(L, F, P, Q, ctr, near_ij, near_tau, near_cap, E);
     else

@@ -271,6 +271,7 @@ void launch_edges_reuse(const EdgeList &parent, long long pcount, const Level &P
     Q.etah = (float)(P.eta_outside ? P.eta_in * P.eta / hp : P.eta_in / hp);
     Q.eps2 = (float)P.eps2;
     Q.G = (float)P.G;
+    Q.hq = 0.f;  // (the pre-test is not used here)
     const unsigned blocks = (unsigned)((pcount + 255) / 256);
     k_edges_filter<<<blocks, 256, 0, s>>>(parent, pcount, PL, PF, Q, mixed ? 1 : 0, inv, C, child, P, ctr, near_ij,
                                           near_tau, near_cap);

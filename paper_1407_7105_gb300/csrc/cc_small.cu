@@ -426,6 +426,7 @@ __global__ void __launch_bounds__(K8_WARPS * 32) k_small(Level L, const int32_t 
     P.near_tol = SP.near_tol;
     MixedTauParams Q;
     Q.eta = (float)SP.eta_in; Q.eps2 = (float)SP.eps2; Q.G = (float)SP.G;
+    Q.hq = 0.f;  // (the pre-test is not used here)
     const NearLog nl = {ctr, near_ij, near_tau, near_cap, SP.near_tol};
     // eta/h0 in float, once: eta/(h0 2^-k) is this times 2^k exactly
     const float etah_c = (float)(SP.eta_outside ? SP.eta_in * SP.eta / SP.h0 : SP.eta_in / SP.h0);
