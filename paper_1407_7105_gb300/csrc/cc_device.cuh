@@ -119,28 +119,42 @@ __device__ __forceinline__ int tau_decide_at(const TauPrep32 &t, float etah)
 // (eta is the factor inside T: Q.eta; hq = h/eta_in, the same as
 // eta/etah in both readings of the eta placement.)  The differences may be
 // formed from the rounded high parts alone: then |dx~ - dx| <= u r + c_x
-// with c_x = 3.5 u X (X = max |x|), likewise c_v for the velocities.  Once
-// c_x/r and c_v/|dv| are below 1e-4, every FP32 quantity used has relative
+// + 3.5 u r with c_x = 7 u max|x_i| (per component |x_j| <= |x_i| + r),
+// likewise c_v for the velocities.  Once (c_x + 3.5 u r)/r and the velocity
+// analogue are below 1e-4, every FP32 quantity used has relative
 // error below 1e-3 (the error model above: 40u + 3(er + ev) plus the rsqrt
 // budget), so a 2 % margin on each inequality makes the test rigorous; a
 // pair it does not settle goes to the certified decision.
+// reciprocal square root, PTX rsqrt.approx.ftz.f32 (relative error below
+// 2^-22.9 for normal inputs; a denormal input is flushed to zero and gives
+// +inf, which the pre-test's comparisons reject)
+__device__ __forceinline__ float rsqrt_ftz(float x)
+{
+    float y;
+    asm("rsqrt.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+    return y;
+}
+
 __device__ __forceinline__ bool tau_quick_apart(float dx0, float dx1, float dx2, float dv0, float dv1, float dv2,
                                                 float mu, float c_x, float c_v, const MixedTauParams &Q)
 {
     const float r2 = fmaf(dx2, dx2, fmaf(dx1, dx1, fmaf(dx0, dx0, Q.eps2)));
     const float v2 = fmaf(dv2, dv2, fmaf(dv1, dv1, dv0 * dv0));
-    const float rinv = rsqrtf(r2);
+    const float rinv = rsqrt_ftz(r2);
     const float r = r2 * rinv;
-    const float s1 = rsqrtf(r * mu);
-    const float s2 = rsqrtf(v2);      // inf for v2 = 0: rejected below
+    const float s1 = rsqrt_ftz(r * mu);
+    const float s2 = rsqrt_ftz(v2);   // inf for v2 = 0: rejected below
     const float vn = v2 * s2;         // |dv|
     const float Tff = Q.etah * r2 * s1;                  // T_ff / h
     const float q = Q.hq * vn * rinv;                    // h |dv| / r
     const float Tfb = Q.etah * r * s2;                   // T_fb / h
     const float g = mu * rinv * s2 * s2;                 // mu / (r v^2)
     const float M = 1.02f;
-    return c_x * rinv <= 1e-4f && v2 > 0.f && c_v * s2 <= 1e-4f && 0.75f * M * q < 1.f &&
-           Tff * fmaf(-0.75f * M, q, 1.f) >= M && Tfb >= M * fmaf(0.5f * Q.eta, 1.f + g, 1.f);
+    // (the bounds below leave 3.5u for a relative part of c_x/r, c_v/|dv|;
+    // all conditions are evaluated: no short-circuit branches)
+    const bool ok = (c_x * rinv <= 0.99e-4f) & (v2 > 0.f) & (c_v * s2 <= 0.99e-4f) & (0.75f * M * q < 1.f) &
+                    (Tff * fmaf(-0.75f * M, q, 1.f) >= M) & (Tfb >= M * fmaf(0.5f * Q.eta, 1.f + g, 1.f));
+    return ok;
 }
 
 __device__ __forceinline__ int tau_decide_fp32(float dx0, float dx1, float dx2, float dv0, float dv1, float dv2,

@@ -190,7 +190,12 @@ __global__ void __launch_bounds__(T) k_tau_mixed(Level L, FFView F, TauParams P,
         iv0 = F.vq[2 * i]; iv1 = F.vq[2 * i + 1];
     }
     const float cX = 11.f * U32 * U32 * F.maxes[0], cV = 11.f * U32 * U32 * F.maxes[1];
-    const float cXh = 3.5f * U32 * F.maxes[0], cVh = 3.5f * U32 * F.maxes[1];  // high parts alone
+    // the pre-test's error terms for high-part differences: per component
+    // |x_j| <= |x_i| + r, so |dx~ - dx| <= u r + 3.5 u (2 max|x_i| + r): c_x =
+    // 7 u max|x_i| per thread, and the remaining 3.5 u r goes to the
+    // threshold (likewise for the velocities)
+    const float cXh = 7.1f * U32 * fmaxf(fabsf(ip0.x), fmaxf(fabsf(ip0.y), fabsf(ip0.z)));
+    const float cVh = 7.1f * U32 * fmaxf(fabsf(iv0.x), fmaxf(fabsf(iv0.y), fabsf(iv0.z)));
     const bool got = mbar_wait(&sm.bar, 0, TMA_WAIT_CYCLES);
     if (__syncthreads_or(!got)) {
         raise_err(ctr, DERR_TMA_TIMEOUT);
@@ -199,16 +204,20 @@ __global__ void __launch_bounds__(T) k_tau_mixed(Level L, FFView F, TauParams P,
     }
     unsigned long long my_edges = 0, my_fp64 = 0;
     const int joff = diag ? 0 : T;  // local index base of the j-tile
-    if (iv) {
-        for (int k = diag ? tid + 1 : 0; k < jn; ++k) {
-            // most pairs: certainly apart by the cheap bound on the high
-            // parts; the rest take the certified decision on the float-float
-            // differences (out of line, so that the common path stays
-            // short) and, if it is undecided, FP64
+    {
+        // one trip count for the whole warp (jn is the block's), so the
+        // common case is a vote: every lane's pair certainly apart by the
+        // cheap bound on the high parts; the rest take the certified decision
+        // on the float-float differences (out of line, so that the common
+        // path stays short) and, if it is undecided, FP64
+        for (int k = 0; k < jn; ++k) {
+            const bool mine = iv && (!diag || k > tid);
             const float4 jp0 = sm.pq[2 * k], jv0 = sm.vq[2 * k];
-            int dec = 0;
-            if (!tau_quick_apart(jp0.x - ip0.x, jp0.y - ip0.y, jp0.z - ip0.z, jv0.x - iv0.x, jv0.y - iv0.y,
-                                 jv0.z - iv0.z, ip0.w + jp0.w, cXh, cVh, Q)) {
+            const bool apart = !mine || tau_quick_apart(jp0.x - ip0.x, jp0.y - ip0.y, jp0.z - ip0.z, jv0.x - iv0.x,
+                                                        jv0.y - iv0.y, jv0.z - iv0.z, ip0.w + jp0.w, cXh, cVh, Q);
+            if (__all_sync(0xffffffffu, apart) || apart) continue;
+            int dec;
+            {
                 const float4 jp1 = sm.pq[2 * k + 1], jv1 = sm.vq[2 * k + 1];
                 dec = tau_decide_fp32_ool((jp0.x - ip0.x) + (jp1.x - ip1.x), (jp0.y - ip0.y) + (jp1.y - ip1.y),
                                           (jp0.z - ip0.z) + (jp1.z - ip1.z), (jv0.x - iv0.x) + (jv1.x - iv1.x),

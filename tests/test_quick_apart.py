@@ -29,7 +29,7 @@ def quick_apart(dx, dv, mu, eta_in, etah, c_x=0.0, c_v=0.0, eps2=0.0):
         Tfb = (f32(etah) * r * s2).astype(f32)
         g = (f32(mu) * rinv * s2 * s2).astype(f32)
         M = f32(1.02)
-        return ((f32(c_x) * rinv <= f32(1e-4)) & (v2 > 0) & (f32(c_v) * s2 <= f32(1e-4)) &
+        return ((f32(c_x) * rinv <= f32(0.99e-4)) & (v2 > 0) & (f32(c_v) * s2 <= f32(0.99e-4)) &
                 (f32(0.75) * M * q < 1) & (Tff * (f32(1) - f32(0.75) * M * q) >= M) &
                 (Tfb >= M * (f32(1) + f32(0.5) * f32(eta_in) * (f32(1) + g))))
 
@@ -89,9 +89,10 @@ def test_pairs_near_threshold(eta_outside):
 @pytest.mark.parametrize("X", [1.0, 30.0, 1000.0])
 def test_high_part_differences(X):
     """The kernel forms the test's differences from the rounded high parts
-    alone, fl32(x_j) - fl32(x_i), and passes c_x = 3.5 u max|x| (likewise for
-    v): bodies far from the origin, at separations down to where that
-    rounding matters, with thresholds placed just above each pair's tau."""
+    alone, fl32(x_j) - fl32(x_i), and passes c_x = 7.1 u max|x_i| per pair
+    (likewise for v): bodies far from the origin, at separations down to
+    where that rounding matters, with thresholds placed just above each
+    pair's tau."""
     rng = np.random.default_rng(int(X))
     n = 4000
     u = 2.0 ** -24
@@ -100,8 +101,6 @@ def test_high_part_differences(X):
     xj = xi + sep
     vi = rng.standard_normal((3, n))
     vj = vi + rng.standard_normal((3, n)) * np.exp(rng.uniform(-8, 0, n))
-    Xm = max(np.abs(xi).max(), np.abs(xj).max())
-    Vm = max(np.abs(vi).max(), np.abs(vj).max())
     dxh = xj.astype(f32) - xi.astype(f32)
     dvh = vj.astype(f32) - vi.astype(f32)
     mi = mj = 1e-4
@@ -109,5 +108,6 @@ def test_high_part_differences(X):
     tau = oracle_tau(xi - xj, vi - vj, mi, mj, eta, 0)
     for rel in (0.5, 0.98, 0.999):
         h = tau / rel  # every pair an edge: none may be certified apart
-        ok = quick_apart(dxh, dvh, mi + mj, eta, eta / h, c_x=3.5 * u * Xm, c_v=3.5 * u * Vm)
+        ok = quick_apart(dxh, dvh, mi + mj, eta, eta / h, c_x=7.1 * u * np.abs(xi.astype(f32)).max(axis=0),
+                         c_v=7.1 * u * np.abs(vi.astype(f32)).max(axis=0))
         assert not ok.any(), (rel, np.flatnonzero(ok)[:5])
