@@ -278,6 +278,7 @@ def run_gpu(args, rank, world):
                "tau_fp64": st1["tau_fp64"] - st0["tau_fp64"], "tau_pairs": st1["tau_pairs"] - st0["tau_pairs"],
                "tau_evaluated": st1["tau_evaluated"] - st0["tau_evaluated"],
                "kick_pairs": st1["kick_pairs"] - st0["kick_pairs"],
+               "edges": st1["edges"] - st0["edges"],
                "dE": (E1 - E0) / abs(E0)}
         return res
 
@@ -369,6 +370,7 @@ def run_gpu(args, rank, world):
             "tau_pairs_per_step": head["tau_pairs"] / args.steps,
             "tau_pairs_evaluated_per_step": head["tau_evaluated"] / args.steps,
             "kick_pairs_per_step": head["kick_pairs"] / args.steps,
+            "edges_per_step": head["edges"] / args.steps,
             "other_form": other_line,
         }
         print(json.dumps(line), flush=True)

@@ -107,6 +107,7 @@ struct __align__(16) MixedTauSmem {
     float4 pq[2 * T];   // positions (hi, Gm), (lo) of the j-tile
     float4 vq[2 * T];   // velocities (hi), (lo)
     int32_t lp[2 * T];  // local union-find over the tile's particles
+    uint32_t q[T / 32][64];  // per warp: pairs waiting for the certified decision
     uint64_t bar;
 };
 
@@ -137,6 +138,12 @@ __device__ __forceinline__ bool luf_union(int32_t *p, int a, int b)
     return false;
 }
 
+__device__ __forceinline__ float4 shfl4(float4 v, int src)
+{
+    return make_float4(__shfl_sync(0xffffffffu, v.x, src), __shfl_sync(0xffffffffu, v.y, src),
+                       __shfl_sync(0xffffffffu, v.z, src), __shfl_sync(0xffffffffu, v.w, src));
+}
+
 __device__ __noinline__ int tau_decide_fp32_ool(float dx0, float dx1, float dx2, float dv0, float dv1, float dv2,
                                                 float mu, float c_x, float c_v, MixedTauParams Q)
 {
@@ -144,7 +151,7 @@ __device__ __noinline__ int tau_decide_fp32_ool(float dx0, float dx1, float dx2,
 }
 
 template <int T>
-__global__ void __launch_bounds__(T) k_tau_mixed(Level L, FFView F, TauParams P, MixedTauParams Q,
+__global__ void __launch_bounds__(T, 1024 / T) k_tau_mixed(Level L, FFView F, TauParams P, MixedTauParams Q,
                                                      DevCounters *ctr, int32_t *near_ij, double *near_tau,
                                                      long long near_cap, EdgeList E)
 {
@@ -204,54 +211,96 @@ __global__ void __launch_bounds__(T) k_tau_mixed(Level L, FFView F, TauParams P,
     }
     unsigned long long my_edges = 0, my_fp64 = 0;
     const int joff = diag ? 0 : T;  // local index base of the j-tile
-    {
-        // one trip count for the whole warp (jn is the block's), so the
-        // common case is a vote: every lane's pair certainly apart by the
-        // cheap bound on the high parts; the rest take the certified decision
-        // on the float-float differences (out of line, so that the common
-        // path stays short) and, if it is undecided, FP64
-        for (int k = 0; k < jn; ++k) {
-            const bool mine = iv && (!diag || k > tid);
-            const float4 jp0 = sm.pq[2 * k], jv0 = sm.vq[2 * k];
-            const bool apart = !mine || tau_quick_apart(jp0.x - ip0.x, jp0.y - ip0.y, jp0.z - ip0.z, jv0.x - iv0.x,
-                                                        jv0.y - iv0.y, jv0.z - iv0.z, ip0.w + jp0.w, cXh, cVh, Q);
-            if (__all_sync(0xffffffffu, apart) || apart) continue;
-            int dec;
-            {
-                const float4 jp1 = sm.pq[2 * k + 1], jv1 = sm.vq[2 * k + 1];
-                dec = tau_decide_fp32_ool((jp0.x - ip0.x) + (jp1.x - ip1.x), (jp0.y - ip0.y) + (jp1.y - ip1.y),
-                                          (jp0.z - ip0.z) + (jp1.z - ip1.z), (jv0.x - iv0.x) + (jv1.x - iv1.x),
-                                          (jv0.y - iv0.y) + (jv1.y - iv1.y), (jv0.z - iv0.z) + (jv1.z - iv1.z),
-                                          ip0.w + jp0.w, cX, cV, Q);
-            }
-            double tau = CUDART_NAN;
+    const int lane = tid & 31, w = tid >> 5;
+    const unsigned lt = (1u << lane) - 1u;
+    // Pairs the cheap bound does not settle are queued per warp and settled
+    // 32 at a time, one per lane: taken as they come, a single such pair
+    // would run the certified decision (and possibly FP64) with one lane of
+    // 32 active.  Entry = (i-tile lane index << 8) | j-tile index.
+    auto settle = [&](int cnt) {
+        const bool has = lane < cnt;
+        const unsigned ent = has ? sm.q[w][lane] : 0u;
+        const int ii = has ? (int)(ent >> 8) : tid, kk = (int)(ent & 255u);
+        const int src = ii & 31;  // the owner of body i is a lane of this warp
+        const float4 a0 = shfl4(ip0, src), a1 = shfl4(ip1, src), b0 = shfl4(iv0, src), b1 = shfl4(iv1, src);
+        int dec = 0;
+        double tau = CUDART_NAN;
+        if (has) {
+            const float4 jp0 = sm.pq[2 * kk], jp1 = sm.pq[2 * kk + 1], jv0 = sm.vq[2 * kk], jv1 = sm.vq[2 * kk + 1];
+            dec = tau_decide_fp32_ool((jp0.x - a0.x) + (jp1.x - a1.x), (jp0.y - a0.y) + (jp1.y - a1.y),
+                                      (jp0.z - a0.z) + (jp1.z - a1.z), (jv0.x - b0.x) + (jv1.x - b1.x),
+                                      (jv0.y - b0.y) + (jv1.y - b1.y), (jv0.z - b0.z) + (jv1.z - b1.z), a0.w + jp0.w,
+                                      cX, cV, Q);
             if (dec < 0) {
                 // undecided: the exact FP64 predicate of the FP64 form
-                const int j = j0 + k;
-                tau = tau_fp64(__dsub_rn(L.x[i], L.x[j]), __dsub_rn(L.y[i], L.y[j]), __dsub_rn(L.z[i], L.z[j]),
-                               __dsub_rn(L.vx[i], L.vx[j]), __dsub_rn(L.vy[i], L.vy[j]), __dsub_rn(L.vz[i], L.vz[j]),
-                               L.m[i], L.m[j], P);
+                const int gi = start + ti * T + ii, gj = j0 + kk;
+                tau = tau_fp64(__dsub_rn(L.x[gi], L.x[gj]), __dsub_rn(L.y[gi], L.y[gj]),
+                               __dsub_rn(L.z[gi], L.z[gj]), __dsub_rn(L.vx[gi], L.vx[gj]),
+                               __dsub_rn(L.vy[gi], L.vy[gj]), __dsub_rn(L.vz[gi], L.vz[gj]), L.m[gi], L.m[gj], P);
                 ++my_fp64;
                 if (fabs(tau - P.h) < P.near_tol * P.h) {
-                    unsigned long long q = atomicAdd(&ctr->near_pairs, 1ull);
+                    const unsigned long long q = atomicAdd(&ctr->near_pairs, 1ull);
                     if ((long long)q < near_cap) {
-                        const int gi = L.gid[i], gj = L.gid[j];
-                        near_ij[2 * q] = gi < gj ? gi : gj;
-                        near_ij[2 * q + 1] = gi < gj ? gj : gi;
+                        const int pi = L.gid[gi], pj = L.gid[gj];
+                        near_ij[2 * q] = pi < pj ? pi : pj;
+                        near_ij[2 * q + 1] = pi < pj ? pj : pi;
                         near_tau[q] = tau;
                     }
                 }
                 dec = tau < P.h ? 1 : 0;
             }
-            if (dec) {
-                ++my_edges;
-                if (!luf_union(sm.lp, tid, joff + k)) raise_err(ctr, DERR_UF_RETRY);
-                // every edge is recorded (the decision at h/2 is left to the
-                // first half's pass: taking it here costs the pair loop
-                // registers); tau = the FP64 value or NaN
-                if (E.rec) record_edge(E, i, j0 + k, -1, tau);
+        }
+        const bool edge = dec > 0;
+        const unsigned eb = __ballot_sync(0xffffffffu, edge);
+        if (eb == 0u) return;
+        if (edge) {
+            ++my_edges;
+            if (!luf_union(sm.lp, ii, joff + kk)) raise_err(ctr, DERR_UF_RETRY);
+        }
+        if (E.rec) {
+            // every edge is recorded (the decision at h/2 is left to the
+            // first half's pass); tau = the FP64 value or NaN.  One counter
+            // update per batch.
+            unsigned long long base = 0;
+            if (lane == 0) base = atomicAdd(E.count, (unsigned long long)__popc(eb));
+            base = __shfl_sync(0xffffffffu, base, 0);
+            const unsigned long long q = base + (unsigned)__popc(eb & lt);
+            if (edge && (long long)q < E.cap) {
+                EdgeRec r;
+                r.a = start + ti * T + ii;
+                r.b = j0 + kk;
+                r.e = -1;
+                r.pad = 0;
+                r.tau = tau;
+                E.rec[q] = r;
             }
         }
+    };
+    int qn = 0;  // entries queued by this warp (warp-uniform)
+    // one trip count for the whole warp (jn is the block's), so the common
+    // case is a vote: every lane's pair certainly apart by the cheap bound on
+    // the high parts
+    for (int k = 0; k < jn; ++k) {
+        const bool mine = iv && (!diag || k > tid);
+        const float4 jp0 = sm.pq[2 * k], jv0 = sm.vq[2 * k];
+        const bool apart = !mine || tau_quick_apart(jp0.x - ip0.x, jp0.y - ip0.y, jp0.z - ip0.z, jv0.x - iv0.x,
+                                                    jv0.y - iv0.y, jv0.z - iv0.z, ip0.w + jp0.w, cXh, cVh, Q);
+        const unsigned open = __ballot_sync(0xffffffffu, !apart);
+        if (open == 0u) continue;
+        if (!apart) sm.q[w][qn + __popc(open & lt)] = ((unsigned)tid << 8) | (unsigned)k;
+        qn += __popc(open);
+        if (qn >= 32) {
+            __syncwarp();
+            settle(32);
+            __syncwarp();
+            if (lane < qn - 32) sm.q[w][lane] = sm.q[w][32 + lane];
+            __syncwarp();
+            qn -= 32;
+        }
+    }
+    if (qn > 0) {
+        __syncwarp();
+        settle(qn);
     }
     __syncthreads();
     // merge the tile's local components into the global forest: one union
