@@ -347,12 +347,14 @@ void launch_tau_mixed(const Level &L, const FFView &F, int ntiles, const TauPara
 // adjacent; rest-set members are their own components).  Grid: (set,
 // i-tile, j-chunk).  Thread r of an i-tile accumulates
 // sum_j G m_j (x_j - x_i) |x_j - x_i|^-3 over the chunk's j whose label
-// differs, in compensated FP32; a j-tile whose labels and the i-tile's are
+// differs in FP32 (groups of MK_GROUP terms, each group sum added with
+// compensation); a j-tile whose labels and the i-tile's are
 // all one component is skipped whole (sorted order: first == last label
 // means a uniform tile).  Partials go to scratch in FP64 unless the set has
 // a single chunk, in which case v is updated directly.
 constexpr int MK_T = 128;
 constexpr int MK_CHUNK_MAX = 16;  // j-tiles per chunk: 1, 4 or 16 (tuned per size bin)
+constexpr int MK_GROUP = 8;       // j terms summed in plain FP32 per compensated addition
 
 struct __align__(16) MixedKickSmem {
     float4 pq[2][2 * MK_T];  // (hi, Gm), (lo) per j, two stages
@@ -437,7 +439,12 @@ __global__ void __launch_bounds__(MK_T) k_kick_mixed(Level L, FFView F, const in
         }
         const int jn = min(MK_T, n - tj * MK_T);
         if (iv) {
-            auto term = [&](int k) {
+            // g += G m_j r^-3 (x_j - x_i) over groups of MK_GROUP j in plain
+            // FP32 (fused), each group sum then added to the compensated
+            // total: the per-term roundings dominate the error either way,
+            // and the compensation costs 4 operations per component
+            float gx, gy, gz;
+            auto term = [&](int k, bool check) {
                 const float4 jp0 = sm.pq[st][2 * k], jp1 = sm.pq[st][2 * k + 1];
                 const float dx = (jp0.x - ip0.x) + (jp1.x - ip1.x);
                 const float dy = (jp0.y - ip0.y) + (jp1.y - ip1.y);
@@ -445,19 +452,33 @@ __global__ void __launch_bounds__(MK_T) k_kick_mixed(Level L, FFView F, const in
                 const float r2 = fmaf(dz, dz, fmaf(dy, dy, fmaf(dx, dx, eps2)));
                 float ri = rsqrtf(r2);
                 ri = ri * fmaf(-0.5f * r2, ri * ri, 1.5f);  // one Newton step
-                const float w = jp0.w * (ri * ri * ri);      // G m_j / r^3
-                kahan_add(sx, cx, w * dx);
-                kahan_add(sy, cy, w * dy);
-                kahan_add(sz, cz, w * dz);
+                float w = jp0.w * (ri * ri * ri);            // G m_j / r^3
+                if (check && sm.lab[st][k] == li) w = 0.f;  // same component (and self)
+                gx = fmaf(w, dx, gx);
+                gy = fmaf(w, dy, gy);
+                gz = fmaf(w, dz, gz);
             };
-            if (sm.apart[q]) {
-#pragma unroll 4
-                for (int k = 0; k < jn; ++k) term(k);
-            } else {
-#pragma unroll 4
-                for (int k = 0; k < jn; ++k)
-                    if (sm.lab[st][k] != li) term(k);  // same component (and self) skipped
-            }
+            auto flush = [&]() {
+                kahan_add(sx, cx, gx);
+                kahan_add(sy, cy, gy);
+                kahan_add(sz, cz, gz);
+            };
+            auto run = [&](bool check) {
+                int k = 0;
+                for (; k + MK_GROUP <= jn; k += MK_GROUP) {
+                    gx = gy = gz = 0.f;
+#pragma unroll
+                    for (int u = 0; u < MK_GROUP; ++u) term(k + u, check);
+                    flush();
+                }
+                if (k < jn) {
+                    gx = gy = gz = 0.f;
+                    for (; k < jn; ++k) term(k, check);
+                    flush();
+                }
+            };
+            if (sm.apart[q]) run(false);
+            else run(true);
         }
         __syncthreads();
     }
