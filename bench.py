@@ -254,6 +254,7 @@ def run_gpu(args, rank, world):
             sampler.start()
         torch.cuda.nvtx.range_push("timed_region")
         total_ms = 0.0
+        step_ms = []
         for _ in range(steps):
             l2_flush.fill_(1)
             torch.cuda.synchronize()
@@ -264,15 +265,18 @@ def run_gpu(args, rank, world):
             ctx.evolve(t)
             e1.record(stream)
             e1.synchronize()
-            total_ms += e0.elapsed_time(e1)
+            step_ms.append(e0.elapsed_time(e1))
+            total_ms += step_ms[-1]
         torch.cuda.synchronize()
         torch.cuda.nvtx.range_pop()
         clocks = sampler.stop() if sampler else None
         st1 = ctx.stats()
         tm = ctx.timing()
+        tuning = ctx.tuning()
         ctx.set_timing(False)
         E1, _, _ = ctx.energy()
-        res = {"ctx": ctx, "t": t, "total_ms": total_ms, "clocks": clocks, "timing": tm,
+        res = {"ctx": ctx, "t": t, "total_ms": total_ms, "step_ms": step_ms, "clocks": clocks, "timing": tm,
+               "tuning": tuning,
                "inter": (st1["tau_pairs"] - st0["tau_pairs"]) + (st1["kick_pairs"] - st0["kick_pairs"]),
                "launches": st1["launches"] - st0["launches"],
                "tau_fp64": st1["tau_fp64"] - st0["tau_fp64"], "tau_pairs": st1["tau_pairs"] - st0["tau_pairs"],
@@ -349,7 +353,14 @@ def run_gpu(args, rank, world):
     if rank == 0:
         line = {
             "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
-            "warmup": args.warmup, "ms_per_step": total_ms / args.steps, "higher_is_better": True,
+            "warmup": args.warmup, "ms_per_step": total_ms / args.steps,
+            "step_ms": [round(x, 4) for x in head["step_ms"]], "higher_is_better": True,
+            # launch shapes the online tuner picked, per kernel and size bin
+            # (pairs in [2^bin, 2^(bin+1))): [kernel, bin, [shape, column
+            # slices] picked, us per 1e6 pairs of each variant]
+            "autotune": [[e["kernel"], e["bin"],
+                          [e["shape"][e["best"]], e["slices"][e["best"]]] if e["best"] >= 0 else None,
+                          e["us_per_mpair"]] for e in head["tuning"]],
             "scaling": "weak", "vs_baseline": None, "dtype": "f32/f64" if fp32 else "f64", "data": "synthetic",
             "config": {"workload": workload_name(N, args.workload, args.nsys), "form": args.form, "h_fp64": f"{args.h_fp64}*dt",
                        "s_small": args.s_small,

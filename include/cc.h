@@ -175,6 +175,33 @@ int cc_near_pairs(cc_ctx *ctx, int32_t *pairs, double *tau, int64_t cap, int64_t
 int cc_set_timing(cc_ctx *ctx, int on);
 int cc_timing(cc_ctx *ctx, cc_timing_t *out);
 
+/* One cell of the launch-shape autotuner: a kernel and a size bin (the
+ * launch's pair count in [2^bin, 2^(bin+1))).  Variant v of the kernel is
+ * the launch shape (shape[v], slices[v]): for the tau kernels the tile edge
+ * (64, 128) and the threads per tile row (its columns split in slices); for
+ * the FP64 kick the tile edge (32, 64, 128), slices 1; for the mixed kick
+ * the j-chunk in tiles of 128 and the column slices of each tile. */
+typedef struct {
+    int32_t kernel;            /* CC_TUNE_TAU_FP64 .. CC_TUNE_KICK_MIXED           */
+    int32_t bin;
+    int32_t best;              /* chosen variant; -1 while variants are tried     */
+    int32_t nvar;              /* variants of this kernel (<= 3)                 */
+    int32_t shape[3];
+    int32_t slices[3];
+    int32_t timed[3];          /* timed launches per variant                      */
+    int32_t reserved;
+    double  us_per_mpair[3];   /* measured microseconds per 1e6 pairs (0: none)   */
+} cc_tune_entry_t;
+
+enum { CC_TUNE_TAU_FP64 = 0, CC_TUNE_TAU_MIXED = 1, CC_TUNE_KICK_FP64 = 2, CC_TUNE_KICK_MIXED = 3 };
+
+/* Copy the autotuner's cells that have at least one timed launch, in
+ * (kernel, bin) order, into out[cap]; *n_out = the number of such cells
+ * (may exceed cap: only cap are written).  Synchronises the context's
+ * stream.  Errors: CC_E_ARG (ctx or n_out NULL, cap < 0, out NULL with
+ * cap > 0), CC_E_CUDA. */
+int cc_tuning(cc_ctx *ctx, cc_tune_entry_t *out, int64_t cap, int64_t *n_out);
+
 /* FMA throughput of the current device, measured by a microbenchmark on
  * `stream` (flop/s, an FMA counting 2): the ALU roofline denominators of
  * the FP64 and FP32 pair kernels.  Errors (message via cc_last_error(NULL)):

@@ -50,6 +50,15 @@ class Timing(C.Structure):
         return {k: getattr(self, k) for k, _ in self._fields_}
 
 
+class TuneEntry(C.Structure):
+    _fields_ = [("kernel", C.c_int32), ("bin", C.c_int32), ("best", C.c_int32), ("nvar", C.c_int32),
+                ("shape", C.c_int32 * 3), ("slices", C.c_int32 * 3), ("timed", C.c_int32 * 3),
+                ("reserved", C.c_int32), ("us_per_mpair", C.c_double * 3)]
+
+
+TUNE_KERNELS = ("tau_fp64", "tau_mixed", "kick_fp64", "kick_mixed")
+
+
 class CCError(RuntimeError):
     def __init__(self, code, msg):
         super().__init__(f"{ERRORS.get(code, code)}: {msg}")
@@ -60,7 +69,7 @@ _lib = None
 
 EXPORTS = ["cc_default_params", "cc_init", "cc_set_systems", "cc_set_stream", "cc_timestep_graph",
            "cc_components", "cc_kick", "cc_drift", "cc_evolve", "cc_get_state", "cc_set_state", "cc_stats",
-           "cc_reset_stats", "cc_energy", "cc_near_pairs", "cc_set_timing", "cc_timing", "cc_probe_peaks",
+           "cc_reset_stats", "cc_energy", "cc_near_pairs", "cc_set_timing", "cc_timing", "cc_tuning", "cc_probe_peaks",
            "cc_components_noalloc", "cc_destroy", "cc_last_error"]
 
 
@@ -90,6 +99,7 @@ def lib():
         L.cc_near_pairs.argtypes = [vp, i32p, dp, i64, C.POINTER(C.c_int64)]
         L.cc_set_timing.argtypes = [vp, C.c_int]
         L.cc_timing.argtypes = [vp, C.POINTER(Timing)]
+        L.cc_tuning.argtypes = [vp, C.POINTER(TuneEntry), i64, C.POINTER(C.c_int64)]
         L.cc_probe_peaks.argtypes = [vp, C.POINTER(C.c_double), C.POINTER(C.c_double)]
         L.cc_components_noalloc.argtypes = [dp, dp, dp, i64, C.POINTER(Params), C.c_double, i32p, vp, vp]
         L.cc_destroy.argtypes = [vp]
@@ -265,6 +275,21 @@ class Context:
         t = Timing()
         self._check(lib().cc_timing(self._h, C.byref(t)))
         return t.as_dict()
+
+    def tuning(self) -> list:
+        """The autotuner's timed cells: one dict per (kernel, size bin)."""
+        n = C.c_int64(0)
+        self._check(lib().cc_tuning(self._h, None, 0, C.byref(n)))
+        k = int(n.value)
+        buf = (TuneEntry * max(1, k))()
+        self._check(lib().cc_tuning(self._h, buf, k, C.byref(n)))
+        out = []
+        for e in buf[:k]:
+            nv = e.nvar
+            out.append({"kernel": TUNE_KERNELS[e.kernel], "bin": e.bin, "best": e.best,
+                        "shape": list(e.shape[:nv]), "slices": list(e.slices[:nv]), "timed": list(e.timed[:nv]),
+                        "us_per_mpair": [round(x, 3) for x in e.us_per_mpair[:nv]]})
+        return out
 
     def near_pairs(self, cap: int = 4096):
         pairs = np.zeros((cap, 2), dtype=np.int32)

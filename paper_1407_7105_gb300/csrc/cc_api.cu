@@ -96,7 +96,7 @@ struct LevelAlloc {
 // choice except through the rounding order of the mixed kick's j-chunks.
 enum TuneKind { TK_TAU64 = 0, TK_TAUMIX = 1, TK_K64 = 2, TK_MK = 3, TK_N = 4 };
 constexpr int TUNE_BINS = 40, TUNE_MAXV = 3, TUNE_TRIALS = 1;
-constexpr int TUNE_NVAR[TK_N] = {N_TAU_VAR, N_TAU_VAR, N_K64_VAR, N_MK_VAR};
+constexpr int TUNE_NVAR[TK_N] = {N_TAU64_VAR, N_TAU_VAR, N_K64_VAR, N_MK_VAR};
 
 struct TuneCell {
     double ms[TUNE_MAXV] = {0, 0, 0}, work[TUNE_MAXV] = {0, 0, 0};
@@ -279,12 +279,23 @@ static int align_up(int v, int a) { return (v + a - 1) / a * a; }
 // variant; *timed tells whether this launch is a tuner sample.  Without
 // autotuning (or before any sample) a rule picks the largest shape that
 // still gives every SM a few blocks.
+// Variants that split tile columns over more threads are only worth trying
+// while the plain variant leaves the GPU short of blocks.
+static bool tune_eligible(const cc_ctx *c, int tkind, const long long *blocks, int v)
+{
+    if (tkind == TK_TAUMIX && TAU_VAR_S[v] > 1) return blocks[0] < 16ll * c->nsm;
+    if (tkind == TK_MK && MK_VAR_SLICE[v] > 1) return blocks[0] < 8ll * c->nsm;
+    return true;
+}
+
 static int tune_pick(cc_ctx *c, int tkind, const long long *blocks, long long work, int *bin_out, bool *timed)
 {
     const int nv = TUNE_NVAR[tkind];
+    bool ok[TUNE_MAXV];
+    for (int v = 0; v < nv; ++v) ok[v] = tune_eligible(c, tkind, blocks, v);
     int rule = 0;
     for (int v = nv - 1; v >= 0; --v)
-        if (blocks[v] >= 3ll * c->nsm) {
+        if (ok[v] && blocks[v] >= 3ll * c->nsm) {
             rule = v;
             break;
         }
@@ -293,13 +304,14 @@ static int tune_pick(cc_ctx *c, int tkind, const long long *blocks, long long wo
     *timed = false;
     if (!c->p_autotune) return rule;
     TuneCell &t = c->tuner.cell[tkind][bin];
-    if (t.best >= 0) return t.best;
+    if (t.best >= 0) return ok[t.best] ? t.best : rule;
     bool all = true;
-    for (int v = 0; v < nv; ++v) all = all && t.timed[v] >= TUNE_TRIALS;
+    for (int v = 0; v < nv; ++v) all = all && (!ok[v] || t.timed[v] >= TUNE_TRIALS);
     if (all) {
-        int best = 0;
+        int best = rule;
         double bq = 1e300;
         for (int v = 0; v < nv; ++v) {
+            if (!ok[v]) continue;
             const double q = t.ms[v] / (t.work[v] > 0 ? t.work[v] : 1.0);
             if (q < bq) {
                 bq = q;
@@ -312,7 +324,7 @@ static int tune_pick(cc_ctx *c, int tkind, const long long *blocks, long long wo
     // explore: the rule's choice first, then the others, fewest picks first
     int pick = rule, fewest = t.picked[rule];
     for (int v = 0; v < nv; ++v)
-        if (t.picked[v] < fewest) {
+        if (ok[v] && t.picked[v] < fewest) {
             fewest = t.picked[v];
             pick = v;
         }
@@ -422,7 +434,7 @@ static int ensure_level(cc_ctx *c, LevelAlloc &a, int need, int nsets)
         for (int v = 0; v < N_TAU_VAR; ++v) { a.tau_off[v] = sq; sq += sc; }
         for (int v = 0; v < N_K64_VAR; ++v) { a.k64_off[v] = sq; sq += sc; }
         for (int v = 0; v < N_MK_VAR; ++v) { a.mk_off[v] = sq; sq += sc; }
-        a.L.tile_off = a.tau_off[N_TAU_VAR - 1];
+        a.L.tile_off = a.tau_off[TAU_VAR_128];
         a.L.itile_off = a.k64_off[1];
         a.L.koff = a.mk_off[1];
         a.set_cap = sc;
@@ -498,7 +510,7 @@ static void make_layout(const std::vector<int32_t> &sizes, SetLayout &S)
         }
         for (int v = 0; v < N_MK_VAR; ++v) {
             S.mk_off[v][s] = (int32_t)mb[v];
-            mb[v] += mixed_kick_blocks((int)n, MK_VAR_CHUNK[v]);
+            mb[v] += mixed_kick_blocks((int)n, MK_VAR_CHUNK[v], MK_VAR_SLICE[v]);
             S.mk_chunks_max[v] = std::max(S.mk_chunks_max[v], mixed_kick_chunks((int)n, MK_VAR_CHUNK[v]));
         }
     }
@@ -682,7 +694,7 @@ static int level_kick(cc_ctx *c, LevelAlloc &a, const int32_t *lab, const int32_
         const int var = tune_pick(c, TK_MK, a.mk_blocks, a.pairs, &bin, &timed);
         CC_TRY(ensure_kpart(c, a.mk_chunks_max[var], a.F.cap));
         const int ev = ev_begin(c, 1, nullptr, timed ? TK_MK : -1, bin, var, (double)a.pairs);
-        launch_kick_mixed(L, a.F, order, a.mk_off[var], (int)a.mk_blocks[var], MK_VAR_CHUNK[var],
+        launch_kick_mixed(L, a.F, order, a.mk_off[var], (int)a.mk_blocks[var], MK_VAR_CHUNK[var], MK_VAR_SLICE[var],
                           a.mk_chunks_max[var] > 1, c->p.eps * c->p.eps, h, c->d_ctr, c->d_kpart, lab, drift_dt, s);
         ev_end(c, ev);
     } else {
@@ -1096,9 +1108,9 @@ int cc_timestep_graph(cc_ctx *c, const int32_t *set, int64_t n_set, double h, in
     const TauParams P = tau_params(c, h);
     const long long nt = (n_set + TAU_TILE - 1) / TAU_TILE;
     Level UL = u.L;
-    UL.tile_off = u.tau_off[N_TAU_VAR - 1];  // 128-wide tiles
+    UL.tile_off = u.tau_off[TAU_VAR_128];  // 128-wide tiles
     launch_init_parent(u.L, nullptr, c->stream);
-    launch_tau_hook(UL, (int)(nt * (nt + 1) / 2), P, N_TAU_VAR - 1, c->d_ctr, nullptr, 0, c->d_near_ij,
+    launch_tau_hook(UL, (int)(nt * (nt + 1) / 2), P, TAU_VAR_128, c->d_ctr, nullptr, 0, c->d_near_ij,
                     c->d_near_tau, c->near_cap, c->stream);
     DevCounters h1;
     CC_CUDA(c, cudaMemcpyAsync(&h1, c->d_ctr, sizeof(h1), cudaMemcpyDeviceToHost, c->stream));
@@ -1118,7 +1130,7 @@ int cc_timestep_graph(cc_ctx *c, const int32_t *set, int64_t n_set, double h, in
         void *ss = (void *)(de + 2 * ne);
         CC_TRY(reset_call_counters(c));
         launch_init_parent(u.L, nullptr, c->stream);
-        launch_tau_hook(UL, (int)(nt * (nt + 1) / 2), P, N_TAU_VAR - 1, c->d_ctr, de, ne, c->d_near_ij,
+        launch_tau_hook(UL, (int)(nt * (nt + 1) / 2), P, TAU_VAR_128, c->d_ctr, de, ne, c->d_near_ij,
                         c->d_near_tau, c->near_cap, c->stream);
         int bits = 0;
         while (bits < 31 && (1ll << bits) <= c->n) ++bits;
@@ -1248,6 +1260,44 @@ int cc_timing(cc_ctx *c, cc_timing_t *out)
     CC_CUDA(c, cudaStreamSynchronize(c->stream));
     ev_resolve(c);
     *out = c->tm;
+    return CC_OK;
+}
+
+int cc_tuning(cc_ctx *c, cc_tune_entry_t *out, int64_t cap, int64_t *n_out)
+{
+    if (!c || !n_out || cap < 0 || (!out && cap > 0)) return CC_E_ARG;
+    CC_CUDA(c, cudaStreamSynchronize(c->stream));
+    ev_resolve(c);
+    static_assert(TK_TAU64 == CC_TUNE_TAU_FP64 && TK_TAUMIX == CC_TUNE_TAU_MIXED && TK_K64 == CC_TUNE_KICK_FP64 &&
+                      TK_MK == CC_TUNE_KICK_MIXED,
+                  "tuner kinds");
+    int64_t n = 0;
+    for (int k = 0; k < TK_N; ++k)
+        for (int b = 0; b < TUNE_BINS; ++b) {
+            const TuneCell &t = c->tuner.cell[k][b];
+            const int nv = TUNE_NVAR[k];
+            bool any = false;
+            for (int v = 0; v < nv; ++v) any = any || t.timed[v] > 0;
+            if (!any) continue;
+            if (n < cap) {
+                cc_tune_entry_t e{};
+                e.kernel = k;
+                e.bin = b;
+                e.best = t.best;
+                e.nvar = nv;
+                for (int v = 0; v < nv; ++v) {
+                    e.shape[v] = (k == TK_TAU64 || k == TK_TAUMIX) ? TAU_VAR_T[v]
+                                 : k == TK_K64                    ? K64_VAR_T[v]
+                                                                  : MK_VAR_CHUNK[v];
+                    e.slices[v] = k == TK_TAUMIX ? TAU_VAR_S[v] : k == TK_MK ? MK_VAR_SLICE[v] : 1;
+                    e.timed[v] = t.timed[v];
+                    e.us_per_mpair[v] = t.work[v] > 0 ? 1e9 * t.ms[v] / t.work[v] : 0.0;
+                }
+                out[n] = e;
+            }
+            ++n;
+        }
+    *n_out = n;
     return CC_OK;
 }
 

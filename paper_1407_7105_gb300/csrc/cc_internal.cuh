@@ -273,12 +273,19 @@ extern unsigned long long g_launches;
 
 // cc_pair.cu
 void launch_init_parent(const Level &L, unsigned long long *edge_count, cudaStream_t s);
-// tunable launch shapes (variant index): tau tiles {64, 128}; FP64 kick
-// tiles {32, 64, 128}; mixed kick j-chunks {1, 4, 16} tiles of 128
-constexpr int N_TAU_VAR = 2, N_K64_VAR = 3, N_MK_VAR = 3;
-constexpr int TAU_VAR_T[N_TAU_VAR] = {64, 128};
+// tunable launch shapes (variant index): tau tiles {64, 128, 64 in two
+// column slices}; FP64 kick tiles {32, 64, 128}; mixed kick (j-chunk in
+// tiles of 128, column slices) {(1, 1), (4, 1), (1, 4)}
+constexpr int N_TAU_VAR = 3, N_K64_VAR = 3, N_MK_VAR = 3;
+// tau variants: tile edge T and column slices S per tile row (the FP64
+// kernel takes the first two)
+constexpr int TAU_VAR_T[N_TAU_VAR] = {64, 128, 64};
+constexpr int TAU_VAR_S[N_TAU_VAR] = {1, 1, 2};
+constexpr int N_TAU64_VAR = 2, TAU_VAR_128 = 1;
+static_assert(TAU_VAR_T[TAU_VAR_128] == 128 && TAU_VAR_S[TAU_VAR_128] == 1, "128-wide tau tiles");
 constexpr int K64_VAR_T[N_K64_VAR] = {32, 64, 128};
-constexpr int MK_VAR_CHUNK[N_MK_VAR] = {1, 4, 16};
+constexpr int MK_VAR_CHUNK[N_MK_VAR] = {1, 4, 1};
+constexpr int MK_VAR_SLICE[N_MK_VAR] = {1, 1, 4};
 constexpr int MK_TILE = 128;
 void launch_tau_hook(const Level &L, int ntiles, const TauParams &P, int variant, DevCounters *ctr,
                      int32_t *edges, long long edge_cap, int32_t *near_ij, double *near_tau, long long near_cap,
@@ -341,7 +348,7 @@ void launch_prep_ff(const Level &L, const FFView &F, double G, bool with_v, cuda
 void launch_tau_mixed(const Level &L, const FFView &F, int ntiles, const TauParams &P, int variant,
                       DevCounters *ctr, int32_t *near_ij, double *near_tau, long long near_cap, const EdgeList &rec,
                       cudaStream_t s);
-int mixed_kick_blocks(int n, int chunk);
+int mixed_kick_blocks(int n, int chunk, int slices);
 int mixed_kick_chunks(int n, int chunk);
 // drift_dt > 0: the level's drift of rest-set members (component size 1 by
 // root) fused in: before the positions are copied (prep), after the kick
@@ -349,8 +356,8 @@ int mixed_kick_chunks(int n, int chunk);
 void launch_prep_kick(const Level &L, const FFView &F, const int32_t *order, const int32_t *root, double G,
                       double drift_dt, cudaStream_t s);
 void launch_kick_mixed(const Level &L, const FFView &F, const int32_t *order, const int32_t *koff, int nblocks,
-                       int chunk, bool multi_chunk, double eps2, double h, DevCounters *ctr, double *partial,
-                       const int32_t *root, double drift_dt, cudaStream_t s);
+                       int chunk, int slices, bool multi_chunk, double eps2, double h, DevCounters *ctr,
+                       double *partial, const int32_t *root, double drift_dt, cudaStream_t s);
 
 // cc_small.cu
 void launch_small(const Level &L, const int32_t *members, const int32_t *comp_start, const int32_t *comp_size,

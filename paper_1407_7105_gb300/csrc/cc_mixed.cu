@@ -102,14 +102,29 @@ void launch_prep_kick(const Level &L, const FFView &F, const int32_t *order, con
 }
 
 
-template <int T>
+template <int T, int S>
 struct __align__(16) MixedTauSmem {
     float4 pq[2 * T];   // positions (hi, Gm), (lo) of the j-tile
     float4 vq[2 * T];   // velocities (hi), (lo)
     int32_t lp[2 * T];  // local union-find over the tile's particles
-    uint32_t q[T / 32][64];  // per warp: pairs waiting for the certified decision
+    uint32_t q[T * S / 32][64];  // per warp: pairs waiting for the certified decision
     uint64_t bar;
 };
+
+// Row ti and column offset of triangular tile t (tiles (ti, tj), tj >= ti,
+// numbered row by row; row ti starts at ti nt - ti (ti - 1) / 2): the root of
+// the quadratic in single precision, then exact integer corrections.
+__device__ __forceinline__ int tri_tile_row(int &t, int nt)
+{
+    auto off = [nt](int x) { return x * nt - (x * (x - 1)) / 2; };
+    const float b = 2.f * (float)nt + 1.f;
+    int ti = (int)(0.5f * (b - sqrtf(fmaxf(b * b - 8.f * (float)t, 0.f))));
+    ti = max(0, min(ti, nt - 1));
+    while (ti > 0 && off(ti) > t) --ti;
+    while (ti + 1 < nt && off(ti + 1) <= t) ++ti;
+    t -= off(ti);
+    return ti;
+}
 
 // local union-find in shared memory (indices 0..2T-1, links to the smaller)
 __device__ __forceinline__ int luf_find(volatile int32_t *p, int x)
@@ -150,13 +165,17 @@ __device__ __noinline__ int tau_decide_fp32_ool(float dx0, float dx1, float dx2,
     return tau_decide_fp32(dx0, dx1, dx2, dv0, dv1, dv2, mu, c_x, c_v, Q);
 }
 
-template <int T>
-__global__ void __launch_bounds__(T, 1024 / T) k_tau_mixed(Level L, FFView F, TauParams P, MixedTauParams Q,
+// Block = T x S threads: thread (row r, slice s) takes pairs (r, k) of the
+// tile with k in the slice's T/S columns (S > 1 shortens each warp's chain
+// for sets with few tiles).
+template <int T, int S>
+__global__ void __launch_bounds__(T * S, 1024 / (T * S)) k_tau_mixed(Level L, FFView F, TauParams P, MixedTauParams Q,
                                                      DevCounters *ctr, int32_t *near_ij, double *near_tau,
                                                      long long near_cap, EdgeList E)
 {
-    __shared__ MixedTauSmem<T> sm;
-    const int tid = threadIdx.x;
+    static_assert(T % 32 == 0 && T % S == 0, "tile shape");
+    __shared__ MixedTauSmem<T, S> sm;
+    const int tid = threadIdx.x, row = tid % T, slice = tid / T;
     int lo = 0, hi = L.nsets;
     while (hi - lo > 1) {
         const int mid = (lo + hi) >> 1;
@@ -166,11 +185,7 @@ __global__ void __launch_bounds__(T, 1024 / T) k_tau_mixed(Level L, FFView F, Ta
     int t = blockIdx.x - L.tile_off[s];
     const int n = L.set_n[s], start = L.set_start[s];
     const int nt = (n + T - 1) / T;
-    int ti = 0;
-    while (t >= nt - ti) {
-        t -= nt - ti;
-        ++ti;
-    }
+    const int ti = tri_tile_row(t, nt);
     const int tj = ti + t;
     const bool diag = ti == tj;
     const int j0 = start + tj * T;
@@ -179,8 +194,7 @@ __global__ void __launch_bounds__(T, 1024 / T) k_tau_mixed(Level L, FFView F, Ta
         mbar_init(&sm.bar, 1);
         fence_mbar_init();
     }
-    sm.lp[tid] = tid;
-    sm.lp[T + tid] = T + tid;
+    for (int e = tid; e < 2 * T; e += T * S) sm.lp[e] = e;
     __syncthreads();
     if (tid == 0) {
         const unsigned bytes = (unsigned)jn * 32u;
@@ -188,7 +202,7 @@ __global__ void __launch_bounds__(T, 1024 / T) k_tau_mixed(Level L, FFView F, Ta
         tma_load_1d(sm.pq, F.pq + 2 * (size_t)j0, bytes, &sm.bar);
         tma_load_1d(sm.vq, F.vq + 2 * (size_t)j0, bytes, &sm.bar);
     }
-    const int il = ti * T + tid;
+    const int il = ti * T + row;
     const bool iv = il < n;
     const int i = start + il;
     float4 ip0 = make_float4(0, 0, 0, 0), ip1 = ip0, iv0 = ip0, iv1 = ip0;
@@ -220,7 +234,7 @@ __global__ void __launch_bounds__(T, 1024 / T) k_tau_mixed(Level L, FFView F, Ta
     auto settle = [&](int cnt) {
         const bool has = lane < cnt;
         const unsigned ent = has ? sm.q[w][lane] : 0u;
-        const int ii = has ? (int)(ent >> 8) : tid, kk = (int)(ent & 255u);
+        const int ii = has ? (int)(ent >> 8) : row, kk = (int)(ent & 255u);
         const int src = ii & 31;  // the owner of body i is a lane of this warp
         const float4 a0 = shfl4(ip0, src), a1 = shfl4(ip1, src), b0 = shfl4(iv0, src), b1 = shfl4(iv1, src);
         int dec = 0;
@@ -280,14 +294,15 @@ __global__ void __launch_bounds__(T, 1024 / T) k_tau_mixed(Level L, FFView F, Ta
     // one trip count for the whole warp (jn is the block's), so the common
     // case is a vote: every lane's pair certainly apart by the cheap bound on
     // the high parts
-    for (int k = 0; k < jn; ++k) {
-        const bool mine = iv && (!diag || k > tid);
+    const int k1 = min(jn, (slice + 1) * (T / S));
+    for (int k = slice * (T / S); k < k1; ++k) {
+        const bool mine = iv && (!diag || k > row);
         const float4 jp0 = sm.pq[2 * k], jv0 = sm.vq[2 * k];
         const bool apart = !mine || tau_quick_apart(jp0.x - ip0.x, jp0.y - ip0.y, jp0.z - ip0.z, jv0.x - iv0.x,
                                                     jv0.y - iv0.y, jv0.z - iv0.z, ip0.w + jp0.w, cXh, cVh, Q);
         const unsigned open = __ballot_sync(0xffffffffu, !apart);
         if (open == 0u) continue;
-        if (!apart) sm.q[w][qn + __popc(open & lt)] = ((unsigned)tid << 8) | (unsigned)k;
+        if (!apart) sm.q[w][qn + __popc(open & lt)] = ((unsigned)row << 8) | (unsigned)k;
         qn += __popc(open);
         if (qn >= 32) {
             __syncwarp();
@@ -305,7 +320,7 @@ __global__ void __launch_bounds__(T, 1024 / T) k_tau_mixed(Level L, FFView F, Ta
     __syncthreads();
     // merge the tile's local components into the global forest: one union
     // per local non-root element instead of one per edge
-    for (int e = tid; e < (diag ? T : 2 * T); e += T) {
+    for (int e = tid; e < (diag ? T : 2 * T); e += T * S) {
         const int r = luf_find(sm.lp, e);
         if (r != e) {
             const int ge = (e < T) ? start + ti * T + e : j0 + (e - T);
@@ -335,10 +350,14 @@ void launch_tau_mixed(const Level &L, const FFView &F, int ntiles, const TauPara
     Q.eps2 = (float)P.eps2;
     Q.G = (float)P.G;
     Q.hq = (float)(P.eta_outside ? P.h / P.eta : P.h);  // h/eta_in in the units of T: eta_in/etah
+    static_assert(TAU_VAR_T[0] == 64 && TAU_VAR_T[1] == 128 && TAU_VAR_T[2] == 64 && TAU_VAR_S[2] == 2,
+                  "tau variants");
     if (variant == 0)
-        k_tau_mixed<64><<<ntiles, 64, 0, s>>>(L, F, P, Q, ctr, near_ij, near_tau, near_cap, E);
+        k_tau_mixed<64, 1><<<ntiles, 64, 0, s>>>(L, F, P, Q, ctr, near_ij, near_tau, near_cap, E);
+    else if (variant == 1)
+        k_tau_mixed<128, 1><<<ntiles, 128, 0, s>>>(L, F, P, Q, ctr, near_ij, near_tau, near_cap, E);
     else
-        k_tau_mixed<128><<<ntiles, 128, 0, s>>>(L, F, P, Q, ctr, near_ij, near_tau, near_cap, E);
+        k_tau_mixed<64, 2><<<ntiles, 128, 0, s>>>(L, F, P, Q, ctr, near_ij, near_tau, near_cap, E);
     CC_COUNT_LAUNCH(1);
 }
 
@@ -353,7 +372,9 @@ void launch_tau_mixed(const Level &L, const FFView &F, int ntiles, const TauPara
 // means a uniform tile).  Partials go to scratch in FP64 unless the set has
 // a single chunk, in which case v is updated directly.
 constexpr int MK_T = 128;
-constexpr int MK_CHUNK_MAX = 16;  // j-tiles per chunk: 1, 4 or 16 (tuned per size bin)
+constexpr int MK_CHUNK_MAX = 4;  // j-tiles per chunk (tuned per size bin)
+static_assert(MK_VAR_CHUNK[0] <= MK_CHUNK_MAX && MK_VAR_CHUNK[1] <= MK_CHUNK_MAX && MK_VAR_CHUNK[2] <= MK_CHUNK_MAX,
+              "chunk variants");
 constexpr int MK_GROUP = 8;       // j terms summed in plain FP32 per compensated addition
 
 struct __align__(16) MixedKickSmem {
@@ -375,12 +396,18 @@ __device__ __forceinline__ void mk_issue(MixedKickSmem &sm, int st, const FFView
     tma_load_1d(sm.lab[st], label + j0, cnt * 4u, &sm.bar[st]);
 }
 
+// Block = MK_T threads = (MK_T / S rows of the i-tile) x (S column slices of
+// each j-tile); the S partial sums of a row are combined in slice order.
+template <int S>
 __global__ void __launch_bounds__(MK_T) k_kick_mixed(Level L, FFView F, const int32_t *order, const int32_t *koff,
                                                       int chunk, float eps2, double h, DevCounters *ctr,
                                                       double *partial)
 {
+    constexpr int R = MK_T / S;  // i rows per block
+    static_assert(R % 32 == 0, "one slice per warp");
     __shared__ MixedKickSmem sm;
-    const int tid = threadIdx.x;
+    __shared__ double red[S > 1 ? S : 1][3][R];
+    const int tid = threadIdx.x, row = tid % R, slice = tid / R;
     int lo = 0, hi = L.nsets;
     while (hi - lo > 1) {
         const int mid = (lo + hi) >> 1;
@@ -393,7 +420,7 @@ __global__ void __launch_bounds__(MK_T) k_kick_mixed(Level L, FFView F, const in
     const int nchunk = (ntile + chunk - 1) / chunk;
     const int ti = b / nchunk, ch = b % nchunk;
     const int tj0 = ch * chunk, tj1 = min(ntile, tj0 + chunk);
-    const int il = ti * MK_T + tid;
+    const int il = ti * R + row;
     const bool iv = il < n;
     const int t = start + il;  // position in the sorted order
     const int32_t *label = L.klab;
@@ -402,7 +429,7 @@ __global__ void __launch_bounds__(MK_T) k_kick_mixed(Level L, FFView F, const in
         mbar_init(&sm.bar[1], 1);
         fence_mbar_init();
         // tiles with at least one cross-component pair
-        const int ia = start + ti * MK_T, ib = start + min(n, (ti + 1) * MK_T) - 1;
+        const int ia = start + ti * R, ib = start + min(n, (ti + 1) * R) - 1;
         const bool iu = label[ia] == label[ib];
         int q = 0;
         for (int tj = tj0; tj < tj1; ++tj) {
@@ -464,16 +491,17 @@ __global__ void __launch_bounds__(MK_T) k_kick_mixed(Level L, FFView F, const in
                 kahan_add(sz, cz, gz);
             };
             auto run = [&](bool check) {
-                int k = 0;
-                for (; k + MK_GROUP <= jn; k += MK_GROUP) {
+                int k = slice * (MK_T / S);
+                const int k1 = min(jn, k + MK_T / S);
+                for (; k + MK_GROUP <= k1; k += MK_GROUP) {
                     gx = gy = gz = 0.f;
 #pragma unroll
                     for (int u = 0; u < MK_GROUP; ++u) term(k + u, check);
                     flush();
                 }
-                if (k < jn) {
+                if (k < k1) {
                     gx = gy = gz = 0.f;
-                    for (; k < jn; ++k) term(k, check);
+                    for (; k < k1; ++k) term(k, check);
                     flush();
                 }
             };
@@ -488,8 +516,20 @@ __global__ void __launch_bounds__(MK_T) k_kick_mixed(Level L, FFView F, const in
         mbar_wait(&sm.bar[1], 0, TMA_WAIT_CYCLES);
         return;
     }
+    double ax = (double)sx - (double)cx, ay = (double)sy - (double)cy, az = (double)sz - (double)cz;
+    if constexpr (S > 1) {
+        red[slice][0][row] = ax;
+        red[slice][1][row] = ay;
+        red[slice][2][row] = az;
+        __syncthreads();
+        if (slice != 0) return;
+        for (int q = 1; q < S; ++q) {
+            ax += red[q][0][row];
+            ay += red[q][1][row];
+            az += red[q][2][row];
+        }
+    }
     if (!iv) return;
-    const double ax = (double)sx - (double)cx, ay = (double)sy - (double)cy, az = (double)sz - (double)cz;
     if (nchunk == 1) {
         const int k = order[t];
         L.vx[k] += h * ax;
@@ -554,10 +594,10 @@ __global__ void k_kick_reduce(Level L, FFView F, const int32_t *order, int chunk
     }
 }
 
-int mixed_kick_blocks(int n, int chunk)
+int mixed_kick_blocks(int n, int chunk, int slices)
 {
-    const int ntile = (n + MK_T - 1) / MK_T;
-    return ntile * ((ntile + chunk - 1) / chunk);
+    const int ntile = (n + MK_T - 1) / MK_T, rows = MK_T / slices;
+    return ((n + rows - 1) / rows) * ((ntile + chunk - 1) / chunk);
 }
 
 int mixed_kick_chunks(int n, int chunk)
@@ -567,11 +607,14 @@ int mixed_kick_chunks(int n, int chunk)
 }
 
 void launch_kick_mixed(const Level &L, const FFView &F, const int32_t *order, const int32_t *koff, int nblocks,
-                       int chunk, bool multi_chunk, double eps2, double h, DevCounters *ctr, double *partial,
-                       const int32_t *root, double drift_dt, cudaStream_t s)
+                       int chunk, int slices, bool multi_chunk, double eps2, double h, DevCounters *ctr,
+                       double *partial, const int32_t *root, double drift_dt, cudaStream_t s)
 {
     if (nblocks > 0) {
-        k_kick_mixed<<<nblocks, MK_T, 0, s>>>(L, F, order, koff, chunk, (float)eps2, h, ctr, partial);
+        if (slices == 4)
+            k_kick_mixed<4><<<nblocks, MK_T, 0, s>>>(L, F, order, koff, chunk, (float)eps2, h, ctr, partial);
+        else
+            k_kick_mixed<1><<<nblocks, MK_T, 0, s>>>(L, F, order, koff, chunk, (float)eps2, h, ctr, partial);
         CC_COUNT_LAUNCH(1);
     }
     if ((multi_chunk && nblocks > 0) || (drift_dt > 0.0 && L.total > 0)) {

@@ -199,6 +199,27 @@ def test_launch_shapes_do_not_change_fp64_results(cclib, plummer_ic):
     assert _rel_ok(out[1][0], s.x3, 1e-10) and _rel_ok(out[1][1], s.v3, 1e-10)
 
 
+def test_tuning_table_reports_the_tried_shapes(cclib, plummer_ic):
+    """cc_tuning lists every (kernel, size bin) cell with a timed launch;
+    once a cell has timed every variant it holds a choice among them."""
+    m, x, v = plummer_ic(1000)
+    c = cclib.Context(m, x, v, dt=1 / 128, precision=cclib.PREC_MIXED)
+    c.evolve(6 / 128)
+    cells = c.tuning()
+    c.close()
+    assert cells and {e["kernel"] for e in cells} <= {"tau_mixed", "kick_mixed"}
+    shapes = {"tau_mixed": ([64, 128, 64], [1, 1, 2]), "kick_mixed": ([1, 4, 1], [1, 1, 4])}
+    for e in cells:
+        assert (e["shape"], e["slices"]) == shapes[e["kernel"]], e
+        assert -1 <= e["best"] < len(e["shape"]), e
+        if e["best"] >= 0:
+            # variants that split tile columns are tried only for launches
+            # with few blocks; every other variant has been timed
+            assert e["timed"][e["best"]] >= 1 and e["us_per_mpair"][e["best"]] > 0, e
+            assert all(t >= 1 for t, sl in zip(e["timed"], e["slices"]) if sl == 1), e
+    assert any(e["best"] >= 0 for e in cells)
+
+
 @pytest.mark.parametrize("s_small", [0, 32])
 def test_first_half_splits_from_parent_records(cclib, plummer_ic, s_small):
     """A first-half split takes its edges from the parent split's tau values
