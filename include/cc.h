@@ -190,7 +190,7 @@ typedef struct {
     int32_t slices[3];
     int32_t timed[3];          /* timed launches per variant                      */
     int32_t reserved;
-    double  us_per_mpair[3];   /* measured microseconds per 1e6 pairs (0: none)   */
+    double  us_per_mpair[3];   /* fastest timed launch: microseconds per 1e6 pairs (0: none) */
 } cc_tune_entry_t;
 
 enum { CC_TUNE_TAU_FP64 = 0, CC_TUNE_TAU_MIXED = 1, CC_TUNE_KICK_FP64 = 2, CC_TUNE_KICK_MIXED = 3 };

@@ -91,15 +91,18 @@ struct LevelAlloc {
 // ------------------------------------------------------------ autotuner
 // Online tuner of launch shapes per (kernel, size bin): the first launches
 // of a bin try each variant (preference order first) while CUDA events time
-// them; once every variant has TUNE_TRIALS timed launches, the one with the
-// least time per pair is kept for the bin.  Results do not depend on the
+// them; once every variant has its trials (one for launches of at least
+// 2^24 pairs, three below, where a launch lasts a few microseconds and a
+// single timing is noisy), the one with the least time per pair over its
+// fastest trial is kept for the bin.  Results do not depend on the
 // choice except through the rounding order of the mixed kick's j-chunks.
 enum TuneKind { TK_TAU64 = 0, TK_TAUMIX = 1, TK_K64 = 2, TK_MK = 3, TK_N = 4 };
-constexpr int TUNE_BINS = 40, TUNE_MAXV = 3, TUNE_TRIALS = 1;
+constexpr int TUNE_BINS = 40, TUNE_MAXV = 3, TUNE_BIG_BIN = 24;
 constexpr int TUNE_NVAR[TK_N] = {N_TAU64_VAR, N_TAU_VAR, N_K64_VAR, N_MK_VAR};
 
 struct TuneCell {
-    double ms[TUNE_MAXV] = {0, 0, 0}, work[TUNE_MAXV] = {0, 0, 0};
+    double qmin[TUNE_MAXV] = {0, 0, 0};  // fastest trial: ms per unit of work
+    double work[TUNE_MAXV] = {0, 0, 0};
     int picked[TUNE_MAXV] = {0, 0, 0}, timed[TUNE_MAXV] = {0, 0, 0};
     int best = -1;
 };
@@ -125,6 +128,11 @@ struct cc_ctx {
     double *d_x3 = nullptr, *d_v3 = nullptr, *d_m = nullptr;
     std::vector<int64_t> sys_off;
     int32_t *d_sys_off = nullptr;
+    // mixed form, one system: level 0 in a Morton order of the positions
+    // (perm[id] = offset), renewed every SPATIAL_RENEW outer steps
+    int32_t *d_perm = nullptr;
+    unsigned *d_box = nullptr;
+    long long perm_age = -1;
     std::vector<LevelAlloc> lv;  // recursion levels
     LevelAlloc unit;             // staging level of the unit entry points
     void *seg_scratch = nullptr;
@@ -202,7 +210,8 @@ static void ev_resolve(cc_ctx *c)
         const cc_ctx::EvRec &r = c->ev_rec[q];
         if (r.tkind >= 0) {
             TuneCell &t = c->tuner.cell[r.tkind][r.bin];
-            t.ms[r.var] += ms;
+            const double q = ms / (r.work > 0 ? r.work : 1.0);
+            if (t.timed[r.var] == 0 || q < t.qmin[r.var]) t.qmin[r.var] = q;
             t.work[r.var] += r.work;
             t.timed[r.var]++;
         }
@@ -305,14 +314,15 @@ static int tune_pick(cc_ctx *c, int tkind, const long long *blocks, long long wo
     if (!c->p_autotune) return rule;
     TuneCell &t = c->tuner.cell[tkind][bin];
     if (t.best >= 0) return ok[t.best] ? t.best : rule;
+    const int trials = bin >= TUNE_BIG_BIN ? 1 : 3;
     bool all = true;
-    for (int v = 0; v < nv; ++v) all = all && (!ok[v] || t.timed[v] >= TUNE_TRIALS);
+    for (int v = 0; v < nv; ++v) all = all && (!ok[v] || t.timed[v] >= trials);
     if (all) {
         int best = rule;
         double bq = 1e300;
         for (int v = 0; v < nv; ++v) {
             if (!ok[v]) continue;
-            const double q = t.ms[v] / (t.work[v] > 0 ? t.work[v] : 1.0);
+            const double q = t.qmin[v];
             if (q < bq) {
                 bq = q;
                 best = v;
@@ -1008,6 +1018,7 @@ int cc_set_state(cc_ctx *c, double t, const double *m, const double *x3, const d
     if (x3) CC_CUDA(c, cudaMemcpyAsync(c->d_x3, sx, 3 * n * 8, cudaMemcpyDeviceToDevice, c->stream));
     if (v3) CC_CUDA(c, cudaMemcpyAsync(c->d_v3, sv, 3 * n * 8, cudaMemcpyDeviceToDevice, c->stream));
     c->t = t;
+    c->perm_age = -1;  // a new state: renew the spatial order
     return CC_OK;
 }
 
@@ -1035,8 +1046,19 @@ int cc_evolve(cc_ctx *c, double t_end, double eta)
         return fail(c, CC_E_ARG, "cc_evolve: t_end - t is not a whole number of steps dt");
     CC_TRY(reset_call_counters(c));
     const double t0 = c->t;
+    const bool spatial = c->p.precision == CC_PREC_MIXED && c->sys_off.size() == 2 && c->n >= SPATIAL_MIN_N;
     for (long long k = 0; k < nsteps; ++k) {
-        launch_pack_state(c->d_x3, c->d_v3, c->d_m, c->n, c->lv[0].L, c->d_sys_off, c->stream);
+        if (spatial && (c->perm_age < 0 || c->perm_age >= SPATIAL_RENEW)) {
+            if (!c->d_perm) {
+                CC_CUDA(c, cudaMalloc(&c->d_perm, (size_t)c->n * 4));
+                CC_CUDA(c, cudaMalloc(&c->d_box, 8 * sizeof(unsigned)));
+            }
+            launch_spatial_order(c->d_x3, c->n, c->d_perm, c->d_box, c->seg_scratch, c->stream);
+            c->perm_age = 0;
+        }
+        launch_pack_state(c->d_x3, c->d_v3, c->d_m, c->n, c->lv[0].L, c->d_sys_off, spatial ? c->d_perm : nullptr,
+                          c->stream);
+        if (spatial) ++c->perm_age;
         int rc = process(c, 0, c->p.dt, nullptr);
         if (rc) return rc;
         launch_unpack_state(c->d_x3, c->d_v3, c->n, c->lv[0].L, c->stream);
@@ -1291,7 +1313,7 @@ int cc_tuning(cc_ctx *c, cc_tune_entry_t *out, int64_t cap, int64_t *n_out)
                                                                   : MK_VAR_CHUNK[v];
                     e.slices[v] = k == TK_TAUMIX ? TAU_VAR_S[v] : k == TK_MK ? MK_VAR_SLICE[v] : 1;
                     e.timed[v] = t.timed[v];
-                    e.us_per_mpair[v] = t.work[v] > 0 ? 1e9 * t.ms[v] / t.work[v] : 0.0;
+                    e.us_per_mpair[v] = t.timed[v] > 0 ? 1e9 * t.qmin[v] : 0.0;
                 }
                 out[n] = e;
             }
@@ -1314,7 +1336,7 @@ int cc_destroy(cc_ctx *c)
     for (auto &a : c->lv) free_level(a);
     free_level(c->unit);
     void *ptrs[] = {c->d_x3, c->d_v3, c->d_m, c->d_ctr, c->d_near_ij, c->d_near_tau, c->d_partial,
-                    c->tmp, c->seg_scratch, c->d_sys_off, c->d_bad, c->d_kpart};
+                    c->tmp, c->seg_scratch, c->d_sys_off, c->d_bad, c->d_kpart, c->d_perm, c->d_box};
     for (void *q : ptrs)
         if (q) cudaFree(q);
     delete c;

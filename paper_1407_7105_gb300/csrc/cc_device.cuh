@@ -157,6 +157,66 @@ __device__ __forceinline__ bool tau_quick_apart(float dx0, float dx1, float dx2,
     return ok;
 }
 
+// The same bounds over every pair of two groups of bodies at once.  A group
+// is summarised by the boxes of its high parts (positions, velocities) and
+// its largest G m.  Over pairs (i in A, j in B): r >= d = the boxes'
+// distance (softened), |dv| <= vmax (the velocity boxes' widest relative
+// speed), mu <= muA + muB.  Free fall: T_ff/h = etah sqrt(r^3/mu) grows with
+// r and falls with mu, q = hq |dv|/r grows with |dv| and falls with r, so
+// (T_ff/h)(1 - 0.75 q) >= 1 for every pair once it holds at (d, vmax,
+// mu_max).  Flyby: with T_fb/h = etah r/v and |dT/dt| <= eta (1 + mu/(r
+// v^2)), tau_fb/h >= f(r, v) = 2 etah r^2 v / ((2 + eta) r v^2 + eta mu),
+// which grows with r and falls with mu; f >= 1 holds for v between the two
+// roots v- < v+ of (2 + eta) d v^2 - 2 etah d^2 v + eta mu_max = 0.  Slow
+// pairs fall below v- (approaching bodies with |dv| -> 0 have tau -> 0 in
+// this form), so the groups are certified apart only for pairs with
+// |dv| >= v-: the function returns true when every pair has tau_ff >= h
+// and vmax <= v+, and sets vthr2 so that a pair whose high-part velocity
+// difference has |dv~|^2 >= vthr2 is certified apart (vthr adds 16 u max|v|
+// for the high parts' rounding and that of their difference: at most
+// sqrt(3) (2 u max|v| + u |dv~|) <= 9.5 u max|v|).  pad_x, pad_v bound |x - x_hi| + |x' - x'_hi|
+// over the two groups (likewise v); the 2 % margin M absorbs the FP32
+// rounding of these few operations.
+struct GroupBox {
+    float xlo[3], xhi[3], vlo[3], vhi[3];
+    float gm;    // max G m of the group (high part)
+    float amax;  // max |x_hi| component
+    float vabs;  // max |v_hi| component
+};
+
+__device__ __forceinline__ bool tau_groups_apart(const GroupBox &A, const GroupBox &B, const MixedTauParams &Q,
+                                                 float &vthr2)
+{
+    const float M = 1.02f;
+    const float pad_x = 4.f * U32 * fmaxf(A.amax, B.amax);
+    const float pad_v = 4.f * U32 * fmaxf(A.vabs, B.vabs);
+    float d2 = Q.eps2, w2 = 0.f;
+#pragma unroll
+    for (int k = 0; k < 3; ++k) {
+        const float g = fmaxf(0.f, fmaxf(B.xlo[k] - A.xhi[k], A.xlo[k] - B.xhi[k]) - pad_x);
+        const float w = fmaxf(0.f, fmaxf(B.vhi[k] - A.vlo[k], A.vhi[k] - B.vlo[k])) + pad_v;
+        d2 = fmaf(g, g, d2);
+        w2 = fmaf(w, w, w2);
+    }
+    const float d = sqrtf(d2), vmax = sqrtf(w2);
+    const float mu = (A.gm + B.gm) * 1.0001f;
+    if (!(d > 0.f) || !(mu > 0.f)) return false;
+    // free fall at (d, vmax, mu_max)
+    const float X = Q.etah * d * sqrtf(d / mu);
+    const float q = Q.hq * vmax / d;
+    if (!(X * (1.f - 0.75f * M * q) >= M)) return false;
+    // flyby: roots of a v^2 - b v + c with the margin M on f >= 1
+    const float a = M * (2.f + Q.eta) * d, b = 2.f * Q.etah * d2, c = M * Q.eta * mu;
+    const float disc = b * b - 4.f * a * c;
+    if (!(disc > 0.f)) return false;
+    const float vp = (b + sqrtf(disc)) / (2.f * a);
+    const float vm = c / (a * vp);  // the product of the roots is c/a
+    if (!(vmax <= vp * 0.9999f)) return false;
+    const float vt = vm * 1.0001f + 4.f * pad_v;
+    vthr2 = vt * vt;
+    return true;
+}
+
 __device__ __forceinline__ int tau_decide_fp32(float dx0, float dx1, float dx2, float dv0, float dv1, float dv2,
                                                float mu, float c_x, float c_v, const MixedTauParams &Q)
 {

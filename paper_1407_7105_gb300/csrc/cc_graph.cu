@@ -642,14 +642,15 @@ void launch_scatter(const Level &P, const Level &C, cudaStream_t s)
     }
 }
 
-// state (id order) -> level 0, system q at set_start[q]
+// state (id order) -> level 0, system q at set_start[q]; perm (one system
+// only, may be null): the particle's offset in its set
 __global__ void k_pack_state(const double *x3, const double *v3, const double *m, long long n, Level L,
-                             const int32_t *sys_off)
+                             const int32_t *sys_off, const int32_t *perm)
 {
     const long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
     if (t >= n) return;
     const int q = upper_find(sys_off, L.nsets, (int)t);
-    const int d = L.set_start[q] + (int)(t - sys_off[q]);
+    const int d = L.set_start[q] + (perm ? perm[t] : (int)(t - sys_off[q]));
     L.x[d] = x3[t]; L.y[d] = x3[n + t]; L.z[d] = x3[2 * n + t];
     L.vx[d] = v3[t]; L.vy[d] = v3[n + t]; L.vz[d] = v3[2 * n + t];
     L.m[d] = m[t];
@@ -659,11 +660,11 @@ __global__ void k_pack_state(const double *x3, const double *v3, const double *m
 }
 
 void launch_pack_state(const double *x3, const double *v3, const double *m, long long n, const Level &L,
-                       const int32_t *sys_off, cudaStream_t s)
+                       const int32_t *sys_off, const int32_t *perm, cudaStream_t s)
 {
     fill_pad(L, s);
     if (n > 0) {
-        k_pack_state<<<(int)((n + 255) / 256), 256, 0, s>>>(x3, v3, m, n, L, sys_off);
+        k_pack_state<<<(int)((n + 255) / 256), 256, 0, s>>>(x3, v3, m, n, L, sys_off, perm);
         CC_COUNT_LAUNCH(1);
     }
 }
@@ -863,6 +864,97 @@ void launch_label_order(const int32_t *labels, int n, int total, int32_t *order,
     }
     k_order_from_sorted<<<(total + 255) / 256, 256, 0, s>>>(val, n, total, order);
     CC_COUNT_LAUNCH(1);
+}
+
+// ------------------------------------------------------------ spatial order
+// A Morton (Z-order) ranking of the particles by position, 10 bits per
+// axis over their bounding box: neighbours in the ranking are neighbours in
+// space, so 32-body groups of a set in this order have small boxes (the
+// group certificates of the mixed tau kernel).  Any permutation gives the
+// same partitions; this one only decides which pairs share a group.
+__device__ __forceinline__ unsigned ordered_bits(float f)
+{
+    const unsigned u = __float_as_uint(f);
+    return (u & 0x80000000u) ? ~u : (u | 0x80000000u);
+}
+
+__device__ __forceinline__ float from_ordered(unsigned u)
+{
+    return __uint_as_float((u & 0x80000000u) ? (u & 0x7fffffffu) : ~u);
+}
+
+__global__ void k_pos_box(const double *x3, long long n, unsigned *box)
+{
+    const long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    unsigned lo[3] = {0xffffffffu, 0xffffffffu, 0xffffffffu}, hi[3] = {0u, 0u, 0u};
+    if (t < n) {
+#pragma unroll
+        for (int k = 0; k < 3; ++k) {
+            const unsigned o = ordered_bits((float)x3[k * n + t]);
+            lo[k] = o;
+            hi[k] = o;
+        }
+    }
+#pragma unroll
+    for (int k = 0; k < 3; ++k) {
+        for (int o = 16; o > 0; o >>= 1) {
+            lo[k] = min(lo[k], __shfl_xor_sync(0xffffffffu, lo[k], o));
+            hi[k] = max(hi[k], __shfl_xor_sync(0xffffffffu, hi[k], o));
+        }
+        if ((threadIdx.x & 31) == 0) {
+            atomicMin(&box[k], lo[k]);
+            atomicMax(&box[3 + k], hi[k]);
+        }
+    }
+}
+
+__device__ __forceinline__ uint32_t spread3(uint32_t v)
+{
+    v &= 0x3ffu;
+    v = (v | (v << 16)) & 0x030000ffu;
+    v = (v | (v << 8)) & 0x0300f00fu;
+    v = (v | (v << 4)) & 0x030c30c3u;
+    v = (v | (v << 2)) & 0x09249249u;
+    return v;
+}
+
+__global__ void k_morton_keys(const double *x3, long long n, const unsigned *box, uint32_t *key, int32_t *val)
+{
+    const long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= n) return;
+    uint32_t code = 0;
+#pragma unroll
+    for (int k = 0; k < 3; ++k) {
+        const float lo = from_ordered(box[k]), hi = from_ordered(box[3 + k]);
+        const float w = hi - lo;
+        float f = w > 0.f ? ((float)x3[k * n + t] - lo) / w * 1023.f : 0.f;
+        f = fminf(fmaxf(f, 0.f), 1023.f);
+        code |= spread3((uint32_t)f) << k;
+    }
+    key[t] = code;
+    val[t] = (int32_t)t;
+}
+
+__global__ void k_perm_from_sorted(const int32_t *val, long long n, int32_t *perm)
+{
+    const long long p = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (p < n) perm[val[p]] = (int32_t)p;
+}
+
+void launch_spatial_order(const double *x3, long long n, int32_t *perm, unsigned *box, void *scratch,
+                          cudaStream_t s)
+{
+    if (n <= 0) return;
+    const int g = (int)((n + 255) / 256);
+    cudaMemsetAsync(box, 0xff, 3 * sizeof(unsigned), s);
+    cudaMemsetAsync(box + 3, 0, 3 * sizeof(unsigned), s);
+    k_pos_box<<<g, 256, 0, s>>>(x3, n, box);
+    uint32_t *key = (uint32_t *)scratch;
+    int32_t *val = (int32_t *)(key + n);
+    k_morton_keys<<<g, 256, 0, s>>>(x3, n, box, key, val);
+    radix_sort(key, val, (int)n, 30, (void *)(val + n), s);
+    k_perm_from_sorted<<<g, 256, 0, s>>>(val, n, perm);
+    CC_COUNT_LAUNCH(3);
 }
 
 // ------------------------------------------------------------ edge order

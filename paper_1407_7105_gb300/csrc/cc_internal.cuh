@@ -16,6 +16,11 @@ namespace cc {
 // bulk copies).  Padding elements carry gid = -1.
 constexpr int SET_ALIGN = 4;
 constexpr int PAD_TAIL = 256;  // slack past the last element (tile over-reads)
+// mixed form: level 0 of a single system of at least SPATIAL_MIN_N bodies is
+// packed in a Morton order of the positions, renewed every SPATIAL_RENEW
+// outer steps (the bodies move little in between; any order is correct)
+constexpr long long SPATIAL_MIN_N = 2048;
+constexpr long long SPATIAL_RENEW = 8;
 
 struct Level {
     double *x, *y, *z, *vx, *vy, *vz, *m;  // packed state, cap entries each
@@ -325,7 +330,12 @@ void launch_scatter(const Level &P, const Level &C, cudaStream_t s);
 void launch_classify(const int32_t *comp_size, const int32_t *ncomp, int s_small, int kepler, int32_t *queue,
                      int32_t *counts, int32_t *klist, int32_t *slist, cudaStream_t s);
 void launch_pack_state(const double *x3, const double *v3, const double *m, long long n, const Level &L,
-                       const int32_t *sys_src_start, cudaStream_t s);
+                       const int32_t *sys_off, const int32_t *perm, cudaStream_t s);
+// Morton ranking of the particles by position (perm[id] = rank); scratch
+// holds 8 n bytes + sort_scratch_bytes(n); box: 6 unsigned of device memory
+void launch_spatial_order(const double *x3, long long n, int32_t *perm, unsigned *box, void *scratch,
+                          cudaStream_t s);
+size_t sort_scratch_bytes(long long n);
 void launch_unpack_state(double *x3, double *v3, long long n, const Level &L, cudaStream_t s);
 void launch_gather_set(const double *x3, const double *v3, const double *m, long long n, const int32_t *set,
                        int nset, const Level &L, unsigned *bad, cudaStream_t s);

@@ -108,8 +108,55 @@ struct __align__(16) MixedTauSmem {
     float4 vq[2 * T];   // velocities (hi), (lo)
     int32_t lp[2 * T];  // local union-find over the tile's particles
     uint32_t q[T * S / 32][64];  // per warp: pairs waiting for the certified decision
+    uint32_t om[T * S / 32][T / S];       // per warp and column: lanes whose pair is still open
+    uint32_t cm[T * S / 32][T / S / 32];  // per warp and column group: columns with open pairs
+    GroupBox jb[T / 32];         // boxes of the j-tile's 32-column groups
+    float gthr[T * S / 32][T / S / 32];  // per warp and column group: |dv~|^2 threshold, < 0: none
     uint64_t bar;
 };
+
+__device__ __forceinline__ float warp_min(float v)
+{
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v = fminf(v, __shfl_xor_sync(0xffffffffu, v, o));
+    return v;
+}
+
+__device__ __forceinline__ float warp_max(float v)
+{
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v = fmaxf(v, __shfl_xor_sync(0xffffffffu, v, o));
+    return v;
+}
+
+// box of the high parts held by the lanes with `on` (p = (x, y, z, G m),
+// v = (vx, vy, vz)); returns false if no lane is on
+__device__ __forceinline__ bool warp_group_box(bool on, float4 p, float4 v, GroupBox &B)
+{
+    const float inf = __int_as_float(0x7f800000);
+    B.xlo[0] = warp_min(on ? p.x : inf);
+    B.xlo[1] = warp_min(on ? p.y : inf);
+    B.xlo[2] = warp_min(on ? p.z : inf);
+    B.xhi[0] = warp_max(on ? p.x : -inf);
+    B.xhi[1] = warp_max(on ? p.y : -inf);
+    B.xhi[2] = warp_max(on ? p.z : -inf);
+    B.vlo[0] = warp_min(on ? v.x : inf);
+    B.vlo[1] = warp_min(on ? v.y : inf);
+    B.vlo[2] = warp_min(on ? v.z : inf);
+    B.vhi[0] = warp_max(on ? v.x : -inf);
+    B.vhi[1] = warp_max(on ? v.y : -inf);
+    B.vhi[2] = warp_max(on ? v.z : -inf);
+    B.gm = warp_max(on ? p.w : 0.f);
+    float a = 0.f, b = 0.f;
+#pragma unroll
+    for (int k = 0; k < 3; ++k) {
+        a = fmaxf(a, fmaxf(fabsf(B.xlo[k]), fabsf(B.xhi[k])));
+        b = fmaxf(b, fmaxf(fabsf(B.vlo[k]), fabsf(B.vhi[k])));
+    }
+    B.amax = a;
+    B.vabs = b;
+    return __any_sync(0xffffffffu, on);
+}
 
 // Row ti and column offset of triangular tile t (tiles (ti, tj), tj >= ti,
 // numbered row by row; row ti starts at ti nt - ti (ti - 1) / 2): the root of
@@ -153,25 +200,86 @@ __device__ __forceinline__ bool luf_union(int32_t *p, int a, int b)
     return false;
 }
 
-__device__ __forceinline__ float4 shfl4(float4 v, int src)
+// Settles the warp's queued pairs sm.q[w][0..cnt), one per lane: the
+// certified FP32 decision on the float-float differences, the exact FP64
+// predicate when it is undecided, then the local union and the edge record
+// (one counter update per batch).  Out of line: the pair loop keeps only the
+// high parts and its queue in registers.
+template <int T, int S>
+__device__ __noinline__ uint2 tau_settle_batch(MixedTauSmem<T, S> &sm, int w, int cnt, int ibase, int j0, int joff,
+                                              const Level &L, const FFView &F, const TauParams &P,
+                                              const MixedTauParams &Q, DevCounters *ctr, int32_t *near_ij,
+                                              double *near_tau, long long near_cap, const EdgeList &E)
 {
-    return make_float4(__shfl_sync(0xffffffffu, v.x, src), __shfl_sync(0xffffffffu, v.y, src),
-                       __shfl_sync(0xffffffffu, v.z, src), __shfl_sync(0xffffffffu, v.w, src));
-}
-
-__device__ __noinline__ int tau_decide_fp32_ool(float dx0, float dx1, float dx2, float dv0, float dv1, float dv2,
-                                                float mu, float c_x, float c_v, MixedTauParams Q)
-{
-    return tau_decide_fp32(dx0, dx1, dx2, dv0, dv1, dv2, mu, c_x, c_v, Q);
+    // returns (edges, FP64 evaluations) of this lane's pair
+    const int lane = threadIdx.x & 31;
+    const unsigned lt = (1u << lane) - 1u;
+    const bool has = lane < cnt;
+    const unsigned ent = has ? sm.q[w][lane] : 0u;
+    const int ii = (int)(ent >> 8), kk = (int)(ent & 255u);
+    int dec = 0;
+    unsigned nfp64 = 0u;
+    double tau = CUDART_NAN;
+    if (has) {
+        const int gi = ibase + ii, gj = j0 + kk;
+        const float4 a0 = F.pq[2 * gi], a1 = F.pq[2 * gi + 1], b0 = F.vq[2 * gi], b1 = F.vq[2 * gi + 1];
+        const float cX = 11.f * U32 * U32 * F.maxes[0], cV = 11.f * U32 * U32 * F.maxes[1];
+        const float4 jp0 = sm.pq[2 * kk], jp1 = sm.pq[2 * kk + 1], jv0 = sm.vq[2 * kk], jv1 = sm.vq[2 * kk + 1];
+        dec = tau_decide_fp32((jp0.x - a0.x) + (jp1.x - a1.x), (jp0.y - a0.y) + (jp1.y - a1.y),
+                              (jp0.z - a0.z) + (jp1.z - a1.z), (jv0.x - b0.x) + (jv1.x - b1.x),
+                              (jv0.y - b0.y) + (jv1.y - b1.y), (jv0.z - b0.z) + (jv1.z - b1.z), a0.w + jp0.w, cX, cV,
+                              Q);
+        if (dec < 0) {
+            // undecided: the exact FP64 predicate of the FP64 form
+            tau = tau_fp64(__dsub_rn(L.x[gi], L.x[gj]), __dsub_rn(L.y[gi], L.y[gj]), __dsub_rn(L.z[gi], L.z[gj]),
+                           __dsub_rn(L.vx[gi], L.vx[gj]), __dsub_rn(L.vy[gi], L.vy[gj]),
+                           __dsub_rn(L.vz[gi], L.vz[gj]), L.m[gi], L.m[gj], P);
+            nfp64 = 1u;
+            if (fabs(tau - P.h) < P.near_tol * P.h) {
+                const unsigned long long q = atomicAdd(&ctr->near_pairs, 1ull);
+                if ((long long)q < near_cap) {
+                    const int pi = L.gid[gi], pj = L.gid[gj];
+                    near_ij[2 * q] = pi < pj ? pi : pj;
+                    near_ij[2 * q + 1] = pi < pj ? pj : pi;
+                    near_tau[q] = tau;
+                }
+            }
+            dec = tau < P.h ? 1 : 0;
+        }
+    }
+    const bool edge = dec > 0;
+    const unsigned eb = __ballot_sync(0xffffffffu, edge);
+    if (eb == 0u) return make_uint2(0u, nfp64);
+    if (edge && !luf_union(sm.lp, ii, joff + kk)) raise_err(ctr, DERR_UF_RETRY);
+    if (E.rec) {
+        // every edge is recorded (the decision at h/2 is left to the first
+        // half's pass); tau = the FP64 value or NaN
+        unsigned long long base = 0;
+        if (lane == 0) base = atomicAdd(E.count, (unsigned long long)__popc(eb));
+        base = __shfl_sync(0xffffffffu, base, 0);
+        const unsigned long long q = base + (unsigned)__popc(eb & lt);
+        if (edge && (long long)q < E.cap) {
+            EdgeRec r;
+            r.a = ibase + ii;
+            r.b = j0 + kk;
+            r.e = -1;
+            r.pad = 0;
+            r.tau = tau;
+            E.rec[q] = r;
+        }
+    }
+    return make_uint2(edge ? 1u : 0u, nfp64);
 }
 
 // Block = T x S threads: thread (row r, slice s) takes pairs (r, k) of the
 // tile with k in the slice's T/S columns (S > 1 shortens each warp's chain
 // for sets with few tiles).
 template <int T, int S>
-__global__ void __launch_bounds__(T * S, 1024 / (T * S)) k_tau_mixed(Level L, FFView F, TauParams P, MixedTauParams Q,
-                                                     DevCounters *ctr, int32_t *near_ij, double *near_tau,
-                                                     long long near_cap, EdgeList E)
+__global__ void __launch_bounds__(T * S, 1024 / (T * S)) k_tau_mixed(const __grid_constant__ Level L, const __grid_constant__ FFView F,
+                                                     const __grid_constant__ TauParams P,
+                                                     const __grid_constant__ MixedTauParams Q, DevCounters *ctr,
+                                                     int32_t *near_ij, double *near_tau, long long near_cap,
+                                                     const __grid_constant__ EdgeList E)
 {
     static_assert(T % 32 == 0 && T % S == 0, "tile shape");
     __shared__ MixedTauSmem<T, S> sm;
@@ -205,18 +313,11 @@ __global__ void __launch_bounds__(T * S, 1024 / (T * S)) k_tau_mixed(Level L, FF
     const int il = ti * T + row;
     const bool iv = il < n;
     const int i = start + il;
-    float4 ip0 = make_float4(0, 0, 0, 0), ip1 = ip0, iv0 = ip0, iv1 = ip0;
+    float4 ip0 = make_float4(0, 0, 0, 0), iv0 = ip0;
     if (iv) {
-        ip0 = F.pq[2 * i]; ip1 = F.pq[2 * i + 1];
-        iv0 = F.vq[2 * i]; iv1 = F.vq[2 * i + 1];
+        ip0 = F.pq[2 * i];
+        iv0 = F.vq[2 * i];
     }
-    const float cX = 11.f * U32 * U32 * F.maxes[0], cV = 11.f * U32 * U32 * F.maxes[1];
-    // the pre-test's error terms for high-part differences: per component
-    // |x_j| <= |x_i| + r, so |dx~ - dx| <= u r + 3.5 u (2 max|x_i| + r): c_x =
-    // 7 u max|x_i| per thread, and the remaining 3.5 u r goes to the
-    // threshold (likewise for the velocities)
-    const float cXh = 7.1f * U32 * fmaxf(fabsf(ip0.x), fmaxf(fabsf(ip0.y), fabsf(ip0.z)));
-    const float cVh = 7.1f * U32 * fmaxf(fabsf(iv0.x), fmaxf(fabsf(iv0.y), fabsf(iv0.z)));
     const bool got = mbar_wait(&sm.bar, 0, TMA_WAIT_CYCLES);
     if (__syncthreads_or(!got)) {
         raise_err(ctr, DERR_TMA_TIMEOUT);
@@ -227,90 +328,109 @@ __global__ void __launch_bounds__(T * S, 1024 / (T * S)) k_tau_mixed(Level L, FF
     const int joff = diag ? 0 : T;  // local index base of the j-tile
     const int lane = tid & 31, w = tid >> 5;
     const unsigned lt = (1u << lane) - 1u;
+    constexpr int NG = T / 32, GW = T / S / 32;  // column groups per tile, per warp
+    // Group certificates: the warp's 32 rows against each 32-column group of
+    // its columns (tau_groups_apart).  A certified group costs each pair one
+    // velocity difference and a comparison.
+    if (w < NG) {
+        const int k = 32 * w + lane;
+        GroupBox B;
+        const bool any = warp_group_box(k < jn, k < jn ? sm.pq[2 * k] : ip0, k < jn ? sm.vq[2 * k] : iv0, B);
+        if (lane == 0) {
+            if (!any) B.gm = -1.f;  // empty group: no pairs
+            sm.jb[w] = B;
+        }
+    }
+    {
+        GroupBox A;
+        const bool any = warp_group_box(iv, ip0, iv0, A);
+        __syncthreads();
+        if (lane < GW) {
+            const GroupBox &B = sm.jb[slice * GW + lane];
+            float thr = -1.f;
+            if (any && B.gm >= 0.f && !diag && !tau_groups_apart(A, B, Q, thr)) thr = -1.f;
+            sm.gthr[w][lane] = thr;
+        }
+        __syncwarp();
+    }
+    // the pre-test's error terms for high-part differences: per component
+    // |x_j| <= |x_i| + r, so |dx~ - dx| <= u r + 3.5 u (2 max|x_i| + r): c_x =
+    // 7 u max|x_i| per thread, and the remaining 3.5 u r goes to the
+    // threshold (likewise for the velocities)
+    const float cXh = 7.1f * U32 * fmaxf(fabsf(ip0.x), fmaxf(fabsf(ip0.y), fabsf(ip0.z)));
+    const float cVh = 7.1f * U32 * fmaxf(fabsf(iv0.x), fmaxf(fabsf(iv0.y), fabsf(iv0.z)));
     // Pairs the cheap bound does not settle are queued per warp and settled
     // 32 at a time, one per lane: taken as they come, a single such pair
     // would run the certified decision (and possibly FP64) with one lane of
     // 32 active.  Entry = (i-tile lane index << 8) | j-tile index.
     auto settle = [&](int cnt) {
-        const bool has = lane < cnt;
-        const unsigned ent = has ? sm.q[w][lane] : 0u;
-        const int ii = has ? (int)(ent >> 8) : row, kk = (int)(ent & 255u);
-        const int src = ii & 31;  // the owner of body i is a lane of this warp
-        const float4 a0 = shfl4(ip0, src), a1 = shfl4(ip1, src), b0 = shfl4(iv0, src), b1 = shfl4(iv1, src);
-        int dec = 0;
-        double tau = CUDART_NAN;
-        if (has) {
-            const float4 jp0 = sm.pq[2 * kk], jp1 = sm.pq[2 * kk + 1], jv0 = sm.vq[2 * kk], jv1 = sm.vq[2 * kk + 1];
-            dec = tau_decide_fp32_ool((jp0.x - a0.x) + (jp1.x - a1.x), (jp0.y - a0.y) + (jp1.y - a1.y),
-                                      (jp0.z - a0.z) + (jp1.z - a1.z), (jv0.x - b0.x) + (jv1.x - b1.x),
-                                      (jv0.y - b0.y) + (jv1.y - b1.y), (jv0.z - b0.z) + (jv1.z - b1.z), a0.w + jp0.w,
-                                      cX, cV, Q);
-            if (dec < 0) {
-                // undecided: the exact FP64 predicate of the FP64 form
-                const int gi = start + ti * T + ii, gj = j0 + kk;
-                tau = tau_fp64(__dsub_rn(L.x[gi], L.x[gj]), __dsub_rn(L.y[gi], L.y[gj]),
-                               __dsub_rn(L.z[gi], L.z[gj]), __dsub_rn(L.vx[gi], L.vx[gj]),
-                               __dsub_rn(L.vy[gi], L.vy[gj]), __dsub_rn(L.vz[gi], L.vz[gj]), L.m[gi], L.m[gj], P);
-                ++my_fp64;
-                if (fabs(tau - P.h) < P.near_tol * P.h) {
-                    const unsigned long long q = atomicAdd(&ctr->near_pairs, 1ull);
-                    if ((long long)q < near_cap) {
-                        const int pi = L.gid[gi], pj = L.gid[gj];
-                        near_ij[2 * q] = pi < pj ? pi : pj;
-                        near_ij[2 * q + 1] = pi < pj ? pj : pi;
-                        near_tau[q] = tau;
-                    }
-                }
-                dec = tau < P.h ? 1 : 0;
-            }
-        }
-        const bool edge = dec > 0;
-        const unsigned eb = __ballot_sync(0xffffffffu, edge);
-        if (eb == 0u) return;
-        if (edge) {
-            ++my_edges;
-            if (!luf_union(sm.lp, ii, joff + kk)) raise_err(ctr, DERR_UF_RETRY);
-        }
-        if (E.rec) {
-            // every edge is recorded (the decision at h/2 is left to the
-            // first half's pass); tau = the FP64 value or NaN.  One counter
-            // update per batch.
-            unsigned long long base = 0;
-            if (lane == 0) base = atomicAdd(E.count, (unsigned long long)__popc(eb));
-            base = __shfl_sync(0xffffffffu, base, 0);
-            const unsigned long long q = base + (unsigned)__popc(eb & lt);
-            if (edge && (long long)q < E.cap) {
-                EdgeRec r;
-                r.a = start + ti * T + ii;
-                r.b = j0 + kk;
-                r.e = -1;
-                r.pad = 0;
-                r.tau = tau;
-                E.rec[q] = r;
-            }
-        }
+        const uint2 c = tau_settle_batch<T, S>(sm, w, cnt, start + ti * T, j0, joff, L, F, P, Q, ctr, near_ij,
+                                               near_tau, near_cap, E);
+        my_edges += c.x;
+        my_fp64 += c.y;
     };
     int qn = 0;  // entries queued by this warp (warp-uniform)
     // one trip count for the whole warp (jn is the block's), so the common
     // case is a vote: every lane's pair certainly apart by the cheap bound on
     // the high parts
-    const int k1 = min(jn, (slice + 1) * (T / S));
-    for (int k = slice * (T / S); k < k1; ++k) {
-        const bool mine = iv && (!diag || k > row);
+    const int kb = slice * (T / S), k1 = min(jn, kb + T / S);
+    // the full high-part certificate of pair (row, k)
+    auto quick = [&](int k) {
         const float4 jp0 = sm.pq[2 * k], jv0 = sm.vq[2 * k];
-        const bool apart = !mine || tau_quick_apart(jp0.x - ip0.x, jp0.y - ip0.y, jp0.z - ip0.z, jv0.x - iv0.x,
-                                                    jv0.y - iv0.y, jv0.z - iv0.z, ip0.w + jp0.w, cXh, cVh, Q);
-        const unsigned open = __ballot_sync(0xffffffffu, !apart);
-        if (open == 0u) continue;
-        if (!apart) sm.q[w][qn + __popc(open & lt)] = ((unsigned)row << 8) | (unsigned)k;
-        qn += __popc(open);
-        if (qn >= 32) {
-            __syncwarp();
-            settle(32);
-            __syncwarp();
-            if (lane < qn - 32) sm.q[w][lane] = sm.q[w][32 + lane];
-            __syncwarp();
-            qn -= 32;
+        return tau_quick_apart(jp0.x - ip0.x, jp0.y - ip0.y, jp0.z - ip0.z, jv0.x - iv0.x, jv0.y - iv0.y,
+                               jv0.z - iv0.z, ip0.w + jp0.w, cXh, cVh, Q);
+    };
+    // Pass 1, the hot loop: certificates only.  A column with open pairs
+    // (rare) leaves its lane word in sm.om and its bit in sm.cm.
+    if (lane < GW) sm.cm[w][lane] = 0u;
+    __syncwarp();
+#pragma unroll 1
+    for (int g = 0; g < GW; ++g) {
+        const int ka = kb + 32 * g, kz = min(k1, ka + 32);
+        const float thr = sm.gthr[w][g];
+        if (thr >= 0.f) {
+            // certified group: one velocity difference per pair; a pair
+            // below the lower speed root takes the full certificate
+            for (int k = ka; k < kz; ++k) {
+                const bool mine = iv && (!diag || k > row);
+                const float4 jv0 = sm.vq[2 * k];
+                const float a = jv0.x - iv0.x, b = jv0.y - iv0.y, c = jv0.z - iv0.z;
+                const bool slow = mine && fmaf(c, c, fmaf(b, b, a * a)) < thr;
+                if (__ballot_sync(0xffffffffu, slow) == 0u) continue;
+                const unsigned open = __ballot_sync(0xffffffffu, slow && !quick(k));
+                if (open && lane == 0) {
+                    sm.om[w][k - kb] = open;
+                    sm.cm[w][g] |= 1u << (k - ka);
+                }
+            }
+        } else {
+            for (int k = ka; k < kz; ++k) {
+                const unsigned open = __ballot_sync(0xffffffffu, iv && (!diag || k > row) && !quick(k));
+                if (open && lane == 0) {
+                    sm.om[w][k - kb] = open;
+                    sm.cm[w][g] |= 1u << (k - ka);
+                }
+            }
+        }
+    }
+    __syncwarp();
+    // Pass 2: the open pairs, queued and settled 32 at a time
+    for (int g = 0; g < GW; ++g) {
+        unsigned cols = sm.cm[w][g];
+        while (cols) {
+            const int k = kb + 32 * g + __ffs(cols) - 1;
+            cols &= cols - 1u;
+            const unsigned open = sm.om[w][k - kb];
+            if ((open >> lane) & 1u) sm.q[w][qn + __popc(open & lt)] = ((unsigned)row << 8) | (unsigned)k;
+            qn += __popc(open);
+            if (qn >= 32) {
+                __syncwarp();
+                settle(32);
+                __syncwarp();
+                if (lane < qn - 32) sm.q[w][lane] = sm.q[w][32 + lane];
+                __syncwarp();
+                qn -= 32;
+            }
         }
     }
     if (qn > 0) {

@@ -98,3 +98,27 @@ def test_mixed_one_step_close_to_oracle(cclib, plummer_ic):
     dv = np.linalg.norm(gv - s.v3, axis=0) / np.linalg.norm(s.v3, axis=0)
     dx = np.linalg.norm(gx - s.x3, axis=0) / np.linalg.norm(s.x3, axis=0)
     assert np.median(dv) < 1e-8 and np.median(dx) < 1e-9, (np.median(dv), np.median(dx))
+
+
+def test_mixed_spatial_order_close_to_fp64(cclib, plummer_ic):
+    """A single system of >= 2048 bodies runs the mixed form with level 0
+    packed in a Morton order of the positions, renewed every 8 outer steps
+    (the group certificates of the tau kernel need groups that are compact
+    in space): 10 steps stay close to the FP64 form, which keeps id order,
+    and every particle comes back."""
+    m, x, v = plummer_ic(4096, seed=6)
+    out = {}
+    for name, prec in (("fp64", cclib.PREC_FP64), ("mixed", cclib.PREC_MIXED)):
+        c = cclib.Context(m, x, v, dt=1 / 256, precision=prec)
+        E0, _, _ = c.energy()
+        c.evolve(10 / 256)
+        E1, _, _ = c.energy()
+        _, gm, gx, gv = c.get_state()
+        out[name] = (gm, gx, gv, (E1 - E0) / abs(E0), c.stats())
+        c.close()
+    gm, gx, gv, dE, st = out["mixed"]
+    assert np.array_equal(gm, m) and np.all(np.isfinite(gx)) and np.all(np.isfinite(gv))
+    dv = np.linalg.norm(gv - out["fp64"][2], axis=0) / np.linalg.norm(out["fp64"][2], axis=0)
+    assert np.median(dv) < 1e-7, np.median(dv)
+    assert abs(dE) < 1e-6 and abs(dE - out["fp64"][3]) < 1e-7, (dE, out["fp64"][3])
+    assert abs(st["splits"] - out["fp64"][4]["splits"]) <= 0.01 * out["fp64"][4]["splits"]
