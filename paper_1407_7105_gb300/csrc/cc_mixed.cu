@@ -102,6 +102,8 @@ void launch_prep_kick(const Level &L, const FFView &F, const int32_t *order, con
 }
 
 
+constexpr int TAU_JG = 8;  // columns per group of the group certificates (rows: a warp's 32)
+
 template <int T, int S>
 struct __align__(16) MixedTauSmem {
     float4 pq[2 * T];   // positions (hi, Gm), (lo) of the j-tile
@@ -109,44 +111,49 @@ struct __align__(16) MixedTauSmem {
     int32_t lp[2 * T];  // local union-find over the tile's particles
     uint32_t q[T * S / 32][64];  // per warp: pairs waiting for the certified decision
     uint32_t om[T * S / 32][T / S];       // per warp and column: lanes whose pair is still open
-    uint32_t cm[T * S / 32][T / S / 32];  // per warp and column group: columns with open pairs
-    GroupBox jb[T / 32];         // boxes of the j-tile's 32-column groups
-    float gthr[T * S / 32][T / S / 32];  // per warp and column group: |dv~|^2 threshold, < 0: none
+    uint32_t cm[T * S / 32][T / S / 32];  // per warp and 32 columns: columns with open pairs
+    GroupBox jb[T / TAU_JG];               // boxes of the j-tile's TAU_JG-column groups
+    float gthr[T * S / 32][T / S / TAU_JG];  // per warp and column group: |dv~|^2 threshold, < 0: none
     uint64_t bar;
 };
 
+// min / max over each aligned segment of W lanes
+template <int W>
 __device__ __forceinline__ float warp_min(float v)
 {
 #pragma unroll
-    for (int o = 16; o > 0; o >>= 1) v = fminf(v, __shfl_xor_sync(0xffffffffu, v, o));
+    for (int o = W / 2; o > 0; o >>= 1) v = fminf(v, __shfl_xor_sync(0xffffffffu, v, o));
     return v;
 }
 
+template <int W>
 __device__ __forceinline__ float warp_max(float v)
 {
 #pragma unroll
-    for (int o = 16; o > 0; o >>= 1) v = fmaxf(v, __shfl_xor_sync(0xffffffffu, v, o));
+    for (int o = W / 2; o > 0; o >>= 1) v = fmaxf(v, __shfl_xor_sync(0xffffffffu, v, o));
     return v;
 }
 
-// box of the high parts held by the lanes with `on` (p = (x, y, z, G m),
-// v = (vx, vy, vz)); returns false if no lane is on
+// box of the high parts held by the lanes with `on` in each aligned segment
+// of W lanes (p = (x, y, z, G m), v = (vx, vy, vz)); returns false if no
+// lane of the segment is on
+template <int W>
 __device__ __forceinline__ bool warp_group_box(bool on, float4 p, float4 v, GroupBox &B)
 {
     const float inf = __int_as_float(0x7f800000);
-    B.xlo[0] = warp_min(on ? p.x : inf);
-    B.xlo[1] = warp_min(on ? p.y : inf);
-    B.xlo[2] = warp_min(on ? p.z : inf);
-    B.xhi[0] = warp_max(on ? p.x : -inf);
-    B.xhi[1] = warp_max(on ? p.y : -inf);
-    B.xhi[2] = warp_max(on ? p.z : -inf);
-    B.vlo[0] = warp_min(on ? v.x : inf);
-    B.vlo[1] = warp_min(on ? v.y : inf);
-    B.vlo[2] = warp_min(on ? v.z : inf);
-    B.vhi[0] = warp_max(on ? v.x : -inf);
-    B.vhi[1] = warp_max(on ? v.y : -inf);
-    B.vhi[2] = warp_max(on ? v.z : -inf);
-    B.gm = warp_max(on ? p.w : 0.f);
+    B.xlo[0] = warp_min<W>(on ? p.x : inf);
+    B.xlo[1] = warp_min<W>(on ? p.y : inf);
+    B.xlo[2] = warp_min<W>(on ? p.z : inf);
+    B.xhi[0] = warp_max<W>(on ? p.x : -inf);
+    B.xhi[1] = warp_max<W>(on ? p.y : -inf);
+    B.xhi[2] = warp_max<W>(on ? p.z : -inf);
+    B.vlo[0] = warp_min<W>(on ? v.x : inf);
+    B.vlo[1] = warp_min<W>(on ? v.y : inf);
+    B.vlo[2] = warp_min<W>(on ? v.z : inf);
+    B.vhi[0] = warp_max<W>(on ? v.x : -inf);
+    B.vhi[1] = warp_max<W>(on ? v.y : -inf);
+    B.vhi[2] = warp_max<W>(on ? v.z : -inf);
+    B.gm = warp_max<W>(on ? p.w : 0.f);
     float a = 0.f, b = 0.f;
 #pragma unroll
     for (int k = 0; k < 3; ++k) {
@@ -155,7 +162,8 @@ __device__ __forceinline__ bool warp_group_box(bool on, float4 p, float4 v, Grou
     }
     B.amax = a;
     B.vabs = b;
-    return __any_sync(0xffffffffu, on);
+    const unsigned seg = (W == 32 ? 0xffffffffu : ((1u << W) - 1u)) << ((threadIdx.x & 31) & ~(W - 1));
+    return (__ballot_sync(0xffffffffu, on) & seg) != 0u;
 }
 
 // Row ti and column offset of triangular tile t (tiles (ti, tj), tj >= ti,
@@ -328,22 +336,24 @@ __global__ void __launch_bounds__(T * S, 1024 / (T * S)) k_tau_mixed(const __gri
     const int joff = diag ? 0 : T;  // local index base of the j-tile
     const int lane = tid & 31, w = tid >> 5;
     const unsigned lt = (1u << lane) - 1u;
-    constexpr int NG = T / 32, GW = T / S / 32;  // column groups per tile, per warp
-    // Group certificates: the warp's 32 rows against each 32-column group of
-    // its columns (tau_groups_apart).  A certified group costs each pair one
-    // velocity difference and a comparison.
-    if (w < NG) {
-        const int k = 32 * w + lane;
+    // column groups per tile, per warp; groups whose boxes a warp computes
+    constexpr int NG = T / TAU_JG, GW = T / S / TAU_JG, GPW = 32 / TAU_JG;
+    // Group certificates: the warp's 32 rows against each TAU_JG-column group
+    // of its columns (tau_groups_apart).  A certified group costs each pair
+    // one velocity difference and a comparison.
+    if (w * GPW < NG) {
+        const int k = TAU_JG * (w * GPW) + lane;  // lane segment s: group w GPW + s
         GroupBox B;
-        const bool any = warp_group_box(k < jn, k < jn ? sm.pq[2 * k] : ip0, k < jn ? sm.vq[2 * k] : iv0, B);
-        if (lane == 0) {
+        const bool any =
+            warp_group_box<TAU_JG>(k < jn, k < jn ? sm.pq[2 * k] : ip0, k < jn ? sm.vq[2 * k] : iv0, B);
+        if ((lane & (TAU_JG - 1)) == 0) {
             if (!any) B.gm = -1.f;  // empty group: no pairs
-            sm.jb[w] = B;
+            sm.jb[w * GPW + lane / TAU_JG] = B;
         }
     }
     {
         GroupBox A;
-        const bool any = warp_group_box(iv, ip0, iv0, A);
+        const bool any = warp_group_box<32>(iv, ip0, iv0, A);
         __syncthreads();
         if (lane < GW) {
             const GroupBox &B = sm.jb[slice * GW + lane];
@@ -382,11 +392,11 @@ __global__ void __launch_bounds__(T * S, 1024 / (T * S)) k_tau_mixed(const __gri
     };
     // Pass 1, the hot loop: certificates only.  A column with open pairs
     // (rare) leaves its lane word in sm.om and its bit in sm.cm.
-    if (lane < GW) sm.cm[w][lane] = 0u;
+    if (lane < T / S / 32) sm.cm[w][lane] = 0u;
     __syncwarp();
 #pragma unroll 1
     for (int g = 0; g < GW; ++g) {
-        const int ka = kb + 32 * g, kz = min(k1, ka + 32);
+        const int ka = kb + TAU_JG * g, kz = min(k1, ka + TAU_JG);
         const float thr = sm.gthr[w][g];
         if (thr >= 0.f) {
             // certified group: one velocity difference per pair; a pair
@@ -400,7 +410,7 @@ __global__ void __launch_bounds__(T * S, 1024 / (T * S)) k_tau_mixed(const __gri
                 const unsigned open = __ballot_sync(0xffffffffu, slow && !quick(k));
                 if (open && lane == 0) {
                     sm.om[w][k - kb] = open;
-                    sm.cm[w][g] |= 1u << (k - ka);
+                    sm.cm[w][(k - kb) >> 5] |= 1u << ((k - kb) & 31);
                 }
             }
         } else {
@@ -408,17 +418,17 @@ __global__ void __launch_bounds__(T * S, 1024 / (T * S)) k_tau_mixed(const __gri
                 const unsigned open = __ballot_sync(0xffffffffu, iv && (!diag || k > row) && !quick(k));
                 if (open && lane == 0) {
                     sm.om[w][k - kb] = open;
-                    sm.cm[w][g] |= 1u << (k - ka);
+                    sm.cm[w][(k - kb) >> 5] |= 1u << ((k - kb) & 31);
                 }
             }
         }
     }
     __syncwarp();
     // Pass 2: the open pairs, queued and settled 32 at a time
-    for (int g = 0; g < GW; ++g) {
-        unsigned cols = sm.cm[w][g];
+    for (int c = 0; c < T / S / 32; ++c) {
+        unsigned cols = sm.cm[w][c];
         while (cols) {
-            const int k = kb + 32 * g + __ffs(cols) - 1;
+            const int k = kb + 32 * c + __ffs(cols) - 1;
             cols &= cols - 1u;
             const unsigned open = sm.om[w][k - kb];
             if ((open >> lane) & 1u) sm.q[w][qn + __popc(open & lt)] = ((unsigned)row << 8) | (unsigned)k;
