@@ -315,8 +315,8 @@ void launch_segment(const Level &L, const int32_t *root, int32_t *members, int32
 // run starts and component offsets (block scans over contiguous chunks),
 // and the ordered scatter of members.  Order within a run must be index
 // order (the input order): runs of at most SEG1_RUN members are scattered
-// by shared-memory cursors and then sorted by index, one warp per run (ranks
-// by counting); each larger run (up to SEG1_BIG of them; the giant
+// by shared-memory cursors and then sorted by index (one thread per run of at
+// most SEG1_THR by insertion, one warp per longer run by counting ranks); each larger run (up to SEG1_BIG of them; the giant
 // component of a dense cluster is one) is written by a stable compaction,
 // a block scan of "key == its root" over the batch.  More large runs than
 // that send the block to a stable single-warp scatter (one warp walks the
@@ -325,15 +325,50 @@ void launch_segment(const Level &L, const int32_t *root, int32_t *members, int32
 constexpr int SEG1_T = 1024;
 constexpr int SEG1_MAX = 16384;
 constexpr int SEG1_RUN = 64;
+constexpr int SEG1_THR = 16;  // runs up to this size are sorted by one thread
 constexpr int SEG1_BIG = 8;
 
-// exclusive block scan of the per-thread value v; *total = the sum
-__device__ __forceinline__ int seg1_scan(int v, int *tmp, int *total)
+// Each warp owns the contiguous range [32 per w, 32 per (w + 1)) of the
+// batch and walks it in rounds of 32 consecutive elements (lane = offset in
+// the round), so shared-memory accesses and global writes are unit-stride.
+// seg1_warp_base: the sum of v over the warp's lanes, exclusively scanned
+// over the warps in order (the warp's base); *total = the block's sum.
+// tmp: SEG1_T / 32 + 1 ints.
+__device__ __forceinline__ int seg1_warp_base(int v, int *tmp, int *total)
 {
-    int t;
-    const int e = block_exclusive_scan(v, tmp, t);
-    *total = t;
-    return e;
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    if (lane == 0) tmp[w] = v;
+    __syncthreads();
+    if (w == 0) {
+        const int x = lane < (int)(blockDim.x >> 5) ? tmp[lane] : 0;
+        int y = x;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const int z = __shfl_up_sync(0xffffffffu, y, o);
+            if (lane >= o) y += z;
+        }
+        if (lane < (int)(blockDim.x >> 5)) tmp[lane] = y - x;
+        if (lane == 31) tmp[32] = y;
+    }
+    __syncthreads();
+    const int base = tmp[w];
+    *total = tmp[32];
+    __syncthreads();
+    return base;
+}
+
+// inclusive scan of v over the warp's lanes
+__device__ __forceinline__ int warp_inclusive_scan(int v)
+{
+    const int lane = threadIdx.x & 31;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const int z = __shfl_up_sync(0xffffffffu, v, o);
+        if (lane >= o) v += z;
+    }
+    return v;
 }
 
 __global__ void __launch_bounds__(SEG1_T) k_segment_small(Level L, int32_t *root_out, int32_t *members,
@@ -344,11 +379,12 @@ __global__ void __launch_bounds__(SEG1_T) k_segment_small(Level L, int32_t *root
     const int n = L.total, tid = threadIdx.x;
     int *s_root = seg1_smem;      // roots (-1: padding), then the member list being built
     int *s_cnt = seg1_smem + n;   // size by root, then run start / cursor by key
-    __shared__ int tmp[32];
+    __shared__ int tmp[SEG1_T / 32 + 1];
     __shared__ int s_nbig, s_big_root[SEG1_BIG], s_big_start[SEG1_BIG], s_big_size[SEG1_BIG];
-    // each thread owns the contiguous chunk [c0, c1) of the batch (scans)
+    // warp ranges walked in rounds of 32 (seg1_warp_base)
     const int per = (n + SEG1_T - 1) / SEG1_T;
-    const int c0 = min(n, tid * per), c1 = min(n, c0 + per);
+    const int lane = tid & 31, wid = tid >> 5, wb = 32 * per * wid;
+    const unsigned lt = (1u << lane) - 1u;
     if (tid == 0) s_nbig = 0;
     if (roots_ready) {
         // roots and sizes from the multi-block compress pass (k_compress)
@@ -377,35 +413,42 @@ __global__ void __launch_bounds__(SEG1_T) k_segment_small(Level L, int32_t *root
         return r < 0 ? 1 : (r == k ? s_cnt[k] : 0);
     };
     int sw = 0, sc = 0;
-    for (int k = c0; k < c1; ++k) {
-        const int w = weight(k);
-        sw += w;
-        sc += (s_root[k] >= 0 && w >= 2) ? 1 : 0;
+    for (int j = 0; j < per; ++j) {
+        const int k = wb + 32 * j + lane;
+        if (k < n) {
+            const int w = weight(k);
+            sw += w;
+            sc += (s_root[k] >= 0 && w >= 2) ? 1 : 0;
+        }
     }
-    __syncthreads();
     int tot_w, tot_c;
-    int ew = seg1_scan(sw, tmp, &tot_w);
-    int ec = seg1_scan(sc, tmp, &tot_c);
-    __syncthreads();
-    // (weights are read before the cursors overwrite s_cnt: one chunk per
-    // thread, and a key's cursor lives at the key's own index)
-    for (int k = c0; k < c1; ++k) {
-        const int w = weight(k);
-        if (s_root[k] >= 0 && w >= 2) {
-            comp_start[ec] = ew;
-            comp_size[ec] = w;
+    int ew = seg1_warp_base(sw, tmp, &tot_w);
+    int ec = seg1_warp_base(sc, tmp, &tot_c);
+    // (an element reads its own weight before writing its own cursor: a key's
+    // cursor lives at the key's own index)
+    for (int j = 0; j < per; ++j) {
+        const int k = wb + 32 * j + lane;
+        const bool in = k < n;
+        const int w = in ? weight(k) : 0;
+        const bool head = in && s_root[k] >= 0 && w >= 2;
+        const int x = warp_inclusive_scan(w);
+        const unsigned hb = __ballot_sync(0xffffffffu, head);
+        const int my_w = ew + x - w, my_c = ec + __popc(hb & lt);
+        if (head) {
+            comp_start[my_c] = my_w;
+            comp_size[my_c] = w;
             if (w > SEG1_RUN) {
                 const int b = atomicAdd(&s_nbig, 1);
                 if (b < SEG1_BIG) {
                     s_big_root[b] = k;
-                    s_big_start[b] = ew;
+                    s_big_start[b] = my_w;
                     s_big_size[b] = w;
                 }
             }
-            ++ec;
         }
-        s_cnt[k] = ew;  // run start of key k (cursor)
-        ew += w;
+        if (in) s_cnt[k] = my_w;  // run start of key k (cursor)
+        ew += __shfl_sync(0xffffffffu, x, 31);
+        ec += __popc(hb);
     }
     if (tid == 0) *ncomp = tot_c;
     __syncthreads();
@@ -419,11 +462,19 @@ __global__ void __launch_bounds__(SEG1_T) k_segment_small(Level L, int32_t *root
         for (int b = 0; b < nbig; ++b) {
             const int rb = s_big_root[b];
             int cnt = 0;
-            for (int k = c0; k < c1; ++k) cnt += s_root[k] == rb ? 1 : 0;
+            for (int j = 0; j < per; ++j) {
+                const int k = wb + 32 * j + lane;
+                cnt += (k < n && s_root[k] == rb) ? 1 : 0;
+            }
             int tot;
-            int pos = s_big_start[b] + seg1_scan(cnt, tmp, &tot);
-            for (int k = c0; k < c1; ++k)
-                if (s_root[k] == rb) members[pos++] = k;
+            int pos = s_big_start[b] + seg1_warp_base(cnt, tmp, &tot);
+            for (int j = 0; j < per; ++j) {
+                const int k = wb + 32 * j + lane;
+                const bool hit = k < n && s_root[k] == rb;
+                const unsigned hb = __ballot_sync(0xffffffffu, hit);
+                if (hit) members[pos + __popc(hb & lt)] = k;
+                pos += __popc(hb);
+            }
             __syncthreads();
         }
         // small runs: unordered scatter into shared memory
@@ -440,10 +491,24 @@ __global__ void __launch_bounds__(SEG1_T) k_segment_small(Level L, int32_t *root
             if (kk[q] >= 0) s_root[atomicAdd(&s_cnt[kk[q]], 1)] = k;
         }
         __syncthreads();
-        const int w = tid >> 5, lane = tid & 31;
-        for (int c = w; c < tot_c; c += SEG1_T / 32) {
+        // runs of at most SEG1_THR members: one thread each, insertion sort
+        for (int c = tid; c < tot_c; c += SEG1_T) {
             const int st = comp_start[c], sz = comp_size[c];
-            if (sz > SEG1_RUN) continue;
+            if (sz > SEG1_THR) continue;
+            for (int a = 1; a < sz; ++a) {
+                const int x = s_root[st + a];
+                int b = a - 1;
+                while (b >= 0 && s_root[st + b] > x) {
+                    s_root[st + b + 1] = s_root[st + b];
+                    --b;
+                }
+                s_root[st + b + 1] = x;
+            }
+        }
+        // longer runs (up to SEG1_RUN): one warp each, ranks by counting
+        for (int c = wid; c < tot_c; c += SEG1_T / 32) {
+            const int st = comp_start[c], sz = comp_size[c];
+            if (sz <= SEG1_THR || sz > SEG1_RUN) continue;
             const int x0 = lane < sz ? s_root[st + lane] : 0x7fffffff;
             const int x1 = lane + 32 < sz ? s_root[st + lane + 32] : 0x7fffffff;
             int r0 = 0, r1 = 0;
@@ -467,7 +532,6 @@ __global__ void __launch_bounds__(SEG1_T) k_segment_small(Level L, int32_t *root
         return;
     }
     if (tid < 32) {
-        const unsigned lt = (1u << tid) - 1u;
         for (int base = 0; base < n; base += 32) {
             const int k = base + tid;
             const bool in = k < n;
