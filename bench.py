@@ -56,6 +56,23 @@ WORKLOADS = {
 }
 
 
+def combine_ranks(maxes, sums, device):
+    """Across the ranks of the process group (if any): the max of each value
+    in `maxes` (times: the slowest rank) and the sum of each in `sums` (work
+    of all replicas).  Without a process group the values come back as they
+    are."""
+    import torch
+    import torch.distributed as dist
+
+    if not (dist.is_available() and dist.is_initialized()):
+        return [float(x) for x in maxes], [float(x) for x in sums]
+    tt = torch.tensor([float(x) for x in maxes], device=device, dtype=torch.float64)
+    dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+    w = torch.tensor([float(x) for x in sums], device=device, dtype=torch.float64)
+    dist.all_reduce(w, op=dist.ReduceOp.SUM)
+    return tt.tolist(), w.tolist()
+
+
 def workload_name(n=N_BODY, workload="plummer", nsys=4096):
     return WORKLOADS[workload]["name"].format(n=n, nsys=nsys)
 
@@ -315,14 +332,7 @@ def run_gpu(args, rank, world):
     e2e_inter = (st3["tau_pairs"] - st2["tau_pairs"]) + (st3["kick_pairs"] - st2["kick_pairs"])
 
     # max over ranks, sums of work
-    sec = total_ms * 1e-3
-    if dist.is_initialized():
-        tt = torch.tensor([sec, e2e_sec], device=dev, dtype=torch.float64)
-        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
-        w = torch.tensor([float(inter), float(e2e_inter)], device=dev, dtype=torch.float64)
-        dist.all_reduce(w, op=dist.ReduceOp.SUM)
-        sec, e2e_sec = float(tt[0]), float(tt[1])
-        inter, e2e_inter = float(w[0]), float(w[1])
+    (sec, e2e_sec), (inter, e2e_inter) = combine_ranks([total_ms * 1e-3, e2e_sec], [inter, e2e_inter], dev)
     value = inter / sec
 
     # roofline of the dominant pairwise kernel (measured live above)
