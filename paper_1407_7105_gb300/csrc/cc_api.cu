@@ -31,7 +31,6 @@ using namespace cc;
 namespace {
 
 constexpr int TAU_TILE = 128;   // must match the tau kernel
-constexpr int KICK_TILE = 64;   // must match the kick kernel
 
 thread_local std::string g_init_err;
 
@@ -1290,8 +1289,8 @@ int cc_tuning(cc_ctx *c, cc_tune_entry_t *out, int64_t cap, int64_t *n_out)
     if (!c || !n_out || cap < 0 || (!out && cap > 0)) return CC_E_ARG;
     CC_CUDA(c, cudaStreamSynchronize(c->stream));
     ev_resolve(c);
-    static_assert(TK_TAU64 == CC_TUNE_TAU_FP64 && TK_TAUMIX == CC_TUNE_TAU_MIXED && TK_K64 == CC_TUNE_KICK_FP64 &&
-                      TK_MK == CC_TUNE_KICK_MIXED,
+    static_assert((int)TK_TAU64 == (int)CC_TUNE_TAU_FP64 && (int)TK_TAUMIX == (int)CC_TUNE_TAU_MIXED &&
+                      (int)TK_K64 == (int)CC_TUNE_KICK_FP64 && (int)TK_MK == (int)CC_TUNE_KICK_MIXED,
                   "tuner kinds");
     int64_t n = 0;
     for (int k = 0; k < TK_N; ++k)
