@@ -115,7 +115,8 @@ int cc_set_systems(cc_ctx *ctx, const int64_t *sys_off, int64_t nsys);
 int cc_set_stream(cc_ctx *ctx, void *stream);
 
 /* Time-step graph of Sec. 2.2 on `set` at threshold h: all pairs of the set,
- * tau(i,j) by Eq. (tauij) in FP64 (reading in the design doc), edge iff
+ * tau(i,j) by Eq. (tauij) in FP64 (T_ff = eta sqrt(r^3/mu), T_fb = eta r/|dv|,
+ * their time derivatives along the pair's motion, dT/dt clamped at 1), edge iff
  * tau(i,j) < h.  *n_edges = edge count.  edges_out (may be NULL) receives
  * min(cap, n_edges) pairs (i<j as particle ids, int32[cap][2]) in
  * lexicographic order.  *n_near = pairs with |tau-h| < near_tol*h (their

@@ -4,7 +4,7 @@
  * __graft_entry__.smoke() and bench.py's CPU baseline; never by the CUDA
  * product path.  Build: gcc -O2 -ffp-contract=off -fPIC -shared.
  *
- * Readings of the paper taken here (each one is listed in the design doc):
+ * Readings of the paper taken here (the GPU kernels implement the same ones):
  *  R1  tau_freefall / tau_flyby are not defined in the paper (it defers to
  *      Pelupessy et al. 2012).  From first principles, for the pair
  *      dx = x_i - x_j, dv = v_i - v_j, r^2 = |dx|^2 + eps^2, mu = G(m_i+m_j):

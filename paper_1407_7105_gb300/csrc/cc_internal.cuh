@@ -163,8 +163,9 @@ __device__ __forceinline__ bool mbar_wait(uint64_t *bar, unsigned parity, long l
 constexpr long long TMA_WAIT_CYCLES = 4000000000LL;  // ~2 s at 2 GHz
 
 // ------------------------------------------------- FP64 tau(i,j), exact
-// Eq. (tauij) with the free-fall / flyby reading stated in the design doc; the
-// operations and their order are fixed (no FMA: explicit _rn intrinsics)
+// Eq. (tauij) with the free-fall / flyby times derived from first principles
+// (T_ff = eta sqrt(r^3/mu), T_fb = eta r/|dv|, their time derivatives along
+// the pair's own motion, dT/dt clamped at 1); the operations and their order are fixed (no FMA: explicit _rn intrinsics)
 // so that the predicate tau < h is bit-identical to a plain IEEE-754
 // evaluation of:
 //   r2 = ((dx0*dx0 + dx1*dx1) + dx2*dx2) + eps2;  r = sqrt(r2)
