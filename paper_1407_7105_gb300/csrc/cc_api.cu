@@ -606,9 +606,11 @@ static int split_launch(cc_ctx *c, LevelAlloc &a, double h, const LevelAlloc *pa
     CC_TRY(ensure_edges(c, a, parent ? parent->ecount : 0));
     launch_init_parent(a.L, a.E.count, s);
     const bool mixed = c->p.precision == CC_PREC_MIXED;
+    bool hook_in_seg = false;  // a first half's child edges hooked by the one-CTA segmentation
     if (parent) {
+        hook_in_seg = segment_hooks_edges(a.L.total);
         launch_edges_reuse(parent->E, parent->ecount, parent->L, parent->F, mixed, parent->inv, a.L, a.E, P, c->d_ctr,
-                           c->d_near_ij, c->d_near_tau, c->near_cap, s);
+                           c->d_near_ij, c->d_near_tau, c->near_cap, s, !hook_in_seg);
     } else {
         const int tk = mixed ? TK_TAUMIX : TK_TAU64;
         int bin;
@@ -631,7 +633,8 @@ static int split_launch(cc_ctx *c, LevelAlloc &a, double h, const LevelAlloc *pa
         }
         ev_end(c, ev);
     }
-    launch_compress_segment(a.L, a.root, a.members, a.comp_start, a.comp_size, a.d_ncomp, c->seg_scratch, s);
+    launch_compress_segment(a.L, a.root, a.members, a.comp_start, a.comp_size, a.d_ncomp, c->seg_scratch, s,
+                            hook_in_seg ? &a.E : nullptr, c->d_ctr);
     // one round trip: count, record count, sizes and (bounded by total/2) starts
     const int maxc = a.L.total / 2 + 1;
     CC_CUDA(c, cudaMemcpyAsync(a.h_info, a.d_ncomp, (size_t)(4 + a.info_cap + maxc) * 4, cudaMemcpyDeviceToHost, s));

@@ -371,9 +371,41 @@ __device__ __forceinline__ int warp_inclusive_scan(int v)
     return v;
 }
 
+// find with path halving in the shared-memory forest (links point to
+// smaller indices)
+__device__ __forceinline__ int seg1_find(volatile int *p, int x)
+{
+    while (true) {
+        const int q = p[x];
+        if (q == x) return x;
+        const int g = p[q];
+        if (g != q) p[x] = g;
+        x = q;
+    }
+}
+
+// union by compare-and-swap in the shared-memory forest (the larger root
+// under the smaller)
+__device__ __forceinline__ bool seg1_union(int *p, int a, int b)
+{
+    volatile int *vp = p;
+    for (int it = 0; it < (1 << 20); ++it) {
+        a = seg1_find(vp, a);
+        b = seg1_find(vp, b);
+        if (a == b) return true;
+        if (a > b) {
+            const int t = a;
+            a = b;
+            b = t;
+        }
+        if (atomicCAS(&p[b], b, a) == b) return true;
+    }
+    return false;
+}
+
 __global__ void __launch_bounds__(SEG1_T) k_segment_small(Level L, int32_t *root_out, int32_t *members,
                                                           int32_t *comp_start, int32_t *comp_size, int32_t *ncomp,
-                                                          int roots_ready)
+                                                          EdgeList hook, DevCounters *ctr)
 {
     extern __shared__ int seg1_smem[];
     const int n = L.total, tid = threadIdx.x;
@@ -386,26 +418,33 @@ __global__ void __launch_bounds__(SEG1_T) k_segment_small(Level L, int32_t *root
     const int lane = tid & 31, wid = tid >> 5, wb = 32 * per * wid;
     const unsigned lt = (1u << lane) - 1u;
     if (tid == 0) s_nbig = 0;
-    if (roots_ready) {
-        // roots and sizes from the multi-block compress pass (k_compress)
-        for (int k = tid; k < n; k += SEG1_T) {
-            s_root[k] = L.gid[k] >= 0 ? root_out[k] : -1;
-            s_cnt[k] = L.cnt[k];
+    // the level's forest into shared memory (padding: its own root), then
+    // the first half's child edges when given (hooked here rather than in
+    // global memory, where thousands of finds of one giant component queue
+    // on its root's line), then every root by finds in shared memory
+    for (int k = tid; k < n; k += SEG1_T) s_root[k] = L.gid[k] >= 0 ? L.parent[k] : k;
+    __syncthreads();
+    if (hook.rec) {
+        const long long ne = (long long)min(*hook.count, (unsigned long long)hook.cap);
+        for (long long t = tid; t < ne; t += SEG1_T) {
+            const EdgeRec r = hook.rec[t];
+            if (!seg1_union(s_root, r.a, r.b)) raise_err(ctr, DERR_UF_RETRY);
         }
         __syncthreads();
-    } else {
-        for (int k = tid; k < n; k += SEG1_T) s_cnt[k] = 0;
-        __syncthreads();
-        for (int k = tid; k < n; k += SEG1_T) {
-            const bool valid = L.gid[k] >= 0;
-            const int r = valid ? uf_find_ca(L.parent, k) : k;
-            s_root[k] = valid ? r : -1;
-            root_out[k] = r;
-            if (valid) atomicAdd(&s_cnt[r], 1);
-        }
-        __syncthreads();
-        for (int k = tid; k < n; k += SEG1_T) L.cnt[k] = s_cnt[k];
     }
+    for (int k = tid; k < n; k += SEG1_T) s_cnt[k] = seg1_find(s_root, k);  // roots, parked in s_cnt
+    __syncthreads();
+    for (int k = tid; k < n; k += SEG1_T) {
+        const int r = s_cnt[k];
+        s_root[k] = L.gid[k] >= 0 ? r : -1;
+        root_out[k] = r;
+        s_cnt[k] = 0;
+    }
+    __syncthreads();
+    for (int k = tid; k < n; k += SEG1_T)
+        if (s_root[k] >= 0) atomicAdd(&s_cnt[s_root[k]], 1);
+    __syncthreads();
+    for (int k = tid; k < n; k += SEG1_T) L.cnt[k] = s_cnt[k];
     // run of key k: w = elements keyed k (key = root for valid elements, own
     // index for padding); a component head has w >= 2
     auto weight = [&](int k) {
@@ -551,8 +590,16 @@ __global__ void __launch_bounds__(SEG1_T) k_segment_small(Level L, int32_t *root
     }
 }
 
+// one CTA hooks the edges of small batches only: a big first half's edge
+// list (tens of thousands of edges, most into one giant component) hooks
+// faster spread over the GPU (k_edges_hook) than in one CTA
+constexpr int SEG1_HOOK_MAX = 4096;
+
+bool segment_hooks_edges(int total) { return total > 0 && total <= SEG1_HOOK_MAX; }
+
 void launch_compress_segment(const Level &L, int32_t *root, int32_t *members, int32_t *comp_start,
-                             int32_t *comp_size, int32_t *d_ncomp, void *scratch, cudaStream_t s)
+                             int32_t *comp_size, int32_t *d_ncomp, void *scratch, cudaStream_t s,
+                             const EdgeList *hook, DevCounters *ctr)
 {
     if (L.total > 0 && L.total <= SEG1_MAX) {
         // opt in to the dynamic shared memory once per device
@@ -563,12 +610,9 @@ void launch_compress_segment(const Level &L, int32_t *root, int32_t *members, in
             cudaFuncSetAttribute(k_segment_small, cudaFuncAttributeMaxDynamicSharedMemorySize, SEG1_MAX * 8);
             attr_set[dev] = true;
         }
-        // past a few thousand elements the finds run faster spread over the
-        // GPU (k_compress) than in the one CTA
-        const bool spread = L.total > 4096;
-        if (spread) launch_compress(L, root, s);  // (sizes start at zero: k_init_parent)
+        const EdgeList none{nullptr, nullptr, 0};
         k_segment_small<<<1, SEG1_T, (size_t)L.total * 8, s>>>(L, root, members, comp_start, comp_size, d_ncomp,
-                                                               spread ? 1 : 0);
+                                                               hook ? *hook : none, ctr);
         CC_COUNT_LAUNCH(1);
         return;
     }

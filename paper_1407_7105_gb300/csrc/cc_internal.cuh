@@ -303,7 +303,8 @@ void launch_tau_hook(const Level &L, int ntiles, const TauParams &P, int variant
 // split: their FP32 decisions at h/2, h/4, ... are taken from it)
 void launch_edges_reuse(const EdgeList &parent, long long pcount, const Level &PL, const FFView &PF, bool mixed,
                         const int32_t *inv, const Level &C, const EdgeList &child, const TauParams &P,
-                        DevCounters *ctr, int32_t *near_ij, double *near_tau, long long near_cap, cudaStream_t s);
+                        DevCounters *ctr, int32_t *near_ij, double *near_tau, long long near_cap, cudaStream_t s,
+                        bool hook = true);
 void launch_kick(const Level &L, const int32_t *label, int nitiles, double G, double eps2, double h,
                  int variant, DevCounters *ctr, cudaStream_t s);
 void launch_energy(const double *x3, const double *v3, const double *m, long long n, double G, double eps2,
@@ -320,8 +321,14 @@ void launch_drift_labels(const Level &L, const int32_t *singleton, double dt, cu
 size_t seg_scratch_bytes(int cap);
 void launch_segment(const Level &L, const int32_t *root, int32_t *members, int32_t *comp_start,
                     int32_t *comp_size, int32_t *d_ncomp, void *scratch, cudaStream_t s);
+// Batches of at most a one-CTA size are segmented by one CTA with the
+// level's union-find in shared memory; there it can also hook a first
+// half's child edges (segment_hooks_edges(total) tells whether it will:
+// then launch_edges_reuse leaves the hooks to it).
+bool segment_hooks_edges(int total);
 void launch_compress_segment(const Level &L, int32_t *root, int32_t *members, int32_t *comp_start,
-                             int32_t *comp_size, int32_t *d_ncomp, void *scratch, cudaStream_t s);
+                             int32_t *comp_size, int32_t *d_ncomp, void *scratch, cudaStream_t s,
+                             const EdgeList *hook = nullptr, DevCounters *ctr = nullptr);
 void launch_gather(const Level &P, const Level &C, const int32_t *members, const int32_t *lcomp_start, int32_t *inv,
                    cudaStream_t s);
 void launch_scatter(const Level &P, const Level &C, cudaStream_t s);

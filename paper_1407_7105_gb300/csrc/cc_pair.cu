@@ -262,7 +262,8 @@ __global__ void k_edges_hook(EdgeList E, int32_t *parent, DevCounters *ctr)
 
 void launch_edges_reuse(const EdgeList &parent, long long pcount, const Level &PL, const FFView &PF, bool mixed,
                         const int32_t *inv, const Level &C, const EdgeList &child, const TauParams &P,
-                        DevCounters *ctr, int32_t *near_ij, double *near_tau, long long near_cap, cudaStream_t s)
+                        DevCounters *ctr, int32_t *near_ij, double *near_tau, long long near_cap, cudaStream_t s,
+                        bool hook)
 {
     if (pcount <= 0) return;
     const double hp = 2.0 * P.h;
@@ -275,9 +276,12 @@ void launch_edges_reuse(const EdgeList &parent, long long pcount, const Level &P
     const unsigned blocks = (unsigned)((pcount + 255) / 256);
     k_edges_filter<<<blocks, 256, 0, s>>>(parent, pcount, PL, PF, Q, mixed ? 1 : 0, inv, C, child, P, ctr, near_ij,
                                           near_tau, near_cap);
-    // the hooks: at most pcount records, usually far fewer (grid-stride)
-    k_edges_hook<<<blocks < 1216u ? blocks : 1216u, 256, 0, s>>>(child, C.parent, ctr);
-    CC_COUNT_LAUNCH(2);
+    CC_COUNT_LAUNCH(1);
+    if (hook) {
+        // the hooks: at most pcount records, usually far fewer (grid-stride)
+        k_edges_hook<<<blocks < 1216u ? blocks : 1216u, 256, 0, s>>>(child, C.parent, ctr);
+        CC_COUNT_LAUNCH(1);
+    }
 }
 
 // Edge-list variant for the time-step-graph entry point: same predicate,
