@@ -48,6 +48,7 @@ struct SetLayout {
 struct LevelAlloc {
     Level L{};
     FFView F{};
+    bool classified = false;  // the last split's segmenting CTA also wrote the integrator lists
     // launch-shape variants: block prefixes over the sets (device) and the
     // total blocks (host) of every tunable shape, for the current layout
     int32_t *tau_off[N_TAU_VAR] = {}, *k64_off[N_K64_VAR] = {}, *mk_off[N_MK_VAR] = {};
@@ -633,8 +634,10 @@ static int split_launch(cc_ctx *c, LevelAlloc &a, double h, const LevelAlloc *pa
         }
         ev_end(c, ev);
     }
-    launch_compress_segment(a.L, a.root, a.members, a.comp_start, a.comp_size, a.d_ncomp, c->seg_scratch, s,
-                            hook_in_seg ? &a.E : nullptr, c->d_ctr);
+    const ClassifyArgs cls{c->p.s_small, c->p.kepler, a.kqueue, a.kqueue + 2, a.klist, a.slist};
+    a.classified = launch_compress_segment(a.L, a.root, a.members, a.comp_start, a.comp_size, a.d_ncomp,
+                                           c->seg_scratch, s, hook_in_seg ? &a.E : nullptr, c->d_ctr,
+                                           a.klist && a.slist && a.kqueue ? &cls : nullptr);
     // one round trip: count, record count, sizes and (bounded by total/2) starts
     const int maxc = a.L.total / 2 + 1;
     CC_CUDA(c, cudaMemcpyAsync(a.h_info, a.d_ncomp, (size_t)(4 + a.info_cap + maxc) * 4, cudaMemcpyDeviceToHost, s));
@@ -774,7 +777,9 @@ static int process(cc_ctx *c, int d, double h, const LevelAlloc *parent)
     const bool small_on = c->p.s_small >= 2 && d + 1 <= c->p.max_depth;
     cudaStream_t side = nullptr;
     if (small_on) CC_TRY(side_stream(c, d, &side));
-    launch_classify(a.comp_size, a.d_ncomp, c->p.s_small, c->p.kepler, a.kqueue, a.kqueue + 2, a.klist, a.slist, s);
+    if (!a.classified)
+        launch_classify(a.comp_size, a.d_ncomp, c->p.s_small, c->p.kepler, a.kqueue, a.kqueue + 2, a.klist, a.slist,
+                        s);
     if (small_on) {
         if (!a.ev_ready) {
             CC_CUDA(c, cudaEventCreateWithFlags(&a.ev_ready, cudaEventDisableTiming));

@@ -371,6 +371,39 @@ __device__ __forceinline__ int warp_inclusive_scan(int v)
     return v;
 }
 
+// The classification of a split's components (see k_classify below) by the
+// CTA that segmented them; sh: 70 ints of shared memory
+__device__ void classify_components(const int32_t *comp_size, int nc, const ClassifyArgs &C, int *sh)
+{
+    int *s_cnt = sh, *s_pos = sh + 34, *s_nk = sh + 68;
+    const int tid = threadIdx.x, nt = blockDim.x;
+    if (tid < 34) s_cnt[tid] = 0;
+    if (tid == 0) *s_nk = 0;
+    __syncthreads();
+    for (int q = tid; q < nc; q += nt) {
+        const int sz = comp_size[q];
+        if (C.kepler && sz == 2) C.klist[atomicAdd(s_nk, 1)] = q;
+        else if (sz <= C.s_small) atomicAdd(&s_cnt[sz], 1);
+    }
+    __syncthreads();
+    if (tid == 0) {
+        int pos = 0;
+        for (int z = C.s_small; z >= 0; --z) {
+            s_pos[z] = pos;
+            pos += s_cnt[z];
+        }
+        C.counts[0] = *s_nk;
+        C.counts[1] = pos;
+        C.queue[0] = 0;
+        C.queue[1] = 0;
+    }
+    __syncthreads();
+    for (int q = tid; q < nc; q += nt) {
+        const int sz = comp_size[q];
+        if (!(C.kepler && sz == 2) && sz <= C.s_small) C.slist[atomicAdd(&s_pos[sz], 1)] = q;
+    }
+}
+
 // find with path halving in the shared-memory forest (links point to
 // smaller indices)
 __device__ __forceinline__ int seg1_find(volatile int *p, int x)
@@ -405,7 +438,7 @@ __device__ __forceinline__ bool seg1_union(int *p, int a, int b)
 
 __global__ void __launch_bounds__(SEG1_T) k_segment_small(Level L, int32_t *root_out, int32_t *members,
                                                           int32_t *comp_start, int32_t *comp_size, int32_t *ncomp,
-                                                          EdgeList hook, DevCounters *ctr)
+                                                          EdgeList hook, DevCounters *ctr, ClassifyArgs cls)
 {
     extern __shared__ int seg1_smem[];
     const int n = L.total, tid = threadIdx.x;
@@ -568,9 +601,7 @@ __global__ void __launch_bounds__(SEG1_T) k_segment_small(Level L, int32_t *root
             for (int b = 0; b < nbig; ++b) in_big |= (k >= s_big_start[b] && k < s_big_start[b] + s_big_size[b]);
             if (!in_big) members[k] = s_root[k];
         }
-        return;
-    }
-    if (tid < 32) {
+    } else if (tid < 32) {
         for (int base = 0; base < n; base += 32) {
             const int k = base + tid;
             const bool in = k < n;
@@ -588,6 +619,13 @@ __global__ void __launch_bounds__(SEG1_T) k_segment_small(Level L, int32_t *root
             __syncwarp();
         }
     }
+    if (cls.queue) {
+        // the components' integrator lists (comp_size is this CTA's own
+        // writes: visible after the barrier)
+        __shared__ int cls_sh[70];
+        __syncthreads();
+        classify_components(comp_size, tot_c, cls, cls_sh);
+    }
 }
 
 // one CTA hooks the edges of small batches only: a big first half's edge
@@ -597,9 +635,9 @@ constexpr int SEG1_HOOK_MAX = 4096;
 
 bool segment_hooks_edges(int total) { return total > 0 && total <= SEG1_HOOK_MAX; }
 
-void launch_compress_segment(const Level &L, int32_t *root, int32_t *members, int32_t *comp_start,
+bool launch_compress_segment(const Level &L, int32_t *root, int32_t *members, int32_t *comp_start,
                              int32_t *comp_size, int32_t *d_ncomp, void *scratch, cudaStream_t s,
-                             const EdgeList *hook, DevCounters *ctr)
+                             const EdgeList *hook, DevCounters *ctr, const ClassifyArgs *cls)
 {
     if (L.total > 0 && L.total <= SEG1_MAX) {
         // opt in to the dynamic shared memory once per device
@@ -611,13 +649,19 @@ void launch_compress_segment(const Level &L, int32_t *root, int32_t *members, in
             attr_set[dev] = true;
         }
         const EdgeList none{nullptr, nullptr, 0};
+        ClassifyArgs nc{};
+        if (cls) {
+            nc = *cls;
+            nc.s_small = nc.s_small < 32 ? nc.s_small : 32;
+        }
         k_segment_small<<<1, SEG1_T, (size_t)L.total * 8, s>>>(L, root, members, comp_start, comp_size, d_ncomp,
-                                                               hook ? *hook : none, ctr);
+                                                               hook ? *hook : none, ctr, nc);
         CC_COUNT_LAUNCH(1);
-        return;
+        return cls != nullptr;
     }
     launch_compress(L, root, s);
     launch_segment(L, root, members, comp_start, comp_size, d_ncomp, scratch, s);
+    return false;
 }
 
 // ------------------------------------------------------------ classification
@@ -631,44 +675,17 @@ void launch_compress_segment(const Level &L, int32_t *root, int32_t *members, in
 // before the host learns the sizes.
 constexpr int CLS_T = 1024;
 
-__global__ void __launch_bounds__(CLS_T) k_classify(const int32_t *comp_size, const int32_t *ncomp, int s_small,
-                                                    int kepler, int32_t *queue, int32_t *counts, int32_t *klist,
-                                                    int32_t *slist)
+__global__ void __launch_bounds__(CLS_T) k_classify(const int32_t *comp_size, const int32_t *ncomp, ClassifyArgs C)
 {
-    __shared__ int s_cnt[34], s_pos[34], s_nk;
-    const int tid = threadIdx.x, nc = *ncomp;
-    if (tid < 34) s_cnt[tid] = 0;
-    if (tid == 0) s_nk = 0;
-    __syncthreads();
-    for (int q = tid; q < nc; q += CLS_T) {
-        const int sz = comp_size[q];
-        if (kepler && sz == 2) klist[atomicAdd(&s_nk, 1)] = q;
-        else if (sz <= s_small) atomicAdd(&s_cnt[sz], 1);
-    }
-    __syncthreads();
-    if (tid == 0) {
-        int pos = 0;
-        for (int z = s_small; z >= 0; --z) {
-            s_pos[z] = pos;
-            pos += s_cnt[z];
-        }
-        counts[0] = s_nk;
-        counts[1] = pos;
-        queue[0] = 0;
-        queue[1] = 0;
-    }
-    __syncthreads();
-    for (int q = tid; q < nc; q += CLS_T) {
-        const int sz = comp_size[q];
-        if (!(kepler && sz == 2) && sz <= s_small) slist[atomicAdd(&s_pos[sz], 1)] = q;
-    }
+    __shared__ int sh[70];
+    classify_components(comp_size, *ncomp, C, sh);
 }
 
 void launch_classify(const int32_t *comp_size, const int32_t *ncomp, int s_small, int kepler, int32_t *queue,
                      int32_t *counts, int32_t *klist, int32_t *slist, cudaStream_t s)
 {
-    k_classify<<<1, CLS_T, 0, s>>>(comp_size, ncomp, s_small < 32 ? s_small : 32, kepler, queue, counts, klist,
-                                   slist);
+    const ClassifyArgs C{s_small < 32 ? s_small : 32, kepler, queue, counts, klist, slist};
+    k_classify<<<1, CLS_T, 0, s>>>(comp_size, ncomp, C);
     CC_COUNT_LAUNCH(1);
 }
 

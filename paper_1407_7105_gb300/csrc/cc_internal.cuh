@@ -326,9 +326,17 @@ void launch_segment(const Level &L, const int32_t *root, int32_t *members, int32
 // half's child edges (segment_hooks_edges(total) tells whether it will:
 // then launch_edges_reuse leaves the hooks to it).
 bool segment_hooks_edges(int total);
-void launch_compress_segment(const Level &L, int32_t *root, int32_t *members, int32_t *comp_start,
+// where the classification (see launch_classify) writes its lists
+struct ClassifyArgs {
+    int s_small, kepler;
+    int32_t *queue, *counts, *klist, *slist;
+};
+// returns true when the segmenting CTA also classified the components
+// (cls given and the batch segmented by one CTA)
+bool launch_compress_segment(const Level &L, int32_t *root, int32_t *members, int32_t *comp_start,
                              int32_t *comp_size, int32_t *d_ncomp, void *scratch, cudaStream_t s,
-                             const EdgeList *hook = nullptr, DevCounters *ctr = nullptr);
+                             const EdgeList *hook = nullptr, DevCounters *ctr = nullptr,
+                             const ClassifyArgs *cls = nullptr);
 void launch_gather(const Level &P, const Level &C, const int32_t *members, const int32_t *lcomp_start, int32_t *inv,
                    cudaStream_t s);
 void launch_scatter(const Level &P, const Level &C, cudaStream_t s);
