@@ -605,8 +605,9 @@ static int split_launch(cc_ctx *c, LevelAlloc &a, double h, const LevelAlloc *pa
     const TauParams P = tau_params(c, h);
     // a first half's records are a subset of its parent's: room for all
     CC_TRY(ensure_edges(c, a, parent ? parent->ecount : 0));
-    launch_init_parent(a.L, a.E.count, s);
     const bool mixed = c->p.precision == CC_PREC_MIXED;
+    // a fresh mixed split initialises its forest in the float-float copy's pass
+    if (parent || !mixed) launch_init_parent(a.L, a.E.count, s);
     bool hook_in_seg = false;  // a first half's child edges hooked by the one-CTA segmentation
     if (parent) {
         hook_in_seg = segment_hooks_edges(a.L.total);
@@ -623,7 +624,7 @@ static int split_launch(cc_ctx *c, LevelAlloc &a, double h, const LevelAlloc *pa
         L.tile_off = a.tau_off[var];
         int ev;
         if (mixed) {
-            launch_prep_ff(a.L, a.F, c->p.G, true, s);
+            launch_prep_ff(a.L, a.F, c->p.G, true, s, true, a.E.count);
             ev = ev_begin(c, 0, nullptr, timed ? tk : -1, bin, var, (double)a.pairs);
             launch_tau_mixed(L, a.F, (int)ntiles, P, var, c->d_ctr, c->d_near_ij, c->d_near_tau, c->near_cap, a.E,
                              s);

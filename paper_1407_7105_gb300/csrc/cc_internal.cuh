@@ -370,7 +370,10 @@ size_t sort_scratch_bytes(long long n);
 double probe_fma(int fp64, int nsm, cudaStream_t s);
 
 // cc_mixed.cu
-void launch_prep_ff(const Level &L, const FFView &F, double G, bool with_v, cudaStream_t s);
+// init_forest: the same pass also starts the split's union-find (parent[k]
+// = k, sizes 0, *edge_count = 0), as launch_init_parent does
+void launch_prep_ff(const Level &L, const FFView &F, double G, bool with_v, cudaStream_t s, bool init_forest = false,
+                    unsigned long long *edge_count = nullptr);
 void launch_tau_mixed(const Level &L, const FFView &F, int ntiles, const TauParams &P, int variant,
                       DevCounters *ctr, int32_t *near_ij, double *near_tau, long long near_cap, const EdgeList &rec,
                       cudaStream_t s);

@@ -21,10 +21,18 @@ namespace cc {
 
 // ------------------------------------------------------------ prep
 // float-float copy of the packed state; per-level maxima of |x| and |v|
-__global__ void k_prep_ff(Level L, FFView F, float G, int with_v)
+__global__ void k_prep_ff(Level L, FFView F, float G, int with_v, int init_forest, unsigned long long *edge_count)
 {
     const int k = blockIdx.x * blockDim.x + threadIdx.x;
     float ax = 0.f, av = 0.f;
+    if (init_forest) {
+        // the split's union-find starts as singletons (what k_init_parent does)
+        if (k < L.total) {
+            L.parent[k] = k;
+            L.cnt[k] = 0;
+        }
+        if (k == 0 && edge_count) *edge_count = 0ull;
+    }
     if (k < L.total && L.gid[k] >= 0) {
         const double xs[3] = {L.x[k], L.y[k], L.z[k]};
         float hi[3], lo[3];
@@ -58,11 +66,13 @@ __global__ void k_prep_ff(Level L, FFView F, float G, int with_v)
     }
 }
 
-void launch_prep_ff(const Level &L, const FFView &F, double G, bool with_v, cudaStream_t s)
+void launch_prep_ff(const Level &L, const FFView &F, double G, bool with_v, cudaStream_t s, bool init_forest,
+                    unsigned long long *edge_count)
 {
     if (L.total <= 0) return;
     cudaMemsetAsync(F.maxes, 0, 2 * sizeof(float), s);
-    k_prep_ff<<<(L.total + 255) / 256, 256, 0, s>>>(L, F, (float)G, with_v ? 1 : 0);
+    k_prep_ff<<<(L.total + 255) / 256, 256, 0, s>>>(L, F, (float)G, with_v ? 1 : 0, init_forest ? 1 : 0,
+                                                    edge_count);
     CC_COUNT_LAUNCH(1);
 }
 
