@@ -291,13 +291,13 @@ __device__ __noinline__ uint2 tau_settle_batch(MixedTauSmem<T, S> &sm, int w, in
 
 // Block = T x S threads: thread (row r, slice s) takes pairs (r, k) of the
 // tile with k in the slice's T/S columns (S > 1 shortens each warp's chain
-// for sets with few tiles).
+// for sets with few tiles).  Parameters are grid constants: the out-of-line
+// settle takes them by reference without a copy.
 template <int T, int S>
-__global__ void __launch_bounds__(T * S, 1024 / (T * S)) k_tau_mixed(const __grid_constant__ Level L, const __grid_constant__ FFView F,
-                                                     const __grid_constant__ TauParams P,
-                                                     const __grid_constant__ MixedTauParams Q, DevCounters *ctr,
-                                                     int32_t *near_ij, double *near_tau, long long near_cap,
-                                                     const __grid_constant__ EdgeList E)
+__global__ void __launch_bounds__(T * S, 1024 / (T * S))
+    k_tau_mixed(const __grid_constant__ Level L, const __grid_constant__ FFView F,
+                const __grid_constant__ TauParams P, const __grid_constant__ MixedTauParams Q, DevCounters *ctr,
+                int32_t *near_ij, double *near_tau, long long near_cap, const __grid_constant__ EdgeList E)
 {
     static_assert(T % 32 == 0 && T % S == 0, "tile shape");
     __shared__ MixedTauSmem<T, S> sm;
@@ -379,10 +379,10 @@ __global__ void __launch_bounds__(T * S, 1024 / (T * S)) k_tau_mixed(const __gri
     // threshold (likewise for the velocities)
     const float cXh = 7.1f * U32 * fmaxf(fabsf(ip0.x), fmaxf(fabsf(ip0.y), fabsf(ip0.z)));
     const float cVh = 7.1f * U32 * fmaxf(fabsf(iv0.x), fmaxf(fabsf(iv0.y), fabsf(iv0.z)));
-    // Pairs the cheap bound does not settle are queued per warp and settled
-    // 32 at a time, one per lane: taken as they come, a single such pair
-    // would run the certified decision (and possibly FP64) with one lane of
-    // 32 active.  Entry = (i-tile lane index << 8) | j-tile index.
+    // Pairs the certificates leave open are queued per warp and settled 32
+    // at a time, one per lane: taken as they come, a single such pair would
+    // run the certified decision (and possibly FP64) with one lane of 32
+    // active.  Entry = (row in the i-tile << 8) | column in the j-tile.
     auto settle = [&](int cnt) {
         const uint2 c = tau_settle_batch<T, S>(sm, w, cnt, start + ti * T, j0, joff, L, F, P, Q, ctr, near_ij,
                                                near_tau, near_cap, E);
@@ -390,9 +390,8 @@ __global__ void __launch_bounds__(T * S, 1024 / (T * S)) k_tau_mixed(const __gri
         my_fp64 += c.y;
     };
     int qn = 0;  // entries queued by this warp (warp-uniform)
-    // one trip count for the whole warp (jn is the block's), so the common
-    // case is a vote: every lane's pair certainly apart by the cheap bound on
-    // the high parts
+    // the warp's columns [kb, k1): one trip count for all its lanes, so each
+    // column ends in a vote (the common case: no lane's pair left open)
     const int kb = slice * (T / S), k1 = min(jn, kb + T / S);
     // the full high-part certificate of pair (row, k)
     auto quick = [&](int k) {
