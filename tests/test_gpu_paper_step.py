@@ -1,4 +1,4 @@
-"""The first global step of the paper's smoothed Plummer test (Sec. 4.1:
+"""The first global step of the paper's smoothed Plummer test (Sec. 3.1:
 1024 equal-mass bodies, eps = 1/256, eta = 0.01, one step of 700/512) on
 the GPU: both forms split, kick and drift exactly as the oracle does (the
 same counts of splits, kick pairs and drifts, 16 levels deep), and the FP64

@@ -1,5 +1,5 @@
 """The oracle against the operation counts the paper prints for its
-smoothed Plummer test (Sec. 4.1, the figure comparing BLOCK, HOLD and CC):
+smoothed Plummer test (Sec. 3.1, the figure comparing BLOCK, HOLD and CC):
 one global step of the CC integrator on a softened 1024-body Plummer sphere
 performs about 1.1e9 kick, 6.6e8 time-step and 5.0e6 drift evaluations.
 The counts follow from the whole method at once: the scale of tau (in a
