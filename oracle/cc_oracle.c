@@ -1,8 +1,16 @@
 /*
- * cc_oracle.c -- plain serial FP64 oracle of the CC split integrator
+ * cc_oracle.c -- plain FP64 oracle of the CC split integrator
  * (arXiv:1407.7105, Sec. 2).  TEST INFRASTRUCTURE ONLY: used by tests/,
  * __graft_entry__.smoke() and bench.py's CPU baseline; never by the CUDA
- * product path.  Build: gcc -O2 -ffp-contract=off -fPIC -shared.
+ * product path.  Build: gcc -O2 -ffp-contract=off -fPIC -shared [-fopenmp].
+ *
+ * With OpenMP the loops over independent rows run in parallel: the tau
+ * evaluations of one breadth-first scan (every unassigned member against
+ * the popped one; the assignments are then made in ascending order, as the
+ * serial scan makes them), the kick's rows (each row summed in ascending j
+ * by one thread) and the drift's rows.  The arithmetic and its order are
+ * those of the serial code, so the results are bit-identical for any
+ * thread count (orc_set_threads(1) gives the serial oracle).
  *
  * Readings of the paper taken here (the GPU kernels implement the same ones):
  *  R1  tau_freefall / tau_flyby are not defined in the paper (it defers to
@@ -40,6 +48,24 @@
 #include <math.h>
 #include <stdlib.h>
 #include <string.h>
+#ifdef _OPENMP
+#include <omp.h>
+#endif
+
+/* sets smaller than this are scanned serially (a parallel region costs
+ * more than the work) */
+#define ORC_PAR_MIN 256
+
+int orc_set_threads(int nthreads)
+{
+#ifdef _OPENMP
+    if (nthreads > 0) omp_set_num_threads(nthreads);
+    return omp_get_max_threads();
+#else
+    (void)nthreads;
+    return 1;
+#endif
+}
 
 /* ------------------------------------------------------------------ */
 /* tau(i,j), Eq. (tauij)                                               */
@@ -102,6 +128,7 @@ int64_t orc_components(int64_t n, const double *x3, const double *v3, const doub
     if (nset < 0) return ORC_E_ARG;
     int64_t *queue = (int64_t *)malloc(sizeof(int64_t) * (nset > 0 ? nset : 1));
     char *assigned = (char *)calloc(nset > 0 ? nset : 1, 1);
+    char *hit = (char *)calloc(nset > 0 ? nset : 1, 1);
     int64_t ncomp = 0;
     if (st) {
         st->splits++;
@@ -117,12 +144,21 @@ int64_t orc_components(int64_t n, const double *x3, const double *v3, const doub
         queue[qt++] = s;
         while (qh < qt) {
             int64_t X = queue[qh++];
-            /* assign to X's component every unassigned U with tau(X,U) < h */
+            /* assign to X's component every unassigned U with tau(X,U) < h:
+             * the tests first (independent), then the assignments in
+             * ascending U */
+            uint64_t evals = 0;
+#pragma omp parallel for schedule(static) reduction(+ : evals) if (nset >= ORC_PAR_MIN)
             for (int64_t U = 0; U < nset; ++U) {
+                hit[U] = 0;
                 if (assigned[U]) continue;
                 double t = orc_tau_ids(n, x3, v3, m, p, set[X], set[U]);
-                if (st) st->tau_evals++;
-                if (t < h) {
+                evals++;
+                hit[U] = t < h;
+            }
+            if (st) st->tau_evals += evals;
+            for (int64_t U = 0; U < nset; ++U) {
+                if (hit[U]) {
                     assigned[U] = 1;
                     labels_out[U] = set[s];
                     queue[qt++] = U;
@@ -135,6 +171,7 @@ int64_t orc_components(int64_t n, const double *x3, const double *v3, const doub
     if (st) st->components += (uint64_t)ncomp;
     free(queue);
     free(assigned);
+    free(hit);
     return ncomp;
 }
 
@@ -171,6 +208,7 @@ void orc_kick(int64_t n, const double *x3, double *v3, const double *m,
     double eps2 = p->eps * p->eps;
     double *acc = (double *)calloc((size_t)(3 * (nset > 0 ? nset : 1)), sizeof(double));
     uint64_t pairs = 0;
+#pragma omp parallel for schedule(dynamic, 16) reduction(+ : pairs) if (nset >= ORC_PAR_MIN)
     for (int64_t a = 0; a < nset; ++a) {
         int64_t i = set[a];
         double ax = 0.0, ay = 0.0, az = 0.0;
@@ -204,6 +242,8 @@ void orc_drift(int64_t n, double *x3, const double *v3,
                const int32_t *set, const int32_t *labels, int64_t nset,
                double dt, orc_stats *st)
 {
+    uint64_t drifts = 0;
+#pragma omp parallel for schedule(static) reduction(+ : drifts) if (nset >= ORC_PAR_MIN)
     for (int64_t a = 0; a < nset; ++a) {
         /* a label shared with any other member marks a component member */
         int single = 1;
@@ -214,8 +254,9 @@ void orc_drift(int64_t n, double *x3, const double *v3,
         x3[i] = x3[i] + dt * v3[i];
         x3[n + i] = x3[n + i] + dt * v3[n + i];
         x3[2 * n + i] = x3[2 * n + i] + dt * v3[2 * n + i];
-        if (st) st->drifts++;
+        drifts++;
     }
+    if (st) st->drifts += drifts;
 }
 
 /* ------------------------------------------------------------------ */

@@ -1,5 +1,5 @@
 /*
- * cc_oracle.h -- plain serial FP64 CPU oracle for the connected-component
+ * cc_oracle.h -- plain FP64 CPU oracle for the connected-component
  * (CC) Hamiltonian-splitting integrator of Jaenes, Pelupessy & Portegies
  * Zwart (arXiv:1407.7105).
  *
@@ -14,7 +14,9 @@
  *
  * Numerics: every routine is plain IEEE-754 double with no fused
  * multiply-add (compile with -ffp-contract=off) and evaluates its formula
- * in the left-to-right order written in its comment.
+ * in the left-to-right order written in its comment.  Built with OpenMP,
+ * independent rows run on several threads with the same arithmetic, so
+ * every result is the serial one bit for bit.
  */
 #ifndef CC_ORACLE_H
 #define CC_ORACLE_H
@@ -114,6 +116,11 @@ int orc_evolve(int64_t n, double *x3, double *v3, const double *m,
 int orc_evolve_systems(int64_t n, double *x3, double *v3, const double *m,
                        const orc_params *p, const int64_t *sys_off, int64_t nsys,
                        int64_t nsteps, orc_stats *st);
+
+/* Threads of the parallel row loops (OpenMP builds; nthreads <= 0 leaves
+ * the setting unchanged).  Returns the threads that loops will use (1
+ * without OpenMP).  Results do not depend on it. */
+int orc_set_threads(int nthreads);
 
 /* Total energy H (Eq. Hamiltonian), linear and angular momentum. */
 void orc_energy(int64_t n, const double *x3, const double *v3, const double *m,

@@ -4,7 +4,9 @@ TEST INFRASTRUCTURE ONLY: imported by tests/, __graft_entry__.smoke() and
 the CPU-baseline leg of bench.py.  The CUDA product path never imports it.
 ``build()`` compiles cc_oracle.c with gcc (-O2 -ffp-contract=off, no FMA
 contraction, so that the operation order written in the source is the
-order executed on x86-64 and on aarch64 alike).
+order executed on x86-64 and on aarch64 alike), with OpenMP when the
+compiler has it: independent rows then run on all host cores, with results
+bit-identical to one thread (``threads(1)``).
 """
 from __future__ import annotations
 
@@ -47,8 +49,10 @@ def build(force: bool = False) -> str:
             and os.path.getmtime(_LIB_PATH) >= max(os.path.getmtime(_SRC), os.path.getmtime(hdr))):
         return _LIB_PATH
     tmp = _LIB_PATH + f".tmp{os.getpid()}"
-    subprocess.check_call(["gcc", "-O2", "-ffp-contract=off", "-fno-fast-math", "-fPIC", "-shared",
-                           "-o", tmp, _SRC, "-lm"])
+    base = ["gcc", "-O2", "-ffp-contract=off", "-fno-fast-math", "-fPIC", "-shared", "-o", tmp, _SRC]
+    r = subprocess.run(base + ["-fopenmp", "-lm"], capture_output=True, text=True)
+    if r.returncode:  # no OpenMP runtime: the serial oracle
+        subprocess.check_call(base + ["-lm"])
     os.replace(tmp, _LIB_PATH)
     return _LIB_PATH
 
@@ -80,10 +84,18 @@ def lib():
             L.orc_evolve.argtypes = [i64, dp, dp, dp, P, i64, S]
             L.orc_evolve_systems.restype = C.c_int
             L.orc_evolve_systems.argtypes = [i64, dp, dp, dp, P, C.POINTER(C.c_int64), i64, i64, S]
+            L.orc_set_threads.restype = C.c_int
+            L.orc_set_threads.argtypes = [C.c_int]
             L.orc_energy.restype = None
             L.orc_energy.argtypes = [i64, dp, dp, dp, d, d, dp, dp, dp]
             _lib = L
         return _lib
+
+
+def threads(n: int = 0) -> int:
+    """Set the threads of the parallel row loops (n <= 0: unchanged);
+    returns the threads they will use."""
+    return int(lib().orc_set_threads(int(n)))
 
 
 def _dp(a):
