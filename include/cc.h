@@ -57,7 +57,18 @@ typedef struct {
                           multiplies the min of Eq. (tauij) literally                  */
     int    autotune;   /* 1: launch shapes tuned online per size bin (default); 0: a
                           fixed rule (run-to-run identical rounding in mixed mode)   */
-    int    reserved[4];
+    int    edge_rec_max;/* 0: default; > 0: at most this many edge records kept per
+                          level for the first-half splits of the next level.  A
+                          split with more edges than that leaves an incomplete
+                          list, and the first halves of its components then run
+                          a fresh split (results are the same, only slower)    */
+    int    fault_test; /* 0 in normal use.  Failure-path test hooks of the FP64 tau
+                          kernel, so that a test can see a bounded wait or retry
+                          run out and the call return CC_E_TIMEOUT without any
+                          GPU fault: 1 = its tile copy is announced but never
+                          issued, so the mbarrier wait gives up after ~2^20
+                          cycles; 2 = the union-find hook gives up at once     */
+    int    reserved[2];
 } cc_params;
 
 typedef struct {
@@ -90,6 +101,10 @@ typedef struct {
     double   tau_ms, kick_ms, small_ms;
     int64_t  tau_launches, kick_launches, small_launches;
     uint64_t tau_pairs, kick_pairs;
+    /* work of the small-component kernel while timing was on: tau pairs it
+     * evaluated (its first-half splits reuse their fresh split's values)
+     * and cross-component pairs it kicked */
+    uint64_t small_tau_evaluated, small_kick_pairs;
 } cc_timing_t;
 
 typedef struct cc_ctx cc_ctx;
@@ -222,14 +237,21 @@ int cc_probe_peaks(void *stream, double *fp64_flops, double *fp32_flops);
  *   labels_out[n] (device-accessible int32): smallest particle index of
  *     each particle's component, identical to cc_components on all n
  *   n_comp_out (device-accessible int64): number of components >= 2
+ * "Device-accessible" means device or managed memory, or pinned host memory
+ * mapped into the device's address space; the call checks each pointer
+ * (cudaPointerGetAttributes) before any launch and refuses pageable host
+ * memory.  It cannot check sizes: the arrays must hold the counts above.
  * The first call on a device looks up the array's device address with
  * that device current; make that first call before any stream capture.
+ * The address is kept until the process exits (a cudaDeviceReset
+ * invalidates it; calls after one are not supported).
  * Calls share the one array per device: calls whose work overlaps on the
  * GPU race and give wrong labels, so serialise them (one stream, or
  * synchronise between calls).  The call synchronises `stream` before it
- * returns.  Errors: CC_E_ARG (NULL pointer, n < 1, h not > 0),
- * CC_E_CAPACITY (n > CC_NOALLOC_MAX_N), CC_E_CUDA (a CUDA call failed),
- * CC_E_TIMEOUT (union-find retry limit reached). */
+ * returns.  Errors: CC_E_ARG (NULL or unreachable pointer, n < 1, h not
+ * > 0, or G, eps, eta, eta_outside out of the range cc_init accepts),
+ * CC_E_CAPACITY (n > CC_NOALLOC_MAX_N), CC_E_CUDA (a CUDA call or launch
+ * failed), CC_E_TIMEOUT (union-find retry limit reached). */
 #define CC_NOALLOC_MAX_N 65536
 int cc_components_noalloc(const double *m, const double *x3, const double *v3,
                           int64_t n, const cc_params *p, double h,

@@ -26,7 +26,8 @@ class Params(C.Structure):
     _fields_ = [("G", C.c_double), ("eps", C.c_double), ("eta", C.c_double), ("dt", C.c_double),
                 ("h_fp64", C.c_double), ("near_tol", C.c_double), ("precision", C.c_int),
                 ("kepler", C.c_int), ("max_depth", C.c_int), ("s_small", C.c_int),
-                ("eta_outside", C.c_int), ("autotune", C.c_int), ("reserved", C.c_int * 4)]
+                ("eta_outside", C.c_int), ("autotune", C.c_int), ("edge_rec_max", C.c_int),
+                ("fault_test", C.c_int), ("reserved", C.c_int * 2)]
 
 
 class Stats(C.Structure):
@@ -44,7 +45,8 @@ class Stats(C.Structure):
 class Timing(C.Structure):
     _fields_ = [("tau_ms", C.c_double), ("kick_ms", C.c_double), ("small_ms", C.c_double),
                 ("tau_launches", C.c_int64), ("kick_launches", C.c_int64), ("small_launches", C.c_int64),
-                ("tau_pairs", C.c_uint64), ("kick_pairs", C.c_uint64)]
+                ("tau_pairs", C.c_uint64), ("kick_pairs", C.c_uint64),
+                ("small_tau_evaluated", C.c_uint64), ("small_kick_pairs", C.c_uint64)]
 
     def as_dict(self):
         return {k: getattr(self, k) for k, _ in self._fields_}
@@ -156,10 +158,31 @@ def probe_peaks(stream=None):
     return float(f64.value), float(f32.value)
 
 
+def _require_cuda(name, t, dtype, numel):
+    """components_noalloc's buffers are read and written by kernels: CUDA
+    tensors of the stated dtype and at least `numel` elements."""
+    import torch
+    if not (isinstance(t, torch.Tensor) and t.is_cuda):
+        raise TypeError(f"{name} must be a CUDA tensor")
+    if t.dtype != dtype:
+        raise TypeError(f"{name} must be {dtype}, got {t.dtype}")
+    if t.numel() < numel:
+        raise ValueError(f"{name} holds {t.numel()} elements, needs {numel}")
+    if not t.is_contiguous():
+        raise ValueError(f"{name} must be contiguous")
+
+
 def components_noalloc(m, x3, v3, h: float, labels_out, n_comp_out, params: Params | None = None, stream=None):
     """cc_components_noalloc: labels of all particles of a device-resident
     state into caller-provided device buffers (labels_out int32[n],
     n_comp_out int64[1]); the library allocates nothing."""
+    import torch
+    n = int(m.shape[0])
+    _require_cuda("m", m, torch.float64, n)
+    _require_cuda("x3", x3, torch.float64, 3 * n)
+    _require_cuda("v3", v3, torch.float64, 3 * n)
+    _require_cuda("labels_out", labels_out, torch.int32, n)
+    _require_cuda("n_comp_out", n_comp_out, torch.int64, 1)
     p = params if params is not None else default_params()
     rc = lib().cc_components_noalloc(_ptr(m), _ptr(x3), _ptr(v3), int(m.shape[0]), C.byref(p), float(h),
                                      _ptr(labels_out), _ptr(n_comp_out),

@@ -15,6 +15,7 @@
 //   DKD     : D_{h/2,T_R} K_{h,V_R+V_CC+V_CR} D_{h/2,T_R} on the batch.
 #include <algorithm>
 #include <cmath>
+#include <cstddef>
 #include <cstdio>
 #include <cstring>
 #include <string>
@@ -471,12 +472,13 @@ constexpr long long EDGE_CAP_MAX = 1ll << 22;
 static int ensure_edges(cc_ctx *c, LevelAlloc &a, long long at_least = 0)
 {
     a.E.count = (unsigned long long *)(a.d_ncomp + 2);  // in the split summary block
+    const long long cap_max = c->p.edge_rec_max > 0 ? (long long)c->p.edge_rec_max : EDGE_CAP_MAX;
     long long want = std::max<long long>(std::max<long long>(4096, 4ll * a.cap), at_least);
     if (a.ecount > a.E.cap) want = std::max(want, 2 * a.ecount);
-    want = std::min(std::max(want, at_least), std::max(EDGE_CAP_MAX, at_least));
+    want = std::min(std::max(want, at_least), std::max(cap_max, at_least));
     if (a.eblock && want <= a.E.cap) return CC_OK;
     // grow geometrically: a reallocation synchronises the device
-    if (a.eblock) want = std::max(want, a.E.cap + a.E.cap / 2);
+    if (a.eblock) want = std::max(want, std::min(a.E.cap + a.E.cap / 2, std::max(cap_max, at_least)));
     if (a.eblock) cudaFree(a.eblock);
     a.eblock = nullptr;
     a.E = EdgeList{nullptr, nullptr, 0};
@@ -571,6 +573,7 @@ static TauParams tau_params(const cc_ctx *c, double h)
     P.eta_outside = c->p.eta_outside;
     P.h = h;
     P.near_tol = c->p.near_tol;
+    P.fault_test = c->p.fault_test;
     return P;
 }
 
@@ -897,8 +900,15 @@ static int harvest_counters(cc_ctx *c)
     c->st.kepler_calls += h.small_kepler;
     c->st.tau_evaluated += h.tau_evals;
     if (h.max_depth_seen > c->st.max_depth_seen) c->st.max_depth_seen = h.max_depth_seen;
-    // tau_fp64 .. tau_evals
-    CC_CUDA(c, cudaMemsetAsync(&c->d_ctr->tau_fp64, 0, sizeof(unsigned long long) * 9, c->stream));
+    if (c->timing) {
+        c->tm.small_tau_evaluated += h.small_tau_evals;
+        c->tm.small_kick_pairs += h.small_kick_pairs;
+    }
+    // tau_fp64 .. small_tau_evals
+    static_assert(offsetof(DevCounters, small_tau_evals) - offsetof(DevCounters, tau_fp64) ==
+                      9 * sizeof(unsigned long long),
+                  "counter block");
+    CC_CUDA(c, cudaMemsetAsync(&c->d_ctr->tau_fp64, 0, sizeof(unsigned long long) * 10, c->stream));
     return CC_OK;
 }
 
@@ -937,7 +947,8 @@ int cc_init(cc_ctx **out, int64_t n, const double *m, const double *x3, const do
     *out = nullptr;
     if (!(p->G > 0.0) || !(p->eps >= 0.0) || !finite_pos(p->eta) || !finite_pos(p->dt) || p->max_depth < 0 ||
         p->max_depth > 200 || (p->precision != CC_PREC_FP64 && p->precision != CC_PREC_MIXED) ||
-        (p->kepler && p->eps != 0.0) || p->s_small < 0 || p->s_small > 32) {
+        (p->kepler && p->eps != 0.0) || p->s_small < 0 || p->s_small > 32 || p->edge_rec_max < 0 ||
+        p->fault_test < 0 || p->fault_test > 2) {
         g_init_err = "cc_init: invalid parameters";
         return CC_E_ARG;
     }

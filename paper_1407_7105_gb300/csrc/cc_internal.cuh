@@ -90,6 +90,7 @@ struct DevCounters {
     unsigned long long small_splits;
     unsigned long long small_components;
     unsigned long long tau_evals;  // pairs whose tau the small kernel or the edge-record pass evaluated
+    unsigned long long small_tau_evals;  // of those, the small kernel's
     unsigned int err;
     int max_depth_seen;
 };
@@ -104,6 +105,7 @@ struct SmallParams {
 struct TauParams {
     double G, eps2, eta_in, eta, h, near_tol;
     int eta_outside;
+    int fault_test;  // failure-path test hooks of the FP64 tau kernel (cc_params.fault_test)
 };
 
 // --------------------------------------------------------------- helpers
@@ -161,6 +163,10 @@ __device__ __forceinline__ bool mbar_wait(uint64_t *bar, unsigned parity, long l
     }
 }
 constexpr long long TMA_WAIT_CYCLES = 4000000000LL;  // ~2 s at 2 GHz
+// the shortened wait of the fault_test = 1 hook: a copy that is never issued
+constexpr long long FAULT_TEST_WAIT_CYCLES = 1LL << 20;
+// union-find: compare-and-swap attempts before a hook gives up
+constexpr int UF_RETRY_MAX = 1 << 24;
 
 // ------------------------------------------------- FP64 tau(i,j), exact
 // Eq. (tauij) with the free-fall / flyby times derived from first principles
@@ -221,11 +227,12 @@ __device__ __forceinline__ int uf_find(int32_t *parent, int x)
 
 // Union of the trees of a and b: link the larger root under the smaller one
 // with compare-and-swap, retrying from the new parent on contention.
-__device__ __forceinline__ bool uf_union(int32_t *parent, int a, int b)
+__device__ __forceinline__ bool uf_union(int32_t *parent, int a, int b, int retry_max = UF_RETRY_MAX)
 {
     int ra = uf_find(parent, a), rb = uf_find(parent, b);
-    for (int it = 0; it < (1 << 24); ++it) {
+    for (int it = 0;; ++it) {
         if (ra == rb) return true;
+        if (it >= retry_max) return false;
         if (ra < rb) {
             int old = atomicCAS(&parent[rb], rb, ra);
             if (old == rb) return true;
@@ -236,7 +243,6 @@ __device__ __forceinline__ bool uf_union(int32_t *parent, int a, int b)
             ra = uf_find(parent, old);
         }
     }
-    return false;
 }
 
 // The same forest operations reading through L1 (ld.global.ca), for passes
@@ -257,7 +263,7 @@ __device__ __forceinline__ int uf_find_ca(const int32_t *parent, int x)
 __device__ __forceinline__ bool uf_union_ca(int32_t *parent, int a, int b)
 {
     int ra = uf_find_ca(parent, a), rb = uf_find_ca(parent, b);
-    for (int it = 0; it < (1 << 24); ++it) {
+    for (int it = 0; it < UF_RETRY_MAX; ++it) {
         if (ra == rb) return true;
         if (ra < rb) {
             int old = atomicCAS(&parent[rb], rb, ra);

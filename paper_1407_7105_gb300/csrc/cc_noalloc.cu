@@ -124,8 +124,26 @@ __global__ void k_na_store(NaScratch S, int64_t *n_comp_out) { *n_comp_out = *S.
 
 using namespace cc;
 
+// Can a kernel on the current device read and write `ptr`?  Device and
+// managed memory, and pinned host memory mapped into the device's address
+// space, can; pageable host memory is refused (a kernel touching it would
+// fault instead of returning an error).
+static bool device_reachable(const void *ptr)
+{
+    cudaPointerAttributes a;
+    if (cudaPointerGetAttributes(&a, ptr) != cudaSuccess) {
+        cudaGetLastError();
+        return false;
+    }
+    if (a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged) return a.devicePointer != nullptr;
+    if (a.type == cudaMemoryTypeHost) return a.devicePointer == ptr;
+    return false;
+}
+
 // device address of the scratch array for the current device, looked up
-// once per device (with that device current)
+// once per device (with that device current) and kept for the life of the
+// process (a cudaDeviceReset invalidates it; calls after one are not
+// supported)
 static int na_scratch(int32_t **out)
 {
     int dev = 0;
@@ -152,7 +170,15 @@ extern "C" int cc_components_noalloc(const double *m, const double *x3, const do
 {
     if (!m || !x3 || !v3 || !p || !labels_out || !n_comp_out || !(h > 0.0) || !isfinite(h) || n < 1)
         return CC_E_ARG;
+    // the parameters cc_init accepts for the same threshold test
+    if (!(p->G > 0.0) || !isfinite(p->G) || !(p->eps >= 0.0) || !isfinite(p->eps) || !(p->eta > 0.0) ||
+        !isfinite(p->eta) || (p->eta_outside != 0 && p->eta_outside != 1))
+        return CC_E_ARG;
     if (n > CC_NOALLOC_MAX_N) return CC_E_CAPACITY;  // beyond the fixed scratch array
+    // every pointer is read or written by a kernel: refuse what it cannot reach
+    const void *ptrs[5] = {m, x3, v3, labels_out, n_comp_out};
+    for (const void *q : ptrs)
+        if (!device_reachable(q)) return CC_E_ARG;
     int32_t *base = nullptr;
     if (na_scratch(&base)) return CC_E_CUDA;
     const cudaStream_t s = (cudaStream_t)stream;
@@ -165,6 +191,7 @@ extern "C" int cc_components_noalloc(const double *m, const double *x3, const do
     P.eta_outside = p->eta_outside;
     P.h = h;
     P.near_tol = 0.0;
+    P.fault_test = 0;
     const int ni = (int)n, g = (ni + 255) / 256;
     const long long nt = (n + NA_T - 1) / NA_T;
     k_na_init<<<g, 256, 0, s>>>(S, ni);
@@ -173,6 +200,10 @@ extern "C" int cc_components_noalloc(const double *m, const double *x3, const do
     k_na_count<<<g, 256, 0, s>>>(ni, S, n_comp_out);
     k_na_store<<<1, 1, 0, s>>>(S, n_comp_out);
     CC_COUNT_LAUNCH(5);
+    if (cudaPeekAtLastError() != cudaSuccess) {  // a launch was refused: nothing was written
+        cudaGetLastError();
+        return CC_E_CUDA;
+    }
     unsigned err = 0;
     if (cudaMemcpyAsync(&err, S.err, sizeof(unsigned), cudaMemcpyDeviceToHost, s) != cudaSuccess ||
         cudaStreamSynchronize(s) != cudaSuccess) {

@@ -87,12 +87,18 @@ __global__ void __launch_bounds__(T) k_tau_hook(Level L, TauParams P, DevCounter
         fence_mbar_init();
     }
     __syncthreads();
+    // fault_test = 1: the copy is announced but never issued, so the wait
+    // below runs out (a test of the bounded wait; no copy is in flight)
+    const bool no_copy = P.fault_test == 1;
+    const long long wait_cycles = no_copy ? FAULT_TEST_WAIT_CYCLES : TMA_WAIT_CYCLES;
     if (tid == 0) {
         const unsigned bytes = (unsigned)((jn + 3) & ~3) * 8u;
         mbar_expect_tx(&sm.bar, 7u * bytes);
         const double *src[7] = {L.x, L.y, L.z, L.vx, L.vy, L.vz, L.m};
+        if (!no_copy) {
 #pragma unroll
-        for (int c = 0; c < 7; ++c) tma_load_1d(sm.col[c], src[c] + j0, bytes, &sm.bar);
+            for (int c = 0; c < 7; ++c) tma_load_1d(sm.col[c], src[c] + j0, bytes, &sm.bar);
+        }
     }
     const int il = ti * T + tid;
     const bool iv = il < n;
@@ -105,11 +111,14 @@ __global__ void __launch_bounds__(T) k_tau_hook(Level L, TauParams P, DevCounter
         mi = L.m[i];
         gi = L.gid[i];
     }
-    if (!mbar_wait(&sm.bar, 0, TMA_WAIT_CYCLES)) {
+    if (!mbar_wait(&sm.bar, 0, wait_cycles)) {
         raise_err(ctr, DERR_TMA_TIMEOUT);
-        mbar_wait(&sm.bar, 0, TMA_WAIT_CYCLES);
+        // let a copy still in flight land before the CTA exits
+        mbar_wait(&sm.bar, 0, wait_cycles);
         return;
     }
+    // fault_test = 2: every hook gives up at once (a test of the retry cap)
+    const int uf_retry = P.fault_test == 2 ? 0 : UF_RETRY_MAX;
     unsigned long long my_edges = 0;
     if (iv) {
         const int kbeg = (ti == tj) ? tid + 1 : 0;
@@ -133,7 +142,7 @@ __global__ void __launch_bounds__(T) k_tau_hook(Level L, TauParams P, DevCounter
             log_pair(P, tau, gi, L.gid[j], ctr, near_ij, near_tau, near_cap);
             if (tau < P.h) {
                 ++my_edges;
-                if (!uf_union(L.parent, i, j)) raise_err(ctr, DERR_UF_RETRY);
+                if (!uf_union(L.parent, i, j, uf_retry)) raise_err(ctr, DERR_UF_RETRY);
                 // a record serves the first half at h/2: kept when the pair
                 // is an edge there or near h/2
                 if (E.rec && (tau < 0.5 * P.h || fabs(tau - 0.5 * P.h) < P.near_tol * 0.5 * P.h))

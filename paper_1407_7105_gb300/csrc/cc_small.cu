@@ -424,6 +424,7 @@ __global__ void __launch_bounds__(K8_WARPS * 32) k_small(Level L, const int32_t 
     TauParams P;
     P.G = SP.G; P.eps2 = SP.eps2; P.eta = SP.eta; P.eta_in = SP.eta_in; P.eta_outside = SP.eta_outside;
     P.near_tol = SP.near_tol;
+    P.fault_test = 0;
     MixedTauParams Q;
     Q.eta = (float)SP.eta_in; Q.eps2 = (float)SP.eps2; Q.G = (float)SP.G;
     Q.hq = 0.f;  // (the pre-test is not used here)
@@ -742,7 +743,10 @@ __global__ void __launch_bounds__(K8_WARPS * 32) k_small(Level L, const int32_t 
         if (v[4]) atomicAdd(&ctr->small_components, v[4]);
         if (v[5]) atomicAdd(&ctr->small_kepler, v[5]);
         if (v[6]) atomicAdd(&ctr->tau_fp64, v[6]);
-        if (v[7]) atomicAdd(&ctr->tau_evals, v[7]);
+        if (v[7]) {
+            atomicAdd(&ctr->tau_evals, v[7]);
+            atomicAdd(&ctr->small_tau_evals, v[7]);
+        }
         atomicMax(&ctr->max_depth_seen, maxd);
     }
 }
