@@ -6,6 +6,7 @@ its force error)."""
 import numpy as np
 import pytest
 
+import _bounds as B
 from oracle import oracle as O
 
 pytestmark = pytest.mark.gpu
@@ -19,7 +20,7 @@ def test_components_and_step_with_eta_outside(cclib, plummer_ic, prec_name):
     s = O.State(m, x, v)
     T = O.tau_matrix(s, p)
     vals = np.sort(T[np.triu_indices(600, 1)])
-    c = cclib.Context(m, x, v, dt=1 / 128, eta=0.03, eta_outside=1, precision=prec)
+    c = cclib.Context(m, x, v, dt=1 / 128, eta=0.03, eta_outside=1, precision=prec, near_tol=1e-6)
     for q in (0.002, 0.02, 0.2):
         h = float(vals[int(q * (vals.size - 1))]) * (1.0 + 1e-9)
         lab, k = c.components(h)
@@ -29,6 +30,7 @@ def test_components_and_step_with_eta_outside(cclib, plummer_ic, prec_name):
     c.evolve(1 / 128)
     _, _, gx, gv = c.get_state()
     st = c.stats()
+    pairs, _, _ = c.near_pairs()
     c.close()
     ost = O.evolve(s, p, 1)
     assert st["splits"] == ost.splits and st["kick_pairs"] == ost.kick_pairs
@@ -37,3 +39,6 @@ def test_components_and_step_with_eta_outside(cclib, plummer_ic, prec_name):
     else:
         dv = np.linalg.norm(gv - s.v3, axis=0) / np.linalg.norm(s.v3, axis=0)
         assert np.median(dv) < 1e-8, np.median(dv)
+        w, _ = B.check_velocity_bound(gv, s.v3, B.abs_accel_sum(m, x), 1 / 128, ost.max_depth_seen,
+                                      exempt=B.near_bodies(pairs))
+        print("eta outside mixed: max error / bound", w)

@@ -3,6 +3,7 @@
 import numpy as np
 import pytest
 
+import _bounds as B
 from oracle import oracle as O
 from paper_1407_7105_gb300 import ics
 
@@ -129,6 +130,40 @@ def test_kepler_mode_binaries(cclib):
     c.close()
 
 
+def test_kepler_mode_well_conditioned_bodies_elementwise(cclib):
+    """Element-wise where the orbits are well conditioned.  At a short
+    outer step (1/2048) the top-level components are mostly the binaries
+    themselves: bodies whose top-level component has at most two members
+    (singletons, and binaries that only the Kepler flow advances inside the
+    step) must agree with the oracle within a bound that scales like the
+    Kepler phase's rounding: 2^14 u64 dt S_i (D + 1), S_i the sum of
+    absolute pair accelerations (for a binary member dominated by its
+    partner's, so that dt S_i ~ |v| x the radians the orbit turns through
+    in the step).  Positions likewise within dt times that."""
+    m, x, v = ics.plummer_with_binaries(512, seed=3)
+    dt = 1 / 2048
+    c = cclib.Context(m, x, v, dt=dt, kepler=1)
+    top, _ = c.components(dt)
+    c.reset_stats()
+    c.evolve(dt)
+    _, _, gx, gv = c.get_state()
+    g = c.stats()
+    c.close()
+    s = O.State(m, x, v)
+    st = O.evolve(s, O.params(dt=dt, kepler=True), 1)
+    assert g["kepler_calls"] == st.kepler_calls > 0
+    sizes = np.bincount(top, minlength=m.shape[0])
+    calm = np.flatnonzero(sizes[top] <= 2)
+    assert calm.size > 0.8 * m.shape[0], calm.size
+    S = B.abs_accel_sum(m, x)
+    tol = 2.0 ** 14 * B.U64 * dt * S * (st.max_depth_seen + 1)
+    ev = np.linalg.norm(gv - s.v3, axis=0)
+    ex = np.linalg.norm(gx - s.x3, axis=0)
+    rv, rx = ev[calm] / tol[calm], ex[calm] / (dt * tol[calm])
+    print("Kepler mode: well-conditioned bodies", calm.size, "max error / bound: v", rv.max(), "x", rx.max())
+    assert rv.max() <= 1.0 and rx.max() <= 1.0, (rv.max(), rx.max())
+
+
 def test_kepler_isolated_binaries_closed_form(cclib):
     """Each two-body component advanced by the GPU Kepler solver equals the
     closed-form orbit (orbital elements, mean anomaly by a library root
@@ -160,6 +195,15 @@ def test_kepler_isolated_binaries_closed_form(cclib):
         ref_r = xr[:, 0] - xr[:, 1]
         # n*dt is several hundred radians here: the phase is good to ~1e-13
         assert np.abs(got_r - ref_r).max() < 1e-10 * a / (1 - e), (k, e)
+        # the relative velocity likewise: |dv| ~ (phase error) x |d v/d phase|,
+        # and the orbital speed peaks at pericentre, n a sqrt((1 + e)/(1 - e))
+        got_u = gv[:, 2 * k] - gv[:, 2 * k + 1]
+        ref_u = vr[:, 0] - vr[:, 1]
+        vmax = n * a * math.sqrt((1 + e) / (1 - e))
+        assert np.abs(got_u - ref_u).max() < 1e-10 * vmax / (1 - e), (k, e)
+        # and the centre of mass moves uniformly (at rest here)
+        com_v = (mm[0] * gv[:, 2 * k] + mm[1] * gv[:, 2 * k + 1]) / mm.sum()
+        assert np.abs(com_v).max() < 1e-13 * vmax
 
 
 def test_errors_are_reported(cclib, plummer_ic):

@@ -8,6 +8,7 @@ FP32 kick is judged by its error against the FP64 kick on the same state.
 import numpy as np
 import pytest
 
+import _bounds as B
 from oracle import oracle as O
 from paper_1407_7105_gb300 import ics
 
@@ -68,6 +69,12 @@ def test_mixed_kick_error(cclib, plummer_ic):
     da_gpu = (gv - v) / h
     err = np.linalg.norm(da_gpu - da_ref, axis=0) / np.linalg.norm(da_ref, axis=0)
     assert np.median(err) < 2e-7 and err.max() < 1e-5, (np.median(err), err.max())
+    # per body: |da_i| <= 32 u S_i (the FP32 error model of the pair terms
+    # and their grouped, compensated sum; one kick, no recursion)
+    S_cross = B.abs_accel_sum(m, x, labels=labels)
+    abs_err = np.linalg.norm(da_gpu - da_ref, axis=0)
+    ratio = abs_err / (B.K_MIXED * B.U32 * S_cross)
+    assert ratio.max() <= 1.0, (int(np.argmax(ratio)), float(ratio.max()))
 
 
 def test_mixed_energy_matches_fp64(cclib, plummer_ic):
@@ -89,15 +96,22 @@ def test_mixed_energy_matches_fp64(cclib, plummer_ic):
 
 def test_mixed_one_step_close_to_oracle(cclib, plummer_ic):
     m, x, v = plummer_ic(16384)
-    c = _mixed(cclib, m, x, v, dt=1 / 256)
+    c = _mixed(cclib, m, x, v, dt=1 / 256, near_tol=1e-6)
     c.evolve(1 / 256)
     _, _, gx, gv = c.get_state()
+    pairs, _, _ = c.near_pairs()
     c.close()
     s = O.State(m, x, v)
-    O.evolve(s, O.params(dt=1 / 256), 1)
+    st = O.evolve(s, O.params(dt=1 / 256), 1)
     dv = np.linalg.norm(gv - s.v3, axis=0) / np.linalg.norm(s.v3, axis=0)
     dx = np.linalg.norm(gx - s.x3, axis=0) / np.linalg.norm(s.x3, axis=0)
     assert np.median(dv) < 1e-8 and np.median(dx) < 1e-9, (np.median(dv), np.median(dx))
+    # every body, not only the median: the per-body FP32 error bound
+    S = B.abs_accel_sum(m, x)
+    ex = B.near_bodies(pairs)
+    wv, _ = B.check_velocity_bound(gv, s.v3, S, 1 / 256, st.max_depth_seen, exempt=ex, what="v")
+    wx, _ = B.check_velocity_bound(gx, s.x3, S / 256, 1 / 256, st.max_depth_seen, exempt=ex, what="x")
+    print("mixed 16384 one step: max error / bound: v", wv, "x", wx, "exempt", ex.size)
 
 
 def test_mixed_spatial_order_close_to_fp64(cclib, plummer_ic):
@@ -108,10 +122,14 @@ def test_mixed_spatial_order_close_to_fp64(cclib, plummer_ic):
     and every particle comes back."""
     m, x, v = plummer_ic(4096, seed=6)
     out = {}
+    pairs = []
     for name, prec in (("fp64", cclib.PREC_FP64), ("mixed", cclib.PREC_MIXED)):
-        c = cclib.Context(m, x, v, dt=1 / 256, precision=prec)
+        c = cclib.Context(m, x, v, dt=1 / 256, precision=prec, near_tol=1e-6)
         E0, _, _ = c.energy()
-        c.evolve(10 / 256)
+        # one step per call, so that every step's near-threshold pairs are read
+        for k in range(10):
+            c.evolve((k + 1) / 256)
+            pairs.append(c.near_pairs()[0])
         E1, _, _ = c.energy()
         _, gm, gx, gv = c.get_state()
         out[name] = (gm, gx, gv, (E1 - E0) / abs(E0), c.stats())
@@ -120,5 +138,9 @@ def test_mixed_spatial_order_close_to_fp64(cclib, plummer_ic):
     assert np.array_equal(gm, m) and np.all(np.isfinite(gx)) and np.all(np.isfinite(gv))
     dv = np.linalg.norm(gv - out["fp64"][2], axis=0) / np.linalg.norm(out["fp64"][2], axis=0)
     assert np.median(dv) < 1e-7, np.median(dv)
+    S = B.abs_accel_sum(m, x)
+    ex = B.near_bodies(np.concatenate(pairs)) if pairs else ()
+    wv, _ = B.check_velocity_bound(gv, out["fp64"][2], S, 1 / 256, st["max_depth_seen"], steps=10, exempt=ex)
+    print("mixed vs FP64, 10 steps: max error / bound", wv, "exempt", len(ex))
     assert abs(dE) < 1e-6 and abs(dE - out["fp64"][3]) < 1e-7, (dE, out["fp64"][3])
     assert abs(st["splits"] - out["fp64"][4]["splits"]) <= 0.01 * out["fp64"][4]["splits"]

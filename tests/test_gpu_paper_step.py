@@ -7,6 +7,7 @@ paper's printed ones in test_oracle_paper_counts.py)."""
 import numpy as np
 import pytest
 
+import _bounds as B
 from oracle import oracle as O
 from paper_1407_7105_gb300 import ics
 
@@ -18,10 +19,11 @@ def test_paper_first_global_step_counts_and_state(cclib):
     s = O.State(m, x, v)
     st = O.evolve(s, O.params(eta=0.01, eps=1.0 / 256, dt=700.0 / 512), 1)
     for prec in (cclib.PREC_FP64, cclib.PREC_MIXED):
-        c = cclib.Context(m, x, v, dt=700.0 / 512, eta=0.01, eps=1.0 / 256, precision=prec)
+        c = cclib.Context(m, x, v, dt=700.0 / 512, eta=0.01, eps=1.0 / 256, precision=prec, near_tol=1e-6)
         c.evolve(700.0 / 512)
         g = c.stats()
         _, _, gx, gv = c.get_state()
+        pairs, _, _ = c.near_pairs()
         c.close()
         assert g["splits"] == st.splits and g["kick_pairs"] == st.kick_pairs and g["drifts"] == st.drifts, (prec, g)
         assert g["tau_pairs"] == st.tau_pairs and g["max_depth_seen"] == st.max_depth_seen
@@ -30,3 +32,6 @@ def test_paper_first_global_step_counts_and_state(cclib):
         else:
             dv = np.linalg.norm(gv - s.v3, axis=0) / np.linalg.norm(s.v3, axis=0)
             assert np.median(dv) < 1e-7, np.median(dv)
+            S = B.abs_accel_sum(m, x, eps=1.0 / 256)
+            w, _ = B.check_velocity_bound(gv, s.v3, S, 700.0 / 512, st.max_depth_seen, exempt=B.near_bodies(pairs))
+            print("paper step mixed: max error / bound", w)

@@ -5,6 +5,7 @@ finishes in seconds."""
 import numpy as np
 import pytest
 
+import _bounds as B
 from oracle import oracle as O
 from paper_1407_7105_gb300 import ics
 
@@ -36,14 +37,21 @@ def test_fractal_components_and_step_fp64(cclib, seed):
 
 def test_fractal_mixed_close_to_oracle(cclib):
     m, x, v = ics.box_fractal(1200, seed=3)
-    c = cclib.Context(m, x, v, dt=1 / 256, precision=cclib.PREC_MIXED)
-    c.evolve(2 / 256)
+    c = cclib.Context(m, x, v, dt=1 / 256, precision=cclib.PREC_MIXED, near_tol=1e-6)
+    pairs = []
+    for k in range(2):
+        c.evolve((k + 1) / 256)
+        pairs.append(c.near_pairs()[0])
     _, _, gx, gv = c.get_state()
     c.close()
     s = O.State(m, x, v)
-    O.evolve(s, O.params(dt=1 / 256), 2)
+    st = O.evolve(s, O.params(dt=1 / 256), 2)
     dv = np.linalg.norm(gv - s.v3, axis=0) / np.linalg.norm(s.v3, axis=0)
     assert np.median(dv) < 1e-8
+    S = B.abs_accel_sum(m, x)
+    ex = B.near_bodies(np.concatenate(pairs))
+    w, _ = B.check_velocity_bound(gv, s.v3, S, 1 / 256, st.max_depth_seen, steps=2, exempt=ex)
+    print("fractal mixed: max error / bound", w, "exempt", ex.size)
 
 
 def _systems(nsys, seed):
@@ -55,9 +63,12 @@ def _systems(nsys, seed):
 def test_small_systems_batch(cclib, prec):
     m, x, v, off = _systems(40, seed=5)
     p = cclib.PREC_FP64 if prec == "fp64" else cclib.PREC_MIXED
-    c = cclib.Context(m, x, v, dt=1 / 64, precision=p)
+    c = cclib.Context(m, x, v, dt=1 / 64, precision=p, near_tol=1e-6)
     c.set_systems(off)
-    c.evolve(2 / 64)
+    pairs = []
+    for k in range(2):
+        c.evolve((k + 1) / 64)
+        pairs.append(c.near_pairs()[0])
     _, _, gx, gv = c.get_state()
     g = c.stats()
     c.close()
@@ -70,6 +81,10 @@ def test_small_systems_batch(cclib, prec):
     else:
         dv = np.linalg.norm(gv - s.v3, axis=0) / np.linalg.norm(s.v3, axis=0)
         assert np.median(dv) < 1e-7, np.median(dv)
+        S = B.abs_accel_sum(m, x, groups=B.system_index(m.shape[0], off))
+        ex = B.near_bodies(np.concatenate(pairs))
+        w, _ = B.check_velocity_bound(gv, s.v3, S, 1 / 64, st.max_depth_seen, steps=2, exempt=ex)
+        print("systems mixed: max error / bound", w, "exempt", ex.size)
         # every system keeps its own momentum (they never interact)
         for a, b in zip(off[:-1], off[1:]):
             P = (m[a:b] * gv[:, a:b]).sum(axis=1)
