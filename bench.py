@@ -7,7 +7,13 @@ component, all in libcc.so's kernels.  The metric counts interactions =
 tau pairs (n(n-1)/2 per split set) + cross-component kick pairs, per second.
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--form fp64|mixed]
-  python bench.py --impl reference ...   (the FP64 CPU oracle, bounded sample)
+  python bench.py --impl reference ...   (the FP64 CPU oracle: full outer steps,
+                                          row loops on all host cores)
+
+The bench line also carries (N = 1, rank 0) the metric's accuracy gate (both
+forms to t = 1: |dE/E|, momentum drift, time to solution), the mixed kick's
+force error against FP64 on the bench state, and the other configurations
+(65536-body fractal, 32768-body binaries, 4096 systems) in both forms.
 
 Multi-GPU: the integrator does not shard (one system per GPU); N ranks run
 N independent replicas (different seeds) and value sums their work over the
@@ -34,9 +40,11 @@ UNIT = "interactions/s"
 N_BODY = 16384
 DT = 1.0 / 256
 ETA = 0.03
-# algorithmic FP64 operations per unordered pair (sqrt and division count 1)
+# algorithmic operations per unordered pair (sqrt and division count 1)
 TAU_FLOPS = 47   # Eq. tauij as evaluated: 3 sqrt, 6 div, 38 add/sub/mul
-KICK_FLOPS = 28  # one pair force applied to both bodies (Eqs. kickij/kickji)
+KICK_FLOPS = 25  # one pair force applied to both bodies (Eqs. kickij/kickji): the difference (3), r^2 (6),
+                 # r^-3 (sqrt, mul, div: 3), the weights (2 x 2) and the two 3-vector updates (2 x 3); the
+                 # row form evaluates each pair from both sides, which is not credited
 
 
 WORKLOADS = {
@@ -165,49 +173,50 @@ def measured_peaks():
 
 
 # ------------------------------------------------------------------ oracle
-def oracle_sample(m, x, v, reps: int = 1):
-    """The FP64 CPU oracle on a bounded sample of the workload: the top-level
-    split_cc of all N bodies at h = dt followed by the level's
-    drift-kick-drift (no recursion).  Returns (interactions, seconds)."""
+def oracle_step(s, steps: int = 1):
+    """The FP64 CPU oracle on the workload itself: `steps` full outer steps
+    evolve_cc(all, dt) of the state s (recursion included), its row loops
+    on every host core (OpenMP; results identical to one thread).  Returns
+    (interactions, seconds, threads): interactions = tau pairs decided +
+    kick pairs, the GPU's count."""
     from oracle import oracle as O
-    s = O.State(m, x, v)
     p = O.params(eta=ETA, dt=DT)
-    inter = 0
+    nthreads = O.threads(0)
+    st = O.Stats()
     t0 = time.perf_counter()
-    for _ in range(reps):
-        st = O.Stats()
-        lab, _ = O.components(s, p, DT, stats=st)
-        ids = np.arange(s.n, dtype=np.int32)
-        O.drift(s, ids, lab, 0.5 * DT, stats=st)
-        O.kick(s, p, ids, lab, DT, stats=st)
-        O.drift(s, ids, lab, 0.5 * DT, stats=st)
-        inter += st.tau_pairs + st.kick_pairs
-    return inter, time.perf_counter() - t0
+    O.evolve(s, p, steps, stats=st)
+    sec = time.perf_counter() - t0
+    return st.tau_pairs + st.kick_pairs, sec, nthreads
+
+
+ORACLE_SAMPLE = ("per step: one full outer step evolve_cc(all, dt=1/256) of the 16384-body sphere, recursion "
+                 "included (the GPU's step), FP64 oracle with its row loops on all host cores (OpenMP, results "
+                 "identical to one thread)")
 
 
 def run_reference(args, rank, world):
     from oracle import oracle as O
-    O.build()
     if rank != 0:
         return 0
+    O.build()
     from paper_1407_7105_gb300 import ics
     m, x, v = ics.plummer(N_BODY, seed=args.seed)
+    s = O.State(m, x, v)
     for _ in range(args.warmup):
-        oracle_sample(m, x, v)
-    inter, sec = 0, 0.0
+        oracle_step(s)
+    inter, sec, cores = 0, 0.0, 1
     for _ in range(args.steps):
-        i, s = oracle_sample(m, x, v)
+        i, dt_s, cores = oracle_step(s)
         inter += i
-        sec += s
+        sec += dt_s
     val = inter / sec
     line = {
         "impl": "reference", "metric": METRIC, "value": val, "unit": UNIT, "n_gpus": args.gpus,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * sec / max(1, args.steps),
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
         "config": {"workload": workload_name(), "form": "oracle"},
-        "cpu_baseline": {"value": val, "unit": UNIT, "cores": 1, "kind": "oracle",
-                         "sample": "per step: top-level split_cc (BFS, lazy tau) of all 16384 bodies at h=dt "
-                                   "plus that level's drift-kick-drift, single thread"},
+        "cpu_baseline": {"value": val, "unit": UNIT, "cores": cores, "kind": "oracle", "sample": ORACLE_SAMPLE,
+                         "same_config": True},
         "e2e": {"value": val, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }
     print(json.dumps(line), flush=True)
@@ -215,11 +224,137 @@ def run_reference(args, rank, world):
 
 
 # ------------------------------------------------------------------ GPU arm
+def _ctx(cc, dm, dx, dv, sys_off, workload, form, h_fp64_rel, s_small):
+    """A context of the given form on a device-resident state."""
+    W = WORKLOADS[workload]
+    prec = cc.PREC_MIXED if form == "mixed" else cc.PREC_FP64
+    ctx = cc.Context(dm, dx, dv, dt=W["dt"], eta=ETA, precision=prec, h_fp64=h_fp64_rel * W["dt"],
+                     s_small=s_small, kepler=int(W["kepler"]))
+    if sys_off is not None:
+        ctx.set_systems(sys_off)
+    return ctx
+
+
+def time_steps(ctx, dt, t, steps, stream, l2_flush=None):
+    """`steps` outer steps, each bracketed by CUDA events on the library's
+    stream (L2 flushed before each when l2_flush is given).  Returns
+    (t, total ms, per-step ms, stats before, stats after)."""
+    import torch
+    st0 = ctx.stats()
+    total, per = 0.0, []
+    for _ in range(steps):
+        if l2_flush is not None:
+            l2_flush.fill_(1)
+        torch.cuda.synchronize()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        t += dt
+        ctx.evolve(t)
+        e1.record(stream)
+        e1.synchronize()
+        per.append(e0.elapsed_time(e1))
+        total += per[-1]
+    return t, total, per, st0, ctx.stats()
+
+
+def _work(st0, st1):
+    d = {k: st1[k] - st0[k] for k in ("tau_pairs", "kick_pairs", "tau_evaluated", "tau_fp64", "edges", "launches",
+                                      "splits")}
+    d["interactions"] = d["tau_pairs"] + d["kick_pairs"]
+    d["interactions_evaluated"] = d["tau_evaluated"] + d["kick_pairs"]
+    return d
+
+
+def accuracy_gate(cc, dm, dx, dv, t_end, h_fp64_rel):
+    """The metric's accuracy gate on the bench workload: each form integrates
+    the same state to t_end (one N-body time = 256 outer steps); |dE/E|,
+    momentum and angular-momentum drift and the time to solution."""
+    import torch
+    out = []
+    steps = int(round(t_end / DT))
+    for form, hf in (("mixed", 0.0), ("mixed", h_fp64_rel), ("fp64", 0.0)):
+        ctx = _ctx(cc, dm, dx, dv, None, "plummer", form, hf, 32)
+        E0, P0, L0 = ctx.energy()
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        ctx.evolve(steps * DT)
+        torch.cuda.synchronize()
+        sec = time.perf_counter() - t0
+        E1, P1, L1 = ctx.energy()
+        st = ctx.stats()
+        ctx.close()
+        inter = st["tau_pairs"] + st["kick_pairs"]
+        out.append({"form": form, "h_fp64": f"{hf}*dt", "t_end": steps * DT, "steps": steps, "seconds": round(sec, 4),
+                    "interactions_per_s": inter / sec, "dE_over_E": (E1 - E0) / abs(E0),
+                    "dP": float(np.abs(P1 - P0).max()), "dL": float(np.abs(L1 - L0).max()),
+                    "max_depth": st["max_depth_seen"], "gate_1e-6": abs((E1 - E0) / E0) <= 1e-6})
+    return out
+
+
+def force_error(cc, m, x, v, dev):
+    """Relative error of the mixed kick's accelerations against the FP64
+    kick on the bench state (every pair: all labels distinct), per body."""
+    import torch
+    n = m.shape[0]
+    labels = np.arange(n, dtype=np.int32)
+    acc = {}
+    for form in ("fp64", "mixed"):
+        dm, dx, dv = (torch.tensor(a, device=dev) for a in (m, x, v))
+        ctx = _ctx(cc, dm, dx, dv, None, "plummer", form, 0.0, 32)
+        ctx.kick(labels, 1.0)
+        _, _, _, gv = ctx.get_state()
+        ctx.close()
+        acc[form] = gv - v
+    err = np.linalg.norm(acc["mixed"] - acc["fp64"], axis=0) / np.linalg.norm(acc["fp64"], axis=0)
+    return {"median": float(np.median(err)), "p99": float(np.quantile(err, 0.99)), "max": float(err.max()),
+            "state": "bench initial state, all N(N-1)/2 pairs"}
+
+
+def other_configs(cc, dev, stream, seed, l2_flush):
+    """The other configurations, both forms, a few steps each: ms per step,
+    interactions/s (decided and evaluated tau pairs) and |dE/E| over the
+    steps.  The binaries also run the mixed form with FP64 forces below
+    h_fp64 = dt/64 (close subsystems)."""
+    import argparse as _ap
+    import torch
+    out = {}
+    plan = (("fractal", 65536, [("mixed", 0.0), ("fp64", 0.0)]),
+            ("binaries", 32768, [("mixed", 0.0), ("mixed", 1.0 / 64), ("fp64", 0.0)]),
+            ("systems", 0, [("mixed", 0.0), ("fp64", 0.0)]))
+    for wl, n, forms in plan:
+        a = _ap.Namespace(workload=wl, n=n, nsys=4096)
+        m, x, v, sys_off = make_workload(a, seed, dev)
+        dm, dx, dv = (torch.tensor(q, device=dev) for q in (m, x, v))
+        rows = []
+        for form, hf in forms:
+            ctx = _ctx(cc, dm, dx, dv, sys_off, wl, form, hf, 32)
+            E0, _, _ = ctx.energy()
+            dtw = WORKLOADS[wl]["dt"]
+            w0 = time.perf_counter()
+            t = dtw
+            ctx.evolve(t)  # warm-up step (allocations, tuner trials)
+            torch.cuda.synchronize()
+            warm_s = time.perf_counter() - w0
+            steps = 3 if warm_s < 0.5 else (2 if warm_s < 3.0 else 1)
+            t, ms, per, st0, st1 = time_steps(ctx, dtw, t, steps, stream, l2_flush)
+            E1, _, _ = ctx.energy()
+            ctx.close()
+            w = _work(st0, st1)
+            rows.append({"form": form, "h_fp64": f"{hf}*dt", "steps": steps, "ms_per_step": ms / steps,
+                         "interactions_per_s": w["interactions"] / (ms * 1e-3),
+                         "evaluated_interactions_per_s": w["interactions_evaluated"] / (ms * 1e-3),
+                         "dE_over_E": (E1 - E0) / abs(E0), "steps_for_dE": steps + 1})
+        out[wl] = {"workload": workload_name(m.shape[0], wl, 4096), "n": int(m.shape[0]), "forms": rows}
+    return out
+
+
+# ------------------------------------------------------------------ GPU arm
 def run_gpu(args, rank, world):
     import torch
     import torch.distributed as dist
 
-    from paper_1407_7105_gb300 import build, cc, ics
+    from paper_1407_7105_gb300 import build, cc
 
     local = int(os.environ.get("LOCAL_RANK", "0"))
     torch.cuda.set_device(local)
@@ -228,40 +363,31 @@ def run_gpu(args, rank, world):
     seed = args.seed + rank
     m, x, v, sys_off = make_workload(args, seed, dev)
     N = int(m.shape[0])
-    W = WORKLOADS[args.workload]
-    DTW = W["dt"]
+    DTW = WORKLOADS[args.workload]["dt"]
+    extras = rank == 0 and world == 1
 
     cpu = None
-    if rank == 0 and world == 1 and not args.no_cpu_baseline and args.workload == "plummer":
+    if extras and not args.no_cpu_baseline and args.workload == "plummer":
         from oracle import oracle as O
         O.build()
-        inter, sec = oracle_sample(m, x, v)
-        cpu = {"value": inter / sec, "unit": UNIT, "cores": 1, "kind": "oracle",
-               "sample": "top-level split_cc (BFS, lazy tau) of all 16384 bodies at h=dt plus that level's "
-                         "drift-kick-drift, single thread, same initial state"}
+        inter, sec, cores = oracle_step(O.State(m, x, v))
+        cpu = {"value": inter / sec, "unit": UNIT, "cores": cores, "kind": "oracle", "sample": ORACLE_SAMPLE
+               .replace("per step: one", "one") + ", same initial state", "seconds": round(sec, 3),
+               "same_config": True}
 
     stream = torch.cuda.current_stream(dev)
     f64_peak, f32_peak = cc.probe_peaks()
     l2_flush = torch.empty(64 * 1024 * 1024, dtype=torch.int32, device=dev)  # 256 MB > L2
     dm, dx, dv = (torch.tensor(a, device=dev) for a in (m, x, v))
 
-    def make_ctx(form):
-        prec = cc.PREC_MIXED if form == "mixed" else cc.PREC_FP64
-        ctx = cc.Context(dm, dx, dv, dt=DTW, eta=ETA, precision=prec, h_fp64=args.h_fp64 * DTW,
-                         s_small=args.s_small, kepler=int(W["kepler"]))
-        if sys_off is not None:
-            ctx.set_systems(sys_off)
-        return ctx
-
     def time_form(form, steps, warmup, clocks_too):
-        ctx = make_ctx(form)
+        ctx = _ctx(cc, dm, dx, dv, sys_off, args.workload, form, args.h_fp64, args.s_small)
         E0, _, _ = ctx.energy()
         t = 0.0
         for _ in range(warmup):
             t += DTW
             ctx.evolve(t)
         torch.cuda.synchronize()
-        st0 = ctx.stats()
         ctx.set_timing(True)
         sampler = ClockSampler(local) if clocks_too else None
         if dist.is_initialized():
@@ -270,47 +396,25 @@ def run_gpu(args, rank, world):
         if sampler:
             sampler.start()
         torch.cuda.nvtx.range_push("timed_region")
-        total_ms = 0.0
-        step_ms = []
-        for _ in range(steps):
-            l2_flush.fill_(1)
-            torch.cuda.synchronize()
-            e0 = torch.cuda.Event(enable_timing=True)
-            e1 = torch.cuda.Event(enable_timing=True)
-            e0.record(stream)
-            t += DTW
-            ctx.evolve(t)
-            e1.record(stream)
-            e1.synchronize()
-            step_ms.append(e0.elapsed_time(e1))
-            total_ms += step_ms[-1]
+        t, total_ms, step_ms, st0, st1 = time_steps(ctx, DTW, t, steps, stream, l2_flush)
         torch.cuda.synchronize()
         torch.cuda.nvtx.range_pop()
         clocks = sampler.stop() if sampler else None
-        st1 = ctx.stats()
         tm = ctx.timing()
         tuning = ctx.tuning()
         ctx.set_timing(False)
         E1, _, _ = ctx.energy()
-        res = {"ctx": ctx, "t": t, "total_ms": total_ms, "step_ms": step_ms, "clocks": clocks, "timing": tm,
-               "tuning": tuning,
-               "inter": (st1["tau_pairs"] - st0["tau_pairs"]) + (st1["kick_pairs"] - st0["kick_pairs"]),
-               "launches": st1["launches"] - st0["launches"],
-               "tau_fp64": st1["tau_fp64"] - st0["tau_fp64"], "tau_pairs": st1["tau_pairs"] - st0["tau_pairs"],
-               "tau_evaluated": st1["tau_evaluated"] - st0["tau_evaluated"],
-               "kick_pairs": st1["kick_pairs"] - st0["kick_pairs"],
-               "edges": st1["edges"] - st0["edges"],
-               "dE": (E1 - E0) / abs(E0)}
-        return res
+        return {"ctx": ctx, "t": t, "total_ms": total_ms, "step_ms": step_ms, "clocks": clocks, "timing": tm,
+                "tuning": tuning, "work": _work(st0, st1), "dE": (E1 - E0) / abs(E0)}
 
     head = time_form(args.form, args.steps, args.warmup, True)
     other_form = "fp64" if args.form == "mixed" else "mixed"
-    other = None if args.single_form else time_form(other_form, max(1, min(args.steps, 3)), 1, False)
+    osteps = max(1, min(args.steps, 3))
+    other = None if args.single_form else time_form(other_form, osteps, 1, False)
     if other:
         other["ctx"].close()
     ctx, t = head["ctx"], head["t"]
-    total_ms, clocks, tm, inter, launches = (head["total_ms"], head["clocks"], head["timing"], head["inter"],
-                                             head["launches"])
+    total_ms, clocks, tm, work = head["total_ms"], head["clocks"], head["timing"], head["work"]
 
     # end to end through the C ABI with host buffers (pinned)
     hm = torch.empty(N, dtype=torch.float64).pin_memory()
@@ -330,12 +434,16 @@ def run_gpu(args, rank, world):
     e2e_sec = time.perf_counter() - w0
     st3 = ctx.stats()
     e2e_inter = (st3["tau_pairs"] - st2["tau_pairs"]) + (st3["kick_pairs"] - st2["kick_pairs"])
+    ctx.close()
 
     # max over ranks, sums of work
-    (sec, e2e_sec), (inter, e2e_inter) = combine_ranks([total_ms * 1e-3, e2e_sec], [inter, e2e_inter], dev)
+    inter = work["interactions"]
+    (sec, e2e_sec), (inter, e2e_inter, inter_eval) = combine_ranks(
+        [total_ms * 1e-3, e2e_sec], [inter, e2e_inter, work["interactions_evaluated"]], dev)
     value = inter / sec
 
-    # roofline of the dominant pairwise kernel (measured live above)
+    # roofline of the dominant pairwise kernel (measured live above) and of
+    # the small-component kernel (tau pairs it evaluated + kick pairs)
     fp32 = args.form == "mixed"
     if tm["tau_ms"] >= tm["kick_ms"]:
         kname, kms, kl, flops = "tau", tm["tau_ms"], tm["tau_launches"], TAU_FLOPS * tm["tau_pairs"]
@@ -345,26 +453,51 @@ def run_gpu(args, rank, world):
             ("k_tau_hook" if kname == "tau" else "k_kick64")
     achieved = flops / (kms * 1e-3) / 1e12 if kms > 0 else None
     peak = (f32_peak if fp32 else f64_peak) / 1e12
+    small_flops = TAU_FLOPS * tm["small_tau_evaluated"] + KICK_FLOPS * tm["small_kick_pairs"]
+    small_ach = small_flops / (tm["small_ms"] * 1e-3) / 1e12 if tm["small_ms"] > 0 else None
     roof = {"bound": "alu", "kernel": kname, "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
             "frac": (achieved / peak) if achieved else None, "traffic": None,
-            "peak_source": ("FP32" if fp32 else "FP64") + " FMA throughput measured by cc_probe_peaks on this GPU",
+            "peak_source": ("FP32" if fp32 else "FP64") + " FMA throughput measured by cc_probe_peaks on this GPU "
+                           "(MEASURED_PEAKS.json has no FP32/FP64 figure)",
             "algorithmic_flops_per_pair": TAU_FLOPS if kname.startswith("k_tau") else KICK_FLOPS,
             "kernel_ms_per_step": kms / args.steps, "launches_per_step": kl / args.steps,
             "tau_ms_per_step": tm["tau_ms"] / args.steps, "kick_ms_per_step": tm["kick_ms"] / args.steps,
-            "small_kernel_ms_per_step": tm["small_ms"] / args.steps,
+            "tau_tflops": TAU_FLOPS * tm["tau_pairs"] / (tm["tau_ms"] * 1e-3) / 1e12 if tm["tau_ms"] > 0 else None,
+            "kick_tflops": KICK_FLOPS * tm["kick_pairs"] / (tm["kick_ms"] * 1e-3) / 1e12 if tm["kick_ms"] else None,
+            "small_kernel": {"kernel": "k_small", "ms_per_step": tm["small_ms"] / args.steps,
+                             "launches_per_step": tm["small_launches"] / args.steps,
+                             "tau_pairs_evaluated_per_step": tm["small_tau_evaluated"] / args.steps,
+                             "kick_pairs_per_step": tm["small_kick_pairs"] / args.steps,
+                             "achieved": small_ach, "frac": small_ach / peak if small_ach else None,
+                             "bound": "latency (one warp per component)"},
             "fp64_peak_tflops": f64_peak / 1e12, "fp32_peak_tflops": f32_peak / 1e12}
     other_line = None
     if other:
-        other_line = {"form": other_form, "value": other["inter"] / (other["total_ms"] * 1e-3),
-                      "ms_per_step": other["total_ms"] / max(1, min(args.steps, 3)), "dE_over_E": other["dE"],
-                      "tau_ms_per_step": other["timing"]["tau_ms"] / max(1, min(args.steps, 3)),
-                      "kick_ms_per_step": other["timing"]["kick_ms"] / max(1, min(args.steps, 3)),
-                      "small_kernel_ms_per_step": other["timing"]["small_ms"] / max(1, min(args.steps, 3))}
+        ow = other["work"]
+        other_line = {"form": other_form, "value": ow["interactions"] / (other["total_ms"] * 1e-3),
+                      "evaluated_value": ow["interactions_evaluated"] / (other["total_ms"] * 1e-3),
+                      "ms_per_step": other["total_ms"] / osteps, "dE_over_E": other["dE"],
+                      "tau_ms_per_step": other["timing"]["tau_ms"] / osteps,
+                      "kick_ms_per_step": other["timing"]["kick_ms"] / osteps,
+                      "small_kernel_ms_per_step": other["timing"]["small_ms"] / osteps,
+                      "tau_tflops": TAU_FLOPS * other["timing"]["tau_pairs"] / (other["timing"]["tau_ms"] * 1e-3) / 1e12
+                      if other["timing"]["tau_ms"] > 0 else None,
+                      "kick_tflops": KICK_FLOPS * other["timing"]["kick_pairs"] / (other["timing"]["kick_ms"] * 1e-3)
+                      / 1e12 if other["timing"]["kick_ms"] > 0 else None}
+
+    accuracy = forces = configs = None
+    if extras and args.workload == "plummer" and not args.no_extras:
+        forces = force_error(cc, m, x, v, dev)
+        accuracy = accuracy_gate(cc, dm, dx, dv, args.t_end, args.h_fp64_gate)
+        configs = other_configs(cc, dev, stream, args.seed, l2_flush)
     if rank == 0:
         line = {
             "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": total_ms / args.steps,
-            "step_ms": [round(x, 4) for x in head["step_ms"]], "higher_is_better": True,
+            "step_ms": [round(q, 4) for q in head["step_ms"]], "higher_is_better": True,
+            # the same steps counting only the tau pairs a kernel evaluated
+            # (first-half splits decide theirs from the parent split's values)
+            "evaluated_value": inter_eval / sec,
             # launch shapes the online tuner picked, per kernel and size bin
             # (pairs in [2^bin, 2^(bin+1))): [kernel, bin, [shape, column
             # slices] picked, us per 1e6 pairs of each variant]
@@ -372,37 +505,39 @@ def run_gpu(args, rank, world):
                           [e["shape"][e["best"]], e["slices"][e["best"]]] if e["best"] >= 0 else None,
                           e["us_per_mpair"]] for e in head["tuning"]],
             "scaling": "weak", "vs_baseline": None, "dtype": "f32/f64" if fp32 else "f64", "data": "synthetic",
-            "config": {"workload": workload_name(N, args.workload, args.nsys), "form": args.form, "h_fp64": f"{args.h_fp64}*dt",
-                       "s_small": args.s_small,
+            "config": {"workload": workload_name(N, args.workload, args.nsys), "form": args.form,
+                       "h_fp64": f"{args.h_fp64}*dt", "s_small": args.s_small,
                        "l2": "flushed (256 MB write) before each step",
                        "parallelism": "replicas" if world > 1 else "single GPU"},
             "e2e": {"value": e2e_inter / e2e_sec, "unit": UNIT, "h2d_bytes_per_step": 7 * N * 8,
                     "d2h_bytes_per_step": 6 * N * 8, "steps": e2e_steps},
-            "gpu_launches": launches,
+            "gpu_launches": work["launches"],
             "roofline": roof,
             "cpu_baseline": cpu,
             "clocks": clocks,
             "dE_over_E": head["dE"],
-            "tau_fp64_fraction": head["tau_fp64"] / max(1, head["tau_pairs"]),
+            "tau_fp64_fraction": work["tau_fp64"] / max(1, work["tau_pairs"]),
             "interactions_per_step": inter / args.steps / world,
             # interactions = tau pairs decided by the splits + kick pairs; a
             # first-half split decides its pairs from the tau values its
             # parent split computed, so fewer pairs are evaluated than decided
-            "tau_pairs_per_step": head["tau_pairs"] / args.steps,
-            "tau_pairs_evaluated_per_step": head["tau_evaluated"] / args.steps,
-            "kick_pairs_per_step": head["kick_pairs"] / args.steps,
-            "edges_per_step": head["edges"] / args.steps,
+            "tau_pairs_per_step": work["tau_pairs"] / args.steps,
+            "tau_pairs_evaluated_per_step": work["tau_evaluated"] / args.steps,
+            "kick_pairs_per_step": work["kick_pairs"] / args.steps,
+            "edges_per_step": work["edges"] / args.steps,
+            "splits_per_step": work["splits"] / args.steps,
             "other_form": other_line,
+            "accuracy": accuracy,
+            "force_error": forces,
+            "configs": configs,
         }
         print(json.dumps(line), flush=True)
-    ctx.close()
     return 0
 
 
 def run_accuracy(args):
-    """The accuracy gate of the metric: both forms integrate the workload to
-    t = 1 (256 outer steps) from the same state; |dE/E|, momentum drift and
-    time to solution are reported per form (JSON lines, not the bench line)."""
+    """The accuracy gate alone (JSON lines): both forms integrate the
+    workload to --t-end from the same state."""
     import torch
 
     from paper_1407_7105_gb300 import build, cc, ics
@@ -410,25 +545,8 @@ def run_accuracy(args):
     m, x, v = ics.plummer(args.n, seed=args.seed)
     dev = torch.device("cuda", 0)
     dm, dx, dv = (torch.tensor(a, device=dev) for a in (m, x, v))
-    steps = int(round(args.t_end / DT))
-    for form, hf in (("mixed", 0.0), ("mixed", args.h_fp64 or 1.0 / 16), ("fp64", 0.0)):
-        prec = cc.PREC_MIXED if form == "mixed" else cc.PREC_FP64
-        ctx = cc.Context(dm, dx, dv, dt=DT, eta=ETA, precision=prec, h_fp64=hf * DT)
-        E0, P0, L0 = ctx.energy()
-        torch.cuda.synchronize()
-        t0 = time.perf_counter()
-        ctx.evolve(steps * DT)
-        torch.cuda.synchronize()
-        sec = time.perf_counter() - t0
-        E1, P1, L1 = ctx.energy()
-        st = ctx.stats()
-        ctx.close()
-        inter = st["tau_pairs"] + st["kick_pairs"]
-        print(json.dumps({"accuracy": True, "form": form, "h_fp64": f"{hf}*dt", "t_end": steps * DT,
-                          "steps": steps, "seconds": sec, "interactions": inter, "interactions_per_s": inter / sec,
-                          "dE_over_E": (E1 - E0) / abs(E0), "dP": float(np.abs(P1 - P0).max()),
-                          "dL": float(np.abs(L1 - L0).max()), "max_depth": st["max_depth_seen"],
-                          "tau_fp64_fraction": st["tau_fp64"] / max(1, st["tau_pairs"])}), flush=True)
+    for row in accuracy_gate(cc, dm, dx, dv, args.t_end, args.h_fp64_gate):
+        print(json.dumps({"accuracy": True, **row}), flush=True)
     return 0
 
 
@@ -445,6 +563,10 @@ def main():
     ap.add_argument("--s-small", type=int, default=32,
                     help="components of at most this many bodies run in the small-component kernel (0: none)")
     ap.add_argument("--accuracy", action="store_true", help="integrate both forms to --t-end and report dE/E")
+    ap.add_argument("--h-fp64-gate", type=float, default=1.0 / 16,
+                    help="accuracy gate: the mixed form's second run takes FP64 forces below this times dt")
+    ap.add_argument("--no-extras", action="store_true",
+                    help="skip the accuracy gate, the force error and the other configurations")
     ap.add_argument("--t-end", type=float, default=1.0)
     ap.add_argument("--seed", type=int, default=1)
     ap.add_argument("--n", type=int, default=None, help="bodies (default per workload)")
