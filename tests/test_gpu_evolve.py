@@ -139,7 +139,10 @@ def test_kepler_mode_well_conditioned_bodies_elementwise(cclib):
     Kepler phase's rounding: 2^14 u64 dt S_i (D + 1), S_i the sum of
     absolute pair accelerations (for a binary member dominated by its
     partner's, so that dt S_i ~ |v| x the radians the orbit turns through
-    in the step).  Positions likewise within dt times that."""
+    in the step), plus the rounding of the coordinates themselves (4 u64
+    |v_i|); positions within dt times the velocity bound plus 4 u64 |x_i|
+    (a wide pair's orbit barely turns in the step, and the rounding of its
+    absolute coordinates is then the larger term)."""
     m, x, v = ics.plummer_with_binaries(512, seed=3)
     dt = 1 / 2048
     c = cclib.Context(m, x, v, dt=dt, kepler=1)
@@ -157,9 +160,11 @@ def test_kepler_mode_well_conditioned_bodies_elementwise(cclib):
     assert calm.size > 0.8 * m.shape[0], calm.size
     S = B.abs_accel_sum(m, x)
     tol = 2.0 ** 14 * B.U64 * dt * S * (st.max_depth_seen + 1)
+    tol_v = tol + 4 * B.U64 * np.linalg.norm(s.v3, axis=0)
+    tol_x = dt * tol + 4 * B.U64 * np.linalg.norm(s.x3, axis=0)
     ev = np.linalg.norm(gv - s.v3, axis=0)
     ex = np.linalg.norm(gx - s.x3, axis=0)
-    rv, rx = ev[calm] / tol[calm], ex[calm] / (dt * tol[calm])
+    rv, rx = ev[calm] / tol_v[calm], ex[calm] / tol_x[calm]
     print("Kepler mode: well-conditioned bodies", calm.size, "max error / bound: v", rv.max(), "x", rx.max())
     assert rv.max() <= 1.0 and rx.max() <= 1.0, (rv.max(), rx.max())
 
