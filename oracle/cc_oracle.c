@@ -479,6 +479,83 @@ int orc_evolve_cc(int64_t n, double *x3, double *v3, const double *m,
     return rc;
 }
 
+/* ------------------------------------------------------------------ */
+/* the HOLD split and evolve_hold (Sec. 2.1, Eq. HOLD)                  */
+/* ------------------------------------------------------------------ */
+int64_t orc_hold_split(int64_t n, const double *x3, const double *v3, const double *m,
+                       const orc_params *p, const int32_t *set, int64_t nset,
+                       double h, int32_t *labels_out, orc_stats *st)
+{
+    if (nset < 0) return ORC_E_ARG;
+    double *tmin = (double *)malloc(sizeof(double) * (nset > 0 ? nset : 1));
+    /* tau(i) = min over j != i of tau(i,j): a row minimum per member (tau is
+     * symmetric bit for bit, so each row holds the pair's one value) */
+#pragma omp parallel for schedule(dynamic, 16) if (nset >= ORC_PAR_MIN)
+    for (int64_t a = 0; a < nset; ++a) {
+        double t = INFINITY;
+        for (int64_t b = 0; b < nset; ++b) {
+            if (b == a) continue;
+            double tab = orc_tau_ids(n, x3, v3, m, p, set[a], set[b]);
+            if (tab < t) t = tab;
+        }
+        tmin[a] = t;
+    }
+    int32_t fmin = 0;
+    int64_t nf = 0;
+    for (int64_t a = 0; a < nset; ++a)
+        if (tmin[a] < h) {
+            if (nf == 0 || set[a] < fmin) fmin = set[a];
+            nf++;
+        }
+    for (int64_t a = 0; a < nset; ++a) labels_out[a] = tmin[a] < h ? fmin : set[a];
+    if (st) {
+        st->splits++;
+        st->tau_pairs += (uint64_t)(nset * (nset - 1) / 2);
+        st->tau_evals += (uint64_t)(nset * (nset - 1) / 2);
+        if (nf >= 2) st->components++;
+    }
+    free(tmin);
+    return nf >= 2 ? 1 : 0;
+}
+
+int orc_evolve_hold(int64_t n, double *x3, double *v3, const double *m,
+                    const orc_params *p, const int32_t *set, int64_t nset,
+                    double h, int depth, orc_stats *st)
+{
+    if (depth > p->max_depth) return ORC_E_DEPTH;
+    if (st && depth > st->max_depth_seen) st->max_depth_seen = depth;
+    int32_t *labels = (int32_t *)malloc(sizeof(int32_t) * (nset > 0 ? nset : 1));
+    int32_t *fast = (int32_t *)malloc(sizeof(int32_t) * (nset > 0 ? nset : 1));
+    /* S and F at h: F is labelled with its smallest id, so a member whose
+     * label is not its own id names F's label */
+    const int64_t K = orc_hold_split(n, x3, v3, m, p, set, nset, h, labels, st);
+    int32_t lf = -1;
+    for (int64_t a = 0; a < nset && K; ++a)
+        if (labels[a] != set[a]) {
+            lf = labels[a];
+            break;
+        }
+    int64_t nf = 0;
+    for (int64_t a = 0; a < nset && K; ++a)
+        if (labels[a] == lf) fast[nf++] = set[a];
+    int rc = ORC_OK;
+    for (int pass = 0; pass < 2 && rc == ORC_OK; ++pass) {
+        if (pass == 1) {
+            /* E_{h,H_S+V_SF} = D_{h/2,T_S} K_{h,V_S+V_SF} D_{h/2,T_S}: the
+             * drift moves the members whose label no other member shares (S),
+             * the kick every pair whose labels differ (not both in F) */
+            orc_drift(n, x3, v3, set, labels, nset, 0.5 * h, st);
+            orc_kick(n, x3, v3, m, p, set, labels, nset, h, st);
+            orc_drift(n, x3, v3, set, labels, nset, 0.5 * h, st);
+        }
+        /* E_{h/2,H_F}: the same split, recursively, at pivot h/2 */
+        if (nf >= 2) rc = orc_evolve_hold(n, x3, v3, m, p, fast, nf, 0.5 * h, depth + 1, st);
+    }
+    free(labels);
+    free(fast);
+    return rc;
+}
+
 static int check_state(int64_t n, const double *x3, const double *v3, const double *m)
 {
     for (int64_t k = 0; k < 3 * n; ++k)
@@ -501,14 +578,17 @@ int orc_evolve_systems(int64_t n, double *x3, double *v3, const double *m,
 {
     if (n < 0 || nsteps < 0 || !(p->dt > 0.0)) return ORC_E_ARG;
     if (p->kepler && p->eps != 0.0) return ORC_E_ARG;
+    if (p->split != 0 && (p->split != 1 || p->kepler)) return ORC_E_ARG;  /* HOLD has no Kepler mode */
     int rc = check_state(n, x3, v3, m);
     if (rc) return rc;
     int32_t *set = (int32_t *)malloc(sizeof(int32_t) * (n > 0 ? n : 1));
     for (int64_t k = 0; k < n; ++k) set[k] = (int32_t)k;
     for (int64_t s = 0; s < nsteps && rc == ORC_OK; ++s)
         for (int64_t q = 0; q < nsys && rc == ORC_OK; ++q)
-            rc = orc_evolve_cc(n, x3, v3, m, p, set + sys_off[q],
-                               sys_off[q + 1] - sys_off[q], p->dt, 0, st);
+            rc = p->split == 1 ? orc_evolve_hold(n, x3, v3, m, p, set + sys_off[q],
+                                                 sys_off[q + 1] - sys_off[q], p->dt, 0, st)
+                               : orc_evolve_cc(n, x3, v3, m, p, set + sys_off[q],
+                                               sys_off[q + 1] - sys_off[q], p->dt, 0, st);
     free(set);
     if (rc == ORC_OK) rc = check_state(n, x3, v3, m);
     return rc;

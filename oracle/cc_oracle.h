@@ -35,7 +35,8 @@ typedef struct {
     int    max_depth;  /* recursion depth cap; exceeding it is an error     */
     int    eta_outside;/* 0 = eta inside T and dT/dt (default reading),
                           1 = literal placement: eta multiplies the min     */
-    int    pad_;
+    int    split;      /* 0 = CC split (Sec. 2.2-2.3), 1 = HOLD split
+                          (Sec. 2.1, Eq. HOLD)                              */
 } orc_params;
 
 typedef struct {
@@ -101,12 +102,28 @@ void orc_drift(int64_t n, double *x3, const double *v3,
 int orc_kepler(int64_t n, double *x3, double *v3, const double *m,
                double G, int64_t i, int64_t j, double dt);
 
+/* The HOLD split of `set` at pivot h (Sec. 2.1): the particle time step
+ * tau(i) is the minimum of tau(i,j) over the other members j of the set
+ * (every pair evaluated); F = {i : tau(i) < h} is the fast set, S = the
+ * rest.  labels_out[k] = the smallest id of F for members of F, set[k]
+ * itself for members of S.  Returns 1 when F is not empty (it then has at
+ * least two members: tau(i,j) = tau(j,i)), else 0. */
+int64_t orc_hold_split(int64_t n, const double *x3, const double *v3, const double *m,
+                       const orc_params *p, const int32_t *set, int64_t nset,
+                       double h, int32_t *labels_out, orc_stats *st);
+
+/* evolve_hold(S, h) of Sec. 2.1 (Eq. HOLD), recursive: E_{h/2,H_F}
+ * D_{h/2,T_S} K_{h,V_S+V_SF} D_{h/2,T_S} E_{h/2,H_F}, H_F at pivot h/2. */
+int orc_evolve_hold(int64_t n, double *x3, double *v3, const double *m,
+                    const orc_params *p, const int32_t *set, int64_t nset,
+                    double h, int depth, orc_stats *st);
+
 /* evolve_cc(S, h) of the CC pseudocode figure (Sec. 2.3), recursive. */
 int orc_evolve_cc(int64_t n, double *x3, double *v3, const double *m,
                   const orc_params *p, const int32_t *set, int64_t nset,
                   double h, int depth, orc_stats *st);
 
-/* nsteps outer steps evolve_cc(all, p->dt). */
+/* nsteps outer steps evolve_cc(all, p->dt) (evolve_hold when p->split = 1). */
 int orc_evolve(int64_t n, double *x3, double *v3, const double *m,
                const orc_params *p, int64_t nsteps, orc_stats *st);
 

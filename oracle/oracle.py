@@ -28,7 +28,7 @@ _lock = threading.Lock()
 class Params(C.Structure):
     _fields_ = [("G", C.c_double), ("eps", C.c_double), ("eta", C.c_double),
                 ("dt", C.c_double), ("kepler", C.c_int), ("max_depth", C.c_int),
-                ("eta_outside", C.c_int), ("pad_", C.c_int)]
+                ("eta_outside", C.c_int), ("split", C.c_int)]
 
 
 class Stats(C.Structure):
@@ -84,6 +84,10 @@ def lib():
             L.orc_evolve.argtypes = [i64, dp, dp, dp, P, i64, S]
             L.orc_evolve_systems.restype = C.c_int
             L.orc_evolve_systems.argtypes = [i64, dp, dp, dp, P, C.POINTER(C.c_int64), i64, i64, S]
+            L.orc_hold_split.restype = i64
+            L.orc_hold_split.argtypes = [i64, dp, dp, dp, P, i32p, i64, d, i32p, S]
+            L.orc_evolve_hold.restype = C.c_int
+            L.orc_evolve_hold.argtypes = [i64, dp, dp, dp, P, i32p, i64, d, C.c_int, S]
             L.orc_set_threads.restype = C.c_int
             L.orc_set_threads.argtypes = [C.c_int]
             L.orc_energy.restype = None
@@ -110,8 +114,11 @@ def _f64(a):
     return np.ascontiguousarray(a, dtype=np.float64)
 
 
-def params(G=1.0, eps=0.0, eta=0.03, dt=1.0 / 64, kepler=False, max_depth=64, eta_outside=False):
-    return Params(G, eps, eta, dt, int(kepler), max_depth, int(eta_outside), 0)
+SPLIT_CC, SPLIT_HOLD = 0, 1
+
+
+def params(G=1.0, eps=0.0, eta=0.03, dt=1.0 / 64, kepler=False, max_depth=64, eta_outside=False, split=SPLIT_CC):
+    return Params(G, eps, eta, dt, int(kepler), max_depth, int(eta_outside), int(split))
 
 
 class State:
@@ -163,6 +170,19 @@ def components(s: State, p: Params, h: float, set_ids=None, stats: Stats | None 
     return lab, int(k)
 
 
+def hold_split(s: State, p: Params, h: float, set_ids=None, stats: Stats | None = None):
+    """HOLD split (Sec. 2.1): labels (F's smallest id for fast members, own
+    id for slow ones) and 1 if the fast set is not empty, else 0."""
+    set_ids = np.arange(s.n, dtype=np.int32) if set_ids is None else np.ascontiguousarray(set_ids, dtype=np.int32)
+    lab = np.zeros(set_ids.shape[0], dtype=np.int32)
+    st = stats if stats is not None else Stats()
+    k = lib().orc_hold_split(s.n, _dp(s.x3), _dp(s.v3), _dp(s.m), C.byref(p), _ip(set_ids),
+                             set_ids.shape[0], h, _ip(lab), C.byref(st))
+    if k < 0:
+        raise RuntimeError(f"orc_hold_split failed: {k}")
+    return lab, int(k)
+
+
 def edges(s: State, p: Params, h: float, set_ids=None, near_tol=1e-12):
     set_ids = np.arange(s.n, dtype=np.int32) if set_ids is None else np.ascontiguousarray(set_ids, dtype=np.int32)
     nn = C.c_int64(0)
@@ -203,6 +223,17 @@ def evolve_cc(s: State, p: Params, h: float, set_ids=None, stats: Stats | None =
                              set_ids.shape[0], h, 0, C.byref(st))
     if rc:
         raise RuntimeError(f"orc_evolve_cc failed: {rc}")
+    return st
+
+
+def evolve_hold(s: State, p: Params, h: float, set_ids=None, stats: Stats | None = None):
+    """evolve_hold(S, h) of Sec. 2.1 (Eq. HOLD) on the given set."""
+    set_ids = np.arange(s.n, dtype=np.int32) if set_ids is None else np.ascontiguousarray(set_ids, dtype=np.int32)
+    st = stats if stats is not None else Stats()
+    rc = lib().orc_evolve_hold(s.n, _dp(s.x3), _dp(s.v3), _dp(s.m), C.byref(p), _ip(set_ids),
+                               set_ids.shape[0], h, 0, C.byref(st))
+    if rc:
+        raise RuntimeError(f"orc_evolve_hold failed: {rc}")
     return st
 
 
