@@ -229,12 +229,13 @@ def run_reference(args, rank, world):
 
 
 # ------------------------------------------------------------------ GPU arm
-def _ctx(cc, dm, dx, dv, sys_off, workload, form, h_fp64_rel, s_small):
-    """A context of the given form on a device-resident state."""
+def _ctx(cc, dm, dx, dv, sys_off, workload, form, h_fp64_rel, s_small, split=0):
+    """A context of the given form (and split: 0 CC, 1 HOLD) on a
+    device-resident state."""
     W = WORKLOADS[workload]
     prec = cc.PREC_MIXED if form == "mixed" else cc.PREC_FP64
     ctx = cc.Context(dm, dx, dv, dt=W["dt"], eta=ETA, precision=prec, h_fp64=h_fp64_rel * W["dt"],
-                     s_small=s_small, kepler=int(W["kepler"]))
+                     s_small=s_small, kepler=int(W["kepler"]), split=split)
     if sys_off is not None:
         ctx.set_systems(sys_off)
     return ctx
@@ -326,16 +327,22 @@ def other_configs(cc, dev, stream, seed, l2_flush):
     out = {}
     plan = (("fractal", 65536, [("mixed", 0.0), ("fp64", 0.0)]),
             ("binaries", 32768, [("mixed", 0.0), ("mixed", 1.0 / 64), ("fp64", 0.0)]),
-            ("systems", 0, [("mixed", 0.0), ("fp64", 0.0)]))
+            ("systems", 0, [("mixed", 0.0), ("fp64", 0.0)]),
+            # the HOLD method (Sec. 2.1) on the same kernels and the bench's
+            # own workload: the paper's comparison of the two splits
+            ("hold", N_BODY, [("mixed", 0.0), ("fp64", 0.0)]))
     for wl, n, forms in plan:
         a = _ap.Namespace(workload=wl, n=n, nsys=4096)
+        if wl == "hold":
+            a.workload = "plummer"
         m, x, v, sys_off = make_workload(a, seed, dev)
         dm, dx, dv = (torch.tensor(q, device=dev) for q in (m, x, v))
         rows = []
+        wname = a.workload
         for form, hf in forms:
-            ctx = _ctx(cc, dm, dx, dv, sys_off, wl, form, hf, 32)
+            ctx = _ctx(cc, dm, dx, dv, sys_off, wname, form, hf, 32, split=1 if wl == "hold" else 0)
             E0, _, _ = ctx.energy()
-            dtw = WORKLOADS[wl]["dt"]
+            dtw = WORKLOADS[wname]["dt"]
             w0 = time.perf_counter()
             t = dtw
             ctx.evolve(t)  # warm-up step (allocations, tuner trials)
@@ -349,8 +356,12 @@ def other_configs(cc, dev, stream, seed, l2_flush):
             rows.append({"form": form, "h_fp64": f"{hf}*dt", "steps": steps, "ms_per_step": ms / steps,
                          "interactions_per_s": w["interactions"] / (ms * 1e-3),
                          "evaluated_interactions_per_s": w["interactions_evaluated"] / (ms * 1e-3),
+                         "tau_pairs_per_step": w["tau_pairs"] / steps, "kick_pairs_per_step": w["kick_pairs"] / steps,
                          "dE_over_E": (E1 - E0) / abs(E0), "steps_for_dE": steps + 1})
-        out[wl] = {"workload": workload_name(m.shape[0], wl, 4096), "n": int(m.shape[0]), "forms": rows}
+        name = workload_name(m.shape[0], wname, 4096)
+        if wl == "hold":
+            name = "HOLD split (Sec. 2.1) on: " + name
+        out[wl] = {"workload": name, "n": int(m.shape[0]), "forms": rows}
     return out
 
 

@@ -36,6 +36,11 @@ extern "C" {
 #define CC_E_KEPLER     -7  /* Kepler solver did not converge                   */
 #define CC_E_NOMEM      -8  /* device allocation failed                         */
 
+#define CC_SPLIT_CC    0    /* connected components of the time-step graph
+                               (Sec. 2.2-2.3)                                   */
+#define CC_SPLIT_HOLD  1    /* slow/fast split by the particle time step
+                               tau(i) = min_j tau(i,j) (Sec. 2.1, Eq. HOLD)     */
+
 #define CC_PREC_FP64   0    /* every force and tau in FP64                      */
 #define CC_PREC_MIXED  1    /* FP32 forces between components, certified FP32
                                tau pre-filter; FP64 state, drift, predicate     */
@@ -68,7 +73,11 @@ typedef struct {
                           GPU fault: 1 = its tile copy is announced but never
                           issued, so the mbarrier wait gives up after ~2^20
                           cycles; 2 = the union-find hook gives up at once     */
-    int    reserved[2];
+    int    split;      /* CC_SPLIT_CC (default) or CC_SPLIT_HOLD: the HOLD method of
+                          Sec. 2.1 on the same kernels -- the fast set F = {i :
+                          tau(i) < h} is the union of the CC components, so it is
+                          split as one set; no Kepler mode                     */
+    int    reserved;
 } cc_params;
 
 typedef struct {
@@ -145,7 +154,11 @@ int cc_timestep_graph(cc_ctx *ctx, const int32_t *set, int64_t n_set, double h,
 /* split_cc of Sec. 2.3 by union-find: labels_out[k] (int32[n_set]) = the
  * smallest particle id of the connected component of set[k] in the
  * time-step graph at h (singletons: their own id; they form the rest set
- * R).  *n_comp = number of non-trivial components (>= 2 members). */
+ * R).  *n_comp = number of non-trivial components (>= 2 members).  With
+ * params.split = CC_SPLIT_HOLD, the HOLD split of Sec. 2.1 instead: the
+ * fast set F (every member with an edge, i.e. tau(i) < h) labelled with
+ * its smallest id, the slow set with their own ids; *n_comp = 1 if F is
+ * not empty, else 0. */
 int cc_components(cc_ctx *ctx, const int32_t *set, int64_t n_set, double h,
                   int32_t *labels_out, int64_t *n_comp);
 

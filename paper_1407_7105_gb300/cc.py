@@ -17,6 +17,8 @@ LIB_PATH = os.path.join(_HERE, "libcc.so")
 
 PREC_FP64 = 0
 PREC_MIXED = 1
+SPLIT_CC = 0
+SPLIT_HOLD = 1
 
 ERRORS = {-1: "CC_E_ARG", -2: "CC_E_CUDA", -3: "CC_E_DEPTH", -4: "CC_E_TIMEOUT", -5: "CC_E_NONFINITE",
           -6: "CC_E_CAPACITY", -7: "CC_E_KEPLER", -8: "CC_E_NOMEM"}
@@ -27,7 +29,7 @@ class Params(C.Structure):
                 ("h_fp64", C.c_double), ("near_tol", C.c_double), ("precision", C.c_int),
                 ("kepler", C.c_int), ("max_depth", C.c_int), ("s_small", C.c_int),
                 ("eta_outside", C.c_int), ("autotune", C.c_int), ("edge_rec_max", C.c_int),
-                ("fault_test", C.c_int), ("reserved", C.c_int * 2)]
+                ("fault_test", C.c_int), ("split", C.c_int), ("reserved", C.c_int)]
 
 
 class Stats(C.Structure):

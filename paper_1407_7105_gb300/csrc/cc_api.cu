@@ -612,8 +612,10 @@ static int split_launch(cc_ctx *c, LevelAlloc &a, double h, const LevelAlloc *pa
     // a fresh mixed split initialises its forest in the float-float copy's pass
     if (parent || !mixed) launch_init_parent(a.L, a.E.count, s);
     bool hook_in_seg = false;  // a first half's child edges hooked by the one-CTA segmentation
+    const bool hold = c->p.split == CC_SPLIT_HOLD;
     if (parent) {
-        hook_in_seg = segment_hooks_edges(a.L.total);
+        // (the HOLD merge needs the complete forest before the segmentation)
+        hook_in_seg = segment_hooks_edges(a.L.total) && !hold;
         launch_edges_reuse(parent->E, parent->ecount, parent->L, parent->F, mixed, parent->inv, a.L, a.E, P, c->d_ctr,
                            c->d_near_ij, c->d_near_tau, c->near_cap, s, !hook_in_seg);
     } else {
@@ -638,6 +640,8 @@ static int split_launch(cc_ctx *c, LevelAlloc &a, double h, const LevelAlloc *pa
         }
         ev_end(c, ev);
     }
+    // HOLD: the set's non-trivial components form one fast set
+    if (hold) launch_hold_merge(a.L, (int32_t *)c->seg_scratch, s);
     const ClassifyArgs cls{c->p.s_small, c->p.kepler, a.kqueue, a.kqueue + 2, a.klist, a.slist};
     a.classified = launch_compress_segment(a.L, a.root, a.members, a.comp_start, a.comp_size, a.d_ncomp,
                                            c->seg_scratch, s, hook_in_seg ? &a.E : nullptr, c->d_ctr,
@@ -777,6 +781,7 @@ static int process(cc_ctx *c, int d, double h, const LevelAlloc *parent)
     SP.precision = c->p.precision;
     SP.depth0 = d + 1;
     SP.max_depth = c->p.max_depth;
+    SP.hold = c->p.split == CC_SPLIT_HOLD;
     const int bound = a.L.total / 2 + 1;  // components of a split, at most
     const bool small_on = c->p.s_small >= 2 && d + 1 <= c->p.max_depth;
     cudaStream_t side = nullptr;
@@ -948,7 +953,8 @@ int cc_init(cc_ctx **out, int64_t n, const double *m, const double *x3, const do
     if (!(p->G > 0.0) || !(p->eps >= 0.0) || !finite_pos(p->eta) || !finite_pos(p->dt) || p->max_depth < 0 ||
         p->max_depth > 200 || (p->precision != CC_PREC_FP64 && p->precision != CC_PREC_MIXED) ||
         (p->kepler && p->eps != 0.0) || p->s_small < 0 || p->s_small > 32 || p->edge_rec_max < 0 ||
-        p->fault_test < 0 || p->fault_test > 2) {
+        p->fault_test < 0 || p->fault_test > 2 || (p->split != CC_SPLIT_CC && p->split != CC_SPLIT_HOLD) ||
+        (p->split == CC_SPLIT_HOLD && p->kepler)) {
         g_init_err = "cc_init: invalid parameters";
         return CC_E_ARG;
     }

@@ -664,6 +664,49 @@ bool launch_compress_segment(const Level &L, int32_t *root, int32_t *members, in
     return false;
 }
 
+// ------------------------------------------------------------ HOLD merge
+// The HOLD split's fast set F = {i : tau(i) < h}, tau(i) = min over the set
+// of tau(i,j), is the set of members with at least one edge at h: the union
+// of the set's non-trivial CC components.  After the edges are hooked, every
+// non-trivial root of a set is linked under the smallest of them (links go
+// from larger to smaller indices, so the forest stays valid while finds run).
+__global__ void k_hold_init(int32_t *anchor, int nsets)
+{
+    const int k = blockIdx.x * blockDim.x + threadIdx.x;
+    if (k < nsets) anchor[k] = 0x7fffffff;
+}
+
+__global__ void k_hold_min(Level L, int32_t *anchor)
+{
+    const int k = blockIdx.x * blockDim.x + threadIdx.x;
+    if (k >= L.total) return;
+    const int s = L.sidx[k];
+    if (s < 0) return;  // padding
+    const int r = uf_find(L.parent, k);
+    if (r != k) atomicMin(&anchor[s], r);  // k is a non-root member: r's component is non-trivial
+}
+
+__global__ void k_hold_link(Level L, const int32_t *anchor)
+{
+    const int k = blockIdx.x * blockDim.x + threadIdx.x;
+    if (k >= L.total) return;
+    const int s = L.sidx[k];
+    if (s < 0) return;
+    const int r = uf_find(L.parent, k);
+    const int a = anchor[s];
+    if (r != k && r != a) L.parent[r] = a;  // a <= r: every non-trivial root of the set
+}
+
+void launch_hold_merge(const Level &L, int32_t *anchor, cudaStream_t s)
+{
+    if (L.total <= 0 || L.nsets <= 0) return;
+    k_hold_init<<<(L.nsets + 255) / 256, 256, 0, s>>>(anchor, L.nsets);
+    const int g = (L.total + 255) / 256;
+    k_hold_min<<<g, 256, 0, s>>>(L, anchor);
+    k_hold_link<<<g, 256, 0, s>>>(L, anchor);
+    CC_COUNT_LAUNCH(3);
+}
+
 // ------------------------------------------------------------ classification
 // Sorts the components of a split for their integrators (one CTA, after the
 // segmentation): two-body components go to klist when Kepler mode is on,

@@ -100,6 +100,7 @@ struct DevCounters {
 struct SmallParams {
     double G, eps2, eta, eta_in, h0, near_tol, h_fp64;
     int eta_outside, kepler, precision, depth0, max_depth;
+    int hold;  // HOLD split: a set's members with an edge form one fast set
 };
 
 struct TauParams {
@@ -343,6 +344,10 @@ bool launch_compress_segment(const Level &L, int32_t *root, int32_t *members, in
                              int32_t *comp_size, int32_t *d_ncomp, void *scratch, cudaStream_t s,
                              const EdgeList *hook = nullptr, DevCounters *ctr = nullptr,
                              const ClassifyArgs *cls = nullptr);
+// HOLD split (Sec. 2.1): join every non-trivial component of a set into one
+// (the fast set F = the members with an edge), rooted at its smallest
+// index; anchor: nsets ints of scratch
+void launch_hold_merge(const Level &L, int32_t *anchor, cudaStream_t s);
 void launch_gather(const Level &P, const Level &C, const int32_t *members, const int32_t *lcomp_start, int32_t *inv,
                    cudaStream_t s);
 void launch_scatter(const Level &P, const Level &C, cudaStream_t s);

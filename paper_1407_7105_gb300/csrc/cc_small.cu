@@ -560,7 +560,11 @@ __global__ void __launch_bounds__(K8_WARPS * 32) k_small(Level L, const int32_t 
                 // (each lane ORs the masks of its own members only: as many
                 // shuffles per round as the largest mask has bits)
                 uint32_t cm = mine ? (adj | me) : 0u;
-                for (int it = 0; it < 6; ++it) {
+                // HOLD split: every member of the set with an edge (tau(i) <
+                // h) is in the one fast set
+                const uint32_t hasedge = __ballot_sync(FULL, mine && adj != 0u);
+                if (SP.hold) cm = mine ? (adj ? (hasedge & mine) : me) : 0u;
+                for (int it = 0; it < 6 && !SP.hold; ++it) {
                     uint32_t nx = cm, rem = cm;
                     const unsigned rounds = __reduce_max_sync(FULL, (unsigned)__popc(cm));
                     for (unsigned t = 0; t < rounds; ++t) {
