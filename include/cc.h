@@ -191,7 +191,9 @@ int cc_stats(cc_ctx *ctx, cc_stats_t *out);
 int cc_reset_stats(cc_ctx *ctx);
 
 /* Total energy H (Eq. Hamiltonian, FP64 all pairs), momentum P[3] and
- * angular momentum L[3] (host pointers, any may be NULL). */
+ * angular momentum L[3] (host pointers, any may be NULL).  With independent
+ * systems (cc_set_systems) H is the sum of the systems' own Hamiltonians:
+ * pairs of two systems, which never interact, are left out. */
 int cc_energy(cc_ctx *ctx, double *E, double *P3, double *L3);
 
 /* Near-threshold pairs logged since the last cc_timestep_graph /

@@ -1264,7 +1264,8 @@ int cc_energy(cc_ctx *c, double *E, double *P3, double *L3)
         CC_CUDA(c, cudaMalloc(&c->d_partial, (size_t)nb * 8 * 8));
         c->partial_cap = nb;
     }
-    launch_energy(c->d_x3, c->d_v3, c->d_m, c->n, c->p.G, c->p.eps * c->p.eps, c->d_partial, nb, c->stream);
+    launch_energy(c->d_x3, c->d_v3, c->d_m, c->n, c->p.G, c->p.eps * c->p.eps, c->d_sys_off,
+                  (int)c->sys_off.size() - 1, c->d_partial, nb, c->stream);
     std::vector<double> h((size_t)nb * 8);
     CC_CUDA(c, cudaMemcpyAsync(h.data(), c->d_partial, h.size() * 8, cudaMemcpyDeviceToHost, c->stream));
     CC_CUDA(c, cudaStreamSynchronize(c->stream));

@@ -315,7 +315,8 @@ void launch_edges_reuse(const EdgeList &parent, long long pcount, const Level &P
 void launch_kick(const Level &L, const int32_t *label, int nitiles, double G, double eps2, double h,
                  int variant, DevCounters *ctr, cudaStream_t s);
 void launch_energy(const double *x3, const double *v3, const double *m, long long n, double G, double eps2,
-                   double *partial /*[nblk*8]*/, int nblk, cudaStream_t s);
+                   const int32_t *sys_off /* nsys + 1 offsets, or null */, int nsys, double *partial /*[nblk*8]*/,
+                   int nblk, cudaStream_t s);
 int energy_blocks(long long n);
 
 // cc_graph.cu

@@ -513,11 +513,17 @@ constexpr int EN_T = 128;
 
 int energy_blocks(long long n) { return (int)((n + EN_T - 1) / EN_T); }
 
+// Kinetic and potential energy, momentum and angular momentum.  With
+// independent systems (sys_off, nsys + 1 offsets) the potential sums only
+// pairs inside one system: systems never interact, so a pair of two
+// systems belongs to no system's Hamiltonian.
 __global__ void __launch_bounds__(EN_T) k_energy(const double *x3, const double *v3, const double *m,
-                                                  long long n, double G, double eps2, double *partial)
+                                                  long long n, double G, double eps2, const int32_t *sys_off,
+                                                  int nsys, double *partial)
 {
     __shared__ double sx[EN_T], sy[EN_T], sz[EN_T], smm[EN_T];
     __shared__ double red[8][EN_T / 32];
+    __shared__ long long blk_hi;
     const long long i = (long long)blockIdx.x * EN_T + threadIdx.x;
     const bool iv = i < n;
     double xi = 0, yi = 0, zi = 0, mi = 0, vx = 0, vy = 0, vz = 0;
@@ -526,8 +532,24 @@ __global__ void __launch_bounds__(EN_T) k_energy(const double *x3, const double 
         vx = v3[i]; vy = v3[n + i]; vz = v3[2 * n + i];
         mi = m[i];
     }
+    // the end of i's system (binary search over the offsets)
+    long long hi = n;
+    if (iv && sys_off && nsys > 1) {
+        int lo = 0, up = nsys;  // sys_off[lo] <= i < sys_off[up]
+        while (up - lo > 1) {
+            const int mid = (lo + up) >> 1;
+            if ((long long)sys_off[mid] <= i) lo = mid;
+            else up = mid;
+        }
+        hi = sys_off[up];
+    }
+    if (threadIdx.x == 0) blk_hi = 0;
+    __syncthreads();
+    if (iv) atomicMax((unsigned long long *)&blk_hi, (unsigned long long)hi);
+    __syncthreads();
+    const long long jend = blk_hi;
     double V = 0.0;
-    for (long long j0 = (long long)blockIdx.x * EN_T; j0 < n; j0 += EN_T) {
+    for (long long j0 = (long long)blockIdx.x * EN_T; j0 < jend; j0 += EN_T) {
         const long long j = j0 + threadIdx.x;
         __syncthreads();
         if (j < n) {
@@ -538,7 +560,7 @@ __global__ void __launch_bounds__(EN_T) k_energy(const double *x3, const double 
         if (iv) {
             const int jn = (int)min((long long)EN_T, n - j0);
             for (int k = 0; k < jn; ++k) {
-                if (j0 + k <= i) continue;
+                if (j0 + k <= i || j0 + k >= hi) continue;
                 const double dx = sx[k] - xi, dy = sy[k] - yi, dz = sz[k] - zi;
                 V -= G * mi * smm[k] / sqrt(dx * dx + dy * dy + dz * dz + eps2);
             }
@@ -566,10 +588,10 @@ __global__ void __launch_bounds__(EN_T) k_energy(const double *x3, const double 
 }
 
 void launch_energy(const double *x3, const double *v3, const double *m, long long n, double G, double eps2,
-                   double *partial, int nblk, cudaStream_t s)
+                   const int32_t *sys_off, int nsys, double *partial, int nblk, cudaStream_t s)
 {
     if (n <= 0) return;
-    k_energy<<<nblk, EN_T, 0, s>>>(x3, v3, m, n, G, eps2, partial);
+    k_energy<<<nblk, EN_T, 0, s>>>(x3, v3, m, n, G, eps2, sys_off, nsys, partial);
     CC_COUNT_LAUNCH(1);
 }
 

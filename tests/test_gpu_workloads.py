@@ -105,3 +105,30 @@ def test_small_systems_without_small_kernel_identical(cclib):
         out.append((gx, gv))
         c.close()
     assert np.array_equal(out[0][0], out[1][0]) and np.array_equal(out[0][1], out[1][1])
+
+
+def test_systems_energy_is_the_sum_of_the_systems(cclib):
+    """With independent systems declared, cc_energy sums each system's own
+    Hamiltonian (the systems overlap in space but never interact); against
+    the oracle's energy of each system separately, and conserved over a
+    step to the integrator's accuracy."""
+    m, x, v, off = _systems(40, seed=5)
+    c = cclib.Context(m, x, v, dt=1 / 64)
+    c.set_systems(off)
+    E, P, L = c.energy()
+    ref = 0.0
+    for a, b in zip(off[:-1], off[1:]):
+        e, _, _ = O.energy(O.State(m[a:b], x[:, a:b], v[:, a:b]))
+        ref += e
+    assert abs(E - ref) < 1e-12 * abs(ref), (E, ref)
+    c.evolve(2 / 64)
+    E1, _, _ = c.energy()
+    c.close()
+    s = O.State(m, x, v)
+    O.evolve(s, O.params(dt=1 / 64), 2, sys_off=off)
+    ref1 = 0.0
+    for a, b in zip(off[:-1], off[1:]):
+        e, _, _ = O.energy(O.State(s.m[a:b], s.x3[:, a:b], s.v3[:, a:b]))
+        ref1 += e
+    assert abs(E1 - ref1) < 1e-10 * abs(ref1), (E1, ref1)
+    assert abs((E1 - E) / E) < 1e-4
