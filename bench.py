@@ -567,6 +567,44 @@ def run_accuracy(args):
     return 0
 
 
+def run_eta_sweep(args):
+    """The metric's gate on the other configurations (JSON lines): the mixed
+    form of the 65536-body fractal and of the 4096-system batch at the eta
+    values {0.03, 0.01, 0.005, 0.0025} over --sweep-steps outer steps:
+    |dE/E| (systems: the sum of the systems' own energies), ms per step,
+    recursion depth.  The configurations leave eta free; the gate picks the
+    largest eta that keeps |dE/E| <= 1e-6."""
+    import argparse as _ap
+    import torch
+
+    from paper_1407_7105_gb300 import build, cc
+    build.build()
+    dev = torch.device("cuda", 0)
+    for wl, n in (("fractal", 65536), ("systems", 0)):
+        a = _ap.Namespace(workload=wl, n=n, nsys=4096)
+        m, x, v, off = make_workload(a, args.seed, dev)
+        dm, dx, dv = (torch.tensor(q, device=dev) for q in (m, x, v))
+        dtw = WORKLOADS[wl]["dt"]
+        for eta in (0.03, 0.01, 0.005, 0.0025):
+            ctx = cc.Context(dm, dx, dv, dt=dtw, eta=eta, precision=cc.PREC_MIXED, kepler=int(WORKLOADS[wl]["kepler"]))
+            if off is not None:
+                ctx.set_systems(off)
+            E0, _, _ = ctx.energy()
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            ctx.evolve(args.sweep_steps * dtw)
+            torch.cuda.synchronize()
+            sec = time.perf_counter() - t0
+            E1, _, _ = ctx.energy()
+            st = ctx.stats()
+            ctx.close()
+            print(json.dumps({"eta_sweep": True, "workload": workload_name(m.shape[0], wl, 4096), "form": "mixed",
+                              "eta": eta, "steps": args.sweep_steps, "t_end": args.sweep_steps * dtw,
+                              "ms_per_step": 1e3 * sec / args.sweep_steps, "dE_over_E": (E1 - E0) / abs(E0),
+                              "max_depth": st["max_depth_seen"]}), flush=True)
+    return 0
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -585,6 +623,9 @@ def main():
     ap.add_argument("--no-extras", action="store_true",
                     help="skip the accuracy gate, the force error and the other configurations")
     ap.add_argument("--t-end", type=float, default=1.0)
+    ap.add_argument("--eta-sweep", action="store_true",
+                    help="energy error of the fractal and the systems batch against eta (mixed form)")
+    ap.add_argument("--sweep-steps", type=int, default=16)
     ap.add_argument("--seed", type=int, default=1)
     ap.add_argument("--n", type=int, default=None, help="bodies (default per workload)")
     ap.add_argument("--workload", default="plummer", choices=sorted(WORKLOADS),
@@ -600,6 +641,8 @@ def main():
         return run_reference(args, rank, world)
     if args.accuracy:
         return run_accuracy(args)
+    if args.eta_sweep:
+        return run_eta_sweep(args)
     if world > 1:
         import torch.distributed as dist
         dist.init_process_group("nccl")
