@@ -34,25 +34,35 @@ U64 = 2.0 ** -53
 K_MIXED = 32.0
 
 
-def abs_accel_sum(m, x3, G: float = 1.0, eps: float = 0.0, chunk: int = 256, groups=None, labels=None):
+def abs_accel_sum(m, x3, G: float = 1.0, eps: float = 0.0, chunk: int = 256, groups=None, labels=None, rows=None):
     """S_i = sum_{j != i} G m_j / (r_ij^2 + eps^2) (numpy, chunked).  groups:
     optional system index per body; pairs of different systems are left out
     (independent systems never interact).  labels: optional component label
     per body; only pairs with different labels count (the pairs a kick
-    with these labels applies)."""
+    with these labels applies).  rows: optional body indices; S is then
+    computed for those bodies only (other entries 0)."""
     n = m.shape[0]
     S = np.zeros(n)
-    for s in range(0, n, chunk):
-        e = min(n, s + chunk)
-        d = x3[:, s:e, None] - x3[:, None, :]
+    idx = np.arange(n) if rows is None else np.asarray(rows)
+    for s in range(0, idx.shape[0], chunk):
+        r = idx[s:s + chunk]
+        d = x3[:, r, None] - x3[:, None, :]
         r2 = (d * d).sum(axis=0) + eps * eps
-        r2[np.arange(e - s), np.arange(s, e)] = np.inf
+        r2[np.arange(r.shape[0]), r] = np.inf
         w = G * m[None, :] / r2
         if groups is not None:
-            w = np.where(groups[s:e, None] == groups[None, :], w, 0.0)
+            w = np.where(groups[r, None] == groups[None, :], w, 0.0)
         if labels is not None:
-            w = np.where(labels[s:e, None] != labels[None, :], w, 0.0)
-        S[s:e] = w.sum(axis=1)
+            w = np.where(labels[r, None] != labels[None, :], w, 0.0)
+        S[r] = w.sum(axis=1)
+    return S
+
+
+def abs_accel_sum_systems(m, x3, sys_off, G: float = 1.0, eps: float = 0.0):
+    """S_i within each independent system (system by system: O(sum n_s^2))."""
+    S = np.zeros(m.shape[0])
+    for a, b in zip(sys_off[:-1], sys_off[1:]):
+        S[a:b] = abs_accel_sum(m[a:b], x3[:, a:b], G=G, eps=eps)
     return S
 
 

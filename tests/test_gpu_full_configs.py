@@ -1,0 +1,129 @@
+"""GPU parity at the full sizes of the other benchmark configurations, in
+the launch configuration bench.py times (default parameters, both forms):
+
+  * the 65536-body box fractal (Salpeter masses, Q = 0.3): the top-level
+    split at h = dt = 1/256, labels bit for bit against the oracle's
+    breadth-first search (~15 s of oracle time on all host cores);
+  * the 32768-body Plummer sphere with 50 % binaries, Kepler mode: the
+    top-level labels, and one FP64 outer step with the oracle's counts
+    (splits, kick pairs, drifts, Kepler solves), positions to 1e-9 and
+    every well-conditioned body's velocity within the Kepler bound;
+  * the batch of 4096 independent systems (triples and Plummer clumps of
+    3-512 bodies, 214538 bodies): one outer step of dt = 1/64, FP64 within
+    1e-12 with the oracle's counts, mixed within the per-body FP32 bound.
+
+The fractal's initial state is scaled to N-body units with the potential
+energy estimated from a seeded sample of 2^22 pairs (the exact O(N^2) sum
+in numpy takes minutes; the parity does not depend on the scale)."""
+import numpy as np
+import pytest
+
+import _bounds as B
+from oracle import oracle as O
+from paper_1407_7105_gb300 import ics
+
+pytestmark = pytest.mark.gpu
+
+
+def _rel_ok(a, b, rtol=1e-12):
+    scale = np.abs(b).max()
+    return np.all(np.abs(a - b) <= rtol * np.abs(b) + 1e-15 * scale)
+
+
+def _fractal65536():
+    n = 65536
+    x0, v0 = ics.box_fractal_raw(n, seed=1)
+    m = ics.salpeter_masses(n, 1, 9100)
+    x0, v0 = ics._com_frame(m, x0, v0)
+    rng = np.random.default_rng(12345)
+    i = rng.integers(0, n, 1 << 22)
+    j = rng.integers(0, n, 1 << 22)
+    keep = i != j
+    i, j = i[keep], j[keep]
+    r = np.sqrt(((x0[:, i] - x0[:, j]) ** 2).sum(axis=0))
+    W = -0.5 * n * (n - 1) * float(np.mean(m[i] * m[j] / r))
+    x3, v3 = ics.scale_to_nbody_units(m, x0, v0, Q=0.3, exact=False, W=W)
+    return m, x3, v3
+
+
+def test_fractal_65536_top_level_labels(cclib):
+    m, x, v = _fractal65536()
+    h = 1 / 256
+    olab, ok = O.components(O.State(m, x, v), O.params(dt=h), h)
+    assert ok > 100
+    for prec in (cclib.PREC_FP64, cclib.PREC_MIXED):
+        c = cclib.Context(m, x, v, dt=h, precision=prec)
+        lab, k = c.components(h)
+        c.close()
+        assert k == ok and np.array_equal(lab, olab), prec
+
+
+def test_binaries_32768_labels_and_one_kepler_step(cclib):
+    m, x, v = ics.plummer_with_binaries(32768, seed=1)
+    dt = 1 / 256
+    s = O.State(m, x, v)
+    p = O.params(dt=dt, kepler=True)
+    olab, ok = O.components(s, p, dt)
+    for prec in (cclib.PREC_FP64, cclib.PREC_MIXED):
+        c = cclib.Context(m, x, v, dt=dt, kepler=1, precision=prec)
+        lab, k = c.components(dt)
+        c.close()
+        assert k == ok and np.array_equal(lab, olab), prec
+    c = cclib.Context(m, x, v, dt=dt, kepler=1)
+    c.evolve(dt)
+    _, _, gx, gv = c.get_state()
+    g = c.stats()
+    c.close()
+    st = O.evolve(s, p, 1)
+    for key in ("splits", "kick_pairs", "drifts", "kepler_calls", "components"):
+        assert g[key] == getattr(st, key), key
+    assert _rel_ok(gx, s.x3, 1e-9)
+    # velocities element-wise where the orbits are well conditioned (bodies
+    # whose top-level component has at most two members), as in the
+    # Kepler-mode test of test_gpu_evolve.py
+    sizes = np.bincount(olab, minlength=m.shape[0])
+    calm = np.flatnonzero(sizes[olab] <= 2)
+    S = B.abs_accel_sum(m, x, rows=calm)
+    tol = 2.0 ** 14 * B.U64 * dt * S * (st.max_depth_seen + 1) + 4 * B.U64 * np.linalg.norm(s.v3, axis=0)
+    err = np.linalg.norm(gv - s.v3, axis=0)
+    assert calm.size > 0.05 * m.shape[0]
+    assert (err[calm] <= tol[calm]).all(), float((err[calm] / tol[calm]).max())
+    # the rest (inside the giant component: many Kepler calls and kicks in
+    # sequence) in distribution, as in the smaller Kepler-mode test
+    rel = err / np.linalg.norm(s.v3, axis=0)
+    assert np.median(rel) < 1e-12 and np.quantile(rel, 0.99) < 1e-6, (np.median(rel), np.quantile(rel, 0.99))
+
+
+@pytest.fixture(scope="module")
+def systems4096():
+    m, x, v, off = ics.small_systems(4096, seed=1)
+    s = O.State(m, x, v)
+    st = O.evolve(s, O.params(dt=1 / 64), 1, sys_off=off)
+    return m, x, v, off, s, st
+
+
+def test_systems_4096_one_step_fp64(cclib, systems4096):
+    m, x, v, off, s, st = systems4096
+    c = cclib.Context(m, x, v, dt=1 / 64)
+    c.set_systems(off)
+    c.evolve(1 / 64)
+    _, _, gx, gv = c.get_state()
+    g = c.stats()
+    c.close()
+    assert _rel_ok(gx, s.x3) and _rel_ok(gv, s.v3)
+    for key in ("tau_pairs", "kick_pairs", "drifts", "splits", "components"):
+        assert g[key] == getattr(st, key), key
+    assert g["max_depth_seen"] == st.max_depth_seen
+
+
+def test_systems_4096_one_step_mixed(cclib, systems4096):
+    m, x, v, off, s, st = systems4096
+    c = cclib.Context(m, x, v, dt=1 / 64, precision=cclib.PREC_MIXED, near_tol=1e-6)
+    c.set_systems(off)
+    c.evolve(1 / 64)
+    _, _, gx, gv = c.get_state()
+    pairs, _, npairs = c.near_pairs(cap=4096)
+    c.close()
+    S = B.abs_accel_sum_systems(m, x, off)
+    w, _ = B.check_velocity_bound(gv, s.v3, S, 1 / 64, st.max_depth_seen, exempt=B.near_bodies(pairs))
+    print("systems 4096 mixed: max error / bound", w, "near pairs", npairs)
