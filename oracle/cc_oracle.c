@@ -201,6 +201,12 @@ int64_t orc_edges(int64_t n, const double *x3, const double *v3, const double *m
 /* ------------------------------------------------------------------ */
 /* kick and drift (Eqs. drift, kickij, kickji)                          */
 /* ------------------------------------------------------------------ */
+static int cmp_i32_any(const void *a, const void *b)
+{
+    int32_t x = *(const int32_t *)a, y = *(const int32_t *)b;
+    return (x > y) - (x < y);
+}
+
 void orc_kick(int64_t n, const double *x3, double *v3, const double *m,
               const orc_params *p, const int32_t *set, const int32_t *labels,
               int64_t nset, double h, orc_stats *st)
@@ -236,6 +242,139 @@ void orc_kick(int64_t n, const double *x3, double *v3, const double *m,
     }
     if (st) st->kick_pairs += pairs;
     free(acc);
+}
+
+/* centre-of-mass approximation of V_CC (Sec. 4.1, Discussion) */
+void orc_kick_com(int64_t n, const double *x3, double *v3, const double *m,
+                  const orc_params *p, const int32_t *set, const int32_t *labels,
+                  int64_t nset, double h, orc_stats *st)
+{
+    if (!(p->theta > 0.0) || nset < 2) {
+        orc_kick(n, x3, v3, m, p, set, labels, nset, h, st);
+        return;
+    }
+    /* the eligible components in ascending label: a sorted copy of the labels */
+    int32_t *srt = (int32_t *)malloc(sizeof(int32_t) * nset);
+    memcpy(srt, labels, sizeof(int32_t) * nset);
+    qsort(srt, nset, sizeof(int32_t), cmp_i32_any);
+    int64_t ke = 0;
+    int32_t *elab = (int32_t *)malloc(sizeof(int32_t) * nset);
+    for (int64_t a = 0; a < nset;) {
+        int64_t b = a;
+        while (b < nset && srt[b] == srt[a]) b++;
+        if (b - a >= 2 && b - a <= p->com_max) elab[ke++] = srt[a];
+        a = b;
+    }
+    free(srt);
+    /* comp[k] = the eligible component of set[k], or -1 */
+    int64_t *comp = (int64_t *)malloc(sizeof(int64_t) * nset);
+    for (int64_t k = 0; k < nset; ++k) {
+        comp[k] = -1;
+        for (int64_t e = 0; e < ke; ++e)
+            if (labels[k] == elab[e]) {
+                comp[k] = e;
+                break;
+            }
+    }
+    double *cm = (double *)calloc((size_t)(ke > 0 ? ke : 1) * 5, sizeof(double)); /* M, X, Y, Z, R */
+    for (int64_t e = 0; e < ke; ++e) {
+        double M = 0.0, sx = 0.0, sy = 0.0, sz = 0.0;
+        for (int64_t k = 0; k < nset; ++k) {
+            if (comp[k] != e) continue;
+            int64_t i = set[k];
+            M = M + m[i];
+            sx = sx + m[i] * x3[i];
+            sy = sy + m[i] * x3[n + i];
+            sz = sz + m[i] * x3[2 * n + i];
+        }
+        double X = sx / M, Y = sy / M, Z = sz / M, R = 0.0;
+        for (int64_t k = 0; k < nset; ++k) {
+            if (comp[k] != e) continue;
+            int64_t i = set[k];
+            double dx = x3[i] - X, dy = x3[n + i] - Y, dz = x3[2 * n + i] - Z;
+            double r = sqrt((dx * dx + dy * dy) + dz * dz);
+            if (r > R) R = r;
+        }
+        cm[5 * e] = M; cm[5 * e + 1] = X; cm[5 * e + 2] = Y; cm[5 * e + 3] = Z; cm[5 * e + 4] = R;
+    }
+    /* far[a*ke + b]: R_a + R_b < theta |X_a - X_b| */
+    char *far = (char *)calloc((size_t)(ke > 0 ? ke * ke : 1), 1);
+    for (int64_t a = 0; a < ke; ++a)
+        for (int64_t b = 0; b < ke; ++b) {
+            if (a == b) continue;
+            double dx = cm[5 * b + 1] - cm[5 * a + 1], dy = cm[5 * b + 2] - cm[5 * a + 2];
+            double dz = cm[5 * b + 3] - cm[5 * a + 3];
+            double d = sqrt((dx * dx + dy * dy) + dz * dz);
+            far[a * ke + b] = (cm[5 * a + 4] + cm[5 * b + 4]) < p->theta * d;
+        }
+    /* 1. exact pairs, the far ones left out (orc_kick's arithmetic) */
+    double eps2 = p->eps * p->eps;
+    double *acc = (double *)calloc((size_t)(3 * nset), sizeof(double));
+    uint64_t pairs = 0, cpairs = 0;
+#pragma omp parallel for schedule(dynamic, 16) reduction(+ : pairs, cpairs) if (nset >= ORC_PAR_MIN)
+    for (int64_t a = 0; a < nset; ++a) {
+        int64_t i = set[a];
+        double ax = 0.0, ay = 0.0, az = 0.0;
+        for (int64_t b = 0; b < nset; ++b) {
+            if (b == a || labels[b] == labels[a]) continue;
+            if (comp[a] >= 0 && comp[b] >= 0 && far[comp[a] * ke + comp[b]]) {
+                if (b > a) cpairs++;
+                continue;
+            }
+            int64_t j = set[b];
+            if (b > a) pairs++;
+            double dx0 = x3[j] - x3[i];
+            double dx1 = x3[n + j] - x3[n + i];
+            double dx2 = x3[2 * n + j] - x3[2 * n + i];
+            double r2 = ((dx0 * dx0 + dx1 * dx1) + dx2 * dx2) + eps2;
+            double rinv3 = 1.0 / (r2 * sqrt(r2));
+            double w = (p->G * m[j]) * rinv3;
+            ax = ax + w * dx0;
+            ay = ay + w * dx1;
+            az = az + w * dx2;
+        }
+        acc[3 * a] = ax; acc[3 * a + 1] = ay; acc[3 * a + 2] = az;
+    }
+    for (int64_t a = 0; a < nset; ++a) {
+        int64_t i = set[a];
+        v3[i] = v3[i] + h * acc[3 * a];
+        v3[n + i] = v3[n + i] + h * acc[3 * a + 1];
+        v3[2 * n + i] = v3[2 * n + i] + h * acc[3 * a + 2];
+    }
+    /* 2. the monopole of every far component */
+    for (int64_t a = 0; a < ke; ++a) {
+        double Ax = 0.0, Ay = 0.0, Az = 0.0;
+        int any = 0;
+        for (int64_t b = 0; b < ke; ++b) {
+            if (!far[a * ke + b]) continue;
+            any = 1;
+            double dx0 = cm[5 * b + 1] - cm[5 * a + 1];
+            double dx1 = cm[5 * b + 2] - cm[5 * a + 2];
+            double dx2 = cm[5 * b + 3] - cm[5 * a + 3];
+            double d2 = ((dx0 * dx0 + dx1 * dx1) + dx2 * dx2) + eps2;
+            double w = (p->G * cm[5 * b]) * (1.0 / (d2 * sqrt(d2)));
+            Ax = Ax + w * dx0;
+            Ay = Ay + w * dx1;
+            Az = Az + w * dx2;
+        }
+        if (!any) continue;
+        for (int64_t k = 0; k < nset; ++k) {
+            if (comp[k] != a) continue;
+            int64_t i = set[k];
+            v3[i] = v3[i] + h * Ax;
+            v3[n + i] = v3[n + i] + h * Ay;
+            v3[2 * n + i] = v3[2 * n + i] + h * Az;
+        }
+    }
+    if (st) {
+        st->kick_pairs += pairs;
+        st->com_pairs += cpairs;
+    }
+    free(acc);
+    free(far);
+    free(cm);
+    free(comp);
+    free(elab);
 }
 
 void orc_drift(int64_t n, double *x3, const double *v3,
@@ -459,7 +598,7 @@ int orc_evolve_cc(int64_t n, double *x3, double *v3, const double *m,
         if (pass == 1) {
             /* 3)-5) D_{h/2,T_R} K_{h,V_R+V_CC+V_CR} D_{h/2,T_R} */
             orc_drift(n, x3, v3, set, labels, nset, 0.5 * h, st);
-            orc_kick(n, x3, v3, m, p, set, labels, nset, h, st);
+            orc_kick_com(n, x3, v3, m, p, set, labels, nset, h, st);
             orc_drift(n, x3, v3, set, labels, nset, 0.5 * h, st);
         }
         for (int64_t c = 0; c < nc && rc == ORC_OK; ++c) {
@@ -579,6 +718,7 @@ int orc_evolve_systems(int64_t n, double *x3, double *v3, const double *m,
     if (n < 0 || nsteps < 0 || !(p->dt > 0.0)) return ORC_E_ARG;
     if (p->kepler && p->eps != 0.0) return ORC_E_ARG;
     if (p->split != 0 && (p->split != 1 || p->kepler)) return ORC_E_ARG;  /* HOLD has no Kepler mode */
+    if (p->theta < 0.0 || (p->theta > 0.0 && (p->split != 0 || p->com_max < 2))) return ORC_E_ARG;
     int rc = check_state(n, x3, v3, m);
     if (rc) return rc;
     int32_t *set = (int32_t *)malloc(sizeof(int32_t) * (n > 0 ? n : 1));

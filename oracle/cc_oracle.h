@@ -37,6 +37,11 @@ typedef struct {
                           1 = literal placement: eta multiplies the min     */
     int    split;      /* 0 = CC split (Sec. 2.2-2.3), 1 = HOLD split
                           (Sec. 2.1, Eq. HOLD)                              */
+    double theta;      /* > 0: centre-of-mass approximation of V_CC (Sec.
+                          4.1) between components whose radii satisfy
+                          R_a + R_b < theta |X_a - X_b|; 0 = exact kicks    */
+    int    com_max;    /* only components of 2..com_max members take part  */
+    int    pad_;
 } orc_params;
 
 typedef struct {
@@ -47,6 +52,8 @@ typedef struct {
     uint64_t kepler_calls; /* two-body Kepler solves                        */
     uint64_t splits;       /* split_cc calls                                */
     uint64_t components;   /* non-trivial components found                  */
+    uint64_t com_pairs;    /* body pairs whose kick the centre-of-mass
+                              approximation replaced                         */
     int      max_depth_seen;
     int      pad_;
 } orc_stats;
@@ -90,6 +97,22 @@ int64_t orc_edges(int64_t n, const double *x3, const double *v3, const double *m
 void orc_kick(int64_t n, const double *x3, double *v3, const double *m,
               const orc_params *p, const int32_t *set, const int32_t *labels,
               int64_t nset, double h, orc_stats *st);
+
+/* The kick K_{h,V} of a split with the centre-of-mass approximation of
+ * V_CC (Sec. 4.1) when p->theta > 0, else orc_kick.  Components (labels
+ * shared by 2..p->com_max members) have mass M_a, centre of mass X_a (sums
+ * over members in ascending id) and radius R_a = max |x_i - X_a|; two of
+ * them are far when R_a + R_b < theta |X_a - X_b|.  Then:
+ *   1. the exact kick of orc_kick with the pairs of far components left out,
+ *      v_i += h a_i;
+ *   2. for each such component a, ascending label, A_a = sum over the far
+ *      components b, ascending label, of (G M_b) (X_b - X_a) / (d2 sqrt(d2)),
+ *      d2 = |X_b - X_a|^2 + eps^2, and v_i += h A_a for its members.
+ * The forces between two components are G M_a M_b d/|d|^3 and its
+ * opposite: momentum and angular momentum are kept. */
+void orc_kick_com(int64_t n, const double *x3, double *v3, const double *m,
+                  const orc_params *p, const int32_t *set, const int32_t *labels,
+                  int64_t nset, double h, orc_stats *st);
 
 /* D_{dt,T_i} (Eq. drift) for members of `set` whose label is shared by no
  * other member: x_i += dt * v_i. */

@@ -28,14 +28,16 @@ _lock = threading.Lock()
 class Params(C.Structure):
     _fields_ = [("G", C.c_double), ("eps", C.c_double), ("eta", C.c_double),
                 ("dt", C.c_double), ("kepler", C.c_int), ("max_depth", C.c_int),
-                ("eta_outside", C.c_int), ("split", C.c_int)]
+                ("eta_outside", C.c_int), ("split", C.c_int), ("theta", C.c_double), ("com_max", C.c_int),
+                ("pad_", C.c_int)]
 
 
 class Stats(C.Structure):
     _fields_ = [("tau_pairs", C.c_uint64), ("tau_evals", C.c_uint64),
                 ("kick_pairs", C.c_uint64), ("drifts", C.c_uint64),
                 ("kepler_calls", C.c_uint64), ("splits", C.c_uint64),
-                ("components", C.c_uint64), ("max_depth_seen", C.c_int), ("pad_", C.c_int)]
+                ("components", C.c_uint64), ("com_pairs", C.c_uint64), ("max_depth_seen", C.c_int),
+                ("pad_", C.c_int)]
 
     def as_dict(self):
         return {k: int(getattr(self, k)) for k, _ in self._fields_ if k != "pad_"}
@@ -74,6 +76,8 @@ def lib():
             L.orc_edges.argtypes = [i64, dp, dp, dp, P, i32p, i64, d, i32p, i64, d, C.POINTER(C.c_int64)]
             L.orc_kick.restype = None
             L.orc_kick.argtypes = [i64, dp, dp, dp, P, i32p, i32p, i64, d, S]
+            L.orc_kick_com.restype = None
+            L.orc_kick_com.argtypes = [i64, dp, dp, dp, P, i32p, i32p, i64, d, S]
             L.orc_drift.restype = None
             L.orc_drift.argtypes = [i64, dp, dp, i32p, i32p, i64, d, S]
             L.orc_kepler.restype = C.c_int
@@ -117,8 +121,9 @@ def _f64(a):
 SPLIT_CC, SPLIT_HOLD = 0, 1
 
 
-def params(G=1.0, eps=0.0, eta=0.03, dt=1.0 / 64, kepler=False, max_depth=64, eta_outside=False, split=SPLIT_CC):
-    return Params(G, eps, eta, dt, int(kepler), max_depth, int(eta_outside), int(split))
+def params(G=1.0, eps=0.0, eta=0.03, dt=1.0 / 64, kepler=False, max_depth=64, eta_outside=False, split=SPLIT_CC,
+           theta=0.0, com_max=32):
+    return Params(G, eps, eta, dt, int(kepler), max_depth, int(eta_outside), int(split), float(theta), int(com_max), 0)
 
 
 class State:
@@ -200,6 +205,15 @@ def kick(s: State, p: Params, set_ids, labels, h, stats: Stats | None = None):
     st = stats if stats is not None else Stats()
     lib().orc_kick(s.n, _dp(s.x3), _dp(s.v3), _dp(s.m), C.byref(p), _ip(set_ids), _ip(labels),
                    set_ids.shape[0], h, C.byref(st))
+
+
+def kick_com(s: State, p: Params, set_ids, labels, h, stats: Stats | None = None):
+    """The kick with the centre-of-mass approximation of V_CC (p.theta > 0)."""
+    set_ids = np.ascontiguousarray(set_ids, dtype=np.int32)
+    labels = np.ascontiguousarray(labels, dtype=np.int32)
+    st = stats if stats is not None else Stats()
+    lib().orc_kick_com(s.n, _dp(s.x3), _dp(s.v3), _dp(s.m), C.byref(p), _ip(set_ids), _ip(labels),
+                       set_ids.shape[0], h, C.byref(st))
 
 
 def drift(s: State, set_ids, labels, dt, stats: Stats | None = None):
