@@ -77,7 +77,15 @@ typedef struct {
                           Sec. 2.1 on the same kernels -- the fast set F = {i :
                           tau(i) < h} is the union of the CC components, so it is
                           split as one set; no Kepler mode                     */
-    int    reserved;
+    int    com_max;    /* centre-of-mass approximation: components of 2..com_max
+                          (<= 64) members take part (default 32)              */
+    double theta;      /* > 0: the centre-of-mass approximation of V_CC (Sec. 4.1)
+                          in the DKD of every set of at least 33 members: two
+                          eligible components with R_a + R_b < theta |X_a - X_b|
+                          (X the centre of mass, R the largest distance of a member
+                          from it) kick each other through their centres of mass,
+                          G M_b (X_b - X_a)/|X_b - X_a|^3 on every member of a, in
+                          place of their pair kicks; 0 (default): exact kicks  */
 } cc_params;
 
 typedef struct {
@@ -96,6 +104,8 @@ typedef struct {
                                pair a split decides, but the split of a component's
                                first half sees the state its parent split saw, and
                                takes the edges from the parent's tau values instead  */
+    uint64_t com_pairs;     /* body pairs whose kick the centre-of-mass approximation
+                               replaced (not in kick_pairs)                         */
     int32_t  max_depth_seen;
     int32_t  reserved;
 } cc_stats_t;

@@ -598,7 +598,11 @@ int orc_evolve_cc(int64_t n, double *x3, double *v3, const double *m,
         if (pass == 1) {
             /* 3)-5) D_{h/2,T_R} K_{h,V_R+V_CC+V_CR} D_{h/2,T_R} */
             orc_drift(n, x3, v3, set, labels, nset, 0.5 * h, st);
-            orc_kick_com(n, x3, v3, m, p, set, labels, nset, h, st);
+            /* the centre-of-mass approximation applies in sets of at least 33 */
+            if (nset >= 33)
+                orc_kick_com(n, x3, v3, m, p, set, labels, nset, h, st);
+            else
+                orc_kick(n, x3, v3, m, p, set, labels, nset, h, st);
             orc_drift(n, x3, v3, set, labels, nset, 0.5 * h, st);
         }
         for (int64_t c = 0; c < nc && rc == ORC_OK; ++c) {

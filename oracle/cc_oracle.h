@@ -109,7 +109,8 @@ void orc_kick(int64_t n, const double *x3, double *v3, const double *m,
  *      components b, ascending label, of (G M_b) (X_b - X_a) / (d2 sqrt(d2)),
  *      d2 = |X_b - X_a|^2 + eps^2, and v_i += h A_a for its members.
  * The forces between two components are G M_a M_b d/|d|^3 and its
- * opposite: momentum and angular momentum are kept. */
+ * opposite: momentum and angular momentum are kept.  orc_evolve_cc uses it
+ * in the kick of sets of at least 33 members (orc_kick in smaller ones). */
 void orc_kick_com(int64_t n, const double *x3, double *v3, const double *m,
                   const orc_params *p, const int32_t *set, const int32_t *labels,
                   int64_t nset, double h, orc_stats *st);

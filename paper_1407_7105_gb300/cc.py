@@ -29,7 +29,7 @@ class Params(C.Structure):
                 ("h_fp64", C.c_double), ("near_tol", C.c_double), ("precision", C.c_int),
                 ("kepler", C.c_int), ("max_depth", C.c_int), ("s_small", C.c_int),
                 ("eta_outside", C.c_int), ("autotune", C.c_int), ("edge_rec_max", C.c_int),
-                ("fault_test", C.c_int), ("split", C.c_int), ("reserved", C.c_int)]
+                ("fault_test", C.c_int), ("split", C.c_int), ("com_max", C.c_int), ("theta", C.c_double)]
 
 
 class Stats(C.Structure):
@@ -37,7 +37,7 @@ class Stats(C.Structure):
                 ("drifts", C.c_uint64), ("kepler_calls", C.c_uint64), ("splits", C.c_uint64),
                 ("components", C.c_uint64), ("edges", C.c_uint64), ("near_pairs", C.c_uint64),
                 ("small_tasks", C.c_uint64), ("launches", C.c_uint64), ("tau_evaluated", C.c_uint64),
-                ("max_depth_seen", C.c_int32),
+                ("com_pairs", C.c_uint64), ("max_depth_seen", C.c_int32),
                 ("reserved", C.c_int32)]
 
     def as_dict(self):

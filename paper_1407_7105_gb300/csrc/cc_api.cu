@@ -87,6 +87,26 @@ struct LevelAlloc {
     // host scratch of the classification, kept between splits (no reallocation)
     std::vector<int32_t> v_lstart, v_lsize;
     SetLayout child_layout;
+    // centre-of-mass approximation (params.theta > 0): the eligible components
+    // of the last split (host lists, built after the split) and their device
+    // copies, centres, far matrices; grow-only
+    int Ke = 0;
+    long long far_bytes = 0;
+    std::vector<int32_t> h_eq, h_eset, h_eloc, h_efirst, h_K;
+    std::vector<long long> h_foff;
+    void *comblock = nullptr;
+    size_t com_cap = 0;
+    void *h_comstage = nullptr;
+    size_t h_comstage_cap = 0;
+    int32_t *d_cl = nullptr;
+    int cl_cap = 0;
+    unsigned char *d_far = nullptr;
+    long long far_cap = 0;
+    ComView cv{nullptr, nullptr, nullptr, nullptr};
+    int32_t *d_eq = nullptr, *d_eset = nullptr, *d_eloc = nullptr, *d_efirst = nullptr, *d_K = nullptr,
+            *d_eany = nullptr;
+    long long *d_foff = nullptr;
+    double *d_cm = nullptr;
 };
 
 // ------------------------------------------------------------ autotuner
@@ -361,6 +381,16 @@ static void free_level(LevelAlloc &a)
     if (a.setblock) cudaFree(a.setblock);
     if (a.listblock) cudaFree(a.listblock);
     if (a.eblock) cudaFree(a.eblock);
+    if (a.comblock) cudaFree(a.comblock);
+    if (a.h_comstage) cudaFreeHost(a.h_comstage);
+    if (a.d_cl) cudaFree(a.d_cl);
+    if (a.d_far) cudaFree(a.d_far);
+    a.comblock = a.h_comstage = nullptr;
+    a.d_cl = nullptr;
+    a.d_far = nullptr;
+    a.com_cap = a.h_comstage_cap = 0;
+    a.cl_cap = 0;
+    a.far_cap = 0;
     a.block = a.setblock = a.listblock = a.eblock = nullptr;
     a.E = EdgeList{nullptr, nullptr, 0};
     a.cap = a.set_cap = a.list_cap = 0;
@@ -688,6 +718,128 @@ static int split_finish(cc_ctx *c, LevelAlloc &a, const LevelAlloc *parent, int 
     return CC_OK;
 }
 
+// Centre-of-mass approximation: the eligible components of the split just
+// taken (2..com_max members, in sets of at least COM_MIN_SET members), their
+// local indices and the far-matrix layout, built on the host from the split
+// summary and uploaded in one pinned transfer.  Components are ordered by
+// root, so the eligible ones come grouped by set, ascending.
+static int com_setup(cc_ctx *c, LevelAlloc &a, int ncomp)
+{
+    a.Ke = 0;
+    a.cv = ComView{nullptr, nullptr, nullptr, nullptr};
+    if (!(c->p.theta > 0.0)) return CC_OK;
+    const int ns = (int)a.h_set_n.size();
+    a.h_eq.clear();
+    a.h_eset.clear();
+    a.h_eloc.clear();
+    a.h_K.assign(ns, 0);
+    a.h_efirst.assign(ns, 0);
+    a.h_foff.assign(ns, 0);
+    std::vector<int32_t> starts(ns);
+    {
+        int pos = 0;
+        for (int s = 0; s < ns; ++s) {
+            starts[s] = pos;
+            pos += align_up(a.h_set_n[s], SET_ALIGN);
+        }
+    }
+    for (int q = 0; q < ncomp; ++q) {
+        const int sz = a.h_size[q];
+        if (sz < 2 || sz > c->p.com_max) continue;
+        const int st = a.h_start[q];
+        const int s = (int)(std::upper_bound(starts.begin(), starts.end(), st) - starts.begin()) - 1;
+        if (s < 0 || a.h_set_n[s] < COM_MIN_SET) continue;
+        if (a.h_K[s] == 0) a.h_efirst[s] = (int)a.h_eq.size();
+        a.h_eq.push_back(q);
+        a.h_eset.push_back(s);
+        a.h_eloc.push_back(a.h_K[s]++);
+    }
+    const int Ke = (int)a.h_eq.size();
+    if (Ke == 0) return CC_OK;
+    long long fb = 0;
+    for (int s = 0; s < ns; ++s) {
+        a.h_foff[s] = fb;
+        fb += (long long)a.h_K[s] * a.h_K[s];
+    }
+    // device buffers: ints (eq, eset, eloc, eany: Ke each; efirst, K: ns
+    // each), foff (ns longs), cm (8 Ke doubles)
+    const size_t ints = (size_t)4 * Ke + 2 * (size_t)ns;
+    const size_t bytes = 256 + ints * 4 + 16 + (size_t)ns * 8 + 16 + (size_t)Ke * 64;
+    if (bytes > a.com_cap) {
+        if (a.comblock) cudaFree(a.comblock);
+        a.comblock = nullptr;
+        a.com_cap = 0;
+        if (cudaMalloc(&a.comblock, 2 * bytes) != cudaSuccess) {
+            cudaGetLastError();
+            return fail(c, CC_E_NOMEM, "device allocation failed (centre-of-mass lists)");
+        }
+        a.com_cap = 2 * bytes;
+        if (a.h_comstage) cudaFreeHost(a.h_comstage);
+        a.h_comstage = nullptr;
+        if (cudaMallocHost(&a.h_comstage, 2 * bytes) != cudaSuccess) {
+            cudaGetLastError();
+            return fail(c, CC_E_NOMEM, "pinned host allocation failed (centre-of-mass lists)");
+        }
+        a.h_comstage_cap = 2 * bytes;
+    }
+    if (fb > a.far_cap) {
+        if (a.d_far) cudaFree(a.d_far);
+        a.d_far = nullptr;
+        if (cudaMalloc(&a.d_far, (size_t)(2 * fb)) != cudaSuccess) {
+            cudaGetLastError();
+            return fail(c, CC_E_NOMEM, "device allocation failed (far matrices)");
+        }
+        a.far_cap = 2 * fb;
+    }
+    if (a.cl_cap < a.cap + PAD_TAIL) {
+        if (a.d_cl) cudaFree(a.d_cl);
+        a.d_cl = nullptr;
+        if (cudaMalloc(&a.d_cl, (size_t)(a.cap + PAD_TAIL) * 4) != cudaSuccess) {
+            cudaGetLastError();
+            return fail(c, CC_E_NOMEM, "device allocation failed (centre-of-mass indices)");
+        }
+        a.cl_cap = a.cap + PAD_TAIL;
+    }
+    // staging laid out like the device block: the ints, then foff, then cm
+    char *hq = (char *)a.h_comstage, *dq = (char *)a.comblock;
+    int32_t *hi = (int32_t *)hq;
+    std::memcpy(hi, a.h_eq.data(), Ke * 4);
+    std::memcpy(hi + Ke, a.h_eset.data(), Ke * 4);
+    std::memcpy(hi + 2 * Ke, a.h_eloc.data(), Ke * 4);
+    std::memcpy(hi + 3 * Ke, a.h_efirst.data(), ns * 4);
+    std::memcpy(hi + 3 * Ke + ns, a.h_K.data(), ns * 4);
+    const size_t foff_at = (ints * 4 + 15) / 16 * 16;
+    std::memcpy(hq + foff_at, a.h_foff.data(), ns * 8);
+    const size_t cm_at = (foff_at + (size_t)ns * 8 + 15) / 16 * 16;
+    int32_t *di = (int32_t *)dq;
+    a.d_eq = di;
+    a.d_eset = di + Ke;
+    a.d_eloc = di + 2 * Ke;
+    a.d_efirst = di + 3 * Ke;
+    a.d_K = di + 3 * Ke + ns;
+    a.d_eany = di + 3 * Ke + 2 * ns;
+    a.d_foff = (long long *)(dq + foff_at);
+    a.d_cm = (double *)(dq + cm_at);
+    CC_CUDA(c, cudaMemcpyAsync(dq, hq, foff_at + (size_t)ns * 8, cudaMemcpyHostToDevice, c->stream));
+    a.Ke = Ke;
+    a.far_bytes = fb;
+    a.cv = ComView{a.d_cl, a.d_foff, a.d_K, a.d_far};
+    return CC_OK;
+}
+
+// the centres and far matrices of the eligible components, from the state
+// at the DKD (their first half has moved them since the split)
+static int com_prepare(cc_ctx *c, LevelAlloc &a)
+{
+    if (a.Ke == 0) return CC_OK;
+    const cudaStream_t s = c->stream;
+    CC_CUDA(c, cudaMemsetAsync(a.d_cl, 0xff, (size_t)a.L.total * 4, s));
+    launch_com_prep(a.L, a.members, a.comp_start, a.comp_size, a.d_eq, a.d_eloc, a.Ke, a.d_cl, a.d_cm, s);
+    launch_com_far(a.d_cm, a.d_eq, a.comp_size, a.d_eset, a.d_eloc, a.d_efirst, a.d_foff, a.d_K, a.Ke, c->p.theta,
+                   c->p.G, c->p.eps * c->p.eps, a.d_far, a.d_eany, c->d_ctr, s);
+    return CC_OK;
+}
+
 static int ensure_kpart(cc_ctx *c, int chunks, int fcap)
 {
     const size_t need = (size_t)std::max(1, chunks) * 3 * (size_t)fcap * sizeof(double);
@@ -724,7 +876,8 @@ static int level_kick(cc_ctx *c, LevelAlloc &a, const int32_t *lab, const int32_
         // FP64: one shape (32-body i-tiles; the row order fixes the rounding)
         L.itile_off = a.k64_off[0];
         const int ev = ev_begin(c, 1, nullptr, -1, 0, 0, (double)a.pairs);
-        launch_kick(L, lab, (int)a.k64_blocks[0], c->p.G, c->p.eps * c->p.eps, h, 0, c->d_ctr, s);
+        launch_kick(L, lab, (int)a.k64_blocks[0], c->p.G, c->p.eps * c->p.eps, h, 0, c->d_ctr, s,
+                    a.Ke > 0 ? &a.cv : nullptr);
         ev_end(c, ev);
     }
     return CC_OK;
@@ -733,16 +886,27 @@ static int level_kick(cc_ctx *c, LevelAlloc &a, const int32_t *lab, const int32_
 static int dkd(cc_ctx *c, LevelAlloc &a, double h)
 {
     const cudaStream_t s = c->stream;
+    // the centre-of-mass approximation: the eligible components' centres and
+    // far matrices at this state (component members are not drifted here)
+    CC_TRY(com_prepare(c, a));
     if (c->p.precision == CC_PREC_MIXED && !(h < c->p.h_fp64)) {
         // positions in the root-sorted order of the split (members of one
         // component adjacent: tiles inside one component are skipped); both
         // drifts ride on the copy and on the partial reduce
         launch_prep_kick(a.L, a.F, a.members, a.root, c->p.G, 0.5 * h, s);
         CC_TRY(level_kick(c, a, a.root, a.members, h, 0.5 * h));
+        if (a.Ke > 0) {
+            // the FP32 kick took the far pairs too: out again, then the monopole
+            launch_com_unkick(a.L, a.members, a.comp_start, a.comp_size, a.d_eq, a.d_eloc, a.d_eset, a.d_efirst,
+                              a.d_foff, a.d_K, a.d_far, a.Ke, c->p.G, c->p.eps * c->p.eps, h, s);
+            launch_com_apply(a.L, a.members, a.comp_start, a.comp_size, a.d_eq, a.d_cm, a.d_eany, a.Ke, h, s);
+        }
         return CC_OK;
     }
     launch_drift(a.L, a.root, 0.5 * h, s);
     CC_TRY(level_kick(c, a, a.root, a.members, h));
+    if (a.Ke > 0)
+        launch_com_apply(a.L, a.members, a.comp_start, a.comp_size, a.d_eq, a.d_cm, a.d_eany, a.Ke, h, s);
     launch_drift(a.L, a.root, 0.5 * h, s);
     return CC_OK;
 }
@@ -805,6 +969,7 @@ static int process(cc_ctx *c, int d, double h, const LevelAlloc *parent)
     if (c->p.kepler) launch_kepler(a.L, a.members, a.comp_start, a.klist, a.kqueue + 2, bound, c->p.G, 0.5 * h, c->d_ctr, s);
     int ncomp = 0;
     CC_TRY(split_finish(c, a, parent, ncomp));
+    CC_TRY(com_setup(c, a, ncomp));
     // the host's part: counts, and the layout of the large components
     std::vector<int32_t> &lstart = a.v_lstart, &lsize = a.v_lsize;
     lstart.clear();
@@ -909,11 +1074,15 @@ static int harvest_counters(cc_ctx *c)
         c->tm.small_tau_evaluated += h.small_tau_evals;
         c->tm.small_kick_pairs += h.small_kick_pairs;
     }
-    // tau_fp64 .. small_tau_evals
-    static_assert(offsetof(DevCounters, small_tau_evals) - offsetof(DevCounters, tau_fp64) ==
-                      9 * sizeof(unsigned long long),
+    // the centre-of-mass approximation's pairs were counted as kick pairs by
+    // the splits (n(n-1)/2 - inner pairs)
+    c->st.kick_pairs -= h.com_pairs;
+    c->st.com_pairs += h.com_pairs;
+    // tau_fp64 .. com_pairs
+    static_assert(offsetof(DevCounters, com_pairs) - offsetof(DevCounters, tau_fp64) ==
+                      10 * sizeof(unsigned long long),
                   "counter block");
-    CC_CUDA(c, cudaMemsetAsync(&c->d_ctr->tau_fp64, 0, sizeof(unsigned long long) * 10, c->stream));
+    CC_CUDA(c, cudaMemsetAsync(&c->d_ctr->tau_fp64, 0, sizeof(unsigned long long) * 11, c->stream));
     return CC_OK;
 }
 
@@ -936,6 +1105,8 @@ int cc_default_params(cc_params *p)
     p->s_small = 32;
     p->eta_outside = 0;
     p->autotune = 1;
+    p->com_max = 32;
+    p->theta = 0.0;
     return CC_OK;
 }
 
@@ -954,7 +1125,8 @@ int cc_init(cc_ctx **out, int64_t n, const double *m, const double *x3, const do
         p->max_depth > 200 || (p->precision != CC_PREC_FP64 && p->precision != CC_PREC_MIXED) ||
         (p->kepler && p->eps != 0.0) || p->s_small < 0 || p->s_small > 32 || p->edge_rec_max < 0 ||
         p->fault_test < 0 || p->fault_test > 2 || (p->split != CC_SPLIT_CC && p->split != CC_SPLIT_HOLD) ||
-        (p->split == CC_SPLIT_HOLD && p->kepler)) {
+        (p->split == CC_SPLIT_HOLD && p->kepler) || !(p->theta >= 0.0) || !std::isfinite(p->theta) ||
+        (p->theta > 0.0 && (p->split != CC_SPLIT_CC || p->com_max < 2 || p->com_max > COM_MAX_MEMBERS))) {
         g_init_err = "cc_init: invalid parameters";
         return CC_E_ARG;
     }

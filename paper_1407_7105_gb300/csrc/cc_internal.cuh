@@ -91,6 +91,7 @@ struct DevCounters {
     unsigned long long small_components;
     unsigned long long tau_evals;  // pairs whose tau the small kernel or the edge-record pass evaluated
     unsigned long long small_tau_evals;  // of those, the small kernel's
+    unsigned long long com_pairs;        // body pairs the centre-of-mass approximation took
     unsigned int err;
     int max_depth_seen;
 };
@@ -312,8 +313,21 @@ void launch_edges_reuse(const EdgeList &parent, long long pcount, const Level &P
                         const int32_t *inv, const Level &C, const EdgeList &child, const TauParams &P,
                         DevCounters *ctr, int32_t *near_ij, double *near_tau, long long near_cap, cudaStream_t s,
                         bool hook = true);
+// centre-of-mass approximation of V_CC (Sec. 4.1): a level's eligible
+// components (2..com_max members, in a set of more than COM_MIN_SET - 1
+// members) have a local index within their set; two of them are far when
+// R_a + R_b < theta |X_a - X_b| (far[foff[s] + a K[s] + b] = 1).  cl = null:
+// the approximation is off.
+constexpr int COM_MIN_SET = 33;
+constexpr int COM_MAX_MEMBERS = 64;
+struct ComView {
+    const int32_t *cl;          // per packed element: local eligible index, -1
+    const long long *foff;      // per set: offset of its far matrix
+    const int32_t *K;           // per set: eligible components
+    const unsigned char *far;   // far matrices, K x K bytes per set
+};
 void launch_kick(const Level &L, const int32_t *label, int nitiles, double G, double eps2, double h,
-                 int variant, DevCounters *ctr, cudaStream_t s);
+                 int variant, DevCounters *ctr, cudaStream_t s, const ComView *com = nullptr);
 void launch_energy(const double *x3, const double *v3, const double *m, long long n, double G, double eps2,
                    const int32_t *sys_off /* nsys + 1 offsets, or null */, int nsys, double *partial /*[nblk*8]*/,
                    int nblk, cudaStream_t s);
@@ -404,6 +418,26 @@ void launch_kick_mixed(const Level &L, const FFView &F, const int32_t *order, co
 void launch_small(const Level &L, const int32_t *members, const int32_t *comp_start, const int32_t *comp_size,
                   const int32_t *slist, const int32_t *ns_ptr, int ns_bound, const SmallParams &SP, DevCounters *ctr,
                   int *queue, int32_t *near_ij, double *near_tau, long long near_cap, int nsm, cudaStream_t s);
+
+// cc_com.cu: the centre-of-mass approximation.  Eligible component g (of Ke)
+// is component eq[g] (members[comp_start[q] ..]) of set eset[g] with local
+// index eloc[g]; efirst[s] = the first g of set s.  cm: 8 doubles per g
+// (M, X, Y, Z, R, Ax, Ay, Az), eany[g] = 1 if g has a far partner.
+void launch_com_prep(const Level &L, const int32_t *members, const int32_t *comp_start, const int32_t *comp_size,
+                     const int32_t *eq, const int32_t *eloc, int Ke, int32_t *cl, double *cm, cudaStream_t s);
+void launch_com_far(double *cm, const int32_t *eq, const int32_t *comp_size, const int32_t *eset,
+                    const int32_t *eloc, const int32_t *efirst, const long long *foff, const int32_t *K, int Ke,
+                    double theta, double G, double eps2, unsigned char *far, int32_t *eany, DevCounters *ctr,
+                    cudaStream_t s);
+// v_i += h A_g for the members of every eligible component with a far partner
+void launch_com_apply(const Level &L, const int32_t *members, const int32_t *comp_start, const int32_t *comp_size,
+                      const int32_t *eq, const double *cm, const int32_t *eany, int Ke, double h, cudaStream_t s);
+// mixed form: the kick kernel kicked every cross pair in FP32; take the far
+// pairs back out (FP64 pair forces) before launch_com_apply adds the monopole
+void launch_com_unkick(const Level &L, const int32_t *members, const int32_t *comp_start, const int32_t *comp_size,
+                       const int32_t *eq, const int32_t *eloc, const int32_t *eset, const int32_t *efirst,
+                       const long long *foff, const int32_t *K, const unsigned char *far, int Ke, double G,
+                       double eps2, double h, cudaStream_t s);
 
 // cc_kepler.cu
 void launch_kepler(const Level &L, const int32_t *members, const int32_t *comp_start, const int32_t *klist,

@@ -425,10 +425,14 @@ struct __align__(16) KickBSmem {
     double f[3][KB_T][KB_T + 1];     // pair forces of the current tile (padded rows)
     double xi[3][KB_T];              // the i-tile
     int32_t li[KB_T];
+    int32_t ci[KB_T], cj[KB_T];      // centre-of-mass approximation: local eligible indices
 };
 
+// COM: pairs of far components (ComView) are left out; their kick is the
+// centre-of-mass one that launch_com_apply adds afterwards
+template <bool COM>
 __global__ void __launch_bounds__(KB_THREADS) k_kick64(Level L, const int32_t *label, double G, double eps2, double h,
-                                                       DevCounters *ctr)
+                                                       DevCounters *ctr, ComView cv)
 {
     __shared__ KickBSmem sm;
     const int tid = threadIdx.x;
@@ -449,6 +453,13 @@ __global__ void __launch_bounds__(KB_THREADS) k_kick64(Level L, const int32_t *l
         sm.xi[1][tid] = v ? L.y[i] : 0.0;
         sm.xi[2][tid] = v ? L.z[i] : 0.0;
         sm.li[tid] = v ? label[i] : 0;
+        if (COM) sm.ci[tid] = v ? cv.cl[i] : -1;
+    }
+    long long fo = 0;
+    int Ks = 0;
+    if (COM) {
+        fo = cv.foff[s];
+        Ks = cv.K[s];
     }
     __syncthreads();
     if (tid == 0) kick_issue(sm.j, 0, L, label, start, min(KB_T, n));
@@ -465,10 +476,16 @@ __global__ void __launch_bounds__(KB_THREADS) k_kick64(Level L, const int32_t *l
             break;
         }
         const int jn = min(KB_T, n - tj * KB_T), jl0 = tj * KB_T;
+        if (COM) {
+            if (tid < KB_T) sm.cj[tid] = tid < jn ? cv.cl[start + jl0 + tid] : -1;
+            __syncthreads();
+        }
 #pragma unroll
         for (int q = 0; q < KB_T * KB_T / KB_THREADS; ++q) {
             const int pidx = tid + q * KB_THREADS, ii = pidx >> 5, jj = pidx & 31;
-            const bool use = ii < ni && jj < jn && il0 + ii != jl0 + jj && sm.li[ii] != sm.j.lab[st][jj];
+            bool use = ii < ni && jj < jn && il0 + ii != jl0 + jj && sm.li[ii] != sm.j.lab[st][jj];
+            if (COM && use && sm.ci[ii] >= 0 && sm.cj[jj] >= 0)
+                use = cv.far[fo + (long long)sm.ci[ii] * Ks + sm.cj[jj]] == 0;
             const double dx0 = __dsub_rn(sm.j.col[st][0][jj], sm.xi[0][ii]);
             const double dx1 = __dsub_rn(sm.j.col[st][1][jj], sm.xi[1][ii]);
             const double dx2 = __dsub_rn(sm.j.col[st][2][jj], sm.xi[2][ii]);
@@ -500,11 +517,14 @@ __global__ void __launch_bounds__(KB_THREADS) k_kick64(Level L, const int32_t *l
 }
 
 void launch_kick(const Level &L, const int32_t *label, int nitiles, double G, double eps2, double h,
-                 int variant, DevCounters *ctr, cudaStream_t s)
+                 int variant, DevCounters *ctr, cudaStream_t s, const ComView *com)
 {
     (void)variant;  // one shape: 32-body tiles (the prefix of variant 0)
     if (nitiles <= 0) return;
-    k_kick64<<<nitiles, KB_THREADS, 0, s>>>(L, label, G, eps2, h, ctr);
+    if (com && com->cl)
+        k_kick64<true><<<nitiles, KB_THREADS, 0, s>>>(L, label, G, eps2, h, ctr, *com);
+    else
+        k_kick64<false><<<nitiles, KB_THREADS, 0, s>>>(L, label, G, eps2, h, ctr, ComView{nullptr, nullptr, nullptr, nullptr});
     CC_COUNT_LAUNCH(1);
 }
 
