@@ -605,6 +605,45 @@ def run_eta_sweep(args):
     return 0
 
 
+def run_com_sweep(args):
+    """The centre-of-mass approximation of V_CC (Sec. 4.1) against the exact
+    kick (JSON lines): the 65536-body fractal and the 16384-body Plummer
+    sphere, both forms, theta in {0, 0.3, 0.5, 0.7} (com_max = 32): ms per
+    step over --sweep-steps outer steps after one warm-up step, kick pairs
+    and pairs taken by the approximation per step, |dE/E| and the momentum
+    drift over the steps."""
+    import argparse as _ap
+    import torch
+
+    from paper_1407_7105_gb300 import build, cc
+    build.build()
+    dev = torch.device("cuda", 0)
+    stream = torch.cuda.current_stream()
+    for wl, n in (("fractal", 65536), ("plummer", N_BODY)):
+        a = _ap.Namespace(workload=wl, n=n, nsys=4096)
+        m, x, v, _ = make_workload(a, args.seed, dev)
+        dm, dx, dv = (torch.tensor(q, device=dev) for q in (m, x, v))
+        dtw = WORKLOADS[wl]["dt"]
+        for form in ("mixed", "fp64"):
+            for theta in (0.0, 0.3, 0.5, 0.7):
+                prec = cc.PREC_MIXED if form == "mixed" else cc.PREC_FP64
+                ctx = cc.Context(dm, dx, dv, dt=dtw, eta=ETA, precision=prec, theta=theta, com_max=32)
+                E0, P0, _ = ctx.energy()
+                ctx.evolve(dtw)
+                torch.cuda.synchronize()
+                steps = 1 if (form == "fp64" and wl == "fractal") else args.sweep_steps
+                _, ms, _, s0, s1 = time_steps(ctx, dtw, dtw, steps, stream)
+                E1, P1, _ = ctx.energy()
+                ctx.close()
+                print(json.dumps({"com_sweep": True, "workload": workload_name(m.shape[0], wl, 4096), "form": form,
+                                  "theta": theta, "steps": steps, "ms_per_step": ms / steps,
+                                  "kick_pairs_per_step": (s1["kick_pairs"] - s0["kick_pairs"]) / steps,
+                                  "com_pairs_per_step": (s1["com_pairs"] - s0["com_pairs"]) / steps,
+                                  "dE_over_E": (E1 - E0) / abs(E0), "dP": float(np.abs(P1 - P0).max()),
+                                  "steps_for_dE": steps + 1}), flush=True)
+    return 0
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -625,6 +664,8 @@ def main():
     ap.add_argument("--t-end", type=float, default=1.0)
     ap.add_argument("--eta-sweep", action="store_true",
                     help="energy error of the fractal and the systems batch against eta (mixed form)")
+    ap.add_argument("--com-sweep", action="store_true",
+                    help="the centre-of-mass approximation of V_CC against the exact kick (both forms, theta sweep)")
     ap.add_argument("--sweep-steps", type=int, default=16)
     ap.add_argument("--seed", type=int, default=1)
     ap.add_argument("--n", type=int, default=None, help="bodies (default per workload)")
@@ -643,6 +684,8 @@ def main():
         return run_accuracy(args)
     if args.eta_sweep:
         return run_eta_sweep(args)
+    if args.com_sweep:
+        return run_com_sweep(args)
     if world > 1:
         import torch.distributed as dist
         dist.init_process_group("nccl")

@@ -56,8 +56,14 @@ typedef struct {
     int    precision;  /* CC_PREC_FP64 or CC_PREC_MIXED                                 */
     int    kepler;     /* 1: CC_KEPLER (Sec. 3.2), two-body components by Kepler flow   */
     int    max_depth;  /* recursion depth cap (levels below the outer step)            */
-    int    s_small;    /* components of at most s_small (<= 32) members run entirely in
-                          the persistent small-component kernel; 0 disables it         */
+    int    s_small;    /* components of at most s_small (<= 512) members run entirely
+                          on-chip in the persistent batched kernel: up to 32 members
+                          one warp each, 33..512 one thread block each (its own
+                          components of <= 32 members on its warps); 0 disables it.
+                          With theta > 0 the limit is 32.  When every system of
+                          cc_set_systems (or the one system of n bodies) has 2..s_small
+                          members (3.. with kepler), an outer step is one launch:
+                          every system one task                                       */
     int    eta_outside;/* 0: eta inside T and dT/dt (default reading); 1: eta
                           multiplies the min of Eq. (tauij) literally                  */
     int    autotune;   /* 1: launch shapes tuned online per size bin (default); 0: a

@@ -193,7 +193,23 @@ struct cc_ctx {
     size_t ev_used = 0;
     cc_timing_t tm{};
     unsigned long long launch_mark = 0;
+    // batched small-component kernel: frame scratch (per resident CTA), and
+    // the whole-batch mode of independent systems (every system a task of
+    // the kernel: tlist, t_start, t_size, count, queue; identity member list)
+    char *batch_scr = nullptr;
+    bool sys_batch = false;
+    int32_t *d_sys_tasks = nullptr;
+    int32_t *d_iota = nullptr;
 };
+
+// components (and systems) of at most this many bodies run in the batched
+// kernel; above 32 only without the centre-of-mass approximation (it acts in
+// sets of more than 32 members, which the host levels run)
+static int small_max(const cc_ctx *c)
+{
+    const int lim = c->p.theta > 0.0 ? 32 : BATCH_NMAX;
+    return std::min(c->p.s_small, lim);
+}
 
 // record the start of a timed launch (user timing on, or a tuner sample);
 // returns the pair index or -1
@@ -672,7 +688,7 @@ static int split_launch(cc_ctx *c, LevelAlloc &a, double h, const LevelAlloc *pa
     }
     // HOLD: the set's non-trivial components form one fast set
     if (hold) launch_hold_merge(a.L, (int32_t *)c->seg_scratch, s);
-    const ClassifyArgs cls{c->p.s_small, c->p.kepler, a.kqueue, a.kqueue + 2, a.klist, a.slist};
+    const ClassifyArgs cls{small_max(c), c->p.kepler, a.kqueue, a.kqueue + 2, a.klist, a.slist};
     a.classified = launch_compress_segment(a.L, a.root, a.members, a.comp_start, a.comp_size, a.d_ncomp,
                                            c->seg_scratch, s, hook_in_seg ? &a.E : nullptr, c->d_ctr,
                                            a.klist && a.slist && a.kqueue ? &cls : nullptr);
@@ -919,6 +935,38 @@ static int side_stream(cc_ctx *c, int d, cudaStream_t *out)
     return CC_OK;
 }
 
+static int ensure_batch_scratch(cc_ctx *c)
+{
+    if (c->batch_scr) return CC_OK;
+    const size_t bytes = batch_scratch_bytes(c->nsm);
+    if (cudaMalloc(&c->batch_scr, bytes) != cudaSuccess) {
+        cudaGetLastError();
+        c->batch_scr = nullptr;
+        return fail(c, CC_E_NOMEM, "device allocation failed (batched-kernel frames)");
+    }
+    CC_CUDA(c, cudaMemset(c->batch_scr, 0, bytes));  // every scratch slot free
+    return CC_OK;
+}
+
+static SmallParams small_params(const cc_ctx *c, double h0, int depth0)
+{
+    SmallParams SP;
+    SP.G = c->p.G;
+    SP.eps2 = c->p.eps * c->p.eps;
+    SP.eta = c->eta_run;
+    SP.eta_in = c->p.eta_outside ? 1.0 : c->eta_run;
+    SP.h0 = h0;
+    SP.near_tol = c->p.near_tol;
+    SP.h_fp64 = c->p.h_fp64;
+    SP.eta_outside = c->p.eta_outside;
+    SP.kepler = c->p.kepler;
+    SP.precision = c->p.precision;
+    SP.depth0 = depth0;
+    SP.max_depth = c->p.max_depth;
+    SP.hold = c->p.split == CC_SPLIT_HOLD;
+    return SP;
+}
+
 static int process(cc_ctx *c, int d, double h, const LevelAlloc *parent)
 {
     if (d > c->p.max_depth) return fail(c, CC_E_DEPTH, "recursion deeper than max_depth");
@@ -932,27 +980,15 @@ static int process(cc_ctx *c, int d, double h, const LevelAlloc *parent)
     // small components' first half (side stream) and the Kepler pairs start
     // while the host waits for the split summary and lays out the large
     // components; they touch disjoint particles.
-    SmallParams SP;
-    SP.G = c->p.G;
-    SP.eps2 = c->p.eps * c->p.eps;
-    SP.eta = c->eta_run;
-    SP.eta_in = c->p.eta_outside ? 1.0 : c->eta_run;
-    SP.h0 = 0.5 * h;
-    SP.near_tol = c->p.near_tol;
-    SP.h_fp64 = c->p.h_fp64;
-    SP.eta_outside = c->p.eta_outside;
-    SP.kepler = c->p.kepler;
-    SP.precision = c->p.precision;
-    SP.depth0 = d + 1;
-    SP.max_depth = c->p.max_depth;
-    SP.hold = c->p.split == CC_SPLIT_HOLD;
+    const SmallParams SP = small_params(c, 0.5 * h, d + 1);
+    const int smax = small_max(c);
     const int bound = a.L.total / 2 + 1;  // components of a split, at most
-    const bool small_on = c->p.s_small >= 2 && d + 1 <= c->p.max_depth;
+    const bool small_on = smax >= 2 && d + 1 <= c->p.max_depth;
+    if (small_on && smax > 32) CC_TRY(ensure_batch_scratch(c));
     cudaStream_t side = nullptr;
     if (small_on) CC_TRY(side_stream(c, d, &side));
     if (!a.classified)
-        launch_classify(a.comp_size, a.d_ncomp, c->p.s_small, c->p.kepler, a.kqueue, a.kqueue + 2, a.klist, a.slist,
-                        s);
+        launch_classify(a.comp_size, a.d_ncomp, smax, c->p.kepler, a.kqueue, a.kqueue + 2, a.klist, a.slist, s);
     if (small_on) {
         if (!a.ev_ready) {
             CC_CUDA(c, cudaEventCreateWithFlags(&a.ev_ready, cudaEventDisableTiming));
@@ -961,8 +997,12 @@ static int process(cc_ctx *c, int d, double h, const LevelAlloc *parent)
         CC_CUDA(c, cudaEventRecord(a.ev_ready, s));
         CC_CUDA(c, cudaStreamWaitEvent(side, a.ev_ready, 0));
         const int ev = ev_begin(c, 2, side);
-        launch_small(a.L, a.members, a.comp_start, a.comp_size, a.slist, a.kqueue + 3, bound, SP, c->d_ctr,
-                     a.kqueue + 0, c->d_near_ij, c->d_near_tau, c->near_cap, c->nsm, side);
+        if (smax > 32)
+            launch_batch(a.L, a.members, a.comp_start, a.comp_size, a.slist, a.kqueue + 3, bound, SP, c->d_ctr,
+                         a.kqueue + 0, c->d_near_ij, c->d_near_tau, c->near_cap, c->nsm, c->batch_scr, side);
+        else
+            launch_small(a.L, a.members, a.comp_start, a.comp_size, a.slist, a.kqueue + 3, bound, SP, c->d_ctr,
+                         a.kqueue + 0, c->d_near_ij, c->d_near_tau, c->near_cap, c->nsm, side);
         ev_end(c, ev, side);
         CC_CUDA(c, cudaEventRecord(a.ev_small, side));
     }
@@ -975,7 +1015,6 @@ static int process(cc_ctx *c, int d, double h, const LevelAlloc *parent)
     lstart.clear();
     lsize.clear();
     int nk = 0, ns = 0;
-    const int smax = std::min(c->p.s_small, 32);
     for (int q = 0; q < ncomp; ++q) {
         const int sz = a.h_size[q];
         if (c->p.kepler && sz == 2) ++nk;
@@ -1006,8 +1045,12 @@ static int process(cc_ctx *c, int d, double h, const LevelAlloc *parent)
                 CC_CUDA(c, cudaEventRecord(a.ev_ready, s));
                 CC_CUDA(c, cudaStreamWaitEvent(side, a.ev_ready, 0));
                 const int ev = ev_begin(c, 2, side);
-                launch_small(a.L, a.members, a.comp_start, a.comp_size, a.slist, a.kqueue + 3, ns, SP, c->d_ctr,
-                             a.kqueue + 1, c->d_near_ij, c->d_near_tau, c->near_cap, c->nsm, side);
+                if (smax > 32)
+                    launch_batch(a.L, a.members, a.comp_start, a.comp_size, a.slist, a.kqueue + 3, ns, SP, c->d_ctr,
+                                 a.kqueue + 1, c->d_near_ij, c->d_near_tau, c->near_cap, c->nsm, c->batch_scr, side);
+                else
+                    launch_small(a.L, a.members, a.comp_start, a.comp_size, a.slist, a.kqueue + 3, ns, SP,
+                                 c->d_ctr, a.kqueue + 1, c->d_near_ij, c->d_near_tau, c->near_cap, c->nsm, side);
                 ev_end(c, ev, side);
                 CC_CUDA(c, cudaEventRecord(a.ev_small, side));
             }
@@ -1041,6 +1084,43 @@ static int setup_systems(cc_ctx *c)
     CC_CUDA(c, cudaMalloc(&c->d_sys_off, off.size() * 4));
     CC_CUDA(c, cudaMemcpyAsync(c->d_sys_off, off.data(), off.size() * 4, cudaMemcpyHostToDevice, c->stream));
     CC_CUDA(c, cudaStreamSynchronize(c->stream));
+    // Whole-batch mode: when every system fits the batched kernel, an outer
+    // step is evolve_cc(system, dt) of every system as one task of one
+    // launch, largest first (no host level).  Kepler mode needs three
+    // bodies or more (a two-body system's first split decides between the
+    // Kepler flow and a kick, which the host level takes).
+    if (c->d_sys_tasks) cudaFree(c->d_sys_tasks);
+    if (c->d_iota) cudaFree(c->d_iota);
+    c->d_sys_tasks = nullptr;
+    c->d_iota = nullptr;
+    c->sys_batch = false;
+    const int smax = small_max(c);
+    const int nmin = c->p.kepler ? 3 : 2;
+    bool all = smax > 32 && c->p.max_depth >= 0;
+    for (int32_t z : sizes) all = all && z >= nmin && z <= smax;
+    if (all) {
+        const int ns = (int)sizes.size();
+        std::vector<int32_t> order(ns);
+        for (int q = 0; q < ns; ++q) order[q] = q;
+        std::stable_sort(order.begin(), order.end(), [&](int a, int b) { return size_bucket(sizes[a]) > size_bucket(sizes[b]); });
+        // tlist, t_start, t_size, [count, queue]
+        std::vector<int32_t> blk(3 * (size_t)ns + 2);
+        for (int q = 0; q < ns; ++q) {
+            blk[q] = order[q];
+            blk[ns + q] = S.start[q];
+            blk[2 * ns + q] = sizes[q];
+        }
+        blk[3 * ns] = ns;
+        blk[3 * ns + 1] = 0;
+        CC_CUDA(c, cudaMalloc(&c->d_sys_tasks, blk.size() * 4));
+        CC_CUDA(c, cudaMemcpy(c->d_sys_tasks, blk.data(), blk.size() * 4, cudaMemcpyHostToDevice));
+        std::vector<int32_t> iota(S.total > 0 ? S.total : 1);
+        for (size_t k = 0; k < iota.size(); ++k) iota[k] = (int32_t)k;
+        CC_CUDA(c, cudaMalloc(&c->d_iota, iota.size() * 4));
+        CC_CUDA(c, cudaMemcpy(c->d_iota, iota.data(), iota.size() * 4, cudaMemcpyHostToDevice));
+        CC_TRY(ensure_batch_scratch(c));
+        c->sys_batch = true;
+    }
     return CC_OK;
 }
 
@@ -1123,7 +1203,7 @@ int cc_init(cc_ctx **out, int64_t n, const double *m, const double *x3, const do
     *out = nullptr;
     if (!(p->G > 0.0) || !(p->eps >= 0.0) || !finite_pos(p->eta) || !finite_pos(p->dt) || p->max_depth < 0 ||
         p->max_depth > 200 || (p->precision != CC_PREC_FP64 && p->precision != CC_PREC_MIXED) ||
-        (p->kepler && p->eps != 0.0) || p->s_small < 0 || p->s_small > 32 || p->edge_rec_max < 0 ||
+        (p->kepler && p->eps != 0.0) || p->s_small < 0 || p->s_small > BATCH_NMAX || p->edge_rec_max < 0 ||
         p->fault_test < 0 || p->fault_test > 2 || (p->split != CC_SPLIT_CC && p->split != CC_SPLIT_HOLD) ||
         (p->split == CC_SPLIT_HOLD && p->kepler) || !(p->theta >= 0.0) || !std::isfinite(p->theta) ||
         (p->theta > 0.0 && (p->split != CC_SPLIT_CC || p->com_max < 2 || p->com_max > COM_MAX_MEMBERS))) {
@@ -1256,7 +1336,19 @@ int cc_evolve(cc_ctx *c, double t_end, double eta)
         launch_pack_state(c->d_x3, c->d_v3, c->d_m, c->n, c->lv[0].L, c->d_sys_off, spatial ? c->d_perm : nullptr,
                           c->stream);
         if (spatial) ++c->perm_age;
-        int rc = process(c, 0, c->p.dt, nullptr);
+        int rc = CC_OK;
+        if (c->sys_batch) {
+            // every system one task: evolve_cc(system, dt), split at depth 0
+            const int ns = (int)c->sys_off.size() - 1;
+            int32_t *tk = c->d_sys_tasks;
+            CC_CUDA(c, cudaMemsetAsync(tk + 3 * ns + 1, 0, 4, c->stream));
+            const SmallParams SP = small_params(c, c->p.dt, 0);
+            launch_batch(c->lv[0].L, c->d_iota, tk + ns, tk + 2 * ns, tk, tk + 3 * ns, ns, SP, c->d_ctr,
+                         tk + 3 * ns + 1, c->d_near_ij, c->d_near_tau, c->near_cap, c->nsm, c->batch_scr, c->stream);
+            c->st.small_tasks += (unsigned long long)ns;
+        } else {
+            rc = process(c, 0, c->p.dt, nullptr);
+        }
         if (rc) return rc;
         launch_unpack_state(c->d_x3, c->d_v3, c->n, c->lv[0].L, c->stream);
         CC_TRY(check_device_error(c));
@@ -1534,7 +1626,8 @@ int cc_destroy(cc_ctx *c)
     for (auto &a : c->lv) free_level(a);
     free_level(c->unit);
     void *ptrs[] = {c->d_x3, c->d_v3, c->d_m, c->d_ctr, c->d_near_ij, c->d_near_tau, c->d_partial,
-                    c->tmp, c->seg_scratch, c->d_sys_off, c->d_bad, c->d_kpart, c->d_perm, c->d_box};
+                    c->tmp, c->seg_scratch, c->d_sys_off, c->d_bad, c->d_kpart, c->d_perm, c->d_box,
+                    c->batch_scr, c->d_sys_tasks, c->d_iota};
     for (void *q : ptrs)
         if (q) cudaFree(q);
     delete c;

@@ -372,23 +372,24 @@ __device__ __forceinline__ int warp_inclusive_scan(int v)
 }
 
 // The classification of a split's components (see k_classify below) by the
-// CTA that segmented them; sh: 70 ints of shared memory
+// CTA that segmented them; sh: CLS_SH ints of shared memory
 __device__ void classify_components(const int32_t *comp_size, int nc, const ClassifyArgs &C, int *sh)
 {
-    int *s_cnt = sh, *s_pos = sh + 34, *s_nk = sh + 68;
+    int *s_cnt = sh, *s_pos = sh + CLS_NB, *s_nk = sh + 2 * CLS_NB;
     const int tid = threadIdx.x, nt = blockDim.x;
-    if (tid < 34) s_cnt[tid] = 0;
+    const int smax = C.s_small;
+    for (int z = tid; z < CLS_NB; z += nt) s_cnt[z] = 0;
     if (tid == 0) *s_nk = 0;
     __syncthreads();
     for (int q = tid; q < nc; q += nt) {
         const int sz = comp_size[q];
         if (C.kepler && sz == 2) C.klist[atomicAdd(s_nk, 1)] = q;
-        else if (sz <= C.s_small) atomicAdd(&s_cnt[sz], 1);
+        else if (sz <= smax) atomicAdd(&s_cnt[size_bucket(sz)], 1);
     }
     __syncthreads();
     if (tid == 0) {
         int pos = 0;
-        for (int z = C.s_small; z >= 0; --z) {
+        for (int z = size_bucket(smax < 0 ? 0 : smax); z >= 0; --z) {
             s_pos[z] = pos;
             pos += s_cnt[z];
         }
@@ -400,7 +401,7 @@ __device__ void classify_components(const int32_t *comp_size, int nc, const Clas
     __syncthreads();
     for (int q = tid; q < nc; q += nt) {
         const int sz = comp_size[q];
-        if (!(C.kepler && sz == 2) && sz <= C.s_small) C.slist[atomicAdd(&s_pos[sz], 1)] = q;
+        if (!(C.kepler && sz == 2) && sz <= smax) C.slist[atomicAdd(&s_pos[size_bucket(sz)], 1)] = q;
     }
 }
 
@@ -622,7 +623,7 @@ __global__ void __launch_bounds__(SEG1_T) k_segment_small(Level L, int32_t *root
     if (cls.queue) {
         // the components' integrator lists (comp_size is this CTA's own
         // writes: visible after the barrier)
-        __shared__ int cls_sh[70];
+        __shared__ int cls_sh[CLS_SH];
         __syncthreads();
         classify_components(comp_size, tot_c, cls, cls_sh);
     }
@@ -650,10 +651,7 @@ bool launch_compress_segment(const Level &L, int32_t *root, int32_t *members, in
         }
         const EdgeList none{nullptr, nullptr, 0};
         ClassifyArgs nc{};
-        if (cls) {
-            nc = *cls;
-            nc.s_small = nc.s_small < 32 ? nc.s_small : 32;
-        }
+        if (cls) nc = *cls;
         k_segment_small<<<1, SEG1_T, (size_t)L.total * 8, s>>>(L, root, members, comp_start, comp_size, d_ncomp,
                                                                hook ? *hook : none, ctr, nc);
         CC_COUNT_LAUNCH(1);
@@ -711,8 +709,9 @@ void launch_hold_merge(const Level &L, int32_t *anchor, cudaStream_t s)
 // Sorts the components of a split for their integrators (one CTA, after the
 // segmentation): two-body components go to klist when Kepler mode is on,
 // components of at most s_small members to slist, largest first (a counting
-// sort by size; order within one size is immaterial: components are
-// independent), larger ones stay for the next level.  Writes counts[0] =
+// sort by size, in bins of 16 above 32 bodies; order within one bin is
+// immaterial: components are independent), larger ones stay for the next
+// level.  Writes counts[0] =
 // nk, counts[1] = ns and zeroes the two work-queue counters of the small
 // kernel (queue[0..1]), so the kernels that read them can be launched
 // before the host learns the sizes.
@@ -720,14 +719,14 @@ constexpr int CLS_T = 1024;
 
 __global__ void __launch_bounds__(CLS_T) k_classify(const int32_t *comp_size, const int32_t *ncomp, ClassifyArgs C)
 {
-    __shared__ int sh[70];
+    __shared__ int sh[CLS_SH];
     classify_components(comp_size, *ncomp, C, sh);
 }
 
 void launch_classify(const int32_t *comp_size, const int32_t *ncomp, int s_small, int kepler, int32_t *queue,
                      int32_t *counts, int32_t *klist, int32_t *slist, cudaStream_t s)
 {
-    const ClassifyArgs C{s_small < 32 ? s_small : 32, kepler, queue, counts, klist, slist};
+    const ClassifyArgs C{s_small < BATCH_NMAX ? s_small : BATCH_NMAX, kepler, queue, counts, klist, slist};
     k_classify<<<1, CLS_T, 0, s>>>(comp_size, ncomp, C);
     CC_COUNT_LAUNCH(1);
 }

@@ -348,6 +348,13 @@ void launch_segment(const Level &L, const int32_t *root, int32_t *members, int32
 // half's child edges (segment_hooks_edges(total) tells whether it will:
 // then launch_edges_reuse leaves the hooks to it).
 bool segment_hooks_edges(int total);
+// The batched small-component kernel takes tasks (components, or whole
+// systems) of up to BATCH_NMAX bodies; the classification orders them
+// largest first by size_bucket (exact up to 32 bodies, bins of 16 above).
+constexpr int BATCH_NMAX = 512;
+__host__ __device__ constexpr int size_bucket(int sz) { return sz <= 32 ? sz : 32 + (sz - 17) / 16; }
+constexpr int CLS_NB = size_bucket(BATCH_NMAX) + 1;
+constexpr int CLS_SH = 2 * CLS_NB + 1;
 // where the classification (see launch_classify) writes its lists
 struct ClassifyArgs {
     int s_small, kepler;
@@ -415,6 +422,14 @@ void launch_kick_mixed(const Level &L, const FFView &F, const int32_t *order, co
                        double *partial, const int32_t *root, double drift_dt, cudaStream_t s);
 
 // cc_small.cu
+// the batched kernel (k_batch): tasks tlist[0..*nt_ptr) (task c: packed
+// indices members[t_start[c] ..][0..t_size[c]), ascending id), largest first;
+// queue: a zeroed work counter; scratch: batch_scratch_bytes(nsm)
+size_t batch_scratch_bytes(int nsm);
+void launch_batch(const Level &L, const int32_t *members, const int32_t *t_start, const int32_t *t_size,
+                  const int32_t *tlist, const int32_t *nt_ptr, int nt_bound, const SmallParams &SP, DevCounters *ctr,
+                  int *queue, int32_t *near_ij, double *near_tau, long long near_cap, int nsm, char *scratch,
+                  cudaStream_t s);
 void launch_small(const Level &L, const int32_t *members, const int32_t *comp_start, const int32_t *comp_size,
                   const int32_t *slist, const int32_t *ns_ptr, int ns_bound, const SmallParams &SP, DevCounters *ctr,
                   int *queue, int32_t *near_ij, double *near_tau, long long near_cap, int nsm, cudaStream_t s);

@@ -402,339 +402,345 @@ __device__ __forceinline__ unsigned k8_pair_handoff(K8Warp &S, int lane, double 
     return e;
 }
 
-__global__ void __launch_bounds__(K8_WARPS * 32) k_small(Level L, const int32_t *members, const int32_t *comp_start,
-                                                          const int32_t *comp_size, const int32_t *slist,
-                                                          const int32_t *ns_ptr,
-                                                          SmallParams SP, DevCounters *ctr, int *queue,
-                                                          int32_t *near_ij, double *near_tau, long long near_cap)
+// counters of the sub-recursions a thread took part in (one atomic per
+// warp at the end of the kernel)
+struct SmallCnt {
+    unsigned long long tau = 0, kick = 0, drift = 0, split = 0, comp = 0, kep = 0, fp64 = 0, eval = 0;
+    int maxd = 0;
+};
+
+// the packed state of a level (what the batched tasks read and write)
+struct SView {
+    double *x, *y, *z, *vx, *vy, *vz;
+    const double *m;
+    const int32_t *gid;
+};
+
+// evolve_cc(C, h0) of one component of n <= 32 bodies (packed indices
+// mem[0..n), ascending particle id) by one warp, its first split at depth
+// depth0.  Errors are raised on ctr; the warp returns early on one.
+__device__ __forceinline__ void small_task(K8Warp &S, const SView V, const int32_t *mem, int n, double h0, int depth0,
+                                        const SmallParams &SP, DevCounters *ctr, const NearLog &nl, SmallCnt &cn,
+                                        PairCounters &pc)
 {
-    __shared__ K8Warp sw[K8_WARPS];
-    const int ns = *ns_ptr;
-    const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    K8Warp &S = sw[w];
+    const int lane = threadIdx.x & 31;
     const uint32_t me = 1u << lane;
     uint32_t mk[K8_MAXD], cmk[K8_MAXD];
     unsigned char ph[K8_MAXD], pm[K8_MAXD];
     signed char cf[K8_MAXD];  // level whose fresh split filled S.e for level k's state (-1: none)
-    PairCounters pc;
-    unsigned long long c_tau = 0, c_kick = 0, c_drift = 0, c_split = 0, c_comp = 0, c_kep = 0, c_fp64 = 0,
-                       c_eval = 0;
-    int maxd = 0;
     const bool mixed = SP.precision == CC_PREC_MIXED;
     TauParams P;
     P.G = SP.G; P.eps2 = SP.eps2; P.eta = SP.eta; P.eta_in = SP.eta_in; P.eta_outside = SP.eta_outside;
     P.near_tol = SP.near_tol;
     P.fault_test = 0;
+    P.h = h0;
     MixedTauParams Q;
     Q.eta = (float)SP.eta_in; Q.eps2 = (float)SP.eps2; Q.G = (float)SP.G;
     Q.hq = 0.f;  // (the pre-test is not used here)
-    const NearLog nl = {ctr, near_ij, near_tau, near_cap, SP.near_tol};
     // eta/h0 in float, once: eta/(h0 2^-k) is this times 2^k exactly
-    const float etah_c = (float)(SP.eta_outside ? SP.eta_in * SP.eta / SP.h0 : SP.eta_in / SP.h0);
-    for (;;) {
-        int q = 0;
-        if (lane == 0) q = atomicAdd(queue, 1);
-        q = __shfl_sync(FULL, q, 0);
-        if (q >= ns) break;
-        const int c = slist[q], n = comp_size[c], base = comp_start[c];
-        const bool act = lane < n;
-        const int p = act ? members[base + lane] : -1;
-        double st[7] = {0, 0, 0, 0, 0, 0, 0};
-        if (act) {
-            st[0] = L.x[p]; st[1] = L.y[p]; st[2] = L.z[p];
-            st[3] = L.vx[p]; st[4] = L.vy[p]; st[5] = L.vz[p];
-            st[6] = L.m[p];
+    const float etah_c = (float)(SP.eta_outside ? SP.eta_in * SP.eta / h0 : SP.eta_in / h0);
+    const bool act = lane < n;
+    const int p = act ? mem[lane] : -1;
+    double st[7] = {0, 0, 0, 0, 0, 0, 0};
+    if (act) {
+        st[0] = V.x[p]; st[1] = V.y[p]; st[2] = V.z[p];
+        st[3] = V.vx[p]; st[4] = V.vy[p]; st[5] = V.vz[p];
+        st[6] = V.m[p];
+    }
+    const uint32_t all = (n >= 32) ? FULL : ((1u << n) - 1u);
+    int k = 0;
+    mk[0] = act ? all : 0u;
+    ph[0] = 0;
+    cf[0] = -1;
+    __syncwarp();
+    S.gid[lane] = act ? V.gid[p] : -1;
+    __syncwarp();
+    bool bad = false;
+    if (depth0 > cn.maxd) cn.maxd = depth0;
+    if (n == 2) {
+        // a two-body component: its whole recursion on the pair path
+        const unsigned e = k8_pair_handoff(S, lane, st, 3u, act, h0, etah_c, depth0, -1, 0, SP, P, Q, mixed, pc,
+                                           nl);
+        if (e) {
+            raise_err(ctr, e);
+            bad = true;
         }
-        const uint32_t all = (n >= 32) ? FULL : ((1u << n) - 1u);
-        int k = 0;
-        mk[0] = act ? all : 0u;
-        ph[0] = 0;
-        cf[0] = -1;
-        __syncwarp();
-        S.gid[lane] = act ? L.gid[p] : -1;
-        __syncwarp();
-        bool bad = false;
-        if (SP.depth0 > maxd) maxd = SP.depth0;
-        if (n == 2) {
-            // a two-body component: its whole recursion on the pair path
-            const unsigned e = k8_pair_handoff(S, lane, st, 3u, act, SP.h0, etah_c, SP.depth0, -1, 0, SP, P, Q, mixed, pc,
-                                               nl);
-            if (e) {
-                raise_err(ctr, e);
-                bad = true;
-            }
-            k = -1;
-        }
-        while (k >= 0 && !bad) {
-            const double h = scale2m(SP.h0, k);
-            const uint32_t mine = mk[k];
-            if (ph[k] == 0) {
-                // ---------------- split at h: tau(i,j) < h inside the lane's set.
-                // A fresh state (the component's start, a second half) takes
-                // every pair's edge depth; a first half reads them, since its
-                // state is the one its parent split.
-                if (cf[k] < 0) {
-                    k8_publish(S, lane, st, mixed);
-                    P.h = h;
-                    const float etah = etah_c * pow2f(k);
-                    const float c11 = 11.f * U32 * U32;
-                    const int levels = K8_MAXD - k;
-                    // FP64 tau of pair (lane, j), in the pair's fixed order
-                    // (symmetric bit for bit)
-                    auto tau64_of = [&](int j) {
-                        const int lo = lane < j ? lane : j, hi = lane < j ? j : lane;
-                        return tau_fp64_ool(__dsub_rn(S.d[0][lo], S.d[0][hi]), __dsub_rn(S.d[1][lo], S.d[1][hi]),
-                                        __dsub_rn(S.d[2][lo], S.d[2][hi]), __dsub_rn(S.d[3][lo], S.d[3][hi]),
-                                        __dsub_rn(S.d[4][lo], S.d[4][hi]), __dsub_rn(S.d[5][lo], S.d[5][hi]),
-                                        S.d[6][lo], S.d[6][hi], P);
-                    };
-                    auto log_of = [&](int j, double tv, double hm) {
-                        if (lane < j) near_log(tv, hm, nl.tol, nl.ctr, S.gid[lane], S.gid[j], nl.ij, nl.tau, nl.cap);
-                    };
-                    // the warp's active lanes at this level: a lane's set is a
-                    // subset, so its pairs are among these (deep levels of a
-                    // big component leave few)
-                    const uint32_t act = __reduce_or_sync(FULL, mine);
-                    if (mine && mixed) {
-                        // the lane's own float-float state in registers (the
-                        // byte stores of the edge depths below may alias any
-                        // shared word, so reads from S would be repeated)
-                        float me_f[13];
+        k = -1;
+    }
+    while (k >= 0 && !bad) {
+        const double h = scale2m(h0, k);
+        const uint32_t mine = mk[k];
+        if (ph[k] == 0) {
+            // ---------------- split at h: tau(i,j) < h inside the lane's set.
+            // A fresh state (the component's start, a second half) takes
+            // every pair's edge depth; a first half reads them, since its
+            // state is the one its parent split.
+            if (cf[k] < 0) {
+                k8_publish(S, lane, st, mixed);
+                P.h = h;
+                const float etah = etah_c * pow2f(k);
+                const float c11 = 11.f * U32 * U32;
+                const int levels = K8_MAXD - k;
+                // FP64 tau of pair (lane, j), in the pair's fixed order
+                // (symmetric bit for bit)
+                auto tau64_of = [&](int j) {
+                    const int lo = lane < j ? lane : j, hi = lane < j ? j : lane;
+                    return tau_fp64_ool(__dsub_rn(S.d[0][lo], S.d[0][hi]), __dsub_rn(S.d[1][lo], S.d[1][hi]),
+                                    __dsub_rn(S.d[2][lo], S.d[2][hi]), __dsub_rn(S.d[3][lo], S.d[3][hi]),
+                                    __dsub_rn(S.d[4][lo], S.d[4][hi]), __dsub_rn(S.d[5][lo], S.d[5][hi]),
+                                    S.d[6][lo], S.d[6][hi], P);
+                };
+                auto log_of = [&](int j, double tv, double hm) {
+                    if (lane < j) near_log(tv, hm, nl.tol, nl.ctr, S.gid[lane], S.gid[j], nl.ij, nl.tau, nl.cap);
+                };
+                // the warp's active lanes at this level: a lane's set is a
+                // subset, so its pairs are among these (deep levels of a
+                // big component leave few)
+                const uint32_t act = __reduce_or_sync(FULL, mine);
+                if (mine && mixed) {
+                    // the lane's own float-float state in registers (the
+                    // byte stores of the edge depths below may alias any
+                    // shared word, so reads from S would be repeated)
+                    float me_f[13];
 #pragma unroll
-                        for (int q = 0; q < 13; ++q) me_f[q] = S.f[q][lane];
-                        const float me_xm = S.xm[lane], me_vm = S.vm[lane];
-                        auto prep = [&](int j) {
-                            return tau_prep_fp32((S.f[0][j] - me_f[0]) + (S.f[6][j] - me_f[6]),
-                                                 (S.f[1][j] - me_f[1]) + (S.f[7][j] - me_f[7]),
-                                                 (S.f[2][j] - me_f[2]) + (S.f[8][j] - me_f[8]),
-                                                 (S.f[3][j] - me_f[3]) + (S.f[9][j] - me_f[9]),
-                                                 (S.f[4][j] - me_f[4]) + (S.f[10][j] - me_f[10]),
-                                                 (S.f[5][j] - me_f[5]) + (S.f[11][j] - me_f[11]),
-                                                 Q.G * (me_f[12] + S.f[12][j]), c11 * fmaxf(me_xm, S.xm[j]),
-                                                 c11 * fmaxf(me_vm, S.vm[j]), Q);
-                        };
-                        auto finish = [&](int j, const TauPrep32 &t) {
-                            if (j == lane || !((mine >> j) & 1u)) return;
-                            int e = 0;
-                            if (tau_decide_at(t, etah) != 0) {
-                                bool used64;
-                                e = edge_depth_mixed(
-                                    t, etah, h, levels, [&]() { return tau64_of(j); },
-                                    [&](double tv, double hm) { log_of(j, tv, hm); }, used64);
-                                if (used64 && lane < j) ++c_fp64;
-                            }
-                            S.e[j][lane] = (unsigned char)e;
-                            if (lane < j) ++c_eval;
-                        };
-                        // two preps in flight, over the active lanes (pairs
-                        // outside the lane's set are computed and dropped)
-                        for (uint32_t rem = act; rem;) {
-                            const int j0 = __ffs(rem) - 1;
-                            rem &= rem - 1u;
-                            const bool two = rem != 0u;
-                            const int j1 = two ? __ffs(rem) - 1 : j0;
-                            if (two) rem &= rem - 1u;
-                            const TauPrep32 t0 = prep(j0), t1 = prep(j1);
-                            finish(j0, t0);
-                            if (two) finish(j1, t1);
+                    for (int q = 0; q < 13; ++q) me_f[q] = S.f[q][lane];
+                    const float me_xm = S.xm[lane], me_vm = S.vm[lane];
+                    auto prep = [&](int j) {
+                        return tau_prep_fp32((S.f[0][j] - me_f[0]) + (S.f[6][j] - me_f[6]),
+                                             (S.f[1][j] - me_f[1]) + (S.f[7][j] - me_f[7]),
+                                             (S.f[2][j] - me_f[2]) + (S.f[8][j] - me_f[8]),
+                                             (S.f[3][j] - me_f[3]) + (S.f[9][j] - me_f[9]),
+                                             (S.f[4][j] - me_f[4]) + (S.f[10][j] - me_f[10]),
+                                             (S.f[5][j] - me_f[5]) + (S.f[11][j] - me_f[11]),
+                                             Q.G * (me_f[12] + S.f[12][j]), c11 * fmaxf(me_xm, S.xm[j]),
+                                             c11 * fmaxf(me_vm, S.vm[j]), Q);
+                    };
+                    auto finish = [&](int j, const TauPrep32 &t) {
+                        if (j == lane || !((mine >> j) & 1u)) return;
+                        int e = 0;
+                        if (tau_decide_at(t, etah) != 0) {
+                            bool used64;
+                            e = edge_depth_mixed(
+                                t, etah, h, levels, [&]() { return tau64_of(j); },
+                                [&](double tv, double hm) { log_of(j, tv, hm); }, used64);
+                            if (used64 && lane < j) ++cn.fp64;
                         }
-                    } else if (mine) {
-                        for (int j = 0; j < n; ++j) {
-                            if (j == lane || !((mine >> j) & 1u)) continue;
-                            const int e = edge_depth_fp64(tau64_of(j), h, levels,
-                                                          [&](double tv, double hm) { log_of(j, tv, hm); });
-                            if (lane < j) ++c_fp64;
-                            S.e[j][lane] = (unsigned char)e;
-                            if (lane < j) ++c_eval;
-                        }
-                    }
-                    cf[k] = (signed char)k;
-                }
-                const int eoff = k - cf[k];
-                uint32_t adj = 0;
-                if (mine) {
-                    for (int j = 0; j < n; ++j)
-                        if (j != lane && ((mine >> j) & 1u) && S.e[j][lane] > eoff) adj |= 1u << j;
-                }
-                // components: closure of the adjacency by mask doubling
-                // (each lane ORs the masks of its own members only: as many
-                // shuffles per round as the largest mask has bits)
-                uint32_t cm = mine ? (adj | me) : 0u;
-                // HOLD split: every member of the set with an edge (tau(i) <
-                // h) is in the one fast set
-                const uint32_t hasedge = __ballot_sync(FULL, mine && adj != 0u);
-                if (SP.hold) cm = mine ? (adj ? (hasedge & mine) : me) : 0u;
-                for (int it = 0; it < 6 && !SP.hold; ++it) {
-                    uint32_t nx = cm, rem = cm;
-                    const unsigned rounds = __reduce_max_sync(FULL, (unsigned)__popc(cm));
-                    for (unsigned t = 0; t < rounds; ++t) {
-                        const int j = rem ? __ffs(rem) - 1 : lane;
+                        S.e[j][lane] = (unsigned char)e;
+                        if (lane < j) ++cn.eval;
+                    };
+                    // two preps in flight, over the active lanes (pairs
+                    // outside the lane's set are computed and dropped)
+                    for (uint32_t rem = act; rem;) {
+                        const int j0 = __ffs(rem) - 1;
                         rem &= rem - 1u;
-                        nx |= __shfl_sync(FULL, cm, j);
+                        const bool two = rem != 0u;
+                        const int j1 = two ? __ffs(rem) - 1 : j0;
+                        if (two) rem &= rem - 1u;
+                        const TauPrep32 t0 = prep(j0), t1 = prep(j1);
+                        finish(j0, t0);
+                        if (two) finish(j1, t1);
                     }
-                    const bool same = __all_sync(FULL, nx == cm);
-                    cm = nx;
-                    if (same) break;
+                } else if (mine) {
+                    for (int j = 0; j < n; ++j) {
+                        if (j == lane || !((mine >> j) & 1u)) continue;
+                        const int e = edge_depth_fp64(tau64_of(j), h, levels,
+                                                      [&](double tv, double hm) { log_of(j, tv, hm); });
+                        if (lane < j) ++cn.fp64;
+                        S.e[j][lane] = (unsigned char)e;
+                        if (lane < j) ++cn.eval;
+                    }
                 }
-                cmk[k] = cm;
-                const int csz = __popc(cm);
-                if (mine && lane == __ffs(mine) - 1) {
-                    const unsigned long long ms = __popc(mine);
-                    ++c_split;
-                    c_tau += ms * (ms - 1) / 2;
+                cf[k] = (signed char)k;
+            }
+            const int eoff = k - cf[k];
+            uint32_t adj = 0;
+            if (mine) {
+                for (int j = 0; j < n; ++j)
+                    if (j != lane && ((mine >> j) & 1u) && S.e[j][lane] > eoff) adj |= 1u << j;
+            }
+            // components: closure of the adjacency by mask doubling
+            // (each lane ORs the masks of its own members only: as many
+            // shuffles per round as the largest mask has bits)
+            uint32_t cm = mine ? (adj | me) : 0u;
+            // HOLD split: every member of the set with an edge (tau(i) <
+            // h) is in the one fast set
+            const uint32_t hasedge = __ballot_sync(FULL, mine && adj != 0u);
+            if (SP.hold) cm = mine ? (adj ? (hasedge & mine) : me) : 0u;
+            for (int it = 0; it < 6 && !SP.hold; ++it) {
+                uint32_t nx = cm, rem = cm;
+                const unsigned rounds = __reduce_max_sync(FULL, (unsigned)__popc(cm));
+                for (unsigned t = 0; t < rounds; ++t) {
+                    const int j = rem ? __ffs(rem) - 1 : lane;
+                    rem &= rem - 1u;
+                    nx |= __shfl_sync(FULL, cm, j);
                 }
-                if (csz >= 2 && lane == __ffs(cm) - 1) {
-                    ++c_comp;
-                    if (SP.kepler && csz == 2) c_kep += 2;
+                const bool same = __all_sync(FULL, nx == cm);
+                cm = nx;
+                if (same) break;
+            }
+            cmk[k] = cm;
+            const int csz = __popc(cm);
+            if (mine && lane == __ffs(mine) - 1) {
+                const unsigned long long ms = __popc(mine);
+                ++cn.split;
+                cn.tau += ms * (ms - 1) / 2;
+            }
+            if (csz >= 2 && lane == __ffs(cm) - 1) {
+                ++cn.comp;
+                if (SP.kepler && csz == 2) cn.kep += 2;
+            }
+            ph[k] = 1;
+            const bool sub = csz >= 2 && !(SP.kepler && csz == 2);
+            // every sub-recursion at this level is a pair: run them on the
+            // pair path (first half now, second half after the DKD)
+            pm[k] = __all_sync(FULL, !sub || csz == 2) ? 1 : 0;
+            if (pm[k] && __any_sync(FULL, sub)) {
+                const unsigned e = k8_pair_handoff(S, lane, st, cm, sub, 0.5 * h, etah_c * pow2f(k + 1),
+                                                   depth0 + k + 1, k + 1 - cf[k], K8_MAXD - cf[k], SP, P, Q,
+                                                   mixed, pc, nl);
+                if (e) {
+                    raise_err(ctr, e);
+                    bad = true;
+                    break;
                 }
-                ph[k] = 1;
-                const bool sub = csz >= 2 && !(SP.kepler && csz == 2);
-                // every sub-recursion at this level is a pair: run them on the
-                // pair path (first half now, second half after the DKD)
-                pm[k] = __all_sync(FULL, !sub || csz == 2) ? 1 : 0;
-                if (pm[k] && __any_sync(FULL, sub)) {
+            } else if (__any_sync(FULL, sub)) {
+                pm[k] = 0;
+                if (depth0 + k + 1 > SP.max_depth || k + 1 >= K8_MAXD) {
+                    bad = true;
+                    raise_err(ctr, DERR_DEPTH);
+                    break;
+                }
+                mk[k + 1] = sub ? cm : 0u;
+                ph[k + 1] = 0;
+                cf[k + 1] = cf[k];  // first half: the state this split saw
+                ++k;
+                if (depth0 + k > cn.maxd) cn.maxd = depth0 + k;
+                continue;
+            }
+        }
+        const uint32_t cm = cmk[k];
+        const int csz = __popc(cm);
+        const bool sub = csz >= 2 && !(SP.kepler && csz == 2);
+        if (ph[k] == 1) {
+            const bool kep = mine && SP.kepler && csz == 2;
+            const bool any_kep = __any_sync(FULL, kep);
+            // the level's DKD has work only where the lane's set holds a
+            // rest-set member or more than one component
+            const bool any_dkd = __any_sync(FULL, mine && (cm != mine || cm == me));
+            for (int half = 0; half < 2; ++half) {
+                if (half == 1 && any_dkd) {
+                    // ------------- D_{h/2,T_R} K_{h,V} D_{h/2,T_R} on the lane's set
+                    const bool single = mine && cm == me;
+                    const double hd = 0.5 * h;
+                    if (single) {
+                        k8_drift(st, hd, !mixed);
+                        cn.drift += 2;
+                    }
+                    const bool fp64_kick = !mixed || h < SP.h_fp64;
+                    k8_publish(S, lane, st, !fp64_kick);
+                    const uint32_t act = __reduce_or_sync(FULL, mine);
+                    if (mine) {
+                        const uint32_t others = mine & ~cm;
+                        cn.kick += __popc(others & ~((me << 1) - 1u));
+                        if (fp64_kick) {
+                            const K8Acc a = k8_kick64(S, n, others, st[0], st[1], st[2], SP.G, SP.eps2);
+                            st[3] = __dadd_rn(st[3], __dmul_rn(h, a.x));
+                            st[4] = __dadd_rn(st[4], __dmul_rn(h, a.y));
+                            st[5] = __dadd_rn(st[5], __dmul_rn(h, a.z));
+                        } else {
+                            // FP32 pair forces from float-float differences
+                            const float xh = S.f[0][lane], yh = S.f[1][lane], zh = S.f[2][lane];
+                            const float xl = S.f[6][lane], yl = S.f[7][lane], zl = S.f[8][lane];
+                            // two compensated accumulators: two independent
+                            // dependency chains for one warp that runs alone on
+                            // its scheduler; j outside the lane's others add an
+                            // exact 0
+                            float sx0 = 0.f, sy0 = 0.f, sz0 = 0.f, cx0 = 0.f, cy0 = 0.f, cz0 = 0.f;
+                            float sx1 = 0.f, sy1 = 0.f, sz1 = 0.f, cx1 = 0.f, cy1 = 0.f, cz1 = 0.f;
+                            const float e2 = (float)SP.eps2;
+                            auto term = [&](int j, float &sx, float &sy, float &sz, float &cx, float &cy,
+                                            float &cz) {
+                                const float dx = (S.f[0][j] - xh) + (S.f[6][j] - xl);
+                                const float dy = (S.f[1][j] - yh) + (S.f[7][j] - yl);
+                                const float dz = (S.f[2][j] - zh) + (S.f[8][j] - zl);
+                                const float r2 = fmaf(dz, dz, fmaf(dy, dy, fmaf(dx, dx, e2)));
+                                float ri = rsqrtf(r2);
+                                ri = ri * fmaf(-0.5f * r2, ri * ri, 1.5f);
+                                const float ww = ((others >> j) & 1u) ? S.f[12][j] * (ri * ri * ri) : 0.f;
+                                kahan_add(sx, cx, ww * dx);
+                                kahan_add(sy, cy, ww * dy);
+                                kahan_add(sz, cz, ww * dz);
+                            };
+                            // over the warp's active lanes, two terms per round
+                            for (uint32_t rem = act; rem;) {
+                                const int j0 = __ffs(rem) - 1;
+                                rem &= rem - 1u;
+                                term(j0, sx0, sy0, sz0, cx0, cy0, cz0);
+                                if (rem) {
+                                    term(__ffs(rem) - 1, sx1, sy1, sz1, cx1, cy1, cz1);
+                                    rem &= rem - 1u;
+                                }
+                            }
+                            const double gh = SP.G * h;
+                            st[3] = fma(gh, (f2d(sx0) - f2d(cx0)) + (f2d(sx1) - f2d(cx1)), st[3]);
+                            st[4] = fma(gh, (f2d(sy0) - f2d(cy0)) + (f2d(sy1) - f2d(cy1)), st[4]);
+                            st[5] = fma(gh, (f2d(sz0) - f2d(cz0)) + (f2d(sz1) - f2d(cz1)), st[5]);
+                        }
+                    }
+                    if (single) k8_drift(st, hd, !mixed);
+                }
+                if (!any_kep) continue;
+                // two-body components: the Kepler flow over h/2
+                k8_publish(S, lane, st, false);
+                if (kep) {
+                    const int other = __ffs(cm & ~me) - 1;
+                    const int a = lane < other ? lane : other, b = lane < other ? other : lane;
+                    double xa[3] = {S.d[0][a], S.d[1][a], S.d[2][a]}, xb[3] = {S.d[0][b], S.d[1][b], S.d[2][b]};
+                    double va[3] = {S.d[3][a], S.d[4][a], S.d[5][a]}, vb[3] = {S.d[3][b], S.d[4][b], S.d[5][b]};
+                    if (!k8_kepler(S.d[6][a], S.d[6][b], xa, xb, va, vb, SP.G, 0.5 * h)) {
+                        raise_err(ctr, DERR_KEPLER);
+                    } else if (lane == a) {
+                        st[0] = xa[0]; st[1] = xa[1]; st[2] = xa[2]; st[3] = va[0]; st[4] = va[1]; st[5] = va[2];
+                    } else {
+                        st[0] = xb[0]; st[1] = xb[1]; st[2] = xb[2]; st[3] = vb[0]; st[4] = vb[1]; st[5] = vb[2];
+                    }
+                }
+            }
+            ph[k] = 2;
+            if (__any_sync(FULL, sub)) {
+                if (pm[k]) {
                     const unsigned e = k8_pair_handoff(S, lane, st, cm, sub, 0.5 * h, etah_c * pow2f(k + 1),
-                                                       SP.depth0 + k + 1, k + 1 - cf[k], K8_MAXD - cf[k], SP, P, Q,
-                                                       mixed, pc, nl);
+                                                       depth0 + k + 1, -1, 0, SP, P, Q, mixed, pc, nl);
                     if (e) {
                         raise_err(ctr, e);
                         bad = true;
                         break;
                     }
-                } else if (__any_sync(FULL, sub)) {
-                    pm[k] = 0;
-                    if (SP.depth0 + k + 1 > SP.max_depth || k + 1 >= K8_MAXD) {
-                        bad = true;
-                        raise_err(ctr, DERR_DEPTH);
-                        break;
-                    }
+                } else {
                     mk[k + 1] = sub ? cm : 0u;
                     ph[k + 1] = 0;
-                    cf[k + 1] = cf[k];  // first half: the state this split saw
+                    cf[k + 1] = -1;  // second half: the DKD moved the state
                     ++k;
-                    if (SP.depth0 + k > maxd) maxd = SP.depth0 + k;
                     continue;
                 }
             }
-            const uint32_t cm = cmk[k];
-            const int csz = __popc(cm);
-            const bool sub = csz >= 2 && !(SP.kepler && csz == 2);
-            if (ph[k] == 1) {
-                const bool kep = mine && SP.kepler && csz == 2;
-                const bool any_kep = __any_sync(FULL, kep);
-                // the level's DKD has work only where the lane's set holds a
-                // rest-set member or more than one component
-                const bool any_dkd = __any_sync(FULL, mine && (cm != mine || cm == me));
-                for (int half = 0; half < 2; ++half) {
-                    if (half == 1 && any_dkd) {
-                        // ------------- D_{h/2,T_R} K_{h,V} D_{h/2,T_R} on the lane's set
-                        const bool single = mine && cm == me;
-                        const double hd = 0.5 * h;
-                        if (single) {
-                            k8_drift(st, hd, !mixed);
-                            c_drift += 2;
-                        }
-                        const bool fp64_kick = !mixed || h < SP.h_fp64;
-                        k8_publish(S, lane, st, !fp64_kick);
-                        const uint32_t act = __reduce_or_sync(FULL, mine);
-                        if (mine) {
-                            const uint32_t others = mine & ~cm;
-                            c_kick += __popc(others & ~((me << 1) - 1u));
-                            if (fp64_kick) {
-                                const K8Acc a = k8_kick64(S, n, others, st[0], st[1], st[2], SP.G, SP.eps2);
-                                st[3] = __dadd_rn(st[3], __dmul_rn(h, a.x));
-                                st[4] = __dadd_rn(st[4], __dmul_rn(h, a.y));
-                                st[5] = __dadd_rn(st[5], __dmul_rn(h, a.z));
-                            } else {
-                                // FP32 pair forces from float-float differences
-                                const float xh = S.f[0][lane], yh = S.f[1][lane], zh = S.f[2][lane];
-                                const float xl = S.f[6][lane], yl = S.f[7][lane], zl = S.f[8][lane];
-                                // two compensated accumulators: two independent
-                                // dependency chains for one warp that runs alone on
-                                // its scheduler; j outside the lane's others add an
-                                // exact 0
-                                float sx0 = 0.f, sy0 = 0.f, sz0 = 0.f, cx0 = 0.f, cy0 = 0.f, cz0 = 0.f;
-                                float sx1 = 0.f, sy1 = 0.f, sz1 = 0.f, cx1 = 0.f, cy1 = 0.f, cz1 = 0.f;
-                                const float e2 = (float)SP.eps2;
-                                auto term = [&](int j, float &sx, float &sy, float &sz, float &cx, float &cy,
-                                                float &cz) {
-                                    const float dx = (S.f[0][j] - xh) + (S.f[6][j] - xl);
-                                    const float dy = (S.f[1][j] - yh) + (S.f[7][j] - yl);
-                                    const float dz = (S.f[2][j] - zh) + (S.f[8][j] - zl);
-                                    const float r2 = fmaf(dz, dz, fmaf(dy, dy, fmaf(dx, dx, e2)));
-                                    float ri = rsqrtf(r2);
-                                    ri = ri * fmaf(-0.5f * r2, ri * ri, 1.5f);
-                                    const float ww = ((others >> j) & 1u) ? S.f[12][j] * (ri * ri * ri) : 0.f;
-                                    kahan_add(sx, cx, ww * dx);
-                                    kahan_add(sy, cy, ww * dy);
-                                    kahan_add(sz, cz, ww * dz);
-                                };
-                                // over the warp's active lanes, two terms per round
-                                for (uint32_t rem = act; rem;) {
-                                    const int j0 = __ffs(rem) - 1;
-                                    rem &= rem - 1u;
-                                    term(j0, sx0, sy0, sz0, cx0, cy0, cz0);
-                                    if (rem) {
-                                        term(__ffs(rem) - 1, sx1, sy1, sz1, cx1, cy1, cz1);
-                                        rem &= rem - 1u;
-                                    }
-                                }
-                                const double gh = SP.G * h;
-                                st[3] = fma(gh, (f2d(sx0) - f2d(cx0)) + (f2d(sx1) - f2d(cx1)), st[3]);
-                                st[4] = fma(gh, (f2d(sy0) - f2d(cy0)) + (f2d(sy1) - f2d(cy1)), st[4]);
-                                st[5] = fma(gh, (f2d(sz0) - f2d(cz0)) + (f2d(sz1) - f2d(cz1)), st[5]);
-                            }
-                        }
-                        if (single) k8_drift(st, hd, !mixed);
-                    }
-                    if (!any_kep) continue;
-                    // two-body components: the Kepler flow over h/2
-                    k8_publish(S, lane, st, false);
-                    if (kep) {
-                        const int other = __ffs(cm & ~me) - 1;
-                        const int a = lane < other ? lane : other, b = lane < other ? other : lane;
-                        double xa[3] = {S.d[0][a], S.d[1][a], S.d[2][a]}, xb[3] = {S.d[0][b], S.d[1][b], S.d[2][b]};
-                        double va[3] = {S.d[3][a], S.d[4][a], S.d[5][a]}, vb[3] = {S.d[3][b], S.d[4][b], S.d[5][b]};
-                        if (!k8_kepler(S.d[6][a], S.d[6][b], xa, xb, va, vb, SP.G, 0.5 * h)) {
-                            raise_err(ctr, DERR_KEPLER);
-                        } else if (lane == a) {
-                            st[0] = xa[0]; st[1] = xa[1]; st[2] = xa[2]; st[3] = va[0]; st[4] = va[1]; st[5] = va[2];
-                        } else {
-                            st[0] = xb[0]; st[1] = xb[1]; st[2] = xb[2]; st[3] = vb[0]; st[4] = vb[1]; st[5] = vb[2];
-                        }
-                    }
-                }
-                ph[k] = 2;
-                if (__any_sync(FULL, sub)) {
-                    if (pm[k]) {
-                        const unsigned e = k8_pair_handoff(S, lane, st, cm, sub, 0.5 * h, etah_c * pow2f(k + 1),
-                                                           SP.depth0 + k + 1, -1, 0, SP, P, Q, mixed, pc, nl);
-                        if (e) {
-                            raise_err(ctr, e);
-                            bad = true;
-                            break;
-                        }
-                    } else {
-                        mk[k + 1] = sub ? cm : 0u;
-                        ph[k + 1] = 0;
-                        cf[k + 1] = -1;  // second half: the DKD moved the state
-                        ++k;
-                        continue;
-                    }
-                }
-            }
-            --k;
         }
-        if (act) {
-            L.x[p] = st[0]; L.y[p] = st[1]; L.z[p] = st[2];
-            L.vx[p] = st[3]; L.vy[p] = st[4]; L.vz[p] = st[5];
-        }
-        __syncwarp();
+        --k;
     }
-    // per-lane counters (lockstep levels + pair paths) -> one atomic per warp
-    if (pc.maxd > maxd) maxd = pc.maxd;
-    unsigned long long v[8] = {c_tau + pc.tau, c_kick + pc.kick, c_drift + pc.drift, c_split + pc.split,
-                               c_comp + pc.comp, c_kep, c_fp64 + pc.fp64, c_eval + pc.evals};
+    if (act) {
+        V.x[p] = st[0]; V.y[p] = st[1]; V.z[p] = st[2];
+        V.vx[p] = st[3]; V.vy[p] = st[4]; V.vz[p] = st[5];
+    }
+    __syncwarp();
+}
+
+// per-lane counters (lockstep levels + pair paths) -> one atomic per warp
+__device__ __forceinline__ void flush_counters(const SmallCnt &cn, const PairCounters &pc, DevCounters *ctr)
+{
+    const int lane = threadIdx.x & 31;
+    int maxd = max(cn.maxd, pc.maxd);
+    unsigned long long v[8] = {cn.tau + pc.tau, cn.kick + pc.kick, cn.drift + pc.drift, cn.split + pc.split,
+                               cn.comp + pc.comp, cn.kep, cn.fp64 + pc.fp64, cn.eval + pc.evals};
 #pragma unroll
     for (int i = 0; i < 8; ++i)
         for (int o = 16; o > 0; o >>= 1) v[i] += __shfl_down_sync(FULL, v[i], o);
@@ -753,6 +759,676 @@ __global__ void __launch_bounds__(K8_WARPS * 32) k_small(Level L, const int32_t 
         }
         atomicMax(&ctr->max_depth_seen, maxd);
     }
+}
+
+__global__ void __launch_bounds__(K8_WARPS * 32) k_small(Level L, const int32_t *members, const int32_t *comp_start,
+                                                          const int32_t *comp_size, const int32_t *slist,
+                                                          const int32_t *ns_ptr,
+                                                          SmallParams SP, DevCounters *ctr, int *queue,
+                                                          int32_t *near_ij, double *near_tau, long long near_cap)
+{
+    __shared__ K8Warp sw[K8_WARPS];
+    const int ns = *ns_ptr;
+    const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const SView V{L.x, L.y, L.z, L.vx, L.vy, L.vz, L.m, L.gid};
+    const NearLog nl = {ctr, near_ij, near_tau, near_cap, SP.near_tol};
+    SmallCnt cn;
+    PairCounters pc;
+    for (;;) {
+        int q = 0;
+        if (lane == 0) q = atomicAdd(queue, 1);
+        q = __shfl_sync(FULL, q, 0);
+        if (q >= ns) break;
+        const int c = slist[q];
+        small_task(sw[w], V, members + comp_start[c], comp_size[c], SP.h0, SP.depth0, SP, ctr, nl, cn, pc);
+    }
+    flush_counters(cn, pc, ctr);
+}
+
+// ------------------------------------------------------------ batched tasks
+// k_batch takes evolve_cc tasks of up to BATCH_NMAX bodies from one queue,
+// largest first.  A task of more than 32 bodies is run by the whole CTA
+// (medium_task): the set's split, DKD and sub-recursions on-chip, its
+// components of at most 32 bodies handed to the CTA's warps (small_task),
+// larger ones to nested frames of the same CTA.  When the queue reaches the
+// tasks of at most 32 bodies the CTA's warps take them one each, as k_small.
+//
+// A frame holds one set of more than 32 bodies (ascending particle id, in
+// `sl`).  Its split: tau(i,j) < h over the set's pairs (the FP64 predicate,
+// or the certified FP32 decision with the FP64 predicate where it cannot
+// decide), union-find over set positions in shared memory (root = the
+// smallest position, so labels are the smallest particle id), then the
+// members by component into `cl` (components in root order, ascending
+// inside): every component is a contiguous, ascending member list, which is
+// what a nested frame or a warp task reads.  The DKD runs in set order, the
+// kick's sum over j ascending: the FP64 form adds the same terms in the same
+// order as the level kernels and the oracle.
+constexpr int KM_T = K8_WARPS * 32;
+constexpr int KM_MAXF = 32;  // nested sets of more than 32 bodies in one task (DERR_DEPTH beyond)
+constexpr size_t KM_FRAME_BYTES = (size_t)BATCH_NMAX * 8;  // cl (int32) + lab (int16) + comp (int16 pairs)
+static_assert(BATCH_NMAX % (2 * KM_T) == 0, "zig-zag rows");
+
+enum : int { KM_SPLIT = 0, KM_H1 = 1, KM_B1 = 2, KM_DKD = 3, KM_H2 = 4, KM_B2 = 5, KM_DONE = 6 };
+
+struct KMFrame {
+    const int32_t *sl;  // the set's packed indices, ascending particle id
+    int32_t *cl;        // the same, by component (root order), ascending inside
+    int16_t *lab;       // by set position: the root's position (components of >= 2), else -1 - position
+    int16_t *comp;      // (start in cl, size) of the components of >= 2 bodies, root order
+    double h;
+    int n, depth, ph, ncomp, it;
+    unsigned long long kick;  // cross-component pairs of the set
+    int nsingle;
+};
+
+struct KMStage {
+    union {
+        double d[7][BATCH_NMAX];  // FP64: x y z vx vy vz m
+        struct {
+            float f[13][BATCH_NMAX];  // mixed: hi/lo of x y z vx vy vz, fl32(m)
+            float xm[BATCH_NMAX], vm[BATCH_NMAX];
+        } s;
+    };
+    int par[BATCH_NMAX];  // union-find forest over set positions, then roots
+    int cnt[BATCH_NMAX];  // component size by root
+    int cst[BATCH_NMAX];  // HOLD edge flags, then component start in cl by root
+    int run[BATCH_NMAX];  // members placed so far by root
+};
+
+// the slot flags, then the slots (256-byte aligned)
+__host__ __device__ constexpr size_t batch_pool_offset(int nslots) { return ((size_t)nslots * 4 + 255) / 256 * 256; }
+
+struct KMShared {
+    union {
+        K8Warp sw[K8_WARPS];  // warp tasks
+        KMStage st;           // a frame's split or DKD
+    } u;
+    KMFrame fr[KM_MAXF];
+    int wsum[2][K8_WARPS];
+    int top, bad, qi, hmin, q;
+};
+
+// exclusive prefix sums of two per-entry values over entries 0..n-1 (n <=
+// BATCH_NMAX, entry e = 4 tid + k); totals returned
+__device__ __forceinline__ void km_scan2(KMShared &sh, const int a[4], const int b[4], int ea[4], int eb[4],
+                                         int &ta, int &tb)
+{
+    const int tid = threadIdx.x, lane = tid & 31, w = tid >> 5;
+    int sa = 0, sb = 0;
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
+        ea[k] = sa;
+        eb[k] = sb;
+        sa += a[k];
+        sb += b[k];
+    }
+    int ia = sa, ib = sb;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const int xa = __shfl_up_sync(FULL, ia, o), xb = __shfl_up_sync(FULL, ib, o);
+        if (lane >= o) {
+            ia += xa;
+            ib += xb;
+        }
+    }
+    if (lane == 31) {
+        sh.wsum[0][w] = ia;
+        sh.wsum[1][w] = ib;
+    }
+    __syncthreads();
+    int oa = 0, ob = 0;
+    ta = 0;
+    tb = 0;
+#pragma unroll
+    for (int q = 0; q < K8_WARPS; ++q) {
+        if (q < w) {
+            oa += sh.wsum[0][q];
+            ob += sh.wsum[1][q];
+        }
+        ta += sh.wsum[0][q];
+        tb += sh.wsum[1][q];
+    }
+    oa += ia - sa;
+    ob += ib - sb;
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
+        ea[k] += oa;
+        eb[k] += ob;
+    }
+    __syncthreads();  // wsum is free again
+}
+
+// the split of the frame's set at F.h (see above); fills cl, lab, comp and
+// the frame's counts
+__device__ void km_split(KMShared &sh, KMFrame &F, const SView V, const SmallParams &SP, float etah, DevCounters *ctr,
+                         const NearLog &nl, SmallCnt &cn)
+{
+    KMStage &T = sh.u.st;
+    const int tid = threadIdx.x, lane = tid & 31;
+    const int n = F.n;
+    const double h = F.h;
+    const bool mixed = SP.precision == CC_PREC_MIXED;
+    for (int p = tid; p < n; p += KM_T) {
+        const int k = F.sl[p];
+        const double st[7] = {V.x[k], V.y[k], V.z[k], V.vx[k], V.vy[k], V.vz[k], V.m[k]};
+        if (mixed) {
+#pragma unroll
+            for (int c = 0; c < 6; ++c) {
+                float hi, lo;
+                ff_split(st[c], hi, lo);
+                T.s.f[c][p] = hi;
+                T.s.f[6 + c][p] = lo;
+            }
+            T.s.f[12][p] = fl32(st[6]);
+            T.s.xm[p] = fmaxf(fabsf(T.s.f[0][p]), fmaxf(fabsf(T.s.f[1][p]), fabsf(T.s.f[2][p])));
+            T.s.vm[p] = fmaxf(fabsf(T.s.f[3][p]), fmaxf(fabsf(T.s.f[4][p]), fabsf(T.s.f[5][p])));
+        } else {
+#pragma unroll
+            for (int c = 0; c < 7; ++c) T.d[c][p] = st[c];
+        }
+        T.par[p] = p;
+        T.cnt[p] = 0;
+        T.cst[p] = 0;
+        T.run[p] = 0;
+    }
+    if (tid == 0) sh.hmin = BATCH_NMAX;
+    __syncthreads();
+    TauParams P;
+    P.G = SP.G; P.eps2 = SP.eps2; P.eta = SP.eta; P.eta_in = SP.eta_in; P.eta_outside = SP.eta_outside;
+    P.near_tol = SP.near_tol;
+    P.fault_test = 0;
+    P.h = h;
+    MixedTauParams Q;
+    Q.eta = (float)SP.eta_in; Q.eps2 = (float)SP.eps2; Q.G = (float)SP.G;
+    Q.hq = 0.f;
+    const float c11 = 11.f * U32 * U32;
+    // the FP64 tau of positions lo < hi, in that order (the other kernels'
+    // pair order; symmetric bit for bit)
+    auto tau64 = [&](int lo, int hi) {
+        if (mixed) {
+            const int a = F.sl[lo], b = F.sl[hi];
+            return tau_fp64_ool(__dsub_rn(V.x[a], V.x[b]), __dsub_rn(V.y[a], V.y[b]), __dsub_rn(V.z[a], V.z[b]),
+                                __dsub_rn(V.vx[a], V.vx[b]), __dsub_rn(V.vy[a], V.vy[b]),
+                                __dsub_rn(V.vz[a], V.vz[b]), V.m[a], V.m[b], P);
+        }
+        return tau_fp64_ool(__dsub_rn(T.d[0][lo], T.d[0][hi]), __dsub_rn(T.d[1][lo], T.d[1][hi]),
+                            __dsub_rn(T.d[2][lo], T.d[2][hi]), __dsub_rn(T.d[3][lo], T.d[3][hi]),
+                            __dsub_rn(T.d[4][lo], T.d[4][hi]), __dsub_rn(T.d[5][lo], T.d[5][hi]), T.d[6][lo],
+                            T.d[6][hi], P);
+    };
+    bool uf_ok = true;
+    // rows p of the pair triangle, zig-zag over the threads (balanced)
+    for (int base = 0; base < n; base += 2 * KM_T) {
+        for (int side = 0; side < 2; ++side) {
+            const int p = side == 0 ? base + tid : base + 2 * KM_T - 1 - tid;
+            if (p >= n - 1) continue;
+            float me_f[13], me_xm = 0.f, me_vm = 0.f;
+            if (mixed) {
+#pragma unroll
+                for (int q = 0; q < 13; ++q) me_f[q] = T.s.f[q][p];
+                me_xm = T.s.xm[p];
+                me_vm = T.s.vm[p];
+            }
+            for (int j = p + 1; j < n; ++j) {
+                bool edge;
+                if (mixed) {
+                    const TauPrep32 t = tau_prep_fp32(
+                        (T.s.f[0][j] - me_f[0]) + (T.s.f[6][j] - me_f[6]),
+                        (T.s.f[1][j] - me_f[1]) + (T.s.f[7][j] - me_f[7]),
+                        (T.s.f[2][j] - me_f[2]) + (T.s.f[8][j] - me_f[8]),
+                        (T.s.f[3][j] - me_f[3]) + (T.s.f[9][j] - me_f[9]),
+                        (T.s.f[4][j] - me_f[4]) + (T.s.f[10][j] - me_f[10]),
+                        (T.s.f[5][j] - me_f[5]) + (T.s.f[11][j] - me_f[11]), Q.G * (me_f[12] + T.s.f[12][j]),
+                        c11 * fmaxf(me_xm, T.s.xm[j]), c11 * fmaxf(me_vm, T.s.vm[j]), Q);
+                    const int dec = tau_decide_at(t, etah);
+                    if (dec >= 0) {
+                        edge = dec > 0;
+                    } else {
+                        const double tau = tau64(p, j);
+                        ++cn.fp64;
+                        edge = tau < h;
+                        near_log(tau, h, nl.tol, nl.ctr, V.gid[F.sl[p]], V.gid[F.sl[j]], nl.ij, nl.tau, nl.cap);
+                    }
+                } else {
+                    const double tau = tau64(p, j);
+                    ++cn.fp64;
+                    edge = tau < h;
+                    near_log(tau, h, nl.tol, nl.ctr, V.gid[F.sl[p]], V.gid[F.sl[j]], nl.ij, nl.tau, nl.cap);
+                }
+                ++cn.eval;
+                if (edge) {
+                    if (SP.hold) {
+                        T.cst[p] = 1;
+                        T.cst[j] = 1;
+                    } else if (!uf_union(T.par, p, j)) {
+                        uf_ok = false;
+                    }
+                }
+            }
+        }
+    }
+    if (!uf_ok) {
+        raise_err(ctr, DERR_UF_RETRY);
+        sh.bad = 1;
+    }
+    __syncthreads();
+    // roots (HOLD: every member with an edge joins the smallest such member)
+    if (SP.hold) {
+        for (int p = tid; p < n; p += KM_T)
+            if (T.cst[p]) atomicMin(&sh.hmin, p);
+        __syncthreads();
+        for (int p = tid; p < n; p += KM_T) T.run[p] = T.cst[p] ? sh.hmin : p;
+    } else {
+        for (int p = tid; p < n; p += KM_T) T.run[p] = uf_find(T.par, p);
+    }
+    __syncthreads();
+    for (int p = tid; p < n; p += KM_T) {
+        T.par[p] = T.run[p];
+        T.run[p] = 0;
+        atomicAdd(&T.cnt[T.par[p]], 1);
+    }
+    __syncthreads();
+    // component starts (sizes by root, in root order) and the table of
+    // components of >= 2 bodies
+    int a[4], b[4], ea[4], eb[4], ta, tb;
+    unsigned long long inner = 0;
+    int nkep = 0;
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
+        const int r = 4 * tid + k;
+        const bool root = r < n && T.par[r] == r;
+        a[k] = root ? T.cnt[r] : 0;
+        b[k] = root && T.cnt[r] >= 2 ? 1 : 0;
+        if (b[k]) {
+            inner += (unsigned long long)T.cnt[r] * (T.cnt[r] - 1) / 2;
+            if (SP.kepler && T.cnt[r] == 2) ++nkep;
+        }
+    }
+    km_scan2(sh, a, b, ea, eb, ta, tb);
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
+        const int r = 4 * tid + k;
+        if (r < n && T.par[r] == r) {
+            T.cst[r] = ea[k];
+            if (b[k]) {
+                F.comp[2 * eb[k]] = (int16_t)ea[k];
+                F.comp[2 * eb[k] + 1] = (int16_t)T.cnt[r];
+            }
+        }
+    }
+    // (inner, nkep, singles) summed over the CTA
+    int single = 0;
+    for (int p = tid; p < n; p += KM_T) single += T.cnt[T.par[p]] == 1 ? 1 : 0;
+    for (int o = 16; o > 0; o >>= 1) {
+        inner += __shfl_down_sync(FULL, inner, o);
+        nkep += __shfl_down_sync(FULL, nkep, o);
+        single += __shfl_down_sync(FULL, single, o);
+    }
+    __shared__ unsigned long long s_inner[K8_WARPS];
+    __shared__ int s_kep[K8_WARPS], s_single[K8_WARPS];
+    if (lane == 0) {
+        s_inner[tid >> 5] = inner;
+        s_kep[tid >> 5] = nkep;
+        s_single[tid >> 5] = single;
+    }
+    __syncthreads();
+    // members by component: one warp, 32 positions a round (peers of one
+    // root ranked by lane, so each component stays ascending)
+    if (tid < 32) {
+        const unsigned lt = (1u << lane) - 1u;
+        for (int c0 = 0; c0 < n; c0 += 32) {
+            const int p = c0 + lane;
+            const bool v = p < n;
+            const int r = v ? T.par[p] : -1 - lane;
+            const unsigned peers = __match_any_sync(FULL, r);
+            if (v) {
+                const int pos = T.cst[r] + T.run[r] + __popc(peers & lt);
+                F.cl[pos] = F.sl[p];
+                F.lab[p] = (int16_t)(T.cnt[r] >= 2 ? r : -1 - p);
+            }
+            __syncwarp();
+            if (v && lane == 31 - __clz(peers)) T.run[r] += __popc(peers);
+            __syncwarp();
+        }
+    }
+    if (tid == 0) {
+        unsigned long long in = 0;
+        int kp = 0, sg = 0;
+        for (int q = 0; q < K8_WARPS; ++q) {
+            in += s_inner[q];
+            kp += s_kep[q];
+            sg += s_single[q];
+        }
+        const unsigned long long pairs = (unsigned long long)n * (n - 1) / 2;
+        F.ncomp = tb;
+        F.kick = pairs - in;
+        F.nsingle = sg;
+        ++cn.split;
+        cn.tau += pairs;
+        cn.comp += tb;
+        cn.kep += 2ull * kp;
+    }
+    __syncthreads();
+}
+
+// D_{h/2,T_R} K_{h,V} D_{h/2,T_R} on the frame's set: rest-set members drift,
+// every cross-component pair kicks (sum over j ascending)
+__device__ void km_dkd(KMShared &sh, const KMFrame &F, const SView V, const SmallParams &SP, SmallCnt &cn)
+{
+    KMStage &T = sh.u.st;
+    const int tid = threadIdx.x;
+    const int n = F.n;
+    const double h = F.h, hd = 0.5 * h;
+    const bool mixed = SP.precision == CC_PREC_MIXED;
+    const bool fp64_kick = !mixed || h < SP.h_fp64;
+    for (int p = tid; p < n; p += KM_T) {
+        const int k = F.sl[p];
+        double st[7] = {V.x[k], V.y[k], V.z[k], V.vx[k], V.vy[k], V.vz[k], V.m[k]};
+        T.par[p] = F.lab[p];  // labels in shared memory for the pair loops
+        if (F.lab[p] < 0) {
+            k8_drift(st, hd, !mixed);
+            V.x[k] = st[0];
+            V.y[k] = st[1];
+            V.z[k] = st[2];
+        }
+        if (fp64_kick) {
+#pragma unroll
+            for (int c = 0; c < 3; ++c) T.d[c][p] = st[c];
+            T.d[6][p] = st[6];
+        } else {
+#pragma unroll
+            for (int c = 0; c < 3; ++c) {
+                float hi, lo;
+                ff_split(st[c], hi, lo);
+                T.s.f[c][p] = hi;
+                T.s.f[6 + c][p] = lo;
+            }
+            T.s.f[12][p] = fl32(st[6]);
+        }
+    }
+    __syncthreads();
+    for (int p = tid; p < n; p += KM_T) {
+        const int k = F.sl[p];
+        const int li = T.par[p];
+        double st[7] = {V.x[k], V.y[k], V.z[k], V.vx[k], V.vy[k], V.vz[k], V.m[k]};
+        if (fp64_kick) {
+            double ax = 0.0, ay = 0.0, az = 0.0;
+            const double xi = T.d[0][p], yi = T.d[1][p], zi = T.d[2][p];
+            for (int j = 0; j < n; ++j) {
+                if (j == p || T.par[j] == li) continue;
+                const double dx0 = __dsub_rn(T.d[0][j], xi);
+                const double dx1 = __dsub_rn(T.d[1][j], yi);
+                const double dx2 = __dsub_rn(T.d[2][j], zi);
+                const double r2 = __dadd_rn(__dadd_rn(__dadd_rn(__dmul_rn(dx0, dx0), __dmul_rn(dx1, dx1)),
+                                                      __dmul_rn(dx2, dx2)), SP.eps2);
+                const double rinv3 = __ddiv_rn(1.0, __dmul_rn(r2, __dsqrt_rn(r2)));
+                const double ww = __dmul_rn(__dmul_rn(SP.G, T.d[6][j]), rinv3);
+                ax = __dadd_rn(ax, __dmul_rn(ww, dx0));
+                ay = __dadd_rn(ay, __dmul_rn(ww, dx1));
+                az = __dadd_rn(az, __dmul_rn(ww, dx2));
+            }
+            st[3] = __dadd_rn(st[3], __dmul_rn(h, ax));
+            st[4] = __dadd_rn(st[4], __dmul_rn(h, ay));
+            st[5] = __dadd_rn(st[5], __dmul_rn(h, az));
+        } else {
+            const float xh = T.s.f[0][p], yh = T.s.f[1][p], zh = T.s.f[2][p];
+            const float xl = T.s.f[6][p], yl = T.s.f[7][p], zl = T.s.f[8][p];
+            const float e2 = (float)SP.eps2;
+            float sx = 0.f, sy = 0.f, sz = 0.f, cx = 0.f, cy = 0.f, cz = 0.f;
+            for (int j = 0; j < n; ++j) {
+                const float dx = (T.s.f[0][j] - xh) + (T.s.f[6][j] - xl);
+                const float dy = (T.s.f[1][j] - yh) + (T.s.f[7][j] - yl);
+                const float dz = (T.s.f[2][j] - zh) + (T.s.f[8][j] - zl);
+                const float r2 = fmaf(dz, dz, fmaf(dy, dy, fmaf(dx, dx, e2)));
+                float ri = rsqrtf(r2);
+                ri = ri * fmaf(-0.5f * r2, ri * ri, 1.5f);
+                const float ww = (j != p && T.par[j] != li) ? T.s.f[12][j] * (ri * ri * ri) : 0.f;
+                kahan_add(sx, cx, ww * dx);
+                kahan_add(sy, cy, ww * dy);
+                kahan_add(sz, cz, ww * dz);
+            }
+            const double gh = SP.G * h;
+            st[3] = fma(gh, f2d(sx) - f2d(cx), st[3]);
+            st[4] = fma(gh, f2d(sy) - f2d(cy), st[4]);
+            st[5] = fma(gh, f2d(sz) - f2d(cz), st[5]);
+        }
+        if (li < 0) k8_drift(st, hd, !mixed);
+        V.x[k] = st[0];
+        V.y[k] = st[1];
+        V.z[k] = st[2];
+        V.vx[k] = st[3];
+        V.vy[k] = st[4];
+        V.vz[k] = st[5];
+    }
+    if (tid == 0) {
+        cn.kick += F.kick;
+        cn.drift += 2ull * F.nsingle;
+    }
+    __syncthreads();
+}
+
+// evolve_cc(C, h0) of one task of 33..BATCH_NMAX bodies (packed indices
+// mem[0..n0), ascending particle id) by the whole CTA, its first split at
+// depth depth0; frame scratch at fs (KM_MAXF frames)
+__device__ void medium_task(KMShared &sh, const SView V, const int32_t *mem, int n0, double h0, int depth0,
+                            const SmallParams &SP, DevCounters *ctr, const NearLog &nl, SmallCnt &cn,
+                            PairCounters &pc, char *fs)
+{
+    const int tid = threadIdx.x, lane = tid & 31, w = tid >> 5;
+    const float etah0 = (float)(SP.eta_outside ? SP.eta_in * SP.eta / h0 : SP.eta_in / h0);
+    auto frame_at = [&](int k, const int32_t *sl, int n, double h, int depth) {
+        KMFrame &F = sh.fr[k];
+        char *b = fs + (size_t)k * KM_FRAME_BYTES;
+        F.sl = sl;
+        F.cl = (int32_t *)b;
+        F.lab = (int16_t *)(b + (size_t)BATCH_NMAX * 4);
+        F.comp = (int16_t *)(b + (size_t)BATCH_NMAX * 6);
+        F.n = n;
+        F.h = h;
+        F.depth = depth;
+        F.ph = KM_SPLIT;
+        F.ncomp = 0;
+        F.it = 0;
+    };
+    if (tid == 0) {
+        frame_at(0, mem, n0, h0, depth0);
+        sh.top = 0;
+        sh.bad = 0;
+        if (depth0 > cn.maxd) cn.maxd = depth0;
+    }
+    __syncthreads();
+    for (;;) {
+        const int top = sh.top;
+        if (top < 0) break;
+        KMFrame &F = sh.fr[top];
+        const int ph = F.ph;
+        __syncthreads();  // every thread has read the control words
+        if (ph == KM_SPLIT) {
+            km_split(sh, F, V, SP, etah0 * pow2f(F.depth - depth0), ctr, nl, cn);
+            if (tid == 0) F.ph = KM_H1;
+        } else if (ph == KM_H1 || ph == KM_H2) {
+            // the Kepler flow of two-body components over h/2 (CC_KEPLER),
+            // then the sub-recursions of components of at most 32 bodies
+            const int nc = F.ncomp;
+            const double hh = 0.5 * F.h;
+            if (SP.kepler) {
+                for (int ci = tid; ci < nc; ci += KM_T) {
+                    if (F.comp[2 * ci + 1] != 2) continue;
+                    const int a = F.cl[F.comp[2 * ci]], b = F.cl[F.comp[2 * ci] + 1];
+                    double xa[3] = {V.x[a], V.y[a], V.z[a]}, xb[3] = {V.x[b], V.y[b], V.z[b]};
+                    double va[3] = {V.vx[a], V.vy[a], V.vz[a]}, vb[3] = {V.vx[b], V.vy[b], V.vz[b]};
+                    if (!k8_kepler(V.m[a], V.m[b], xa, xb, va, vb, SP.G, hh)) {
+                        raise_err(ctr, DERR_KEPLER);
+                    } else {
+                        V.x[a] = xa[0]; V.y[a] = xa[1]; V.z[a] = xa[2];
+                        V.vx[a] = va[0]; V.vy[a] = va[1]; V.vz[a] = va[2];
+                        V.x[b] = xb[0]; V.y[b] = xb[1]; V.z[b] = xb[2];
+                        V.vx[b] = vb[0]; V.vy[b] = vb[1]; V.vz[b] = vb[2];
+                    }
+                }
+            }
+            bool subs = false;
+            for (int ci = 0; ci < nc && !subs; ++ci) {
+                const int z = F.comp[2 * ci + 1];
+                subs = !(SP.kepler && z == 2);
+            }
+            if (subs && F.depth + 1 > SP.max_depth) {
+                if (tid == 0) {
+                    raise_err(ctr, DERR_DEPTH);
+                    sh.bad = 1;
+                }
+            } else if (subs) {
+                if (tid == 0) sh.qi = 0;
+                __syncthreads();
+                for (;;) {
+                    int ci = 0;
+                    if (lane == 0) ci = atomicAdd(&sh.qi, 1);
+                    ci = __shfl_sync(FULL, ci, 0);
+                    if (ci >= nc) break;
+                    const int z = F.comp[2 * ci + 1];
+                    if (z > 32 || (SP.kepler && z == 2)) continue;
+                    small_task(sh.u.sw[w], V, F.cl + F.comp[2 * ci], z, hh, F.depth + 1, SP, ctr, nl, cn, pc);
+                }
+            }
+            if (tid == 0) {
+                F.ph = ph == KM_H1 ? KM_B1 : KM_B2;
+                F.it = 0;
+            }
+        } else if (ph == KM_B1 || ph == KM_B2) {
+            // the next component of more than 32 bodies: a nested frame
+            if (tid == 0) {
+                int ci = F.it;
+                while (ci < F.ncomp && F.comp[2 * ci + 1] <= 32) ++ci;
+                if (ci < F.ncomp) {
+                    F.it = ci + 1;
+                    if (top + 1 >= KM_MAXF || F.depth + 1 > SP.max_depth) {
+                        raise_err(ctr, DERR_DEPTH);
+                        sh.bad = 1;
+                    } else {
+                        frame_at(top + 1, F.cl + F.comp[2 * ci], F.comp[2 * ci + 1], 0.5 * F.h, F.depth + 1);
+                        sh.top = top + 1;
+                        if (F.depth + 1 > cn.maxd) cn.maxd = F.depth + 1;
+                    }
+                } else {
+                    F.ph = ph == KM_B1 ? KM_DKD : KM_DONE;
+                }
+            }
+        } else if (ph == KM_DKD) {
+            if (F.kick > 0 || F.nsingle > 0) km_dkd(sh, F, V, SP, cn);
+            if (tid == 0) F.ph = KM_H2;
+        } else {
+            if (tid == 0) sh.top = top - 1;
+        }
+        __syncthreads();
+        if (sh.bad) {
+            __syncthreads();
+            if (tid == 0) sh.top = -1;
+            __syncthreads();
+            break;
+        }
+    }
+    __syncthreads();
+}
+
+__global__ void __launch_bounds__(KM_T) k_batch(Level L, const int32_t *members, const int32_t *t_start,
+                                                 const int32_t *t_size, const int32_t *tlist, const int32_t *nt_ptr,
+                                                 SmallParams SP, DevCounters *ctr, int *queue, int32_t *near_ij,
+                                                 double *near_tau, long long near_cap, char *scratch, int nslots)
+{
+    __shared__ KMShared sh;
+    __shared__ int s_slot;
+    const int nt = *nt_ptr;
+    const int tid = threadIdx.x, w = tid >> 5, lane = tid & 31;
+    const SView V{L.x, L.y, L.z, L.vx, L.vy, L.vz, L.m, L.gid};
+    const NearLog nl = {ctr, near_ij, near_tau, near_cap, SP.near_tol};
+    // frame scratch: a slot of the pool, claimed at the first CTA task (the
+    // pool holds as many slots as CTAs of this kernel can be resident, over
+    // all launches in flight, so a resident CTA always finds one)
+    int *slot_flag = (int *)scratch;
+    char *pool = scratch + batch_pool_offset(nslots);
+    if (tid == 0) s_slot = -1;
+    SmallCnt cn;
+    PairCounters pc;
+    // CTA mode while the queue's head task has more than 32 bodies
+    int first = -1;
+    for (;;) {
+        if (tid == 0) sh.q = atomicAdd(queue, 1);
+        __syncthreads();
+        const int q = sh.q;
+        __syncthreads();
+        if (q >= nt) break;
+        const int c = tlist[q], n = t_size[c];
+        if (n > 32) {
+            if (tid == 0 && s_slot < 0) {
+                for (int r = 0; r < 4 * nslots && s_slot < 0; ++r) {
+                    const int k = (int)((blockIdx.x + (unsigned)r) % (unsigned)nslots);
+                    if (atomicCAS(&slot_flag[k], 0, 1) == 0) s_slot = k;
+                }
+                if (s_slot < 0) raise_err(ctr, DERR_SMALL_OVERFLOW);
+            }
+            __syncthreads();
+            if (s_slot < 0) break;
+            medium_task(sh, V, members + t_start[c], n, SP.h0, SP.depth0, SP, ctr, nl, cn, pc,
+                        pool + (size_t)s_slot * KM_MAXF * KM_FRAME_BYTES);
+            continue;
+        }
+        first = q;  // warp mode from here: this task to warp 0, the rest from the queue
+        break;
+    }
+    if (first >= 0) {
+        for (int q = (w == 0) ? first : -1;;) {
+            if (q < 0) {
+                if (lane == 0) q = atomicAdd(queue, 1);
+                q = __shfl_sync(FULL, q, 0);
+            }
+            if (q >= nt) break;
+            const int c = tlist[q];
+            small_task(sh.u.sw[w], V, members + t_start[c], t_size[c], SP.h0, SP.depth0, SP, ctr, nl, cn, pc);
+            q = -1;
+        }
+    }
+    __syncthreads();
+    if (tid == 0 && s_slot >= 0) {
+        __threadfence();
+        atomicExch(&slot_flag[s_slot], 0);
+    }
+    flush_counters(cn, pc, ctr);
+}
+
+// CTAs of k_batch resident on the whole GPU (the launch's grid; the frame
+// scratch is per CTA)
+static int batch_grid(int nsm)
+{
+    static int occ = 0;
+    if (occ == 0) {
+        int o = 0;
+        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&o, k_batch, KM_T, 0) != cudaSuccess || o < 1) {
+            cudaGetLastError();
+            o = 1;
+        }
+        occ = o;
+    }
+    return occ * (nsm > 0 ? nsm : 1);
+}
+
+size_t batch_scratch_bytes(int nsm)
+{
+    const int g = batch_grid(nsm);
+    return batch_pool_offset(g) + (size_t)g * KM_MAXF * KM_FRAME_BYTES;
+}
+
+void launch_batch(const Level &L, const int32_t *members, const int32_t *t_start, const int32_t *t_size,
+                  const int32_t *tlist, const int32_t *nt_ptr, int nt_bound, const SmallParams &SP, DevCounters *ctr,
+                  int *queue, int32_t *near_ij, double *near_tau, long long near_cap, int nsm, char *scratch,
+                  cudaStream_t s)
+{
+    if (nt_bound <= 0) return;
+    // *queue is zero on entry; CTAs beyond the work exit at the first read
+    const int g = batch_grid(nsm);
+    const int grid = nt_bound < g ? nt_bound : g;
+    k_batch<<<grid, KM_T, 0, s>>>(L, members, t_start, t_size, tlist, nt_ptr, SP, ctr, queue, near_ij, near_tau,
+                                  near_cap, scratch, g);
+    CC_COUNT_LAUNCH(1);
 }
 
 void launch_small(const Level &L, const int32_t *members, const int32_t *comp_start, const int32_t *comp_size,

@@ -92,3 +92,23 @@ def check_velocity_bound(gv, ov, S, dt, depth, steps=1, K=K_MIXED, u=U32, exempt
     assert ratio[mask].max() <= 1.0, (what, "body", worst, "ratio", float(ratio[worst]), "err", float(err[worst]),
                                       "tol", float(tol[worst]))
     return float(ratio[mask].max()), int((ratio[~mask] > 1.0).sum())
+
+
+def check_position_bound(gx, ox, S, dt, depth, steps=1, K=K_MIXED, u=U32, exempt=(), what=""):
+    """Positions of the mixed form: a body's position is its start plus the
+    drifts of the step, each taking a velocity within the bound of
+    check_velocity_bound, so |gx_i - ox_i| <= dt (K u dt S_i (depth + 1)
+    steps) steps, plus the FP64 roundings of the drifts (at most one ulp of
+    |x| per level).  Asserted for every body not in `exempt`; returns the
+    largest ratio."""
+    err = np.linalg.norm(gx - ox, axis=0)
+    tol = dt * steps * (K * u * dt * S * (depth + 1) * steps) + 4 * U64 * (depth + 1) * np.linalg.norm(ox, axis=0)
+    ratio = err / tol
+    mask = np.ones(ratio.shape[0], dtype=bool)
+    ex = np.asarray(exempt, dtype=np.int64)
+    if ex.size:
+        mask[ex] = False
+    worst = int(np.argmax(np.where(mask, ratio, -1.0)))
+    assert ratio[mask].max() <= 1.0, (what, "body", worst, "ratio", float(ratio[worst]), "err", float(err[worst]),
+                                      "tol", float(tol[worst]))
+    return float(ratio[mask].max())

@@ -102,9 +102,12 @@ def systems4096():
     return m, x, v, off, s, st
 
 
-def test_systems_4096_one_step_fp64(cclib, systems4096):
+@pytest.mark.parametrize("s_small", [32, 512])
+def test_systems_4096_one_step_fp64(cclib, systems4096, s_small):
+    """s_small = 512: every system one task of the batched kernel (one
+    launch per outer step)."""
     m, x, v, off, s, st = systems4096
-    c = cclib.Context(m, x, v, dt=1 / 64)
+    c = cclib.Context(m, x, v, dt=1 / 64, s_small=s_small)
     c.set_systems(off)
     c.evolve(1 / 64)
     _, _, gx, gv = c.get_state()
@@ -116,9 +119,10 @@ def test_systems_4096_one_step_fp64(cclib, systems4096):
     assert g["max_depth_seen"] == st.max_depth_seen
 
 
-def test_systems_4096_one_step_mixed(cclib, systems4096):
+@pytest.mark.parametrize("s_small", [32, 512])
+def test_systems_4096_one_step_mixed(cclib, systems4096, s_small):
     m, x, v, off, s, st = systems4096
-    c = cclib.Context(m, x, v, dt=1 / 64, precision=cclib.PREC_MIXED, near_tol=1e-6)
+    c = cclib.Context(m, x, v, dt=1 / 64, precision=cclib.PREC_MIXED, near_tol=1e-6, s_small=s_small)
     c.set_systems(off)
     c.evolve(1 / 64)
     _, _, gx, gv = c.get_state()
