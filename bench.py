@@ -280,7 +280,7 @@ def accuracy_gate(cc, dm, dx, dv, t_end, h_fp64_rel):
     out = []
     steps = int(round(t_end / DT))
     for form, hf in (("mixed", 0.0), ("mixed", h_fp64_rel), ("fp64", 0.0)):
-        ctx = _ctx(cc, dm, dx, dv, None, "plummer", form, hf, 32)
+        ctx = _ctx(cc, dm, dx, dv, None, "plummer", form, hf, cc.SMALL_AUTO)
         E0, P0, L0 = ctx.energy()
         torch.cuda.synchronize()
         t0 = time.perf_counter()
@@ -307,7 +307,7 @@ def force_error(cc, m, x, v, dev):
     acc = {}
     for form in ("fp64", "mixed"):
         dm, dx, dv = (torch.tensor(a, device=dev) for a in (m, x, v))
-        ctx = _ctx(cc, dm, dx, dv, None, "plummer", form, 0.0, 32)
+        ctx = _ctx(cc, dm, dx, dv, None, "plummer", form, 0.0, cc.SMALL_AUTO)
         ctx.kick(labels, 1.0)
         _, _, _, gv = ctx.get_state()
         ctx.close()
@@ -340,7 +340,7 @@ def other_configs(cc, dev, stream, seed, l2_flush):
         rows = []
         wname = a.workload
         for form, hf in forms:
-            ctx = _ctx(cc, dm, dx, dv, sys_off, wname, form, hf, 32, split=1 if wl == "hold" else 0)
+            ctx = _ctx(cc, dm, dx, dv, sys_off, wname, form, hf, cc.SMALL_AUTO, split=1 if wl == "hold" else 0)
             E0, _, _ = ctx.energy()
             dtw = WORKLOADS[wname]["dt"]
             w0 = time.perf_counter()
@@ -481,12 +481,13 @@ def run_gpu(args, rank, world):
             "tau_ms_per_step": tm["tau_ms"] / args.steps, "kick_ms_per_step": tm["kick_ms"] / args.steps,
             "tau_tflops": TAU_FLOPS * tm["tau_pairs"] / (tm["tau_ms"] * 1e-3) / 1e12 if tm["tau_ms"] > 0 else None,
             "kick_tflops": KICK_FLOPS * tm["kick_pairs"] / (tm["kick_ms"] * 1e-3) / 1e12 if tm["kick_ms"] else None,
-            "small_kernel": {"kernel": "k_small", "ms_per_step": tm["small_ms"] / args.steps,
+            "small_kernel": {"kernel": ("k_batch" if args.s_small > 32 or (args.s_small < 0 and args.form == "mixed")
+                                        else "k_small"), "ms_per_step": tm["small_ms"] / args.steps,
                              "launches_per_step": tm["small_launches"] / args.steps,
                              "tau_pairs_evaluated_per_step": tm["small_tau_evaluated"] / args.steps,
                              "kick_pairs_per_step": tm["small_kick_pairs"] / args.steps,
                              "achieved": small_ach, "frac": small_ach / peak if small_ach else None,
-                             "bound": "latency (one warp per component)"},
+                             "bound": "latency (one warp per component of <= 32 bodies, one CTA above)"},
             "fp64_peak_tflops": f64_peak / 1e12, "fp32_peak_tflops": f32_peak / 1e12}
     other_line = None
     if other:
@@ -654,8 +655,9 @@ def main():
     ap.add_argument("--h-fp64", type=float, default=0.0,
                     help="mixed form: sets split at h < h_fp64*dt take FP64 forces")
     ap.add_argument("--single-form", action="store_true", help="skip timing the other form")
-    ap.add_argument("--s-small", type=int, default=32,
-                    help="components of at most this many bodies run in the small-component kernel (0: none)")
+    ap.add_argument("--s-small", type=int, default=-1,
+                    help="components of at most this many bodies (<= 512) run on-chip in the batched kernel "
+                         "(0: none; -1: the library's choice, 512 mixed / 32 FP64)")
     ap.add_argument("--accuracy", action="store_true", help="integrate both forms to --t-end and report dE/E")
     ap.add_argument("--h-fp64-gate", type=float, default=1.0 / 16,
                     help="accuracy gate: the mixed form's second run takes FP64 forces below this times dt")

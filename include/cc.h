@@ -41,6 +41,8 @@ extern "C" {
 #define CC_SPLIT_HOLD  1    /* slow/fast split by the particle time step
                                tau(i) = min_j tau(i,j) (Sec. 2.1, Eq. HOLD)     */
 
+#define CC_SMALL_AUTO -1    /* cc_params.s_small: the library picks the limit    */
+
 #define CC_PREC_FP64   0    /* every force and tau in FP64                      */
 #define CC_PREC_MIXED  1    /* FP32 forces between components, certified FP32
                                tau pre-filter; FP64 state, drift, predicate     */
@@ -56,7 +58,8 @@ typedef struct {
     int    precision;  /* CC_PREC_FP64 or CC_PREC_MIXED                                 */
     int    kepler;     /* 1: CC_KEPLER (Sec. 3.2), two-body components by Kepler flow   */
     int    max_depth;  /* recursion depth cap (levels below the outer step)            */
-    int    s_small;    /* components of at most s_small (<= 512) members run entirely
+    int    s_small;    /* CC_SMALL_AUTO (-1, default): 512 in the mixed form, 32 in FP64.
+                          Components of at most s_small (<= 512) members run entirely
                           on-chip in the persistent batched kernel: up to 32 members
                           one warp each, 33..512 one thread block each (its own
                           components of <= 32 members on its warps); 0 disables it.
@@ -135,7 +138,8 @@ typedef struct {
 typedef struct cc_ctx cc_ctx;
 
 /* Fill *p with defaults: G=1, eps=0, eta=0.03, dt=1/64, h_fp64=0,
- * near_tol=1e-12, FP64, kepler off, max_depth=64, s_small=32, autotune on. */
+ * near_tol=1e-12, FP64, kepler off, max_depth=64, s_small=CC_SMALL_AUTO,
+ * autotune on. */
 int cc_default_params(cc_params *p);
 
 /* Create a context holding n particles (Sec. 2.1: masses m_i, positions q_i,

@@ -1182,7 +1182,7 @@ int cc_default_params(cc_params *p)
     p->precision = CC_PREC_FP64;
     p->kepler = 0;
     p->max_depth = 64;
-    p->s_small = 32;
+    p->s_small = CC_SMALL_AUTO;
     p->eta_outside = 0;
     p->autotune = 1;
     p->com_max = 32;
@@ -1203,7 +1203,7 @@ int cc_init(cc_ctx **out, int64_t n, const double *m, const double *x3, const do
     *out = nullptr;
     if (!(p->G > 0.0) || !(p->eps >= 0.0) || !finite_pos(p->eta) || !finite_pos(p->dt) || p->max_depth < 0 ||
         p->max_depth > 200 || (p->precision != CC_PREC_FP64 && p->precision != CC_PREC_MIXED) ||
-        (p->kepler && p->eps != 0.0) || p->s_small < 0 || p->s_small > BATCH_NMAX || p->edge_rec_max < 0 ||
+        (p->kepler && p->eps != 0.0) || p->s_small < CC_SMALL_AUTO || p->s_small > BATCH_NMAX || p->edge_rec_max < 0 ||
         p->fault_test < 0 || p->fault_test > 2 || (p->split != CC_SPLIT_CC && p->split != CC_SPLIT_HOLD) ||
         (p->split == CC_SPLIT_HOLD && p->kepler) || !(p->theta >= 0.0) || !std::isfinite(p->theta) ||
         (p->theta > 0.0 && (p->split != CC_SPLIT_CC || p->com_max < 2 || p->com_max > COM_MAX_MEMBERS))) {
@@ -1213,6 +1213,10 @@ int cc_init(cc_ctx **out, int64_t n, const double *m, const double *x3, const do
     cc_ctx *c = new cc_ctx();
     c->n = n;
     c->p = *p;
+    // automatic size limit of the batched kernel: 512 for the mixed form; 32
+    // for FP64, where one SM's FP64 rate makes a large on-chip task the
+    // critical path of the step
+    if (c->p.s_small == CC_SMALL_AUTO) c->p.s_small = c->p.precision == CC_PREC_MIXED ? BATCH_NMAX : 32;
     c->eta_run = p->eta;
     c->p_autotune = p->autotune != 0;
     c->stream = (cudaStream_t)stream;

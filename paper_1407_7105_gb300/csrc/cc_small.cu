@@ -821,13 +821,15 @@ struct KMFrame {
     int nsingle;
 };
 
+// A frame's set staged in shared memory, four 16-byte words per body (one
+// vector load each in the pair loops):
+//   split, FP64: {x, y} {z, vx} {vy, vz} {m, -}
+//   split, mixed: (x, y, z hi, fl32 m) (x, y, z lo, max |x hi|) (v hi, max |v hi|) (v lo, -)
+//   DKD, FP64: {x, y} {z, m};  DKD, mixed: (x, y, z hi, fl32 m) (x, y, z lo, label bits)
 struct KMStage {
     union {
-        double d[7][BATCH_NMAX];  // FP64: x y z vx vy vz m
-        struct {
-            float f[13][BATCH_NMAX];  // mixed: hi/lo of x y z vx vy vz, fl32(m)
-            float xm[BATCH_NMAX], vm[BATCH_NMAX];
-        } s;
+        double2 d[4][BATCH_NMAX];
+        float4 q[4][BATCH_NMAX];
     };
     int par[BATCH_NMAX];  // union-find forest over set positions, then roots
     int cnt[BATCH_NMAX];  // component size by root
@@ -912,19 +914,20 @@ __device__ void km_split(KMShared &sh, KMFrame &F, const SView V, const SmallPar
         const int k = F.sl[p];
         const double st[7] = {V.x[k], V.y[k], V.z[k], V.vx[k], V.vy[k], V.vz[k], V.m[k]};
         if (mixed) {
+            float hi[6], lo[6];
 #pragma unroll
-            for (int c = 0; c < 6; ++c) {
-                float hi, lo;
-                ff_split(st[c], hi, lo);
-                T.s.f[c][p] = hi;
-                T.s.f[6 + c][p] = lo;
-            }
-            T.s.f[12][p] = fl32(st[6]);
-            T.s.xm[p] = fmaxf(fabsf(T.s.f[0][p]), fmaxf(fabsf(T.s.f[1][p]), fabsf(T.s.f[2][p])));
-            T.s.vm[p] = fmaxf(fabsf(T.s.f[3][p]), fmaxf(fabsf(T.s.f[4][p]), fabsf(T.s.f[5][p])));
+            for (int c = 0; c < 6; ++c) ff_split(st[c], hi[c], lo[c]);
+            const float xm = fmaxf(fabsf(hi[0]), fmaxf(fabsf(hi[1]), fabsf(hi[2])));
+            const float vm = fmaxf(fabsf(hi[3]), fmaxf(fabsf(hi[4]), fabsf(hi[5])));
+            T.q[0][p] = make_float4(hi[0], hi[1], hi[2], fl32(st[6]));
+            T.q[1][p] = make_float4(lo[0], lo[1], lo[2], xm);
+            T.q[2][p] = make_float4(hi[3], hi[4], hi[5], vm);
+            T.q[3][p] = make_float4(lo[3], lo[4], lo[5], 0.f);
         } else {
-#pragma unroll
-            for (int c = 0; c < 7; ++c) T.d[c][p] = st[c];
+            T.d[0][p] = make_double2(st[0], st[1]);
+            T.d[1][p] = make_double2(st[2], st[3]);
+            T.d[2][p] = make_double2(st[4], st[5]);
+            T.d[3][p] = make_double2(st[6], 0.0);
         }
         T.par[p] = p;
         T.cnt[p] = 0;
@@ -951,59 +954,52 @@ __device__ void km_split(KMShared &sh, KMFrame &F, const SView V, const SmallPar
                                 __dsub_rn(V.vx[a], V.vx[b]), __dsub_rn(V.vy[a], V.vy[b]),
                                 __dsub_rn(V.vz[a], V.vz[b]), V.m[a], V.m[b], P);
         }
-        return tau_fp64_ool(__dsub_rn(T.d[0][lo], T.d[0][hi]), __dsub_rn(T.d[1][lo], T.d[1][hi]),
-                            __dsub_rn(T.d[2][lo], T.d[2][hi]), __dsub_rn(T.d[3][lo], T.d[3][hi]),
-                            __dsub_rn(T.d[4][lo], T.d[4][hi]), __dsub_rn(T.d[5][lo], T.d[5][hi]), T.d[6][lo],
-                            T.d[6][hi], P);
+        const double2 a0 = T.d[0][lo], a1 = T.d[1][lo], a2 = T.d[2][lo], a3 = T.d[3][lo];
+        const double2 b0 = T.d[0][hi], b1 = T.d[1][hi], b2 = T.d[2][hi], b3 = T.d[3][hi];
+        return tau_fp64_ool(__dsub_rn(a0.x, b0.x), __dsub_rn(a0.y, b0.y), __dsub_rn(a1.x, b1.x),
+                            __dsub_rn(a1.y, b1.y), __dsub_rn(a2.x, b2.x), __dsub_rn(a2.y, b2.y), a3.x, b3.x, P);
     };
     bool uf_ok = true;
+    auto edge_found = [&](int p, int j) {
+        if (SP.hold) {
+            T.cst[p] = 1;
+            T.cst[j] = 1;
+        } else if (!uf_union(T.par, p, j)) {
+            uf_ok = false;
+        }
+    };
+    auto decide64 = [&](int p, int j) {
+        const double tau = tau64(p, j);
+        ++cn.fp64;
+        near_log(tau, h, nl.tol, nl.ctr, V.gid[F.sl[p]], V.gid[F.sl[j]], nl.ij, nl.tau, nl.cap);
+        return tau < h;
+    };
     // rows p of the pair triangle, zig-zag over the threads (balanced)
     for (int base = 0; base < n; base += 2 * KM_T) {
         for (int side = 0; side < 2; ++side) {
             const int p = side == 0 ? base + tid : base + 2 * KM_T - 1 - tid;
             if (p >= n - 1) continue;
-            float me_f[13], me_xm = 0.f, me_vm = 0.f;
+            cn.eval += (unsigned long long)(n - 1 - p);
             if (mixed) {
-#pragma unroll
-                for (int q = 0; q < 13; ++q) me_f[q] = T.s.f[q][p];
-                me_xm = T.s.xm[p];
-                me_vm = T.s.vm[p];
-            }
-            for (int j = p + 1; j < n; ++j) {
-                bool edge;
-                if (mixed) {
-                    const TauPrep32 t = tau_prep_fp32(
-                        (T.s.f[0][j] - me_f[0]) + (T.s.f[6][j] - me_f[6]),
-                        (T.s.f[1][j] - me_f[1]) + (T.s.f[7][j] - me_f[7]),
-                        (T.s.f[2][j] - me_f[2]) + (T.s.f[8][j] - me_f[8]),
-                        (T.s.f[3][j] - me_f[3]) + (T.s.f[9][j] - me_f[9]),
-                        (T.s.f[4][j] - me_f[4]) + (T.s.f[10][j] - me_f[10]),
-                        (T.s.f[5][j] - me_f[5]) + (T.s.f[11][j] - me_f[11]), Q.G * (me_f[12] + T.s.f[12][j]),
-                        c11 * fmaxf(me_xm, T.s.xm[j]), c11 * fmaxf(me_vm, T.s.vm[j]), Q);
+                const float4 a0 = T.q[0][p], a1 = T.q[1][p], a2 = T.q[2][p], a3 = T.q[3][p];
+                auto prep = [&](int j) {
+                    const float4 b0 = T.q[0][j], b1 = T.q[1][j], b2 = T.q[2][j], b3 = T.q[3][j];
+                    return tau_prep_fp32((b0.x - a0.x) + (b1.x - a1.x), (b0.y - a0.y) + (b1.y - a1.y),
+                                         (b0.z - a0.z) + (b1.z - a1.z), (b2.x - a2.x) + (b3.x - a3.x),
+                                         (b2.y - a2.y) + (b3.y - a3.y), (b2.z - a2.z) + (b3.z - a3.z),
+                                         Q.G * (a0.w + b0.w), c11 * fmaxf(a1.w, b1.w), c11 * fmaxf(a2.w, b2.w), Q);
+                };
+                auto finish = [&](int j, const TauPrep32 &t) {
                     const int dec = tau_decide_at(t, etah);
-                    if (dec >= 0) {
-                        edge = dec > 0;
-                    } else {
-                        const double tau = tau64(p, j);
-                        ++cn.fp64;
-                        edge = tau < h;
-                        near_log(tau, h, nl.tol, nl.ctr, V.gid[F.sl[p]], V.gid[F.sl[j]], nl.ij, nl.tau, nl.cap);
-                    }
-                } else {
-                    const double tau = tau64(p, j);
-                    ++cn.fp64;
-                    edge = tau < h;
-                    near_log(tau, h, nl.tol, nl.ctr, V.gid[F.sl[p]], V.gid[F.sl[j]], nl.ij, nl.tau, nl.cap);
-                }
-                ++cn.eval;
-                if (edge) {
-                    if (SP.hold) {
-                        T.cst[p] = 1;
-                        T.cst[j] = 1;
-                    } else if (!uf_union(T.par, p, j)) {
-                        uf_ok = false;
-                    }
-                }
+                    const bool edge = dec >= 0 ? dec > 0 : decide64(p, j);
+                    if (edge) edge_found(p, j);
+                };
+                // one pair at a time: two in flight shortened a lone task's
+                // split but cost throughput when every SM was busy with tasks
+                for (int j = p + 1; j < n; ++j) finish(j, prep(j));
+            } else {
+                for (int j = p + 1; j < n; ++j)
+                    if (decide64(p, j)) edge_found(p, j);
             }
         }
     }
@@ -1124,26 +1120,23 @@ __device__ void km_dkd(KMShared &sh, const KMFrame &F, const SView V, const Smal
     for (int p = tid; p < n; p += KM_T) {
         const int k = F.sl[p];
         double st[7] = {V.x[k], V.y[k], V.z[k], V.vx[k], V.vy[k], V.vz[k], V.m[k]};
-        T.par[p] = F.lab[p];  // labels in shared memory for the pair loops
-        if (F.lab[p] < 0) {
+        const int lab = F.lab[p];
+        T.par[p] = lab;  // labels in shared memory for the pair loops
+        if (lab < 0) {
             k8_drift(st, hd, !mixed);
             V.x[k] = st[0];
             V.y[k] = st[1];
             V.z[k] = st[2];
         }
         if (fp64_kick) {
-#pragma unroll
-            for (int c = 0; c < 3; ++c) T.d[c][p] = st[c];
-            T.d[6][p] = st[6];
+            T.d[0][p] = make_double2(st[0], st[1]);
+            T.d[1][p] = make_double2(st[2], st[6]);
         } else {
+            float hi[3], lo[3];
 #pragma unroll
-            for (int c = 0; c < 3; ++c) {
-                float hi, lo;
-                ff_split(st[c], hi, lo);
-                T.s.f[c][p] = hi;
-                T.s.f[6 + c][p] = lo;
-            }
-            T.s.f[12][p] = fl32(st[6]);
+            for (int c = 0; c < 3; ++c) ff_split(st[c], hi[c], lo[c]);
+            T.q[0][p] = make_float4(hi[0], hi[1], hi[2], fl32(st[6]));
+            T.q[1][p] = make_float4(lo[0], lo[1], lo[2], __int_as_float(lab));
         }
     }
     __syncthreads();
@@ -1152,45 +1145,70 @@ __device__ void km_dkd(KMShared &sh, const KMFrame &F, const SView V, const Smal
         const int li = T.par[p];
         double st[7] = {V.x[k], V.y[k], V.z[k], V.vx[k], V.vy[k], V.vz[k], V.m[k]};
         if (fp64_kick) {
+            // the level kernels' row sum: terms of two j computed side by
+            // side, added in ascending j
             double ax = 0.0, ay = 0.0, az = 0.0;
-            const double xi = T.d[0][p], yi = T.d[1][p], zi = T.d[2][p];
-            for (int j = 0; j < n; ++j) {
-                if (j == p || T.par[j] == li) continue;
-                const double dx0 = __dsub_rn(T.d[0][j], xi);
-                const double dx1 = __dsub_rn(T.d[1][j], yi);
-                const double dx2 = __dsub_rn(T.d[2][j], zi);
+            const double2 i0 = T.d[0][p], i1 = T.d[1][p];
+            auto term = [&](int j, double &fx, double &fy, double &fz) {
+                const double2 b0 = T.d[0][j], b1 = T.d[1][j];
+                const double dx0 = __dsub_rn(b0.x, i0.x);
+                const double dx1 = __dsub_rn(b0.y, i0.y);
+                const double dx2 = __dsub_rn(b1.x, i1.x);
                 const double r2 = __dadd_rn(__dadd_rn(__dadd_rn(__dmul_rn(dx0, dx0), __dmul_rn(dx1, dx1)),
                                                       __dmul_rn(dx2, dx2)), SP.eps2);
                 const double rinv3 = __ddiv_rn(1.0, __dmul_rn(r2, __dsqrt_rn(r2)));
-                const double ww = __dmul_rn(__dmul_rn(SP.G, T.d[6][j]), rinv3);
-                ax = __dadd_rn(ax, __dmul_rn(ww, dx0));
-                ay = __dadd_rn(ay, __dmul_rn(ww, dx1));
-                az = __dadd_rn(az, __dmul_rn(ww, dx2));
+                const double ww = __dmul_rn(__dmul_rn(SP.G, b1.y), rinv3);
+                fx = __dmul_rn(ww, dx0);
+                fy = __dmul_rn(ww, dx1);
+                fz = __dmul_rn(ww, dx2);
+            };
+            for (int j = 0; j < n; j += 2) {
+                const bool u0 = j != p && T.par[j] != li;
+                const bool u1 = j + 1 < n && j + 1 != p && T.par[j + 1] != li;
+                double f0x = 0.0, f0y = 0.0, f0z = 0.0, f1x = 0.0, f1y = 0.0, f1z = 0.0;
+                if (u0) term(j, f0x, f0y, f0z);
+                if (u1) term(j + 1, f1x, f1y, f1z);
+                if (u0) {
+                    ax = __dadd_rn(ax, f0x);
+                    ay = __dadd_rn(ay, f0y);
+                    az = __dadd_rn(az, f0z);
+                }
+                if (u1) {
+                    ax = __dadd_rn(ax, f1x);
+                    ay = __dadd_rn(ay, f1y);
+                    az = __dadd_rn(az, f1z);
+                }
             }
             st[3] = __dadd_rn(st[3], __dmul_rn(h, ax));
             st[4] = __dadd_rn(st[4], __dmul_rn(h, ay));
             st[5] = __dadd_rn(st[5], __dmul_rn(h, az));
         } else {
-            const float xh = T.s.f[0][p], yh = T.s.f[1][p], zh = T.s.f[2][p];
-            const float xl = T.s.f[6][p], yl = T.s.f[7][p], zl = T.s.f[8][p];
+            const float4 a0 = T.q[0][p], a1 = T.q[1][p];
             const float e2 = (float)SP.eps2;
-            float sx = 0.f, sy = 0.f, sz = 0.f, cx = 0.f, cy = 0.f, cz = 0.f;
-            for (int j = 0; j < n; ++j) {
-                const float dx = (T.s.f[0][j] - xh) + (T.s.f[6][j] - xl);
-                const float dy = (T.s.f[1][j] - yh) + (T.s.f[7][j] - yl);
-                const float dz = (T.s.f[2][j] - zh) + (T.s.f[8][j] - zl);
+            // two compensated accumulators (even and odd j): two independent chains
+            float sx0 = 0.f, sy0 = 0.f, sz0 = 0.f, cx0 = 0.f, cy0 = 0.f, cz0 = 0.f;
+            float sx1 = 0.f, sy1 = 0.f, sz1 = 0.f, cx1 = 0.f, cy1 = 0.f, cz1 = 0.f;
+            auto term = [&](int j, float &sx, float &sy, float &sz, float &cx, float &cy, float &cz) {
+                const float4 b0 = T.q[0][j], b1 = T.q[1][j];
+                const float dx = (b0.x - a0.x) + (b1.x - a1.x);
+                const float dy = (b0.y - a0.y) + (b1.y - a1.y);
+                const float dz = (b0.z - a0.z) + (b1.z - a1.z);
                 const float r2 = fmaf(dz, dz, fmaf(dy, dy, fmaf(dx, dx, e2)));
                 float ri = rsqrtf(r2);
                 ri = ri * fmaf(-0.5f * r2, ri * ri, 1.5f);
-                const float ww = (j != p && T.par[j] != li) ? T.s.f[12][j] * (ri * ri * ri) : 0.f;
+                const float ww = (j != p && __float_as_int(b1.w) != li) ? b0.w * (ri * ri * ri) : 0.f;
                 kahan_add(sx, cx, ww * dx);
                 kahan_add(sy, cy, ww * dy);
                 kahan_add(sz, cz, ww * dz);
+            };
+            for (int j = 0; j < n; j += 2) {
+                term(j, sx0, sy0, sz0, cx0, cy0, cz0);
+                if (j + 1 < n) term(j + 1, sx1, sy1, sz1, cx1, cy1, cz1);
             }
             const double gh = SP.G * h;
-            st[3] = fma(gh, f2d(sx) - f2d(cx), st[3]);
-            st[4] = fma(gh, f2d(sy) - f2d(cy), st[4]);
-            st[5] = fma(gh, f2d(sz) - f2d(cz), st[5]);
+            st[3] = fma(gh, (f2d(sx0) - f2d(cx0)) + (f2d(sx1) - f2d(cx1)), st[3]);
+            st[4] = fma(gh, (f2d(sy0) - f2d(cy0)) + (f2d(sy1) - f2d(cy1)), st[4]);
+            st[5] = fma(gh, (f2d(sz0) - f2d(cz0)) + (f2d(sz1) - f2d(cz1)), st[5]);
         }
         if (li < 0) k8_drift(st, hd, !mixed);
         V.x[k] = st[0];
