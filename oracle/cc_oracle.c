@@ -699,6 +699,197 @@ int orc_evolve_hold(int64_t n, double *x3, double *v3, const double *m,
     return rc;
 }
 
+/* ------------------------------------------------------------------ */
+/* the OK split (Sec. 4.2): interactions partitioned by tau(i,j)        */
+/* ------------------------------------------------------------------ */
+/* Reading (R15): as HOLD partitions the particles of a set, the OK split
+ * partitions its interactions.  The interaction list I of a particle set S
+ * (at the outer step: every pair of S) splits at pivot h into the fast list
+ * I_F = {(i,j) in I : tau(i,j) < h} and the slow list I_S = I \ I_F; F is the
+ * set of particles of I_F.  With H_F = T_F + V_{I_F} and H_S = T_{S\F} +
+ * V_{I_S}, one step is
+ *     E_{h/2,H_F} D_{h/2,T_{S\F}} K_{h,V_{I_S}} D_{h/2,T_{S\F}} E_{h/2,H_F},
+ * E_{h/2,H_F} = evolve_ok(F, I_F, h/2), the same split at half the pivot.
+ * Every slow interaction is kicked at the pivot of the level where tau
+ * first fails the threshold: the power of two at or below tau(i,j).
+ * Pair lists hold (a, b), a < b particle ids, sorted by (a, b).  Kick order
+ * (R5): a_i sums its slow partners j in ascending id. */
+
+/* the pair term of body i from body j, orc_kick's arithmetic */
+static inline void pair_term(int64_t n, const double *x3, const double *m, double G, double eps2,
+                             int64_t i, int64_t j, double *ax, double *ay, double *az)
+{
+    double dx0 = x3[j] - x3[i];
+    double dx1 = x3[n + j] - x3[n + i];
+    double dx2 = x3[2 * n + j] - x3[2 * n + i];
+    double r2 = ((dx0 * dx0 + dx1 * dx1) + dx2 * dx2) + eps2;
+    double rinv3 = 1.0 / (r2 * sqrt(r2));
+    double w = (G * m[j]) * rinv3;
+    *ax = *ax + w * dx0;
+    *ay = *ay + w * dx1;
+    *az = *az + w * dx2;
+}
+
+static int cmp_pair(const void *x, const void *y)
+{
+    const int32_t *a = (const int32_t *)x, *b = (const int32_t *)y;
+    if (a[0] != b[0]) return (a[0] > b[0]) - (a[0] < b[0]);
+    return (a[1] > b[1]) - (a[1] < b[1]);
+}
+
+/* both directions (i, j) and (j, i) of each pair, sorted by (i, j) */
+static int32_t *directed(const int32_t *pairs, int64_t np)
+{
+    int32_t *d = (int32_t *)malloc(sizeof(int32_t) * 4 * (np > 0 ? np : 1));
+    for (int64_t k = 0; k < np; ++k) {
+        d[4 * k] = pairs[2 * k];
+        d[4 * k + 1] = pairs[2 * k + 1];
+        d[4 * k + 2] = pairs[2 * k + 1];
+        d[4 * k + 3] = pairs[2 * k];
+    }
+    qsort(d, (size_t)(2 * np), 2 * sizeof(int32_t), cmp_pair);
+    return d;
+}
+
+int orc_evolve_ok(int64_t n, double *x3, double *v3, const double *m,
+                  const orc_params *p, const int32_t *set, int64_t nset,
+                  const int32_t *pairs, int64_t npairs, double h, int depth, orc_stats *st)
+{
+    if (depth > p->max_depth) return ORC_E_DEPTH;
+    if (st && depth > st->max_depth_seen) st->max_depth_seen = depth;
+    const double eps2 = p->eps * p->eps;
+    const int all = pairs == NULL;
+    const int64_t ni = all ? nset * (nset - 1) / 2 : npairs;
+    /* 1) the fast list (in the order of I: sorted) and the slow count */
+    int64_t cap = 16, nf = 0;
+    int32_t *fast = (int32_t *)malloc(sizeof(int32_t) * 2 * cap);
+    if (all) {
+        for (int64_t a = 0; a < nset; ++a)
+            for (int64_t b = a + 1; b < nset; ++b)
+                if (orc_tau_ids(n, x3, v3, m, p, set[a], set[b]) < h) {
+                    if (nf == cap) {
+                        cap *= 2;
+                        fast = (int32_t *)realloc(fast, sizeof(int32_t) * 2 * cap);
+                    }
+                    fast[2 * nf] = set[a];
+                    fast[2 * nf + 1] = set[b];
+                    nf++;
+                }
+    } else {
+        for (int64_t k = 0; k < npairs; ++k)
+            if (orc_tau_ids(n, x3, v3, m, p, pairs[2 * k], pairs[2 * k + 1]) < h) {
+                if (nf == cap) {
+                    cap *= 2;
+                    fast = (int32_t *)realloc(fast, sizeof(int32_t) * 2 * cap);
+                }
+                fast[2 * nf] = pairs[2 * k];
+                fast[2 * nf + 1] = pairs[2 * k + 1];
+                nf++;
+            }
+    }
+    if (st) {
+        st->splits++;
+        st->tau_pairs += (uint64_t)ni;
+        st->tau_evals += (uint64_t)ni;
+        if (nf > 0) st->components++;
+    }
+    /* F: the particles of the fast list, ascending */
+    int32_t *F = (int32_t *)malloc(sizeof(int32_t) * (2 * nf > 0 ? 2 * nf : 1));
+    for (int64_t k = 0; k < 2 * nf; ++k) F[k] = fast[k];
+    qsort(F, (size_t)(2 * nf), sizeof(int32_t), cmp_i32);
+    int64_t nF = 0;
+    for (int64_t k = 0; k < 2 * nf; ++k)
+        if (nF == 0 || F[nF - 1] != F[k]) F[nF++] = F[k];
+    /* the fast partners of every particle, for the slow kick */
+    int32_t *fd = directed(fast, nf);
+    /* the slow list when I is explicit */
+    int32_t *slow = NULL;
+    int64_t ns = 0;
+    if (!all) {
+        slow = (int32_t *)malloc(sizeof(int32_t) * 2 * (npairs - nf > 0 ? npairs - nf : 1));
+        int64_t kf = 0;
+        for (int64_t k = 0; k < npairs; ++k) {
+            if (kf < nf && fast[2 * kf] == pairs[2 * k] && fast[2 * kf + 1] == pairs[2 * k + 1]) {
+                kf++;
+                continue;
+            }
+            slow[2 * ns] = pairs[2 * k];
+            slow[2 * ns + 1] = pairs[2 * k + 1];
+            ns++;
+        }
+    }
+    int rc = ORC_OK;
+    for (int pass = 0; pass < 2 && rc == ORC_OK; ++pass) {
+        if (pass == 1) {
+            /* D_{h/2,T_{S\F}} K_{h,V_{I_S}} D_{h/2,T_{S\F}} */
+            for (int half = 0; half < 2; ++half) {
+                if (half == 1) {
+                    double *acc = (double *)calloc((size_t)(3 * (nset > 0 ? nset : 1)), sizeof(double));
+                    if (all) {
+                        /* every pair of the set but the fast ones */
+                        int64_t q = 0;
+                        for (int64_t a = 0; a < nset; ++a) {
+                            const int64_t i = set[a];
+                            while (q < 2 * nf && fd[2 * q] < i) q++;
+                            int64_t r = q;
+                            double ax = 0.0, ay = 0.0, az = 0.0;
+                            for (int64_t b = 0; b < nset; ++b) {
+                                const int64_t j = set[b];
+                                if (j == i) continue;
+                                while (r < 2 * nf && fd[2 * r] == i && fd[2 * r + 1] < j) r++;
+                                if (r < 2 * nf && fd[2 * r] == i && fd[2 * r + 1] == j) continue;
+                                pair_term(n, x3, m, p->G, eps2, i, j, &ax, &ay, &az);
+                            }
+                            acc[3 * a] = ax; acc[3 * a + 1] = ay; acc[3 * a + 2] = az;
+                        }
+                        if (st) st->kick_pairs += (uint64_t)(ni - nf);
+                    } else {
+                        /* the slow partners of each member, ascending */
+                        int32_t *sd = directed(slow, ns);
+                        int64_t q = 0;
+                        for (int64_t a = 0; a < nset; ++a) {
+                            const int64_t i = set[a];
+                            while (q < 2 * ns && sd[2 * q] < i) q++;
+                            double ax = 0.0, ay = 0.0, az = 0.0;
+                            for (int64_t r = q; r < 2 * ns && sd[2 * r] == i; ++r)
+                                pair_term(n, x3, m, p->G, eps2, i, sd[2 * r + 1], &ax, &ay, &az);
+                            acc[3 * a] = ax; acc[3 * a + 1] = ay; acc[3 * a + 2] = az;
+                        }
+                        free(sd);
+                        if (st) st->kick_pairs += (uint64_t)ns;
+                    }
+                    for (int64_t a = 0; a < nset; ++a) {
+                        const int64_t i = set[a];
+                        v3[i] = v3[i] + h * acc[3 * a];
+                        v3[n + i] = v3[n + i] + h * acc[3 * a + 1];
+                        v3[2 * n + i] = v3[2 * n + i] + h * acc[3 * a + 2];
+                    }
+                    free(acc);
+                }
+                /* the drift of the members outside F */
+                int64_t f = 0;
+                for (int64_t a = 0; a < nset; ++a) {
+                    const int32_t i = set[a];
+                    while (f < nF && F[f] < i) f++;
+                    if (f < nF && F[f] == i) continue;
+                    const double dt = 0.5 * h;
+                    x3[i] = x3[i] + dt * v3[i];
+                    x3[n + i] = x3[n + i] + dt * v3[n + i];
+                    x3[2 * n + i] = x3[2 * n + i] + dt * v3[2 * n + i];
+                    if (st) st->drifts++;
+                }
+            }
+        }
+        /* E_{h/2,H_F}: the fast list's particles and interactions at h/2 */
+        if (nf > 0) rc = orc_evolve_ok(n, x3, v3, m, p, F, nF, fast, nf, 0.5 * h, depth + 1, st);
+    }
+    free(fast);
+    free(F);
+    free(fd);
+    free(slow);
+    return rc;
+}
+
 static int check_state(int64_t n, const double *x3, const double *v3, const double *m)
 {
     for (int64_t k = 0; k < 3 * n; ++k)
@@ -721,7 +912,8 @@ int orc_evolve_systems(int64_t n, double *x3, double *v3, const double *m,
 {
     if (n < 0 || nsteps < 0 || !(p->dt > 0.0)) return ORC_E_ARG;
     if (p->kepler && p->eps != 0.0) return ORC_E_ARG;
-    if (p->split != 0 && (p->split != 1 || p->kepler)) return ORC_E_ARG;  /* HOLD has no Kepler mode */
+    if (p->split < 0 || p->split > 2 || (p->split != 0 && p->kepler))
+        return ORC_E_ARG; /* HOLD and the OK split have no Kepler mode */
     if (p->theta < 0.0 || (p->theta > 0.0 && (p->split != 0 || p->com_max < 2))) return ORC_E_ARG;
     int rc = check_state(n, x3, v3, m);
     if (rc) return rc;
@@ -729,10 +921,12 @@ int orc_evolve_systems(int64_t n, double *x3, double *v3, const double *m,
     for (int64_t k = 0; k < n; ++k) set[k] = (int32_t)k;
     for (int64_t s = 0; s < nsteps && rc == ORC_OK; ++s)
         for (int64_t q = 0; q < nsys && rc == ORC_OK; ++q)
-            rc = p->split == 1 ? orc_evolve_hold(n, x3, v3, m, p, set + sys_off[q],
-                                                 sys_off[q + 1] - sys_off[q], p->dt, 0, st)
-                               : orc_evolve_cc(n, x3, v3, m, p, set + sys_off[q],
-                                               sys_off[q + 1] - sys_off[q], p->dt, 0, st);
+            rc = p->split == 1   ? orc_evolve_hold(n, x3, v3, m, p, set + sys_off[q],
+                                                   sys_off[q + 1] - sys_off[q], p->dt, 0, st)
+                 : p->split == 2 ? orc_evolve_ok(n, x3, v3, m, p, set + sys_off[q],
+                                                 sys_off[q + 1] - sys_off[q], NULL, 0, p->dt, 0, st)
+                                 : orc_evolve_cc(n, x3, v3, m, p, set + sys_off[q],
+                                                 sys_off[q + 1] - sys_off[q], p->dt, 0, st);
     free(set);
     if (rc == ORC_OK) rc = check_state(n, x3, v3, m);
     return rc;

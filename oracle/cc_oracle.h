@@ -36,7 +36,7 @@ typedef struct {
     int    eta_outside;/* 0 = eta inside T and dT/dt (default reading),
                           1 = literal placement: eta multiplies the min     */
     int    split;      /* 0 = CC split (Sec. 2.2-2.3), 1 = HOLD split
-                          (Sec. 2.1, Eq. HOLD)                              */
+                          (Sec. 2.1, Eq. HOLD), 2 = OK split (Sec. 4.2)     */
     double theta;      /* > 0: centre-of-mass approximation of V_CC (Sec.
                           4.1) between components whose radii satisfy
                           R_a + R_b < theta |X_a - X_b|; 0 = exact kicks    */
@@ -142,12 +142,22 @@ int orc_evolve_hold(int64_t n, double *x3, double *v3, const double *m,
                     const orc_params *p, const int32_t *set, int64_t nset,
                     double h, int depth, orc_stats *st);
 
+/* evolve_ok(S, I, h) of the OK split (Sec. 4.2, reading R15 in the .c
+ * file): the interaction list I of the set S (pairs == NULL: every pair of
+ * S; else npairs pairs (a, b), a < b ids, sorted) split at pivot h into
+ * fast (tau < h) and slow interactions; the fast ones and their particles
+ * evolve at h/2 before and after D_{h/2} K_{h, slow} D_{h/2} of the rest. */
+int orc_evolve_ok(int64_t n, double *x3, double *v3, const double *m,
+                  const orc_params *p, const int32_t *set, int64_t nset,
+                  const int32_t *pairs, int64_t npairs, double h, int depth, orc_stats *st);
+
 /* evolve_cc(S, h) of the CC pseudocode figure (Sec. 2.3), recursive. */
 int orc_evolve_cc(int64_t n, double *x3, double *v3, const double *m,
                   const orc_params *p, const int32_t *set, int64_t nset,
                   double h, int depth, orc_stats *st);
 
-/* nsteps outer steps evolve_cc(all, p->dt) (evolve_hold when p->split = 1). */
+/* nsteps outer steps evolve_cc(all, p->dt) (evolve_hold when p->split = 1,
+ * evolve_ok when p->split = 2). */
 int orc_evolve(int64_t n, double *x3, double *v3, const double *m,
                const orc_params *p, int64_t nsteps, orc_stats *st);
 

@@ -92,6 +92,8 @@ def lib():
             L.orc_hold_split.argtypes = [i64, dp, dp, dp, P, i32p, i64, d, i32p, S]
             L.orc_evolve_hold.restype = C.c_int
             L.orc_evolve_hold.argtypes = [i64, dp, dp, dp, P, i32p, i64, d, C.c_int, S]
+            L.orc_evolve_ok.restype = C.c_int
+            L.orc_evolve_ok.argtypes = [i64, dp, dp, dp, P, i32p, i64, i32p, i64, d, C.c_int, S]
             L.orc_set_threads.restype = C.c_int
             L.orc_set_threads.argtypes = [C.c_int]
             L.orc_energy.restype = None
@@ -118,7 +120,7 @@ def _f64(a):
     return np.ascontiguousarray(a, dtype=np.float64)
 
 
-SPLIT_CC, SPLIT_HOLD = 0, 1
+SPLIT_CC, SPLIT_HOLD, SPLIT_OK = 0, 1, 2
 
 
 def params(G=1.0, eps=0.0, eta=0.03, dt=1.0 / 64, kepler=False, max_depth=64, eta_outside=False, split=SPLIT_CC,
@@ -237,6 +239,23 @@ def evolve_cc(s: State, p: Params, h: float, set_ids=None, stats: Stats | None =
                              set_ids.shape[0], h, 0, C.byref(st))
     if rc:
         raise RuntimeError(f"orc_evolve_cc failed: {rc}")
+    return st
+
+
+def evolve_ok(s: State, p: Params, h: float, set_ids=None, pairs=None, stats: Stats | None = None):
+    """evolve_ok(S, I, h) of the OK split (Sec. 4.2): I = every pair of the
+    set when pairs is None, else an (npairs, 2) array of ids (a < b, sorted)."""
+    set_ids = np.arange(s.n, dtype=np.int32) if set_ids is None else np.ascontiguousarray(set_ids, dtype=np.int32)
+    st = stats if stats is not None else Stats()
+    if pairs is None:
+        pp, npairs = None, 0
+    else:
+        pa = np.ascontiguousarray(pairs, dtype=np.int32).reshape(-1, 2)
+        pp, npairs = _ip(pa), pa.shape[0]
+    rc = lib().orc_evolve_ok(s.n, _dp(s.x3), _dp(s.v3), _dp(s.m), C.byref(p), _ip(set_ids),
+                             set_ids.shape[0], pp, npairs, h, 0, C.byref(st))
+    if rc:
+        raise RuntimeError(f"orc_evolve_ok failed: {rc}")
     return st
 
 
