@@ -40,6 +40,8 @@ extern "C" {
                                (Sec. 2.2-2.3)                                   */
 #define CC_SPLIT_HOLD  1    /* slow/fast split by the particle time step
                                tau(i) = min_j tau(i,j) (Sec. 2.1, Eq. HOLD)     */
+#define CC_SPLIT_OK    2    /* the OK split (Sec. 4.2): interactions, not
+                               particles, split by tau(i,j) < h; FP64 only      */
 
 #define CC_SMALL_AUTO -1    /* cc_params.s_small: the library picks the limit    */
 
@@ -82,10 +84,13 @@ typedef struct {
                           GPU fault: 1 = its tile copy is announced but never
                           issued, so the mbarrier wait gives up after ~2^20
                           cycles; 2 = the union-find hook gives up at once     */
-    int    split;      /* CC_SPLIT_CC (default) or CC_SPLIT_HOLD: the HOLD method of
+    int    split;      /* CC_SPLIT_CC (default); CC_SPLIT_HOLD: the HOLD method of
                           Sec. 2.1 on the same kernels -- the fast set F = {i :
                           tau(i) < h} is the union of the CC components, so it is
-                          split as one set; no Kepler mode                     */
+                          split as one set; CC_SPLIT_OK: the OK split of Sec.
+                          4.2 -- the pairs with tau(i,j) < h and their particles
+                          recurse at h/2 around D K D of the other particles and
+                          pairs (FP64 form only); neither has a Kepler mode   */
     int    com_max;    /* centre-of-mass approximation: components of 2..com_max
                           (<= 64) members take part (default 32)              */
     double theta;      /* > 0: the centre-of-mass approximation of V_CC (Sec. 4.1)

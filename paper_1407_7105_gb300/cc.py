@@ -19,6 +19,7 @@ PREC_FP64 = 0
 PREC_MIXED = 1
 SPLIT_CC = 0
 SPLIT_HOLD = 1
+SPLIT_OK = 2
 SMALL_AUTO = -1
 
 ERRORS = {-1: "CC_E_ARG", -2: "CC_E_CUDA", -3: "CC_E_DEPTH", -4: "CC_E_TIMEOUT", -5: "CC_E_NONFINITE",

@@ -200,6 +200,20 @@ struct cc_ctx {
     bool sys_batch = false;
     int32_t *d_sys_tasks = nullptr;
     int32_t *d_iota = nullptr;
+    // the OK split (split = CC_SPLIT_OK): the outer level's fast pairs and
+    // their directed copy (ok_cap pairs each, grown on demand), the level's
+    // inverse id map, row pointers and drift flags, each set's segment and
+    // arena offset, the arena of the recursion, node stamps and positions
+    int32_t *ok_edges = nullptr, *ok_dir = nullptr;
+    long long ok_cap = 0;
+    void *ok_sort = nullptr;
+    int32_t *ok_inv = nullptr, *ok_row = nullptr, *ok_rest = nullptr, *ok_loc = nullptr;
+    unsigned long long *ok_stamp = nullptr, ok_launch = 0;
+    long long *ok_seg = nullptr, *ok_aoff = nullptr;
+    int ok_lvl_cap = 0, ok_set_cap = 0;
+    char *ok_arena = nullptr;
+    size_t ok_arena_cap = 0;
+    std::vector<long long> ok_hseg, ok_haoff;
 };
 
 // components (and systems) of at most this many bodies run in the batched
@@ -1070,6 +1084,131 @@ static int process(cc_ctx *c, int d, double h, const LevelAlloc *parent)
     return CC_OK;
 }
 
+// ------------------------------------------------------------ the OK split
+// Bytes of one set's arena: a node of np pairs takes at most 55 np + 192
+// bytes (fast flags, particle list, child list, flags, incoming lists and
+// runs; nS <= 2 np), and a path of the tree holds at most max_depth + 1
+// nodes, none larger than the set's outer-level fast list.
+static size_t ok_arena_bytes(long long np, int max_depth)
+{
+    if (np <= 0) return 0;
+    return (size_t)4096 + ((size_t)55 * (size_t)np + 192) * (size_t)(max_depth + 1);
+}
+
+static int ok_grow(cc_ctx *c, void **p, size_t bytes)
+{
+    if (*p) cudaFree(*p);
+    *p = nullptr;
+    if (cudaMalloc(p, bytes) != cudaSuccess) {
+        cudaGetLastError();
+        *p = nullptr;
+        return fail(c, CC_E_NOMEM, "device allocation failed (OK split)");
+    }
+    return CC_OK;
+}
+
+// One outer step of the OK split (Sec. 4.2) on level 0 (every set a system):
+// the outer level here, the rest of the recursion in k_ok_tree.
+static int ok_step(cc_ctx *c)
+{
+    LevelAlloc &a = c->lv[0];
+    const cudaStream_t s = c->stream;
+    const double dt = c->p.dt;
+    const int total = a.L.total, ns = a.L.nsets;
+    if (c->ok_lvl_cap < total + 1) {
+        CC_TRY(ok_grow(c, (void **)&c->ok_inv, (size_t)(total + 1) * 4));
+        CC_TRY(ok_grow(c, (void **)&c->ok_row, (size_t)(total + 1) * 4));
+        CC_TRY(ok_grow(c, (void **)&c->ok_rest, (size_t)(total + 1) * 4));
+        CC_TRY(ok_grow(c, (void **)&c->ok_loc, (size_t)(total + 1) * 4));
+        CC_TRY(ok_grow(c, (void **)&c->ok_stamp, (size_t)(total + 1) * 8));
+        CC_CUDA(c, cudaMemsetAsync(c->ok_stamp, 0, (size_t)(total + 1) * 8, s));
+        c->ok_lvl_cap = total + 1;
+    }
+    if (c->ok_set_cap < ns + 1) {
+        CC_TRY(ok_grow(c, (void **)&c->ok_seg, (size_t)(ns + 1) * 8));
+        CC_TRY(ok_grow(c, (void **)&c->ok_aoff, (size_t)(ns + 1) * 8));
+        c->ok_set_cap = ns + 1;
+    }
+    if (c->ok_cap == 0) {
+        c->ok_cap = std::max<long long>(4096, (long long)total * 4);
+        CC_TRY(ok_grow(c, (void **)&c->ok_edges, (size_t)c->ok_cap * 8));
+        CC_TRY(ok_grow(c, (void **)&c->ok_dir, (size_t)c->ok_cap * 16));
+        CC_TRY(ok_grow(c, &c->ok_sort, edge_sort_scratch_bytes(2 * c->ok_cap)));
+    }
+    // the outer level's tau over every pair of each set, its fast pairs
+    const TauParams P = tau_params(c, dt);
+    Level UL = a.L;
+    UL.tile_off = a.tau_off[TAU_VAR_128];
+    const long long ntiles = a.tau_blocks[TAU_VAR_128];
+    if (ntiles > 0x7fffffff) return fail(c, CC_E_ARG, "set too large for the tile grid");
+    // (the edge kernel takes its list slots from the edge counter: it starts
+    // at zero, and the count goes to the statistics from the host)
+    long long ne = 0;
+    for (int pass = 0; pass < 2; ++pass) {
+        CC_CUDA(c, cudaMemsetAsync(&c->d_ctr->edges, 0, 8, s));
+        launch_init_parent(a.L, nullptr, s);
+        launch_tau_hook(UL, (int)ntiles, P, TAU_VAR_128, c->d_ctr, c->ok_edges, c->ok_cap, c->d_near_ij,
+                        c->d_near_tau, c->near_cap, s);
+        unsigned long long e1 = 0;
+        CC_CUDA(c, cudaMemcpyAsync(&e1, &c->d_ctr->edges, 8, cudaMemcpyDeviceToHost, s));
+        CC_CUDA(c, cudaStreamSynchronize(s));
+        CC_CUDA(c, cudaMemsetAsync(&c->d_ctr->edges, 0, 8, s));
+        ne = (long long)e1;
+        if (ne <= c->ok_cap) break;
+        // more fast pairs than room: grow and redo
+        c->ok_cap = 2 * ne;
+        CC_TRY(ok_grow(c, (void **)&c->ok_edges, (size_t)c->ok_cap * 8));
+        CC_TRY(ok_grow(c, (void **)&c->ok_dir, (size_t)c->ok_cap * 16));
+        CC_TRY(ok_grow(c, &c->ok_sort, edge_sort_scratch_bytes(2 * c->ok_cap)));
+    }
+    launch_ok_level(a.L, c->ok_edges, ne, c->ok_inv, c->ok_dir, c->ok_sort, c->ok_row, c->ok_rest, c->ok_seg,
+                    c->d_ctr, s);
+    // each set's arena, from its segment of the fast list
+    c->ok_hseg.resize(ns + 1);
+    c->ok_haoff.resize(ns + 1);
+    CC_CUDA(c, cudaMemcpyAsync(c->ok_hseg.data(), c->ok_seg, (size_t)(ns + 1) * 8, cudaMemcpyDeviceToHost, s));
+    CC_CUDA(c, cudaStreamSynchronize(s));
+    size_t off = 0;
+    unsigned long long nonempty = 0;
+    for (int q = 0; q < ns; ++q) {
+        c->ok_haoff[q] = (long long)off;
+        const long long np = c->ok_hseg[q + 1] - c->ok_hseg[q];
+        nonempty += np > 0 ? 1 : 0;
+        off += (ok_arena_bytes(np, c->p.max_depth) + 255) / 256 * 256;
+    }
+    c->ok_haoff[ns] = (long long)off;
+    if (off > c->ok_arena_cap) {
+        CC_TRY(ok_grow(c, (void **)&c->ok_arena, off));
+        c->ok_arena_cap = off;
+    }
+    CC_CUDA(c, cudaMemcpyAsync(c->ok_aoff, c->ok_haoff.data(), (size_t)(ns + 1) * 8, cudaMemcpyHostToDevice, s));
+    // the outer level's counts (the tree counts its own nodes on the device)
+    c->st.splits += (unsigned long long)ns;
+    c->st.tau_pairs += (unsigned long long)a.pairs;
+    c->st.tau_evaluated += (unsigned long long)a.pairs;
+    c->st.kick_pairs += (unsigned long long)a.pairs - (unsigned long long)ne;
+    c->st.components += nonempty;
+    c->st.edges += (unsigned long long)ne;
+    const OkView okv{c->ok_row, c->ok_dir};
+    Level KL = a.L;
+    KL.itile_off = a.k64_off[0];
+    const double G = c->p.G, eps2 = c->p.eps * c->p.eps;
+    for (int half = 0; half < 2; ++half) {
+        if (half == 1) {
+            // D_{h/2} of the particles without a fast pair, K_h of every
+            // slow pair of each set (the fast ones masked), D_{h/2}
+            launch_drift_labels(a.L, c->ok_rest, 0.5 * dt, s);
+            launch_kick(KL, a.L.gid, (int)a.k64_blocks[0], G, eps2, dt, 0, c->d_ctr, s, nullptr, &okv);
+            launch_drift_labels(a.L, c->ok_rest, 0.5 * dt, s);
+        }
+        if (ne > 0)
+            launch_ok_tree(a.L, c->ok_edges, c->ok_seg, c->ok_aoff, c->ok_arena, c->ok_stamp, c->ok_loc,
+                           (++c->ok_launch) << 40, 0.5 * dt, 1, c->p.max_depth, P, G, eps2, c->d_ctr,
+                           c->d_near_ij, c->d_near_tau, c->near_cap, s);
+    }
+    return CC_OK;
+}
+
 // level-0 layout of the systems
 static int setup_systems(cc_ctx *c)
 {
@@ -1096,7 +1235,7 @@ static int setup_systems(cc_ctx *c)
     c->sys_batch = false;
     const int smax = small_max(c);
     const int nmin = c->p.kepler ? 3 : 2;
-    bool all = smax > 32 && c->p.max_depth >= 0;
+    bool all = smax > 32 && c->p.max_depth >= 0 && c->p.split != CC_SPLIT_OK;
     for (int32_t z : sizes) all = all && z >= nmin && z <= smax;
     if (all) {
         const int ns = (int)sizes.size();
@@ -1204,8 +1343,10 @@ int cc_init(cc_ctx **out, int64_t n, const double *m, const double *x3, const do
     if (!(p->G > 0.0) || !(p->eps >= 0.0) || !finite_pos(p->eta) || !finite_pos(p->dt) || p->max_depth < 0 ||
         p->max_depth > 200 || (p->precision != CC_PREC_FP64 && p->precision != CC_PREC_MIXED) ||
         (p->kepler && p->eps != 0.0) || p->s_small < CC_SMALL_AUTO || p->s_small > BATCH_NMAX || p->edge_rec_max < 0 ||
-        p->fault_test < 0 || p->fault_test > 2 || (p->split != CC_SPLIT_CC && p->split != CC_SPLIT_HOLD) ||
-        (p->split == CC_SPLIT_HOLD && p->kepler) || !(p->theta >= 0.0) || !std::isfinite(p->theta) ||
+        p->fault_test < 0 || p->fault_test > 2 ||
+        (p->split != CC_SPLIT_CC && p->split != CC_SPLIT_HOLD && p->split != CC_SPLIT_OK) ||
+        (p->split != CC_SPLIT_CC && p->kepler) ||
+        (p->split == CC_SPLIT_OK && p->precision != CC_PREC_FP64) || !(p->theta >= 0.0) || !std::isfinite(p->theta) ||
         (p->theta > 0.0 && (p->split != CC_SPLIT_CC || p->com_max < 2 || p->com_max > COM_MAX_MEMBERS))) {
         g_init_err = "cc_init: invalid parameters";
         return CC_E_ARG;
@@ -1350,6 +1491,8 @@ int cc_evolve(cc_ctx *c, double t_end, double eta)
             launch_batch(c->lv[0].L, c->d_iota, tk + ns, tk + 2 * ns, tk, tk + 3 * ns, ns, SP, c->d_ctr,
                          tk + 3 * ns + 1, c->d_near_ij, c->d_near_tau, c->near_cap, c->nsm, c->batch_scr, c->stream);
             c->st.small_tasks += (unsigned long long)ns;
+        } else if (c->p.split == CC_SPLIT_OK) {
+            rc = ok_step(c);
         } else {
             rc = process(c, 0, c->p.dt, nullptr);
         }
@@ -1631,7 +1774,9 @@ int cc_destroy(cc_ctx *c)
     free_level(c->unit);
     void *ptrs[] = {c->d_x3, c->d_v3, c->d_m, c->d_ctr, c->d_near_ij, c->d_near_tau, c->d_partial,
                     c->tmp, c->seg_scratch, c->d_sys_off, c->d_bad, c->d_kpart, c->d_perm, c->d_box,
-                    c->batch_scr, c->d_sys_tasks, c->d_iota};
+                    c->batch_scr, c->d_sys_tasks, c->d_iota, c->ok_edges, c->ok_dir, c->ok_sort,
+                    c->ok_inv, c->ok_row, c->ok_rest, c->ok_loc, c->ok_stamp, c->ok_seg, c->ok_aoff,
+                    c->ok_arena};
     for (void *q : ptrs)
         if (q) cudaFree(q);
     delete c;

@@ -326,8 +326,28 @@ struct ComView {
     const int32_t *K;           // per set: eligible components
     const unsigned char *far;   // far matrices, K x K bytes per set
 };
+// OK split (Sec. 4.2): the fast pairs of the outer level, both directions
+// sorted by (row, partner) in col (pairs), rows delimited by row_ptr
+struct OkView {
+    const int32_t *row_ptr;  // [total + 1]
+    const int32_t *col;      // (row, partner) pairs
+};
 void launch_kick(const Level &L, const int32_t *label, int nitiles, double G, double eps2, double h,
-                 int variant, DevCounters *ctr, cudaStream_t s, const ComView *com = nullptr);
+                 int variant, DevCounters *ctr, cudaStream_t s, const ComView *com = nullptr,
+                 const OkView *okv = nullptr);
+// the OK split's outer level after its tau kernel wrote the fast pairs
+// (particle ids, count ne): pairs to packed indices and sorted, both
+// directions sorted (dir, 2 ne pairs), row pointers, the drift flags of the
+// particles without a fast partner (rest), each set's segment of the list
+void launch_ok_level(const Level &L, int32_t *edges, long long ne, int32_t *inv, int32_t *dir, void *sort_scratch,
+                     int32_t *row_ptr, int32_t *rest, long long *seg, DevCounters *ctr, cudaStream_t s);
+// the rest of the OK recursion: one CTA per set evolves (F, I_F) of its
+// segment of the sorted fast list at pivot h0 (depth depth0), node arrays in
+// the set's arena [arena_off[s], arena_off[s+1])
+void launch_ok_tree(const Level &L, const int32_t *list, const long long *seg, const long long *arena_off,
+                    char *arena, unsigned long long *stamp, int32_t *loc, unsigned long long stamp_base, double h0,
+                    int depth0, int max_depth, const TauParams &P, double G, double eps2, DevCounters *ctr,
+                    int32_t *near_ij, double *near_tau, long long near_cap, cudaStream_t s);
 void launch_energy(const double *x3, const double *v3, const double *m, long long n, double G, double eps2,
                    const int32_t *sys_off /* nsys + 1 offsets, or null */, int nsys, double *partial /*[nblk*8]*/,
                    int nblk, cudaStream_t s);

@@ -1,0 +1,476 @@
+// cc_ok.cu -- the OK split (arXiv:1407.7105 Sec. 4.2): the interactions of a
+// set, not its particles, partitioned by tau(i,j) against the pivot h.
+//
+// Reading: the interaction list I of a particle set S (at the outer step:
+// every pair of S) splits at pivot h into the fast list I_F = {tau(i,j) < h}
+// and the slow list I_S; F = the particles of I_F.  One step is
+//     E_{h/2,T_F+V_{I_F}} D_{h/2,T_{S\F}} K_{h,V_{I_S}} D_{h/2,T_{S\F}} E_{h/2,T_F+V_{I_F}},
+// each E the same split of (F, I_F) at h/2.  The outer step's level (every
+// pair of each set) runs on the level kernels (tau with an edge list; the
+// FP64 kick with the fast pairs masked); the rest of the recursion, whose
+// lists are the fast pairs, runs in k_ok_tree: one CTA per set takes its
+// set's whole recursion tree depth first, with an explicit stack of nodes
+// and each node's arrays in the set's arena (stack discipline).
+//
+// FP64 only, every operation an explicit IEEE one in the oracle's order: a
+// pair's tau from (x_a - x_b, v_a - v_b), a < b; a particle's kick sums its
+// slow partners in ascending index (pairs (j, i), j < i, in the list's
+// order, then (i, j)), then v += h a; drifts x += (h/2) v.
+#include "cc_internal.cuh"
+
+namespace cc {
+
+// ------------------------------------------------------------ level helpers
+__global__ void k_ok_inv(Level L, int32_t *inv)
+{
+    const int k = blockIdx.x * blockDim.x + threadIdx.x;
+    if (k >= L.total) return;
+    const int g = L.gid[k];
+    if (g >= 0) inv[g] = k;
+}
+
+// particle-id pairs -> packed-index pairs (packing keeps id order in a set)
+__global__ void k_ok_to_packed(int32_t *edges, long long ne, const int32_t *inv)
+{
+    const long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (e >= ne) return;
+    edges[2 * e] = inv[edges[2 * e]];
+    edges[2 * e + 1] = inv[edges[2 * e + 1]];
+}
+
+// both directions of each pair: (a, b) and (b, a)
+__global__ void k_ok_directed(const int32_t *edges, long long ne, int32_t *dir)
+{
+    const long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (e >= ne) return;
+    const int a = edges[2 * e], b = edges[2 * e + 1];
+    dir[4 * e] = a;
+    dir[4 * e + 1] = b;
+    dir[4 * e + 2] = b;
+    dir[4 * e + 3] = a;
+}
+
+// first entry >= key in the first column of a sorted pair list
+__device__ __forceinline__ long long lower_first(const int32_t *p, long long n, int key)
+{
+    long long lo = 0, hi = n;
+    while (lo < hi) {
+        const long long mid = (lo + hi) >> 1;
+        if (p[2 * mid] < key) lo = mid + 1;
+        else hi = mid;
+    }
+    return lo;
+}
+
+// row pointers of the directed adjacency (rows = packed indices 0..total)
+// and the drift flags of the outer level: rest[k] = 1 for a particle with
+// no fast partner (it drifts at this level)
+__global__ void k_ok_rows(Level L, const int32_t *dir, long long nd, int32_t *row_ptr, int32_t *rest,
+                          DevCounters *ctr)
+{
+    const int k = blockIdx.x * blockDim.x + threadIdx.x;
+    if (k > L.total) return;
+    row_ptr[k] = (int32_t)lower_first(dir, nd, k);
+    if (k == L.total) return;
+    const bool in = L.gid[k] >= 0;
+    const long long r1 = lower_first(dir, nd, k + 1);
+    const int r = in && r1 == row_ptr[k] ? 1 : 0;
+    rest[k] = r;
+    if (r) atomicAdd(&ctr->small_drifts, 2ull);
+}
+
+// segment of each set in the sorted fast list (sets are packed in order)
+__global__ void k_ok_segments(Level L, const int32_t *edges, long long ne, long long *seg)
+{
+    const int s = blockIdx.x * blockDim.x + threadIdx.x;
+    if (s > L.nsets) return;
+    seg[s] = s == L.nsets ? ne : lower_first(edges, ne, L.set_start[s]);
+}
+
+void launch_ok_level(const Level &L, int32_t *edges, long long ne, int32_t *inv, int32_t *dir, void *sort_scratch,
+                     int32_t *row_ptr, int32_t *rest, long long *seg, DevCounters *ctr, cudaStream_t s)
+{
+    k_ok_inv<<<(L.total + 255) / 256, 256, 0, s>>>(L, inv);
+    int launches = 1;
+    int bits = 0;
+    while (bits < 31 && (1ll << bits) <= (long long)L.total) ++bits;
+    if (ne > 0) {
+        k_ok_to_packed<<<(int)((ne + 255) / 256), 256, 0, s>>>(edges, ne, inv);
+        launch_sort_edges(edges, ne, bits, sort_scratch, s);
+        k_ok_directed<<<(int)((ne + 255) / 256), 256, 0, s>>>(edges, ne, dir);
+        launch_sort_edges(dir, 2 * ne, bits, sort_scratch, s);
+        launches += 2;
+    }
+    k_ok_rows<<<(L.total + 1 + 255) / 256, 256, 0, s>>>(L, dir, 2 * ne, row_ptr, rest, ctr);
+    k_ok_segments<<<(L.nsets + 1 + 255) / 256, 256, 0, s>>>(L, edges, ne, seg);
+    CC_COUNT_LAUNCH(launches + 2);
+}
+
+// ------------------------------------------------------------ the tree
+constexpr int KO_T = 256;
+constexpr int KO_MAXF = 72;  // nested nodes of one tree (DERR_DEPTH beyond)
+
+enum : int { KO_SPLIT = 0, KO_H1 = 1, KO_DKD = 2, KO_H2 = 3, KO_DONE = 4 };
+
+struct OkNode {
+    const int32_t *list;  // (a, b) pairs, packed indices, sorted
+    unsigned char *fast;  // [np] tau < h
+    int32_t *child;       // [2 nf] the fast pairs, in list order
+    int32_t *S;           // [nS] the particles of the list
+    unsigned char *isF;   // [nS] particle of a fast pair
+    int32_t *in_start;    // [nS + 1] incoming slow pairs by particle
+    int32_t *in_cur;      // [nS] placement cursor
+    int32_t *in_list;     // [ns] their smaller partner, ascending
+    int32_t *out_beg, *out_end;  // [nS] the particle's run of pairs (i, *) in the list
+    double h;
+    size_t mark;  // arena offset at entry
+    int np, nf, nS, depth, ph;
+};
+
+struct OkShared {
+    OkNode fr[KO_MAXF];
+    size_t top, cap;
+    unsigned long long stamp;
+    int nf, nS, bad, wsum[KO_T / 32];
+};
+
+struct OkArgs {
+    double *x, *y, *z, *vx, *vy, *vz;
+    const double *m;
+    const int32_t *gid;
+    const int32_t *list;     // the outer level's fast list, sorted, all sets
+    const long long *seg;    // [nsets + 1] each set's segment
+    const long long *arena_off;  // [nsets + 1] bytes
+    char *arena;
+    unsigned long long *stamp;   // [total] node stamp of a particle's last claim
+    int32_t *loc;                // [total] the particle's position in its node's S
+    unsigned long long stamp_base;
+    double h0;  // pivot of the tree's root (dt/2)
+    int depth0, max_depth;
+    TauParams P;
+    double G, eps2;
+    DevCounters *ctr;
+    int32_t *near_ij;
+    double *near_tau;
+    long long near_cap;
+};
+
+// arena allocation by thread 0 (16-byte aligned); sets bad on overflow
+__device__ __forceinline__ char *ok_alloc(OkShared &sh, char *base, size_t bytes, DevCounters *ctr)
+{
+    const size_t at = (sh.top + 15) & ~(size_t)15;
+    if (at + bytes > sh.cap) {
+        if (!sh.bad) raise_err(ctr, DERR_SMALL_OVERFLOW);
+        sh.bad = 1;
+        return base;
+    }
+    sh.top = at + bytes;
+    return base + at;
+}
+
+// exclusive prefix of one value per thread over the CTA; total returned
+__device__ __forceinline__ int ok_scan(OkShared &sh, int v, int &total)
+{
+    const int tid = threadIdx.x, lane = tid & 31, w = tid >> 5;
+    int inc = v;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const int y = __shfl_up_sync(0xffffffffu, inc, o);
+        if (lane >= o) inc += y;
+    }
+    if (lane == 31) sh.wsum[w] = inc;
+    __syncthreads();
+    int off = 0;
+    total = 0;
+#pragma unroll
+    for (int q = 0; q < KO_T / 32; ++q) {
+        if (q < w) off += sh.wsum[q];
+        total += sh.wsum[q];
+    }
+    __syncthreads();
+    return off + inc - v;
+}
+
+__device__ __forceinline__ void ok_term(const OkArgs &A, int i, int j, double &ax, double &ay, double &az)
+{
+    const double dx0 = __dsub_rn(A.x[j], A.x[i]);
+    const double dx1 = __dsub_rn(A.y[j], A.y[i]);
+    const double dx2 = __dsub_rn(A.z[j], A.z[i]);
+    const double r2 = __dadd_rn(__dadd_rn(__dadd_rn(__dmul_rn(dx0, dx0), __dmul_rn(dx1, dx1)), __dmul_rn(dx2, dx2)),
+                                A.eps2);
+    const double rinv3 = __ddiv_rn(1.0, __dmul_rn(r2, __dsqrt_rn(r2)));
+    const double w = __dmul_rn(__dmul_rn(A.G, A.m[j]), rinv3);
+    ax = __dadd_rn(ax, __dmul_rn(w, dx0));
+    ay = __dadd_rn(ay, __dmul_rn(w, dx1));
+    az = __dadd_rn(az, __dmul_rn(w, dx2));
+}
+
+__device__ __forceinline__ void ok_drift(const OkArgs &A, int i, double dt)
+{
+    A.x[i] = __dadd_rn(A.x[i], __dmul_rn(dt, A.vx[i]));
+    A.y[i] = __dadd_rn(A.y[i], __dmul_rn(dt, A.vy[i]));
+    A.z[i] = __dadd_rn(A.z[i], __dmul_rn(dt, A.vz[i]));
+}
+
+// the split of a node: fast flags, the child list (fast pairs in order), the
+// particle list S with its F flags, outgoing runs, and the incoming slow
+// pairs of each particle in ascending partner (a stable counting sort)
+__device__ void ok_split(OkShared &sh, OkNode &N, const OkArgs &A, char *base, unsigned long long *cnt)
+{
+    const int tid = threadIdx.x, lane = tid & 31;
+    const int np = N.np;
+    TauParams P = A.P;
+    P.h = N.h;
+    if (tid == 0) {
+        sh.nf = 0;
+        sh.nS = 0;
+        sh.stamp += 1;
+        N.fast = (unsigned char *)ok_alloc(sh, base, (size_t)np, A.ctr);
+        N.S = (int32_t *)ok_alloc(sh, base, (size_t)8 * np, A.ctr);
+    }
+    __syncthreads();
+    if (sh.bad) return;
+    const unsigned long long stamp = sh.stamp;
+    int nf_local = 0;
+    for (int k = tid; k < np; k += KO_T) {
+        const int a = N.list[2 * k], b = N.list[2 * k + 1];
+        const double tau =
+            tau_fp64(__dsub_rn(A.x[a], A.x[b]), __dsub_rn(A.y[a], A.y[b]), __dsub_rn(A.z[a], A.z[b]),
+                     __dsub_rn(A.vx[a], A.vx[b]), __dsub_rn(A.vy[a], A.vy[b]), __dsub_rn(A.vz[a], A.vz[b]), A.m[a],
+                     A.m[b], P);
+        if (fabs(tau - P.h) < P.near_tol * P.h) {
+            const unsigned long long z = atomicAdd(&A.ctr->near_pairs, 1ull);
+            if ((long long)z < A.near_cap) {
+                const int ga = A.gid[a], gb = A.gid[b];
+                A.near_ij[2 * z] = ga < gb ? ga : gb;
+                A.near_ij[2 * z + 1] = ga < gb ? gb : ga;
+                A.near_tau[z] = tau;
+            }
+        }
+        const bool f = tau < P.h;
+        N.fast[k] = f ? 1 : 0;
+        nf_local += f ? 1 : 0;
+        // the particles of the list: the first claim of this node's stamp
+        // appends the particle
+        for (int q = 0; q < 2; ++q) {
+            const int e = q == 0 ? a : b;
+            if (atomicExch(&A.stamp[e], stamp) != stamp) {
+                const int li = atomicAdd(&sh.nS, 1);
+                N.S[li] = e;
+                A.loc[e] = li;
+            }
+        }
+    }
+    atomicAdd(&sh.nf, nf_local);
+    __syncthreads();
+    const int nf = sh.nf, nS = sh.nS;
+    if (tid == 0) {
+        N.nf = nf;
+        N.nS = nS;
+        N.child = (int32_t *)ok_alloc(sh, base, (size_t)8 * nf, A.ctr);
+        N.isF = (unsigned char *)ok_alloc(sh, base, (size_t)nS, A.ctr);
+        N.in_start = (int32_t *)ok_alloc(sh, base, (size_t)4 * (nS + 1), A.ctr);
+        N.in_cur = (int32_t *)ok_alloc(sh, base, (size_t)4 * nS, A.ctr);
+        N.in_list = (int32_t *)ok_alloc(sh, base, (size_t)4 * (np - nf), A.ctr);
+        N.out_beg = (int32_t *)ok_alloc(sh, base, (size_t)4 * nS, A.ctr);
+        N.out_end = (int32_t *)ok_alloc(sh, base, (size_t)4 * nS, A.ctr);
+        cnt[0] += 1;                       // split
+        cnt[1] += (unsigned long long)np;  // tau pairs
+        cnt[2] += nf > 0 ? 1 : 0;          // components (non-empty fast lists)
+        cnt[3] += (unsigned long long)np;  // tau evaluated, FP64
+    }
+    __syncthreads();
+    if (sh.bad) return;
+    for (int li = tid; li < nS; li += KO_T) {
+        N.isF[li] = 0;
+        N.in_start[li] = 0;
+        N.out_beg[li] = 0;
+        N.out_end[li] = 0;
+    }
+    __syncthreads();
+    // fast flags of particles, outgoing runs, incoming slow counts
+    for (int k = tid; k < np; k += KO_T) {
+        const int a = N.list[2 * k], b = N.list[2 * k + 1];
+        const int la = A.loc[a], lb = A.loc[b];
+        if (N.fast[k]) {
+            N.isF[la] = 1;
+            N.isF[lb] = 1;
+        } else {
+            atomicAdd(&N.in_start[lb], 1);
+        }
+        if (k == 0 || N.list[2 * (k - 1)] != a) N.out_beg[la] = k;
+        if (k == np - 1 || N.list[2 * (k + 1)] != a) N.out_end[la] = k + 1;
+    }
+    __syncthreads();
+    // child list: the fast pairs in list order (chunks of KO_T, one per thread)
+    int base_f = 0;
+    for (int c0 = 0; c0 < np; c0 += KO_T) {
+        const int k = c0 + tid;
+        const int f = k < np ? N.fast[k] : 0;
+        int tot;
+        const int at = ok_scan(sh, f, tot) + base_f;
+        if (f) {
+            N.child[2 * at] = N.list[2 * k];
+            N.child[2 * at + 1] = N.list[2 * k + 1];
+        }
+        base_f += tot;
+    }
+    // incoming starts: exclusive prefix of the counts over S
+    int base_s = 0;
+    for (int c0 = 0; c0 < nS; c0 += KO_T) {
+        const int li = c0 + tid;
+        const int v = li < nS ? N.in_start[li] : 0;
+        int tot;
+        const int at = ok_scan(sh, v, tot) + base_s;
+        if (li < nS) {
+            N.in_start[li] = at;
+            N.in_cur[li] = at;
+        }
+        base_s += tot;
+    }
+    if (tid == 0) N.in_start[nS] = base_s;
+    __syncthreads();
+    // the incoming lists: one warp walks the list in order, ranking the slow
+    // pairs of one particle by lane (stable: ascending smaller partner)
+    if (tid < 32) {
+        const unsigned lt = (1u << lane) - 1u;
+        for (int c0 = 0; c0 < np; c0 += 32) {
+            const int k = c0 + lane;
+            const bool slow = k < np && !N.fast[k];
+            const int key = slow ? A.loc[N.list[2 * k + 1]] : -1 - lane;
+            const unsigned peers = __match_any_sync(0xffffffffu, key);
+            if (slow) N.in_list[N.in_cur[key] + __popc(peers & lt)] = N.list[2 * k];
+            __syncwarp();
+            if (slow && lane == 31 - __clz(peers)) N.in_cur[key] += __popc(peers);
+            __syncwarp();
+        }
+    }
+    __syncthreads();
+}
+
+// D_{h/2} K_{h, slow} D_{h/2} of a node
+__device__ void ok_dkd(OkShared &sh, const OkNode &N, const OkArgs &A, unsigned long long *cnt)
+{
+    const int tid = threadIdx.x;
+    const double hd = 0.5 * N.h;
+    int drifts = 0;
+    for (int li = tid; li < N.nS; li += KO_T)
+        if (!N.isF[li]) {
+            ok_drift(A, N.S[li], hd);
+            ++drifts;
+        }
+    __syncthreads();
+    for (int li = tid; li < N.nS; li += KO_T) {
+        const int i = N.S[li];
+        double ax = 0.0, ay = 0.0, az = 0.0;
+        for (int q = N.in_start[li]; q < N.in_start[li + 1]; ++q) ok_term(A, i, N.in_list[q], ax, ay, az);
+        for (int k = N.out_beg[li]; k < N.out_end[li]; ++k)
+            if (!N.fast[k]) ok_term(A, i, N.list[2 * k + 1], ax, ay, az);
+        A.vx[i] = __dadd_rn(A.vx[i], __dmul_rn(N.h, ax));
+        A.vy[i] = __dadd_rn(A.vy[i], __dmul_rn(N.h, ay));
+        A.vz[i] = __dadd_rn(A.vz[i], __dmul_rn(N.h, az));
+    }
+    __syncthreads();
+    for (int li = tid; li < N.nS; li += KO_T)
+        if (!N.isF[li]) ok_drift(A, N.S[li], hd);
+    atomicAdd((unsigned long long *)&cnt[5], (unsigned long long)(2 * drifts));
+    if (tid == 0) cnt[4] += (unsigned long long)(N.np - N.nf);  // kick pairs
+    __syncthreads();
+}
+
+__global__ void __launch_bounds__(KO_T) k_ok_tree(OkArgs A)
+{
+    __shared__ OkShared sh;
+    __shared__ unsigned long long cnt[6];  // splits, tau, comps, evals, kicks, drifts
+    const int s = blockIdx.x, tid = threadIdx.x;
+    const long long l0 = A.seg[s], l1 = A.seg[s + 1];
+    if (l1 <= l0) return;
+    char *base = A.arena + A.arena_off[s];
+    if (tid < 6) cnt[tid] = 0;
+    if (tid == 0) {
+        sh.top = 0;
+        sh.cap = (size_t)(A.arena_off[s + 1] - A.arena_off[s]);
+        sh.stamp = A.stamp_base + ((unsigned long long)s << 24);
+        sh.bad = 0;
+        OkNode &R = sh.fr[0];
+        R.list = A.list + 2 * l0;
+        R.np = (int)(l1 - l0);
+        R.h = A.h0;
+        R.depth = A.depth0;
+        R.ph = KO_SPLIT;
+        R.mark = 0;
+    }
+    int maxd = A.depth0;
+    int top = 0;
+    __syncthreads();
+    if (A.depth0 > A.max_depth) {
+        if (tid == 0) raise_err(A.ctr, DERR_DEPTH);
+        return;
+    }
+    for (;;) {
+        OkNode &N = sh.fr[top];
+        const int ph = N.ph;
+        __syncthreads();
+        if (ph == KO_SPLIT) {
+            ok_split(sh, N, A, base, cnt);
+            if (tid == 0) N.ph = KO_H1;
+        } else if (ph == KO_H1 || ph == KO_H2) {
+            if (tid == 0) {
+                N.ph = ph == KO_H1 ? KO_DKD : KO_DONE;
+                if (N.nf > 0) {
+                    if (N.depth + 1 > A.max_depth || top + 1 >= KO_MAXF) {
+                        raise_err(A.ctr, DERR_DEPTH);
+                        sh.bad = 1;
+                    } else {
+                        OkNode &C = sh.fr[top + 1];
+                        C.list = N.child;
+                        C.np = N.nf;
+                        C.h = 0.5 * N.h;
+                        C.depth = N.depth + 1;
+                        C.ph = KO_SPLIT;
+                        C.mark = sh.top;
+                    }
+                }
+            }
+            __syncthreads();
+            if (!sh.bad && N.nf > 0) {
+                ++top;
+                if (top + A.depth0 > maxd) maxd = top + A.depth0;
+            }
+        } else if (ph == KO_DKD) {
+            ok_dkd(sh, N, A, cnt);
+            if (tid == 0) N.ph = KO_H2;
+        } else {
+            if (tid == 0) sh.top = N.mark;
+            --top;
+        }
+        __syncthreads();
+        if (sh.bad || top < 0) break;
+    }
+    __syncthreads();
+    if (tid == 0) {
+        atomicAdd(&A.ctr->small_splits, cnt[0]);
+        atomicAdd(&A.ctr->small_tau_pairs, cnt[1]);
+        atomicAdd(&A.ctr->small_components, cnt[2]);
+        atomicAdd(&A.ctr->tau_evals, cnt[3]);
+        atomicAdd(&A.ctr->tau_fp64, cnt[3]);
+        atomicAdd(&A.ctr->small_kick_pairs, cnt[4]);
+        atomicAdd(&A.ctr->small_drifts, cnt[5]);
+        atomicMax(&A.ctr->max_depth_seen, maxd);
+    }
+}
+
+void launch_ok_tree(const Level &L, const int32_t *list, const long long *seg, const long long *arena_off,
+                    char *arena, unsigned long long *stamp, int32_t *loc, unsigned long long stamp_base, double h0,
+                    int depth0, int max_depth, const TauParams &P, double G, double eps2, DevCounters *ctr,
+                    int32_t *near_ij, double *near_tau, long long near_cap, cudaStream_t s)
+{
+    if (L.nsets <= 0) return;
+    OkArgs A{L.x,      L.y,   L.z,    L.vx,       L.vy,  L.vz,      L.m,        L.gid,   list, seg, arena_off,
+             arena,    stamp, loc,    stamp_base, h0,    depth0,    max_depth,  P,       G,    eps2, ctr,
+             near_ij,  near_tau, near_cap};
+    k_ok_tree<<<L.nsets, KO_T, 0, s>>>(A);
+    CC_COUNT_LAUNCH(1);
+}
+
+}  // namespace cc

@@ -426,14 +426,19 @@ struct __align__(16) KickBSmem {
     double xi[3][KB_T];              // the i-tile
     int32_t li[KB_T];
     int32_t ci[KB_T], cj[KB_T];      // centre-of-mass approximation: local eligible indices
+    int32_t okc[KB_T], oke[KB_T];    // OK split: each row's cursor / end in its sorted fast partners
+    uint32_t okm[KB_T];              // OK split: fast partners of each row in the current j-tile
 };
 
-// COM: pairs of far components (ComView) are left out; their kick is the
-// centre-of-mass one that launch_com_apply adds afterwards
-template <bool COM>
+// MODE 1 (centre-of-mass approximation): pairs of far components (ComView)
+// are left out; their kick is the centre-of-mass one that launch_com_apply
+// adds afterwards.  MODE 2 (OK split): the fast pairs (OkView: each row's
+// partners, sorted) are left out, every other pair of the set kicks.
+template <int MODE>
 __global__ void __launch_bounds__(KB_THREADS) k_kick64(Level L, const int32_t *label, double G, double eps2, double h,
-                                                       DevCounters *ctr, ComView cv)
+                                                       DevCounters *ctr, ComView cv, OkView okv)
 {
+    constexpr bool COM = MODE == 1, OKM = MODE == 2;
     __shared__ KickBSmem sm;
     const int tid = threadIdx.x;
     const int s = find_set(L.itile_off, L.nsets, blockIdx.x);
@@ -454,6 +459,10 @@ __global__ void __launch_bounds__(KB_THREADS) k_kick64(Level L, const int32_t *l
         sm.xi[2][tid] = v ? L.z[i] : 0.0;
         sm.li[tid] = v ? label[i] : 0;
         if (COM) sm.ci[tid] = v ? cv.cl[i] : -1;
+        if (OKM) {
+            sm.okc[tid] = v ? okv.row_ptr[i] : 0;
+            sm.oke[tid] = v ? okv.row_ptr[i + 1] : 0;
+        }
     }
     long long fo = 0;
     int Ks = 0;
@@ -480,12 +489,31 @@ __global__ void __launch_bounds__(KB_THREADS) k_kick64(Level L, const int32_t *l
             if (tid < KB_T) sm.cj[tid] = tid < jn ? cv.cl[start + jl0 + tid] : -1;
             __syncthreads();
         }
+        if (OKM) {
+            // the row's fast partners inside this j-tile (partners ascend, so
+            // the cursor only moves forward)
+            if (tid < KB_T) {
+                const int jb = start + jl0;
+                uint32_t mk = 0u;
+                int q = sm.okc[tid];
+                const int qe = sm.oke[tid];
+                while (q < qe && okv.col[2 * q + 1] < jb + jn) {
+                    const int d = okv.col[2 * q + 1] - jb;
+                    if (d >= 0) mk |= 1u << d;
+                    ++q;
+                }
+                sm.okc[tid] = q;
+                sm.okm[tid] = mk;
+            }
+            __syncthreads();
+        }
 #pragma unroll
         for (int q = 0; q < KB_T * KB_T / KB_THREADS; ++q) {
             const int pidx = tid + q * KB_THREADS, ii = pidx >> 5, jj = pidx & 31;
             bool use = ii < ni && jj < jn && il0 + ii != jl0 + jj && sm.li[ii] != sm.j.lab[st][jj];
             if (COM && use && sm.ci[ii] >= 0 && sm.cj[jj] >= 0)
                 use = cv.far[fo + (long long)sm.ci[ii] * Ks + sm.cj[jj]] == 0;
+            if (OKM && use) use = ((sm.okm[ii] >> jj) & 1u) == 0u;
             const double dx0 = __dsub_rn(sm.j.col[st][0][jj], sm.xi[0][ii]);
             const double dx1 = __dsub_rn(sm.j.col[st][1][jj], sm.xi[1][ii]);
             const double dx2 = __dsub_rn(sm.j.col[st][2][jj], sm.xi[2][ii]);
@@ -517,14 +545,18 @@ __global__ void __launch_bounds__(KB_THREADS) k_kick64(Level L, const int32_t *l
 }
 
 void launch_kick(const Level &L, const int32_t *label, int nitiles, double G, double eps2, double h,
-                 int variant, DevCounters *ctr, cudaStream_t s, const ComView *com)
+                 int variant, DevCounters *ctr, cudaStream_t s, const ComView *com, const OkView *okv)
 {
     (void)variant;  // one shape: 32-body tiles (the prefix of variant 0)
     if (nitiles <= 0) return;
-    if (com && com->cl)
-        k_kick64<true><<<nitiles, KB_THREADS, 0, s>>>(L, label, G, eps2, h, ctr, *com);
+    const ComView nc{nullptr, nullptr, nullptr, nullptr};
+    const OkView no{nullptr, nullptr};
+    if (okv && okv->row_ptr)
+        k_kick64<2><<<nitiles, KB_THREADS, 0, s>>>(L, label, G, eps2, h, ctr, nc, *okv);
+    else if (com && com->cl)
+        k_kick64<1><<<nitiles, KB_THREADS, 0, s>>>(L, label, G, eps2, h, ctr, *com, no);
     else
-        k_kick64<false><<<nitiles, KB_THREADS, 0, s>>>(L, label, G, eps2, h, ctr, ComView{nullptr, nullptr, nullptr, nullptr});
+        k_kick64<0><<<nitiles, KB_THREADS, 0, s>>>(L, label, G, eps2, h, ctr, nc, no);
     CC_COUNT_LAUNCH(1);
 }
 
