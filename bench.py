@@ -330,17 +330,20 @@ def other_configs(cc, dev, stream, seed, l2_flush):
             ("systems", 0, [("mixed", 0.0), ("fp64", 0.0)]),
             # the HOLD method (Sec. 2.1) on the same kernels and the bench's
             # own workload: the paper's comparison of the two splits
-            ("hold", N_BODY, [("mixed", 0.0), ("fp64", 0.0)]))
+            ("hold", N_BODY, [("mixed", 0.0), ("fp64", 0.0)]),
+            # the OK split (Sec. 4.2, FP64 only) on the bench's workload
+            ("ok", N_BODY, [("fp64", 0.0)]))
     for wl, n, forms in plan:
         a = _ap.Namespace(workload=wl, n=n, nsys=4096)
-        if wl == "hold":
+        if wl in ("hold", "ok"):
             a.workload = "plummer"
         m, x, v, sys_off = make_workload(a, seed, dev)
         dm, dx, dv = (torch.tensor(q, device=dev) for q in (m, x, v))
         rows = []
         wname = a.workload
         for form, hf in forms:
-            ctx = _ctx(cc, dm, dx, dv, sys_off, wname, form, hf, cc.SMALL_AUTO, split=1 if wl == "hold" else 0)
+            split = {"hold": cc.SPLIT_HOLD, "ok": cc.SPLIT_OK}.get(wl, cc.SPLIT_CC)
+            ctx = _ctx(cc, dm, dx, dv, sys_off, wname, form, hf, cc.SMALL_AUTO, split=split)
             E0, _, _ = ctx.energy()
             dtw = WORKLOADS[wname]["dt"]
             w0 = time.perf_counter()
@@ -361,6 +364,8 @@ def other_configs(cc, dev, stream, seed, l2_flush):
         name = workload_name(m.shape[0], wname, 4096)
         if wl == "hold":
             name = "HOLD split (Sec. 2.1) on: " + name
+        if wl == "ok":
+            name = "OK split (Sec. 4.2) on: " + name
         out[wl] = {"workload": name, "n": int(m.shape[0]), "forms": rows}
     return out
 
