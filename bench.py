@@ -650,6 +650,40 @@ def run_com_sweep(args):
     return 0
 
 
+def run_split_compare(args):
+    """The three splits on the same Plummer spheres (JSON lines): CC, HOLD
+    (Sec. 2.1) and OK (Sec. 4.2), FP64, N = 256 and 1024 at dt = 1/64 to
+    t = 1: ms per step, kick and tau pairs per step, recursion depth and
+    |dE/E| at t = 1 -- the paper's comparison of evaluation counts and
+    energy error (Sec. 3.1, 4.2)."""
+    import torch
+
+    from paper_1407_7105_gb300 import build, cc, ics
+    build.build()
+    dev = torch.device("cuda", 0)
+    dt, steps = 1.0 / 64, 64
+    for n in (256, 1024):
+        m, x, v = ics.plummer(n, seed=args.seed)
+        dm, dx, dv = (torch.tensor(q, device=dev) for q in (m, x, v))
+        for name, split in (("CC", cc.SPLIT_CC), ("HOLD", cc.SPLIT_HOLD), ("OK", cc.SPLIT_OK)):
+            ctx = cc.Context(dm, dx, dv, dt=dt, eta=ETA, split=split)
+            E0, _, _ = ctx.energy()
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            ctx.evolve(steps * dt)
+            torch.cuda.synchronize()
+            sec = time.perf_counter() - t0
+            E1, _, _ = ctx.energy()
+            st = ctx.stats()
+            ctx.close()
+            print(json.dumps({"split_compare": True, "workload": f"Plummer N={n}, equal masses, N-body units, eps=0, eta={ETA}, dt=1/64",
+                              "split": name, "form": "fp64", "steps": steps, "t_end": steps * dt,
+                              "ms_per_step": 1e3 * sec / steps, "kick_pairs_per_step": st["kick_pairs"] / steps,
+                              "tau_pairs_per_step": st["tau_pairs"] / steps, "max_depth": st["max_depth_seen"],
+                              "dE_over_E": (E1 - E0) / abs(E0)}), flush=True)
+    return 0
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -673,6 +707,8 @@ def main():
                     help="energy error of the fractal and the systems batch against eta (mixed form)")
     ap.add_argument("--com-sweep", action="store_true",
                     help="the centre-of-mass approximation of V_CC against the exact kick (both forms, theta sweep)")
+    ap.add_argument("--split-compare", action="store_true",
+                    help="CC, HOLD and OK splits on 256- and 1024-body spheres to t = 1 (FP64)")
     ap.add_argument("--sweep-steps", type=int, default=16)
     ap.add_argument("--seed", type=int, default=1)
     ap.add_argument("--n", type=int, default=None, help="bodies (default per workload)")
@@ -693,6 +729,8 @@ def main():
         return run_eta_sweep(args)
     if args.com_sweep:
         return run_com_sweep(args)
+    if args.split_compare:
+        return run_split_compare(args)
     if world > 1:
         import torch.distributed as dist
         dist.init_process_group("nccl")
