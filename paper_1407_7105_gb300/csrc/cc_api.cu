@@ -1013,7 +1013,7 @@ static int process(cc_ctx *c, int d, double h, const LevelAlloc *parent)
         const int ev = ev_begin(c, 2, side);
         if (smax > 32)
             launch_batch(a.L, a.members, a.comp_start, a.comp_size, a.slist, a.kqueue + 3, bound, SP, c->d_ctr,
-                         a.kqueue + 0, c->d_near_ij, c->d_near_tau, c->near_cap, c->nsm, c->batch_scr, side);
+                         a.kqueue + 0, c->d_near_ij, c->d_near_tau, c->near_cap, c->nsm, c->batch_scr, side, 8);
         else
             launch_small(a.L, a.members, a.comp_start, a.comp_size, a.slist, a.kqueue + 3, bound, SP, c->d_ctr,
                          a.kqueue + 0, c->d_near_ij, c->d_near_tau, c->near_cap, c->nsm, side);
@@ -1061,7 +1061,7 @@ static int process(cc_ctx *c, int d, double h, const LevelAlloc *parent)
                 const int ev = ev_begin(c, 2, side);
                 if (smax > 32)
                     launch_batch(a.L, a.members, a.comp_start, a.comp_size, a.slist, a.kqueue + 3, ns, SP, c->d_ctr,
-                                 a.kqueue + 1, c->d_near_ij, c->d_near_tau, c->near_cap, c->nsm, c->batch_scr, side);
+                                 a.kqueue + 1, c->d_near_ij, c->d_near_tau, c->near_cap, c->nsm, c->batch_scr, side, 8);
                 else
                     launch_small(a.L, a.members, a.comp_start, a.comp_size, a.slist, a.kqueue + 3, ns, SP,
                                  c->d_ctr, a.kqueue + 1, c->d_near_ij, c->d_near_tau, c->near_cap, c->nsm, side);
@@ -1484,12 +1484,15 @@ int cc_evolve(cc_ctx *c, double t_end, double eta)
         int rc = CC_OK;
         if (c->sys_batch) {
             // every system one task: evolve_cc(system, dt), split at depth 0
+            // (8 warps per CTA while there are fewer systems than SMs: each
+            // task's CTA-level phases are then the step's critical path)
             const int ns = (int)c->sys_off.size() - 1;
             int32_t *tk = c->d_sys_tasks;
             CC_CUDA(c, cudaMemsetAsync(tk + 3 * ns + 1, 0, 4, c->stream));
             const SmallParams SP = small_params(c, c->p.dt, 0);
             launch_batch(c->lv[0].L, c->d_iota, tk + ns, tk + 2 * ns, tk, tk + 3 * ns, ns, SP, c->d_ctr,
-                         tk + 3 * ns + 1, c->d_near_ij, c->d_near_tau, c->near_cap, c->nsm, c->batch_scr, c->stream);
+                         tk + 3 * ns + 1, c->d_near_ij, c->d_near_tau, c->near_cap, c->nsm, c->batch_scr, c->stream,
+                         ns < c->nsm ? 8 : 4);
             c->st.small_tasks += (unsigned long long)ns;
         } else if (c->p.split == CC_SPLIT_OK) {
             rc = ok_step(c);

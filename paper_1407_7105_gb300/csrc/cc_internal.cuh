@@ -444,12 +444,13 @@ void launch_kick_mixed(const Level &L, const FFView &F, const int32_t *order, co
 // cc_small.cu
 // the batched kernel (k_batch): tasks tlist[0..*nt_ptr) (task c: packed
 // indices members[t_start[c] ..][0..t_size[c]), ascending id), largest first;
-// queue: a zeroed work counter; scratch: batch_scratch_bytes(nsm)
+// queue: a zeroed work counter; scratch: batch_scratch_bytes(nsm); warps: 4
+// or 8 per CTA (8: shorter CTA-level phases, 4: more resident warp tasks)
 size_t batch_scratch_bytes(int nsm);
 void launch_batch(const Level &L, const int32_t *members, const int32_t *t_start, const int32_t *t_size,
                   const int32_t *tlist, const int32_t *nt_ptr, int nt_bound, const SmallParams &SP, DevCounters *ctr,
                   int *queue, int32_t *near_ij, double *near_tau, long long near_cap, int nsm, char *scratch,
-                  cudaStream_t s);
+                  cudaStream_t s, int warps);
 void launch_small(const Level &L, const int32_t *members, const int32_t *comp_start, const int32_t *comp_size,
                   const int32_t *slist, const int32_t *ns_ptr, int ns_bound, const SmallParams &SP, DevCounters *ctr,
                   int *queue, int32_t *near_ij, double *near_tau, long long near_cap, int nsm, cudaStream_t s);

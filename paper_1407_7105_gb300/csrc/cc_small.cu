@@ -17,6 +17,7 @@
 // The arithmetic of every step is the same as the level kernels', so the
 // FP64 form stays bit-identical to the oracle.
 #include "cc_device.cuh"
+#include <algorithm>
 
 namespace cc {
 
@@ -803,10 +804,12 @@ __global__ void __launch_bounds__(K8_WARPS * 32) k_small(Level L, const int32_t 
 // what a nested frame or a warp task reads.  The DKD runs in set order, the
 // kick's sum over j ascending: the FP64 form adds the same terms in the same
 // order as the level kernels and the oracle.
-constexpr int KM_T = K8_WARPS * 32;
+// A CTA has W warps (template): 8 where a launch holds few tasks (latency:
+// the CTA-level phases of the largest tasks), 4 for the batch of systems
+// (thousands of tasks: more resident warps for the warp tasks).
 constexpr int KM_MAXF = 32;  // nested sets of more than 32 bodies in one task (DERR_DEPTH beyond)
 constexpr size_t KM_FRAME_BYTES = (size_t)BATCH_NMAX * 8;  // cl (int32) + lab (int16) + comp (int16 pairs)
-static_assert(BATCH_NMAX % (2 * KM_T) == 0, "zig-zag rows");
+static_assert(BATCH_NMAX % (2 * 8 * 32) == 0, "zig-zag rows");
 
 enum : int { KM_SPLIT = 0, KM_H1 = 1, KM_B1 = 2, KM_DKD = 3, KM_H2 = 4, KM_B2 = 5, KM_DONE = 6 };
 
@@ -840,19 +843,21 @@ struct KMStage {
 // the slot flags, then the slots (256-byte aligned)
 __host__ __device__ constexpr size_t batch_pool_offset(int nslots) { return ((size_t)nslots * 4 + 255) / 256 * 256; }
 
+template <int W>
 struct KMShared {
     union {
-        K8Warp sw[K8_WARPS];  // warp tasks
-        KMStage st;           // a frame's split or DKD
+        K8Warp sw[W];  // warp tasks
+        KMStage st;    // a frame's split or DKD
     } u;
     KMFrame fr[KM_MAXF];
-    int wsum[2][K8_WARPS];
+    int wsum[2][W];
     int top, bad, qi, hmin, q;
 };
 
 // exclusive prefix sums of two per-entry values over entries 0..n-1 (n <=
 // BATCH_NMAX, entry e = 4 tid + k); totals returned
-__device__ __forceinline__ void km_scan2(KMShared &sh, const int a[4], const int b[4], int ea[4], int eb[4],
+template <int W>
+__device__ __forceinline__ void km_scan2(KMShared<W> &sh, const int a[4], const int b[4], int ea[4], int eb[4],
                                          int &ta, int &tb)
 {
     const int tid = threadIdx.x, lane = tid & 31, w = tid >> 5;
@@ -882,7 +887,7 @@ __device__ __forceinline__ void km_scan2(KMShared &sh, const int a[4], const int
     ta = 0;
     tb = 0;
 #pragma unroll
-    for (int q = 0; q < K8_WARPS; ++q) {
+    for (int q = 0; q < W; ++q) {
         if (q < w) {
             oa += sh.wsum[0][q];
             ob += sh.wsum[1][q];
@@ -902,9 +907,11 @@ __device__ __forceinline__ void km_scan2(KMShared &sh, const int a[4], const int
 
 // the split of the frame's set at F.h (see above); fills cl, lab, comp and
 // the frame's counts
-__device__ void km_split(KMShared &sh, KMFrame &F, const SView V, const SmallParams &SP, float etah, DevCounters *ctr,
-                         const NearLog &nl, SmallCnt &cn)
+template <int W>
+__device__ void km_split(KMShared<W> &sh, KMFrame &F, const SView V, const SmallParams &SP, float etah,
+                         DevCounters *ctr, const NearLog &nl, SmallCnt &cn)
 {
+    constexpr int KM_T = W * 32;
     KMStage &T = sh.u.st;
     const int tid = threadIdx.x, lane = tid & 31;
     const int n = F.n;
@@ -1060,8 +1067,8 @@ __device__ void km_split(KMShared &sh, KMFrame &F, const SView V, const SmallPar
         nkep += __shfl_down_sync(FULL, nkep, o);
         single += __shfl_down_sync(FULL, single, o);
     }
-    __shared__ unsigned long long s_inner[K8_WARPS];
-    __shared__ int s_kep[K8_WARPS], s_single[K8_WARPS];
+    __shared__ unsigned long long s_inner[W];
+    __shared__ int s_kep[W], s_single[W];
     if (lane == 0) {
         s_inner[tid >> 5] = inner;
         s_kep[tid >> 5] = nkep;
@@ -1090,7 +1097,7 @@ __device__ void km_split(KMShared &sh, KMFrame &F, const SView V, const SmallPar
     if (tid == 0) {
         unsigned long long in = 0;
         int kp = 0, sg = 0;
-        for (int q = 0; q < K8_WARPS; ++q) {
+        for (int q = 0; q < W; ++q) {
             in += s_inner[q];
             kp += s_kep[q];
             sg += s_single[q];
@@ -1109,8 +1116,10 @@ __device__ void km_split(KMShared &sh, KMFrame &F, const SView V, const SmallPar
 
 // D_{h/2,T_R} K_{h,V} D_{h/2,T_R} on the frame's set: rest-set members drift,
 // every cross-component pair kicks (sum over j ascending)
-__device__ void km_dkd(KMShared &sh, const KMFrame &F, const SView V, const SmallParams &SP, SmallCnt &cn)
+template <int W>
+__device__ void km_dkd(KMShared<W> &sh, const KMFrame &F, const SView V, const SmallParams &SP, SmallCnt &cn)
 {
+    constexpr int KM_T = W * 32;
     KMStage &T = sh.u.st;
     const int tid = threadIdx.x;
     const int n = F.n;
@@ -1228,10 +1237,12 @@ __device__ void km_dkd(KMShared &sh, const KMFrame &F, const SView V, const Smal
 // evolve_cc(C, h0) of one task of 33..BATCH_NMAX bodies (packed indices
 // mem[0..n0), ascending particle id) by the whole CTA, its first split at
 // depth depth0; frame scratch at fs (KM_MAXF frames)
-__device__ void medium_task(KMShared &sh, const SView V, const int32_t *mem, int n0, double h0, int depth0,
+template <int W>
+__device__ void medium_task(KMShared<W> &sh, const SView V, const int32_t *mem, int n0, double h0, int depth0,
                             const SmallParams &SP, DevCounters *ctr, const NearLog &nl, SmallCnt &cn,
                             PairCounters &pc, char *fs)
 {
+    constexpr int KM_T = W * 32;
     const int tid = threadIdx.x, lane = tid & 31, w = tid >> 5;
     const float etah0 = (float)(SP.eta_outside ? SP.eta_in * SP.eta / h0 : SP.eta_in / h0);
     auto frame_at = [&](int k, const int32_t *sl, int n, double h, int depth) {
@@ -1348,12 +1359,13 @@ __device__ void medium_task(KMShared &sh, const SView V, const int32_t *mem, int
     __syncthreads();
 }
 
-__global__ void __launch_bounds__(KM_T) k_batch(Level L, const int32_t *members, const int32_t *t_start,
+template <int W>
+__global__ void __launch_bounds__(W * 32) k_batch(Level L, const int32_t *members, const int32_t *t_start,
                                                  const int32_t *t_size, const int32_t *tlist, const int32_t *nt_ptr,
                                                  SmallParams SP, DevCounters *ctr, int *queue, int32_t *near_ij,
                                                  double *near_tau, long long near_cap, char *scratch, int nslots)
 {
-    __shared__ KMShared sh;
+    __shared__ KMShared<W> sh;
     __shared__ int s_slot;
     const int nt = *nt_ptr;
     const int tid = threadIdx.x, w = tid >> 5, lane = tid & 31;
@@ -1413,14 +1425,14 @@ __global__ void __launch_bounds__(KM_T) k_batch(Level L, const int32_t *members,
     flush_counters(cn, pc, ctr);
 }
 
-// CTAs of k_batch resident on the whole GPU (the launch's grid; the frame
-// scratch is per CTA)
+// CTAs of k_batch<W> resident on the whole GPU (a launch's grid)
+template <int W>
 static int batch_grid(int nsm)
 {
     static int occ = 0;
     if (occ == 0) {
         int o = 0;
-        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&o, k_batch, KM_T, 0) != cudaSuccess || o < 1) {
+        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&o, k_batch<W>, W * 32, 0) != cudaSuccess || o < 1) {
             cudaGetLastError();
             o = 1;
         }
@@ -1429,23 +1441,34 @@ static int batch_grid(int nsm)
     return occ * (nsm > 0 ? nsm : 1);
 }
 
+// the frame-scratch pool: one slot per CTA that can be resident, for the
+// variant with the most resident CTAs (several launches of either variant
+// in flight at once hold at most that many)
+static int batch_slots(int nsm) { return std::max(batch_grid<4>(nsm), batch_grid<8>(nsm)); }
+
 size_t batch_scratch_bytes(int nsm)
 {
-    const int g = batch_grid(nsm);
+    const int g = batch_slots(nsm);
     return batch_pool_offset(g) + (size_t)g * KM_MAXF * KM_FRAME_BYTES;
 }
 
 void launch_batch(const Level &L, const int32_t *members, const int32_t *t_start, const int32_t *t_size,
                   const int32_t *tlist, const int32_t *nt_ptr, int nt_bound, const SmallParams &SP, DevCounters *ctr,
                   int *queue, int32_t *near_ij, double *near_tau, long long near_cap, int nsm, char *scratch,
-                  cudaStream_t s)
+                  cudaStream_t s, int warps)
 {
     if (nt_bound <= 0) return;
     // *queue is zero on entry; CTAs beyond the work exit at the first read
-    const int g = batch_grid(nsm);
-    const int grid = nt_bound < g ? nt_bound : g;
-    k_batch<<<grid, KM_T, 0, s>>>(L, members, t_start, t_size, tlist, nt_ptr, SP, ctr, queue, near_ij, near_tau,
-                                  near_cap, scratch, g);
+    const int slots = batch_slots(nsm);
+    if (warps == 8) {
+        const int g = batch_grid<8>(nsm), grid = nt_bound < g ? nt_bound : g;
+        k_batch<8><<<grid, 8 * 32, 0, s>>>(L, members, t_start, t_size, tlist, nt_ptr, SP, ctr, queue, near_ij,
+                                           near_tau, near_cap, scratch, slots);
+    } else {
+        const int g = batch_grid<4>(nsm), grid = nt_bound < g ? nt_bound : g;
+        k_batch<4><<<grid, 4 * 32, 0, s>>>(L, members, t_start, t_size, tlist, nt_ptr, SP, ctr, queue, near_ij,
+                                           near_tau, near_cap, scratch, slots);
+    }
     CC_COUNT_LAUNCH(1);
 }
 
