@@ -362,8 +362,43 @@ __device__ __forceinline__ void stumpff(double z, double &c2, double &c3)
     }
 }
 
+// The same functions in FP32 (the starter of the iteration below), every
+// operation an explicit IEEE one so that every translation unit computes
+// the same starter (a contracted multiply-add would move it by an ulp, and
+// the FP64 iteration's stopping point with it)
+__device__ __forceinline__ void stumpff_f(float z, float &c2, float &c3)
+{
+    if (fabsf(z) < 0.1f) {
+        float t2 = 0.5f, t3 = 1.0f / 6.0f;
+        c2 = 0.0f;
+        c3 = 0.0f;
+#pragma unroll
+        for (int k = 0; k < 6; ++k) {
+            c2 = __fadd_rn(c2, t2);
+            c3 = __fadd_rn(c3, t3);
+            t2 = __fmul_rn(t2, __fdiv_rn(-z, (float)((2 * k + 3) * (2 * k + 4))));
+            t3 = __fmul_rn(t3, __fdiv_rn(-z, (float)((2 * k + 4) * (2 * k + 5))));
+        }
+    } else if (z > 0.0f) {
+        const float s = __fsqrt_rn(z);
+        float sn, cs;
+        sincosf(s, &sn, &cs);
+        c2 = __fdiv_rn(__fsub_rn(1.0f, cs), z);
+        c3 = __fdiv_rn(__fsub_rn(s, sn), __fmul_rn(z, s));
+    } else {
+        const float s = __fsqrt_rn(-z);
+        c2 = __fdiv_rn(__fsub_rn(coshf(s), 1.0f), -z);
+        c3 = __fdiv_rn(__fsub_rn(sinhf(s), s), __fmul_rn(-z, s));
+    }
+}
+
 // Advance the relative orbit (r0, v0) under mu by dt; returns false when
-// the iteration does not converge.
+// the iteration does not converge.  The Laguerre-Conway iteration runs in
+// FP32 first (a GB300 FP64 instruction costs the pipe ~64 cycles, an FP32
+// one ~4) until its step falls to a few FP32 ulps of chi; the FP64
+// iteration then converges from there in one or two steps to the same
+// FP64 criterion (and starts from the usual guess if the FP32 pass left no
+// finite value).
 __device__ __forceinline__ bool kepler_universal(const double r0[3], const double v0[3], double mu, double dt, double r1[3],
                                  double v1[3])
 {
@@ -381,6 +416,36 @@ __device__ __forceinline__ bool kepler_universal(const double r0[3], const doubl
     const double a1 = sig / smu, a2 = 1.0 - alpha * r0n;
     double chi = (alpha > 0.0) ? smu * alpha * dt : smu * dt / r0n;
     if (alpha > 0.0 && fabs(alpha * r0n) < 1e-3) chi = smu * dt / r0n;
+    {
+        const float af = (float)alpha, a1f = (float)a1, a2f = (float)a2, r0f = (float)r0n;
+        const float tf = (float)(smu * dt);
+        float xf = (float)chi;
+        bool ok32 = false;
+        for (int it = 0; it < 60; ++it) {
+            const float x2 = __fmul_rn(xf, xf), z = __fmul_rn(af, x2);
+            float c2f, c3f;
+            stumpff_f(z, c2f, c3f);
+            const float zc3 = __fsub_rn(1.0f, __fmul_rn(z, c3f)), zc2 = __fsub_rn(1.0f, __fmul_rn(z, c2f));
+            const float F = __fsub_rn(__fadd_rn(__fadd_rn(__fmul_rn(__fmul_rn(a1f, x2), c2f),
+                                                          __fmul_rn(__fmul_rn(__fmul_rn(a2f, x2), xf), c3f)),
+                                                __fmul_rn(r0f, xf)),
+                                      tf);
+            const float G1 = __fadd_rn(__fadd_rn(__fmul_rn(__fmul_rn(a1f, xf), zc3), __fmul_rn(__fmul_rn(a2f, x2), c2f)),
+                                       r0f);
+            const float G2 = __fadd_rn(__fmul_rn(a1f, zc2), __fmul_rn(__fmul_rn(a2f, xf), zc3));
+            const float disc = __fsqrt_rn(fabsf(__fsub_rn(__fmul_rn(__fmul_rn(16.0f, G1), G1),
+                                                          __fmul_rn(__fmul_rn(20.0f, F), G2))));
+            const float den = __fadd_rn(G1, copysignf(disc, G1));
+            const float d = (den != 0.0f) ? __fdiv_rn(__fmul_rn(5.0f, F), den) : __fdiv_rn(F, G1);
+            xf = __fsub_rn(xf, d);
+            if (!isfinite(xf)) break;
+            if (fabsf(d) <= 4e-7f * fabsf(xf)) {
+                ok32 = true;
+                break;
+            }
+        }
+        if (ok32) chi = (double)xf;
+    }
     double c2 = 0.5, c3 = 1.0 / 6.0, F1 = r0n;
     bool conv = false;
     // Laguerre-Conway iteration (order n = 5) on the universal Kepler equation

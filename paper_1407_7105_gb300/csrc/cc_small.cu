@@ -115,7 +115,8 @@ __device__ __noinline__ K8Acc k8_kick64(const K8Warp &S, int n, uint32_t others,
 }
 
 // the Kepler flow of a two-body component over dt (positions and
-// velocities of both bodies in place)
+// velocities of both bodies in place); the one copy of the solver that
+// every kernel of this file calls
 __device__ __noinline__ bool k8_kepler(double ma, double mb, double *xa, double *xb, double *va, double *vb, double G,
                                        double dt)
 {
@@ -1470,6 +1471,40 @@ void launch_batch(const Level &L, const int32_t *members, const int32_t *t_start
                                            near_tau, near_cap, scratch, slots);
     }
     CC_COUNT_LAUNCH(1);
+}
+
+// ------------------------------------------------------------ Kepler pairs
+// CC_KEPLER (Sec. 3.2): a component of two particles is advanced by the
+// universal-variable Kepler flow instead of recursion.  One thread per
+// two-body component of a level.  The solver is the one out-of-line
+// k8_kepler of this translation unit that the warp and CTA tasks call too,
+// so a two-body component gets the same bits whichever kernel takes it.
+__global__ void k_kepler(Level L, const int32_t *members, const int32_t *comp_start, const int32_t *klist,
+                         const int32_t *nk_ptr, double G, double dt, DevCounters *ctr)
+{
+    const int t = blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= *nk_ptr) return;
+    const int c = klist[t];
+    const int a = members[comp_start[c]], b = members[comp_start[c] + 1];
+    double xa[3] = {L.x[a], L.y[a], L.z[a]}, xb[3] = {L.x[b], L.y[b], L.z[b]};
+    double va[3] = {L.vx[a], L.vy[a], L.vz[a]}, vb[3] = {L.vx[b], L.vy[b], L.vz[b]};
+    if (!k8_kepler(L.m[a], L.m[b], xa, xb, va, vb, G, dt)) {
+        raise_err(ctr, DERR_KEPLER);
+        return;
+    }
+    L.x[a] = xa[0]; L.y[a] = xa[1]; L.z[a] = xa[2];
+    L.x[b] = xb[0]; L.y[b] = xb[1]; L.z[b] = xb[2];
+    L.vx[a] = va[0]; L.vy[a] = va[1]; L.vz[a] = va[2];
+    L.vx[b] = vb[0]; L.vy[b] = vb[1]; L.vz[b] = vb[2];
+}
+
+void launch_kepler(const Level &L, const int32_t *members, const int32_t *comp_start, const int32_t *klist,
+                   const int32_t *nk_ptr, int nk_bound, double G, double dt, DevCounters *ctr, cudaStream_t s)
+{
+    if (nk_bound > 0) {
+        k_kepler<<<(nk_bound + 127) / 128, 128, 0, s>>>(L, members, comp_start, klist, nk_ptr, G, dt, ctr);
+        CC_COUNT_LAUNCH(1);
+    }
 }
 
 void launch_small(const Level &L, const int32_t *members, const int32_t *comp_start, const int32_t *comp_size,
