@@ -214,6 +214,25 @@ struct cc_ctx {
     char *ok_arena = nullptr;
     size_t ok_arena_cap = 0;
     std::vector<long long> ok_hseg, ok_haoff;
+    // the OK split's GPU-wide nodes (lists too long for one CTA): per-depth
+    // flags, prefix, child list, particle list and F flags; per-particle and
+    // per-set stamps; the node counters; scan, directed-pair and sort scratch
+    struct OkDepth {
+        int *fast = nullptr, *pos = nullptr;
+        int32_t *child = nullptr, *S = nullptr;
+        unsigned char *isF = nullptr;
+        long long cap = 0;
+    };
+    std::vector<OkDepth> okd;
+    unsigned long long *ok_hst = nullptr;  // [4 * total + 2 * nsets] S, F stamps; set stamps
+    int ok_hst_total = 0, ok_hst_sets = 0;
+    unsigned long long ok_node_stamp = 0;
+    unsigned long long *ok_cnt = nullptr;
+    int *ok_scan = nullptr;
+    long long ok_scan_cap = 0;
+    int32_t *ok_ndir = nullptr;
+    void *ok_nsort = nullptr;
+    long long ok_ndir_cap = 0;
 };
 
 // components (and systems) of at most this many bodies run in the batched
@@ -1107,6 +1126,116 @@ static int ok_grow(cc_ctx *c, void **p, size_t bytes)
     return CC_OK;
 }
 
+// Lists of at most this many pairs go to k_ok_tree (one CTA per set runs
+// the rest of the set's tree); longer ones are GPU-wide nodes.
+constexpr long long OK_NODE_MIN = 8192;
+
+// evolve_ok of a sorted fast list (all sets) at pivot h, depth `depth`, by
+// k_ok_tree: each set's segment of the list and its arena
+static int ok_tree_small(cc_ctx *c, const int32_t *list, long long np, double h, int depth)
+{
+    LevelAlloc &a = c->lv[0];
+    const cudaStream_t s = c->stream;
+    const int ns = a.L.nsets;
+    launch_ok_segments(a.L, list, np, c->ok_seg, s);
+    c->ok_hseg.resize(ns + 1);
+    c->ok_haoff.resize(ns + 1);
+    CC_CUDA(c, cudaMemcpyAsync(c->ok_hseg.data(), c->ok_seg, (size_t)(ns + 1) * 8, cudaMemcpyDeviceToHost, s));
+    CC_CUDA(c, cudaStreamSynchronize(s));
+    size_t off = 0;
+    for (int q = 0; q < ns; ++q) {
+        c->ok_haoff[q] = (long long)off;
+        off += (ok_arena_bytes(c->ok_hseg[q + 1] - c->ok_hseg[q], c->p.max_depth) + 255) / 256 * 256;
+    }
+    c->ok_haoff[ns] = (long long)off;
+    if (off > c->ok_arena_cap) {
+        CC_TRY(ok_grow(c, (void **)&c->ok_arena, off));
+        c->ok_arena_cap = off;
+    }
+    CC_CUDA(c, cudaMemcpyAsync(c->ok_aoff, c->ok_haoff.data(), (size_t)(ns + 1) * 8, cudaMemcpyHostToDevice, s));
+    launch_ok_tree(a.L, list, c->ok_seg, c->ok_aoff, c->ok_arena, c->ok_stamp, c->ok_loc, (++c->ok_launch) << 40, h,
+                   depth, c->p.max_depth, tau_params(c, h), c->p.G, c->p.eps * c->p.eps, c->d_ctr, c->d_near_ij,
+                   c->d_near_tau, c->near_cap, s);
+    // (the host-side copies must outlive the asynchronous upload)
+    CC_CUDA(c, cudaStreamSynchronize(s));
+    return CC_OK;
+}
+
+// evolve_ok(F, I, h) of a sorted list I (all sets) at depth `depth`
+static int ok_node(cc_ctx *c, const int32_t *list, long long np, double h, int depth)
+{
+    if (np <= 0) return CC_OK;
+    if (depth > c->p.max_depth) return fail(c, CC_E_DEPTH, "recursion deeper than max_depth");
+    if (np <= OK_NODE_MIN) return ok_tree_small(c, list, np, h, depth);
+    LevelAlloc &a = c->lv[0];
+    const cudaStream_t s = c->stream;
+    const int total = a.L.total, ns = a.L.nsets;
+    if (c->okd.size() < (size_t)c->p.max_depth + 2) c->okd.resize((size_t)c->p.max_depth + 2);
+    if (c->ok_hst_total < total + 1 || c->ok_hst_sets < ns + 1) {
+        const size_t n8 = (size_t)2 * (total + 1) + 2 * (size_t)(ns + 1);
+        CC_TRY(ok_grow(c, (void **)&c->ok_hst, n8 * 8));
+        CC_CUDA(c, cudaMemsetAsync(c->ok_hst, 0, n8 * 8, s));
+        c->ok_hst_total = total + 1;
+        c->ok_hst_sets = ns + 1;
+    }
+    if (!c->ok_cnt) CC_TRY(ok_grow(c, (void **)&c->ok_cnt, 64));
+    {
+        cc_ctx::OkDepth &D = c->okd[depth];
+        if (D.cap < np) {
+            const long long cap = 2 * np;
+            CC_TRY(ok_grow(c, (void **)&D.fast, (size_t)cap * 4));
+            CC_TRY(ok_grow(c, (void **)&D.pos, (size_t)cap * 4));
+            CC_TRY(ok_grow(c, (void **)&D.child, (size_t)cap * 8));
+            CC_TRY(ok_grow(c, (void **)&D.S, (size_t)cap * 8));
+            CC_TRY(ok_grow(c, (void **)&D.isF, (size_t)cap * 2));
+            D.cap = cap;
+        }
+    }
+    if (c->ok_scan_cap < scan_scratch_ints((int)np)) {
+        c->ok_scan_cap = 2 * (long long)scan_scratch_ints((int)np);
+        CC_TRY(ok_grow(c, (void **)&c->ok_scan, (size_t)c->ok_scan_cap * 4));
+    }
+    if (c->ok_ndir_cap < np) {
+        c->ok_ndir_cap = 2 * np;
+        CC_TRY(ok_grow(c, (void **)&c->ok_ndir, (size_t)c->ok_ndir_cap * 16));
+        CC_TRY(ok_grow(c, &c->ok_nsort, edge_sort_scratch_bytes(2 * c->ok_ndir_cap)));
+    }
+    cc_ctx::OkDepth &D = c->okd[depth];  // (okd does not resize below this point)
+    unsigned long long *sst = c->ok_hst, *fst = sst + c->ok_hst_total;
+    unsigned long long *sys_st = fst + c->ok_hst_total, *sysf_st = sys_st + c->ok_hst_sets;
+    const unsigned long long stamp = ++c->ok_node_stamp;
+    const TauParams P = tau_params(c, h);
+    CC_CUDA(c, cudaMemsetAsync(c->ok_cnt, 0, 32, s));
+    launch_okh_split(a.L, list, np, P, stamp, D.fast, D.S, sst, fst, sys_st, sysf_st, c->ok_cnt, c->d_ctr,
+                     c->d_near_ij, c->d_near_tau, c->near_cap, s);
+    launch_exclusive_scan(D.fast, D.pos, (int)np, c->ok_scan, s);
+    unsigned long long hc[4] = {0, 0, 0, 0};
+    CC_CUDA(c, cudaMemcpyAsync(hc, c->ok_cnt, 32, cudaMemcpyDeviceToHost, s));
+    CC_CUDA(c, cudaStreamSynchronize(s));
+    const long long nf = (long long)hc[0], nS = (long long)hc[1];
+    launch_okh_compact(list, np, D.fast, D.pos, D.child, D.S, nS, fst, stamp, D.isF, s);
+    c->st.splits += hc[2];
+    c->st.tau_pairs += (unsigned long long)np;
+    c->st.tau_evaluated += (unsigned long long)np;
+    c->st.tau_fp64 += (unsigned long long)np;
+    c->st.components += hc[3];
+    if (depth > c->st.max_depth_seen) c->st.max_depth_seen = depth;
+    int32_t *child = D.child, *S = D.S;
+    int *fast = D.fast, *pos = D.pos;
+    unsigned char *isF = D.isF;
+    const double G = c->p.G, eps2 = c->p.eps * c->p.eps;
+    for (int half = 0; half < 2; ++half) {
+        if (half == 1) {
+            launch_okh_drift(a.L, S, nS, isF, 0.5 * h, c->d_ctr, true, s);
+            launch_okh_kick(a.L, list, np, fast, pos, np - nf, c->ok_ndir, c->ok_nsort, G, eps2, h, s);
+            launch_okh_drift(a.L, S, nS, isF, 0.5 * h, c->d_ctr, false, s);
+            c->st.kick_pairs += (unsigned long long)(np - nf);
+        }
+        CC_TRY(ok_node(c, child, nf, 0.5 * h, depth + 1));
+    }
+    return CC_OK;
+}
+
 // One outer step of the OK split (Sec. 4.2) on level 0 (every set a system):
 // the outer level here, the rest of the recursion in k_ok_tree.
 static int ok_step(cc_ctx *c)
@@ -1163,26 +1292,14 @@ static int ok_step(cc_ctx *c)
     }
     launch_ok_level(a.L, c->ok_edges, ne, c->ok_inv, c->ok_dir, c->ok_sort, c->ok_row, c->ok_rest, c->ok_seg,
                     c->d_ctr, s);
-    // each set's arena, from its segment of the fast list
-    c->ok_hseg.resize(ns + 1);
-    c->ok_haoff.resize(ns + 1);
-    CC_CUDA(c, cudaMemcpyAsync(c->ok_hseg.data(), c->ok_seg, (size_t)(ns + 1) * 8, cudaMemcpyDeviceToHost, s));
-    CC_CUDA(c, cudaStreamSynchronize(s));
-    size_t off = 0;
     unsigned long long nonempty = 0;
-    for (int q = 0; q < ns; ++q) {
-        c->ok_haoff[q] = (long long)off;
-        const long long np = c->ok_hseg[q + 1] - c->ok_hseg[q];
-        nonempty += np > 0 ? 1 : 0;
-        off += (ok_arena_bytes(np, c->p.max_depth) + 255) / 256 * 256;
+    {
+        c->ok_hseg.resize(ns + 1);
+        CC_CUDA(c, cudaMemcpyAsync(c->ok_hseg.data(), c->ok_seg, (size_t)(ns + 1) * 8, cudaMemcpyDeviceToHost, s));
+        CC_CUDA(c, cudaStreamSynchronize(s));
+        for (int q = 0; q < ns; ++q) nonempty += c->ok_hseg[q + 1] > c->ok_hseg[q] ? 1 : 0;
     }
-    c->ok_haoff[ns] = (long long)off;
-    if (off > c->ok_arena_cap) {
-        CC_TRY(ok_grow(c, (void **)&c->ok_arena, off));
-        c->ok_arena_cap = off;
-    }
-    CC_CUDA(c, cudaMemcpyAsync(c->ok_aoff, c->ok_haoff.data(), (size_t)(ns + 1) * 8, cudaMemcpyHostToDevice, s));
-    // the outer level's counts (the tree counts its own nodes on the device)
+    // the outer level's counts (the nodes below count their own)
     c->st.splits += (unsigned long long)ns;
     c->st.tau_pairs += (unsigned long long)a.pairs;
     c->st.tau_evaluated += (unsigned long long)a.pairs;
@@ -1201,10 +1318,7 @@ static int ok_step(cc_ctx *c)
             launch_kick(KL, a.L.gid, (int)a.k64_blocks[0], G, eps2, dt, 0, c->d_ctr, s, nullptr, &okv);
             launch_drift_labels(a.L, c->ok_rest, 0.5 * dt, s);
         }
-        if (ne > 0)
-            launch_ok_tree(a.L, c->ok_edges, c->ok_seg, c->ok_aoff, c->ok_arena, c->ok_stamp, c->ok_loc,
-                           (++c->ok_launch) << 40, 0.5 * dt, 1, c->p.max_depth, P, G, eps2, c->d_ctr,
-                           c->d_near_ij, c->d_near_tau, c->near_cap, s);
+        CC_TRY(ok_node(c, c->ok_edges, ne, 0.5 * dt, 1));
     }
     return CC_OK;
 }
@@ -1779,9 +1893,14 @@ int cc_destroy(cc_ctx *c)
                     c->tmp, c->seg_scratch, c->d_sys_off, c->d_bad, c->d_kpart, c->d_perm, c->d_box,
                     c->batch_scr, c->d_sys_tasks, c->d_iota, c->ok_edges, c->ok_dir, c->ok_sort,
                     c->ok_inv, c->ok_row, c->ok_rest, c->ok_loc, c->ok_stamp, c->ok_seg, c->ok_aoff,
-                    c->ok_arena};
+                    c->ok_arena, c->ok_hst, c->ok_cnt, c->ok_scan, c->ok_ndir, c->ok_nsort};
     for (void *q : ptrs)
         if (q) cudaFree(q);
+    for (auto &D : c->okd) {
+        void *dp[] = {D.fast, D.pos, D.child, D.S, D.isF};
+        for (void *q : dp)
+            if (q) cudaFree(q);
+    }
     delete c;
     return CC_OK;
 }

@@ -112,6 +112,13 @@ static void device_scan(const int *in, int *out, int n, int *bsum, int *grand, c
     }
 }
 
+int scan_scratch_ints(int n) { return scan_blocks(n) + 1; }
+
+void launch_exclusive_scan(const int *in, int *out, int n, int *scratch, cudaStream_t s)
+{
+    device_scan(in, out, n, scratch, nullptr, s);
+}
+
 // ------------------------------------------------------------ radix sort
 // Stable LSD radix sort of (key, val) pairs, 8-bit digits.  Per pass:
 // per-tile digit histograms, one exclusive scan over [digit][tile], and a

@@ -341,6 +341,22 @@ void launch_kick(const Level &L, const int32_t *label, int nitiles, double G, do
 // particles without a fast partner (rest), each set's segment of the list
 void launch_ok_level(const Level &L, int32_t *edges, long long ne, int32_t *inv, int32_t *dir, void *sort_scratch,
                      int32_t *row_ptr, int32_t *rest, long long *seg, DevCounters *ctr, cudaStream_t s);
+// a node of the OK recursion on the whole GPU (lists too long for one CTA):
+// the split (fast flags, the node's particles S, per-set presence counts in
+// counters = {nf, nS, nsys, nsysf}, u64, zeroed by the caller), the child
+// list and the F flags of S, the drifts of S \ F, the kick of the slow pairs
+void launch_okh_split(const Level &L, const int32_t *list, long long np, const TauParams &P, unsigned long long stamp,
+                      int *fast, int32_t *S, unsigned long long *sst, unsigned long long *fst,
+                      unsigned long long *sys_st, unsigned long long *sysf_st, void *counters, DevCounters *ctr,
+                      int32_t *near_ij, double *near_tau, long long near_cap, cudaStream_t s);
+void launch_okh_compact(const int32_t *list, long long np, const int *fast, const int *pos, int32_t *child,
+                        const int32_t *S, long long nS, const unsigned long long *fst, unsigned long long stamp,
+                        unsigned char *isF, cudaStream_t s);
+void launch_okh_drift(const Level &L, const int32_t *S, long long nS, const unsigned char *isF, double dt,
+                      DevCounters *ctr, bool count, cudaStream_t s);
+void launch_okh_kick(const Level &L, const int32_t *list, long long np, const int *fast, const int *pos,
+                     long long ns, int32_t *dir, void *sort_scratch, double G, double eps2, double h, cudaStream_t s);
+void launch_ok_segments(const Level &L, const int32_t *list, long long np, long long *seg, cudaStream_t s);
 // the rest of the OK recursion: one CTA per set evolves (F, I_F) of its
 // segment of the sorted fast list at pivot h0 (depth depth0), node arrays in
 // the set's arena [arena_off[s], arena_off[s+1])
@@ -415,6 +431,9 @@ void launch_singleton_from_labels(const int32_t *labels, int n, int32_t *singlet
                                   cudaStream_t s);
 void launch_label_order(const int32_t *labels, int n, int total, int32_t *order, void *scratch, cudaStream_t s);
 void launch_sort_edges(int32_t *edges, long long ne, int bits, void *scratch, cudaStream_t s);
+// exclusive prefix sums of n ints (scratch: scan_scratch_ints(n) ints)
+int scan_scratch_ints(int n);
+void launch_exclusive_scan(const int *in, int *out, int n, int *scratch, cudaStream_t s);
 size_t edge_sort_scratch_bytes(long long ne);
 void launch_check_state(const double *m, const double *x3, const double *v3, long long n, unsigned *bad,
                         cudaStream_t s);

@@ -106,6 +106,174 @@ void launch_ok_level(const Level &L, int32_t *edges, long long ne, int32_t *inv,
     CC_COUNT_LAUNCH(launches + 2);
 }
 
+// ------------------------------------------------------------ large nodes
+// A node whose list is too long for one CTA runs on the whole GPU, driven
+// by the host (ok_node in cc_api.cu): the split here, the child list by a
+// scan, then the DKD.  The lists of all sets are processed together (sets
+// never interact); per-set counts come from stamps on the set index.
+struct OkNodeCounters {
+    unsigned long long nf, nS, nsys, nsysf;
+};
+
+__global__ void k_okh_split(Level L, const int32_t *list, long long np, TauParams P, unsigned long long stamp,
+                            int *fast, int32_t *S, unsigned long long *sst, unsigned long long *fst,
+                            unsigned long long *sys_st, unsigned long long *sysf_st, OkNodeCounters *cnt,
+                            DevCounters *ctr, int32_t *near_ij, double *near_tau, long long near_cap)
+{
+    const long long k = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    bool f = false;
+    if (k < np) {
+        const int a = list[2 * k], b = list[2 * k + 1];
+        const double tau = tau_fp64(__dsub_rn(L.x[a], L.x[b]), __dsub_rn(L.y[a], L.y[b]), __dsub_rn(L.z[a], L.z[b]),
+                                    __dsub_rn(L.vx[a], L.vx[b]), __dsub_rn(L.vy[a], L.vy[b]),
+                                    __dsub_rn(L.vz[a], L.vz[b]), L.m[a], L.m[b], P);
+        if (fabs(tau - P.h) < P.near_tol * P.h) {
+            const unsigned long long z = atomicAdd(&ctr->near_pairs, 1ull);
+            if ((long long)z < near_cap) {
+                const int ga = L.gid[a], gb = L.gid[b];
+                near_ij[2 * z] = ga < gb ? ga : gb;
+                near_ij[2 * z + 1] = ga < gb ? gb : ga;
+                near_tau[z] = tau;
+            }
+        }
+        f = tau < P.h;
+        fast[k] = f ? 1 : 0;
+        for (int q = 0; q < 2; ++q) {
+            const int e = q == 0 ? a : b;
+            if (atomicExch(&sst[e], stamp) != stamp) S[atomicAdd(&cnt->nS, 1ull)] = e;
+            if (f) fst[e] = stamp;
+        }
+        const int sy = L.sidx[a];
+        if (atomicExch(&sys_st[sy], stamp) != stamp) atomicAdd(&cnt->nsys, 1ull);
+        if (f && atomicExch(&sysf_st[sy], stamp) != stamp) atomicAdd(&cnt->nsysf, 1ull);
+    }
+    const unsigned fb = __ballot_sync(0xffffffffu, f);
+    if ((threadIdx.x & 31) == 0 && fb) atomicAdd(&cnt->nf, (unsigned long long)__popc(fb));
+}
+
+// the fast pairs in list order (pos = exclusive prefix of the flags)
+__global__ void k_okh_compact(const int32_t *list, long long np, const int *fast, const int *pos, int32_t *child)
+{
+    const long long k = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (k >= np || !fast[k]) return;
+    const int at = pos[k];
+    child[2 * at] = list[2 * k];
+    child[2 * at + 1] = list[2 * k + 1];
+}
+
+// which particles of the node's list belong to a fast pair (read before a
+// child node restamps them)
+__global__ void k_okh_isf(const int32_t *S, long long nS, const unsigned long long *fst, unsigned long long stamp,
+                          unsigned char *isF)
+{
+    const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < nS) isF[i] = fst[S[i]] == stamp ? 1 : 0;
+}
+
+__global__ void k_okh_drift(Level L, const int32_t *S, long long nS, const unsigned char *isF, double dt,
+                            DevCounters *ctr, int count)
+{
+    const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    bool d = false;
+    if (i < nS && !isF[i]) {
+        const int k = S[i];
+        L.x[k] = __dadd_rn(L.x[k], __dmul_rn(dt, L.vx[k]));
+        L.y[k] = __dadd_rn(L.y[k], __dmul_rn(dt, L.vy[k]));
+        L.z[k] = __dadd_rn(L.z[k], __dmul_rn(dt, L.vz[k]));
+        d = true;
+    }
+    const unsigned db = __ballot_sync(0xffffffffu, d);
+    if (count && (threadIdx.x & 31) == 0 && db) atomicAdd(&ctr->small_drifts, 2ull * __popc(db));
+}
+
+// both directions of every slow pair (slow index = k - pos[k])
+__global__ void k_okh_slow(const int32_t *list, long long np, const int *fast, const int *pos, int32_t *dir)
+{
+    const long long k = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (k >= np || fast[k]) return;
+    const long long si = k - pos[k];
+    const int a = list[2 * k], b = list[2 * k + 1];
+    dir[4 * si] = a;
+    dir[4 * si + 1] = b;
+    dir[4 * si + 2] = b;
+    dir[4 * si + 3] = a;
+}
+
+// K_h over the slow pairs: the head of each row (sorted by (row, partner))
+// sums its partners in ascending index, v += h a
+__global__ void k_okh_kick(Level L, const int32_t *dir, long long nd, double G, double eps2, double h)
+{
+    const long long q = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (q >= nd) return;
+    const int i = dir[2 * q];
+    if (q > 0 && dir[2 * (q - 1)] == i) return;
+    double ax = 0.0, ay = 0.0, az = 0.0;
+    const double xi = L.x[i], yi = L.y[i], zi = L.z[i];
+    for (long long r = q; r < nd && dir[2 * r] == i; ++r) {
+        const int j = dir[2 * r + 1];
+        const double dx0 = __dsub_rn(L.x[j], xi), dx1 = __dsub_rn(L.y[j], yi), dx2 = __dsub_rn(L.z[j], zi);
+        const double r2 = __dadd_rn(__dadd_rn(__dadd_rn(__dmul_rn(dx0, dx0), __dmul_rn(dx1, dx1)),
+                                              __dmul_rn(dx2, dx2)), eps2);
+        const double rinv3 = __ddiv_rn(1.0, __dmul_rn(r2, __dsqrt_rn(r2)));
+        const double w = __dmul_rn(__dmul_rn(G, L.m[j]), rinv3);
+        ax = __dadd_rn(ax, __dmul_rn(w, dx0));
+        ay = __dadd_rn(ay, __dmul_rn(w, dx1));
+        az = __dadd_rn(az, __dmul_rn(w, dx2));
+    }
+    L.vx[i] = __dadd_rn(L.vx[i], __dmul_rn(h, ax));
+    L.vy[i] = __dadd_rn(L.vy[i], __dmul_rn(h, ay));
+    L.vz[i] = __dadd_rn(L.vz[i], __dmul_rn(h, az));
+}
+
+static int okb(long long n) { return (int)((n + 255) / 256); }
+
+void launch_okh_split(const Level &L, const int32_t *list, long long np, const TauParams &P, unsigned long long stamp,
+                      int *fast, int32_t *S, unsigned long long *sst, unsigned long long *fst,
+                      unsigned long long *sys_st, unsigned long long *sysf_st, void *counters, DevCounters *ctr,
+                      int32_t *near_ij, double *near_tau, long long near_cap, cudaStream_t s)
+{
+    if (np <= 0) return;
+    k_okh_split<<<okb(np), 256, 0, s>>>(L, list, np, P, stamp, fast, S, sst, fst, sys_st, sysf_st,
+                                        (OkNodeCounters *)counters, ctr, near_ij, near_tau, near_cap);
+    CC_COUNT_LAUNCH(1);
+}
+
+void launch_okh_compact(const int32_t *list, long long np, const int *fast, const int *pos, int32_t *child,
+                        const int32_t *S, long long nS, const unsigned long long *fst, unsigned long long stamp,
+                        unsigned char *isF, cudaStream_t s)
+{
+    if (np > 0) k_okh_compact<<<okb(np), 256, 0, s>>>(list, np, fast, pos, child);
+    if (nS > 0) k_okh_isf<<<okb(nS), 256, 0, s>>>(S, nS, fst, stamp, isF);
+    CC_COUNT_LAUNCH(2);
+}
+
+void launch_okh_drift(const Level &L, const int32_t *S, long long nS, const unsigned char *isF, double dt,
+                      DevCounters *ctr, bool count, cudaStream_t s)
+{
+    if (nS <= 0) return;
+    k_okh_drift<<<okb(nS), 256, 0, s>>>(L, S, nS, isF, dt, ctr, count ? 1 : 0);
+    CC_COUNT_LAUNCH(1);
+}
+
+void launch_okh_kick(const Level &L, const int32_t *list, long long np, const int *fast, const int *pos,
+                     long long ns, int32_t *dir, void *sort_scratch, double G, double eps2, double h, cudaStream_t s)
+{
+    if (ns <= 0) return;
+    int bits = 0;
+    while (bits < 31 && (1ll << bits) <= (long long)L.total) ++bits;
+    k_okh_slow<<<okb(np), 256, 0, s>>>(list, np, fast, pos, dir);
+    launch_sort_edges(dir, 2 * ns, bits, sort_scratch, s);
+    k_okh_kick<<<okb(2 * ns), 256, 0, s>>>(L, dir, 2 * ns, G, eps2, h);
+    CC_COUNT_LAUNCH(2);
+}
+
+// segments of a sorted list by set (the tree takes one set per CTA)
+void launch_ok_segments(const Level &L, const int32_t *list, long long np, long long *seg, cudaStream_t s)
+{
+    k_ok_segments<<<(L.nsets + 1 + 255) / 256, 256, 0, s>>>(L, list, np, seg);
+    CC_COUNT_LAUNCH(1);
+}
+
 // ------------------------------------------------------------ the tree
 constexpr int KO_T = 256;
 constexpr int KO_MAXF = 72;  // nested nodes of one tree (DERR_DEPTH beyond)

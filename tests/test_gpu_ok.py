@@ -33,10 +33,22 @@ def _case(name):
     if name == "plummer256":
         m, x, v = ics.plummer(256, seed=1)
         return m, x, v, None, 1 / 64
+    if name == "plummer2000_long":
+        # 1.27e6 fast pairs at the outer level: its nodes run GPU-wide until
+        # the lists are short enough for one CTA per set
+        m, x, v = ics.plummer(2000, seed=1)
+        return m, x, v, None, 1 / 16
+    if name == "two_systems_long":
+        parts = [ics.plummer(1000, seed=s) for s in (3, 4)]
+        m = np.concatenate([p[0] for p in parts])
+        x = np.ascontiguousarray(np.concatenate([p[1] for p in parts], axis=1))
+        v = np.ascontiguousarray(np.concatenate([p[2] for p in parts], axis=1))
+        return m, x, v, np.array([0, 1000, 2000], dtype=np.int64), 1 / 16
     raise ValueError(name)
 
 
-@pytest.mark.parametrize("name,steps", [("plummer1000", 1), ("fractal1200", 1), ("systems", 1), ("plummer256", 4)])
+@pytest.mark.parametrize("name,steps", [("plummer1000", 1), ("fractal1200", 1), ("systems", 1), ("plummer256", 4),
+                                        ("plummer2000_long", 1), ("two_systems_long", 1)])
 def test_ok_matches_oracle(cclib, name, steps):
     m, x, v, off, dt = _case(name)
     c = cclib.Context(m, x, v, dt=dt, split=cclib.SPLIT_OK)
