@@ -1167,6 +1167,7 @@ static int ok_node(cc_ctx *c, const int32_t *list, long long np, double h, int d
     if (np <= 0) return CC_OK;
     if (depth > c->p.max_depth) return fail(c, CC_E_DEPTH, "recursion deeper than max_depth");
     if (np <= OK_NODE_MIN) return ok_tree_small(c, list, np, h, depth);
+    if (np > (1ll << 30)) return fail(c, CC_E_ARG, "OK split: a fast list longer than 2^30 pairs");
     LevelAlloc &a = c->lv[0];
     const cudaStream_t s = c->stream;
     const int total = a.L.total, ns = a.L.nsets;
