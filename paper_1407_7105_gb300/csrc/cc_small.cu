@@ -782,6 +782,10 @@ __global__ void __launch_bounds__(K8_WARPS * 32) k_small(Level L, const int32_t 
         q = __shfl_sync(FULL, q, 0);
         if (q >= ns) break;
         const int c = slist[q];
+        if (comp_size[c] > 32) {  // (a warp holds at most 32 bodies: a task list out of order)
+            if (lane == 0) raise_err(ctr, DERR_SMALL_OVERFLOW);
+            continue;
+        }
         small_task(sw[w], V, members + comp_start[c], comp_size[c], SP.h0, SP.depth0, SP, ctr, nl, cn, pc);
     }
     flush_counters(cn, pc, ctr);
@@ -1414,7 +1418,14 @@ __global__ void __launch_bounds__(W * 32) k_batch(Level L, const int32_t *member
             }
             if (q >= nt) break;
             const int c = tlist[q];
-            small_task(sh.u.sw[w], V, members + t_start[c], t_size[c], SP.h0, SP.depth0, SP, ctr, nl, cn, pc);
+            if (t_size[c] > 32) {
+                // warp mode assumes the queue holds the CTA tasks first (the
+                // classification's order): a larger task here is an error,
+                // never a silent partial step
+                if (lane == 0) raise_err(ctr, DERR_SMALL_OVERFLOW);
+            } else {
+                small_task(sh.u.sw[w], V, members + t_start[c], t_size[c], SP.h0, SP.depth0, SP, ctr, nl, cn, pc);
+            }
             q = -1;
         }
     }
