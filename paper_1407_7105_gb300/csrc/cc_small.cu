@@ -267,10 +267,13 @@ __device__ unsigned pair_path(double A[7], double B[7], double h0, int depth0, i
 // Mixed form, in the pair's own coordinates: inside evolve_cc({a,b}, .)
 // only the pair's mutual force acts, so the centre of mass moves uniformly
 // and the relative state (r = x_a - x_b, u = v_a - v_b, FP64) carries
-// everything.  A leaf is r += h/2 u; u -= h G M r/|r|^3 (FP32 force from
-// fl32(r), rsqrt + Newton); r += h/2 u: nine FP64 FMAs.  The edge decision
-// takes fl32(r), fl32(u) (relative error u) and falls back to the exact
-// FP64 predicate on (r, u); below h_fp64 the force is FP64 as well.
+// everything.  A leaf is r += h/2 u; u -= h G M r/|r|^3; r += h/2 u: nine
+// FP64 FMAs.  The FP32 force takes the drifted position in FP32, fl32(r) +
+// (h/2) fl32(u) (a few units of u off the drifted FP64 r, like the force's
+// own rounding), so the first drift's FP64 FMAs run beside the force
+// instead of before it.  The edge decision takes fl32(r), fl32(u)
+// (relative error u) and falls back to the exact FP64 predicate on (r, u);
+// below h_fp64 the force is FP64 as well.
 // Returns 0, DERR_DEPTH or DERR_SMALL_OVERFLOW.
 __device__ unsigned pair_path_rel(double A[7], double B[7], double h0, int depth0, int e0, const SmallParams &SP,
                                   const TauParams &P, const MixedTauParams &Q, PairCounters &pc, const NearLog &nl,
@@ -292,6 +295,9 @@ __device__ unsigned pair_path_rel(double A[7], double B[7], double h0, int depth
     const float etah0 = Q.etah;  // eta/h0 in float (the caller's, exact power-of-two scaling of its own)
     const int dmax = min(SP.max_depth - depth0, 61);
     const double c0 = -GM * h0;
+    // h0 in float: h0 2^-(d+1) by exponent subtraction while it stays normal
+    const float h0f = fl32(h0);
+    const int h0x = (__float_as_int(h0f) >> 23) & 0xFF;
     // depths whose pivot h0 2^-d is below h_fp64 take FP64 forces
     int d64 = 64;
     if (SP.h_fp64 > 0.0) {
@@ -301,9 +307,10 @@ __device__ unsigned pair_path_rel(double A[7], double B[7], double h0, int depth
     unsigned long long pend = 0ull;
     int d = 0, e = e0;
     for (long long work = 0; work < PAIR_VISIT_LIMIT;) {
+        const float fr0 = fl32(r[0]), fr1 = fl32(r[1]), fr2 = fl32(r[2]);
+        const float fu0 = fl32(u[0]), fu1 = fl32(u[1]), fu2 = fl32(u[2]);
         if (e < 0) {
-            const TauPrep32 t = tau_prep_fp32(fl32(r[0]), fl32(r[1]), fl32(r[2]), fl32(u[0]), fl32(u[1]),
-                                              fl32(u[2]), muf, 0.f, 0.f, Q);
+            const TauPrep32 t = tau_prep_fp32(fr0, fr1, fr2, fu0, fu1, fu2, muf, 0.f, 0.f, Q);
             ++pc.evals;
             bool used64;
             e = edge_depth_mixed(
@@ -333,7 +340,17 @@ __device__ unsigned pair_path_rel(double A[7], double B[7], double h0, int depth
             u[1] = fma(w, r[1], u[1]);
             u[2] = fma(w, r[2], u[2]);
         } else {
-            const float gx = fl32(r[0]), gy = fl32(r[1]), gz = fl32(r[2]);
+            float gx, gy, gz;
+            if (h0x - (d + 1) >= 1) {
+                const float hdf = __int_as_float(__float_as_int(h0f) - ((d + 1) << 23));
+                gx = fmaf(hdf, fu0, fr0);
+                gy = fmaf(hdf, fu1, fr1);
+                gz = fmaf(hdf, fu2, fr2);
+            } else {
+                gx = fl32(r[0]);
+                gy = fl32(r[1]);
+                gz = fl32(r[2]);
+            }
             const float q2 = fmaf(gz, gz, fmaf(gy, gy, fmaf(gx, gx, e2)));
             float ri = rsqrtf(q2);
             ri = ri * fmaf(-0.5f * q2, ri * ri, 1.5f);
