@@ -200,6 +200,13 @@ struct cc_ctx {
     bool sys_batch = false;
     int32_t *d_sys_tasks = nullptr;
     int32_t *d_iota = nullptr;
+    // the whole-batch outer step captured as a CUDA graph (pack, queue reset,
+    // the batched kernel, unpack), for the eta it was captured with, and
+    // the kernels one replay launches
+    cudaGraphExec_t sys_exec = nullptr;
+    cudaStream_t cap_stream = nullptr;
+    double sys_exec_eta = 0.0;
+    unsigned long long sys_exec_launches = 0;
     // the OK split (split = CC_SPLIT_OK): the outer level's fast pairs and
     // their directed copy (ok_cap pairs each, grown on demand), the level's
     // inverse id map, row pointers and drift flags, each set's segment and
@@ -1343,6 +1350,8 @@ static int setup_systems(cc_ctx *c)
     // launch, largest first (no host level).  Kepler mode needs three
     // bodies or more (a two-body system's first split decides between the
     // Kepler flow and a kick, which the host level takes).
+    if (c->sys_exec) cudaGraphExecDestroy(c->sys_exec);
+    c->sys_exec = nullptr;
     if (c->d_sys_tasks) cudaFree(c->d_sys_tasks);
     if (c->d_iota) cudaFree(c->d_iota);
     c->d_sys_tasks = nullptr;
@@ -1375,6 +1384,55 @@ static int setup_systems(cc_ctx *c)
         CC_TRY(ensure_batch_scratch(c));
         c->sys_batch = true;
     }
+    return CC_OK;
+}
+
+// One outer step of the whole-batch mode on stream s: every system one task,
+// evolve_cc(system, dt) split at depth 0 (8 warps per CTA while there are
+// fewer systems than SMs: each task's CTA-level phases are then the step's
+// critical path)
+static void sys_step_launches(cc_ctx *c, cudaStream_t s)
+{
+    const int ns = (int)c->sys_off.size() - 1;
+    int32_t *tk = c->d_sys_tasks;
+    launch_pack_state(c->d_x3, c->d_v3, c->d_m, c->n, c->lv[0].L, c->d_sys_off, nullptr, s);
+    cudaMemsetAsync(tk + 3 * ns + 1, 0, 4, s);
+    const SmallParams SP = small_params(c, c->p.dt, 0);
+    launch_batch(c->lv[0].L, c->d_iota, tk + ns, tk + 2 * ns, tk, tk + 3 * ns, ns, SP, c->d_ctr, tk + 3 * ns + 1,
+                 c->d_near_ij, c->d_near_tau, c->near_cap, c->nsm, c->batch_scr, s, ns < c->nsm ? 8 : 4);
+    launch_unpack_state(c->d_x3, c->d_v3, c->n, c->lv[0].L, s);
+}
+
+// The whole-batch step's launch sequence depends on nothing the step
+// computes, so it is captured once into a CUDA graph (again when eta
+// changes; set_systems drops it) and each outer step is one graph launch,
+// with no host round trip between steps.
+static int sys_step_graph(cc_ctx *c)
+{
+    if (c->sys_exec && c->sys_exec_eta == c->eta_run) return CC_OK;
+    if (c->sys_exec) cudaGraphExecDestroy(c->sys_exec);
+    c->sys_exec = nullptr;
+    if (!c->cap_stream) CC_CUDA(c, cudaStreamCreateWithFlags(&c->cap_stream, cudaStreamNonBlocking));
+    const unsigned long long g0 = g_launches;
+    CC_CUDA(c, cudaStreamBeginCapture(c->cap_stream, cudaStreamCaptureModeThreadLocal));
+    sys_step_launches(c, c->cap_stream);
+    cudaGraph_t g = nullptr;
+    const cudaError_t ec = cudaStreamEndCapture(c->cap_stream, &g);
+    c->sys_exec_launches = g_launches - g0;
+    g_launches = g0;  // (captured, not launched)
+    if (ec != cudaSuccess || !g) {
+        if (g) cudaGraphDestroy(g);
+        cudaGetLastError();
+        return fail(c, CC_E_CUDA, "capture of the whole-batch step failed");
+    }
+    const cudaError_t ei = cudaGraphInstantiate(&c->sys_exec, g, 0);
+    cudaGraphDestroy(g);
+    if (ei != cudaSuccess) {
+        c->sys_exec = nullptr;
+        cudaGetLastError();
+        return fail(c, CC_E_CUDA, "instantiation of the whole-batch step graph failed");
+    }
+    c->sys_exec_eta = c->eta_run;
     return CC_OK;
 }
 
@@ -1584,6 +1642,23 @@ int cc_evolve(cc_ctx *c, double t_end, double eta)
     CC_TRY(reset_call_counters(c));
     const double t0 = c->t;
     const bool spatial = c->p.precision == CC_PREC_MIXED && c->sys_off.size() == 2 && c->n >= SPATIAL_MIN_N;
+    if (c->sys_batch && !spatial && nsteps > 0) {
+        // every step one replay of the captured step; device errors are read
+        // after the call's last step (the state is undefined after one, as
+        // after an error of any step)
+        CC_TRY(sys_step_graph(c));
+        const unsigned long long ns = (unsigned long long)c->sys_off.size() - 1;
+        for (long long k = 0; k < nsteps; ++k) {
+            CC_CUDA(c, cudaGraphLaunch(c->sys_exec, c->stream));
+            g_launches += c->sys_exec_launches;
+            c->st.small_tasks += ns;
+        }
+        CC_TRY(check_device_error(c));
+        c->t = t0 + (double)nsteps * c->p.dt;
+        CC_CUDA(c, cudaGetLastError());
+        CC_TRY(harvest_counters(c));
+        return CC_OK;
+    }
     for (long long k = 0; k < nsteps; ++k) {
         if (spatial && (c->perm_age < 0 || c->perm_age >= SPATIAL_RENEW)) {
             if (!c->d_perm) {
@@ -1597,19 +1672,7 @@ int cc_evolve(cc_ctx *c, double t_end, double eta)
                           c->stream);
         if (spatial) ++c->perm_age;
         int rc = CC_OK;
-        if (c->sys_batch) {
-            // every system one task: evolve_cc(system, dt), split at depth 0
-            // (8 warps per CTA while there are fewer systems than SMs: each
-            // task's CTA-level phases are then the step's critical path)
-            const int ns = (int)c->sys_off.size() - 1;
-            int32_t *tk = c->d_sys_tasks;
-            CC_CUDA(c, cudaMemsetAsync(tk + 3 * ns + 1, 0, 4, c->stream));
-            const SmallParams SP = small_params(c, c->p.dt, 0);
-            launch_batch(c->lv[0].L, c->d_iota, tk + ns, tk + 2 * ns, tk, tk + 3 * ns, ns, SP, c->d_ctr,
-                         tk + 3 * ns + 1, c->d_near_ij, c->d_near_tau, c->near_cap, c->nsm, c->batch_scr, c->stream,
-                         ns < c->nsm ? 8 : 4);
-            c->st.small_tasks += (unsigned long long)ns;
-        } else if (c->p.split == CC_SPLIT_OK) {
+        if (c->p.split == CC_SPLIT_OK) {
             rc = ok_step(c);
         } else {
             rc = process(c, 0, c->p.dt, nullptr);
@@ -1882,6 +1945,8 @@ int cc_destroy(cc_ctx *c)
 {
     if (!c) return CC_OK;
     if (c->stream) cudaStreamSynchronize(c->stream);
+    if (c->sys_exec) cudaGraphExecDestroy(c->sys_exec);
+    if (c->cap_stream) cudaStreamDestroy(c->cap_stream);
     for (cudaStream_t st : c->sides)
         if (st) {
             cudaStreamSynchronize(st);

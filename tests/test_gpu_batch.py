@@ -158,3 +158,27 @@ def test_batch_s_small_is_checked(cclib, plummer_ic):
     with pytest.raises(cclib.CCError) as e:
         cclib.Context(m, x, v, s_small=513)
     assert e.value.code == -1
+
+
+def test_batch_step_graph_replays(cclib):
+    """Whole-batch mode runs each outer step as one replay of a captured CUDA
+    graph; a call with another eta captures the step again.  Several calls
+    and an eta change give the level path's result bit for bit (FP64)."""
+    m, x, v, off, dt = _case("systems")
+    out = []
+    for s_small in (512, 32):
+        c = cclib.Context(m, x, v, dt=dt, s_small=s_small)
+        c.set_systems(off)
+        c.evolve(dt)
+        c.evolve(3 * dt)
+        c.evolve(4 * dt, eta=0.02)
+        c.evolve(5 * dt, eta=0.03)
+        t, _, gx, gv = c.get_state()
+        out.append((gx, gv, c.stats()))
+        c.close()
+        assert abs(t - 5 * dt) < 1e-15
+    assert np.array_equal(out[0][0], out[1][0]) and np.array_equal(out[0][1], out[1][1])
+    for k in KEYS:
+        assert out[0][2][k] == out[1][2][k], k
+    # fill, pack, the batched kernel, unpack: four kernels per replayed step
+    assert out[0][2]["launches"] <= 4 * 5, out[0][2]["launches"]
