@@ -203,7 +203,10 @@ int cc_drift(cc_ctx *ctx, const int32_t *set, int64_t n_set,
  * pseudocode figure, Sec. 2.3), then t += dt.  (t_end - t) must be a whole
  * number of steps dt (relative slack 1e-9) else CC_E_ARG.  eta > 0
  * overrides params.eta.  Errors: CC_E_DEPTH, CC_E_TIMEOUT, CC_E_KEPLER,
- * CC_E_NONFINITE (state became non-finite). */
+ * CC_E_NONFINITE (state became non-finite); the state is undefined after
+ * one.  When every system fits the batched kernel (s_small) each step is
+ * one launch of a CUDA graph captured from the step (again after an eta
+ * change), and a device error is reported after the call's last step. */
 int cc_evolve(cc_ctx *ctx, double t_end, double eta);
 
 /* Copy out / replace the state (any pointer may be NULL to skip). */
