@@ -892,7 +892,7 @@ static int com_prepare(cc_ctx *c, LevelAlloc &a)
     CC_CUDA(c, cudaMemsetAsync(a.d_cl, 0xff, (size_t)a.L.total * 4, s));
     launch_com_prep(a.L, a.members, a.comp_start, a.comp_size, a.d_eq, a.d_eloc, a.Ke, a.d_cl, a.d_cm, s);
     launch_com_far(a.d_cm, a.d_eq, a.comp_size, a.d_eset, a.d_eloc, a.d_efirst, a.d_foff, a.d_K, a.Ke, c->p.theta,
-                   c->p.G, c->p.eps * c->p.eps, a.d_far, a.d_eany, c->d_ctr, s);
+                   c->p.G, c->p.eps * c->p.eps, a.d_far, a.d_eany, c->d_ctr, s, c->p.precision == CC_PREC_MIXED);
     return CC_OK;
 }
 
@@ -926,7 +926,8 @@ static int level_kick(cc_ctx *c, LevelAlloc &a, const int32_t *lab, const int32_
         CC_TRY(ensure_kpart(c, a.mk_chunks_max[var], a.F.cap));
         const int ev = ev_begin(c, 1, nullptr, timed ? TK_MK : -1, bin, var, (double)a.pairs);
         launch_kick_mixed(L, a.F, order, a.mk_off[var], (int)a.mk_blocks[var], MK_VAR_CHUNK[var], MK_VAR_SLICE[var],
-                          a.mk_chunks_max[var] > 1, c->p.eps * c->p.eps, h, c->d_ctr, c->d_kpart, lab, drift_dt, s);
+                          a.mk_chunks_max[var] > 1, c->p.eps * c->p.eps, h, c->d_ctr, c->d_kpart, lab, drift_dt, s,
+                          a.Ke > 0 ? &a.cv : nullptr);
         ev_end(c, ev);
     } else {
         // FP64: one shape (32-body i-tiles; the row order fixes the rounding)
@@ -951,12 +952,9 @@ static int dkd(cc_ctx *c, LevelAlloc &a, double h)
         // drifts ride on the copy and on the partial reduce
         launch_prep_kick(a.L, a.F, a.members, a.root, c->p.G, 0.5 * h, s);
         CC_TRY(level_kick(c, a, a.root, a.members, h, 0.5 * h));
-        if (a.Ke > 0) {
-            // the FP32 kick took the far pairs too: out again, then the monopole
-            launch_com_unkick(a.L, a.members, a.comp_start, a.comp_size, a.d_eq, a.d_eloc, a.d_eset, a.d_efirst,
-                              a.d_foff, a.d_K, a.d_far, a.Ke, c->p.G, c->p.eps * c->p.eps, h, s);
+        // the FP32 kick left the far pairs out: the monopole kick instead
+        if (a.Ke > 0)
             launch_com_apply(a.L, a.members, a.comp_start, a.comp_size, a.d_eq, a.d_cm, a.d_eany, a.Ke, h, s);
-        }
         return CC_OK;
     }
     launch_drift(a.L, a.root, 0.5 * h, s);

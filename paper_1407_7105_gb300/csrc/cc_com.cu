@@ -89,6 +89,61 @@ __global__ void k_com_far(double *cm, const int32_t *eq, const int32_t *comp_siz
     if (pairs) atomicAdd(&ctr->com_pairs, pairs);
 }
 
+// mixed form: one warp per eligible component a, its lanes over the
+// partners b (the same far decisions in the same FP64 operations), the
+// monopole sum reduced across the lanes (another FP64 rounding order: the
+// mixed form is not bit-tied to the oracle); K rows of K partners on
+// 32 K lanes instead of K
+__global__ void k_com_far_warp(double *cm, const int32_t *eq, const int32_t *comp_size, const int32_t *eset,
+                               const int32_t *eloc, const int32_t *efirst, const long long *foff, const int32_t *K,
+                               int Ke, double theta, double G, double eps2, unsigned char *far, int32_t *eany,
+                               DevCounters *ctr)
+{
+    const int g = (int)((blockIdx.x * blockDim.x + threadIdx.x) >> 5), lane = threadIdx.x & 31;
+    if (g >= Ke) return;  // (the whole warp)
+    const int s = eset[g], a = eloc[g], Ks = K[s], g0 = efirst[s];
+    const double *ca = cm + 8 * (size_t)g;
+    unsigned char *row = far + foff[s] + (long long)a * Ks;
+    double Ax = 0.0, Ay = 0.0, Az = 0.0;
+    int any = 0;
+    unsigned long long pairs = 0;
+    const int na = comp_size[eq[g]];
+    for (int b = lane; b < Ks; b += 32) {
+        unsigned char f = 0;
+        if (b != a) {
+            const double *cb = cm + 8 * (size_t)(g0 + b);
+            const double dx = __dsub_rn(cb[1], ca[1]), dy = __dsub_rn(cb[2], ca[2]), dz = __dsub_rn(cb[3], ca[3]);
+            const double dd = __dadd_rn(__dadd_rn(__dmul_rn(dx, dx), __dmul_rn(dy, dy)), __dmul_rn(dz, dz));
+            const double d = __dsqrt_rn(dd);
+            f = __dadd_rn(ca[4], cb[4]) < __dmul_rn(theta, d) ? 1 : 0;
+            if (f) {
+                const double d2 = __dadd_rn(dd, eps2);
+                const double w = __dmul_rn(__dmul_rn(G, cb[0]), __ddiv_rn(1.0, __dmul_rn(d2, __dsqrt_rn(d2))));
+                Ax = __dadd_rn(Ax, __dmul_rn(w, dx));
+                Ay = __dadd_rn(Ay, __dmul_rn(w, dy));
+                Az = __dadd_rn(Az, __dmul_rn(w, dz));
+                any = 1;
+                if (b > a) pairs += (unsigned long long)na * (unsigned long long)comp_size[eq[g0 + b]];
+            }
+        }
+        row[b] = f;
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        Ax += __shfl_xor_sync(0xffffffffu, Ax, o);
+        Ay += __shfl_xor_sync(0xffffffffu, Ay, o);
+        Az += __shfl_xor_sync(0xffffffffu, Az, o);
+        any |= __shfl_xor_sync(0xffffffffu, any, o);
+        pairs += __shfl_xor_sync(0xffffffffu, pairs, o);
+    }
+    if (lane == 0) {
+        double *c = cm + 8 * (size_t)g;
+        c[5] = Ax; c[6] = Ay; c[7] = Az;
+        eany[g] = any;
+        if (pairs) atomicAdd(&ctr->com_pairs, pairs);
+    }
+}
+
 // one block per eligible component, one thread per member
 __global__ void k_com_apply(Level L, const int32_t *members, const int32_t *comp_start, const int32_t *comp_size,
                             const int32_t *eq, const double *cm, const int32_t *eany, double h)
@@ -104,40 +159,6 @@ __global__ void k_com_apply(Level L, const int32_t *members, const int32_t *comp
     L.vz[i] = __dadd_rn(L.vz[i], __dmul_rn(h, c[7]));
 }
 
-// mixed form: one block per eligible component a, one thread per member i:
-// v_i -= h sum over the members j of a's far partners of the FP64 pair
-// force (the FP32 kick took them; what stays is its rounding)
-__global__ void k_com_unkick(Level L, const int32_t *members, const int32_t *comp_start, const int32_t *comp_size,
-                             const int32_t *eq, const int32_t *eloc, const int32_t *eset, const int32_t *efirst,
-                             const long long *foff, const int32_t *K, const unsigned char *far, double G, double eps2,
-                             double h)
-{
-    const int g = blockIdx.x;
-    const int q = eq[g];
-    if ((int)threadIdx.x >= comp_size[q]) return;
-    const int i = members[comp_start[q] + threadIdx.x];
-    const int s = eset[g], a = eloc[g], Ks = K[s], g0 = efirst[s];
-    const unsigned char *row = far + foff[s] + (long long)a * Ks;
-    const double xi = L.x[i], yi = L.y[i], zi = L.z[i];
-    double ax = 0.0, ay = 0.0, az = 0.0;
-    for (int b = 0; b < Ks; ++b) {
-        if (!row[b]) continue;
-        const int qb = eq[g0 + b], j0 = comp_start[qb], nb = comp_size[qb];
-        for (int k = 0; k < nb; ++k) {
-            const int j = members[j0 + k];
-            const double dx = L.x[j] - xi, dy = L.y[j] - yi, dz = L.z[j] - zi;
-            const double r2 = fma(dz, dz, fma(dy, dy, fma(dx, dx, eps2)));
-            const double w = G * L.m[j] / (r2 * sqrt(r2));
-            ax = fma(w, dx, ax);
-            ay = fma(w, dy, ay);
-            az = fma(w, dz, az);
-        }
-    }
-    L.vx[i] -= h * ax;
-    L.vy[i] -= h * ay;
-    L.vz[i] -= h * az;
-}
-
 void launch_com_prep(const Level &L, const int32_t *members, const int32_t *comp_start, const int32_t *comp_size,
                      const int32_t *eq, const int32_t *eloc, int Ke, int32_t *cl, double *cm, cudaStream_t s)
 {
@@ -149,11 +170,15 @@ void launch_com_prep(const Level &L, const int32_t *members, const int32_t *comp
 void launch_com_far(double *cm, const int32_t *eq, const int32_t *comp_size, const int32_t *eset,
                     const int32_t *eloc, const int32_t *efirst, const long long *foff, const int32_t *K, int Ke,
                     double theta, double G, double eps2, unsigned char *far, int32_t *eany, DevCounters *ctr,
-                    cudaStream_t s)
+                    cudaStream_t s, bool mixed)
 {
     if (Ke <= 0) return;
-    k_com_far<<<(Ke + 127) / 128, 128, 0, s>>>(cm, eq, comp_size, eset, eloc, efirst, foff, K, Ke, theta, G, eps2,
-                                               far, eany, ctr);
+    if (mixed)
+        k_com_far_warp<<<(unsigned)(((long long)Ke * 32 + 127) / 128), 128, 0, s>>>(
+            cm, eq, comp_size, eset, eloc, efirst, foff, K, Ke, theta, G, eps2, far, eany, ctr);
+    else
+        k_com_far<<<(Ke + 127) / 128, 128, 0, s>>>(cm, eq, comp_size, eset, eloc, efirst, foff, K, Ke, theta, G,
+                                                   eps2, far, eany, ctr);
     CC_COUNT_LAUNCH(1);
 }
 
@@ -162,17 +187,6 @@ void launch_com_apply(const Level &L, const int32_t *members, const int32_t *com
 {
     if (Ke <= 0) return;
     k_com_apply<<<Ke, COM_MAX_MEMBERS, 0, s>>>(L, members, comp_start, comp_size, eq, cm, eany, h);
-    CC_COUNT_LAUNCH(1);
-}
-
-void launch_com_unkick(const Level &L, const int32_t *members, const int32_t *comp_start, const int32_t *comp_size,
-                       const int32_t *eq, const int32_t *eloc, const int32_t *eset, const int32_t *efirst,
-                       const long long *foff, const int32_t *K, const unsigned char *far, int Ke, double G,
-                       double eps2, double h, cudaStream_t s)
-{
-    if (Ke <= 0) return;
-    k_com_unkick<<<Ke, COM_MAX_MEMBERS, 0, s>>>(L, members, comp_start, comp_size, eq, eloc, eset, efirst, foff, K,
-                                                far, G, eps2, h);
     CC_COUNT_LAUNCH(1);
 }
 

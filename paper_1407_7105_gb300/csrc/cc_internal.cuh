@@ -458,7 +458,8 @@ void launch_prep_kick(const Level &L, const FFView &F, const int32_t *order, con
                       double drift_dt, cudaStream_t s);
 void launch_kick_mixed(const Level &L, const FFView &F, const int32_t *order, const int32_t *koff, int nblocks,
                        int chunk, int slices, bool multi_chunk, double eps2, double h, DevCounters *ctr,
-                       double *partial, const int32_t *root, double drift_dt, cudaStream_t s);
+                       double *partial, const int32_t *root, double drift_dt, cudaStream_t s,
+                       const ComView *com = nullptr);
 
 // cc_small.cu
 // the batched kernel (k_batch): tasks tlist[0..*nt_ptr) (task c: packed
@@ -483,16 +484,10 @@ void launch_com_prep(const Level &L, const int32_t *members, const int32_t *comp
 void launch_com_far(double *cm, const int32_t *eq, const int32_t *comp_size, const int32_t *eset,
                     const int32_t *eloc, const int32_t *efirst, const long long *foff, const int32_t *K, int Ke,
                     double theta, double G, double eps2, unsigned char *far, int32_t *eany, DevCounters *ctr,
-                    cudaStream_t s);
+                    cudaStream_t s, bool mixed);
 // v_i += h A_g for the members of every eligible component with a far partner
 void launch_com_apply(const Level &L, const int32_t *members, const int32_t *comp_start, const int32_t *comp_size,
                       const int32_t *eq, const double *cm, const int32_t *eany, int Ke, double h, cudaStream_t s);
-// mixed form: the kick kernel kicked every cross pair in FP32; take the far
-// pairs back out (FP64 pair forces) before launch_com_apply adds the monopole
-void launch_com_unkick(const Level &L, const int32_t *members, const int32_t *comp_start, const int32_t *comp_size,
-                       const int32_t *eq, const int32_t *eloc, const int32_t *eset, const int32_t *efirst,
-                       const long long *foff, const int32_t *K, const unsigned char *far, int Ke, double G,
-                       double eps2, double h, cudaStream_t s);
 
 // cc_kepler.cu
 void launch_kepler(const Level &L, const int32_t *members, const int32_t *comp_start, const int32_t *klist,

@@ -519,6 +519,7 @@ constexpr int MK_GROUP = 8;       // j terms summed in plain FP32 per compensate
 struct __align__(16) MixedKickSmem {
     float4 pq[2][2 * MK_T];  // (hi, Gm), (lo) per j, two stages
     int32_t lab[2][MK_T];
+    int32_t cj[MK_T];        // centre-of-mass approximation: the j-tile's eligible components
     int32_t tiles[MK_CHUNK_MAX];
     int32_t apart[MK_CHUNK_MAX];  // 1: no label of the j-tile is one of the i-tile's
     int32_t ntiles;
@@ -537,10 +538,12 @@ __device__ __forceinline__ void mk_issue(MixedKickSmem &sm, int st, const FFView
 
 // Block = MK_T threads = (MK_T / S rows of the i-tile) x (S column slices of
 // each j-tile); the S partial sums of a row are combined in slice order.
-template <int S>
+// COM: pairs of two far components (ComView, the centre-of-mass
+// approximation) are left out, as in the FP64 kick.
+template <int S, bool COM>
 __global__ void __launch_bounds__(MK_T) k_kick_mixed(Level L, FFView F, const int32_t *order, const int32_t *koff,
                                                       int chunk, float eps2, double h, DevCounters *ctr,
-                                                      double *partial)
+                                                      double *partial, ComView cv)
 {
     constexpr int R = MK_T / S;  // i rows per block
     static_assert(R % 32 == 0, "one slice per warp");
@@ -584,11 +587,20 @@ __global__ void __launch_bounds__(MK_T) k_kick_mixed(Level L, FFView F, const in
     const int nt = sm.ntiles;
     if (tid == 0 && nt > 0) mk_issue(sm, 0, F, label, start + sm.tiles[0] * MK_T, min(MK_T, n - sm.tiles[0] * MK_T));
     float4 ip0 = make_float4(0, 0, 0, 0), ip1 = ip0;
-    int li = 0;
+    int li = 0, ci = -1;
     if (iv) {
         ip0 = F.pq[2 * t];
         ip1 = F.pq[2 * t + 1];
         li = label[t];
+        if constexpr (COM) ci = cv.cl[order[t]];
+    }
+    long long fo = 0;
+    int Ks = 0;
+    bool iany = false;
+    if constexpr (COM) {
+        fo = cv.foff[s];
+        Ks = cv.K[s];
+        iany = __syncthreads_or(ci >= 0) != 0;
     }
     float sx = 0.f, sy = 0.f, sz = 0.f, cx = 0.f, cy = 0.f, cz = 0.f;
     bool ok = true;
@@ -604,6 +616,13 @@ __global__ void __launch_bounds__(MK_T) k_kick_mixed(Level L, FFView F, const in
             break;
         }
         const int jn = min(MK_T, n - tj * MK_T);
+        bool fchk = false;  // far pairs possible in this tile
+        if constexpr (COM) {
+            int c = -1;
+            if (tid < jn) c = cv.cl[order[start + tj * MK_T + tid]];
+            sm.cj[tid] = c;
+            fchk = (__syncthreads_or(c >= 0) != 0) && iany;
+        }
         if (iv) {
             // g += G m_j r^-3 (x_j - x_i) over groups of MK_GROUP j in plain
             // FP32 (fused), each group sum then added to the compensated
@@ -620,6 +639,10 @@ __global__ void __launch_bounds__(MK_T) k_kick_mixed(Level L, FFView F, const in
                 ri = ri * fmaf(-0.5f * r2, ri * ri, 1.5f);  // one Newton step
                 float w = jp0.w * (ri * ri * ri);            // G m_j / r^3
                 if (check && sm.lab[st][k] == li) w = 0.f;  // same component (and self)
+                if constexpr (COM) {
+                    const int c = sm.cj[k];
+                    if (fchk && ci >= 0 && c >= 0 && cv.far[fo + (long long)ci * Ks + c]) w = 0.f;
+                }
                 gx = fmaf(w, dx, gx);
                 gy = fmaf(w, dy, gy);
                 gz = fmaf(w, dz, gz);
@@ -747,13 +770,22 @@ int mixed_kick_chunks(int n, int chunk)
 
 void launch_kick_mixed(const Level &L, const FFView &F, const int32_t *order, const int32_t *koff, int nblocks,
                        int chunk, int slices, bool multi_chunk, double eps2, double h, DevCounters *ctr,
-                       double *partial, const int32_t *root, double drift_dt, cudaStream_t s)
+                       double *partial, const int32_t *root, double drift_dt, cudaStream_t s, const ComView *com)
 {
     if (nblocks > 0) {
-        if (slices == 4)
-            k_kick_mixed<4><<<nblocks, MK_T, 0, s>>>(L, F, order, koff, chunk, (float)eps2, h, ctr, partial);
-        else
-            k_kick_mixed<1><<<nblocks, MK_T, 0, s>>>(L, F, order, koff, chunk, (float)eps2, h, ctr, partial);
+        const ComView cv = com ? *com : ComView{nullptr, nullptr, nullptr, nullptr};
+        const float e2 = (float)eps2;
+        if (com) {
+            if (slices == 4)
+                k_kick_mixed<4, true><<<nblocks, MK_T, 0, s>>>(L, F, order, koff, chunk, e2, h, ctr, partial, cv);
+            else
+                k_kick_mixed<1, true><<<nblocks, MK_T, 0, s>>>(L, F, order, koff, chunk, e2, h, ctr, partial, cv);
+        } else {
+            if (slices == 4)
+                k_kick_mixed<4, false><<<nblocks, MK_T, 0, s>>>(L, F, order, koff, chunk, e2, h, ctr, partial, cv);
+            else
+                k_kick_mixed<1, false><<<nblocks, MK_T, 0, s>>>(L, F, order, koff, chunk, e2, h, ctr, partial, cv);
+        }
         CC_COUNT_LAUNCH(1);
     }
     if ((multi_chunk && nblocks > 0) || (drift_dt > 0.0 && L.total > 0)) {
