@@ -78,12 +78,14 @@ typedef struct {
                           split with more edges than that leaves an incomplete
                           list, and the first halves of its components then run
                           a fresh split (results are the same, only slower)    */
-    int    fault_test; /* 0 in normal use.  Failure-path test hooks of the FP64 tau
-                          kernel, so that a test can see a bounded wait or retry
-                          run out and the call return CC_E_TIMEOUT without any
-                          GPU fault: 1 = its tile copy is announced but never
-                          issued, so the mbarrier wait gives up after ~2^20
-                          cycles; 2 = the union-find hook gives up at once     */
+    int    fault_test; /* 0 in normal use.  Failure-path test hooks of the tau
+                          kernels (the certified one of every split, the FP64
+                          one of cc_timestep_graph), so that a test can see a
+                          bounded wait or retry run out and the call return
+                          CC_E_TIMEOUT without any GPU fault: 1 = the tile copy
+                          is announced but never issued, so the mbarrier wait
+                          gives up after ~2^20 cycles; 2 = the union-find hook
+                          gives up at once                                      */
     int    split;      /* CC_SPLIT_CC (default); CC_SPLIT_HOLD: the HOLD method of
                           Sec. 2.1 on the same kernels -- the fast set F = {i :
                           tau(i) < h} is the union of the CC components, so it is

@@ -694,18 +694,21 @@ static int split_launch(cc_ctx *c, LevelAlloc &a, double h, const LevelAlloc *pa
     const TauParams P = tau_params(c, h);
     // a first half's records are a subset of its parent's: room for all
     CC_TRY(ensure_edges(c, a, parent ? parent->ecount : 0));
-    const bool mixed = c->p.precision == CC_PREC_MIXED;
-    // a fresh mixed split initialises its forest in the float-float copy's pass
-    if (parent || !mixed) launch_init_parent(a.L, a.E.count, s);
+    // Both forms decide the edge predicate tau(i,j) < h with the certified
+    // FP32 kernel, the FP64 tau where the FP32 bounds leave it open: the
+    // decisions are the FP64 predicate's, so the FP64 form's components,
+    // and with them its state, stay the oracle's bit for bit.
+    // (a fresh split initialises its forest in the float-float copy's pass)
+    if (parent) launch_init_parent(a.L, a.E.count, s);
     bool hook_in_seg = false;  // a first half's child edges hooked by the one-CTA segmentation
     const bool hold = c->p.split == CC_SPLIT_HOLD;
     if (parent) {
         // (the HOLD merge needs the complete forest before the segmentation)
         hook_in_seg = segment_hooks_edges(a.L.total) && !hold;
-        launch_edges_reuse(parent->E, parent->ecount, parent->L, parent->F, mixed, parent->inv, a.L, a.E, P, c->d_ctr,
+        launch_edges_reuse(parent->E, parent->ecount, parent->L, parent->F, true, parent->inv, a.L, a.E, P, c->d_ctr,
                            c->d_near_ij, c->d_near_tau, c->near_cap, s, !hook_in_seg);
     } else {
-        const int tk = mixed ? TK_TAUMIX : TK_TAU64;
+        const int tk = TK_TAUMIX;
         int bin;
         bool timed;
         const int var = tune_pick(c, tk, a.tau_blocks, a.pairs, &bin, &timed);
@@ -713,17 +716,9 @@ static int split_launch(cc_ctx *c, LevelAlloc &a, double h, const LevelAlloc *pa
         if (ntiles > 0x7fffffff) return fail(c, CC_E_ARG, "set too large for the tile grid");
         Level L = a.L;
         L.tile_off = a.tau_off[var];
-        int ev;
-        if (mixed) {
-            launch_prep_ff(a.L, a.F, c->p.G, true, s, true, a.E.count);
-            ev = ev_begin(c, 0, nullptr, timed ? tk : -1, bin, var, (double)a.pairs);
-            launch_tau_mixed(L, a.F, (int)ntiles, P, var, c->d_ctr, c->d_near_ij, c->d_near_tau, c->near_cap, a.E,
-                             s);
-        } else {
-            ev = ev_begin(c, 0, nullptr, timed ? tk : -1, bin, var, (double)a.pairs);
-            launch_tau_hook(L, (int)ntiles, P, var, c->d_ctr, nullptr, 0, c->d_near_ij, c->d_near_tau, c->near_cap,
-                            s, &a.E);
-        }
+        launch_prep_ff(a.L, a.F, c->p.G, true, s, true, a.E.count);
+        const int ev = ev_begin(c, 0, nullptr, timed ? tk : -1, bin, var, (double)a.pairs);
+        launch_tau_mixed(L, a.F, (int)ntiles, P, var, c->d_ctr, c->d_near_ij, c->d_near_tau, c->near_cap, a.E, s);
         ev_end(c, ev);
     }
     // HOLD: the set's non-trivial components form one fast set

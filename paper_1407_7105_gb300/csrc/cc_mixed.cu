@@ -322,11 +322,17 @@ __global__ void __launch_bounds__(T * S, 1024 / (T * S))
     }
     for (int e = tid; e < 2 * T; e += T * S) sm.lp[e] = e;
     __syncthreads();
+    // fault_test = 1: the copy is announced but never issued, so the wait
+    // below runs out (a test of the bounded wait; no copy is in flight)
+    const bool no_copy = P.fault_test == 1;
+    const long long wait_cycles = no_copy ? FAULT_TEST_WAIT_CYCLES : TMA_WAIT_CYCLES;
     if (tid == 0) {
         const unsigned bytes = (unsigned)jn * 32u;
         mbar_expect_tx(&sm.bar, 2u * bytes);
-        tma_load_1d(sm.pq, F.pq + 2 * (size_t)j0, bytes, &sm.bar);
-        tma_load_1d(sm.vq, F.vq + 2 * (size_t)j0, bytes, &sm.bar);
+        if (!no_copy) {
+            tma_load_1d(sm.pq, F.pq + 2 * (size_t)j0, bytes, &sm.bar);
+            tma_load_1d(sm.vq, F.vq + 2 * (size_t)j0, bytes, &sm.bar);
+        }
     }
     const int il = ti * T + row;
     const bool iv = il < n;
@@ -336,10 +342,11 @@ __global__ void __launch_bounds__(T * S, 1024 / (T * S))
         ip0 = F.pq[2 * i];
         iv0 = F.vq[2 * i];
     }
-    const bool got = mbar_wait(&sm.bar, 0, TMA_WAIT_CYCLES);
+    const bool got = mbar_wait(&sm.bar, 0, wait_cycles);
     if (__syncthreads_or(!got)) {
         raise_err(ctr, DERR_TMA_TIMEOUT);
-        mbar_wait(&sm.bar, 0, TMA_WAIT_CYCLES);
+        // let a copy still in flight land before the CTA exits
+        mbar_wait(&sm.bar, 0, wait_cycles);
         return;
     }
     unsigned long long my_edges = 0, my_fp64 = 0;
@@ -464,7 +471,8 @@ __global__ void __launch_bounds__(T * S, 1024 / (T * S))
         if (r != e) {
             const int ge = (e < T) ? start + ti * T + e : j0 + (e - T);
             const int gr = (r < T) ? start + ti * T + r : j0 + (r - T);
-            if (!uf_union(L.parent, ge, gr)) raise_err(ctr, DERR_UF_RETRY);
+            // (fault_test = 2: every hook gives up at once, a test of the retry cap)
+            if (!uf_union(L.parent, ge, gr, P.fault_test == 2 ? 0 : UF_RETRY_MAX)) raise_err(ctr, DERR_UF_RETRY);
         }
     }
 #pragma unroll
