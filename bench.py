@@ -684,6 +684,41 @@ def run_split_compare(args):
     return 0
 
 
+def run_paper_step(args):
+    """The paper's worked case (Sec. 3.1): the first global step of its
+    smoothed Plummer test, N = 1024, eps = 1/256, eta = 0.01, dt = 700/512,
+    both forms (JSON lines): wall time of the step (a warm-up step of the
+    same state first), splits, kick pairs, drifts, depth -- the counts the
+    paper prints for its serial code."""
+    import torch
+
+    from paper_1407_7105_gb300 import build, cc, ics
+    build.build()
+    dev = torch.device("cuda", 0)
+    m, x, v = ics.plummer(1024, seed=args.seed)
+    dm, dx, dv = (torch.tensor(q, device=dev) for q in (m, x, v))
+    dt = 700.0 / 512
+    for form in ("fp64", "mixed"):
+        prec = cc.PREC_MIXED if form == "mixed" else cc.PREC_FP64
+        ctx = cc.Context(dm, dx, dv, dt=dt, eta=0.01, eps=1.0 / 256, precision=prec, s_small=args.s_small)
+        ctx.evolve(dt)  # warm-up: allocations and the launch-shape tuner's trials
+        ctx.set_state(0.0, dm, dx, dv)
+        ctx.reset_stats()
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        ctx.evolve(dt)
+        torch.cuda.synchronize()
+        sec = time.perf_counter() - t0
+        st = ctx.stats()
+        ctx.close()
+        print(json.dumps({"paper_step": True, "workload": "Plummer N=1024, eps=1/256, eta=0.01, one step dt=700/512",
+                          "form": form, "s_small": args.s_small, "seconds": sec, "splits": st["splits"],
+                          "kick_pairs": st["kick_pairs"],
+                          "tau_pairs": st["tau_pairs"], "tau_pairs_evaluated": st["tau_evaluated"],
+                          "drifts": st["drifts"], "max_depth": st["max_depth_seen"]}), flush=True)
+    return 0
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -707,6 +742,8 @@ def main():
                     help="energy error of the fractal and the systems batch against eta (mixed form)")
     ap.add_argument("--com-sweep", action="store_true",
                     help="the centre-of-mass approximation of V_CC against the exact kick (both forms, theta sweep)")
+    ap.add_argument("--paper-step", action="store_true",
+                    help="the paper's worked case (Sec. 3.1, N = 1024, one step of 700/512): both forms' wall time and counts")
     ap.add_argument("--split-compare", action="store_true",
                     help="CC, HOLD and OK splits on 256- and 1024-body spheres to t = 1 (FP64)")
     ap.add_argument("--sweep-steps", type=int, default=16)
@@ -731,6 +768,8 @@ def main():
         return run_com_sweep(args)
     if args.split_compare:
         return run_split_compare(args)
+    if args.paper_step:
+        return run_paper_step(args)
     if world > 1:
         import torch.distributed as dist
         dist.init_process_group("nccl")

@@ -1047,11 +1047,15 @@ static int process(cc_ctx *c, int d, double h, const LevelAlloc *parent)
     std::vector<int32_t> &lstart = a.v_lstart, &lsize = a.v_lsize;
     lstart.clear();
     lsize.clear();
+    // (the classification's rule: a lone large component stays on the levels)
+    int n_solo = 0;
+    for (int q = 0; q < ncomp; ++q) n_solo += (a.h_size[q] > BATCH_SOLO && a.h_size[q] <= smax) ? 1 : 0;
+    const int slim = batch_limit(smax, n_solo);
     int nk = 0, ns = 0;
     for (int q = 0; q < ncomp; ++q) {
         const int sz = a.h_size[q];
         if (c->p.kepler && sz == 2) ++nk;
-        else if (sz <= smax) ++ns;
+        else if (sz <= slim) ++ns;
         else {
             lstart.push_back(a.h_start[q]);
             lsize.push_back(sz);

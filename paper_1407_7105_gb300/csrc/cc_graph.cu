@@ -382,12 +382,21 @@ __device__ __forceinline__ int warp_inclusive_scan(int v)
 // CTA that segmented them; sh: CLS_SH ints of shared memory
 __device__ void classify_components(const int32_t *comp_size, int nc, const ClassifyArgs &C, int *sh)
 {
-    int *s_cnt = sh, *s_pos = sh + CLS_NB, *s_nk = sh + 2 * CLS_NB;
+    int *s_cnt = sh, *s_pos = sh + CLS_NB, *s_nk = sh + 2 * CLS_NB, *s_solo = sh + 2 * CLS_NB + 1;
     const int tid = threadIdx.x, nt = blockDim.x;
-    const int smax = C.s_small;
     for (int z = tid; z < CLS_NB; z += nt) s_cnt[z] = 0;
-    if (tid == 0) *s_nk = 0;
+    if (tid == 0) {
+        *s_nk = 0;
+        *s_solo = 0;
+    }
     __syncthreads();
+    // the components above BATCH_SOLO bodies that the batched kernel could take
+    for (int q = tid; q < nc; q += nt) {
+        const int sz = comp_size[q];
+        if (sz > BATCH_SOLO && sz <= C.s_small) atomicAdd(s_solo, 1);
+    }
+    __syncthreads();
+    const int smax = batch_limit(C.s_small, *s_solo);
     for (int q = tid; q < nc; q += nt) {
         const int sz = comp_size[q];
         if (C.kepler && sz == 2) C.klist[atomicAdd(s_nk, 1)] = q;

@@ -390,7 +390,18 @@ bool segment_hooks_edges(int total);
 constexpr int BATCH_NMAX = 512;
 __host__ __device__ constexpr int size_bucket(int sz) { return sz <= 32 ? sz : 32 + (sz - 17) / 16; }
 constexpr int CLS_NB = size_bucket(BATCH_NMAX) + 1;
-constexpr int CLS_SH = 2 * CLS_NB + 1;
+constexpr int CLS_SH = 2 * CLS_NB + 2;
+// A component of more than BATCH_SOLO bodies goes to the batched kernel only
+// when at least BATCH_SOLO_MIN such components of the split share its
+// launch: alone, one CTA's whole recursion of a few hundred bodies is longer
+// than the GPU-wide levels (the paper's 1024-body step: 1.19 s with every
+// component of <= 512 bodies in the batched kernel, 0.70 s with <= 128).
+// The device classification and the host's lists apply the same rule.
+constexpr int BATCH_SOLO = 128, BATCH_SOLO_MIN = 8;
+__host__ __device__ constexpr int batch_limit(int smax, int n_above_solo)
+{
+    return (smax > BATCH_SOLO && n_above_solo < BATCH_SOLO_MIN) ? BATCH_SOLO : smax;
+}
 // where the classification (see launch_classify) writes its lists
 struct ClassifyArgs {
     int s_small, kepler;
