@@ -470,8 +470,10 @@ def run_gpu(args, rank, world):
         kname, kms, kl, flops = "tau", tm["tau_ms"], tm["tau_launches"], TAU_FLOPS * tm["tau_pairs"]
     else:
         kname, kms, kl, flops = "kick", tm["kick_ms"], tm["kick_launches"], KICK_FLOPS * tm["kick_pairs"]
-    kname = ("k_tau_mixed" if kname == "tau" else "k_kick_mixed") if fp32 else \
-            ("k_tau_hook" if kname == "tau" else "k_kick64")
+    # both forms' splits run the certified FP32 tau kernel; the kicks are the
+    # form's own (FP32 in the mixed form, FP64 in the FP64 form)
+    fp32 = fp32 or kname == "tau"
+    kname = "k_tau_mixed" if kname == "tau" else ("k_kick_mixed" if fp32 else "k_kick64")
     achieved = flops / (kms * 1e-3) / 1e12 if kms > 0 else None
     peak = (f32_peak if fp32 else f64_peak) / 1e12
     small_flops = TAU_FLOPS * tm["small_tau_evaluated"] + KICK_FLOPS * tm["small_kick_pairs"]
