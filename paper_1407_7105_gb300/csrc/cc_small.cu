@@ -7,8 +7,8 @@
 // all sets of the same level are advanced in lockstep (they are independent
 // closed Hamiltonians, Sec. 2.2), level by level with an explicit stack:
 //   phase 0: split the lane's set at h_k: tau(i,j) < h_k over the set (the
-//            exact FP64 predicate, or the certified FP32 decision with FP64
-//            fallback), components by mask closure; push level k+1 with
+//            certified FP32 decision, the exact FP64 predicate where it
+//            stays open: both forms), components by mask closure; push level k+1 with
 //            the non-trivial components (first half)
 //   phase 1: Kepler half step of two-body components (CC_KEPLER), the DKD
 //            of level k, the second Kepler half step; push level k+1 again
@@ -145,7 +145,7 @@ struct NearLog {
     double tol;
 };
 
-// FP64 form: edge depth over `levels` thresholds h 2^-m (returns levels when
+// The FP64 tau's edge depth over `levels` thresholds h 2^-m (returns levels when
 // every one is an edge).  log(tau, h_m) runs at the thresholds next to tau
 // (h_m just above and at or below it): the only ones a near-threshold pair
 // can sit at.
@@ -216,22 +216,31 @@ __device__ __forceinline__ bool pair_next(unsigned long long &pend, int &d)
 // arithmetic (bit-identical to the oracle): the leaf's row sums are
 // a_a = (G m_b) r^-3 (x_b - x_a) and a_b with -dx.
 // Returns 0, DERR_DEPTH or DERR_SMALL_OVERFLOW (work cap).
+// The edge decisions are the certified FP32 ones from the rounded FP64
+// differences (relative error u, as in the mixed pair path), the FP64 tau
+// where they stay open: the FP64 predicate's decisions (Q.etah = eta/h0).
 __device__ unsigned pair_path(double A[7], double B[7], double h0, int depth0, int e0, const SmallParams &SP,
-                              const TauParams &P, PairCounters &pc, const NearLog &nl, int ga, int gb)
+                              const TauParams &P, const MixedTauParams &Q, PairCounters &pc, const NearLog &nl,
+                              int ga, int gb)
 {
     const int dmax = min(SP.max_depth - depth0, 61);  // an edge at node d needs d + 1 <= dmax
+    const float muf = Q.G * (fl32(A[6]) + fl32(B[6]));
     unsigned long long pend = 0ull;
     int d = 0, e = e0;
     for (long long work = 0; work < PAIR_VISIT_LIMIT;) {
         if (e < 0) {
-            const double tau = tau_fp64_ool(__dsub_rn(A[0], B[0]), __dsub_rn(A[1], B[1]), __dsub_rn(A[2], B[2]),
-                                        __dsub_rn(A[3], B[3]), __dsub_rn(A[4], B[4]), __dsub_rn(A[5], B[5]), A[6],
-                                        B[6], P);
-            ++pc.fp64;
+            const double dx0 = __dsub_rn(A[0], B[0]), dx1 = __dsub_rn(A[1], B[1]), dx2 = __dsub_rn(A[2], B[2]);
+            const double dv0 = __dsub_rn(A[3], B[3]), dv1 = __dsub_rn(A[4], B[4]), dv2 = __dsub_rn(A[5], B[5]);
+            const TauPrep32 t = tau_prep_fp32(fl32(dx0), fl32(dx1), fl32(dx2), fl32(dv0), fl32(dv1), fl32(dv2), muf,
+                                              0.f, 0.f, Q);
             ++pc.evals;
-            e = edge_depth_fp64(tau, scale2m(h0, d), max(dmax - d + 1, 1), [&](double tv, double hm) {
-                near_log(tv, hm, nl.tol, nl.ctr, ga, gb, nl.ij, nl.tau, nl.cap);
-            });
+            bool used64;
+            e = edge_depth_mixed(
+                t, Q.etah * pow2f(d), scale2m(h0, d), max(dmax - d + 1, 1),
+                [&]() { return tau_fp64_ool(dx0, dx1, dx2, dv0, dv1, dv2, A[6], B[6], P); },
+                [&](double tv, double hm) { near_log(tv, hm, nl.tol, nl.ctr, ga, gb, nl.ij, nl.tau, nl.cap); },
+                used64);
+            pc.fp64 += used64 ? 1 : 0;
         }
         if (e > 0 && d + e > dmax) return DERR_DEPTH;  // an edge at a node below the cap
         pc.split += e + 1;
@@ -403,12 +412,12 @@ __device__ __forceinline__ unsigned k8_pair_handoff(K8Warp &S, int lane, double 
         const int ga = S.gid[lane], gb = S.gid[j];
         const int ec = S.e[j][lane];
         const int e0 = (eoff >= 0 && ec < ecap) ? ec - eoff : -1;
-        if (mixed) {
-            MixedTauParams Qs = Q;
-            Qs.etah = etah_sub;  // eta/hsub
+        MixedTauParams Qs = Q;
+        Qs.etah = etah_sub;  // eta/hsub
+        if (mixed)
             err = pair_path_rel(st, B, hsub, dsub, e0, SP, P, Qs, pc, nl, ga, gb);
-        } else
-            err = pair_path(st, B, hsub, dsub, e0, SP, P, pc, nl, ga, gb);
+        else
+            err = pair_path(st, B, hsub, dsub, e0, SP, P, Qs, pc, nl, ga, gb);
 #pragma unroll
         for (int c = 0; c < 6; ++c) S.d[c][j] = B[c];
     }
@@ -495,7 +504,9 @@ __device__ __forceinline__ void small_task(K8Warp &S, const SView V, const int32
             // every pair's edge depth; a first half reads them, since its
             // state is the one its parent split.
             if (cf[k] < 0) {
-                k8_publish(S, lane, st, mixed);
+                // (both forms: the certified FP32 decisions need the
+                // float-float state; the FP64 tau settles what they leave open)
+                k8_publish(S, lane, st, true);
                 P.h = h;
                 const float etah = etah_c * pow2f(k);
                 const float c11 = 11.f * U32 * U32;
@@ -516,7 +527,7 @@ __device__ __forceinline__ void small_task(K8Warp &S, const SView V, const int32
                 // subset, so its pairs are among these (deep levels of a
                 // big component leave few)
                 const uint32_t act = __reduce_or_sync(FULL, mine);
-                if (mine && mixed) {
+                if (mine) {
                     // the lane's own float-float state in registers (the
                     // byte stores of the edge depths below may alias any
                     // shared word, so reads from S would be repeated)
@@ -558,15 +569,6 @@ __device__ __forceinline__ void small_task(K8Warp &S, const SView V, const int32
                         const TauPrep32 t0 = prep(j0), t1 = prep(j1);
                         finish(j0, t0);
                         if (two) finish(j1, t1);
-                    }
-                } else if (mine) {
-                    for (int j = 0; j < n; ++j) {
-                        if (j == lane || !((mine >> j) & 1u)) continue;
-                        const int e = edge_depth_fp64(tau64_of(j), h, levels,
-                                                      [&](double tv, double hm) { log_of(j, tv, hm); });
-                        if (lane < j) ++cn.fp64;
-                        S.e[j][lane] = (unsigned char)e;
-                        if (lane < j) ++cn.eval;
                     }
                 }
                 cf[k] = (signed char)k;
@@ -817,9 +819,9 @@ __global__ void __launch_bounds__(K8_WARPS * 32) k_small(Level L, const int32_t 
 // tasks of at most 32 bodies the CTA's warps take them one each, as k_small.
 //
 // A frame holds one set of more than 32 bodies (ascending particle id, in
-// `sl`).  Its split: tau(i,j) < h over the set's pairs (the FP64 predicate,
-// or the certified FP32 decision with the FP64 predicate where it cannot
-// decide), union-find over set positions in shared memory (root = the
+// `sl`).  Its split: tau(i,j) < h over the set's pairs (in both forms the
+// certified FP32 decision, the FP64 predicate where it cannot decide),
+// union-find over set positions in shared memory (root = the
 // smallest position, so labels are the smallest particle id), then the
 // members by component into `cl` (components in root order, ascending
 // inside): every component is a contiguous, ascending member list, which is
@@ -848,8 +850,7 @@ struct KMFrame {
 
 // A frame's set staged in shared memory, four 16-byte words per body (one
 // vector load each in the pair loops):
-//   split, FP64: {x, y} {z, vx} {vy, vz} {m, -}
-//   split, mixed: (x, y, z hi, fl32 m) (x, y, z lo, max |x hi|) (v hi, max |v hi|) (v lo, -)
+//   split (both forms): (x, y, z hi, fl32 m) (x, y, z lo, max |x hi|) (v hi, max |v hi|) (v lo, -)
 //   DKD, FP64: {x, y} {z, m};  DKD, mixed: (x, y, z hi, fl32 m) (x, y, z lo, label bits)
 struct KMStage {
     union {
@@ -938,26 +939,20 @@ __device__ void km_split(KMShared<W> &sh, KMFrame &F, const SView V, const Small
     const int tid = threadIdx.x, lane = tid & 31;
     const int n = F.n;
     const double h = F.h;
-    const bool mixed = SP.precision == CC_PREC_MIXED;
+    // both forms: the certified FP32 decision from the float-float state,
+    // the FP64 tau (from the FP64 state) where it stays open
     for (int p = tid; p < n; p += KM_T) {
         const int k = F.sl[p];
         const double st[7] = {V.x[k], V.y[k], V.z[k], V.vx[k], V.vy[k], V.vz[k], V.m[k]};
-        if (mixed) {
-            float hi[6], lo[6];
+        float hi[6], lo[6];
 #pragma unroll
-            for (int c = 0; c < 6; ++c) ff_split(st[c], hi[c], lo[c]);
-            const float xm = fmaxf(fabsf(hi[0]), fmaxf(fabsf(hi[1]), fabsf(hi[2])));
-            const float vm = fmaxf(fabsf(hi[3]), fmaxf(fabsf(hi[4]), fabsf(hi[5])));
-            T.q[0][p] = make_float4(hi[0], hi[1], hi[2], fl32(st[6]));
-            T.q[1][p] = make_float4(lo[0], lo[1], lo[2], xm);
-            T.q[2][p] = make_float4(hi[3], hi[4], hi[5], vm);
-            T.q[3][p] = make_float4(lo[3], lo[4], lo[5], 0.f);
-        } else {
-            T.d[0][p] = make_double2(st[0], st[1]);
-            T.d[1][p] = make_double2(st[2], st[3]);
-            T.d[2][p] = make_double2(st[4], st[5]);
-            T.d[3][p] = make_double2(st[6], 0.0);
-        }
+        for (int c = 0; c < 6; ++c) ff_split(st[c], hi[c], lo[c]);
+        const float xm = fmaxf(fabsf(hi[0]), fmaxf(fabsf(hi[1]), fabsf(hi[2])));
+        const float vm = fmaxf(fabsf(hi[3]), fmaxf(fabsf(hi[4]), fabsf(hi[5])));
+        T.q[0][p] = make_float4(hi[0], hi[1], hi[2], fl32(st[6]));
+        T.q[1][p] = make_float4(lo[0], lo[1], lo[2], xm);
+        T.q[2][p] = make_float4(hi[3], hi[4], hi[5], vm);
+        T.q[3][p] = make_float4(lo[3], lo[4], lo[5], 0.f);
         T.par[p] = p;
         T.cnt[p] = 0;
         T.cst[p] = 0;
@@ -977,16 +972,10 @@ __device__ void km_split(KMShared<W> &sh, KMFrame &F, const SView V, const Small
     // the FP64 tau of positions lo < hi, in that order (the other kernels'
     // pair order; symmetric bit for bit)
     auto tau64 = [&](int lo, int hi) {
-        if (mixed) {
-            const int a = F.sl[lo], b = F.sl[hi];
-            return tau_fp64_ool(__dsub_rn(V.x[a], V.x[b]), __dsub_rn(V.y[a], V.y[b]), __dsub_rn(V.z[a], V.z[b]),
-                                __dsub_rn(V.vx[a], V.vx[b]), __dsub_rn(V.vy[a], V.vy[b]),
-                                __dsub_rn(V.vz[a], V.vz[b]), V.m[a], V.m[b], P);
-        }
-        const double2 a0 = T.d[0][lo], a1 = T.d[1][lo], a2 = T.d[2][lo], a3 = T.d[3][lo];
-        const double2 b0 = T.d[0][hi], b1 = T.d[1][hi], b2 = T.d[2][hi], b3 = T.d[3][hi];
-        return tau_fp64_ool(__dsub_rn(a0.x, b0.x), __dsub_rn(a0.y, b0.y), __dsub_rn(a1.x, b1.x),
-                            __dsub_rn(a1.y, b1.y), __dsub_rn(a2.x, b2.x), __dsub_rn(a2.y, b2.y), a3.x, b3.x, P);
+        const int a = F.sl[lo], b = F.sl[hi];
+        return tau_fp64_ool(__dsub_rn(V.x[a], V.x[b]), __dsub_rn(V.y[a], V.y[b]), __dsub_rn(V.z[a], V.z[b]),
+                            __dsub_rn(V.vx[a], V.vx[b]), __dsub_rn(V.vy[a], V.vy[b]),
+                            __dsub_rn(V.vz[a], V.vz[b]), V.m[a], V.m[b], P);
     };
     bool uf_ok = true;
     auto edge_found = [&](int p, int j) {
@@ -1009,7 +998,7 @@ __device__ void km_split(KMShared<W> &sh, KMFrame &F, const SView V, const Small
             const int p = side == 0 ? base + tid : base + 2 * KM_T - 1 - tid;
             if (p >= n - 1) continue;
             cn.eval += (unsigned long long)(n - 1 - p);
-            if (mixed) {
+            {
                 const float4 a0 = T.q[0][p], a1 = T.q[1][p], a2 = T.q[2][p], a3 = T.q[3][p];
                 auto prep = [&](int j) {
                     const float4 b0 = T.q[0][j], b1 = T.q[1][j], b2 = T.q[2][j], b3 = T.q[3][j];
@@ -1026,9 +1015,6 @@ __device__ void km_split(KMShared<W> &sh, KMFrame &F, const SView V, const Small
                 // one pair at a time: two in flight shortened a lone task's
                 // split but cost throughput when every SM was busy with tasks
                 for (int j = p + 1; j < n; ++j) finish(j, prep(j));
-            } else {
-                for (int j = p + 1; j < n; ++j)
-                    if (decide64(p, j)) edge_found(p, j);
             }
         }
     }
