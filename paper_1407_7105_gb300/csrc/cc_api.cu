@@ -212,6 +212,8 @@ struct cc_ctx {
     // inverse id map, row pointers and drift flags, each set's segment and
     // arena offset, the arena of the recursion, node stamps and positions
     int32_t *ok_edges = nullptr, *ok_dir = nullptr;
+    EdgeRec *ok_rec = nullptr;                // the outer level's edge records (certified kernel)
+    unsigned long long *ok_reccnt = nullptr;
     long long ok_cap = 0;
     void *ok_sort = nullptr;
     int32_t *ok_inv = nullptr, *ok_row = nullptr, *ok_rest = nullptr, *ok_loc = nullptr;
@@ -757,7 +759,7 @@ static int split_finish(cc_ctx *c, LevelAlloc &a, const LevelAlloc *parent, int 
     }
     c->st.splits += a.h_set_n.size();
     c->st.tau_pairs += tp;
-    if (c->p.precision != CC_PREC_MIXED) c->st.tau_fp64 += tp;
+    // (tau_fp64: the split kernels count the pairs whose FP64 tau they took)
     if (!parent) c->st.tau_evaluated += tp;
     if (c->timing) {
         if (!parent) c->tm.tau_pairs += tp;
@@ -1222,7 +1224,6 @@ static int ok_node(cc_ctx *c, const int32_t *list, long long np, double h, int d
     c->st.splits += hc[2];
     c->st.tau_pairs += (unsigned long long)np;
     c->st.tau_evaluated += (unsigned long long)np;
-    c->st.tau_fp64 += (unsigned long long)np;
     c->st.components += hc[3];
     if (depth > c->st.max_depth_seen) c->st.max_depth_seen = depth;
     int32_t *child = D.child, *S = D.S;
@@ -1266,25 +1267,29 @@ static int ok_step(cc_ctx *c)
     if (c->ok_cap == 0) {
         c->ok_cap = std::max<long long>(4096, (long long)total * 4);
         CC_TRY(ok_grow(c, (void **)&c->ok_edges, (size_t)c->ok_cap * 8));
+        CC_TRY(ok_grow(c, (void **)&c->ok_rec, (size_t)c->ok_cap * sizeof(EdgeRec)));
         CC_TRY(ok_grow(c, (void **)&c->ok_dir, (size_t)c->ok_cap * 16));
         CC_TRY(ok_grow(c, &c->ok_sort, edge_sort_scratch_bytes(2 * c->ok_cap)));
     }
+    if (!c->ok_reccnt) CC_TRY(ok_grow(c, (void **)&c->ok_reccnt, 8));
     // the outer level's tau over every pair of each set, its fast pairs
     const TauParams P = tau_params(c, dt);
     Level UL = a.L;
     UL.tile_off = a.tau_off[TAU_VAR_128];
     const long long ntiles = a.tau_blocks[TAU_VAR_128];
     if (ntiles > 0x7fffffff) return fail(c, CC_E_ARG, "set too large for the tile grid");
-    // (the edge kernel takes its list slots from the edge counter: it starts
-    // at zero, and the count goes to the statistics from the host)
+    // The certified tau kernel (every split's: the FP64 predicate's
+    // decisions) records every fast pair; the record count is the list
+    // length (the kernel's edge counter goes to the statistics from the host)
     long long ne = 0;
     for (int pass = 0; pass < 2; ++pass) {
         CC_CUDA(c, cudaMemsetAsync(&c->d_ctr->edges, 0, 8, s));
-        launch_init_parent(a.L, nullptr, s);
-        launch_tau_hook(UL, (int)ntiles, P, TAU_VAR_128, c->d_ctr, c->ok_edges, c->ok_cap, c->d_near_ij,
-                        c->d_near_tau, c->near_cap, s);
+        // the float-float copy, the forest as singletons, the record count 0
+        launch_prep_ff(a.L, a.F, c->p.G, true, s, true, c->ok_reccnt);
+        launch_tau_mixed(UL, a.F, (int)ntiles, P, TAU_VAR_128, c->d_ctr, c->d_near_ij, c->d_near_tau, c->near_cap,
+                         EdgeList{c->ok_rec, c->ok_reccnt, c->ok_cap}, s);
         unsigned long long e1 = 0;
-        CC_CUDA(c, cudaMemcpyAsync(&e1, &c->d_ctr->edges, 8, cudaMemcpyDeviceToHost, s));
+        CC_CUDA(c, cudaMemcpyAsync(&e1, c->ok_reccnt, 8, cudaMemcpyDeviceToHost, s));
         CC_CUDA(c, cudaStreamSynchronize(s));
         CC_CUDA(c, cudaMemsetAsync(&c->d_ctr->edges, 0, 8, s));
         ne = (long long)e1;
@@ -1292,9 +1297,11 @@ static int ok_step(cc_ctx *c)
         // more fast pairs than room: grow and redo
         c->ok_cap = 2 * ne;
         CC_TRY(ok_grow(c, (void **)&c->ok_edges, (size_t)c->ok_cap * 8));
+        CC_TRY(ok_grow(c, (void **)&c->ok_rec, (size_t)c->ok_cap * sizeof(EdgeRec)));
         CC_TRY(ok_grow(c, (void **)&c->ok_dir, (size_t)c->ok_cap * 16));
         CC_TRY(ok_grow(c, &c->ok_sort, edge_sort_scratch_bytes(2 * c->ok_cap)));
     }
+    launch_ok_rec_pairs(c->ok_rec, ne, a.L.gid, c->ok_edges, s);
     launch_ok_level(a.L, c->ok_edges, ne, c->ok_inv, c->ok_dir, c->ok_sort, c->ok_row, c->ok_rest, c->ok_seg,
                     c->d_ctr, s);
     unsigned long long nonempty = 0;
@@ -1954,7 +1961,7 @@ int cc_destroy(cc_ctx *c)
     free_level(c->unit);
     void *ptrs[] = {c->d_x3, c->d_v3, c->d_m, c->d_ctr, c->d_near_ij, c->d_near_tau, c->d_partial,
                     c->tmp, c->seg_scratch, c->d_sys_off, c->d_bad, c->d_kpart, c->d_perm, c->d_box,
-                    c->batch_scr, c->d_sys_tasks, c->d_iota, c->ok_edges, c->ok_dir, c->ok_sort,
+                    c->batch_scr, c->d_sys_tasks, c->d_iota, c->ok_edges, c->ok_rec, c->ok_reccnt, c->ok_dir, c->ok_sort,
                     c->ok_inv, c->ok_row, c->ok_rest, c->ok_loc, c->ok_stamp, c->ok_seg, c->ok_aoff,
                     c->ok_arena, c->ok_hst, c->ok_cnt, c->ok_scan, c->ok_ndir, c->ok_nsort};
     for (void *q : ptrs)

@@ -339,6 +339,8 @@ void launch_kick(const Level &L, const int32_t *label, int nitiles, double G, do
 // (particle ids, count ne): pairs to packed indices and sorted, both
 // directions sorted (dir, 2 ne pairs), row pointers, the drift flags of the
 // particles without a fast partner (rest), each set's segment of the list
+// the certified tau kernel's edge records -> particle-id pairs (OK split's outer level)
+void launch_ok_rec_pairs(const EdgeRec *rec, long long ne, const int32_t *gid, int32_t *edges, cudaStream_t s);
 void launch_ok_level(const Level &L, int32_t *edges, long long ne, int32_t *inv, int32_t *dir, void *sort_scratch,
                      int32_t *row_ptr, int32_t *rest, long long *seg, DevCounters *ctr, cudaStream_t s);
 // a node of the OK recursion on the whole GPU (lists too long for one CTA):

@@ -15,10 +15,69 @@
 // FP64 only, every operation an explicit IEEE one in the oracle's order: a
 // pair's tau from (x_a - x_b, v_a - v_b), a < b; a particle's kick sums its
 // slow partners in ascending index (pairs (j, i), j < i, in the list's
-// order, then (i, j)), then v += h a; drifts x += (h/2) v.
-#include "cc_internal.cuh"
+// order, then (i, j)), then v += h a; drifts x += (h/2) v.  The pivot test
+// tau(a,b) < h is decided as in every split: the certified FP32 decision,
+// the FP64 tau where it stays open (the FP64 predicate's decisions).
+#include "cc_device.cuh"
 
 namespace cc {
+
+// the FP32 decision's constants at the pivot P.h
+__host__ __device__ inline MixedTauParams ok_q(const TauParams &P)
+{
+    MixedTauParams Q;
+    Q.eta = (float)P.eta_in;
+    Q.etah = (float)(P.eta_outside ? P.eta_in * P.eta / P.h : P.eta_in / P.h);
+    Q.eps2 = (float)P.eps2;
+    Q.G = (float)P.G;
+    Q.hq = 0.f;
+    return Q;
+}
+
+// tau(a,b) < P.h from the rounded FP64 differences (a < b): certified FP32,
+// else the FP64 tau (logged when within near_tol of the pivot; ++nfp64)
+__device__ __forceinline__ bool ok_fast(const double *x, const double *y, const double *z, const double *vx,
+                                        const double *vy, const double *vz, const double *m, const int32_t *gid,
+                                        int a, int b, const TauParams &P, const MixedTauParams &Q, DevCounters *ctr,
+                                        int32_t *near_ij, double *near_tau, long long near_cap,
+                                        unsigned long long &nfp64)
+{
+    const double dx0 = __dsub_rn(x[a], x[b]), dx1 = __dsub_rn(y[a], y[b]), dx2 = __dsub_rn(z[a], z[b]);
+    const double dv0 = __dsub_rn(vx[a], vx[b]), dv1 = __dsub_rn(vy[a], vy[b]), dv2 = __dsub_rn(vz[a], vz[b]);
+    const TauPrep32 t = tau_prep_fp32(fl32(dx0), fl32(dx1), fl32(dx2), fl32(dv0), fl32(dv1), fl32(dv2),
+                                      Q.G * (fl32(m[a]) + fl32(m[b])), 0.f, 0.f, Q);
+    const int dec = tau_decide_at(t, Q.etah);
+    if (dec >= 0) return dec > 0;
+    ++nfp64;
+    const double tau = tau_fp64(dx0, dx1, dx2, dv0, dv1, dv2, m[a], m[b], P);
+    if (fabs(tau - P.h) < P.near_tol * P.h) {
+        const unsigned long long z = atomicAdd(&ctr->near_pairs, 1ull);
+        if ((long long)z < near_cap) {
+            const int ga = gid[a], gb = gid[b];
+            near_ij[2 * z] = ga < gb ? ga : gb;
+            near_ij[2 * z + 1] = ga < gb ? gb : ga;
+            near_tau[z] = tau;
+        }
+    }
+    return tau < P.h;
+}
+
+// the certified kernel's edge records (packed indices) -> particle-id pairs
+__global__ void k_ok_rec_pairs(const EdgeRec *rec, long long ne, const int32_t *gid, int32_t *edges)
+{
+    const long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (e >= ne) return;
+    const int ga = gid[rec[e].a], gb = gid[rec[e].b];
+    edges[2 * e] = ga < gb ? ga : gb;
+    edges[2 * e + 1] = ga < gb ? gb : ga;
+}
+
+void launch_ok_rec_pairs(const EdgeRec *rec, long long ne, const int32_t *gid, int32_t *edges, cudaStream_t s)
+{
+    if (ne <= 0) return;
+    k_ok_rec_pairs<<<(unsigned)((ne + 255) / 256), 256, 0, s>>>(rec, ne, gid, edges);
+    CC_COUNT_LAUNCH(1);
+}
 
 // ------------------------------------------------------------ level helpers
 __global__ void k_ok_inv(Level L, int32_t *inv)
@@ -115,28 +174,19 @@ struct OkNodeCounters {
     unsigned long long nf, nS, nsys, nsysf;
 };
 
-__global__ void k_okh_split(Level L, const int32_t *list, long long np, TauParams P, unsigned long long stamp,
-                            int *fast, int32_t *S, unsigned long long *sst, unsigned long long *fst,
-                            unsigned long long *sys_st, unsigned long long *sysf_st, OkNodeCounters *cnt,
-                            DevCounters *ctr, int32_t *near_ij, double *near_tau, long long near_cap)
+__global__ void k_okh_split(Level L, const int32_t *list, long long np, TauParams P, MixedTauParams Q,
+                            unsigned long long stamp, int *fast, int32_t *S, unsigned long long *sst,
+                            unsigned long long *fst, unsigned long long *sys_st, unsigned long long *sysf_st,
+                            OkNodeCounters *cnt, DevCounters *ctr, int32_t *near_ij, double *near_tau,
+                            long long near_cap)
 {
     const long long k = (long long)blockIdx.x * blockDim.x + threadIdx.x;
     bool f = false;
+    unsigned long long nfp64 = 0;
     if (k < np) {
         const int a = list[2 * k], b = list[2 * k + 1];
-        const double tau = tau_fp64(__dsub_rn(L.x[a], L.x[b]), __dsub_rn(L.y[a], L.y[b]), __dsub_rn(L.z[a], L.z[b]),
-                                    __dsub_rn(L.vx[a], L.vx[b]), __dsub_rn(L.vy[a], L.vy[b]),
-                                    __dsub_rn(L.vz[a], L.vz[b]), L.m[a], L.m[b], P);
-        if (fabs(tau - P.h) < P.near_tol * P.h) {
-            const unsigned long long z = atomicAdd(&ctr->near_pairs, 1ull);
-            if ((long long)z < near_cap) {
-                const int ga = L.gid[a], gb = L.gid[b];
-                near_ij[2 * z] = ga < gb ? ga : gb;
-                near_ij[2 * z + 1] = ga < gb ? gb : ga;
-                near_tau[z] = tau;
-            }
-        }
-        f = tau < P.h;
+        f = ok_fast(L.x, L.y, L.z, L.vx, L.vy, L.vz, L.m, L.gid, a, b, P, Q, ctr, near_ij, near_tau, near_cap,
+                    nfp64);
         fast[k] = f ? 1 : 0;
         for (int q = 0; q < 2; ++q) {
             const int e = q == 0 ? a : b;
@@ -149,6 +199,8 @@ __global__ void k_okh_split(Level L, const int32_t *list, long long np, TauParam
     }
     const unsigned fb = __ballot_sync(0xffffffffu, f);
     if ((threadIdx.x & 31) == 0 && fb) atomicAdd(&cnt->nf, (unsigned long long)__popc(fb));
+    const unsigned f64 = __ballot_sync(0xffffffffu, nfp64 != 0);
+    if ((threadIdx.x & 31) == 0 && f64) atomicAdd(&ctr->tau_fp64, (unsigned long long)__popc(f64));
 }
 
 // the fast pairs in list order (pos = exclusive prefix of the flags)
@@ -233,7 +285,7 @@ void launch_okh_split(const Level &L, const int32_t *list, long long np, const T
                       int32_t *near_ij, double *near_tau, long long near_cap, cudaStream_t s)
 {
     if (np <= 0) return;
-    k_okh_split<<<okb(np), 256, 0, s>>>(L, list, np, P, stamp, fast, S, sst, fst, sys_st, sysf_st,
+    k_okh_split<<<okb(np), 256, 0, s>>>(L, list, np, P, ok_q(P), stamp, fast, S, sst, fst, sys_st, sysf_st,
                                         (OkNodeCounters *)counters, ctr, near_ij, near_tau, near_cap);
     CC_COUNT_LAUNCH(1);
 }
@@ -400,22 +452,12 @@ __device__ void ok_split(OkShared &sh, OkNode &N, const OkArgs &A, char *base, u
     if (sh.bad) return;
     const unsigned long long stamp = sh.stamp;
     int nf_local = 0;
+    const MixedTauParams Q = ok_q(P);
+    unsigned long long nfp64 = 0;
     for (int k = tid; k < np; k += KO_T) {
         const int a = N.list[2 * k], b = N.list[2 * k + 1];
-        const double tau =
-            tau_fp64(__dsub_rn(A.x[a], A.x[b]), __dsub_rn(A.y[a], A.y[b]), __dsub_rn(A.z[a], A.z[b]),
-                     __dsub_rn(A.vx[a], A.vx[b]), __dsub_rn(A.vy[a], A.vy[b]), __dsub_rn(A.vz[a], A.vz[b]), A.m[a],
-                     A.m[b], P);
-        if (fabs(tau - P.h) < P.near_tol * P.h) {
-            const unsigned long long z = atomicAdd(&A.ctr->near_pairs, 1ull);
-            if ((long long)z < A.near_cap) {
-                const int ga = A.gid[a], gb = A.gid[b];
-                A.near_ij[2 * z] = ga < gb ? ga : gb;
-                A.near_ij[2 * z + 1] = ga < gb ? gb : ga;
-                A.near_tau[z] = tau;
-            }
-        }
-        const bool f = tau < P.h;
+        const bool f = ok_fast(A.x, A.y, A.z, A.vx, A.vy, A.vz, A.m, A.gid, a, b, P, Q, A.ctr, A.near_ij,
+                               A.near_tau, A.near_cap, nfp64);
         N.fast[k] = f ? 1 : 0;
         nf_local += f ? 1 : 0;
         // the particles of the list: the first claim of this node's stamp
@@ -430,6 +472,7 @@ __device__ void ok_split(OkShared &sh, OkNode &N, const OkArgs &A, char *base, u
         }
     }
     atomicAdd(&sh.nf, nf_local);
+    if (nfp64) atomicAdd(&A.ctr->tau_fp64, nfp64);
     __syncthreads();
     const int nf = sh.nf, nS = sh.nS;
     if (tid == 0) {
@@ -445,7 +488,7 @@ __device__ void ok_split(OkShared &sh, OkNode &N, const OkArgs &A, char *base, u
         cnt[0] += 1;                       // split
         cnt[1] += (unsigned long long)np;  // tau pairs
         cnt[2] += nf > 0 ? 1 : 0;          // components (non-empty fast lists)
-        cnt[3] += (unsigned long long)np;  // tau evaluated, FP64
+        cnt[3] += (unsigned long long)np;  // tau evaluated
     }
     __syncthreads();
     if (sh.bad) return;
@@ -621,7 +664,6 @@ __global__ void __launch_bounds__(KO_T) k_ok_tree(OkArgs A)
         atomicAdd(&A.ctr->small_tau_pairs, cnt[1]);
         atomicAdd(&A.ctr->small_components, cnt[2]);
         atomicAdd(&A.ctr->tau_evals, cnt[3]);
-        atomicAdd(&A.ctr->tau_fp64, cnt[3]);
         atomicAdd(&A.ctr->small_kick_pairs, cnt[4]);
         atomicAdd(&A.ctr->small_drifts, cnt[5]);
         atomicMax(&A.ctr->max_depth_seen, maxd);
