@@ -107,7 +107,7 @@ struct SmallParams {
 struct TauParams {
     double G, eps2, eta_in, eta, h, near_tol;
     int eta_outside;
-    int fault_test;  // failure-path test hooks of the FP64 tau kernel (cc_params.fault_test)
+    int fault_test;  // failure-path test hooks of the tau kernels (cc_params.fault_test)
 };
 
 // --------------------------------------------------------------- helpers

@@ -5,6 +5,7 @@
 //    rigorous per-pair error bound; a pair whose FP32 value is too close to
 //    h for the bound to decide is re-evaluated with the exact FP64
 //    predicate (tau_fp64), so the edge set is identical to the FP64 one.
+//    Every split of both forms (and the OK split's outer level) runs it.
 //  * k_kick_mixed: pair forces in FP32 from float-float position
 //    differences, rsqrt plus one Newton step, Kahan-compensated FP32 sums,
 //    partial sums over j-chunks combined in FP64; v stays FP64.
@@ -248,7 +249,7 @@ __device__ __noinline__ uint2 tau_settle_batch(MixedTauSmem<T, S> &sm, int w, in
                               (jv0.y - b0.y) + (jv1.y - b1.y), (jv0.z - b0.z) + (jv1.z - b1.z), a0.w + jp0.w, cX, cV,
                               Q);
         if (dec < 0) {
-            // undecided: the exact FP64 predicate of the FP64 form
+            // undecided: the exact FP64 predicate
             tau = tau_fp64(__dsub_rn(L.x[gi], L.x[gj]), __dsub_rn(L.y[gi], L.y[gj]), __dsub_rn(L.z[gi], L.z[gj]),
                            __dsub_rn(L.vx[gi], L.vx[gj]), __dsub_rn(L.vy[gi], L.vy[gj]),
                            __dsub_rn(L.vz[gi], L.vz[gj]), L.m[gi], L.m[gj], P);
