@@ -402,7 +402,8 @@ def run_gpu(args, rank, world):
     dm, dx, dv = (torch.tensor(a, device=dev) for a in (m, x, v))
 
     def time_form(form, steps, warmup, clocks_too):
-        ctx = _ctx(cc, dm, dx, dv, sys_off, args.workload, form, args.h_fp64, args.s_small)
+        ctx = _ctx(cc, dm, dx, dv, sys_off, args.workload, form, args.h_fp64, args.s_small,
+                   split={"cc": cc.SPLIT_CC, "hold": cc.SPLIT_HOLD, "ok": cc.SPLIT_OK}[args.split])
         E0, _, _ = ctx.energy()
         t = 0.0
         for _ in range(warmup):
@@ -431,7 +432,8 @@ def run_gpu(args, rank, world):
     head = time_form(args.form, args.steps, args.warmup, True)
     other_form = "fp64" if args.form == "mixed" else "mixed"
     osteps = max(1, min(args.steps, 3))
-    other = None if args.single_form else time_form(other_form, osteps, 1, False)
+    # (the OK split has the FP64 form only)
+    other = None if (args.single_form or args.split == "ok") else time_form(other_form, osteps, 1, False)
     if other:
         other["ctx"].close()
     ctx, t = head["ctx"], head["t"]
@@ -529,8 +531,10 @@ def run_gpu(args, rank, world):
             "autotune": [[e["kernel"], e["bin"],
                           [e["shape"][e["best"]], e["slices"][e["best"]]] if e["best"] >= 0 else None,
                           e["us_per_mpair"]] for e in head["tuning"]],
-            "scaling": "weak", "vs_baseline": None, "dtype": "f32/f64" if fp32 else "f64", "data": "synthetic",
+            "scaling": "weak", "vs_baseline": None, "dtype": "f32/f64" if args.form == "mixed" else "f64",
+            "data": "synthetic",
             "config": {"workload": workload_name(N, args.workload, args.nsys), "form": args.form,
+                       "split": args.split,
                        "h_fp64": f"{args.h_fp64}*dt", "s_small": args.s_small,
                        "l2": "flushed (256 MB write) before each step",
                        "parallelism": "replicas" if world > 1 else "single GPU"},
@@ -728,6 +732,8 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="cc", choices=["cc", "reference"])
     ap.add_argument("--form", default="mixed", choices=["fp64", "mixed"])
+    ap.add_argument("--split", default="cc", choices=["cc", "hold", "ok"],
+                    help="the split of the timed steps (ok: FP64 form only)")
     ap.add_argument("--h-fp64", type=float, default=0.0,
                     help="mixed form: sets split at h < h_fp64*dt take FP64 forces")
     ap.add_argument("--single-form", action="store_true", help="skip timing the other form")
