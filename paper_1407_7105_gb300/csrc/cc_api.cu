@@ -175,6 +175,13 @@ struct cc_ctx {
     int nsm = 152;
     double *d_kpart = nullptr;  // mixed-kick chunk partials
     size_t kpart_sz = 0;
+    // FP64 kick: the precomputed r^-3 matrices of a level's sets and their
+    // offsets (one buffer: the levels' kicks run one after another)
+    double *pf_S = nullptr;
+    size_t pf_bytes = 0;
+    long long *pf_moff = nullptr;
+    int pf_sets = 0;
+    std::vector<long long> h_moff;
     cc_stats_t st{};
     std::string err;
     double eta_run = 0.03;
@@ -893,6 +900,11 @@ static int com_prepare(cc_ctx *c, LevelAlloc &a)
     return CC_OK;
 }
 
+// device memory the FP64 kick's precomputed r^-3 matrices may take (a
+// 16384-body set needs 2.1 GB, a 32768-body one 8.6 GB; larger levels
+// compute r^-3 in the kick)
+constexpr size_t PF_BUDGET = (size_t)12 << 30;
+
 static int ensure_kpart(cc_ctx *c, int chunks, int fcap)
 {
     const size_t need = (size_t)std::max(1, chunks) * 3 * (size_t)fcap * sizeof(double);
@@ -927,11 +939,48 @@ static int level_kick(cc_ctx *c, LevelAlloc &a, const int32_t *lab, const int32_
                           a.Ke > 0 ? &a.cv : nullptr);
         ev_end(c, ev);
     } else {
-        // FP64: one shape (32-body i-tiles; the row order fixes the rounding)
+        // FP64: one shape (32-body i-tiles; the row order fixes the rounding).
+        // Without the centre-of-mass approximation each pair's r^-3 is
+        // computed once for both directions into per-set matrices (while
+        // they fit PF_BUDGET), then read by the kick in its row order.
         L.itile_off = a.k64_off[0];
+        L.tile_off = a.tau_off[TAU_VAR_128];
+        PairFactors pf{nullptr, nullptr, 0};
+        if (a.Ke == 0 && a.tau_blocks[TAU_VAR_128] <= 0x7fffffff) {
+            const int ns = (int)a.h_set_n.size();
+            c->h_moff.resize(ns + 1);
+            long long tot = 0;
+            for (int q = 0; q < ns; ++q) {
+                c->h_moff[q] = tot;
+                tot += (long long)a.h_set_n[q] * a.h_set_n[q];
+            }
+            c->h_moff[ns] = tot;
+            const size_t bytes = (size_t)tot * sizeof(double);
+            if (tot > 0 && bytes <= PF_BUDGET) {
+                if (bytes > c->pf_bytes) {
+                    if (c->pf_S) cudaFree(c->pf_S);
+                    c->pf_S = nullptr;
+                    c->pf_bytes = 0;
+                    if (cudaMalloc(&c->pf_S, bytes) == cudaSuccess) c->pf_bytes = bytes;
+                    else cudaGetLastError();
+                }
+                if (ns + 1 > c->pf_sets) {
+                    if (c->pf_moff) cudaFree(c->pf_moff);
+                    c->pf_moff = nullptr;
+                    c->pf_sets = 0;
+                    if (cudaMalloc(&c->pf_moff, (size_t)(ns + 1) * 8) == cudaSuccess) c->pf_sets = ns + 1;
+                    else cudaGetLastError();
+                }
+                if (c->pf_S && c->pf_moff && bytes <= c->pf_bytes && ns + 1 <= c->pf_sets) {
+                    CC_CUDA(c, cudaMemcpyAsync(c->pf_moff, c->h_moff.data(), (size_t)(ns + 1) * 8,
+                                               cudaMemcpyHostToDevice, s));
+                    pf = PairFactors{c->pf_S, c->pf_moff, (int)a.tau_blocks[TAU_VAR_128]};
+                }
+            }
+        }
         const int ev = ev_begin(c, 1, nullptr, -1, 0, 0, (double)a.pairs);
         launch_kick(L, lab, (int)a.k64_blocks[0], c->p.G, c->p.eps * c->p.eps, h, 0, c->d_ctr, s,
-                    a.Ke > 0 ? &a.cv : nullptr);
+                    a.Ke > 0 ? &a.cv : nullptr, nullptr, pf.S ? &pf : nullptr);
         ev_end(c, ev);
     }
     return CC_OK;
@@ -1960,7 +2009,7 @@ int cc_destroy(cc_ctx *c)
     for (auto &a : c->lv) free_level(a);
     free_level(c->unit);
     void *ptrs[] = {c->d_x3, c->d_v3, c->d_m, c->d_ctr, c->d_near_ij, c->d_near_tau, c->d_partial,
-                    c->tmp, c->seg_scratch, c->d_sys_off, c->d_bad, c->d_kpart, c->d_perm, c->d_box,
+                    c->tmp, c->seg_scratch, c->d_sys_off, c->d_bad, c->d_kpart, c->pf_S, c->pf_moff, c->d_perm, c->d_box,
                     c->batch_scr, c->d_sys_tasks, c->d_iota, c->ok_edges, c->ok_rec, c->ok_reccnt, c->ok_dir, c->ok_sort,
                     c->ok_inv, c->ok_row, c->ok_rest, c->ok_loc, c->ok_stamp, c->ok_seg, c->ok_aoff,
                     c->ok_arena, c->ok_hst, c->ok_cnt, c->ok_scan, c->ok_ndir, c->ok_nsort};

@@ -510,4 +510,19 @@ __device__ __forceinline__ bool kepler_pair(double ma, double mb, double xa[3], 
     return true;
 }
 
+// Row ti and column offset of triangular tile t (tiles (ti, tj), tj >= ti,
+// numbered row by row; row ti starts at ti nt - ti (ti - 1) / 2): the root of
+// the quadratic in single precision, then exact integer corrections.
+__device__ __forceinline__ int tri_tile_row(int &t, int nt)
+{
+    auto off = [nt](int x) { return x * nt - (x * (x - 1)) / 2; };
+    const float b = 2.f * (float)nt + 1.f;
+    int ti = (int)(0.5f * (b - sqrtf(fmaxf(b * b - 8.f * (float)t, 0.f))));
+    ti = max(0, min(ti, nt - 1));
+    while (ti > 0 && off(ti) > t) --ti;
+    while (ti + 1 < nt && off(ti + 1) <= t) ++ti;
+    t -= off(ti);
+    return ti;
+}
+
 }  // namespace cc

@@ -332,9 +332,16 @@ struct OkView {
     const int32_t *row_ptr;  // [total + 1]
     const int32_t *col;      // (row, partner) pairs
 };
+// FP64 kick: r^-3 of every ordered pair of each set, precomputed (k_rinv3)
+struct PairFactors {
+    double *S;               // n x n per set, row-major
+    const long long *moff;   // per set: offset of its matrix in S
+    int nblocks;             // k_rinv3's grid: the level's 128-wide triangular tiles
+};
 void launch_kick(const Level &L, const int32_t *label, int nitiles, double G, double eps2, double h,
                  int variant, DevCounters *ctr, cudaStream_t s, const ComView *com = nullptr,
-                 const OkView *okv = nullptr);
+                 const OkView *okv = nullptr,
+                 const PairFactors *pf = nullptr);
 // the OK split's outer level after its tau kernel wrote the fast pairs
 // (particle ids, count ne): pairs to packed indices and sorted, both
 // directions sorted (dir, 2 ne pairs), row pointers, the drift flags of the

@@ -177,21 +177,6 @@ __device__ __forceinline__ bool warp_group_box(bool on, float4 p, float4 v, Grou
     return (__ballot_sync(0xffffffffu, on) & seg) != 0u;
 }
 
-// Row ti and column offset of triangular tile t (tiles (ti, tj), tj >= ti,
-// numbered row by row; row ti starts at ti nt - ti (ti - 1) / 2): the root of
-// the quadratic in single precision, then exact integer corrections.
-__device__ __forceinline__ int tri_tile_row(int &t, int nt)
-{
-    auto off = [nt](int x) { return x * nt - (x * (x - 1)) / 2; };
-    const float b = 2.f * (float)nt + 1.f;
-    int ti = (int)(0.5f * (b - sqrtf(fmaxf(b * b - 8.f * (float)t, 0.f))));
-    ti = max(0, min(ti, nt - 1));
-    while (ti > 0 && off(ti) > t) --ti;
-    while (ti + 1 < nt && off(ti + 1) <= t) ++ti;
-    t -= off(ti);
-    return ti;
-}
-
 // local union-find in shared memory (indices 0..2T-1, links to the smaller)
 __device__ __forceinline__ int luf_find(volatile int32_t *p, int x)
 {

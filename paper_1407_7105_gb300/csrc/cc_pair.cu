@@ -434,11 +434,13 @@ struct __align__(16) KickBSmem {
 // are left out; their kick is the centre-of-mass one that launch_com_apply
 // adds afterwards.  MODE 2 (OK split): the fast pairs (OkView: each row's
 // partners, sorted) are left out, every other pair of the set kicks.
+// MODE 3: as MODE 0 with each pair's r^-3 read from the matrix k_rinv3
+// filled (PairFactors) instead of computed.
 template <int MODE>
 __global__ void __launch_bounds__(KB_THREADS) k_kick64(Level L, const int32_t *label, double G, double eps2, double h,
-                                                       DevCounters *ctr, ComView cv, OkView okv)
+                                                       DevCounters *ctr, ComView cv, OkView okv, PairFactors pf)
 {
-    constexpr bool COM = MODE == 1, OKM = MODE == 2;
+    constexpr bool COM = MODE == 1, OKM = MODE == 2, PRE = MODE == 3;
     __shared__ KickBSmem sm;
     const int tid = threadIdx.x;
     const int s = find_set(L.itile_off, L.nsets, blockIdx.x);
@@ -517,9 +519,15 @@ __global__ void __launch_bounds__(KB_THREADS) k_kick64(Level L, const int32_t *l
             const double dx0 = __dsub_rn(sm.j.col[st][0][jj], sm.xi[0][ii]);
             const double dx1 = __dsub_rn(sm.j.col[st][1][jj], sm.xi[1][ii]);
             const double dx2 = __dsub_rn(sm.j.col[st][2][jj], sm.xi[2][ii]);
-            const double r2 = __dadd_rn(
-                __dadd_rn(__dadd_rn(__dmul_rn(dx0, dx0), __dmul_rn(dx1, dx1)), __dmul_rn(dx2, dx2)), eps2);
-            const double rinv3 = __ddiv_rn(1.0, __dmul_rn(r2, __dsqrt_rn(r2)));
+            double rinv3;
+            if (PRE) {
+                // (row i of the set's matrix, column j: consecutive threads, consecutive j)
+                rinv3 = (ii < ni && jj < jn) ? pf.S[pf.moff[s] + (long long)(il0 + ii) * n + (jl0 + jj)] : 0.0;
+            } else {
+                const double r2 = __dadd_rn(
+                    __dadd_rn(__dadd_rn(__dmul_rn(dx0, dx0), __dmul_rn(dx1, dx1)), __dmul_rn(dx2, dx2)), eps2);
+                rinv3 = __ddiv_rn(1.0, __dmul_rn(r2, __dsqrt_rn(r2)));
+            }
             const double w = __dmul_rn(__dmul_rn(G, sm.j.col[st][3][jj]), rinv3);
             sm.f[0][ii][jj] = use ? __dmul_rn(w, dx0) : 0.0;
             sm.f[1][ii][jj] = use ? __dmul_rn(w, dx1) : 0.0;
@@ -544,19 +552,90 @@ __global__ void __launch_bounds__(KB_THREADS) k_kick64(Level L, const int32_t *l
     }
 }
 
+// r^-3 of every ordered pair (i, j) of each set into its n x n matrix at
+// pf.moff[s] (row i, column j; the diagonal unused).  One block per 128-wide
+// triangular tile (TI <= TJ; the grid and prefix L.tile_off of the 128-wide
+// tau tiles), in 32 x 32 sub-tiles: every unordered pair is evaluated once
+// with the kick's own operations (dx = x_j - x_i; the squares make r^2, and
+// so r^-3, the same bits for (j, i)), then written to both halves, the
+// transposed half through shared memory.
+constexpr int KR_T = 32, KR_W = 128;
+static_assert(KR_T == KB_T, "the factor sub-tiles are the kick's i-tiles");
+static_assert(KR_W == TAU_VAR_T[TAU_VAR_128], "the factor tiles are the 128-wide tau tiles");
+__global__ void __launch_bounds__(KB_THREADS) k_rinv3(Level L, double eps2, PairFactors pf)
+{
+    __shared__ double xi[3][KR_W];
+    __shared__ double xj[3][KR_W];
+    __shared__ double t[KR_T][KR_T + 1];
+    const int tid = threadIdx.x;
+    const int s = find_set(L.tile_off, L.nsets, blockIdx.x);
+    int tt = blockIdx.x - L.tile_off[s];
+    const int n = L.set_n[s], start = L.set_start[s];
+    const int nT = (n + KR_W - 1) / KR_W;
+    const int TI = tri_tile_row(tt, nT), TJ = TI + tt;
+    const int i0 = TI * KR_W, j0 = TJ * KR_W;
+    const int ni = min(KR_W, n - i0), nj = min(KR_W, n - j0);
+    double *S = pf.S + pf.moff[s];
+    for (int e = tid; e < KR_W; e += KB_THREADS) {
+        const bool vi = e < ni, vj = e < nj;
+        xi[0][e] = vi ? L.x[start + i0 + e] : 0.0;
+        xi[1][e] = vi ? L.y[start + i0 + e] : 0.0;
+        xi[2][e] = vi ? L.z[start + i0 + e] : 0.0;
+        xj[0][e] = vj ? L.x[start + j0 + e] : 0.0;
+        xj[1][e] = vj ? L.y[start + j0 + e] : 0.0;
+        xj[2][e] = vj ? L.z[start + j0 + e] : 0.0;
+    }
+    for (int a = 0; a < KR_W / KR_T; ++a) {
+        for (int b = TI == TJ ? a : 0; b < KR_W / KR_T; ++b) {
+            const int il = a * KR_T, jl = b * KR_T;
+            if (il >= ni || jl >= nj) continue;  // (uniform over the block)
+            __syncthreads();  // (the staged rows, or the previous sub-tile's transposed write)
+#pragma unroll
+            for (int q = 0; q < KR_T * KR_T / KB_THREADS; ++q) {
+                const int pidx = tid + q * KB_THREADS, ii = pidx >> 5, jj = pidx & 31;
+                const int gi = il + ii, gj = jl + jj;
+                if (gi < ni && gj < nj && j0 + gj > i0 + gi) {
+                    const double dx0 = __dsub_rn(xj[0][gj], xi[0][gi]);
+                    const double dx1 = __dsub_rn(xj[1][gj], xi[1][gi]);
+                    const double dx2 = __dsub_rn(xj[2][gj], xi[2][gi]);
+                    const double r2 = __dadd_rn(
+                        __dadd_rn(__dadd_rn(__dmul_rn(dx0, dx0), __dmul_rn(dx1, dx1)), __dmul_rn(dx2, dx2)), eps2);
+                    const double v = __ddiv_rn(1.0, __dmul_rn(r2, __dsqrt_rn(r2)));
+                    S[(long long)(i0 + gi) * n + (j0 + gj)] = v;
+                    t[ii][jj] = v;
+                }
+            }
+            __syncthreads();
+#pragma unroll
+            for (int q = 0; q < KR_T * KR_T / KB_THREADS; ++q) {
+                const int pidx = tid + q * KB_THREADS, jj = pidx >> 5, ii = pidx & 31;
+                const int gi = il + ii, gj = jl + jj;
+                if (gi < ni && gj < nj && j0 + gj > i0 + gi) S[(long long)(j0 + gj) * n + (i0 + gi)] = t[ii][jj];
+            }
+        }
+    }
+}
+
 void launch_kick(const Level &L, const int32_t *label, int nitiles, double G, double eps2, double h,
-                 int variant, DevCounters *ctr, cudaStream_t s, const ComView *com, const OkView *okv)
+                 int variant, DevCounters *ctr, cudaStream_t s, const ComView *com, const OkView *okv,
+                 const PairFactors *pf)
 {
     (void)variant;  // one shape: 32-body tiles (the prefix of variant 0)
     if (nitiles <= 0) return;
     const ComView nc{nullptr, nullptr, nullptr, nullptr};
     const OkView no{nullptr, nullptr};
-    if (okv && okv->row_ptr)
-        k_kick64<2><<<nitiles, KB_THREADS, 0, s>>>(L, label, G, eps2, h, ctr, nc, *okv);
-    else if (com && com->cl)
-        k_kick64<1><<<nitiles, KB_THREADS, 0, s>>>(L, label, G, eps2, h, ctr, *com, no);
-    else
-        k_kick64<0><<<nitiles, KB_THREADS, 0, s>>>(L, label, G, eps2, h, ctr, nc, no);
+    const PairFactors np{nullptr, nullptr, 0};
+    if (okv && okv->row_ptr) {
+        k_kick64<2><<<nitiles, KB_THREADS, 0, s>>>(L, label, G, eps2, h, ctr, nc, *okv, np);
+    } else if (com && com->cl) {
+        k_kick64<1><<<nitiles, KB_THREADS, 0, s>>>(L, label, G, eps2, h, ctr, *com, no, np);
+    } else if (pf && pf->S) {
+        k_rinv3<<<pf->nblocks, KB_THREADS, 0, s>>>(L, eps2, *pf);
+        k_kick64<3><<<nitiles, KB_THREADS, 0, s>>>(L, label, G, eps2, h, ctr, nc, no, *pf);
+        CC_COUNT_LAUNCH(1);
+    } else {
+        k_kick64<0><<<nitiles, KB_THREADS, 0, s>>>(L, label, G, eps2, h, ctr, nc, no, np);
+    }
     CC_COUNT_LAUNCH(1);
 }
 
