@@ -921,6 +921,44 @@ static int ensure_kpart(cc_ctx *c, int chunks, int fcap)
     return CC_OK;
 }
 
+// Device matrices of the FP64 kick's pair weights G m_j r_ij^-3 for the
+// sets of level a (n x n per set, row-major), when they fit PF_BUDGET; pf
+// stays empty otherwise (the kick then computes r^-3 itself).
+static int pair_factors(cc_ctx *c, LevelAlloc &a, PairFactors &pf)
+{
+    pf = PairFactors{nullptr, nullptr, 0};
+    if (a.tau_blocks[TAU_VAR_128] > 0x7fffffff) return CC_OK;
+    const int ns = (int)a.h_set_n.size();
+    c->h_moff.resize(ns + 1);
+    long long tot = 0;
+    for (int q = 0; q < ns; ++q) {
+        c->h_moff[q] = tot;
+        tot += (long long)a.h_set_n[q] * a.h_set_n[q];
+    }
+    c->h_moff[ns] = tot;
+    const size_t bytes = (size_t)tot * sizeof(double);
+    if (tot <= 0 || bytes > PF_BUDGET) return CC_OK;
+    if (bytes > c->pf_bytes) {
+        if (c->pf_S) cudaFree(c->pf_S);
+        c->pf_S = nullptr;
+        c->pf_bytes = 0;
+        if (cudaMalloc(&c->pf_S, bytes) == cudaSuccess) c->pf_bytes = bytes;
+        else cudaGetLastError();
+    }
+    if (ns + 1 > c->pf_sets) {
+        if (c->pf_moff) cudaFree(c->pf_moff);
+        c->pf_moff = nullptr;
+        c->pf_sets = 0;
+        if (cudaMalloc(&c->pf_moff, (size_t)(ns + 1) * 8) == cudaSuccess) c->pf_sets = ns + 1;
+        else cudaGetLastError();
+    }
+    if (!c->pf_S || !c->pf_moff || bytes > c->pf_bytes || ns + 1 > c->pf_sets) return CC_OK;
+    CC_CUDA(c, cudaMemcpyAsync(c->pf_moff, c->h_moff.data(), (size_t)(ns + 1) * 8, cudaMemcpyHostToDevice,
+                               c->stream));
+    pf = PairFactors{c->pf_S, c->pf_moff, (int)a.tau_blocks[TAU_VAR_128]};
+    return CC_OK;
+}
+
 // K_{h,V} on a level: labels lab (packed order); order = the root-sorted
 // order of the mixed kick (its labels at L.klab, prepared by the caller)
 static int level_kick(cc_ctx *c, LevelAlloc &a, const int32_t *lab, const int32_t *order, double h,
@@ -946,38 +984,7 @@ static int level_kick(cc_ctx *c, LevelAlloc &a, const int32_t *lab, const int32_
         L.itile_off = a.k64_off[0];
         L.tile_off = a.tau_off[TAU_VAR_128];
         PairFactors pf{nullptr, nullptr, 0};
-        if (a.Ke == 0 && a.tau_blocks[TAU_VAR_128] <= 0x7fffffff) {
-            const int ns = (int)a.h_set_n.size();
-            c->h_moff.resize(ns + 1);
-            long long tot = 0;
-            for (int q = 0; q < ns; ++q) {
-                c->h_moff[q] = tot;
-                tot += (long long)a.h_set_n[q] * a.h_set_n[q];
-            }
-            c->h_moff[ns] = tot;
-            const size_t bytes = (size_t)tot * sizeof(double);
-            if (tot > 0 && bytes <= PF_BUDGET) {
-                if (bytes > c->pf_bytes) {
-                    if (c->pf_S) cudaFree(c->pf_S);
-                    c->pf_S = nullptr;
-                    c->pf_bytes = 0;
-                    if (cudaMalloc(&c->pf_S, bytes) == cudaSuccess) c->pf_bytes = bytes;
-                    else cudaGetLastError();
-                }
-                if (ns + 1 > c->pf_sets) {
-                    if (c->pf_moff) cudaFree(c->pf_moff);
-                    c->pf_moff = nullptr;
-                    c->pf_sets = 0;
-                    if (cudaMalloc(&c->pf_moff, (size_t)(ns + 1) * 8) == cudaSuccess) c->pf_sets = ns + 1;
-                    else cudaGetLastError();
-                }
-                if (c->pf_S && c->pf_moff && bytes <= c->pf_bytes && ns + 1 <= c->pf_sets) {
-                    CC_CUDA(c, cudaMemcpyAsync(c->pf_moff, c->h_moff.data(), (size_t)(ns + 1) * 8,
-                                               cudaMemcpyHostToDevice, s));
-                    pf = PairFactors{c->pf_S, c->pf_moff, (int)a.tau_blocks[TAU_VAR_128]};
-                }
-            }
-        }
+        if (a.Ke == 0) CC_TRY(pair_factors(c, a, pf));
         const int ev = ev_begin(c, 1, nullptr, -1, 0, 0, (double)a.pairs);
         launch_kick(L, lab, (int)a.k64_blocks[0], c->p.G, c->p.eps * c->p.eps, h, 0, c->d_ctr, s,
                     a.Ke > 0 ? &a.cv : nullptr, nullptr, pf.S ? &pf : nullptr);
@@ -1370,13 +1377,17 @@ static int ok_step(cc_ctx *c)
     const OkView okv{c->ok_row, c->ok_dir};
     Level KL = a.L;
     KL.itile_off = a.k64_off[0];
+    KL.tile_off = a.tau_off[TAU_VAR_128];
+    PairFactors pf;
+    CC_TRY(pair_factors(c, a, pf));
     const double G = c->p.G, eps2 = c->p.eps * c->p.eps;
     for (int half = 0; half < 2; ++half) {
         if (half == 1) {
             // D_{h/2} of the particles without a fast pair, K_h of every
             // slow pair of each set (the fast ones masked), D_{h/2}
             launch_drift_labels(a.L, c->ok_rest, 0.5 * dt, s);
-            launch_kick(KL, a.L.gid, (int)a.k64_blocks[0], G, eps2, dt, 0, c->d_ctr, s, nullptr, &okv);
+            launch_kick(KL, a.L.gid, (int)a.k64_blocks[0], G, eps2, dt, 0, c->d_ctr, s, nullptr, &okv,
+                        pf.S ? &pf : nullptr);
             launch_drift_labels(a.L, c->ok_rest, 0.5 * dt, s);
         }
         CC_TRY(ok_node(c, c->ok_edges, ne, 0.5 * dt, 1));

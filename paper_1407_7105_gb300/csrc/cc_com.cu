@@ -73,7 +73,7 @@ __global__ void k_com_far(double *cm, const int32_t *eq, const int32_t *comp_siz
             f = __dadd_rn(ca[4], cb[4]) < __dmul_rn(theta, d) ? 1 : 0;
             if (f) {
                 const double d2 = __dadd_rn(dd, eps2);
-                const double w = __dmul_rn(__dmul_rn(G, cb[0]), __ddiv_rn(1.0, __dmul_rn(d2, __dsqrt_rn(d2))));
+                const double w = __dmul_rn(__dmul_rn(G, cb[0]), __drcp_rn(__dmul_rn(d2, __dsqrt_rn(d2))));
                 Ax = __dadd_rn(Ax, __dmul_rn(w, dx));
                 Ay = __dadd_rn(Ay, __dmul_rn(w, dy));
                 Az = __dadd_rn(Az, __dmul_rn(w, dz));
@@ -118,7 +118,7 @@ __global__ void k_com_far_warp(double *cm, const int32_t *eq, const int32_t *com
             f = __dadd_rn(ca[4], cb[4]) < __dmul_rn(theta, d) ? 1 : 0;
             if (f) {
                 const double d2 = __dadd_rn(dd, eps2);
-                const double w = __dmul_rn(__dmul_rn(G, cb[0]), __ddiv_rn(1.0, __dmul_rn(d2, __dsqrt_rn(d2))));
+                const double w = __dmul_rn(__dmul_rn(G, cb[0]), __drcp_rn(__dmul_rn(d2, __dsqrt_rn(d2))));
                 Ax = __dadd_rn(Ax, __dmul_rn(w, dx));
                 Ay = __dadd_rn(Ay, __dmul_rn(w, dy));
                 Az = __dadd_rn(Az, __dmul_rn(w, dz));

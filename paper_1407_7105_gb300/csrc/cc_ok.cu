@@ -266,7 +266,7 @@ __global__ void k_okh_kick(Level L, const int32_t *dir, long long nd, double G, 
         const double dx0 = __dsub_rn(L.x[j], xi), dx1 = __dsub_rn(L.y[j], yi), dx2 = __dsub_rn(L.z[j], zi);
         const double r2 = __dadd_rn(__dadd_rn(__dadd_rn(__dmul_rn(dx0, dx0), __dmul_rn(dx1, dx1)),
                                               __dmul_rn(dx2, dx2)), eps2);
-        const double rinv3 = __ddiv_rn(1.0, __dmul_rn(r2, __dsqrt_rn(r2)));
+        const double rinv3 = __drcp_rn(__dmul_rn(r2, __dsqrt_rn(r2)));
         const double w = __dmul_rn(__dmul_rn(G, L.m[j]), rinv3);
         ax = __dadd_rn(ax, __dmul_rn(w, dx0));
         ay = __dadd_rn(ay, __dmul_rn(w, dx1));
@@ -418,7 +418,7 @@ __device__ __forceinline__ void ok_term(const OkArgs &A, int i, int j, double &a
     const double dx2 = __dsub_rn(A.z[j], A.z[i]);
     const double r2 = __dadd_rn(__dadd_rn(__dadd_rn(__dmul_rn(dx0, dx0), __dmul_rn(dx1, dx1)), __dmul_rn(dx2, dx2)),
                                 A.eps2);
-    const double rinv3 = __ddiv_rn(1.0, __dmul_rn(r2, __dsqrt_rn(r2)));
+    const double rinv3 = __drcp_rn(__dmul_rn(r2, __dsqrt_rn(r2)));
     const double w = __dmul_rn(__dmul_rn(A.G, A.m[j]), rinv3);
     ax = __dadd_rn(ax, __dmul_rn(w, dx0));
     ay = __dadd_rn(ay, __dmul_rn(w, dx1));

@@ -434,13 +434,14 @@ struct __align__(16) KickBSmem {
 // are left out; their kick is the centre-of-mass one that launch_com_apply
 // adds afterwards.  MODE 2 (OK split): the fast pairs (OkView: each row's
 // partners, sorted) are left out, every other pair of the set kicks.
-// MODE 3: as MODE 0 with each pair's r^-3 read from the matrix k_rinv3
-// filled (PairFactors) instead of computed.
+// MODE 3: as MODE 0 with each pair's weight G m_j r_ij^-3 read from the
+// matrix k_pair_weights filled (PairFactors) instead of computed; MODE 4: as
+// MODE 2 with the weights read.
 template <int MODE>
 __global__ void __launch_bounds__(KB_THREADS) k_kick64(Level L, const int32_t *label, double G, double eps2, double h,
                                                        DevCounters *ctr, ComView cv, OkView okv, PairFactors pf)
 {
-    constexpr bool COM = MODE == 1, OKM = MODE == 2, PRE = MODE == 3;
+    constexpr bool COM = MODE == 1, OKM = MODE == 2 || MODE == 4, PRE = MODE >= 3;
     __shared__ KickBSmem sm;
     const int tid = threadIdx.x;
     const int s = find_set(L.itile_off, L.nsets, blockIdx.x);
@@ -519,16 +520,16 @@ __global__ void __launch_bounds__(KB_THREADS) k_kick64(Level L, const int32_t *l
             const double dx0 = __dsub_rn(sm.j.col[st][0][jj], sm.xi[0][ii]);
             const double dx1 = __dsub_rn(sm.j.col[st][1][jj], sm.xi[1][ii]);
             const double dx2 = __dsub_rn(sm.j.col[st][2][jj], sm.xi[2][ii]);
-            double rinv3;
+            double w;
             if (PRE) {
                 // (row i of the set's matrix, column j: consecutive threads, consecutive j)
-                rinv3 = (ii < ni && jj < jn) ? pf.S[pf.moff[s] + (long long)(il0 + ii) * n + (jl0 + jj)] : 0.0;
+                w = (ii < ni && jj < jn) ? pf.S[pf.moff[s] + (long long)(il0 + ii) * n + (jl0 + jj)] : 0.0;
             } else {
                 const double r2 = __dadd_rn(
                     __dadd_rn(__dadd_rn(__dmul_rn(dx0, dx0), __dmul_rn(dx1, dx1)), __dmul_rn(dx2, dx2)), eps2);
-                rinv3 = __ddiv_rn(1.0, __dmul_rn(r2, __dsqrt_rn(r2)));
+                const double rinv3 = __drcp_rn(__dmul_rn(r2, __dsqrt_rn(r2)));
+                w = __dmul_rn(__dmul_rn(G, sm.j.col[st][3][jj]), rinv3);
             }
-            const double w = __dmul_rn(__dmul_rn(G, sm.j.col[st][3][jj]), rinv3);
             sm.f[0][ii][jj] = use ? __dmul_rn(w, dx0) : 0.0;
             sm.f[1][ii][jj] = use ? __dmul_rn(w, dx1) : 0.0;
             sm.f[2][ii][jj] = use ? __dmul_rn(w, dx2) : 0.0;
@@ -552,20 +553,20 @@ __global__ void __launch_bounds__(KB_THREADS) k_kick64(Level L, const int32_t *l
     }
 }
 
-// r^-3 of every ordered pair (i, j) of each set into its n x n matrix at
-// pf.moff[s] (row i, column j; the diagonal unused).  One block per 128-wide
+// The weight G m_j r_ij^-3 of every ordered pair (i, j) of each set into its
+// n x n matrix at pf.moff[s] (row i, column j; the diagonal unused).  One block per 128-wide
 // triangular tile (TI <= TJ; the grid and prefix L.tile_off of the 128-wide
 // tau tiles), in 32 x 32 sub-tiles: every unordered pair is evaluated once
 // with the kick's own operations (dx = x_j - x_i; the squares make r^2, and
-// so r^-3, the same bits for (j, i)), then written to both halves, the
-// transposed half through shared memory.
+// so r^-3, the same bits for (j, i)); (G m_j) r^-3 goes to row i directly,
+// (G m_i) r^-3 to row j through shared memory.
 constexpr int KR_T = 32, KR_W = 128;
 static_assert(KR_T == KB_T, "the factor sub-tiles are the kick's i-tiles");
 static_assert(KR_W == TAU_VAR_T[TAU_VAR_128], "the factor tiles are the 128-wide tau tiles");
-__global__ void __launch_bounds__(KB_THREADS) k_rinv3(Level L, double eps2, PairFactors pf)
+__global__ void __launch_bounds__(KB_THREADS) k_pair_weights(Level L, double G, double eps2, PairFactors pf)
 {
-    __shared__ double xi[3][KR_W];
-    __shared__ double xj[3][KR_W];
+    __shared__ double xi[4][KR_W];  // x, y, z, G m
+    __shared__ double xj[4][KR_W];
     __shared__ double t[KR_T][KR_T + 1];
     const int tid = threadIdx.x;
     const int s = find_set(L.tile_off, L.nsets, blockIdx.x);
@@ -581,9 +582,11 @@ __global__ void __launch_bounds__(KB_THREADS) k_rinv3(Level L, double eps2, Pair
         xi[0][e] = vi ? L.x[start + i0 + e] : 0.0;
         xi[1][e] = vi ? L.y[start + i0 + e] : 0.0;
         xi[2][e] = vi ? L.z[start + i0 + e] : 0.0;
+        xi[3][e] = vi ? __dmul_rn(G, L.m[start + i0 + e]) : 0.0;
         xj[0][e] = vj ? L.x[start + j0 + e] : 0.0;
         xj[1][e] = vj ? L.y[start + j0 + e] : 0.0;
         xj[2][e] = vj ? L.z[start + j0 + e] : 0.0;
+        xj[3][e] = vj ? __dmul_rn(G, L.m[start + j0 + e]) : 0.0;
     }
     for (int a = 0; a < KR_W / KR_T; ++a) {
         for (int b = TI == TJ ? a : 0; b < KR_W / KR_T; ++b) {
@@ -600,9 +603,9 @@ __global__ void __launch_bounds__(KB_THREADS) k_rinv3(Level L, double eps2, Pair
                     const double dx2 = __dsub_rn(xj[2][gj], xi[2][gi]);
                     const double r2 = __dadd_rn(
                         __dadd_rn(__dadd_rn(__dmul_rn(dx0, dx0), __dmul_rn(dx1, dx1)), __dmul_rn(dx2, dx2)), eps2);
-                    const double v = __ddiv_rn(1.0, __dmul_rn(r2, __dsqrt_rn(r2)));
-                    S[(long long)(i0 + gi) * n + (j0 + gj)] = v;
-                    t[ii][jj] = v;
+                    const double v = __drcp_rn(__dmul_rn(r2, __dsqrt_rn(r2)));
+                    S[(long long)(i0 + gi) * n + (j0 + gj)] = __dmul_rn(xj[3][gj], v);
+                    t[ii][jj] = __dmul_rn(xi[3][gi], v);
                 }
             }
             __syncthreads();
@@ -625,12 +628,16 @@ void launch_kick(const Level &L, const int32_t *label, int nitiles, double G, do
     const ComView nc{nullptr, nullptr, nullptr, nullptr};
     const OkView no{nullptr, nullptr};
     const PairFactors np{nullptr, nullptr, 0};
-    if (okv && okv->row_ptr) {
+    if (okv && okv->row_ptr && pf && pf->S) {
+        k_pair_weights<<<pf->nblocks, KB_THREADS, 0, s>>>(L, G, eps2, *pf);
+        k_kick64<4><<<nitiles, KB_THREADS, 0, s>>>(L, label, G, eps2, h, ctr, nc, *okv, *pf);
+        CC_COUNT_LAUNCH(1);
+    } else if (okv && okv->row_ptr) {
         k_kick64<2><<<nitiles, KB_THREADS, 0, s>>>(L, label, G, eps2, h, ctr, nc, *okv, np);
     } else if (com && com->cl) {
         k_kick64<1><<<nitiles, KB_THREADS, 0, s>>>(L, label, G, eps2, h, ctr, *com, no, np);
     } else if (pf && pf->S) {
-        k_rinv3<<<pf->nblocks, KB_THREADS, 0, s>>>(L, eps2, *pf);
+        k_pair_weights<<<pf->nblocks, KB_THREADS, 0, s>>>(L, G, eps2, *pf);
         k_kick64<3><<<nitiles, KB_THREADS, 0, s>>>(L, label, G, eps2, h, ctr, nc, no, *pf);
         CC_COUNT_LAUNCH(1);
     } else {

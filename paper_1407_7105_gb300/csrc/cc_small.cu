@@ -105,7 +105,7 @@ __device__ __noinline__ K8Acc k8_kick64(const K8Warp &S, int n, uint32_t others,
         const double dx2 = __dsub_rn(S.d[2][j], zi);
         const double r2 = __dadd_rn(__dadd_rn(__dadd_rn(__dmul_rn(dx0, dx0), __dmul_rn(dx1, dx1)),
                                               __dmul_rn(dx2, dx2)), eps2);
-        const double rinv3 = __ddiv_rn(1.0, __dmul_rn(r2, __dsqrt_rn(r2)));
+        const double rinv3 = __drcp_rn(__dmul_rn(r2, __dsqrt_rn(r2)));
         const double ww = __dmul_rn(__dmul_rn(G, S.d[6][j]), rinv3);
         ax = __dadd_rn(ax, __dmul_rn(ww, dx0));
         ay = __dadd_rn(ay, __dmul_rn(ww, dx1));
@@ -255,7 +255,7 @@ __device__ unsigned pair_path(double A[7], double B[7], double h0, int depth0, i
         const double dx0 = __dsub_rn(B[0], A[0]), dx1 = __dsub_rn(B[1], A[1]), dx2 = __dsub_rn(B[2], A[2]);
         const double r2 = __dadd_rn(__dadd_rn(__dadd_rn(__dmul_rn(dx0, dx0), __dmul_rn(dx1, dx1)),
                                               __dmul_rn(dx2, dx2)), SP.eps2);
-        const double rinv3 = __ddiv_rn(1.0, __dmul_rn(r2, __dsqrt_rn(r2)));
+        const double rinv3 = __drcp_rn(__dmul_rn(r2, __dsqrt_rn(r2)));
         const double wa = __dmul_rn(__dmul_rn(SP.G, B[6]), rinv3), wb = __dmul_rn(__dmul_rn(SP.G, A[6]), rinv3);
         A[3] = __dadd_rn(A[3], __dmul_rn(h, __dmul_rn(wa, dx0)));
         A[4] = __dadd_rn(A[4], __dmul_rn(h, __dmul_rn(wa, dx1)));
@@ -1173,7 +1173,7 @@ __device__ void km_dkd(KMShared<W> &sh, const KMFrame &F, const SView V, const S
                 const double dx2 = __dsub_rn(b1.x, i1.x);
                 const double r2 = __dadd_rn(__dadd_rn(__dadd_rn(__dmul_rn(dx0, dx0), __dmul_rn(dx1, dx1)),
                                                       __dmul_rn(dx2, dx2)), SP.eps2);
-                const double rinv3 = __ddiv_rn(1.0, __dmul_rn(r2, __dsqrt_rn(r2)));
+                const double rinv3 = __drcp_rn(__dmul_rn(r2, __dsqrt_rn(r2)));
                 const double ww = __dmul_rn(__dmul_rn(SP.G, b1.y), rinv3);
                 fx = __dmul_rn(ww, dx0);
                 fy = __dmul_rn(ww, dx1);
