@@ -900,10 +900,10 @@ static int com_prepare(cc_ctx *c, LevelAlloc &a)
     return CC_OK;
 }
 
-// device memory the FP64 kick's precomputed r^-3 matrices may take (a
-// 16384-body set needs 2.1 GB, a 32768-body one 8.6 GB; larger levels
-// compute r^-3 in the kick)
-constexpr size_t PF_BUDGET = (size_t)12 << 30;
+// device memory the FP64 kick's precomputed pair-force matrices may take (a
+// 16384-body set needs 6.4 GB, a 28000-body one 18.8 GB; larger levels
+// compute the forces in the kick)
+constexpr size_t PF_BUDGET = (size_t)24 << 30;
 
 static int ensure_kpart(cc_ctx *c, int chunks, int fcap)
 {
@@ -921,9 +921,9 @@ static int ensure_kpart(cc_ctx *c, int chunks, int fcap)
     return CC_OK;
 }
 
-// Device matrices of the FP64 kick's pair weights G m_j r_ij^-3 for the
-// sets of level a (n x n per set, row-major), when they fit PF_BUDGET; pf
-// stays empty otherwise (the kick then computes r^-3 itself).
+// Device matrices of the FP64 kick's pair forces G m_j r_ij^-3 (x_j - x_i)
+// for the sets of level a (three n x n per set, row-major), when they fit
+// PF_BUDGET; pf stays empty otherwise (the kick then computes the forces).
 static int pair_factors(cc_ctx *c, LevelAlloc &a, PairFactors &pf)
 {
     pf = PairFactors{nullptr, nullptr, 0};
@@ -933,7 +933,7 @@ static int pair_factors(cc_ctx *c, LevelAlloc &a, PairFactors &pf)
     long long tot = 0;
     for (int q = 0; q < ns; ++q) {
         c->h_moff[q] = tot;
-        tot += (long long)a.h_set_n[q] * a.h_set_n[q];
+        tot += 3LL * a.h_set_n[q] * a.h_set_n[q];
     }
     c->h_moff[ns] = tot;
     const size_t bytes = (size_t)tot * sizeof(double);
@@ -978,9 +978,9 @@ static int level_kick(cc_ctx *c, LevelAlloc &a, const int32_t *lab, const int32_
         ev_end(c, ev);
     } else {
         // FP64: one shape (32-body i-tiles; the row order fixes the rounding).
-        // Without the centre-of-mass approximation each pair's r^-3 is
-        // computed once for both directions into per-set matrices (while
-        // they fit PF_BUDGET), then read by the kick in its row order.
+        // Without the centre-of-mass approximation each unordered pair's
+        // force is computed once for both directions into per-set matrices
+        // (while they fit PF_BUDGET), then summed by the kick in its row order.
         L.itile_off = a.k64_off[0];
         L.tile_off = a.tau_off[TAU_VAR_128];
         PairFactors pf{nullptr, nullptr, 0};

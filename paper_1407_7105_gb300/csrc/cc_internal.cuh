@@ -332,12 +332,12 @@ struct OkView {
     const int32_t *row_ptr;  // [total + 1]
     const int32_t *col;      // (row, partner) pairs
 };
-// FP64 kick: the weight G m_j r_ij^-3 of every ordered pair (i, j) of each
-// set, precomputed (k_pair_weights)
+// FP64 kick: the force G m_j r_ij^-3 (x_j - x_i) of every ordered pair (i, j)
+// of each set, precomputed (k_pair_forces)
 struct PairFactors {
-    double *S;               // n x n per set, row-major
+    double *S;               // per set: three n x n matrices (x, y, z), row-major
     const long long *moff;   // per set: offset of its matrix in S
-    int nblocks;             // k_pair_weights' grid: the level's 128-wide triangular tiles
+    int nblocks;             // k_pair_forces' grid: the level's 128-wide triangular tiles
 };
 void launch_kick(const Level &L, const int32_t *label, int nitiles, double G, double eps2, double h,
                  int variant, DevCounters *ctr, cudaStream_t s, const ComView *com = nullptr,

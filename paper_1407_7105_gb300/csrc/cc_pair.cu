@@ -418,6 +418,7 @@ __device__ __forceinline__ void kick_issue(KickSmem<T> &sm, int st, const Level 
 // FP64 pipe sees eight warps per block instead of one thread per body.
 constexpr int KB_T = 32;        // i-tile and j-tile
 constexpr int KB_THREADS = 256;
+constexpr int KB_Q = KB_T * KB_T / KB_THREADS;  // pairs of a tile per thread
 static_assert(K64_VAR_T[0] == KB_T, "the FP64 kick runs on the 32-body i-tile prefix");
 
 struct __align__(16) KickBSmem {
@@ -434,9 +435,9 @@ struct __align__(16) KickBSmem {
 // are left out; their kick is the centre-of-mass one that launch_com_apply
 // adds afterwards.  MODE 2 (OK split): the fast pairs (OkView: each row's
 // partners, sorted) are left out, every other pair of the set kicks.
-// MODE 3: as MODE 0 with each pair's weight G m_j r_ij^-3 read from the
-// matrix k_pair_weights filled (PairFactors) instead of computed; MODE 4: as
-// MODE 2 with the weights read.
+// MODE 3: as MODE 0 with each pair's force G m_j r_ij^-3 (x_j - x_i) read
+// from the matrices k_pair_forces filled (PairFactors) instead of computed;
+// MODE 4: as MODE 2 with the forces read.
 template <int MODE>
 __global__ void __launch_bounds__(KB_THREADS) k_kick64(Level L, const int32_t *label, double G, double eps2, double h,
                                                        DevCounters *ctr, ComView cv, OkView okv, PairFactors pf)
@@ -478,6 +479,24 @@ __global__ void __launch_bounds__(KB_THREADS) k_kick64(Level L, const int32_t *l
     const int r = tid & 31, c = tid >> 5;  // summing threads: row r, component c (tid < 96)
     double acc = 0.0;
     bool ok = true;
+    // MODE 3/4: this thread's pairs (row (tid >> 5) + 8 q, column tid & 31)
+    // of a j-tile, all three components, loaded a tile ahead
+    double fr[3][KB_Q];
+    const long long nn = (long long)n * n;
+    const double *F = PRE ? pf.S + pf.moff[s] : nullptr;
+    auto load_f = [&](int tj) {
+        const int jl0 = tj * KB_T, jn = min(KB_T, n - jl0);
+#pragma unroll
+        for (int q = 0; q < KB_Q; ++q) {
+            const int ii = (tid >> 5) + q * (KB_THREADS / KB_T), jj = tid & 31;
+            const bool v = ii < ni && jj < jn;
+            const long long e = (long long)(il0 + ii) * n + (jl0 + jj);
+            fr[0][q] = v ? F[e] : 0.0;
+            fr[1][q] = v ? F[nn + e] : 0.0;
+            fr[2][q] = v ? F[2 * nn + e] : 0.0;
+        }
+    };
+    if (PRE) load_f(0);
     for (int tj = 0; tj < nt; ++tj) {
         const int st = tj & 1;
         if (tid == 0 && tj + 1 < nt)
@@ -511,29 +530,31 @@ __global__ void __launch_bounds__(KB_THREADS) k_kick64(Level L, const int32_t *l
             __syncthreads();
         }
 #pragma unroll
-        for (int q = 0; q < KB_T * KB_T / KB_THREADS; ++q) {
+        for (int q = 0; q < KB_Q; ++q) {
             const int pidx = tid + q * KB_THREADS, ii = pidx >> 5, jj = pidx & 31;
             bool use = ii < ni && jj < jn && il0 + ii != jl0 + jj && sm.li[ii] != sm.j.lab[st][jj];
             if (COM && use && sm.ci[ii] >= 0 && sm.cj[jj] >= 0)
                 use = cv.far[fo + (long long)sm.ci[ii] * Ks + sm.cj[jj]] == 0;
             if (OKM && use) use = ((sm.okm[ii] >> jj) & 1u) == 0u;
+            if (PRE) {
+                sm.f[0][ii][jj] = use ? fr[0][q] : 0.0;
+                sm.f[1][ii][jj] = use ? fr[1][q] : 0.0;
+                sm.f[2][ii][jj] = use ? fr[2][q] : 0.0;
+                continue;
+            }
             const double dx0 = __dsub_rn(sm.j.col[st][0][jj], sm.xi[0][ii]);
             const double dx1 = __dsub_rn(sm.j.col[st][1][jj], sm.xi[1][ii]);
             const double dx2 = __dsub_rn(sm.j.col[st][2][jj], sm.xi[2][ii]);
-            double w;
-            if (PRE) {
-                // (row i of the set's matrix, column j: consecutive threads, consecutive j)
-                w = (ii < ni && jj < jn) ? pf.S[pf.moff[s] + (long long)(il0 + ii) * n + (jl0 + jj)] : 0.0;
-            } else {
-                const double r2 = __dadd_rn(
-                    __dadd_rn(__dadd_rn(__dmul_rn(dx0, dx0), __dmul_rn(dx1, dx1)), __dmul_rn(dx2, dx2)), eps2);
-                const double rinv3 = __drcp_rn(__dmul_rn(r2, __dsqrt_rn(r2)));
-                w = __dmul_rn(__dmul_rn(G, sm.j.col[st][3][jj]), rinv3);
-            }
+            const double r2 = __dadd_rn(
+                __dadd_rn(__dadd_rn(__dmul_rn(dx0, dx0), __dmul_rn(dx1, dx1)), __dmul_rn(dx2, dx2)), eps2);
+            const double rinv3 = __drcp_rn(__dmul_rn(r2, __dsqrt_rn(r2)));
+            const double w = __dmul_rn(__dmul_rn(G, sm.j.col[st][3][jj]), rinv3);
             sm.f[0][ii][jj] = use ? __dmul_rn(w, dx0) : 0.0;
             sm.f[1][ii][jj] = use ? __dmul_rn(w, dx1) : 0.0;
             sm.f[2][ii][jj] = use ? __dmul_rn(w, dx2) : 0.0;
         }
+        // the next j-tile's forces into registers while this one is summed
+        if (PRE && tj + 1 < nt) load_f(tj + 1);
         __syncthreads();
         if (tid < 3 * KB_T)
             for (int jj = 0; jj < jn; ++jj) acc = __dadd_rn(acc, sm.f[c][r][jj]);
@@ -553,25 +574,27 @@ __global__ void __launch_bounds__(KB_THREADS) k_kick64(Level L, const int32_t *l
     }
 }
 
-// The weight G m_j r_ij^-3 of every ordered pair (i, j) of each set into its
-// n x n matrix at pf.moff[s] (row i, column j; the diagonal unused).  One block per 128-wide
-// triangular tile (TI <= TJ; the grid and prefix L.tile_off of the 128-wide
-// tau tiles), in 32 x 32 sub-tiles: every unordered pair is evaluated once
-// with the kick's own operations (dx = x_j - x_i; the squares make r^2, and
-// so r^-3, the same bits for (j, i)); (G m_j) r^-3 goes to row i directly,
-// (G m_i) r^-3 to row j through shared memory.
+// The force G m_j r_ij^-3 (x_j - x_i) of every ordered pair (i, j) of each
+// set into its three n x n matrices (components x, y, z) at pf.moff[s] (row
+// i, column j; the diagonal unused).  One block per 128-wide triangular tile
+// (TI <= TJ; the grid and prefix L.tile_off of the 128-wide tau tiles), in
+// 32 x 32 sub-tiles: every unordered pair is evaluated once with the kick's
+// own operations (dx = x_j - x_i; the squares make r^2, and so r^-3, the same
+// bits for (j, i), and x_i - x_j = -dx exactly); (G m_j) r^-3 dx goes to row
+// i directly, -(G m_i) r^-3 dx to row j through shared memory.
 constexpr int KR_T = 32, KR_W = 128;
-static_assert(KR_T == KB_T, "the factor sub-tiles are the kick's i-tiles");
-static_assert(KR_W == TAU_VAR_T[TAU_VAR_128], "the factor tiles are the 128-wide tau tiles");
-__global__ void __launch_bounds__(KB_THREADS) k_pair_weights(Level L, double G, double eps2, PairFactors pf)
+static_assert(KR_T == KB_T, "the force sub-tiles are the kick's i-tiles");
+static_assert(KR_W == TAU_VAR_T[TAU_VAR_128], "the force tiles are the 128-wide tau tiles");
+__global__ void __launch_bounds__(KB_THREADS) k_pair_forces(Level L, double G, double eps2, PairFactors pf)
 {
     __shared__ double xi[4][KR_W];  // x, y, z, G m
     __shared__ double xj[4][KR_W];
-    __shared__ double t[KR_T][KR_T + 1];
+    __shared__ double t[3][KR_T][KR_T + 1];
     const int tid = threadIdx.x;
     const int s = find_set(L.tile_off, L.nsets, blockIdx.x);
     int tt = blockIdx.x - L.tile_off[s];
     const int n = L.set_n[s], start = L.set_start[s];
+    const long long nn = (long long)n * n;
     const int nT = (n + KR_W - 1) / KR_W;
     const int TI = tri_tile_row(tt, nT), TJ = TI + tt;
     const int i0 = TI * KR_W, j0 = TJ * KR_W;
@@ -594,7 +617,7 @@ __global__ void __launch_bounds__(KB_THREADS) k_pair_weights(Level L, double G, 
             if (il >= ni || jl >= nj) continue;  // (uniform over the block)
             __syncthreads();  // (the staged rows, or the previous sub-tile's transposed write)
 #pragma unroll
-            for (int q = 0; q < KR_T * KR_T / KB_THREADS; ++q) {
+            for (int q = 0; q < KB_Q; ++q) {
                 const int pidx = tid + q * KB_THREADS, ii = pidx >> 5, jj = pidx & 31;
                 const int gi = il + ii, gj = jl + jj;
                 if (gi < ni && gj < nj && j0 + gj > i0 + gi) {
@@ -604,16 +627,27 @@ __global__ void __launch_bounds__(KB_THREADS) k_pair_weights(Level L, double G, 
                     const double r2 = __dadd_rn(
                         __dadd_rn(__dadd_rn(__dmul_rn(dx0, dx0), __dmul_rn(dx1, dx1)), __dmul_rn(dx2, dx2)), eps2);
                     const double v = __drcp_rn(__dmul_rn(r2, __dsqrt_rn(r2)));
-                    S[(long long)(i0 + gi) * n + (j0 + gj)] = __dmul_rn(xj[3][gj], v);
-                    t[ii][jj] = __dmul_rn(xi[3][gi], v);
+                    const double wij = __dmul_rn(xj[3][gj], v), wji = __dmul_rn(xi[3][gi], v);
+                    const long long e = (long long)(i0 + gi) * n + (j0 + gj);
+                    S[e] = __dmul_rn(wij, dx0);
+                    S[nn + e] = __dmul_rn(wij, dx1);
+                    S[2 * nn + e] = __dmul_rn(wij, dx2);
+                    t[0][ii][jj] = -__dmul_rn(wji, dx0);
+                    t[1][ii][jj] = -__dmul_rn(wji, dx1);
+                    t[2][ii][jj] = -__dmul_rn(wji, dx2);
                 }
             }
             __syncthreads();
 #pragma unroll
-            for (int q = 0; q < KR_T * KR_T / KB_THREADS; ++q) {
+            for (int q = 0; q < KB_Q; ++q) {
                 const int pidx = tid + q * KB_THREADS, jj = pidx >> 5, ii = pidx & 31;
                 const int gi = il + ii, gj = jl + jj;
-                if (gi < ni && gj < nj && j0 + gj > i0 + gi) S[(long long)(j0 + gj) * n + (i0 + gi)] = t[ii][jj];
+                if (gi < ni && gj < nj && j0 + gj > i0 + gi) {
+                    const long long e = (long long)(j0 + gj) * n + (i0 + gi);
+                    S[e] = t[0][ii][jj];
+                    S[nn + e] = t[1][ii][jj];
+                    S[2 * nn + e] = t[2][ii][jj];
+                }
             }
         }
     }
@@ -629,7 +663,7 @@ void launch_kick(const Level &L, const int32_t *label, int nitiles, double G, do
     const OkView no{nullptr, nullptr};
     const PairFactors np{nullptr, nullptr, 0};
     if (okv && okv->row_ptr && pf && pf->S) {
-        k_pair_weights<<<pf->nblocks, KB_THREADS, 0, s>>>(L, G, eps2, *pf);
+        k_pair_forces<<<pf->nblocks, KB_THREADS, 0, s>>>(L, G, eps2, *pf);
         k_kick64<4><<<nitiles, KB_THREADS, 0, s>>>(L, label, G, eps2, h, ctr, nc, *okv, *pf);
         CC_COUNT_LAUNCH(1);
     } else if (okv && okv->row_ptr) {
@@ -637,7 +671,7 @@ void launch_kick(const Level &L, const int32_t *label, int nitiles, double G, do
     } else if (com && com->cl) {
         k_kick64<1><<<nitiles, KB_THREADS, 0, s>>>(L, label, G, eps2, h, ctr, *com, no, np);
     } else if (pf && pf->S) {
-        k_pair_weights<<<pf->nblocks, KB_THREADS, 0, s>>>(L, G, eps2, *pf);
+        k_pair_forces<<<pf->nblocks, KB_THREADS, 0, s>>>(L, G, eps2, *pf);
         k_kick64<3><<<nitiles, KB_THREADS, 0, s>>>(L, label, G, eps2, h, ctr, nc, no, *pf);
         CC_COUNT_LAUNCH(1);
     } else {
