@@ -44,12 +44,14 @@ ETA = 0.03
 TAU_FLOPS = 47   # Eq. tauij as evaluated: 3 sqrt, 6 div, 38 add/sub/mul
 KICK_FLOPS = 25  # one pair force applied to both bodies (Eqs. kickij/kickji): the difference (3), r^2 (6),
                  # r^-3 (sqrt, mul, div: 3), the weights (2 x 2) and the two 3-vector updates (2 x 3); the
-                 # row form evaluates each pair from both sides, which is not credited
+                 # mixed form's row kick evaluates each pair from both sides, which is not credited (the
+                 # FP64 kick evaluates each unordered pair once, k_pair_forces, and sums rows, k_kick64)
 # DRAM bytes (read + write) per launch of the pair kernels, averaged over the
 # launches of one step in an ncu capture (dram__bytes_read.sum +
 # dram__bytes_write.sum): profiles/launches_plummer16384_mixed.md (mixed form)
-# and profiles/k_tau_hook_k_kick64_plummer16384_fp64.md (FP64 form)
-KERNEL_TRAFFIC = {"k_kick_mixed": 391e3, "k_tau_mixed": 850e3, "k_kick64": 434e3, "k_tau_hook": 616e3}
+# and profiles/k_tau_hook_k_kick64_plummer16384_fp64.md (FP64 form; the FP64
+# kick's two kernels per kick call: profiles/launches_plummer16384_fp64.md)
+KERNEL_TRAFFIC = {"k_kick_mixed": 391e3, "k_tau_mixed": 850e3, "k_pair_forces+k_kick64": 3.07e9, "k_tau_hook": 616e3}
 
 
 WORKLOADS = {
@@ -475,14 +477,15 @@ def run_gpu(args, rank, world):
     # both forms' splits run the certified FP32 tau kernel; the kicks are the
     # form's own (FP32 in the mixed form, FP64 in the FP64 form)
     fp32 = fp32 or kname == "tau"
-    kname = "k_tau_mixed" if kname == "tau" else ("k_kick_mixed" if fp32 else "k_kick64")
+    kname = "k_tau_mixed" if kname == "tau" else ("k_kick_mixed" if fp32 else "k_pair_forces+k_kick64")
     achieved = flops / (kms * 1e-3) / 1e12 if kms > 0 else None
     peak = (f32_peak if fp32 else f64_peak) / 1e12
     small_flops = TAU_FLOPS * tm["small_tau_evaluated"] + KICK_FLOPS * tm["small_kick_pairs"]
     small_ach = small_flops / (tm["small_ms"] * 1e-3) / 1e12 if tm["small_ms"] > 0 else None
     roof = {"bound": "alu", "kernel": kname, "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
             "frac": (achieved / peak) if achieved else None, "traffic": KERNEL_TRAFFIC.get(kname),
-            "traffic_note": "bytes per launch from an ncu capture of the same kernel (profiles/)",
+            "traffic_note": ("bytes per kick call (both kernels)" if "+" in kname else "bytes per launch")
+                            + " from an ncu capture of the same kernel (profiles/)",
             "peak_source": ("FP32" if fp32 else "FP64") + " FMA throughput measured by cc_probe_peaks on this GPU "
                            "(MEASURED_PEAKS.json has no FP32/FP64 figure)",
             "algorithmic_flops_per_pair": TAU_FLOPS if kname.startswith("k_tau") else KICK_FLOPS,

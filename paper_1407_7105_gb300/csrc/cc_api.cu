@@ -904,6 +904,11 @@ static int com_prepare(cc_ctx *c, LevelAlloc &a)
 // 16384-body set needs 6.4 GB, a 28000-body one 18.8 GB; larger levels
 // compute the forces in the kick)
 constexpr size_t PF_BUDGET = (size_t)24 << 30;
+// levels with fewer pairs kick with the forces computed in place: the ~24
+// FP64 operations a precomputed pair saves do not pay for the second launch
+// and the offsets' upload (Plummer 256 and 1024: 20-35 % slower per step
+// with the matrices at every level)
+constexpr long long PF_MIN_PAIRS = 1LL << 18;
 
 static int ensure_kpart(cc_ctx *c, int chunks, int fcap)
 {
@@ -927,7 +932,7 @@ static int ensure_kpart(cc_ctx *c, int chunks, int fcap)
 static int pair_factors(cc_ctx *c, LevelAlloc &a, PairFactors &pf)
 {
     pf = PairFactors{nullptr, nullptr, 0};
-    if (a.tau_blocks[TAU_VAR_128] > 0x7fffffff) return CC_OK;
+    if (a.pairs < PF_MIN_PAIRS || a.tau_blocks[TAU_VAR_128] > 0x7fffffff) return CC_OK;
     const int ns = (int)a.h_set_n.size();
     c->h_moff.resize(ns + 1);
     long long tot = 0;
