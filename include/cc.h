@@ -151,8 +151,15 @@ int cc_default_params(cc_params *p);
 
 /* Create a context holding n particles (Sec. 2.1: masses m_i, positions q_i,
  * velocities v_i = p_i/m_i).  m[n], x3[3n], v3[3n] host or device.
- * stream: a cudaStream_t (NULL = default stream).  Errors: CC_E_ARG (n < 1,
- * bad params), CC_E_NONFINITE (non-finite state or m <= 0), CC_E_NOMEM. */
+ * stream: a cudaStream_t (NULL = default stream).  Device memory grows with
+ * the recursion: each depth's level buffers at first use, and for the FP64
+ * kicks (the FP64 form; the mixed form below h_fp64) of levels with at least
+ * 2^18 pairs and no centre-of-mass approximation, the pair forces of every
+ * set (3 n^2 doubles per set; 6.4 GB for a 16384-body set), kept up to 24 GB
+ * for the context's lifetime; when that allocation fails, or a level needs
+ * more, the kick computes the forces in place (same results, no error).
+ * Errors: CC_E_ARG (n < 1, bad params), CC_E_NONFINITE (non-finite state or
+ * m <= 0), CC_E_NOMEM. */
 int cc_init(cc_ctx **out, int64_t n, const double *m, const double *x3,
             const double *v3, const cc_params *p, void *stream);
 
